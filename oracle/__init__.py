@@ -1,0 +1,298 @@
+"""FP64 CPU oracle for the EPID transit Monte Carlo path.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, ``__graft_entry__.smoke()`` and
+the CPU legs of ``bench.py`` (``cpu_baseline`` and ``--impl reference``).  The
+CUDA product path never imports it.  It shares no code with the CUDA library:
+transport, ray tracing and gamma live in ``archer_oracle.c`` (plain C, double
+precision, built with gcc), and the short closed-form steps below (Eq. 1, the
+bilinear k(t,s) lookup of Sec. 3.1, batch statistics) are plain numpy in FP64.
+
+Pins: every function here is checked in ``tests/test_oracle_*.py`` against
+something other than itself (closed forms, numerical integration, brute-force
+enumeration, the paper's Table 1).  The magnitudes of the builder's
+photoelectric, pair and bremsstrahlung fits have no external data to compare
+with in this container: parity unpinned for those magnitudes, while their
+structure (exponents, edge, threshold, mixture rule) is pinned.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "archer_oracle.c"
+_LIB = _HERE / "liborc.so"
+
+MAXL = 8
+COUNTER_NAMES = ("flights_ct", "real_ct", "compton", "photo", "pair", "esteps_ct", "esteps_epid",
+                 "moller", "brem", "primaries_at_epid", "uncollided_at_epid", "lost", "flights_epid",
+                 "electrons", "positrons", "secondary_photons")
+
+
+def build(force: bool = False) -> Path:
+    """Compile the C oracle with gcc (a plain -O2 build, no fast-math)."""
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB.with_suffix(f".{os.getpid()}.tmp.so")
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", str(tmp), str(_SRC),
+                        "-lm", "-lpthread"], check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("hu", C.POINTER(C.c_int16)), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("vox", C.c_double * 3), ("origin", C.c_double * 3),
+        ("n_layers", C.c_int), ("layer_mat", C.c_int * MAXL), ("layer_thick", C.c_double * MAXL),
+        ("layer_rho", C.c_double * MAXL), ("sens_layer", C.c_int), ("npx", C.c_int), ("npy", C.c_int),
+        ("pitch", C.c_double),
+        ("n_seg", C.c_int), ("n_pairs", C.c_int), ("pair_edges", C.POINTER(C.c_double)),
+        ("leaves", C.POINTER(C.c_double)), ("jaws", C.POINTER(C.c_double)), ("mu", C.POINTER(C.c_double)),
+        ("gantry_deg", C.c_double), ("sad", C.c_double), ("sid", C.c_double), ("iso", C.c_double * 3),
+        ("coupled", C.c_int), ("e_max", C.c_double), ("mono_e", C.c_double), ("pcut", C.c_double),
+        ("ecut", C.c_double), ("wcc", C.c_double), ("wcb", C.c_double), ("step_frac", C.c_double),
+        ("n_batches", C.c_int), ("max_steps", C.c_int),
+    ]
+
+
+class _Result(C.Structure):
+    _fields_ = [
+        ("tally", C.POINTER(C.c_double)), ("e_src", C.c_double), ("e_ct", C.c_double),
+        ("e_epid", C.c_double * MAXL), ("e_esc", C.c_double), ("e_lost", C.c_double),
+        ("counters", C.c_uint64 * len(COUNTER_NAMES)),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(str(build()))
+        d, i, u64, u32 = C.c_double, C.c_int, C.c_uint64, C.c_uint32
+        P = C.POINTER
+        _lib.orc_sigma_kn.restype = d
+        _lib.orc_sigma_kn.argtypes = [d]
+        _lib.orc_mu_photon.argtypes = [i, d, P(d)]
+        for name in ("orc_lcol", "orc_sigma_moller", "orc_lrad_soft", "orc_sigma_brem"):
+            getattr(_lib, name).restype = d
+            getattr(_lib, name).argtypes = [i, d, d]
+        _lib.orc_lambda1_inv.restype = d
+        _lib.orc_lambda1_inv.argtypes = [i, d]
+        _lib.orc_wentzel_A.restype = d
+        _lib.orc_wentzel_A.argtypes = [d]
+        _lib.orc_philox.argtypes = [P(u32), P(u32), P(u32)]
+        _lib.orc_child_ordinal.restype = u32
+        _lib.orc_child_ordinal.argtypes = [u32, u32, u32]
+        _lib.orc_uniforms.argtypes = [u64, u64, u32, u32, P(d)]
+        _lib.orc_sample_kn_many.argtypes = [d, u64, u64, P(d), P(d)]
+        _lib.orc_sample_spectrum_many.argtypes = [d, d, u64, u64, P(d)]
+        _lib.orc_sample_moller_many.argtypes = [d, d, u64, u64, P(d)]
+        _lib.orc_sample_ms_many.argtypes = [d, u64, u64, P(d)]
+        _lib.orc_csda_path.restype = d
+        _lib.orc_csda_path.argtypes = [i, d, d, d, d, d, d]
+        _lib.orc_hu_to_rho_mat.argtypes = [i, P(d), P(i)]
+        _lib.orc_run.restype = i
+        _lib.orc_run.argtypes = [P(_Problem), u64, u64, u64, i, P(_Result)]
+        _lib.orc_first_interaction.argtypes = [P(_Problem), d, P(d), P(d), u64, u64, P(C.c_int64),
+                                               P(C.c_int32)]
+        _lib.orc_tmap.argtypes = [P(_Problem), P(C.c_int32), P(C.c_int32), C.c_int64, P(d)]
+        _lib.orc_siddon_ray.restype = d
+        _lib.orc_siddon_ray.argtypes = [P(_Problem), P(d), P(d)]
+        _lib.orc_gamma.restype = d
+        _lib.orc_gamma.argtypes = [P(d), P(d), i, i, d, d, d, d, d, d, P(d)]
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class _Marshalled:
+    """Keeps the numpy buffers alive while the C struct points at them."""
+
+    def __init__(self, problem, physics=None, field=None):
+        ph, ep = problem.phantom, problem.epid
+        fld = field if field is not None else problem.field
+        phy = physics if physics is not None else problem.physics
+        self.hu = np.ascontiguousarray(ph.hu, dtype=np.int16)
+        self.edges = np.ascontiguousarray(fld.pair_edges, dtype=np.float64)
+        self.leaves = np.ascontiguousarray(fld.leaves, dtype=np.float64)
+        self.jaws = np.ascontiguousarray(fld.jaws, dtype=np.float64)
+        self.mu = np.ascontiguousarray(fld.mu, dtype=np.float64)
+        s = _Problem()
+        s.hu = self.hu.ctypes.data_as(C.POINTER(C.c_int16))
+        nz, ny, nx = self.hu.shape
+        s.nx, s.ny, s.nz = nx, ny, nz
+        s.vox[:] = [float(v) for v in ph.vox]
+        s.origin[:] = [float(v) for v in ph.origin]
+        if not 1 <= len(ep.layers) <= MAXL:
+            raise ValueError("EPID needs 1..8 layers")
+        s.n_layers = len(ep.layers)
+        for l, (m, t, r) in enumerate(ep.layers):
+            s.layer_mat[l], s.layer_thick[l], s.layer_rho[l] = int(m), float(t), float(r)
+        s.sens_layer, s.npx, s.npy, s.pitch = ep.sensitive, ep.npx, ep.npy, ep.pitch
+        s.n_seg, s.n_pairs = self.leaves.shape[0], self.leaves.shape[1]
+        s.pair_edges, s.leaves, s.jaws, s.mu = _dp(self.edges), _dp(self.leaves), _dp(self.jaws), _dp(self.mu)
+        s.gantry_deg, s.sad, s.sid = fld.gantry_deg, fld.sad, fld.sid
+        s.iso[:] = [float(v) for v in fld.iso]
+        s.coupled = int(phy.coupled)
+        s.e_max, s.mono_e = phy.e_max, phy.mono_energy
+        s.pcut, s.ecut, s.wcc, s.wcb = phy.photon_cutoff, phy.electron_cutoff, phy.wcc, phy.wcb
+        s.step_frac, s.n_batches, s.max_steps = phy.step_fraction, phy.n_batches, phy.max_steps
+        self.s = s
+
+
+def run(problem, n_histories=None, seed=None, hist_begin=0, threads=None, physics=None, field=None):
+    """Transport `n_histories` histories (ids hist_begin..) and return the tally
+    [B][npy][npx] in MeV, the energy balance and the event counters."""
+    m = _Marshalled(problem, physics, field)
+    n = int(problem.n_histories if n_histories is None else n_histories)
+    sd = int(problem.seed if seed is None else seed)
+    B = m.s.n_batches
+    tally = np.zeros((B, m.s.npy, m.s.npx), dtype=np.float64)
+    r = _Result()
+    r.tally = _dp(tally)
+    nthr = int(threads if threads is not None else (os.cpu_count() or 1))
+    rc = lib().orc_run(C.byref(m.s), sd, int(hist_begin), n, nthr, C.byref(r))
+    if rc != 0:
+        raise RuntimeError(f"orc_run failed with code {rc}")
+    return {
+        "tally": tally,
+        "e_src": r.e_src, "e_ct": r.e_ct, "e_epid": np.array(r.e_epid[:len(problem.epid.layers)]),
+        "e_esc": r.e_esc, "e_lost": r.e_lost,
+        "counters": dict(zip(COUNTER_NAMES, [int(v) for v in r.counters])),
+        "threads": min(nthr, B),
+    }
+
+
+def first_interaction(problem, E, start, direction, n, seed=0):
+    m = _Marshalled(problem)
+    st = np.ascontiguousarray(start, dtype=np.float64)
+    dr = np.ascontiguousarray(direction, dtype=np.float64)
+    vox = np.empty(n, dtype=np.int64)
+    typ = np.empty(n, dtype=np.int32)
+    lib().orc_first_interaction(C.byref(m.s), float(E), _dp(st), _dp(dr), int(seed), int(n),
+                                vox.ctypes.data_as(C.POINTER(C.c_int64)),
+                                typ.ctypes.data_as(C.POINTER(C.c_int32)))
+    return vox, typ
+
+
+def tmap(problem, ix=None, iy=None, field=None):
+    """Radiological thickness (cm) for EPID pixels; all pixels when ix is None."""
+    m = _Marshalled(problem, field=field)
+    if ix is None:
+        yy, xx = np.meshgrid(np.arange(m.s.npy), np.arange(m.s.npx), indexing="ij")
+        ix, iy = xx.ravel(), yy.ravel()
+        shape = (m.s.npy, m.s.npx)
+    else:
+        shape = np.shape(ix)
+    ix = np.ascontiguousarray(ix, dtype=np.int32).ravel()
+    iy = np.ascontiguousarray(iy, dtype=np.int32).ravel()
+    t = np.empty(ix.size, dtype=np.float64)
+    lib().orc_tmap(C.byref(m.s), ix.ctypes.data_as(C.POINTER(C.c_int32)),
+                   iy.ctypes.data_as(C.POINTER(C.c_int32)), ix.size, _dp(t))
+    return t.reshape(shape)
+
+
+def siddon_ray(problem, p1, p2):
+    m = _Marshalled(problem)
+    a = np.ascontiguousarray(p1, dtype=np.float64)
+    b = np.ascontiguousarray(p2, dtype=np.float64)
+    return lib().orc_siddon_ray(C.byref(m.s), _dp(a), _dp(b))
+
+
+def gamma(ref, ev, pixel_mm, dd=0.01, dta_mm=1.0, threshold=0.10, step_mm=None, radius_mm=None):
+    """Global gamma pass rate of `ev` against `ref` (the form used in Sec. 2.3.3)."""
+    ref = np.ascontiguousarray(ref, dtype=np.float64)
+    ev = np.ascontiguousarray(ev, dtype=np.float64)
+    ny, nx = ref.shape
+    h = step_mm if step_mm is not None else min(pixel_mm, dta_mm / 10.0)
+    rad = radius_mm if radius_mm is not None else 3.0 * dta_mm
+    g = np.empty_like(ref)
+    rate = lib().orc_gamma(_dp(ref), _dp(ev), nx, ny, float(pixel_mm), float(dd), float(dta_mm),
+                           float(threshold), float(h), float(rad), _dp(g))
+    return rate, g
+
+
+# --------------------------------------------------------------------------
+# Closed-form steps in numpy (FP64)
+# --------------------------------------------------------------------------
+
+def hu_to_rho_mat(hu):
+    """HU -> (density, material) per the stated curve, through the C routine."""
+    hu = np.asarray(hu).ravel()
+    rho = np.empty(hu.size)
+    mat = np.empty(hu.size, dtype=np.int32)
+    r, mm = C.c_double(), C.c_int()
+    for i, v in enumerate(hu):
+        lib().orc_hu_to_rho_mat(int(v), C.byref(r), C.byref(mm))
+        rho[i], mat[i] = r.value, mm.value
+    return rho, mat
+
+
+def aperture_bbox(field):
+    """Bounding rectangle (a along X, b along Y) of the union of open apertures (Sec. 2.2)."""
+    x0 = y0 = np.inf
+    x1 = y1 = -np.inf
+    for k in range(field.leaves.shape[0]):
+        jx1, jx2, jy1, jy2 = field.jaws[k]
+        for j in range(field.leaves.shape[1]):
+            lx = max(field.leaves[k, j, 0], jx1)
+            rx = min(field.leaves[k, j, 1], jx2)
+            ly = max(field.pair_edges[j], jy1)
+            ry = min(field.pair_edges[j + 1], jy2)
+            if rx > lx and ry > ly and field.mu[k] > 0:
+                x0, x1, y0, y1 = min(x0, lx), max(x1, rx), min(y0, ly), max(y1, ry)
+    return x1 - x0, y1 - y0
+
+
+def effective_field_size(field, literal=False):
+    """Eq. 1.  As printed, s = ab / (2(a+b)) gives 2.5 cm for a 10x10 field, which
+    cannot index Table 1; the reading used is the equivalent square 2ab/(a+b)."""
+    a, b = aperture_bbox(field)
+    return a * b / (2.0 * (a + b)) if literal else 2.0 * a * b / (a + b)
+
+
+def lut_k(lut, t, s):
+    """Bilinear k(t, s) on the node grids, clamped at the edges (Sec. 3.1)."""
+    tn, sn, K = np.asarray(lut.t_nodes, float), np.asarray(lut.s_nodes, float), np.asarray(lut.k, float)
+    t = np.clip(np.asarray(t, float), tn[0], tn[-1])
+    s = float(np.clip(s, sn[0], sn[-1]))
+    it = np.clip(np.searchsorted(tn, t, side="right") - 1, 0, tn.size - 2)
+    js = int(np.clip(np.searchsorted(sn, s, side="right") - 1, 0, sn.size - 2))
+    ft = (t - tn[it]) / (tn[it + 1] - tn[it])
+    fs = (s - sn[js]) / (sn[js + 1] - sn[js])
+    k00, k01 = K[js, it], K[js, it + 1]
+    k10, k11 = K[js + 1, it], K[js + 1, it + 1]
+    return (1 - fs) * ((1 - ft) * k00 + ft * k01) + fs * ((1 - ft) * k10 + ft * k11)
+
+
+def batch_counts(n_hist, B, hist_begin=0):
+    """Number of history ids h in [hist_begin, hist_begin+n) with h mod B == b."""
+    ids = np.arange(B)
+    first = (ids - hist_begin) % B
+    return np.where(first < n_hist, (n_hist - first + B - 1) // B, 0).astype(np.int64)
+
+
+def dose_stats(tally_mev, n_hist, epid, hist_begin=0):
+    """Per-history dose (Gy) in the sensitive layer, its batch standard error and
+    the mean relative uncertainty over pixels above half the maximum."""
+    tally_mev = np.asarray(tally_mev, dtype=np.float64)
+    B = tally_mev.shape[0]
+    _, thick, rho = epid.layers[epid.sensitive]
+    mass_kg = rho * epid.pitch * epid.pitch * thick * 1e-3
+    conv = 1.602176634e-13 / mass_kg
+    nb = batch_counts(n_hist, B, hist_begin).astype(np.float64)
+    mean = tally_mev.sum(axis=0) / n_hist * conv
+    with np.errstate(invalid="ignore", divide="ignore"):
+        dbat = tally_mev / nb[:, None, None] * conv
+    sigma = np.sqrt(((dbat - mean[None]) ** 2).sum(axis=0) / (B * (B - 1)))
+    sel = mean > 0.5 * mean.max() if mean.max() > 0 else np.zeros_like(mean, dtype=bool)
+    u = float(np.mean(sigma[sel] / mean[sel])) if sel.any() else float("nan")
+    return mean, sigma, u

@@ -1,0 +1,1163 @@
+/*
+ * FP64 CPU oracle for the EPID transit Monte Carlo path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  It shares
+ * no code, header, table or constant with the CUDA path: every formula below is
+ * evaluated directly in double precision from the written model, with no
+ * tabulation, blocking or reordering beyond what the model states.
+ *
+ * What it computes (paper, Sec. 2.1): photons from an MLC-shaped point source
+ * (Sec. 2.1.1; the paper's phase-space source is replaced by an ideal aperture)
+ * are transported through a CT-derived voxel patient (Sec. 2.1.2: photoelectric,
+ * Compton, pair production; Class II condensed-history electrons with hard
+ * collisions and CSDA soft losses; cutoffs 10 keV photons / 200 keV electrons)
+ * into a multi-layer EPID slab (Sec. 2.1.3) whose sensitive-layer energy is
+ * tallied per pixel.  The paper gives the model class but no cross sections;
+ * the parameterised fits, the HU curve and the sampling algorithms below are
+ * the readings of the paper this project states, with the draw order fixed so
+ * that a second implementation fed the same Philox keys replays each history.
+ *
+ * Parity pins: each sampler and cross section has an external check in the
+ * CPU test suite (closed forms, numerical integration, brute-force
+ * enumeration).  The absolute values of the builder's photoelectric, pair and
+ * bremsstrahlung fits are model definitions with no external data to compare
+ * against ("parity unpinned" for their magnitudes; their structure is pinned).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define O_PI 3.14159265358979323846
+#define O_RE 2.8179403262e-13      /* classical electron radius, cm */
+#define O_MC2 0.51099895           /* electron rest energy, MeV */
+#define O_NA 6.02214076e23         /* Avogadro, 1/mol */
+#define O_ALPHA (1.0 / 137.035999084)
+#define O_PE_A 4.56e-33            /* photoelectric fit: a Z^4.5 E^-3.2, cm^2 (E in MeV) */
+#define O_PE_N 4.5
+#define O_PE_P 3.2
+#define O_GD_EK 0.05024            /* Gd K edge, MeV */
+#define O_GD_JUMP 5.3              /* Gd K-edge jump ratio */
+#define O_PAIR_C 2.57e-27          /* pair fit: C Z(Z+1) (1-2mc^2/E)^4, cm^2 */
+#define O_BREM_B 4.65e-27          /* bremsstrahlung fit: dsigma/dk = B Z(Z+1)/k, cm^2 */
+#define O_ES 21.2                  /* Rossi scattering energy, MeV */
+#define O_TSTOP 1e-6               /* an electron stops once T <= cutoff + this, MeV */
+#define O_NMAT 7
+#define O_MAXL 8
+
+/* ------------------------------------------------------------------------ */
+/* Materials: elemental mass fractions and mean excitation energies.         */
+/* ------------------------------------------------------------------------ */
+typedef struct { int Z; double A; double w; } o_elem;
+typedef struct { int n; o_elem e[10]; double I_eV; } o_matdef;
+
+static const o_matdef O_MATS[O_NMAT] = {
+    /* 0 dry air */
+    {4, {{7, 14.007, 0.755268}, {8, 15.999, 0.231781}, {18, 39.948, 0.012827}, {6, 12.011, 0.000124}}, 85.7},
+    /* 1 lung (ICRU-44 composition) */
+    {9, {{1, 1.008, 0.103}, {6, 12.011, 0.105}, {7, 14.007, 0.031}, {8, 15.999, 0.749}, {11, 22.990, 0.002},
+         {15, 30.974, 0.002}, {16, 32.06, 0.003}, {17, 35.45, 0.003}, {19, 39.098, 0.002}}, 75.3},
+    /* 2 water / soft tissue */
+    {2, {{1, 1.008, 0.111894}, {8, 15.999, 0.888106}}, 75.0},
+    /* 3 cortical bone (ICRU-44 composition) */
+    {9, {{1, 1.008, 0.034}, {6, 12.011, 0.155}, {7, 14.007, 0.042}, {8, 15.999, 0.435}, {11, 22.990, 0.001},
+         {12, 24.305, 0.002}, {15, 30.974, 0.103}, {16, 32.06, 0.003}, {20, 40.078, 0.225}}, 106.4},
+    /* 4 copper */
+    {1, {{29, 63.546, 1.0}}, 322.0},
+    /* 5 Gd2O2S, mass fractions from molar masses */
+    {3, {{64, 157.25, 0.830790}, {8, 15.999, 0.084524}, {16, 32.06, 0.084686}}, 437.0},
+    /* 6 amorphous silicon */
+    {1, {{14, 28.085, 1.0}}, 173.0},
+};
+
+/* ------------------------------------------------------------------------ */
+/* Photon cross sections, cm^2/g.                                            */
+/* ------------------------------------------------------------------------ */
+
+/* Klein-Nishina total cross section per free electron, cm^2 (closed form). */
+double orc_sigma_kn(double E) {
+    double k = E / O_MC2;
+    double a = 1.0 + 2.0 * k;
+    double L = log(a);
+    double t1 = (1.0 + k) / (k * k) * (2.0 * (1.0 + k) / a - L / k);
+    double t2 = L / (2.0 * k);
+    double t3 = (1.0 + 3.0 * k) / (a * a);
+    return 2.0 * O_PI * O_RE * O_RE * (t1 + t2 - t3);
+}
+
+/* Per-gram partial attenuation coefficients of material m at photon energy E.
+ * out[0] Compton, out[1] photoelectric, out[2] pair. */
+void orc_mu_photon(int m, double E, double out[3]) {
+    const o_matdef* md = &O_MATS[m];
+    double zA = 0.0, pe = 0.0, zz = 0.0;
+    for (int i = 0; i < md->n; i++) {
+        const o_elem* el = &md->e[i];
+        zA += el->w * el->Z / el->A;
+        double pz = el->w / el->A * pow((double)el->Z, O_PE_N);
+        if (el->Z == 64 && E < O_GD_EK) pz /= O_GD_JUMP;
+        pe += pz;
+        zz += el->w * el->Z * (el->Z + 1.0) / el->A;
+    }
+    out[0] = O_NA * zA * orc_sigma_kn(E);
+    out[1] = O_NA * O_PE_A * pow(E, -O_PE_P) * pe;
+    double thr = 2.0 * O_MC2;
+    out[2] = (E > thr) ? O_NA * O_PAIR_C * zz * pow(1.0 - thr / E, 4.0) : 0.0;
+}
+
+static double mu_total(int m, double E) {
+    double p[3];
+    orc_mu_photon(m, E, p);
+    return p[0] + p[1] + p[2];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Electron quantities (per gram).                                           */
+/* ------------------------------------------------------------------------ */
+static double mat_zA(int m) {
+    double s = 0.0;
+    for (int i = 0; i < O_MATS[m].n; i++) s += O_MATS[m].e[i].w * O_MATS[m].e[i].Z / O_MATS[m].e[i].A;
+    return s;
+}
+static double mat_zz(int m) {
+    double s = 0.0;
+    for (int i = 0; i < O_MATS[m].n; i++) {
+        const o_elem* el = &O_MATS[m].e[i];
+        s += el->w * el->Z * (el->Z + 1.0) / el->A;
+    }
+    return s;
+}
+/* inverse radiation length, cm^2/g: 4 alpha r_e^2 N_A sum (w/A) Z(Z+1) ln(183 Z^-1/3) */
+static double mat_x0inv(int m) {
+    double s = 0.0;
+    for (int i = 0; i < O_MATS[m].n; i++) {
+        const o_elem* el = &O_MATS[m].e[i];
+        s += el->w / el->A * el->Z * (el->Z + 1.0) * log(183.0 * pow((double)el->Z, -1.0 / 3.0));
+    }
+    return 4.0 * O_ALPHA * O_RE * O_RE * O_NA * s;
+}
+
+/* Restricted collision stopping power (Bethe, soft Moller losses below wcc,
+ * no density effect), MeV cm^2/g. */
+double orc_lcol(int m, double T, double wcc) {
+    double tau = T / O_MC2, g = tau + 1.0, b2 = 1.0 - 1.0 / (g * g);
+    double D = fmin(wcc, 0.5 * T) / O_MC2;
+    double Imc = O_MATS[m].I_eV * 1e-6 / O_MC2;
+    double F = -1.0 - b2 + log((tau - D) * D) + tau / (tau - D)
+               + (0.5 * D * D + (2.0 * tau + 1.0) * log(1.0 - D / tau)) / (g * g);
+    double pref = 2.0 * O_PI * O_RE * O_RE * O_MC2 * O_NA * mat_zA(m) / b2;
+    return pref * (log(2.0 * (tau + 2.0) / (Imc * Imc)) + F);
+}
+
+/* Bremsstrahlung strength A_m = N_A B sum (w/A) Z(Z+1), cm^2/g. */
+static double brem_A(int m) { return O_NA * O_BREM_B * mat_zz(m); }
+
+/* Soft (k < wcb) radiative stopping power, MeV cm^2/g. */
+double orc_lrad_soft(int m, double T, double wcb) { return brem_A(m) * fmin(wcb, T); }
+
+/* Hard Moller cross section (secondary above wcc), cm^2/g. */
+double orc_sigma_moller(int m, double T, double wcc) {
+    if (T <= 2.0 * wcc) return 0.0;
+    double tau = T / O_MC2, g = tau + 1.0, b2 = 1.0 - 1.0 / (g * g);
+    double ec = wcc / T, c = tau / g, bb = (2.0 * tau + 1.0) / (g * g);
+    double br = 1.0 / ec - 1.0 / (1.0 - ec) + (0.5 - ec) * c * c - bb * log((1.0 - ec) / ec);
+    return O_NA * mat_zA(m) * 2.0 * O_PI * O_RE * O_RE * O_MC2 / (b2 * T) * br;
+}
+
+/* Hard bremsstrahlung cross section (photon above wcb), cm^2/g. */
+double orc_sigma_brem(int m, double T, double wcb) { return (T > wcb) ? brem_A(m) * log(T / wcb) : 0.0; }
+
+/* Inverse first transport mean free path (Rossi scattering power), cm^2/g. */
+double orc_lambda1_inv(int m, double T) {
+    double pc2 = T * (T + 2.0 * O_MC2);
+    double b2p2 = pc2 * pc2 / ((T + O_MC2) * (T + O_MC2));
+    return 0.5 * O_ES * O_ES * mat_x0inv(m) / b2p2;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and the per-particle    */
+/* draw stream.  Draw d of particle (hist h, ordinal o) is word d mod 4 of   */
+/* Philox(counter = (d div 4, o, h_lo, h_hi), key = (seed_lo, seed_hi)),     */
+/* mapped to ((u >> 8) + 0.5) 2^-24.                                         */
+/* ------------------------------------------------------------------------ */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; r++) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* MurmurHash3 32-bit finaliser, used to derive secondary ordinals. */
+static uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16; h *= 0x85EBCA6Bu; h ^= h >> 13; h *= 0xC2B2AE35u; h ^= h >> 16;
+    return h;
+}
+uint32_t orc_child_ordinal(uint32_t parent, uint32_t draws, uint32_t slot) {
+    return fmix32(parent * 0x85EBCA6Bu + (draws * 8u + slot + 1u));
+}
+
+typedef struct {
+    uint32_t key[2];
+    uint32_t ord, hlo, hhi;
+    uint32_t d;
+    uint32_t cblk; int cvalid; uint32_t cbuf[4];
+} o_rng;
+
+static double rng_u(o_rng* r) {
+    uint32_t blk = r->d >> 2, w = r->d & 3u;
+    if (!r->cvalid || r->cblk != blk) {
+        uint32_t ctr[4] = {blk, r->ord, r->hlo, r->hhi};
+        orc_philox(ctr, r->key, r->cbuf);
+        r->cblk = blk; r->cvalid = 1;
+    }
+    r->d++;
+    return ((double)(r->cbuf[w] >> 8) + 0.5) * (1.0 / 16777216.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Samplers.                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Source spectrum: E = Emax X, X ~ Beta(3/2, 7/2) drawn exactly as
+ * G1/(G1+G2) with G1 ~ Gamma(3/2) = Exp + N^2/2 and G2 ~ Gamma(7/2) =
+ * Exp+Exp+Exp + N'^2/2, the two normals from one Box-Muller pair.  Six draws
+ * per attempt (u_a, u_b, u_c, u_d, u_1, u_2); attempts below the photon
+ * cutoff are redrawn. */
+static double sample_spectrum(o_rng* r, double emax, double ecut) {
+    for (;;) {
+        double ua = rng_u(r), ub = rng_u(r), uc = rng_u(r), ud = rng_u(r);
+        double u1 = rng_u(r), u2 = rng_u(r);
+        double L = -log(u1);
+        double c = cos(2.0 * O_PI * u2);
+        double g1 = -log(ua) + L * c * c;
+        double g2 = -log(ub * uc * ud) + L * (1.0 - c * c);
+        double E = emax * g1 / (g1 + g2);
+        if (E >= ecut) return E;
+    }
+}
+
+/* Klein-Nishina: composition-rejection on eps = E'/E (three draws per attempt),
+ * then returns eps and cos(theta). */
+static void sample_kn(o_rng* r, double E, double* eps_out, double* cos_out) {
+    double k = E / O_MC2;
+    double e0 = 1.0 / (1.0 + 2.0 * k);
+    double a1 = log(1.0 + 2.0 * k);
+    double a2 = 0.5 * (1.0 - e0 * e0);
+    for (;;) {
+        double r1 = rng_u(r), r2 = rng_u(r), r3 = rng_u(r);
+        double eps;
+        if (r1 * (a1 + a2) < a1) eps = exp(-a1 * r2);
+        else eps = sqrt(e0 * e0 + (1.0 - e0 * e0) * r2);
+        double t = (1.0 - eps) / (k * eps);
+        double s2 = t * (2.0 - t);
+        double g = 1.0 - eps * s2 / (1.0 + eps * eps);
+        if (r3 < g) { *eps_out = eps; *cos_out = 1.0 - t; return; }
+    }
+}
+
+/* Moller: eps = W/T on [wcc/T, 1/2] from 1/eps^2, rejection on the bracket. */
+static double sample_moller_eps(o_rng* r, double T, double wcc) {
+    double tau = T / O_MC2, g = tau + 1.0;
+    double ec = wcc / T, c = tau / g, bb = (2.0 * tau + 1.0) / (g * g);
+    double gmax = 2.0 - bb + 0.25 * c * c;
+    for (;;) {
+        double r1 = rng_u(r), r2 = rng_u(r);
+        double eps = ec / (1.0 - r1 * (1.0 - 2.0 * ec));
+        double x = eps / (1.0 - eps);
+        double gv = 1.0 + x * x + c * c * eps * eps - bb * x;
+        if (r2 * gmax < gv) return eps;
+    }
+}
+
+/* Mean of mu=(1-cos)/2 under the screened-Rutherford law with screening A. */
+static double wentzel_mean(double A) {
+    if (A > 100.0) {
+        double x = 1.0 / A, s = 0.0, xn = 1.0;
+        for (int n = 1; n <= 10; n++) { s += ((n & 1) ? 1.0 : -1.0) * xn / (n * (n + 1.0)); xn *= x; }
+        return s;
+    }
+    return A * ((1.0 + A) * log1p(1.0 / A) - 1.0);
+}
+
+/* Screening parameter A such that <1-cos> = 1 - exp(-G); A<0 flags isotropic. */
+double orc_wentzel_A(double G) {
+    if (G <= 0.0) return 0.0;
+    double m = -0.5 * expm1(-G);
+    if (0.5 - m < 1e-6) return -1.0;
+    double y = (m < 0.3) ? log(m / fmax(log(1.0 / m) - 1.0, 1.0)) : log(1.0 / (6.0 * (0.5 - m)));
+    for (int it = 0; it < 200; it++) {
+        double A = exp(y);
+        double f = wentzel_mean(A) - m;
+        double dm = (A > 100.0) ? (1.0 / (6.0 * A * A) - 1.0 / (6.0 * A * A * A)) : ((1.0 + 2.0 * A) * log1p(1.0 / A) - 2.0);
+        double step = f / (A * dm);
+        if (step > 2.0) step = 2.0;
+        if (step < -2.0) step = -2.0;
+        y -= step;
+        if (fabs(step) < 1e-13) break;
+    }
+    return exp(y);
+}
+
+static double sample_ms_mu(double A, double xi) {
+    if (A < 0.0) return xi;            /* isotropic */
+    return A * xi / (1.0 - xi + A);
+}
+
+/* Rotate unit direction u by polar cos ct and azimuth phi. */
+static void rotate(double u[3], double ct, double phi) {
+    double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double cp = cos(phi), sp = sin(phi);
+    double w = u[2];
+    if (fabs(w) > 0.99999999) {
+        double sg = (w > 0) ? 1.0 : -1.0;
+        u[0] = st * cp; u[1] = st * sp; u[2] = sg * ct;
+    } else {
+        double tmp = sqrt(1.0 - w * w);
+        double nu = u[0] * ct + st * (u[0] * w * cp - u[1] * sp) / tmp;
+        double nv = u[1] * ct + st * (u[1] * w * cp + u[0] * sp) / tmp;
+        double nw = w * ct - tmp * st * cp;
+        u[0] = nu; u[1] = nv; u[2] = nw;
+    }
+    double n = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    u[0] /= n; u[1] /= n; u[2] /= n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Problem description and results (mirrored by the Python wrapper).         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const int16_t* hu; int nx, ny, nz; double vox[3]; double origin[3];
+    int n_layers; int layer_mat[O_MAXL]; double layer_thick[O_MAXL]; double layer_rho[O_MAXL];
+    int sens_layer; int npx, npy; double pitch;
+    int n_seg, n_pairs; const double* pair_edges; const double* leaves; const double* jaws; const double* mu;
+    double gantry_deg, sad, sid; double iso[3];
+    int coupled; double e_max, mono_e, pcut, ecut, wcc, wcb, step_frac; int n_batches; int max_steps;
+} orc_problem;
+
+enum { C_FLIGHTS_CT, C_REAL_CT, C_COMPTON, C_PHOTO, C_PAIR, C_ESTEP_CT, C_ESTEP_EPID, C_MOLLER, C_BREM,
+       C_PRIM_EPID, C_UNCOLLIDED, C_LOST, C_FLIGHTS_EPID, C_ELECTRONS, C_POSITRONS, C_PHOTONS2, C_NCOUNT };
+
+typedef struct {
+    double* tally;               /* [B][npy][npx] MeV */
+    double e_src, e_ct, e_epid[O_MAXL], e_esc, e_lost;
+    uint64_t counters[C_NCOUNT];
+} orc_result;
+
+/* ------------------------------------------------------------------------ */
+/* Transport.                                                                 */
+/* ------------------------------------------------------------------------ */
+enum { Z_CT = 0, Z_EPID = 1 };
+enum { P_PHOTON = 0, P_ELECTRON = 1, P_POSITRON = 2 };
+
+typedef struct {
+    int type, zone;
+    double x[3], u[3], E;
+    int cell[3];                 /* CT voxel index, or [0] = EPID layer */
+    int collided;                /* primaries only: has had a real interaction */
+    o_rng rng;
+} o_part;
+
+typedef struct {
+    const orc_problem* P;
+    double ex[3], ey[3], ez[3];       /* beam-frame axes in patient coordinates */
+    double zplane[O_MAXL + 1];        /* EPID layer planes, beam-frame Z, top first */
+    double half_w[2];                 /* EPID lateral half widths */
+    double rho_max[4];                /* per CT material */
+    int mat_present[4];
+    double* rect;                     /* source rectangles: x0,x1,y0,y1 */
+    double* cdf;                      /* cumulative weight */
+    int n_rect;
+    /* per worker */
+    double* tally; double e_src, e_ct, e_epid[O_MAXL], e_esc, e_lost;
+    uint64_t cnt[C_NCOUNT];
+    uint64_t hist;
+    o_part* stack; int sp, cap;
+} o_ctx;
+
+/* HU -> density (g/cm^3) and material (stated reading of the curve in Sec. 2.1.2). */
+void orc_hu_to_rho_mat(int hu, double* rho, int* mat) {
+    if (hu < -1024) hu = -1024;
+    if (hu > 3071) hu = 3071;
+    double r = (hu <= 0) ? 1.0 + hu / 1000.0 : 1.0 + 0.6 * hu / 1000.0;
+    if (r < 0.001205) r = 0.001205;
+    *rho = r;
+    *mat = (hu < -900) ? 0 : (hu < -200) ? 1 : (hu < 300) ? 2 : 3;
+}
+
+static void to_patient(const o_ctx* c, const double b[3], double p[3]) {
+    for (int i = 0; i < 3; i++) p[i] = c->P->iso[i] + b[0] * c->ex[i] + b[1] * c->ey[i] + b[2] * c->ez[i];
+}
+static void to_patient_dir(const o_ctx* c, const double b[3], double p[3]) {
+    for (int i = 0; i < 3; i++) p[i] = b[0] * c->ex[i] + b[1] * c->ey[i] + b[2] * c->ez[i];
+}
+static void to_beam(const o_ctx* c, const double p[3], double b[3]) {
+    double d[3] = {p[0] - c->P->iso[0], p[1] - c->P->iso[1], p[2] - c->P->iso[2]};
+    b[0] = d[0] * c->ex[0] + d[1] * c->ex[1] + d[2] * c->ex[2];
+    b[1] = d[0] * c->ey[0] + d[1] * c->ey[1] + d[2] * c->ey[2];
+    b[2] = d[0] * c->ez[0] + d[1] * c->ez[1] + d[2] * c->ez[2];
+}
+static void to_beam_dir(const o_ctx* c, const double p[3], double b[3]) {
+    b[0] = p[0] * c->ex[0] + p[1] * c->ex[1] + p[2] * c->ex[2];
+    b[1] = p[0] * c->ey[0] + p[1] * c->ey[1] + p[2] * c->ey[2];
+    b[2] = p[0] * c->ez[0] + p[1] * c->ez[1] + p[2] * c->ez[2];
+}
+
+static void push(o_ctx* c, const o_part* p) {
+    if (c->sp == c->cap) {
+        c->cap = c->cap ? 2 * c->cap : 64;
+        c->stack = (o_part*)realloc(c->stack, sizeof(o_part) * c->cap);
+    }
+    c->stack[c->sp++] = *p;
+}
+
+static double rest_extra(const o_part* p) { return (p->type == P_POSITRON) ? 2.0 * O_MC2 : 0.0; }
+
+static void deposit(o_ctx* c, const o_part* p, const double pos[3], int layer, double dE) {
+    if (dE == 0.0) return;
+    if (p->zone == Z_CT) { c->e_ct += dE; return; }
+    c->e_epid[layer] += dE;
+    const orc_problem* P = c->P;
+    if (layer != P->sens_layer) return;
+    int ix = (int)floor((pos[0] + c->half_w[0]) / P->pitch);
+    int iy = (int)floor((pos[1] + c->half_w[1]) / P->pitch);
+    if (ix < 0) ix = 0;
+    if (ix >= P->npx) ix = P->npx - 1;
+    if (iy < 0) iy = 0;
+    if (iy >= P->npy) iy = P->npy - 1;
+    int b = (int)(c->hist % (uint64_t)P->n_batches);
+    c->tally[((size_t)b * P->npy + iy) * P->npx + ix] += dE;
+}
+
+static double sigma_max_ct(const o_ctx* c, double E) {
+    double s = 0.0;
+    for (int m = 0; m < 4; m++)
+        if (c->mat_present[m]) s = fmax(s, c->rho_max[m] * mu_total(m, E));
+    return s;
+}
+
+static int ct_voxel(const o_ctx* c, const double x[3], int idx[3]) {
+    const orc_problem* P = c->P;
+    int n[3] = {P->nx, P->ny, P->nz};
+    for (int a = 0; a < 3; a++) {
+        idx[a] = (int)floor((x[a] - P->origin[a]) / P->vox[a]);
+        if (idx[a] < 0 || idx[a] >= n[a]) return 0;
+    }
+    return 1;
+}
+
+static void ct_props(const o_ctx* c, const int idx[3], double* rho, int* mat) {
+    const orc_problem* P = c->P;
+    int hu = P->hu[((size_t)idx[2] * P->ny + idx[1]) * P->nx + idx[0]];
+    orc_hu_to_rho_mat(hu, rho, mat);
+}
+
+/* Send a particle that has left the CT (or never entered it) across the
+ * vacuum gap: into the EPID's top layer if its line meets the detector face,
+ * otherwise out of the world. */
+static void transfer_to_epid(o_ctx* c, o_part* p) {
+    double b[3], ub[3];
+    to_beam(c, p->x, b);
+    to_beam_dir(c, p->u, ub);
+    double Eexit = p->E + rest_extra(p);
+    if (ub[2] >= 0.0) { c->e_esc += Eexit; return; }
+    double t = (c->zplane[0] - b[2]) / ub[2];
+    if (t < 0.0) { c->e_esc += Eexit; return; }
+    double X = b[0] + t * ub[0], Y = b[1] + t * ub[1];
+    if (!(fabs(X) < c->half_w[0] && fabs(Y) < c->half_w[1])) { c->e_esc += Eexit; return; }
+    p->zone = Z_EPID;
+    p->x[0] = X; p->x[1] = Y; p->x[2] = c->zplane[0];
+    p->u[0] = ub[0]; p->u[1] = ub[1]; p->u[2] = ub[2];
+    p->cell[0] = 0;
+    if (p->type == P_PHOTON && p->rng.ord == 0 && !p->collided) c->cnt[C_UNCOLLIDED]++;
+    if (p->type == P_PHOTON && p->rng.ord == 0) c->cnt[C_PRIM_EPID]++;
+    push(c, p);
+}
+
+static void enter_world(o_ctx* c, o_part* p) {
+    /* p is a photon at the source, patient frame.  Move it to the CT box entry
+     * if its line meets the box, else send it to the EPID. */
+    const orc_problem* P = c->P;
+    double lo[3], hi[3];
+    int n[3] = {P->nx, P->ny, P->nz};
+    double t0 = -INFINITY, t1 = INFINITY;
+    for (int a = 0; a < 3; a++) {
+        lo[a] = P->origin[a];
+        hi[a] = P->origin[a] + n[a] * P->vox[a];
+        if (p->u[a] != 0.0) {
+            double ta = (lo[a] - p->x[a]) / p->u[a], tb = (hi[a] - p->x[a]) / p->u[a];
+            if (ta > tb) { double t = ta; ta = tb; tb = t; }
+            if (ta > t0) t0 = ta;
+            if (tb < t1) t1 = tb;
+        } else if (p->x[a] < lo[a] || p->x[a] > hi[a]) {
+            t0 = INFINITY;
+        }
+    }
+    if (t0 < t1 && t1 > 0.0) {
+        double t = fmax(t0, 0.0);
+        for (int a = 0; a < 3; a++) p->x[a] += t * p->u[a];
+        p->zone = Z_CT;
+        push(c, p);
+    } else {
+        transfer_to_epid(c, p);
+    }
+}
+
+static void make_child(const o_part* parent, o_part* ch, int type, uint32_t slot) {
+    memset(ch, 0, sizeof(*ch));
+    ch->type = type;
+    ch->zone = parent->zone;
+    ch->cell[0] = parent->cell[0]; ch->cell[1] = parent->cell[1]; ch->cell[2] = parent->cell[2];
+    ch->x[0] = parent->x[0]; ch->x[1] = parent->x[1]; ch->x[2] = parent->x[2];
+    ch->collided = 1;
+    ch->rng = parent->rng;
+    ch->rng.ord = orc_child_ordinal(parent->rng.ord, parent->rng.d, slot);
+    ch->rng.d = 0;
+    ch->rng.cvalid = 0;
+}
+
+/* Annihilation at rest: two mc^2 photons, isotropic, back to back; they are
+ * the parent's children with slots 0 and 1 after its two direction draws. */
+static void annihilate(o_ctx* c, o_part* parent) {
+    double ct = 2.0 * rng_u(&parent->rng) - 1.0;
+    double ph = 2.0 * O_PI * rng_u(&parent->rng);
+    double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double d[3] = {st * cos(ph), st * sin(ph), ct};
+    for (int k = 0; k < 2; k++) {
+        o_part g;
+        make_child(parent, &g, P_PHOTON, (uint32_t)k);
+        double sg = k ? -1.0 : 1.0;
+        g.u[0] = sg * d[0]; g.u[1] = sg * d[1]; g.u[2] = sg * d[2];
+        g.E = O_MC2;
+        c->cnt[C_PHOTONS2]++;
+        push(c, &g);
+    }
+}
+
+static int layer_mat(const o_ctx* c, int l) { return c->P->layer_mat[l]; }
+
+/* Emit an electron or positron of kinetic energy T created by `parent`, or
+ * deposit it when transport is off or T is at the cutoff. */
+static void emit_charged(o_ctx* c, o_part* parent, int type, double T, const double dir[3], uint32_t slot,
+                         int layer) {
+    const orc_problem* P = c->P;
+    if (P->coupled && T > P->ecut + O_TSTOP) {
+        o_part e;
+        make_child(parent, &e, type, slot);
+        e.u[0] = dir[0]; e.u[1] = dir[1]; e.u[2] = dir[2];
+        e.E = T;
+        c->cnt[type == P_POSITRON ? C_POSITRONS : C_ELECTRONS]++;
+        push(c, &e);
+    } else {
+        deposit(c, parent, parent->x, layer, T);
+    }
+}
+
+/* A real photon interaction at p->x in material m.  Returns 1 if the photon
+ * survives (Compton above the cutoff), 0 if it is absorbed. */
+static int photon_interact(o_ctx* c, o_part* p, int m, int layer) {
+    const orc_problem* P = c->P;
+    double mu[3];
+    orc_mu_photon(m, p->E, mu);
+    double tot = mu[0] + mu[1] + mu[2];
+    double xi = rng_u(&p->rng);
+    p->collided = 1;
+    if (xi * tot < mu[0]) {
+        c->cnt[C_COMPTON]++;
+        double eps, ct;
+        sample_kn(&p->rng, p->E, &eps, &ct);
+        double phi = 2.0 * O_PI * rng_u(&p->rng);
+        double E0 = p->E, E1 = eps * E0;
+        double u0[3] = {p->u[0], p->u[1], p->u[2]};
+        rotate(p->u, ct, phi);
+        double T = E0 - E1;
+        double pe[3] = {E0 * u0[0] - E1 * p->u[0], E0 * u0[1] - E1 * p->u[1], E0 * u0[2] - E1 * p->u[2]};
+        double n = sqrt(pe[0] * pe[0] + pe[1] * pe[1] + pe[2] * pe[2]);
+        if (n > 0.0) { pe[0] /= n; pe[1] /= n; pe[2] /= n; } else { pe[0] = u0[0]; pe[1] = u0[1]; pe[2] = u0[2]; }
+        emit_charged(c, p, P_ELECTRON, T, pe, 0, layer);
+        p->E = E1;
+        if (p->E < P->pcut) { deposit(c, p, p->x, layer, p->E); return 0; }
+        return 1;
+    } else if (xi * tot < mu[0] + mu[1]) {
+        c->cnt[C_PHOTO]++;
+        emit_charged(c, p, P_ELECTRON, p->E, p->u, 0, layer);
+        return 0;
+    } else {
+        c->cnt[C_PAIR]++;
+        double avail = p->E - 2.0 * O_MC2;
+        double xu = rng_u(&p->rng);
+        double Tm = xu * avail, Tp = avail - Tm;
+        if (P->coupled) {
+            emit_charged(c, p, P_ELECTRON, Tm, p->u, 0, layer);
+            if (Tp > P->ecut + O_TSTOP) {
+                emit_charged(c, p, P_POSITRON, Tp, p->u, 1, layer);
+            } else {
+                /* a positron born at the cutoff stops and annihilates at once */
+                deposit(c, p, p->x, layer, Tp);
+                annihilate(c, p);
+            }
+        } else {
+            deposit(c, p, p->x, layer, Tm + Tp);
+            annihilate(c, p);
+        }
+        return 0;
+    }
+}
+
+static void photon_ct(o_ctx* c, o_part* p) {
+    const orc_problem* P = c->P;
+    for (int f = 0; f < P->max_steps; f++) {
+        double smax = sigma_max_ct(c, p->E);
+        double s = -log(rng_u(&p->rng)) / smax;
+        for (int a = 0; a < 3; a++) p->x[a] += s * p->u[a];
+        c->cnt[C_FLIGHTS_CT]++;
+        int idx[3];
+        if (!ct_voxel(c, p->x, idx)) { transfer_to_epid(c, p); return; }
+        double rho; int m;
+        ct_props(c, idx, &rho, &m);
+        double sig = rho * mu_total(m, p->E);
+        if (!(rng_u(&p->rng) * smax < sig)) continue;      /* virtual */
+        c->cnt[C_REAL_CT]++;
+        p->cell[0] = idx[0]; p->cell[1] = idx[1]; p->cell[2] = idx[2];
+        if (!photon_interact(c, p, m, 0)) return;
+    }
+    c->e_lost += p->E;
+    c->cnt[C_LOST]++;
+}
+
+/* distance along u to leave EPID layer l: which = 0 (z plane), 1 (x edge), 2 (y edge) */
+static double epid_dist(const o_ctx* c, const double x[3], const double u[3], int l, int* which) {
+    double dz = INFINITY, dx = INFINITY, dy = INFINITY;
+    if (u[2] < 0.0) dz = (c->zplane[l + 1] - x[2]) / u[2];
+    else if (u[2] > 0.0) dz = (c->zplane[l] - x[2]) / u[2];
+    if (u[0] > 0.0) dx = (c->half_w[0] - x[0]) / u[0];
+    else if (u[0] < 0.0) dx = (-c->half_w[0] - x[0]) / u[0];
+    if (u[1] > 0.0) dy = (c->half_w[1] - x[1]) / u[1];
+    else if (u[1] < 0.0) dy = (-c->half_w[1] - x[1]) / u[1];
+    double d = dz; *which = 0;
+    if (dx < d) { d = dx; *which = 1; }
+    if (dy < d) { d = dy; *which = 2; }
+    return fmax(d, 0.0);
+}
+
+static void photon_epid(o_ctx* c, o_part* p) {
+    const orc_problem* P = c->P;
+    for (int f = 0; f < P->max_steps; f++) {
+        double tau = -log(rng_u(&p->rng));
+        c->cnt[C_FLIGHTS_EPID]++;
+        for (;;) {
+            int l = p->cell[0];
+            double mu = P->layer_rho[l] * mu_total(layer_mat(c, l), p->E);
+            int which;
+            double d = epid_dist(c, p->x, p->u, l, &which);
+            if (tau < mu * d) {
+                double s = tau / mu;
+                for (int a = 0; a < 3; a++) p->x[a] += s * p->u[a];
+                break;
+            }
+            tau -= mu * d;
+            for (int a = 0; a < 3; a++) p->x[a] += d * p->u[a];
+            if (which != 0) { c->e_esc += p->E; return; }
+            int nl = l + (p->u[2] < 0.0 ? 1 : -1);
+            if (nl < 0 || nl >= P->n_layers) { c->e_esc += p->E; return; }
+            p->cell[0] = nl;
+        }
+        if (!photon_interact(c, p, layer_mat(c, p->cell[0]), p->cell[0])) return;
+    }
+    c->e_lost += p->E;
+    c->cnt[C_LOST]++;
+}
+
+/* CT voxel boundary distance for charged-particle steps. */
+static double ct_dist(const o_ctx* c, const double x[3], const double u[3], const int cell[3], int* axis) {
+    const orc_problem* P = c->P;
+    double best = INFINITY; *axis = -1;
+    for (int a = 0; a < 3; a++) {
+        double d = INFINITY;
+        if (u[a] > 0.0) d = (P->origin[a] + (cell[a] + 1) * P->vox[a] - x[a]) / u[a];
+        else if (u[a] < 0.0) d = (P->origin[a] + cell[a] * P->vox[a] - x[a]) / u[a];
+        if (d < best) { best = d; *axis = a; }
+    }
+    return fmax(best, 0.0);
+}
+
+static void electron(o_ctx* c, o_part* p) {
+    const orc_problem* P = c->P;
+    const double tcut = P->ecut, tstop = P->ecut + O_TSTOP;
+    for (int step = 0; step < P->max_steps; step++) {
+        double rho; int m; int layer = 0;
+        if (p->zone == Z_CT) {
+            ct_props(c, p->cell, &rho, &m);
+            c->cnt[C_ESTEP_CT]++;
+        } else {
+            layer = p->cell[0];
+            rho = P->layer_rho[layer];
+            m = layer_mat(c, layer);
+            c->cnt[C_ESTEP_EPID]++;
+        }
+        double T = p->E;
+        /* (a) energy-loss limited step with midpoint stopping power */
+        double dEt = P->step_frac * T;
+        if (T - dEt < tstop) dEt = T - tcut;
+        double Tm = T - 0.5 * dEt;
+        double L = rho * (orc_lcol(m, Tm, P->wcc) + orc_lrad_soft(m, Tm, P->wcb));
+        double sE = dEt / L;
+        /* (b) distance to a hard event, majorant = value at the step's start */
+        double Sh = rho * (orc_sigma_moller(m, T, P->wcc) + orc_sigma_brem(m, T, P->wcb));
+        double sh = -log(rng_u(&p->rng)) / Sh;
+        /* (c) distance to the cell boundary */
+        int ax;
+        double sb = (p->zone == Z_CT) ? ct_dist(c, p->x, p->u, p->cell, &ax) : epid_dist(c, p->x, p->u, layer, &ax);
+        double s = sE; int lim = 0;
+        if (sh < s) { s = sh; lim = 1; }
+        if (sb < s) { s = sb; lim = 2; }
+        double xh = rng_u(&p->rng), xmu = rng_u(&p->rng), xph = rng_u(&p->rng);
+        double s1 = xh * s;
+        for (int a = 0; a < 3; a++) p->x[a] += s1 * p->u[a];
+        double hinge[3] = {p->x[0], p->x[1], p->x[2]};
+        int hcell[3] = {p->cell[0], p->cell[1], p->cell[2]};
+        /* random-hinge deflection for the whole step */
+        double G = s * rho * orc_lambda1_inv(m, T);
+        double A = orc_wentzel_A(G);
+        double mu = (G > 0.0) ? sample_ms_mu(A, xmu) : 0.0;
+        rotate(p->u, 1.0 - 2.0 * mu, 2.0 * O_PI * xph);
+        double s2 = s - s1;
+        int ax2;
+        double sb2 = (p->zone == Z_CT) ? ct_dist(c, p->x, p->u, p->cell, &ax2) : epid_dist(c, p->x, p->u, layer, &ax2);
+        int crossed = 0;
+        if (s2 >= sb2) { s2 = sb2; crossed = 1; }
+        for (int a = 0; a < 3; a++) p->x[a] += s2 * p->u[a];
+        double dE = dEt * ((s1 + s2) / sE);
+        double Tn = T - dE;
+        o_part here = *p;
+        here.cell[0] = hcell[0]; here.cell[1] = hcell[1]; here.cell[2] = hcell[2];
+        if (Tn <= tstop) {
+            /* the particle stops at its hinge point */
+            deposit(c, &here, hinge, hcell[0], dE + Tn);
+            if (p->type == P_POSITRON) {
+                p->x[0] = hinge[0]; p->x[1] = hinge[1]; p->x[2] = hinge[2];
+                p->cell[0] = hcell[0]; p->cell[1] = hcell[1]; p->cell[2] = hcell[2];
+                annihilate(c, p);
+            }
+            return;
+        }
+        deposit(c, &here, hinge, hcell[0], dE);
+        p->E = Tn;
+        if (crossed) {
+            if (p->zone == Z_CT) {
+                p->cell[ax2] += (p->u[ax2] > 0.0) ? 1 : -1;
+                int n[3] = {P->nx, P->ny, P->nz};
+                if (p->cell[ax2] < 0 || p->cell[ax2] >= n[ax2]) { transfer_to_epid(c, p); return; }
+            } else {
+                if (ax2 != 0) { c->e_esc += p->E + rest_extra(p); return; }
+                int nl = layer + (p->u[2] < 0.0 ? 1 : -1);
+                if (nl < 0 || nl >= P->n_layers) { c->e_esc += p->E + rest_extra(p); return; }
+                p->cell[0] = nl;
+            }
+            continue;
+        }
+        if (lim == 1) {
+            double Sn_m = rho * orc_sigma_moller(m, Tn, P->wcc);
+            double Sn_b = rho * orc_sigma_brem(m, Tn, P->wcb);
+            if (!(rng_u(&p->rng) * Sh < Sn_m + Sn_b)) continue;        /* delta event */
+            if (rng_u(&p->rng) * (Sn_m + Sn_b) < Sn_m) {
+                c->cnt[C_MOLLER]++;
+                double eps = sample_moller_eps(&p->rng, Tn, P->wcc);
+                double phi = 2.0 * O_PI * rng_u(&p->rng);
+                double W = eps * Tn, Tp = Tn - W;
+                double cs = sqrt(W * (Tn + 2.0 * O_MC2) / (Tn * (W + 2.0 * O_MC2)));
+                double cp = sqrt(Tp * (Tn + 2.0 * O_MC2) / (Tn * (Tp + 2.0 * O_MC2)));
+                double us[3] = {p->u[0], p->u[1], p->u[2]};
+                rotate(us, cs, phi);
+                rotate(p->u, cp, phi + O_PI);
+                emit_charged(c, p, P_ELECTRON, W, us, 0, layer);
+                p->E = Tp;
+            } else {
+                c->cnt[C_BREM]++;
+                double k = P->wcb * exp(rng_u(&p->rng) * log(Tn / P->wcb));
+                o_part g;
+                make_child(p, &g, P_PHOTON, 0);
+                g.u[0] = p->u[0]; g.u[1] = p->u[1]; g.u[2] = p->u[2];
+                g.E = k;
+                c->cnt[C_PHOTONS2]++;
+                push(c, &g);
+                p->E = Tn - k;
+            }
+            if (p->E <= tstop) {
+                deposit(c, p, p->x, layer, p->E);
+                if (p->type == P_POSITRON) annihilate(c, p);
+                return;
+            }
+        }
+    }
+    c->e_lost += p->E + rest_extra(p);
+    c->cnt[C_LOST]++;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Source (Sec. 2.1.1 with the jaw/MLC transport replaced by an ideal        */
+/* aperture): rectangle chosen with weight MU_k x area, point uniform in it  */
+/* at the isocentre plane, direction from the point source.                  */
+/* ------------------------------------------------------------------------ */
+static int build_source(o_ctx* c) {
+    const orc_problem* P = c->P;
+    int nmax = P->n_seg * P->n_pairs;
+    c->rect = (double*)malloc(sizeof(double) * 4 * (size_t)(nmax > 0 ? nmax : 1));
+    c->cdf = (double*)malloc(sizeof(double) * (size_t)(nmax > 0 ? nmax : 1));
+    double acc = 0.0;
+    int n = 0;
+    for (int k = 0; k < P->n_seg; k++) {
+        const double* jw = P->jaws + 4 * k;
+        for (int j = 0; j < P->n_pairs; j++) {
+            const double* lf = P->leaves + 2 * ((size_t)k * P->n_pairs + j);
+            double x0 = fmax(lf[0], jw[0]), x1 = fmin(lf[1], jw[1]);
+            double y0 = fmax(P->pair_edges[j], jw[2]), y1 = fmin(P->pair_edges[j + 1], jw[3]);
+            if (x1 > x0 && y1 > y0 && P->mu[k] > 0.0) {
+                acc += P->mu[k] * (x1 - x0) * (y1 - y0);
+                c->rect[4 * n] = x0; c->rect[4 * n + 1] = x1; c->rect[4 * n + 2] = y0; c->rect[4 * n + 3] = y1;
+                c->cdf[n] = acc;
+                n++;
+            }
+        }
+    }
+    c->n_rect = n;
+    for (int i = 0; i < n; i++) c->cdf[i] /= acc;
+    return n > 0;
+}
+
+static void run_history(o_ctx* c, uint64_t h, uint64_t seed) {
+    const orc_problem* P = c->P;
+    c->hist = h;
+    o_part p;
+    memset(&p, 0, sizeof(p));
+    p.type = P_PHOTON;
+    p.rng.key[0] = (uint32_t)seed; p.rng.key[1] = (uint32_t)(seed >> 32);
+    p.rng.ord = 0; p.rng.hlo = (uint32_t)h; p.rng.hhi = (uint32_t)(h >> 32);
+    p.rng.d = 0; p.rng.cvalid = 0;
+    /* rectangle: first index whose cumulative weight exceeds the draw */
+    double xi = rng_u(&p.rng);
+    int lo = 0, hi = c->n_rect - 1;
+    while (lo < hi) {
+        int mid = (lo + hi) / 2;
+        if (xi < c->cdf[mid]) hi = mid; else lo = mid + 1;
+    }
+    const double* r = c->rect + 4 * lo;
+    double X = r[0] + (r[1] - r[0]) * rng_u(&p.rng);
+    double Y = r[2] + (r[3] - r[2]) * rng_u(&p.rng);
+    p.E = (P->mono_e > 0.0) ? P->mono_e : sample_spectrum(&p.rng, P->e_max, P->pcut);
+    c->e_src += p.E;
+    double nb = sqrt(X * X + Y * Y + P->sad * P->sad);
+    double ub[3] = {X / nb, Y / nb, -P->sad / nb};
+    double sb[3] = {0.0, 0.0, P->sad};
+    to_patient(c, sb, p.x);
+    to_patient_dir(c, ub, p.u);
+    enter_world(c, &p);
+    while (c->sp > 0) {
+        o_part q = c->stack[--c->sp];
+        if (q.type == P_PHOTON) {
+            if (q.zone == Z_CT) photon_ct(c, &q); else photon_epid(c, &q);
+        } else {
+            electron(c, &q);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Driver: threads own disjoint sub-tallies (b = h mod B), so the tally is    */
+/* independent of the thread count.                                          */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    o_ctx local; uint64_t seed, h0, n; int tid, nthreads;
+} o_job;
+
+static void ctx_geometry(o_ctx* c, const orc_problem* P) {
+    memset(c, 0, sizeof(*c));
+    c->P = P;
+    double g = P->gantry_deg * O_PI / 180.0;
+    c->ex[0] = cos(g); c->ex[1] = sin(g); c->ex[2] = 0.0;
+    c->ey[0] = 0.0; c->ey[1] = 0.0; c->ey[2] = 1.0;
+    c->ez[0] = sin(g); c->ez[1] = -cos(g); c->ez[2] = 0.0;
+    double zs = P->sad - P->sid;
+    double z = zs + 0.5 * P->layer_thick[P->sens_layer];
+    for (int l = P->sens_layer - 1; l >= 0; l--) z += P->layer_thick[l];
+    c->zplane[0] = z;
+    for (int l = 0; l < P->n_layers; l++) c->zplane[l + 1] = c->zplane[l] - P->layer_thick[l];
+    c->half_w[0] = 0.5 * P->npx * P->pitch;
+    c->half_w[1] = 0.5 * P->npy * P->pitch;
+    size_t nv = (size_t)P->nx * P->ny * P->nz;
+    for (size_t i = 0; i < nv; i++) {
+        double rho; int m;
+        orc_hu_to_rho_mat(P->hu[i], &rho, &m);
+        c->mat_present[m] = 1;
+        if (rho > c->rho_max[m]) c->rho_max[m] = rho;
+    }
+}
+
+static void* worker(void* arg) {
+    o_job* J = (o_job*)arg;
+    o_ctx* c = &J->local;
+    uint64_t B = (uint64_t)c->P->n_batches;
+    for (uint64_t i = 0; i < J->n; i++) {
+        uint64_t h = J->h0 + i;
+        if ((int)((h % B) % (uint64_t)J->nthreads) != J->tid) continue;
+        run_history(c, h, J->seed);
+    }
+    return NULL;
+}
+
+int orc_run(const orc_problem* P, uint64_t seed, uint64_t hist_begin, uint64_t n_hist, int n_threads,
+            orc_result* R) {
+    if (!P || !R || !R->tally || P->n_layers < 1 || P->n_layers > O_MAXL || P->n_batches < 1) return 1;
+    o_ctx base;
+    ctx_geometry(&base, P);
+    if (!build_source(&base)) { free(base.rect); free(base.cdf); return 2; }
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > P->n_batches) n_threads = P->n_batches;
+    o_job* jobs = (o_job*)calloc((size_t)n_threads, sizeof(o_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+    for (int t = 0; t < n_threads; t++) {
+        jobs[t].local = base;
+        jobs[t].local.tally = R->tally;
+        jobs[t].local.stack = NULL; jobs[t].local.sp = 0; jobs[t].local.cap = 0;
+        jobs[t].seed = seed; jobs[t].h0 = hist_begin; jobs[t].n = n_hist;
+        jobs[t].tid = t; jobs[t].nthreads = n_threads;
+    }
+    for (int t = 1; t < n_threads; t++) pthread_create(&th[t], NULL, worker, &jobs[t]);
+    worker(&jobs[0]);
+    for (int t = 1; t < n_threads; t++) pthread_join(th[t], NULL);
+    for (int t = 0; t < n_threads; t++) {
+        o_ctx* l = &jobs[t].local;
+        R->e_src += l->e_src; R->e_ct += l->e_ct; R->e_esc += l->e_esc; R->e_lost += l->e_lost;
+        for (int k = 0; k < O_MAXL; k++) R->e_epid[k] += l->e_epid[k];
+        for (int k = 0; k < C_NCOUNT; k++) R->counters[k] += l->cnt[k];
+        free(l->stack);
+    }
+    free(jobs); free(th); free(base.rect); free(base.cdf);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Test hooks: single samplers exposed for the CPU pins.                     */
+/* ------------------------------------------------------------------------ */
+static void hook_rng(o_rng* r, uint64_t seed, uint64_t h) {
+    memset(r, 0, sizeof(*r));
+    r->key[0] = (uint32_t)seed; r->key[1] = (uint32_t)(seed >> 32);
+    r->hlo = (uint32_t)h; r->hhi = (uint32_t)(h >> 32);
+}
+
+void orc_uniforms(uint64_t seed, uint64_t h, uint32_t ord, uint32_t n, double* out) {
+    o_rng r; hook_rng(&r, seed, h); r.ord = ord;
+    for (uint32_t i = 0; i < n; i++) out[i] = rng_u(&r);
+}
+
+void orc_sample_kn_many(double E, uint64_t seed, uint64_t n, double* eps, double* cost) {
+    for (uint64_t i = 0; i < n; i++) {
+        o_rng r; hook_rng(&r, seed, i);
+        sample_kn(&r, E, &eps[i], &cost[i]);
+    }
+}
+
+void orc_sample_spectrum_many(double emax, double ecut, uint64_t seed, uint64_t n, double* out) {
+    for (uint64_t i = 0; i < n; i++) {
+        o_rng r; hook_rng(&r, seed, i);
+        out[i] = sample_spectrum(&r, emax, ecut);
+    }
+}
+
+void orc_sample_moller_many(double T, double wcc, uint64_t seed, uint64_t n, double* eps) {
+    for (uint64_t i = 0; i < n; i++) {
+        o_rng r; hook_rng(&r, seed, i);
+        eps[i] = sample_moller_eps(&r, T, wcc);
+    }
+}
+
+void orc_sample_ms_many(double G, uint64_t seed, uint64_t n, double* cost) {
+    double A = orc_wentzel_A(G);
+    for (uint64_t i = 0; i < n; i++) {
+        o_rng r; hook_rng(&r, seed, i);
+        double mu = (G > 0.0) ? sample_ms_mu(A, rng_u(&r)) : 0.0;
+        cost[i] = 1.0 - 2.0 * mu;
+    }
+}
+
+/* CSDA path length of an electron in an unbounded medium of material m with
+ * hard events and deflections switched off: the step rule alone. */
+double orc_csda_path(int m, double rho, double T0, double ecut, double wcc, double wcb, double step_frac) {
+    double T = T0, path = 0.0;
+    const double tstop = ecut + O_TSTOP;
+    for (int i = 0; i < 1000000 && T > tstop; i++) {
+        double dEt = step_frac * T;
+        if (T - dEt < tstop) dEt = T - ecut;
+        double Tm = T - 0.5 * dEt;
+        double L = rho * (orc_lcol(m, Tm, wcc) + orc_lrad_soft(m, Tm, wcb));
+        path += dEt / L;
+        T -= dEt;
+    }
+    return path;
+}
+
+/* First real photon interaction along one fixed ray through the CT of P:
+ * for n photons of energy E starting at `start` (patient frame) along `dir`,
+ * record the flat voxel index (-1 if none before leaving the box) and the
+ * interaction type (0 Compton, 1 photoelectric, 2 pair). */
+void orc_first_interaction(const orc_problem* P, double E, const double start[3], const double dir[3],
+                           uint64_t seed, uint64_t n, int64_t* vox, int32_t* type) {
+    o_ctx c;
+    ctx_geometry(&c, P);
+    for (uint64_t i = 0; i < n; i++) {
+        o_rng r; hook_rng(&r, seed, i);
+        double x[3] = {start[0], start[1], start[2]};
+        vox[i] = -1; type[i] = -1;
+        for (int f = 0; f < 100000; f++) {
+            double smax = sigma_max_ct(&c, E);
+            double s = -log(rng_u(&r)) / smax;
+            for (int a = 0; a < 3; a++) x[a] += s * dir[a];
+            int idx[3];
+            if (!ct_voxel(&c, x, idx)) break;
+            double rho; int m;
+            ct_props(&c, idx, &rho, &m);
+            double mu[3];
+            orc_mu_photon(m, E, mu);
+            double tot = mu[0] + mu[1] + mu[2];
+            if (!(rng_u(&r) * smax < rho * tot)) continue;
+            double xi = rng_u(&r);
+            vox[i] = ((int64_t)idx[2] * P->ny + idx[1]) * P->nx + idx[0];
+            type[i] = (xi * tot < mu[0]) ? 0 : (xi * tot < mu[0] + mu[1]) ? 1 : 2;
+            break;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Radiological thickness (Sec. 2.2, step 1): exact Siddon (1985) ray sum     */
+/* t = sum_v rho_v l_v from the source to each requested pixel centre.        */
+/* ------------------------------------------------------------------------ */
+static int cmp_d(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x < y) ? -1 : (x > y) ? 1 : 0;
+}
+
+double orc_siddon_ray(const orc_problem* P, const double p1[3], const double p2[3]) {
+    int n[3] = {P->nx, P->ny, P->nz};
+    double d[3] = {p2[0] - p1[0], p2[1] - p1[1], p2[2] - p1[2]};
+    double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double amin = 0.0, amax = 1.0;
+    for (int a = 0; a < 3; a++) {
+        double lo = P->origin[a], hi = P->origin[a] + n[a] * P->vox[a];
+        if (d[a] != 0.0) {
+            double a0 = (lo - p1[a]) / d[a], a1 = (hi - p1[a]) / d[a];
+            amin = fmax(amin, fmin(a0, a1));
+            amax = fmin(amax, fmax(a0, a1));
+        } else if (p1[a] <= lo || p1[a] >= hi) {
+            return 0.0;
+        }
+    }
+    if (amin >= amax) return 0.0;
+    size_t cap = (size_t)(n[0] + n[1] + n[2] + 8);
+    double* al = (double*)malloc(sizeof(double) * cap);
+    size_t k = 0;
+    al[k++] = amin; al[k++] = amax;
+    for (int a = 0; a < 3; a++) {
+        if (d[a] == 0.0) continue;
+        for (int i = 0; i <= n[a]; i++) {
+            double av = (P->origin[a] + i * P->vox[a] - p1[a]) / d[a];
+            if (av > amin && av < amax) al[k++] = av;
+        }
+    }
+    qsort(al, k, sizeof(double), cmp_d);
+    double t = 0.0;
+    for (size_t i = 0; i + 1 < k; i++) {
+        double am = 0.5 * (al[i] + al[i + 1]);
+        int idx[3], ok = 1;
+        for (int a = 0; a < 3; a++) {
+            idx[a] = (int)floor((p1[a] + am * d[a] - P->origin[a]) / P->vox[a]);
+            if (idx[a] < 0 || idx[a] >= n[a]) ok = 0;
+        }
+        if (!ok) continue;
+        double rho; int m;
+        int hu = P->hu[((size_t)idx[2] * P->ny + idx[1]) * P->nx + idx[0]];
+        orc_hu_to_rho_mat(hu, &rho, &m);
+        t += rho * (al[i + 1] - al[i]) * len;
+    }
+    free(al);
+    return t;
+}
+
+/* t for pixels (ix[i], iy[i]) of the EPID grid, rays from the source to the
+ * pixel centres on the sensitive layer's mid-plane (SID from the source). */
+void orc_tmap(const orc_problem* P, const int32_t* ix, const int32_t* iy, int64_t n, double* t) {
+    o_ctx c;
+    ctx_geometry(&c, P);
+    double sb[3] = {0.0, 0.0, P->sad}, src[3];
+    to_patient(&c, sb, src);
+    for (int64_t i = 0; i < n; i++) {
+        double pb[3] = {-c.half_w[0] + (ix[i] + 0.5) * P->pitch, -c.half_w[1] + (iy[i] + 0.5) * P->pitch,
+                        P->sad - P->sid};
+        double pp[3];
+        to_patient(&c, pb, pp);
+        t[i] = orc_siddon_ray(P, src, pp);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Global gamma index (Low et al. 1998) with a low-dose threshold, the form  */
+/* of the paper's image comparisons (Sec. 2.3.3).  ref is the reference      */
+/* image; ev is bilinearly interpolated on a sub-grid of step h (mm) over a  */
+/* search radius rad (mm).  Returns the pass rate; gamma values go to gam    */
+/* (NaN for pixels below the threshold).                                     */
+/* ------------------------------------------------------------------------ */
+static double bilin(const double* img, int nx, int ny, double fx, double fy) {
+    if (fx < 0) fx = 0;
+    if (fy < 0) fy = 0;
+    if (fx > nx - 1) fx = nx - 1;
+    if (fy > ny - 1) fy = ny - 1;
+    int x0 = (int)floor(fx), y0 = (int)floor(fy);
+    int x1 = x0 + 1 < nx ? x0 + 1 : x0, y1 = y0 + 1 < ny ? y0 + 1 : y0;
+    double ax = fx - x0, ay = fy - y0;
+    return (1 - ay) * ((1 - ax) * img[(size_t)y0 * nx + x0] + ax * img[(size_t)y0 * nx + x1]) +
+           ay * ((1 - ax) * img[(size_t)y1 * nx + x0] + ax * img[(size_t)y1 * nx + x1]);
+}
+
+double orc_gamma(const double* ref, const double* ev, int nx, int ny, double pix_mm, double dd_frac,
+                 double dta_mm, double thr_frac, double h_mm, double rad_mm, double* gam) {
+    double rmax = 0.0;
+    for (size_t i = 0; i < (size_t)nx * ny; i++) rmax = fmax(rmax, ref[i]);
+    double ddabs = dd_frac * rmax;
+    long npass = 0, neval = 0;
+    int nsub = (int)ceil(rad_mm / h_mm);
+    for (int y = 0; y < ny; y++) {
+        for (int x = 0; x < nx; x++) {
+            size_t i = (size_t)y * nx + x;
+            if (ref[i] < thr_frac * rmax) { if (gam) gam[i] = NAN; continue; }
+            neval++;
+            double best = INFINITY;
+            for (int sy = -nsub; sy <= nsub && best > 0.0; sy++) {
+                for (int sx = -nsub; sx <= nsub; sx++) {
+                    double dx = sx * h_mm, dy = sy * h_mm;
+                    double r2 = dx * dx + dy * dy;
+                    if (r2 > rad_mm * rad_mm) continue;
+                    double dist2 = r2 / (dta_mm * dta_mm);
+                    if (dist2 >= best) continue;
+                    double v = bilin(ev, nx, ny, x + dx / pix_mm, y + dy / pix_mm);
+                    double dv = (v - ref[i]) / ddabs;
+                    double g2 = dist2 + dv * dv;
+                    if (g2 < best) best = g2;
+                }
+            }
+            double gv = sqrt(best);
+            if (gam) gam[i] = gv;
+            if (gv <= 1.0) npass++;
+        }
+    }
+    return neval ? (double)npass / neval : 1.0;
+}
