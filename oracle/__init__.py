@@ -104,6 +104,8 @@ def lib():
         _lib.orc_tmap.argtypes = [P(_Problem), P(C.c_int32), P(C.c_int32), C.c_int64, P(d)]
         _lib.orc_siddon_ray.restype = d
         _lib.orc_siddon_ray.argtypes = [P(_Problem), P(d), P(d)]
+        _lib.orc_sample_source_many.restype = i
+        _lib.orc_sample_source_many.argtypes = [P(_Problem), u64, u64, u64, P(d), P(d), P(d)]
         _lib.orc_gamma.restype = d
         _lib.orc_gamma.argtypes = [P(d), P(d), i, i, d, d, d, d, d, d, P(d)]
     return _lib
@@ -181,6 +183,17 @@ def first_interaction(problem, E, start, direction, n, seed=0):
                                 vox.ctypes.data_as(C.POINTER(C.c_int64)),
                                 typ.ctypes.data_as(C.POINTER(C.c_int32)))
     return vox, typ
+
+
+def sample_source(problem, n, seed=0, hist_begin=0):
+    """Isocentre-plane points (X, Y) and energies of the primaries of histories
+    hist_begin.. drawn exactly as the transport draws them."""
+    m = _Marshalled(problem)
+    X, Y, E = np.empty(n), np.empty(n), np.empty(n)
+    rc = lib().orc_sample_source_many(C.byref(m.s), int(seed), int(hist_begin), int(n), _dp(X), _dp(Y), _dp(E))
+    if rc:
+        raise RuntimeError("field has no open aperture")
+    return X, Y, E
 
 
 def tmap(problem, ix=None, iy=None, field=None):

@@ -471,8 +471,11 @@ static void transfer_to_epid(o_ctx* c, o_part* p) {
     to_beam_dir(c, p->u, ub);
     double Eexit = p->E + rest_extra(p);
     if (ub[2] >= 0.0) { c->e_esc += Eexit; return; }
+    /* Any point of the vacuum line will do: a Woodcock flight may have carried
+     * the photon past the detector plane, but the CT lies wholly above it, so
+     * the line's crossing of the detector face is always downstream of the
+     * true exit point. */
     double t = (c->zplane[0] - b[2]) / ub[2];
-    if (t < 0.0) { c->e_esc += Eexit; return; }
     double X = b[0] + t * ub[0], Y = b[1] + t * ub[1];
     if (!(fabs(X) < c->half_w[0] && fabs(Y) < c->half_w[1])) { c->e_esc += Eexit; return; }
     p->zone = Z_EPID;
@@ -835,6 +838,22 @@ static int build_source(o_ctx* c) {
     return n > 0;
 }
 
+/* Draws of a primary: rectangle (1), X (1), Y (1), then the spectrum. */
+static void sample_source(const o_ctx* c, o_rng* r, double* X, double* Y, double* E) {
+    const orc_problem* P = c->P;
+    /* rectangle: first index whose cumulative weight exceeds the draw */
+    double xi = rng_u(r);
+    int lo = 0, hi = c->n_rect - 1;
+    while (lo < hi) {
+        int mid = (lo + hi) / 2;
+        if (xi < c->cdf[mid]) hi = mid; else lo = mid + 1;
+    }
+    const double* q = c->rect + 4 * lo;
+    *X = q[0] + (q[1] - q[0]) * rng_u(r);
+    *Y = q[2] + (q[3] - q[2]) * rng_u(r);
+    *E = (P->mono_e > 0.0) ? P->mono_e : sample_spectrum(r, P->e_max, P->pcut);
+}
+
 static void run_history(o_ctx* c, uint64_t h, uint64_t seed) {
     const orc_problem* P = c->P;
     c->hist = h;
@@ -844,17 +863,8 @@ static void run_history(o_ctx* c, uint64_t h, uint64_t seed) {
     p.rng.key[0] = (uint32_t)seed; p.rng.key[1] = (uint32_t)(seed >> 32);
     p.rng.ord = 0; p.rng.hlo = (uint32_t)h; p.rng.hhi = (uint32_t)(h >> 32);
     p.rng.d = 0; p.rng.cvalid = 0;
-    /* rectangle: first index whose cumulative weight exceeds the draw */
-    double xi = rng_u(&p.rng);
-    int lo = 0, hi = c->n_rect - 1;
-    while (lo < hi) {
-        int mid = (lo + hi) / 2;
-        if (xi < c->cdf[mid]) hi = mid; else lo = mid + 1;
-    }
-    const double* r = c->rect + 4 * lo;
-    double X = r[0] + (r[1] - r[0]) * rng_u(&p.rng);
-    double Y = r[2] + (r[3] - r[2]) * rng_u(&p.rng);
-    p.E = (P->mono_e > 0.0) ? P->mono_e : sample_spectrum(&p.rng, P->e_max, P->pcut);
+    double X, Y;
+    sample_source(c, &p.rng, &X, &Y, &p.E);
     c->e_src += p.E;
     double nb = sqrt(X * X + Y * Y + P->sad * P->sad);
     double ub[3] = {X / nb, Y / nb, -P->sad / nb};
@@ -1160,4 +1170,18 @@ double orc_gamma(const double* ref, const double* ev, int nx, int ny, double pix
         }
     }
     return neval ? (double)npass / neval : 1.0;
+}
+
+/* Source samples (isocentre-plane X, Y and energy) of histories h0..h0+n-1. */
+int orc_sample_source_many(const orc_problem* P, uint64_t seed, uint64_t h0, uint64_t n, double* X, double* Y,
+                           double* E) {
+    o_ctx c;
+    ctx_geometry(&c, P);
+    if (!build_source(&c)) { free(c.rect); free(c.cdf); return 2; }
+    for (uint64_t i = 0; i < n; i++) {
+        o_rng r; hook_rng(&r, seed, h0 + i);
+        sample_source(&c, &r, &X[i], &Y[i], &E[i]);
+    }
+    free(c.rect); free(c.cdf);
+    return 0;
 }

@@ -1,0 +1,575 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test checks one oracle function against a closed form, a numerical
+integral of a textbook differential cross section, a brute-force enumeration,
+a published known-answer vector or the paper's Table 1, chosen so that a
+plausible slip (a dropped term, a wrong sign or index, a transposed operand)
+fails one of them.  All inputs are seeded, so the statistical tests are
+deterministic; their thresholds are set at >= 3 standard deviations.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, special, stats
+
+import oracle
+from paper_2510_24154_b300 import workloads as W
+
+pytestmark = pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarning")
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+RE = 2.8179403262e-13
+MC2 = 0.51099895
+NA = 6.02214076e23
+L = oracle.lib()
+
+
+def _mu(m, E):
+    out = (np.ctypeslib.ctypes.c_double * 3)()
+    L.orc_mu_photon(m, E, out)
+    return np.array(out[:])
+
+
+# ---------------------------------------------------------------- Philox ---
+
+def test_philox_known_answers():
+    import ctypes as C
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        ctr, key, want = (C.c_uint32 * 4)(*v[0:4]), (C.c_uint32 * 2)(*v[4:6]), v[6:10]
+        out = (C.c_uint32 * 4)()
+        L.orc_philox(ctr, key, out)
+        assert list(out) == want
+
+
+def test_draw_stream_layout():
+    """Draw d is word d mod 4 of block d div 4 on a 24-bit grid strictly inside (0,1)."""
+    import ctypes as C
+    seed, h, ord_ = 0x1234_5678_9ABC, 77, 5
+    out = (C.c_double * 9)()
+    L.orc_uniforms(seed, h, ord_, 9, out)
+    got = np.array(out[:])
+    key = (C.c_uint32 * 2)(seed & 0xFFFFFFFF, seed >> 32)
+    want = []
+    for blk in range(3):
+        w = (C.c_uint32 * 4)()
+        L.orc_philox((C.c_uint32 * 4)(blk, ord_, h, 0), key, w)
+        want += [((x >> 8) + 0.5) / 2 ** 24 for x in w]
+    assert np.array_equal(got, np.array(want[:9]))
+    assert np.all((got > 0) & (got < 1))
+
+
+def test_child_ordinals_distinct():
+    kids = {L.orc_child_ordinal(p, d, s) for p in (0, 1, 99) for d in range(200) for s in range(4)}
+    assert len(kids) == 3 * 200 * 4
+    assert 0 not in kids
+
+
+# ------------------------------------------------------- photon physics ---
+
+def _kn_dcs(ct, k):
+    """Klein-Nishina dsigma/dOmega per electron (cm^2/sr)."""
+    eps = 1.0 / (1.0 + k * (1.0 - ct))
+    return 0.5 * RE * RE * eps * eps * (eps + 1.0 / eps - (1.0 - ct * ct))
+
+
+@pytest.mark.parametrize("E", [0.01, 0.05, 0.2, 0.511, 1.0, 2.0, 6.0])
+def test_kn_total_matches_integrated_dcs(E):
+    k = E / MC2
+    num, _ = integrate.quad(lambda c: 2 * math.pi * _kn_dcs(c, k), -1, 1, epsabs=0, epsrel=1e-12)
+    assert L.orc_sigma_kn(E) == pytest.approx(num, rel=1e-9)
+
+
+def test_kn_thomson_limit():
+    sig_t = 8 * math.pi * RE * RE / 3
+    E = 1e-4
+    # sigma_KN = sigma_T (1 - 2k + O(k^2)) for small k
+    assert L.orc_sigma_kn(E) == pytest.approx(sig_t * (1 - 2 * E / MC2), rel=1e-6)
+
+
+@pytest.mark.parametrize("E", [0.1, 1.0, 5.0])
+def test_kn_sampler_chi2(E):
+    n = 200_000
+    eps, ct = np.empty(n), np.empty(n)
+    P = np.ctypeslib.ctypes.POINTER(np.ctypeslib.ctypes.c_double)
+    L.orc_sample_kn_many(E, 11, n, eps.ctypes.data_as(P), ct.ctypes.data_as(P))
+    k = E / MC2
+    # kinematics: eps = 1/(1 + k(1-cos))
+    assert np.allclose(eps, 1.0 / (1.0 + k * (1.0 - ct)), rtol=1e-12)
+    edges = np.linspace(-1, 1, 41)
+    tot = integrate.quad(lambda c: _kn_dcs(c, k), -1, 1, epsrel=1e-12)[0]
+    p = np.array([integrate.quad(lambda c: _kn_dcs(c, k), a, b, epsrel=1e-12)[0]
+                  for a, b in zip(edges[:-1], edges[1:])]) / tot
+    obs, _ = np.histogram(ct, edges)
+    chi2 = ((obs - n * p) ** 2 / (n * p)).sum()
+    assert stats.chi2.sf(chi2, len(p) - 1) > 1e-3
+
+
+def test_photoelectric_structure():
+    # power law E^-3.2 away from the Gd edge (water, copper, Gd2O2S above the edge)
+    for m in (W.MAT_WATER, W.MAT_CU, W.MAT_BONE):
+        r = _mu(m, 0.2)[1] / _mu(m, 0.1)[1]
+        assert r == pytest.approx(2 ** -3.2, rel=1e-12)
+    r = _mu(W.MAT_GOS, 0.2)[1] / _mu(W.MAT_GOS, 0.1)[1]
+    assert r == pytest.approx(2 ** -3.2, rel=1e-12)
+    # K edge at 50.24 keV: continuous for copper, a jump below 5.3 (Gd's own ratio) for Gd2O2S
+    ek = 0.05024
+    assert _mu(W.MAT_CU, ek * (1 + 1e-9))[1] == pytest.approx(_mu(W.MAT_CU, ek * (1 - 1e-9))[1], rel=1e-7)
+    jump = _mu(W.MAT_GOS, ek * (1 + 1e-9))[1] / _mu(W.MAT_GOS, ek * (1 - 1e-9))[1]
+    assert 4.5 < jump < 5.3
+
+
+def test_pair_structure():
+    for m in range(7):
+        assert _mu(m, 1.0219)[2] == 0.0
+        assert _mu(m, 1.02)[2] == 0.0
+        assert _mu(m, 1.03)[2] > 0.0
+    # per-atom pair cross section scales as Z(Z+1): copper vs silicon
+    cu, si = _mu(W.MAT_CU, 4.0)[2] * 63.546, _mu(W.MAT_SI, 4.0)[2] * 28.085
+    assert cu / si == pytest.approx(29 * 30 / (14 * 15), rel=1e-12)
+
+
+def test_compton_uses_electron_density():
+    zA_water = 0.111894 * 1 / 1.008 + 0.888106 * 8 / 15.999
+    for E in (0.05, 1.0, 5.0):
+        assert _mu(W.MAT_WATER, E)[0] == pytest.approx(NA * zA_water * L.orc_sigma_kn(E), rel=1e-12)
+
+
+# ------------------------------------------------------------- spectrum ---
+
+def _spectrum(n, seed=3, emax=6.0, ecut=0.01):
+    out = np.empty(n)
+    L.orc_sample_spectrum_many(emax, ecut, seed, n,
+                               out.ctypes.data_as(np.ctypeslib.ctypes.POINTER(np.ctypeslib.ctypes.c_double)))
+    return out
+
+
+def test_spectrum_beta_ks_and_mean():
+    n = 200_000
+    E = _spectrum(n)
+    xc = 0.01 / 6.0
+    F = lambda x: special.betainc(1.5, 3.5, x)
+    Fc = F(xc)
+    cdf = lambda e: (F(np.clip(e / 6.0, xc, 1.0)) - Fc) / (1.0 - Fc)
+    assert stats.kstest(E, cdf).pvalue > 1e-3
+    # untruncated mean is 6 * 1.5/5 = 1.8 MeV; truncation at 10 keV shifts it slightly
+    pdf = lambda x: x ** 0.5 * (1 - x) ** 2.5 / special.beta(1.5, 3.5)
+    mean_t = 6.0 * integrate.quad(lambda x: x * pdf(x), xc, 1)[0] / (1 - Fc)
+    assert abs(mean_t - 1.8) < 1e-3
+    assert abs(E.mean() - mean_t) < 4 * E.std() / math.sqrt(n)
+    assert E.min() >= 0.01 and E.max() <= 6.0
+
+
+# ---------------------------------------------------- transport pins -----
+
+@pytest.mark.parametrize("E,n", [(1.0, 2_000_000), (2.0, 1_000_000), (5.0, 1_000_000)])
+def test_narrow_beam_attenuation(E, n):
+    """Uncollided transmission of a pencil beam through 20 cm of water = exp(-mu x)."""
+    prob = W.config_water_open(n_histories=n, field_cm=0.1)
+    phys = W.Physics(coupled=False, mono_energy=E)
+    r = oracle.run(prob, physics=phys)
+    mu = _mu(W.MAT_WATER, E).sum() * 1.0
+    expect = math.exp(-mu * 20.0)
+    got = r["counters"]["uncollided_at_epid"] / n
+    sd = math.sqrt(expect * (1 - expect) / n)
+    assert 0.005 * expect > 3 * sd          # the 0.5 % bar is at least 3 sigma
+    assert abs(got / expect - 1) < 0.005
+
+
+def _voxel_chords(origin, vox, shape, start, d):
+    """Exact chord of the ray start + t d (t >= 0) in each voxel, by slab clipping."""
+    nz, ny, nx = shape
+    rows = []
+    for iz in range(nz):
+        for iy in range(ny):
+            for ix in range(nx):
+                lo = np.array([origin[0] + ix * vox, origin[1] + iy * vox, origin[2] + iz * vox])
+                hi = lo + vox
+                t0, t1 = 0.0, np.inf
+                for a in range(3):
+                    if d[a] != 0:
+                        ta, tb = sorted(((lo[a] - start[a]) / d[a], (hi[a] - start[a]) / d[a]))
+                        t0, t1 = max(t0, ta), min(t1, tb)
+                    elif not lo[a] <= start[a] <= hi[a]:
+                        t1 = -1
+                if t1 > t0:
+                    rows.append((t0, t1 - t0, (iz * ny + iy) * nx + ix))
+    rows.sort()
+    return rows
+
+
+@pytest.mark.parametrize("E", [0.08, 5.0])
+def test_woodcock_first_interaction_enumeration(E):
+    """First real interaction voxel and type on a random 4^3 grid vs the exact
+    probabilities prod_{u<v} e^{-mu_u l_u} (1 - e^{-mu_v l_v}) mu_j/mu_v."""
+    rng = np.random.default_rng(5)
+    hu = rng.choice([-1000, -750, -300, 0, 80, 700, 1400], size=(4, 4, 4)).astype(np.int16)
+    ph = W.Phantom(hu, (1.0, 1.0, 1.0), (-2.0, -2.0, -2.0))
+    prob = W.config_water_open(n_histories=1)
+    prob.phantom = ph
+    start = np.array([-1.7, -2.0, -1.1])
+    d = np.array([0.35, 1.0, 0.22]); d /= np.linalg.norm(d)
+    n = 300_000
+    vox, typ = oracle.first_interaction(prob, E, start, d, n, seed=9)
+    rho, mat = oracle.hu_to_rho_mat(hu.ravel())
+    cats, probs, trans = [], [], 1.0
+    for _, l, v in _voxel_chords(ph.origin, 1.0, hu.shape, start, d):
+        mu = _mu(mat[v], E) * rho[v]
+        tot = mu.sum()
+        pint = trans * (1 - math.exp(-tot * l))
+        for j in range(3):
+            if mu[j] > 0:
+                cats.append((v, j)); probs.append(pint * mu[j] / tot)
+        trans *= math.exp(-tot * l)
+    cats.append((-1, -1)); probs.append(trans)
+    probs = np.array(probs)
+    assert abs(probs.sum() - 1) < 1e-12
+    index = {c: i for i, c in enumerate(cats)}
+    obs = np.zeros(len(cats))
+    for v, t in zip(vox, typ):
+        obs[index[(int(v), int(t))]] += 1
+    exp_ = n * probs
+    big = exp_ >= 5
+    chi2 = ((obs[big] - exp_[big]) ** 2 / exp_[big]).sum()
+    rest_o, rest_e = obs[~big].sum(), exp_[~big].sum()
+    dof = big.sum() - 1
+    if rest_e > 0:
+        chi2 += (rest_o - rest_e) ** 2 / rest_e
+        dof += 1
+    assert stats.chi2.sf(chi2, dof) > 1e-3
+
+
+@pytest.mark.parametrize("coupled", [False, True])
+def test_energy_conservation(coupled):
+    prob = W.config_thorax_imrt(n_histories=4000, scale=4, epid_scale=4)
+    prob.physics.coupled = coupled
+    r = oracle.run(prob)
+    out = r["e_ct"] + r["e_epid"].sum() + r["e_esc"] + r["e_lost"]
+    assert abs(out - r["e_src"]) / r["e_src"] < 1e-9
+    assert r["counters"]["lost"] == 0
+    assert r["tally"].sum() == pytest.approx(r["e_epid"][prob.epid.sensitive], rel=1e-12)
+
+
+def test_thread_count_invariance():
+    prob = W.config_thorax_imrt(n_histories=3000, scale=4, epid_scale=8)
+    a = oracle.run(prob, threads=1)
+    b = oracle.run(prob, threads=8)
+    assert np.array_equal(a["tally"], b["tally"])
+    assert a["counters"] == b["counters"]
+    assert a["e_src"] == pytest.approx(b["e_src"], rel=1e-13)
+
+
+# ---------------------------------------------------- electron physics ---
+
+def _unrestricted_bethe(m_zA, I_eV, T):
+    """ICRU 37 unrestricted electron collision stopping power, no density effect."""
+    tau = T / MC2
+    g = tau + 1
+    b2 = 1 - 1 / g ** 2
+    F = 1 - b2 + (tau ** 2 / 8 - (2 * tau + 1) * math.log(2)) / g ** 2
+    pref = 2 * math.pi * RE ** 2 * MC2 * NA * m_zA / b2
+    return pref * (math.log(tau ** 2 * (tau + 2) / (2 * (I_eV * 1e-6 / MC2) ** 2)) + F)
+
+
+ZA_WATER = 0.111894 / 1.008 + 0.888106 * 8 / 15.999
+
+
+@pytest.mark.parametrize("T", [0.25, 0.35, 1.0, 4.0])
+def test_stopping_power_unrestricted_limit(T):
+    # restricted formula with the cut at T/2 must equal the unrestricted closed form
+    assert L.orc_lcol(W.MAT_WATER, T, T / 2) == pytest.approx(_unrestricted_bethe(ZA_WATER, 75.0, T), rel=1e-12)
+
+
+def _moller_f(eps, tau):
+    g = tau + 1
+    c, b = tau / g, (2 * tau + 1) / g ** 2
+    return 1 / eps ** 2 + 1 / (1 - eps) ** 2 + c * c - b / (eps * (1 - eps))
+
+
+@pytest.mark.parametrize("T", [0.5, 1.0, 3.0, 6.0])
+def test_moller_cross_section_and_restricted_loss(T):
+    """sigma_hard and the soft/hard split of the stopping power both follow from
+    the Moller differential cross section integrated numerically."""
+    wcc = 0.2
+    tau = T / MC2
+    b2 = 1 - 1 / (tau + 1) ** 2
+    pref = NA * ZA_WATER * 2 * math.pi * RE ** 2 * MC2 / b2
+    ec = wcc / T
+    sig = pref / T * integrate.quad(lambda e: _moller_f(e, tau), ec, 0.5, epsrel=1e-12)[0]
+    assert L.orc_sigma_moller(W.MAT_WATER, T, wcc) == pytest.approx(sig, rel=1e-9)
+    hard_loss = pref * integrate.quad(lambda e: e * _moller_f(e, tau), ec, 0.5, epsrel=1e-12)[0]
+    diff = L.orc_lcol(W.MAT_WATER, T, T / 2) - L.orc_lcol(W.MAT_WATER, T, wcc)
+    assert diff == pytest.approx(hard_loss, rel=1e-9)
+
+
+@pytest.mark.parametrize("T", [0.6, 3.0])
+def test_moller_sampler_chi2(T):
+    n = 200_000
+    eps = np.empty(n)
+    L.orc_sample_moller_many(T, 0.2, 21, n,
+                             eps.ctypes.data_as(np.ctypeslib.ctypes.POINTER(np.ctypeslib.ctypes.c_double)))
+    tau, ec = T / MC2, 0.2 / T
+    assert eps.min() >= ec and eps.max() <= 0.5
+    edges = np.geomspace(ec, 0.5, 31)
+    tot = integrate.quad(lambda e: _moller_f(e, tau), ec, 0.5, epsrel=1e-12)[0]
+    p = np.array([integrate.quad(lambda e: _moller_f(e, tau), a, b, epsrel=1e-12)[0]
+                  for a, b in zip(edges[:-1], edges[1:])]) / tot
+    obs, _ = np.histogram(eps, edges)
+    chi2 = ((obs - n * p) ** 2 / (n * p)).sum()
+    assert stats.chi2.sf(chi2, len(p) - 1) > 1e-3
+
+
+def test_brem_and_hard_cross_sections_monotone():
+    """The hard-event majorant is taken at the step's start energy, which is
+    valid only if sigma_moller + sigma_brem never decreases with T."""
+    T = np.geomspace(0.2, 6.1, 3000)
+    for m in range(7):
+        s = np.array([L.orc_sigma_moller(m, t, 0.2) + L.orc_sigma_brem(m, t, 0.01) for t in T])
+        assert np.all(np.diff(s) >= 0)
+        # hard brems is A ln(T/wcb) and soft radiative loss A wcb for one A per material
+        A = L.orc_lrad_soft(m, 1.0, 0.01) / 0.01
+        assert L.orc_sigma_brem(m, 2.0, 0.01) == pytest.approx(A * math.log(200.0), rel=1e-12)
+
+
+@pytest.mark.parametrize("T0", [0.5, 1.0, 3.0, 6.0])
+def test_csda_path_matches_range_integral(T0):
+    f = lambda T: 1.0 / (L.orc_lcol(W.MAT_WATER, T, 0.2) + L.orc_lrad_soft(W.MAT_WATER, T, 0.01))
+    rng_int = integrate.quad(f, 0.2, T0, epsrel=1e-10, points=[0.4] if T0 > 0.4 else None)[0]
+    path = L.orc_csda_path(W.MAT_WATER, 1.0, T0, 0.2, 0.2, 0.01, 0.05)
+    assert path == pytest.approx(rng_int, rel=2e-4)
+    # the same path scales as 1/rho
+    assert L.orc_csda_path(W.MAT_WATER, 2.0, T0, 0.2, 0.2, 0.01, 0.05) == pytest.approx(path / 2, rel=1e-12)
+
+
+@pytest.mark.parametrize("G", [0.003, 0.05, 0.3, 1.5])
+def test_multiple_scattering_first_moment_and_shape(G):
+    n = 400_000
+    ct = np.empty(n)
+    L.orc_sample_ms_many(G, 31, n, ct.ctypes.data_as(np.ctypeslib.ctypes.POINTER(np.ctypeslib.ctypes.c_double)))
+    x = 1 - ct
+    target = 1 - math.exp(-G)
+    assert abs(x.mean() - target) < 4 * x.std() / math.sqrt(n)
+    # screened-Rutherford shape: P(mu <= y) = (1+A) y / (y + A), mu = (1-cos)/2
+    A = L.orc_wentzel_A(G)
+    mu = x / 2
+    assert stats.kstest(mu, lambda y: (1 + A) * y / (y + A)).pvalue > 1e-3
+
+
+def test_wentzel_solver_limits():
+    assert L.orc_wentzel_A(0.0) == 0.0
+    assert L.orc_wentzel_A(30.0) < 0       # isotropic flag
+    for G in (1e-6, 1e-3, 0.1, 1.0, 5.0):
+        A = L.orc_wentzel_A(G)
+        mean = A * ((1 + A) * math.log1p(1 / A) - 1)
+        assert mean == pytest.approx(-0.5 * math.expm1(-G), rel=1e-10)
+
+
+def test_lambda1_rossi_scaling():
+    # small-angle limit: <theta^2>/2 per cm = Es^2 / (2 X0 p^2 beta^2); check the 1/(p beta)^2 law
+    def pb2(T):
+        pc2 = T * (T + 2 * MC2)
+        return pc2 * pc2 / (T + MC2) ** 2
+    r = L.orc_lambda1_inv(W.MAT_WATER, 1.0) / L.orc_lambda1_inv(W.MAT_WATER, 3.0)
+    assert r == pytest.approx(pb2(3.0) / pb2(1.0), rel=1e-12)
+    # water: X0 from the textbook radiation-length formula lies within 5 % of 36.08 g/cm^2
+    X0 = 0.5 * 21.2 ** 2 / (L.orc_lambda1_inv(W.MAT_WATER, 1.0) * pb2(1.0))
+    assert 34.0 < X0 < 38.5
+
+
+# -------------------------------------------------------- HU curve --------
+
+def test_hu_curve_special_values():
+    hu = np.array([-2000, -1024, -1000, -901, -900, -201, -200, 0, 299, 300, 1000, 5000])
+    rho, mat = oracle.hu_to_rho_mat(hu)
+    assert list(mat) == [0, 0, 0, 0, 1, 1, 2, 2, 2, 3, 3, 3]
+    assert rho[0] == rho[1] == rho[2] == pytest.approx(0.001205)
+    assert rho[7] == 1.0
+    assert rho[10] == pytest.approx(1.6)
+    assert rho[11] == pytest.approx(1 + 0.6 * 3.071)
+    assert np.all(np.diff(rho) >= 0)
+
+
+# ------------------------------------------------------------ source ------
+
+def test_source_aperture_uniform_and_mu_weighted():
+    edges = np.array([-6.0, -2.0, 2.0, 6.0])
+    leaves = np.array([[[-5.0, 0.0], [-5.0, 0.0], [-5.0, 0.0]],
+                       [[1.0, 1.0], [2.0, 4.0], [1.0, 1.0]]])
+    jaws = np.array([[-10, 10, -5, 5], [-10, 10, -10, 10]], dtype=float)
+    fld = W.Field(edges, leaves, jaws, np.array([1.0, 3.0]))
+    prob = W.config_water_open(n_histories=1)
+    prob.field = fld
+    n = 300_000
+    X, Y, E = oracle.sample_source(prob, n, seed=4)
+    inA = (X >= -5) & (X <= 0) & (Y >= -5) & (Y <= 5)
+    inB = (X >= 2) & (X <= 4) & (Y >= -2) & (Y <= 2)
+    assert np.all(inA | inB)
+    pA = 1.0 * 50.0 / (50.0 + 3.0 * 8.0)
+    assert abs(inA.mean() - pA) < 4 * math.sqrt(pA * (1 - pA) / n)
+    # flat fluence inside segment A: 10 x 10 cells
+    h, _, _ = np.histogram2d(X[inA], Y[inA], bins=[np.linspace(-5, 0, 11), np.linspace(-5, 5, 11)])
+    e = inA.sum() / 100.0
+    assert stats.chi2.sf(((h - e) ** 2 / e).sum(), 99) > 1e-3
+
+
+# ------------------------------------------------------------ Siddon ------
+
+def test_siddon_homogeneous_chord():
+    prob = W.config_water_open(n_histories=1)
+    rng = np.random.default_rng(2)
+    ph = prob.phantom
+    lo = np.array(ph.origin)
+    hi = lo + np.array(ph.shape_xyz) * 0.5
+    for _ in range(20):
+        p1 = rng.uniform(-60, 60, 3); p1[1] = -100.0
+        p2 = rng.uniform(-30, 30, 3); p2[1] = 50.0
+        d = p2 - p1
+        t0, t1 = 0.0, 1.0
+        for a in range(3):
+            ta, tb = sorted(((lo[a] - p1[a]) / d[a], (hi[a] - p1[a]) / d[a]))
+            t0, t1 = max(t0, ta), min(t1, tb)
+        chord = max(0.0, t1 - t0) * np.linalg.norm(d)
+        assert oracle.siddon_ray(prob, p1, p2) == pytest.approx(chord, rel=1e-12, abs=1e-12)
+
+
+def test_siddon_random_grid_vs_quadrature():
+    rng = np.random.default_rng(8)
+    hu = rng.integers(-1000, 1500, size=(6, 7, 5)).astype(np.int16)
+    ph = W.Phantom(hu, (1.3, 0.7, 1.1), (-3.0, -2.5, -3.3))
+    prob = W.config_water_open(n_histories=1)
+    prob.phantom = ph
+    rho, _ = oracle.hu_to_rho_mat(hu.ravel())
+    nx, ny, nz = 5, 7, 6
+    for _ in range(5):
+        p1 = rng.uniform(-8, 8, 3); p1[1] = -20.0
+        p2 = rng.uniform(-4, 4, 3); p2[1] = 20.0
+        npts = 400_000
+        ts = (np.arange(npts) + 0.5) / npts
+        pts = p1[None] + ts[:, None] * (p2 - p1)[None]
+        ix = np.floor((pts[:, 0] + 3.0) / 1.3).astype(int)
+        iy = np.floor((pts[:, 1] + 2.5) / 0.7).astype(int)
+        iz = np.floor((pts[:, 2] + 3.3) / 1.1).astype(int)
+        ok = (ix >= 0) & (ix < nx) & (iy >= 0) & (iy < ny) & (iz >= 0) & (iz < nz)
+        vals = np.zeros(npts)
+        vals[ok] = rho[(iz[ok] * ny + iy[ok]) * nx + ix[ok]]
+        quad = vals.sum() * np.linalg.norm(p2 - p1) / npts
+        assert oracle.siddon_ray(prob, p1, p2) == pytest.approx(quad, rel=2e-3, abs=1e-3)
+
+
+def test_tmap_central_pixel_water_slab():
+    prob = W.config_water_open(n_histories=1)
+    t = oracle.tmap(prob, np.array([64]), np.array([64]))
+    # pixel centre (0.15, 0.15) at 150 cm: the ray crosses y in [-10, 10] at a tiny angle
+    x, y, z = 0.15, -50.0, 0.15      # beam frame (X, Z, Y) mapped to the slab axes
+    cosfac = math.sqrt(0.15 ** 2 + 0.15 ** 2 + 150.0 ** 2) / 150.0
+    assert t[0] == pytest.approx(20.0 * cosfac, rel=1e-12)
+
+
+# ---------------------------------------------- Eq. 1 and the LUT ---------
+
+def test_eq1_equivalent_square():
+    for a, b in ((10, 10), (5, 20), (3.5, 12.25)):
+        f = W.open_field(a, b)
+        assert oracle.effective_field_size(f) == pytest.approx(2 * a * b / (a + b), rel=1e-12)
+    assert oracle.effective_field_size(W.open_field(10, 10)) == pytest.approx(10.0)
+    assert oracle.effective_field_size(W.open_field(10, 10), literal=True) == pytest.approx(2.5)
+
+
+def test_aperture_bbox_vs_raster():
+    f = W.imrt_field(np.random.default_rng(3), 5)
+    a, b = oracle.aperture_bbox(f)
+    h = 0.01
+    xs = np.arange(-12, 12, h) + h / 2
+    X0, X1, Y0, Y1 = np.inf, -np.inf, np.inf, -np.inf
+    for k in range(5):
+        for j in range(60):
+            y0, y1 = max(f.pair_edges[j], f.jaws[k, 2]), min(f.pair_edges[j + 1], f.jaws[k, 3])
+            xin = xs[(xs >= max(f.leaves[k, j, 0], f.jaws[k, 0])) & (xs <= min(f.leaves[k, j, 1], f.jaws[k, 1]))]
+            if y1 > y0 and xin.size:
+                X0, X1, Y0, Y1 = min(X0, xin.min()), max(X1, xin.max()), min(Y0, y0), max(Y1, y1)
+    assert a == pytest.approx(X1 - X0, abs=2 * h)
+    assert b == pytest.approx(Y1 - Y0, abs=1e-12)
+
+
+def test_lut_reproduces_table1_and_interpolates():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table1_k_ts.txt")) if not l.startswith("#")]
+    s_nodes = [float(r[0]) for r in rows]
+    K = np.array([[float(v) for v in r[1:]] for r in rows])
+    lut = W.lut_table1()
+    for i, s in enumerate(s_nodes):
+        for j, t in enumerate([0, 5, 10, 15, 20]):
+            assert oracle.lut_k(lut, t, s) == pytest.approx(K[i, j], abs=1e-15)
+    # midpoints along t are the average of the two neighbours, centres of four cells the mean of four
+    assert oracle.lut_k(lut, 7.5, 10) == pytest.approx((K[1, 1] + K[1, 2]) / 2, abs=1e-15)
+    assert oracle.lut_k(lut, 7.5, 12.5) == pytest.approx(K[1:3, 1:3].mean(), abs=1e-15)
+    # clamped outside the grid
+    assert oracle.lut_k(lut, -3, 2) == pytest.approx(K[0, 0], abs=1e-15)
+    assert oracle.lut_k(lut, 35, 40) == pytest.approx(K[3, 4], abs=1e-15)
+
+
+def test_lut_bilinear_table_exact():
+    lut = W.lut_bilinear()
+    rng = np.random.default_rng(1)
+    t = rng.uniform(0, 40, 1000)
+    for s in rng.uniform(2, 30, 10):
+        want = 1 + 0.1 * ((s - 16) / 14) * (t / 40)
+        assert np.allclose(oracle.lut_k(lut, t, s), want, rtol=0, atol=1e-14)
+
+
+# ------------------------------------------------------------ gamma -------
+
+def test_gamma_identical_and_offset():
+    rng = np.random.default_rng(0)
+    ref = 1 + rng.random((40, 50))
+    rate, g = oracle.gamma(ref, ref, pixel_mm=2.5, dd=0.03, dta_mm=3.0)
+    assert rate == 1.0 and np.nanmax(g) == 0.0
+    flat = np.full((30, 30), 2.0)
+    rate, g = oracle.gamma(flat, flat * 1.05, pixel_mm=2.5, dd=0.03, dta_mm=3.0)
+    assert np.allclose(g[np.isfinite(g)], 0.05 / 0.03, rtol=1e-12)
+    assert rate == 0.0
+
+
+def test_gamma_shifted_ramp_closed_form():
+    """Ramp R = a + g x shifted by s: gamma = |s g| / sqrt(DD^2 + g^2 DTA^2),
+    reached at a displacement g^2 s DTA^2 / (DD^2 + g^2 DTA^2) (here ~0.9 mm)."""
+    nx, pix = 20, 1.0
+    x = np.arange(nx) * pix
+    gslope, s, dta = 0.2, 1.0, 2.0
+    ref = np.tile(1.0 + gslope * x, (5, 1))
+    ev = np.tile(1.0 + gslope * (x - s), (5, 1))
+    dd_abs = 0.03 * ref.max()
+    want = abs(s * gslope) / math.sqrt(dd_abs ** 2 + gslope ** 2 * dta ** 2)
+    _, g = oracle.gamma(ref, ev, pixel_mm=pix, dd=0.03, dta_mm=dta, threshold=0.0, step_mm=0.005,
+                        radius_mm=2.0)
+    assert np.allclose(g[:, 4:16], want, rtol=1e-4)
+
+
+# ------------------------------------------------------ statistics --------
+
+def test_batch_statistics_unbiased():
+    """With independent batch values of known spread, sigma estimates the
+    standard error of the mean and u is its mean relative value."""
+    B, npix, n = 16, 20_000, 1600
+    rng = np.random.default_rng(12)
+    epid = W.epid_default(npix, 1, 0.1)
+    per_hist_mev, tau = 2.0, 0.3
+    nb = oracle.batch_counts(n, B)
+    assert nb.sum() == n and np.all(nb == 100)
+    tally = (per_hist_mev + tau * rng.standard_normal((B, 1, npix))) * nb[:, None, None]
+    mean, sigma, u = oracle.dose_stats(tally, n, epid)
+    _, thick, rho = epid.layers[epid.sensitive]
+    conv = 1.602176634e-13 / (rho * 0.1 * 0.1 * thick * 1e-3)
+    assert np.allclose(mean, tally.sum(0) / n * conv)
+    # E[sigma^2] = tau^2 / B in dose units
+    assert np.mean(sigma ** 2) == pytest.approx((tau * conv) ** 2 / B, rel=0.03)
+    assert u == pytest.approx(np.mean(sigma / mean), rel=1e-12)
+
+
+def test_batch_counts_ragged():
+    for n, h0 in ((0, 0), (5, 0), (37, 3), (1000, 15)):
+        ids = np.arange(h0, h0 + n) % 16
+        assert np.array_equal(oracle.batch_counts(n, 16, h0), np.bincount(ids, minlength=16))
