@@ -179,7 +179,8 @@ double orc_lambda1_inv(int m, double T) {
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and the per-particle    */
 /* draw stream.  Draw d of particle (hist h, ordinal o) is word d mod 4 of   */
 /* Philox(counter = (d div 4, o, h_lo, h_hi), key = (seed_lo, seed_hi)),     */
-/* mapped to ((u >> 8) + 0.5) 2^-24.                                         */
+/* mapped to ((u >> 9) + 0.5) 2^-23, a value exact in single and double      */
+/* precision and strictly inside (0, 1).                                     */
 /* ------------------------------------------------------------------------ */
 void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
     uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
@@ -222,7 +223,7 @@ static double rng_u(o_rng* r) {
         r->cblk = blk; r->cvalid = 1;
     }
     r->d++;
-    return ((double)(r->cbuf[w] >> 8) + 0.5) * (1.0 / 16777216.0);
+    return ((double)(r->cbuf[w] >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -319,7 +320,7 @@ static void rotate(double u[3], double ct, double phi) {
     double st = sqrt(fmax(0.0, 1.0 - ct * ct));
     double cp = cos(phi), sp = sin(phi);
     double w = u[2];
-    if (fabs(w) > 0.99999999) {
+    if (fabs(w) > 0.99999) {          /* polar frame near the z axis */
         double sg = (w > 0) ? 1.0 : -1.0;
         u[0] = st * cp; u[1] = st * sp; u[2] = sg * ct;
     } else {

@@ -47,7 +47,7 @@ def test_philox_known_answers():
 
 
 def test_draw_stream_layout():
-    """Draw d is word d mod 4 of block d div 4 on a 24-bit grid strictly inside (0,1)."""
+    """Draw d is word d mod 4 of block d div 4 on a 23-bit grid strictly inside (0,1)."""
     import ctypes as C
     seed, h, ord_ = 0x1234_5678_9ABC, 77, 5
     out = (C.c_double * 9)()
@@ -58,7 +58,7 @@ def test_draw_stream_layout():
     for blk in range(3):
         w = (C.c_uint32 * 4)()
         L.orc_philox((C.c_uint32 * 4)(blk, ord_, h, 0), key, w)
-        want += [((x >> 8) + 0.5) / 2 ** 24 for x in w]
+        want += [((x >> 9) + 0.5) / 2 ** 23 for x in w]
     assert np.array_equal(got, np.array(want[:9]))
     assert np.all((got > 0) & (got < 1))
 
