@@ -1,0 +1,221 @@
+/*
+ * archer_epid.h -- C ABI of the B300 EPID transit Monte Carlo library.
+ *
+ * The library computes, on one GPU, the data-parallel core of the method of
+ * "A GPU-based Monte Carlo framework for IMRT QA using EPID transit dosimetry"
+ * (ARCHER-EPID): photons from an MLC-shaped 6 MV source (Sec. 2.1.1) are
+ * transported with coupled photon/electron Monte Carlo through a CT-derived
+ * voxel patient (Sec. 2.1.2) into a multi-layer EPID (Sec. 2.1.3); the energy
+ * deposited in the sensitive layer is tallied per pixel and converted into a
+ * detector signal with the k(t, s) table of Sec. 2.2 / Sec. 3.1 (Eq. 1, Eq. 2,
+ * Table 1).
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an mc_status; no C++ exception crosses the ABI.
+ *    mc_last_error() returns a description of the last failure of a context.
+ *  - Pointers are plain host or device addresses as stated per argument; the
+ *    caller owns every array it passes and every output buffer.  Inputs are
+ *    copied, so they may be freed when the call returns (device inputs: once
+ *    the stream has reached the call).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    ordered on it; mc_run synchronizes it before returning.
+ *  - Units: cm, MeV, g/cm^3; doses in Gy per source history.
+ *  - Arrays are row-major, last index fastest: CT [nz][ny][nx], EPID images
+ *    [npy][npx], tallies [B][npy][npx], k-table [ns][nt].
+ *  - A context is bound to one device and is not thread-safe; use one context
+ *    per host thread.
+ */
+#ifndef ARCHER_EPID_H
+#define ARCHER_EPID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mc_status {
+    MC_OK = 0,
+    MC_ERR_ARG = 1,        /* invalid argument (null pointer, size, range, order of calls) */
+    MC_ERR_CUDA = 2,       /* a CUDA runtime call failed; see mc_last_error */
+    MC_ERR_OOM = 3,        /* device allocation failed */
+    MC_ERR_STATE = 4,      /* call out of order (e.g. mc_run before mc_set_field) */
+    MC_ERR_TIMEOUT = 5,    /* a bounded device wait gave up */
+    MC_ERR_CANCELLED = 6,  /* mc_cancel() stopped the run between waves */
+    MC_ERR_NUMERIC = 7,    /* non-finite value detected */
+    MC_ERR_OVERFLOW = 8    /* a particle bank filled; the run's energy balance is incomplete */
+} mc_status;
+
+/* Material ids (compositions are the library's stated readings; the paper
+ * names the materials of Sec. 2.1.2 / Sec. 2.1.3 without giving data). */
+enum {
+    MC_MAT_AIR = 0, MC_MAT_LUNG = 1, MC_MAT_WATER = 2, MC_MAT_BONE = 3,
+    MC_MAT_CU = 4, MC_MAT_GD2O2S = 5, MC_MAT_SI = 6, MC_NUM_MATERIALS = 7
+};
+
+#define MC_MAX_LAYERS 8
+#define MC_NUM_COUNTERS 16
+
+/* Event counters, in the order of mc_run_stats.counters. */
+enum {
+    MC_CNT_FLIGHTS_CT = 0, MC_CNT_REAL_CT, MC_CNT_COMPTON, MC_CNT_PHOTO, MC_CNT_PAIR,
+    MC_CNT_ESTEPS_CT, MC_CNT_ESTEPS_EPID, MC_CNT_MOLLER, MC_CNT_BREM, MC_CNT_PRIMARIES_AT_EPID,
+    MC_CNT_UNCOLLIDED_AT_EPID, MC_CNT_LOST, MC_CNT_FLIGHTS_EPID, MC_CNT_ELECTRONS, MC_CNT_POSITRONS,
+    MC_CNT_SECONDARY_PHOTONS
+};
+
+/* Transport and execution settings.  Physics fields follow Sec. 2.1.2
+ * (10 keV photon and 200 keV electron cutoffs, Class II condensed history);
+ * the others are stated readings.  Fill with mc_config_default() first. */
+typedef struct mc_config {
+    int coupled;                  /* 1: transport electrons/positrons; 0: deposit them where created */
+    double e_max_mev;             /* 6 MV spectrum end point: E = e_max * Beta(3/2, 7/2) */
+    double mono_energy_mev;       /* > 0: monoenergetic source instead of the spectrum */
+    double photon_cutoff_mev;     /* 0.01 */
+    double electron_cutoff_mev;   /* 0.2 */
+    double wcc_mev;               /* hard Moller threshold, 0.2 */
+    double wcb_mev;               /* hard bremsstrahlung threshold, 0.01 */
+    double step_fraction;         /* largest CSDA energy-loss fraction per electron step, 0.05 */
+    int n_batches;                /* B sub-tallies (history id mod B) for the uncertainty, 16 */
+    int max_steps;                /* per-particle step cap; beyond it the energy is counted as lost */
+    int block_size;               /* threads per CTA of the transport kernels (multiple of 32), 0 = 256 */
+    int ctas_per_sm;              /* resident CTAs per SM for the persistent kernels, 0 = occupancy limit */
+    uint32_t bank_capacity;       /* particles per bank, 0 = 1<<22 */
+    uint32_t primaries_per_wave;  /* new histories per transport wave, 0 = bank_capacity / 4 */
+} mc_config;
+
+/* EPID layer stack from the source side (Sec. 2.1.3).  The centre of the
+ * sensitive layer lies on the plane at SID from the source; the pixel grid
+ * (npx along beam-frame X, npy along Y, pitch at the detector plane) also
+ * sets the detector's lateral extent. */
+typedef struct mc_epid_desc {
+    int n_layers;                         /* 1 .. MC_MAX_LAYERS */
+    int material[MC_MAX_LAYERS];          /* MC_MAT_* */
+    double thickness_cm[MC_MAX_LAYERS];
+    double density[MC_MAX_LAYERS];
+    int sensitive_layer;
+    int npx, npy;
+    double pitch_cm;
+} mc_epid_desc;
+
+/* One static IMRT field (Sec. 2.1.1): MLC segments at the isocentre plane.
+ * Host pointers; copied by mc_set_field. */
+typedef struct mc_field_desc {
+    int n_segments, n_pairs;
+    const double* pair_edges_cm;  /* [n_pairs + 1] leaf-pair boundaries along Y, increasing */
+    const double* leaves_cm;      /* [n_segments][n_pairs][2] left/right leaf tips along X */
+    const double* jaws_cm;        /* [n_segments][4] x1, x2, y1, y2 */
+    const double* mu;             /* [n_segments] monitor units (>= 0, not all zero) */
+    double gantry_deg;            /* rotation of source and EPID about the patient z axis */
+    double sad_cm, sid_cm;
+    double iso_cm[3];             /* isocentre in CT coordinates */
+    int eq1_literal;              /* 0: s = 2ab/(a+b); 1: s = ab/(2(a+b)) exactly as Eq. 1 is printed */
+} mc_field_desc;
+
+/* k(t, s) table of Sec. 3.1 (Eq. 2, Table 1): k[is * nt + it] on strictly
+ * increasing node axes, bilinear inside and clamped outside.  Host pointers. */
+typedef struct mc_lut_desc {
+    int nt, ns;                   /* 2 .. 1024 each */
+    const double* t_nodes;        /* radiological thickness, cm */
+    const double* s_nodes;        /* equivalent square field size, cm */
+    const double* k;              /* [ns][nt] */
+    double k_scale;               /* signal = k_scale * k(t, s) * dose */
+    double t_offset_cm;           /* added to every ray sum (e.g. a couch) */
+} mc_lut_desc;
+
+/* Cumulative results since the last mc_set_field / mc_reset_tally. */
+typedef struct mc_run_stats {
+    uint64_t histories;
+    double e_src_mev, e_ct_mev, e_epid_mev[MC_MAX_LAYERS], e_esc_mev, e_lost_mev;
+    uint64_t counters[MC_NUM_COUNTERS];
+    int waves;                    /* transport waves of the last mc_run */
+    uint32_t error_flags;         /* device-side error bits of the last mc_run */
+    double gpu_ms;                /* device time of the last mc_run (CUDA events) */
+} mc_run_stats;
+
+typedef struct mc_ctx mc_ctx;
+
+/* Defaults stated above. */
+void mc_config_default(mc_config* cfg);
+
+/* Creates a context on `device`, allocating its particle banks and tables.
+ * cfg may be NULL (defaults).  *out is NULL on failure. */
+mc_status mc_create(const mc_config* cfg, int device, mc_ctx** out);
+
+/* Frees every device and host allocation of ctx (NULL is a no-op). */
+mc_status mc_destroy(mc_ctx* ctx);
+
+/* Step a1 (Sec. 2.1.2, HU-to-density curve): copies the int16 HU volume
+ * [nz][ny][nx] (host pointer, or device pointer when hu_on_device != 0) and
+ * converts it on the GPU to per-voxel density; material follows from the
+ * density thresholds.  vox_cm: voxel size, origin_cm: lower corner of the box.
+ * Also takes the EPID stack.  Invalidates any field set before. */
+mc_status mc_init_geometry(mc_ctx* ctx, const int16_t* hu, int nx, int ny, int nz, const double vox_cm[3],
+                           const double origin_cm[3], const mc_epid_desc* epid, int hu_on_device,
+                           void* stream);
+
+/* Steps a2 (source set-up), a9 (radiological thickness, Sec. 2.2 item 1: a
+ * ray sum of density from the source to every pixel centre, FP64
+ * accumulation), a10 (Eq. 1 on the bounding rectangle of the union of open
+ * apertures) and the k-table upload.  Resets the tally.  lut may be NULL
+ * (then mc_get_epid_image is unavailable). */
+mc_status mc_set_field(mc_ctx* ctx, const mc_field_desc* field, const mc_lut_desc* lut, void* stream);
+
+/* Steps a2-a7: transports n_histories histories (ids continue from the
+ * previous run, so repeated calls equal one longer run) with Philox keyed by
+ * seed, adding to the tally.  Synchronizes `stream`.  stats may be NULL. */
+mc_status mc_run(mc_ctx* ctx, uint64_t n_histories, uint64_t seed, void* stream, mc_run_stats* stats);
+
+/* Step a8: per-history dose (Gy) in the sensitive layer and its batch
+ * standard error, [npy][npx] doubles (host or device per on_device); sigma
+ * may be NULL.  u_out (host, may be NULL) receives the mean relative
+ * uncertainty over pixels above half the maximum dose. */
+mc_status mc_get_dose(mc_ctx* ctx, double* dose, double* sigma, double* u_out, int on_device, void* stream);
+
+/* Step a11 (Sec. 3.1): signal = k_scale * k(t, s) * dose per pixel, float32
+ * [npy][npx] (host or device per on_device). */
+mc_status mc_get_epid_image(mc_ctx* ctx, float* signal, int on_device, void* stream);
+
+/* The radiological thickness map t (cm, FP64) of the current field. */
+mc_status mc_get_tmap(mc_ctx* ctx, double* t, int on_device, void* stream);
+
+/* Raw integer sub-tallies [B][npy][npx], unit 2^-8 eV. */
+mc_status mc_get_tally(mc_ctx* ctx, uint64_t* tally, int on_device, void* stream);
+
+/* Equivalent square s (Eq. 1 reading) and bounding rectangle sides a, b (cm). */
+mc_status mc_field_size(mc_ctx* ctx, double* s, double* a, double* b);
+
+/* Cumulative statistics (energy balance from the fixed-point counters). */
+mc_status mc_get_stats(mc_ctx* ctx, mc_run_stats* stats);
+
+/* Clears tally, counters and the history id sequence. */
+mc_status mc_reset_tally(mc_ctx* ctx, void* stream);
+
+/* Checkpoint / resume: the state is the sub-tallies, counters and next history
+ * id.  mc_state_size gives the byte size; get/set copy it to/from a host
+ * buffer.  Because the random streams are keyed by history id, a resumed run
+ * is bitwise identical to an uninterrupted one. */
+mc_status mc_state_size(mc_ctx* ctx, size_t* bytes);
+mc_status mc_get_state(mc_ctx* ctx, void* host_buf, size_t bytes, void* stream);
+mc_status mc_set_state(mc_ctx* ctx, const void* host_buf, size_t bytes, void* stream);
+
+/* Requests that a running mc_run on another host thread stop after its
+ * current wave (it then returns MC_ERR_CANCELLED). */
+mc_status mc_cancel(mc_ctx* ctx);
+
+const char* mc_last_error(const mc_ctx* ctx);
+const char* mc_status_string(mc_status s);
+
+/* Diagnostic: Philox4x32-10 (Salmon et al., SC'11) on the GPU.  in: device
+ * [n][6] uint32 (ctr0..3, key0, key1), out: device [n][4]. */
+mc_status mc_test_philox(const uint32_t* in, uint32_t* out, int n, void* stream);
+
+/* Diagnostic: the first n uniforms of the draw stream of particle (hist, ord)
+ * under seed, as the transport kernels draw them.  out: device float [n]. */
+mc_status mc_test_uniforms(uint64_t seed, uint64_t hist, uint32_t ord, int n, float* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ARCHER_EPID_H */

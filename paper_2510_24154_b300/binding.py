@@ -1,0 +1,337 @@
+"""Thin Python binding of libarcher_epid.so (the C ABI in include/archer_epid.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  There is no CPU fallback; if the library cannot be loaded, importing
+this module raises.  Device buffers and streams come from PyTorch.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+from . import build as _build
+
+MAX_LAYERS = 8
+NUM_COUNTERS = 16
+COUNTER_NAMES = ("flights_ct", "real_ct", "compton", "photo", "pair", "esteps_ct", "esteps_epid",
+                 "moller", "brem", "primaries_at_epid", "uncollided_at_epid", "lost", "flights_epid",
+                 "electrons", "positrons", "secondary_photons")
+STATUS = {0: "MC_OK", 1: "MC_ERR_ARG", 2: "MC_ERR_CUDA", 3: "MC_ERR_OOM", 4: "MC_ERR_STATE",
+          5: "MC_ERR_TIMEOUT", 6: "MC_ERR_CANCELLED", 7: "MC_ERR_NUMERIC", 8: "MC_ERR_OVERFLOW"}
+
+# Every entry point declared in include/archer_epid.h.
+EXPORTED = ("mc_config_default", "mc_create", "mc_destroy", "mc_init_geometry", "mc_set_field", "mc_run",
+            "mc_get_dose", "mc_get_epid_image", "mc_get_tmap", "mc_get_tally", "mc_field_size", "mc_get_stats",
+            "mc_reset_tally", "mc_state_size", "mc_get_state", "mc_set_state", "mc_cancel", "mc_last_error",
+            "mc_status_string", "mc_test_philox", "mc_test_uniforms")
+
+
+class Config(C.Structure):
+    _fields_ = [("coupled", C.c_int), ("e_max_mev", C.c_double), ("mono_energy_mev", C.c_double),
+                ("photon_cutoff_mev", C.c_double), ("electron_cutoff_mev", C.c_double),
+                ("wcc_mev", C.c_double), ("wcb_mev", C.c_double), ("step_fraction", C.c_double),
+                ("n_batches", C.c_int), ("max_steps", C.c_int), ("block_size", C.c_int),
+                ("ctas_per_sm", C.c_int), ("bank_capacity", C.c_uint32), ("primaries_per_wave", C.c_uint32)]
+
+
+class EpidDesc(C.Structure):
+    _fields_ = [("n_layers", C.c_int), ("material", C.c_int * MAX_LAYERS),
+                ("thickness_cm", C.c_double * MAX_LAYERS), ("density", C.c_double * MAX_LAYERS),
+                ("sensitive_layer", C.c_int), ("npx", C.c_int), ("npy", C.c_int), ("pitch_cm", C.c_double)]
+
+
+class FieldDesc(C.Structure):
+    _fields_ = [("n_segments", C.c_int), ("n_pairs", C.c_int), ("pair_edges_cm", C.POINTER(C.c_double)),
+                ("leaves_cm", C.POINTER(C.c_double)), ("jaws_cm", C.POINTER(C.c_double)),
+                ("mu", C.POINTER(C.c_double)), ("gantry_deg", C.c_double), ("sad_cm", C.c_double),
+                ("sid_cm", C.c_double), ("iso_cm", C.c_double * 3), ("eq1_literal", C.c_int)]
+
+
+class LutDesc(C.Structure):
+    _fields_ = [("nt", C.c_int), ("ns", C.c_int), ("t_nodes", C.POINTER(C.c_double)),
+                ("s_nodes", C.POINTER(C.c_double)), ("k", C.POINTER(C.c_double)), ("k_scale", C.c_double),
+                ("t_offset_cm", C.c_double)]
+
+
+class RunStats(C.Structure):
+    _fields_ = [("histories", C.c_uint64), ("e_src_mev", C.c_double), ("e_ct_mev", C.c_double),
+                ("e_epid_mev", C.c_double * MAX_LAYERS), ("e_esc_mev", C.c_double), ("e_lost_mev", C.c_double),
+                ("counters", C.c_uint64 * NUM_COUNTERS), ("waves", C.c_int), ("error_flags", C.c_uint32),
+                ("gpu_ms", C.c_double)]
+
+
+class MCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> Path:
+    return _build.LIB
+
+
+def load(build_if_stale: bool = True):
+    """Load (building first if the sources are newer) the CUDA library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_stale:
+        _build.build()
+    if not _build.LIB.exists():
+        raise ImportError(f"CUDA library {_build.LIB} is missing; run paper_2510_24154_b300/build.py")
+    lib = C.CDLL(str(_build.LIB))
+    P, vp, i, u64, u32, d = C.POINTER, C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_double
+    lib.mc_config_default.restype = None
+    lib.mc_config_default.argtypes = [P(Config)]
+    lib.mc_create.argtypes = [P(Config), i, P(vp)]
+    lib.mc_destroy.argtypes = [vp]
+    lib.mc_init_geometry.argtypes = [vp, vp, i, i, i, P(d), P(d), P(EpidDesc), i, vp]
+    lib.mc_set_field.argtypes = [vp, P(FieldDesc), P(LutDesc), vp]
+    lib.mc_run.argtypes = [vp, u64, u64, vp, P(RunStats)]
+    lib.mc_get_dose.argtypes = [vp, vp, vp, P(d), i, vp]
+    lib.mc_get_epid_image.argtypes = [vp, vp, i, vp]
+    lib.mc_get_tmap.argtypes = [vp, vp, i, vp]
+    lib.mc_get_tally.argtypes = [vp, vp, i, vp]
+    lib.mc_field_size.argtypes = [vp, P(d), P(d), P(d)]
+    lib.mc_get_stats.argtypes = [vp, P(RunStats)]
+    lib.mc_reset_tally.argtypes = [vp, vp]
+    lib.mc_state_size.argtypes = [vp, P(C.c_size_t)]
+    lib.mc_get_state.argtypes = [vp, vp, C.c_size_t, vp]
+    lib.mc_set_state.argtypes = [vp, vp, C.c_size_t, vp]
+    lib.mc_cancel.argtypes = [vp]
+    lib.mc_last_error.restype = C.c_char_p
+    lib.mc_last_error.argtypes = [vp]
+    lib.mc_status_string.restype = C.c_char_p
+    lib.mc_status_string.argtypes = [i]
+    lib.mc_test_philox.argtypes = [vp, vp, i, vp]
+    lib.mc_test_uniforms.argtypes = [u64, u64, u32, i, vp, vp]
+    for name in EXPORTED:
+        if name not in ("mc_config_default", "mc_last_error", "mc_status_string"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def default_config(physics=None, **overrides) -> Config:
+    lib = load()
+    cfg = Config()
+    lib.mc_config_default(C.byref(cfg))
+    if physics is not None:
+        cfg.coupled = int(physics.coupled)
+        cfg.e_max_mev = physics.e_max
+        cfg.mono_energy_mev = physics.mono_energy
+        cfg.photon_cutoff_mev = physics.photon_cutoff
+        cfg.electron_cutoff_mev = physics.electron_cutoff
+        cfg.wcc_mev = physics.wcc
+        cfg.wcb_mev = physics.wcb
+        cfg.step_fraction = physics.step_fraction
+        cfg.n_batches = physics.n_batches
+        cfg.max_steps = physics.max_steps
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor, or host pointer of a numpy array."""
+    if isinstance(x, np.ndarray):
+        return C.c_void_p(x.ctypes.data)
+    return C.c_void_p(x.data_ptr())
+
+
+class Simulator:
+    """One library context on one GPU: geometry, field, runs and read-outs."""
+
+    def __init__(self, physics=None, device: int = 0, **overrides):
+        self.lib = load()
+        self.cfg = default_config(physics, **overrides)
+        h = C.c_void_p()
+        self._check(self.lib.mc_create(C.byref(self.cfg), device, C.byref(h)), None)
+        self.h = h
+        self.device = device
+        self.epid = None
+        self._keep = []
+
+    def _check(self, st, h="self"):
+        if st != 0:
+            hh = self.h if h == "self" else h
+            msg = self.lib.mc_last_error(hh).decode() if hh else self.lib.mc_status_string(st).decode()
+            raise MCError(st, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- set-up -------------------------------------------------------------
+    def init_geometry(self, phantom, epid, stream=None, hu_device=None):
+        """a1: HU volume (numpy int16 [nz][ny][nx], or a CUDA int16 tensor via hu_device)."""
+        nz, ny, nx = phantom.hu.shape
+        vox = (C.c_double * 3)(*phantom.vox)
+        org = (C.c_double * 3)(*phantom.origin)
+        e = EpidDesc()
+        e.n_layers = len(epid.layers)
+        for l, (m, t, r) in enumerate(epid.layers):
+            e.material[l], e.thickness_cm[l], e.density[l] = int(m), float(t), float(r)
+        e.sensitive_layer, e.npx, e.npy, e.pitch_cm = epid.sensitive, epid.npx, epid.npy, epid.pitch
+        if hu_device is not None:
+            ptr, on_dev = _ptr(hu_device), 1
+        else:
+            hu = np.ascontiguousarray(phantom.hu, dtype=np.int16)
+            self._keep = [hu]
+            ptr, on_dev = C.c_void_p(hu.ctypes.data), 0
+        self._check(self.lib.mc_init_geometry(self.h, ptr, nx, ny, nz, vox, org, C.byref(e), on_dev,
+                                              _stream_ptr(stream)))
+        self.epid = epid
+
+    def set_field(self, field, lut=None, stream=None):
+        """a2 set-up, a9 t-map, a10 Eq. 1, k-table upload; resets the tally."""
+        edges = np.ascontiguousarray(field.pair_edges, dtype=np.float64)
+        leaves = np.ascontiguousarray(field.leaves, dtype=np.float64)
+        jaws = np.ascontiguousarray(field.jaws, dtype=np.float64)
+        mu = np.ascontiguousarray(field.mu, dtype=np.float64)
+        f = FieldDesc()
+        f.n_segments, f.n_pairs = leaves.shape[0], leaves.shape[1]
+        f.pair_edges_cm, f.leaves_cm, f.jaws_cm, f.mu = _dp(edges), _dp(leaves), _dp(jaws), _dp(mu)
+        f.gantry_deg, f.sad_cm, f.sid_cm = field.gantry_deg, field.sad, field.sid
+        f.iso_cm[:] = [float(v) for v in field.iso]
+        f.eq1_literal = int(lut.eq1_literal) if lut is not None else 0
+        lp = None
+        if lut is not None:
+            tn = np.ascontiguousarray(lut.t_nodes, dtype=np.float64)
+            sn = np.ascontiguousarray(lut.s_nodes, dtype=np.float64)
+            k = np.ascontiguousarray(lut.k, dtype=np.float64)
+            L = LutDesc()
+            L.nt, L.ns = tn.size, sn.size
+            L.t_nodes, L.s_nodes, L.k = _dp(tn), _dp(sn), _dp(k)
+            L.k_scale, L.t_offset_cm = lut.k_scale, lut.t_offset
+            lp = C.byref(L)
+        self._check(self.lib.mc_set_field(self.h, C.byref(f), lp, _stream_ptr(stream)))
+
+    # -- transport ------------------------------------------------------------
+    def run(self, n_histories, seed, stream=None) -> dict:
+        """a2-a7: transport n_histories more histories."""
+        st = RunStats()
+        self._check(self.lib.mc_run(self.h, int(n_histories), int(seed), _stream_ptr(stream), C.byref(st)))
+        return stats_dict(st)
+
+    def stats(self) -> dict:
+        st = RunStats()
+        self._check(self.lib.mc_get_stats(self.h, C.byref(st)))
+        return stats_dict(st)
+
+    # -- read-outs ------------------------------------------------------------
+    def _npix(self):
+        return self.epid.npy, self.epid.npx
+
+    def dose(self, stream=None, with_sigma=True):
+        """a8: (dose, sigma, u) as numpy arrays (Gy per history) and the scalar u."""
+        ny, nx = self._npix()
+        d = np.empty((ny, nx))
+        s = np.empty((ny, nx)) if with_sigma else None
+        u = C.c_double()
+        self._check(self.lib.mc_get_dose(self.h, C.c_void_p(d.ctypes.data),
+                                         C.c_void_p(s.ctypes.data) if s is not None else None,
+                                         C.byref(u) if with_sigma else None, 0, _stream_ptr(stream)))
+        return d, s, u.value
+
+    def dose_device(self, dose, sigma=None, stream=None):
+        self._check(self.lib.mc_get_dose(self.h, _ptr(dose), _ptr(sigma) if sigma is not None else None, None, 1,
+                                         _stream_ptr(stream)))
+
+    def epid_image(self, stream=None):
+        """a11: k(t, s)-corrected signal, float32 numpy [npy][npx]."""
+        ny, nx = self._npix()
+        out = np.empty((ny, nx), dtype=np.float32)
+        self._check(self.lib.mc_get_epid_image(self.h, C.c_void_p(out.ctypes.data), 0, _stream_ptr(stream)))
+        return out
+
+    def epid_image_device(self, out, stream=None):
+        self._check(self.lib.mc_get_epid_image(self.h, _ptr(out), 1, _stream_ptr(stream)))
+
+    def tmap(self, stream=None):
+        ny, nx = self._npix()
+        out = np.empty((ny, nx))
+        self._check(self.lib.mc_get_tmap(self.h, C.c_void_p(out.ctypes.data), 0, _stream_ptr(stream)))
+        return out
+
+    def tally(self, stream=None):
+        ny, nx = self._npix()
+        out = np.empty((self.cfg.n_batches, ny, nx), dtype=np.uint64)
+        self._check(self.lib.mc_get_tally(self.h, C.c_void_p(out.ctypes.data), 0, _stream_ptr(stream)))
+        return out
+
+    def field_size(self):
+        s, a, b = C.c_double(), C.c_double(), C.c_double()
+        self._check(self.lib.mc_field_size(self.h, C.byref(s), C.byref(a), C.byref(b)))
+        return s.value, a.value, b.value
+
+    def reset_tally(self, stream=None):
+        self._check(self.lib.mc_reset_tally(self.h, _stream_ptr(stream)))
+
+    def get_state(self, stream=None) -> bytes:
+        n = C.c_size_t()
+        self._check(self.lib.mc_state_size(self.h, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(self.lib.mc_get_state(self.h, buf, n.value, _stream_ptr(stream)))
+        return bytes(buf.raw)
+
+    def set_state(self, blob: bytes, stream=None):
+        buf = C.create_string_buffer(blob, len(blob))
+        self._check(self.lib.mc_set_state(self.h, buf, len(blob), _stream_ptr(stream)))
+
+
+def stats_dict(st: RunStats) -> dict:
+    return {
+        "histories": int(st.histories),
+        "e_src": st.e_src_mev, "e_ct": st.e_ct_mev, "e_epid": np.array(st.e_epid_mev[:]),
+        "e_esc": st.e_esc_mev, "e_lost": st.e_lost_mev,
+        "counters": dict(zip(COUNTER_NAMES, [int(v) for v in st.counters])),
+        "waves": int(st.waves), "error_flags": int(st.error_flags), "gpu_ms": float(st.gpu_ms),
+    }
+
+
+def test_philox(ctr_key, stream=None):
+    """Philox4x32-10 on the GPU for rows (ctr0..3, key0, key1); returns [n][4] uint32."""
+    import torch
+    lib = load()
+    a = torch.as_tensor(np.ascontiguousarray(ctr_key, dtype=np.uint32).view(np.int32), device="cuda")
+    out = torch.empty((a.shape[0], 4), dtype=torch.int32, device="cuda")
+    st = lib.mc_test_philox(_ptr(a), _ptr(out), a.shape[0], _stream_ptr(stream))
+    if st:
+        raise MCError(st, "mc_test_philox")
+    return out.cpu().numpy().view(np.uint32)
+
+
+def test_uniforms(seed, hist, ord_, n, stream=None):
+    import torch
+    lib = load()
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    st = lib.mc_test_uniforms(int(seed), int(hist), int(ord_), int(n), _ptr(out), _stream_ptr(stream))
+    if st:
+        raise MCError(st, "mc_test_uniforms")
+    return out.cpu().numpy()

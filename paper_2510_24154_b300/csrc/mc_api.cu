@@ -1,0 +1,770 @@
+// C ABI of the EPID transit Monte Carlo library (declared in archer_epid.h):
+// context lifecycle, geometry and field set-up, the transport wave loop,
+// statistics, the dose-to-signal correction and checkpointing.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "archer_epid.h"
+#include "mc_aux.h"
+#include "mc_device.cuh"
+#include "physics_tables.h"
+
+using mc::BankPtr;
+using mc::Ctl;
+using mc::Params;
+
+struct mc_ctx {
+    int device = 0;
+    int sm_count = 0;
+    mc_config cfg{};
+    std::string err;
+    std::atomic<int> cancel{0};
+    // physics tables
+    mcphys::Tables tabs;
+    float2* d_ptab = nullptr;
+    float2* d_etab = nullptr;
+    // transport launch shape per bank type
+    int block = 256;
+    int grid[mc::kNumBanks] = {0, 0, 0, 0};
+    // banks
+    void* bank_mem = nullptr;
+    BankPtr bank[mc::kNumBanks][2];
+    uint32_t cap = 0;
+    Ctl* d_ctl = nullptr;
+    Ctl* h_ctl = nullptr;        // pinned
+    // geometry
+    bool has_geom = false;
+    int nx = 0, ny = 0, nz = 0;
+    double vox[3] = {0, 0, 0}, origin[3] = {0, 0, 0};
+    int16_t* d_hu = nullptr;
+    float* d_rho = nullptr;
+    size_t nvox_alloc = 0;
+    unsigned int* d_rho_max = nullptr;
+    float* d_thr = nullptr;
+    float rho_max[4] = {0, 0, 0, 0};
+    float thr[3] = {0, 0, 0};
+    mc_epid_desc epid{};
+    double zp[MC_MAX_LAYERS + 1] = {};
+    // field
+    bool has_field = false;
+    double ex[3], ey[3], ez[3], iso[3], sad = 100, sid = 150;
+    int n_rect = 0;
+    float4* d_rect = nullptr;
+    double* d_cdf = nullptr;
+    double s_eq = 0, bbox_a = 0, bbox_b = 0;
+    double* d_tmap = nullptr;
+    bool has_lut = false;
+    int lut_nt = 0;
+    double* d_lut_t = nullptr;
+    double* d_lut_ks = nullptr;
+    double k_scale = 1.0, t_offset = 0.0;
+    // tallies
+    unsigned long long* d_tally = nullptr;
+    size_t tally_n = 0;
+    unsigned long long* d_energy = nullptr;
+    unsigned long long* d_events = nullptr;
+    uint64_t hist_done = 0;
+    // statistics scratch
+    double* d_dose = nullptr;
+    double* d_sigma = nullptr;
+    double* d_nb = nullptr;
+    double* d_u = nullptr;
+    unsigned long long* d_maxbits = nullptr;
+    double* d_part = nullptr;
+    unsigned int* d_partc = nullptr;
+    float* d_signal = nullptr;
+    int last_waves = 0;
+    uint32_t last_error = 0;
+    double last_ms = 0;
+};
+
+namespace {
+
+mc_status fail(mc_ctx* c, mc_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                         \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? MC_ERR_OOM : MC_ERR_CUDA,          \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+    } while (0)
+
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+constexpr double kQuantaPerMeV = 2.56e8;
+constexpr double kJoulePerMeV = 1.602176634e-13;
+
+void free_field(mc_ctx* c) {
+    dfree(c->d_rect);
+    dfree(c->d_cdf);
+    dfree(c->d_tmap);
+    dfree(c->d_lut_t);
+    dfree(c->d_lut_ks);
+    dfree(c->d_dose);
+    dfree(c->d_sigma);
+    dfree(c->d_part);
+    dfree(c->d_partc);
+    dfree(c->d_signal);
+    dfree(c->d_tally);
+    c->has_field = false;
+    c->has_lut = false;
+}
+
+int npix(const mc_ctx* c) { return c->epid.npx * c->epid.npy; }
+
+mc_status ensure_tally(mc_ctx* c) {
+    const size_t n = static_cast<size_t>(c->cfg.n_batches) * npix(c);
+    if (c->d_tally && c->tally_n == n) return MC_OK;
+    dfree(c->d_tally);
+    CUDA_TRY(c, cudaMalloc(&c->d_tally, n * sizeof(unsigned long long)));
+    c->tally_n = n;
+    const int parts = (npix(c) + 255) / 256;
+    dfree(c->d_dose);
+    dfree(c->d_sigma);
+    dfree(c->d_part);
+    dfree(c->d_partc);
+    dfree(c->d_signal);
+    CUDA_TRY(c, cudaMalloc(&c->d_dose, sizeof(double) * npix(c)));
+    CUDA_TRY(c, cudaMalloc(&c->d_sigma, sizeof(double) * npix(c)));
+    CUDA_TRY(c, cudaMalloc(&c->d_part, sizeof(double) * parts));
+    CUDA_TRY(c, cudaMalloc(&c->d_partc, sizeof(unsigned int) * parts));
+    CUDA_TRY(c, cudaMalloc(&c->d_signal, sizeof(float) * npix(c)));
+    return MC_OK;
+}
+
+mc_status clear_tally(mc_ctx* c, cudaStream_t s) {
+    if (c->d_tally) CUDA_TRY(c, cudaMemsetAsync(c->d_tally, 0, c->tally_n * sizeof(unsigned long long), s));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_energy, 0, sizeof(unsigned long long) * mc::kNumEnergy, s));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_events, 0, sizeof(unsigned long long) * mc::kNumEvents, s));
+    c->hist_done = 0;
+    return MC_OK;
+}
+
+void make_params(const mc_ctx* c, Params& P, uint64_t seed) {
+    std::memset(&P, 0, sizeof(P));
+    P.nx = c->nx; P.ny = c->ny; P.nz = c->nz;
+    P.ox = static_cast<float>(c->origin[0]); P.oy = static_cast<float>(c->origin[1]);
+    P.oz = static_cast<float>(c->origin[2]);
+    P.vx = static_cast<float>(c->vox[0]); P.vy = static_cast<float>(c->vox[1]); P.vz = static_cast<float>(c->vox[2]);
+    P.ivx = 1.0f / P.vx; P.ivy = 1.0f / P.vy; P.ivz = 1.0f / P.vz;
+    P.rho = c->d_rho;
+    for (int m = 0; m < 4; ++m) P.rho_max[m] = c->rho_max[m];
+    for (int k = 0; k < 3; ++k) {
+        P.thr[k] = c->thr[k];
+        P.ex[k] = static_cast<float>(c->ex[k]);
+        P.ey[k] = static_cast<float>(c->ey[k]);
+        P.ez[k] = static_cast<float>(c->ez[k]);
+        P.iso[k] = static_cast<float>(c->iso[k]);
+    }
+    P.sad = static_cast<float>(c->sad);
+    const mc_epid_desc& E = c->epid;
+    P.nl = E.n_layers; P.sens = E.sensitive_layer; P.npx = E.npx; P.npy = E.npy;
+    P.pitch = static_cast<float>(E.pitch_cm);
+    P.ipitch = 1.0f / P.pitch;
+    P.hwx = static_cast<float>(0.5 * E.npx * E.pitch_cm);
+    P.hwy = static_cast<float>(0.5 * E.npy * E.pitch_cm);
+    for (int l = 0; l <= E.n_layers; ++l) P.zp[l] = static_cast<float>(c->zp[l]);
+    for (int l = 0; l < E.n_layers; ++l) {
+        P.lmat[l] = E.material[l];
+        P.lrho[l] = static_cast<float>(E.density[l]);
+    }
+    P.n_rect = c->n_rect; P.rect = c->d_rect; P.cdf = c->d_cdf;
+    P.e_max = static_cast<float>(c->cfg.e_max_mev);
+    P.mono_e = static_cast<float>(c->cfg.mono_energy_mev);
+    P.pcut = static_cast<float>(c->cfg.photon_cutoff_mev);
+    P.ecut = static_cast<float>(c->cfg.electron_cutoff_mev);
+    P.tstop = P.ecut + mc::kStopMargin;
+    P.wcc = static_cast<float>(c->cfg.wcc_mev);
+    P.wcb = static_cast<float>(c->cfg.wcb_mev);
+    P.ln_wcb = logf(P.wcb);
+    P.step_frac = static_cast<float>(c->cfg.step_fraction);
+    P.max_steps = c->cfg.max_steps;
+    P.coupled = c->cfg.coupled;
+    P.nbatch = c->cfg.n_batches;
+    for (int m = 0; m < mc::kNumMat; ++m) {
+        const mcphys::MaterialCoefs& k = c->tabs.mat[m];
+        P.mat[m] = {static_cast<float>(k.ne_barn), static_cast<float>(k.pe_above), static_cast<float>(k.pe_below),
+                    static_cast<float>(k.pair), static_cast<float>(k.brem), static_cast<float>(k.msc)};
+    }
+    P.ptab = c->d_ptab;
+    P.p_lnE0 = static_cast<float>(c->tabs.p_lnE0);
+    P.p_idx = static_cast<float>(c->tabs.p_inv_dlnE);
+    P.etab = c->d_etab;
+    P.e_lnT0 = static_cast<float>(c->tabs.e_lnT0);
+    P.e_idx = static_cast<float>(c->tabs.e_inv_dlnT);
+    P.seed = seed;
+    P.hist_base = c->hist_done;
+    P.tally = c->d_tally;
+    P.energy = c->d_energy;
+    P.events = c->d_events;
+    P.ctl = c->d_ctl;
+    for (int t = 0; t < mc::kNumBanks; ++t)
+        for (int k = 0; k < 2; ++k) P.bank[t][k] = c->bank[t][k];
+    P.cap = c->cap;
+    P.flush_lanes = 8;
+}
+
+bool increasing(const double* a, int n) {
+    for (int i = 1; i < n; ++i)
+        if (!(a[i] > a[i - 1])) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mc_config_default(mc_config* cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->coupled = 1;
+    cfg->e_max_mev = 6.0;
+    cfg->mono_energy_mev = 0.0;
+    cfg->photon_cutoff_mev = 0.01;
+    cfg->electron_cutoff_mev = 0.2;
+    cfg->wcc_mev = 0.2;
+    cfg->wcb_mev = 0.01;
+    cfg->step_fraction = 0.05;
+    cfg->n_batches = 16;
+    cfg->max_steps = 10000;
+    cfg->block_size = 256;
+    cfg->ctas_per_sm = 0;
+    cfg->bank_capacity = 1u << 22;
+    cfg->primaries_per_wave = 0;
+}
+
+const char* mc_status_string(mc_status s) {
+    switch (s) {
+        case MC_OK: return "ok";
+        case MC_ERR_ARG: return "invalid argument";
+        case MC_ERR_CUDA: return "CUDA error";
+        case MC_ERR_OOM: return "out of device memory";
+        case MC_ERR_STATE: return "call out of order";
+        case MC_ERR_TIMEOUT: return "bounded wait exceeded";
+        case MC_ERR_CANCELLED: return "cancelled";
+        case MC_ERR_NUMERIC: return "non-finite value";
+        case MC_ERR_OVERFLOW: return "particle bank overflow";
+    }
+    return "unknown status";
+}
+
+const char* mc_last_error(const mc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+mc_status mc_create(const mc_config* cfg_in, int device, mc_ctx** out) {
+    if (!out) return MC_ERR_ARG;
+    *out = nullptr;
+    mc_config cfg;
+    if (cfg_in) cfg = *cfg_in; else mc_config_default(&cfg);
+    if (cfg.block_size == 0) cfg.block_size = 256;
+    if (cfg.bank_capacity == 0) cfg.bank_capacity = 1u << 22;
+    if (cfg.primaries_per_wave == 0) cfg.primaries_per_wave = cfg.bank_capacity / 4;
+    if (cfg.block_size % 32 != 0 || cfg.block_size < 32 || cfg.block_size > 256) return MC_ERR_ARG;
+    if (cfg.n_batches < 2 || cfg.n_batches > 1024 || cfg.max_steps < 1) return MC_ERR_ARG;
+    if (!(cfg.photon_cutoff_mev > 0) || !(cfg.electron_cutoff_mev > 0) || !(cfg.wcb_mev > 0) ||
+        !(cfg.wcc_mev > 0) || !(cfg.step_fraction > 0 && cfg.step_fraction < 1) || !(cfg.e_max_mev > 0))
+        return MC_ERR_ARG;
+    if (cfg.bank_capacity < 1024 || cfg.primaries_per_wave < 32) return MC_ERR_ARG;
+
+    mc_ctx* c = new mc_ctx();
+    c->cfg = cfg;
+    c->device = device;
+    auto bail = [&](mc_status s) { mc_destroy(c); return s; };
+    if (cudaSetDevice(device) != cudaSuccess) return bail(MC_ERR_CUDA);
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return bail(MC_ERR_CUDA);
+
+    const double emax = std::fmax(cfg.e_max_mev, cfg.mono_energy_mev);
+    c->tabs = mcphys::build_tables(0.95 * std::fmin(cfg.photon_cutoff_mev, cfg.wcb_mev), 1.02 * emax,
+                                   0.99 * cfg.electron_cutoff_mev, 1.02 * emax, cfg.wcc_mev, cfg.wcb_mev);
+    if (cudaMalloc(&c->d_ptab, sizeof(float) * c->tabs.photon.size()) != cudaSuccess ||
+        cudaMalloc(&c->d_etab, sizeof(float) * c->tabs.electron.size()) != cudaSuccess)
+        return bail(MC_ERR_OOM);
+    cudaMemcpy(c->d_ptab, c->tabs.photon.data(), sizeof(float) * c->tabs.photon.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_etab, c->tabs.electron.data(), sizeof(float) * c->tabs.electron.size(), cudaMemcpyHostToDevice);
+
+    c->cap = cfg.bank_capacity;
+    const size_t per = static_cast<size_t>(c->cap) * 4;
+    const size_t total = per * 12 * mc::kNumBanks * 2;
+    if (cudaMalloc(&c->bank_mem, total) != cudaSuccess) return bail(MC_ERR_OOM);
+    char* base = static_cast<char*>(c->bank_mem);
+    for (int t = 0; t < mc::kNumBanks; ++t) {
+        for (int k = 0; k < 2; ++k) {
+            BankPtr& b = c->bank[t][k];
+            float** f[7] = {&b.x, &b.y, &b.z, &b.u, &b.v, &b.w, &b.E};
+            for (int i = 0; i < 7; ++i) { *f[i] = reinterpret_cast<float*>(base); base += per; }
+            uint32_t** q[5] = {&b.hist, &b.ord, &b.draws, &b.cell, &b.flags};
+            for (int i = 0; i < 5; ++i) { *q[i] = reinterpret_cast<uint32_t*>(base); base += per; }
+        }
+    }
+    if (cudaMalloc(&c->d_ctl, sizeof(Ctl)) != cudaSuccess || cudaMallocHost(&c->h_ctl, sizeof(Ctl)) != cudaSuccess)
+        return bail(MC_ERR_OOM);
+    if (cudaMalloc(&c->d_energy, sizeof(unsigned long long) * mc::kNumEnergy) != cudaSuccess ||
+        cudaMalloc(&c->d_events, sizeof(unsigned long long) * mc::kNumEvents) != cudaSuccess ||
+        cudaMalloc(&c->d_rho_max, sizeof(unsigned int) * 4) != cudaSuccess ||
+        cudaMalloc(&c->d_thr, sizeof(float) * 3) != cudaSuccess ||
+        cudaMalloc(&c->d_nb, sizeof(double) * cfg.n_batches) != cudaSuccess ||
+        cudaMalloc(&c->d_u, sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_maxbits, sizeof(unsigned long long)) != cudaSuccess)
+        return bail(MC_ERR_OOM);
+    cudaMemset(c->d_energy, 0, sizeof(unsigned long long) * mc::kNumEnergy);
+    cudaMemset(c->d_events, 0, sizeof(unsigned long long) * mc::kNumEvents);
+
+    c->block = cfg.block_size;
+    for (int t = 0; t < mc::kNumBanks; ++t) {
+        int occ = 0;
+        if (mc::transport_occupancy(t, c->block, &occ) != cudaSuccess || occ < 1) return bail(MC_ERR_CUDA);
+        const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, occ) : occ;
+        c->grid[t] = c->sm_count * per_sm;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return bail(MC_ERR_CUDA);
+    *out = c;
+    return MC_OK;
+}
+
+mc_status mc_destroy(mc_ctx* c) {
+    if (!c) return MC_OK;
+    cudaSetDevice(c->device);
+    free_field(c);
+    dfree(c->d_ptab);
+    dfree(c->d_etab);
+    if (c->bank_mem) cudaFree(c->bank_mem);
+    dfree(c->d_ctl);
+    if (c->h_ctl) cudaFreeHost(c->h_ctl);
+    dfree(c->d_hu);
+    dfree(c->d_rho);
+    dfree(c->d_rho_max);
+    dfree(c->d_thr);
+    dfree(c->d_energy);
+    dfree(c->d_events);
+    dfree(c->d_nb);
+    dfree(c->d_u);
+    dfree(c->d_maxbits);
+    delete c;
+    return MC_OK;
+}
+
+mc_status mc_init_geometry(mc_ctx* c, const int16_t* hu, int nx, int ny, int nz, const double vox_cm[3],
+                           const double origin_cm[3], const mc_epid_desc* epid, int hu_on_device, void* stream) {
+    if (!c) return MC_ERR_ARG;
+    if (!hu || !vox_cm || !origin_cm || !epid) return fail(c, MC_ERR_ARG, "null pointer");
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 1024 || ny > 1024 || nz > 1024)
+        return fail(c, MC_ERR_ARG, "CT dimensions must be 1..1024 per axis");
+    for (int k = 0; k < 3; ++k)
+        if (!(vox_cm[k] > 0) || !std::isfinite(origin_cm[k])) return fail(c, MC_ERR_ARG, "bad voxel size or origin");
+    const mc_epid_desc& E = *epid;
+    if (E.n_layers < 1 || E.n_layers > MC_MAX_LAYERS || E.sensitive_layer < 0 || E.sensitive_layer >= E.n_layers)
+        return fail(c, MC_ERR_ARG, "bad EPID layer stack");
+    if (E.npx < 1 || E.npy < 1 || E.npx > 8192 || E.npy > 8192 || !(E.pitch_cm > 0))
+        return fail(c, MC_ERR_ARG, "bad EPID pixel grid");
+    for (int l = 0; l < E.n_layers; ++l)
+        if (E.material[l] < 0 || E.material[l] >= MC_NUM_MATERIALS || !(E.thickness_cm[l] > 0) || !(E.density[l] > 0))
+            return fail(c, MC_ERR_ARG, "bad EPID layer");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaStream_t s = as_stream(stream);
+    free_field(c);
+    const size_t nvox = static_cast<size_t>(nx) * ny * nz;
+    if (nvox > c->nvox_alloc) {
+        dfree(c->d_hu);
+        dfree(c->d_rho);
+        CUDA_TRY(c, cudaMalloc(&c->d_hu, nvox * sizeof(int16_t) + 16));
+        CUDA_TRY(c, cudaMalloc(&c->d_rho, nvox * sizeof(float) + 32));
+        c->nvox_alloc = nvox;
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_hu, hu, nvox * sizeof(int16_t),
+                                hu_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_rho_max, 0, sizeof(unsigned int) * 4, s));
+    CUDA_TRY(c, mc::launch_hu_to_rho(c->d_hu, c->d_rho, nvox, c->d_rho_max, c->d_thr, c->sm_count, s));
+    unsigned int bits[4];
+    CUDA_TRY(c, cudaMemcpyAsync(bits, c->d_rho_max, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->thr, c->d_thr, sizeof(c->thr), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    for (int m = 0; m < 4; ++m) std::memcpy(&c->rho_max[m], &bits[m], sizeof(float));
+    c->nx = nx; c->ny = ny; c->nz = nz;
+    for (int k = 0; k < 3; ++k) { c->vox[k] = vox_cm[k]; c->origin[k] = origin_cm[k]; }
+    c->epid = E;
+    c->has_geom = true;
+    return MC_OK;
+}
+
+mc_status mc_set_field(mc_ctx* c, const mc_field_desc* f, const mc_lut_desc* lut, void* stream) {
+    if (!c) return MC_ERR_ARG;
+    if (!c->has_geom) return fail(c, MC_ERR_STATE, "mc_init_geometry must come first");
+    if (!f || !f->pair_edges_cm || !f->leaves_cm || !f->jaws_cm || !f->mu) return fail(c, MC_ERR_ARG, "null field");
+    if (f->n_segments < 1 || f->n_pairs < 1 || f->n_segments * f->n_pairs > (1 << 20))
+        return fail(c, MC_ERR_ARG, "bad segment / pair count");
+    if (!(f->sad_cm > 0) || !(f->sid_cm > f->sad_cm)) return fail(c, MC_ERR_ARG, "need 0 < SAD < SID");
+    if (!increasing(f->pair_edges_cm, f->n_pairs + 1)) return fail(c, MC_ERR_ARG, "pair edges must increase");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaStream_t s = as_stream(stream);
+    free_field(c);
+
+    // source rectangles with weight MU x area, cumulative in double
+    std::vector<float4> rect;
+    std::vector<double> cdf;
+    double acc = 0.0, X0 = INFINITY, X1 = -INFINITY, Y0 = INFINITY, Y1 = -INFINITY;
+    for (int k = 0; k < f->n_segments; ++k) {
+        const double* jw = f->jaws_cm + 4 * k;
+        const double mu = f->mu[k];
+        if (!(mu >= 0.0)) return fail(c, MC_ERR_ARG, "MU weights must be >= 0");
+        for (int j = 0; j < f->n_pairs; ++j) {
+            const double* lf = f->leaves_cm + 2 * (static_cast<size_t>(k) * f->n_pairs + j);
+            const double x0 = std::fmax(lf[0], jw[0]), x1 = std::fmin(lf[1], jw[1]);
+            const double y0 = std::fmax(f->pair_edges_cm[j], jw[2]), y1 = std::fmin(f->pair_edges_cm[j + 1], jw[3]);
+            if (x1 > x0 && y1 > y0 && mu > 0.0) {
+                acc += mu * (x1 - x0) * (y1 - y0);
+                rect.push_back(make_float4(static_cast<float>(x0), static_cast<float>(x1), static_cast<float>(y0),
+                                           static_cast<float>(y1)));
+                cdf.push_back(acc);
+                X0 = std::fmin(X0, x0); X1 = std::fmax(X1, x1); Y0 = std::fmin(Y0, y0); Y1 = std::fmax(Y1, y1);
+            }
+        }
+    }
+    if (rect.empty()) return fail(c, MC_ERR_ARG, "field has no open aperture");
+    for (double& v : cdf) v /= acc;
+    c->bbox_a = X1 - X0;
+    c->bbox_b = Y1 - Y0;
+    // Eq. 1 as printed gives ab / (2(a+b)) (2.5 cm for 10 x 10), which cannot index
+    // Table 1; the default reading is the equivalent square 2ab / (a+b).
+    c->s_eq = f->eq1_literal ? c->bbox_a * c->bbox_b / (2.0 * (c->bbox_a + c->bbox_b))
+                             : 2.0 * c->bbox_a * c->bbox_b / (c->bbox_a + c->bbox_b);
+
+    const double g = f->gantry_deg * 3.14159265358979323846 / 180.0;
+    c->ex[0] = std::cos(g); c->ex[1] = std::sin(g); c->ex[2] = 0.0;
+    c->ey[0] = 0.0; c->ey[1] = 0.0; c->ey[2] = 1.0;
+    c->ez[0] = std::sin(g); c->ez[1] = -std::cos(g); c->ez[2] = 0.0;
+    for (int k = 0; k < 3; ++k) c->iso[k] = f->iso_cm[k];
+    c->sad = f->sad_cm;
+    c->sid = f->sid_cm;
+    const mc_epid_desc& E = c->epid;
+    double z = (c->sad - c->sid) + 0.5 * E.thickness_cm[E.sensitive_layer];
+    for (int l = E.sensitive_layer - 1; l >= 0; --l) z += E.thickness_cm[l];
+    c->zp[0] = z;
+    for (int l = 0; l < E.n_layers; ++l) c->zp[l + 1] = c->zp[l] - E.thickness_cm[l];
+    // the vacuum transfer needs the whole CT above the detector face and below the source
+    for (int corner = 0; corner < 8; ++corner) {
+        double p[3];
+        const int n[3] = {c->nx, c->ny, c->nz};
+        for (int k = 0; k < 3; ++k) p[k] = c->origin[k] + ((corner >> k) & 1) * n[k] * c->vox[k] - c->iso[k];
+        const double Z = p[0] * c->ez[0] + p[1] * c->ez[1] + p[2] * c->ez[2];
+        if (!(Z > c->zp[0] + 1e-3) || !(Z < c->sad))
+            return fail(c, MC_ERR_ARG, "CT box must lie between the source and the EPID face");
+    }
+
+    mc_status st = ensure_tally(c);
+    if (st != MC_OK) return st;
+    c->n_rect = static_cast<int>(rect.size());
+    CUDA_TRY(c, cudaMalloc(&c->d_rect, sizeof(float4) * rect.size()));
+    CUDA_TRY(c, cudaMalloc(&c->d_cdf, sizeof(double) * cdf.size()));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_rect, rect.data(), sizeof(float4) * rect.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_cdf, cdf.data(), sizeof(double) * cdf.size(), cudaMemcpyHostToDevice, s));
+
+    // radiological thickness map (a9)
+    c->t_offset = lut ? lut->t_offset_cm : 0.0;
+    CUDA_TRY(c, cudaMalloc(&c->d_tmap, sizeof(double) * npix(c)));
+    mc::TmapArgs A;
+    A.nx = c->nx; A.ny = c->ny; A.nz = c->nz;
+    A.ox = static_cast<float>(c->origin[0]); A.oy = static_cast<float>(c->origin[1]);
+    A.oz = static_cast<float>(c->origin[2]);
+    A.vx = static_cast<float>(c->vox[0]); A.vy = static_cast<float>(c->vox[1]); A.vz = static_cast<float>(c->vox[2]);
+    A.rho = c->d_rho;
+    for (int k = 0; k < 3; ++k) {
+        A.src[k] = static_cast<float>(c->iso[k] + c->sad * c->ez[k]);
+        A.iso[k] = static_cast<float>(c->iso[k]);
+        A.ex[k] = static_cast<float>(c->ex[k]);
+        A.ey[k] = static_cast<float>(c->ey[k]);
+        A.ez[k] = static_cast<float>(c->ez[k]);
+    }
+    A.npx = E.npx; A.npy = E.npy;
+    A.pitch = static_cast<float>(E.pitch_cm);
+    A.hwx = static_cast<float>(0.5 * E.npx * E.pitch_cm);
+    A.hwy = static_cast<float>(0.5 * E.npy * E.pitch_cm);
+    A.zs = static_cast<float>(c->sad - c->sid);
+    A.t_offset = c->t_offset;
+    CUDA_TRY(c, mc::launch_tmap(A, c->d_tmap, s));
+
+    // k-table: the column at this field's s, for the per-pixel step along t
+    if (lut) {
+        if (lut->nt < 2 || lut->ns < 2 || lut->nt > 1024 || lut->ns > 1024 || !lut->t_nodes || !lut->s_nodes || !lut->k)
+            return fail(c, MC_ERR_ARG, "bad k-table");
+        if (!increasing(lut->t_nodes, lut->nt) || !increasing(lut->s_nodes, lut->ns))
+            return fail(c, MC_ERR_ARG, "k-table nodes must increase");
+        const double sc = std::fmin(std::fmax(c->s_eq, lut->s_nodes[0]), lut->s_nodes[lut->ns - 1]);
+        int js = 0;
+        while (js + 1 < lut->ns - 1 && lut->s_nodes[js + 1] <= sc) ++js;
+        const double fs = (sc - lut->s_nodes[js]) / (lut->s_nodes[js + 1] - lut->s_nodes[js]);
+        std::vector<double> ks(lut->nt);
+        for (int it = 0; it < lut->nt; ++it)
+            ks[it] = (1.0 - fs) * lut->k[static_cast<size_t>(js) * lut->nt + it] +
+                     fs * lut->k[static_cast<size_t>(js + 1) * lut->nt + it];
+        CUDA_TRY(c, cudaMalloc(&c->d_lut_t, sizeof(double) * lut->nt));
+        CUDA_TRY(c, cudaMalloc(&c->d_lut_ks, sizeof(double) * lut->nt));
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_lut_t, lut->t_nodes, sizeof(double) * lut->nt, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_lut_ks, ks.data(), sizeof(double) * lut->nt, cudaMemcpyHostToDevice, s));
+        c->lut_nt = lut->nt;
+        c->k_scale = lut->k_scale;
+        c->has_lut = true;
+    }
+    st = clear_tally(c, s);
+    if (st != MC_OK) return st;
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    c->has_field = true;
+    return MC_OK;
+}
+
+mc_status mc_run(mc_ctx* c, uint64_t n, uint64_t seed, void* stream, mc_run_stats* stats) {
+    if (!c) return MC_ERR_ARG;
+    if (!c->has_field) return fail(c, MC_ERR_STATE, "mc_set_field must come first");
+    if (n > 0xffffffffull) return fail(c, MC_ERR_ARG, "at most 2^32-1 histories per call");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaStream_t s = as_stream(stream);
+    c->cancel.store(0);
+    Params P;
+    make_params(c, P, seed);
+    Ctl& h = *c->h_ctl;
+    std::memset(&h, 0, sizeof(h));
+    h.n_total = n;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    CUDA_TRY(c, cudaEventCreate(&e1));
+    CUDA_TRY(c, cudaEventRecord(e0, s));
+    const int order[4] = {mc::kPhotonCT, mc::kElectronCT, mc::kPhotonEPID, mc::kElectronEPID};
+    int waves = 0;
+    mc_status result = MC_OK;
+    const int max_waves = 1000000;
+    for (; waves < max_waves; ++waves) {
+        CUDA_TRY(c, mc::launch_wave_begin(c->d_ctl, c->cfg.primaries_per_wave, s));
+        for (int t : order) {
+            const bool electron = (t == mc::kElectronCT || t == mc::kElectronEPID);
+            if (electron && !c->cfg.coupled) continue;
+            CUDA_TRY(c, mc::launch_transport(t, P, c->grid[t], c->block, s));
+            CUDA_TRY(c, mc::launch_swap(c->d_ctl, t, s));
+        }
+        CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        if (h.error) { result = fail(c, MC_ERR_OVERFLOW, "particle bank overflow"); ++waves; break; }
+        bool empty = h.next_prim >= h.n_total;
+        for (int t = 0; t < mc::kNumBanks; ++t) empty = empty && h.count[t][h.cur[t]] == 0u;
+        if (empty) { ++waves; break; }
+        if (c->cancel.load()) { result = fail(c, MC_ERR_CANCELLED, "cancelled"); ++waves; break; }
+    }
+    if (waves >= max_waves && result == MC_OK) result = fail(c, MC_ERR_TIMEOUT, "wave limit reached");
+    CUDA_TRY(c, cudaEventRecord(e1, s));
+    CUDA_TRY(c, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->hist_done += n;
+    c->last_waves = waves;
+    c->last_error = h.error;
+    c->last_ms = ms;
+    if (stats) {
+        mc_status st = mc_get_stats(c, stats);
+        if (st != MC_OK) return st;
+    }
+    return result;
+}
+
+mc_status mc_get_stats(mc_ctx* c, mc_run_stats* st) {
+    if (!c || !st) return MC_ERR_ARG;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    unsigned long long en[mc::kNumEnergy], ev[mc::kNumEvents];
+    CUDA_TRY(c, cudaMemcpy(en, c->d_energy, sizeof(en), cudaMemcpyDeviceToHost));
+    CUDA_TRY(c, cudaMemcpy(ev, c->d_events, sizeof(ev), cudaMemcpyDeviceToHost));
+    std::memset(st, 0, sizeof(*st));
+    st->histories = c->hist_done;
+    st->e_src_mev = en[mc::kESrc] / kQuantaPerMeV;
+    st->e_ct_mev = en[mc::kECT] / kQuantaPerMeV;
+    st->e_esc_mev = en[mc::kEEsc] / kQuantaPerMeV;
+    st->e_lost_mev = en[mc::kELost] / kQuantaPerMeV;
+    for (int l = 0; l < MC_MAX_LAYERS; ++l) st->e_epid_mev[l] = en[mc::kEEpid0 + l] / kQuantaPerMeV;
+    for (int k = 0; k < MC_NUM_COUNTERS; ++k) st->counters[k] = ev[k];
+    st->waves = c->last_waves;
+    st->error_flags = c->last_error;
+    st->gpu_ms = c->last_ms;
+    return MC_OK;
+}
+
+static mc_status compute_dose(mc_ctx* c, double* dose, double* sigma, double* u_dev, cudaStream_t s) {
+    const int B = c->cfg.n_batches;
+    const uint64_t N = c->hist_done;
+    if (N == 0) return fail(c, MC_ERR_STATE, "no histories run");
+    std::vector<double> nb(B);
+    for (int b = 0; b < B; ++b) nb[b] = static_cast<double>(N / B + (static_cast<uint64_t>(b) < N % B ? 1 : 0));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_nb, nb.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+    const mc_epid_desc& E = c->epid;
+    const int l = E.sensitive_layer;
+    const double mass_kg = E.density[l] * E.pitch_cm * E.pitch_cm * E.thickness_cm[l] * 1e-3;
+    CUDA_TRY(c, mc::launch_dose(c->d_tally, npix(c), B, c->d_nb, static_cast<double>(N), kJoulePerMeV / mass_kg,
+                                dose, sigma, c->d_maxbits, c->d_part, c->d_partc, u_dev, s));
+    return MC_OK;
+}
+
+mc_status mc_get_dose(mc_ctx* c, double* dose, double* sigma, double* u_out, int on_device, void* stream) {
+    if (!c) return MC_ERR_ARG;
+    if (!c->has_field) return fail(c, MC_ERR_STATE, "no field");
+    if (!dose) return fail(c, MC_ERR_ARG, "null dose");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaStream_t s = as_stream(stream);
+    double* dd = on_device ? dose : c->d_dose;
+    double* ds = on_device ? (sigma ? sigma : c->d_sigma) : c->d_sigma;
+    mc_status st = compute_dose(c, dd, ds, u_out ? c->d_u : nullptr, s);
+    if (st != MC_OK) return st;
+    const size_t bytes = sizeof(double) * npix(c);
+    if (!on_device) {
+        CUDA_TRY(c, cudaMemcpyAsync(dose, c->d_dose, bytes, cudaMemcpyDeviceToHost, s));
+        if (sigma) CUDA_TRY(c, cudaMemcpyAsync(sigma, c->d_sigma, bytes, cudaMemcpyDeviceToHost, s));
+    }
+    if (u_out) CUDA_TRY(c, cudaMemcpyAsync(u_out, c->d_u, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (!on_device || u_out) CUDA_TRY(c, cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
+mc_status mc_get_epid_image(mc_ctx* c, float* signal, int on_device, void* stream) {
+    if (!c) return MC_ERR_ARG;
+    if (!c->has_field || !c->has_lut) return fail(c, MC_ERR_STATE, "no field or no k-table");
+    if (!signal) return fail(c, MC_ERR_ARG, "null signal");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaStream_t s = as_stream(stream);
+    mc_status st = compute_dose(c, c->d_dose, c->d_sigma, nullptr, s);
+    if (st != MC_OK) return st;
+    float* out = on_device ? signal : c->d_signal;
+    CUDA_TRY(c, mc::launch_lut(c->d_dose, c->d_tmap, npix(c), c->d_lut_t, c->d_lut_ks, c->lut_nt, c->k_scale, out, s));
+    if (!on_device) {
+        CUDA_TRY(c, cudaMemcpyAsync(signal, c->d_signal, sizeof(float) * npix(c), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+    }
+    return MC_OK;
+}
+
+mc_status mc_get_tmap(mc_ctx* c, double* t, int on_device, void* stream) {
+    if (!c) return MC_ERR_ARG;
+    if (!c->has_field) return fail(c, MC_ERR_STATE, "no field");
+    if (!t) return fail(c, MC_ERR_ARG, "null output");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaStream_t s = as_stream(stream);
+    CUDA_TRY(c, cudaMemcpyAsync(t, c->d_tmap, sizeof(double) * npix(c),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
+mc_status mc_get_tally(mc_ctx* c, uint64_t* tally, int on_device, void* stream) {
+    if (!c) return MC_ERR_ARG;
+    if (!c->has_field) return fail(c, MC_ERR_STATE, "no field");
+    if (!tally) return fail(c, MC_ERR_ARG, "null output");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaStream_t s = as_stream(stream);
+    CUDA_TRY(c, cudaMemcpyAsync(tally, c->d_tally, sizeof(uint64_t) * c->tally_n,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
+mc_status mc_field_size(mc_ctx* c, double* sz, double* a, double* b) {
+    if (!c) return MC_ERR_ARG;
+    if (!c->has_field) return fail(c, MC_ERR_STATE, "no field");
+    if (sz) *sz = c->s_eq;
+    if (a) *a = c->bbox_a;
+    if (b) *b = c->bbox_b;
+    return MC_OK;
+}
+
+mc_status mc_reset_tally(mc_ctx* c, void* stream) {
+    if (!c) return MC_ERR_ARG;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaStream_t s = as_stream(stream);
+    mc_status st = clear_tally(c, s);
+    if (st != MC_OK) return st;
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
+// State layout: magic, B, npx, npy, next history id, energy counters,
+// event counters, sub-tallies (all uint64).
+static size_t state_words(const mc_ctx* c) {
+    return 5 + mc::kNumEnergy + mc::kNumEvents + c->tally_n;
+}
+static const uint64_t kStateMagic = 0x4550494453543031ull;   // "EPIDST01"
+
+mc_status mc_state_size(mc_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return MC_ERR_ARG;
+    if (!c->has_field) return fail(c, MC_ERR_STATE, "no field");
+    *bytes = state_words(c) * sizeof(uint64_t);
+    return MC_OK;
+}
+
+mc_status mc_get_state(mc_ctx* c, void* buf, size_t bytes, void* stream) {
+    if (!c || !buf) return MC_ERR_ARG;
+    if (!c->has_field) return fail(c, MC_ERR_STATE, "no field");
+    if (bytes < state_words(c) * sizeof(uint64_t)) return fail(c, MC_ERR_ARG, "state buffer too small");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaStream_t s = as_stream(stream);
+    uint64_t* w = static_cast<uint64_t*>(buf);
+    w[0] = kStateMagic; w[1] = c->cfg.n_batches; w[2] = c->epid.npx; w[3] = c->epid.npy; w[4] = c->hist_done;
+    CUDA_TRY(c, cudaMemcpyAsync(w + 5, c->d_energy, sizeof(uint64_t) * mc::kNumEnergy, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaMemcpyAsync(w + 5 + mc::kNumEnergy, c->d_events, sizeof(uint64_t) * mc::kNumEvents,
+                                cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaMemcpyAsync(w + 5 + mc::kNumEnergy + mc::kNumEvents, c->d_tally, sizeof(uint64_t) * c->tally_n,
+                                cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
+mc_status mc_set_state(mc_ctx* c, const void* buf, size_t bytes, void* stream) {
+    if (!c || !buf) return MC_ERR_ARG;
+    if (!c->has_field) return fail(c, MC_ERR_STATE, "no field");
+    if (bytes < state_words(c) * sizeof(uint64_t)) return fail(c, MC_ERR_ARG, "state buffer too small");
+    const uint64_t* w = static_cast<const uint64_t*>(buf);
+    if (w[0] != kStateMagic || w[1] != static_cast<uint64_t>(c->cfg.n_batches) ||
+        w[2] != static_cast<uint64_t>(c->epid.npx) || w[3] != static_cast<uint64_t>(c->epid.npy))
+        return fail(c, MC_ERR_ARG, "state does not match this context");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaStream_t s = as_stream(stream);
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_energy, w + 5, sizeof(uint64_t) * mc::kNumEnergy, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_events, w + 5 + mc::kNumEnergy, sizeof(uint64_t) * mc::kNumEvents,
+                                cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_tally, w + 5 + mc::kNumEnergy + mc::kNumEvents, sizeof(uint64_t) * c->tally_n,
+                                cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    c->hist_done = w[4];
+    return MC_OK;
+}
+
+mc_status mc_cancel(mc_ctx* c) {
+    if (!c) return MC_ERR_ARG;
+    c->cancel.store(1);
+    return MC_OK;
+}
+
+mc_status mc_test_philox(const uint32_t* in, uint32_t* out, int n, void* stream) {
+    if (!in || !out || n < 0) return MC_ERR_ARG;
+    if (n == 0) return MC_OK;
+    if (mc::launch_test_philox(in, out, n, as_stream(stream)) != cudaSuccess) return MC_ERR_CUDA;
+    return cudaStreamSynchronize(as_stream(stream)) == cudaSuccess ? MC_OK : MC_ERR_CUDA;
+}
+
+mc_status mc_test_uniforms(uint64_t seed, uint64_t hist, uint32_t ord, int n, float* out, void* stream) {
+    if (!out || n < 0) return MC_ERR_ARG;
+    if (n == 0) return MC_OK;
+    if (mc::launch_test_uniforms(seed, hist, ord, n, out, as_stream(stream)) != cudaSuccess) return MC_ERR_CUDA;
+    return cudaStreamSynchronize(as_stream(stream)) == cudaSuccess ? MC_OK : MC_ERR_CUDA;
+}
+
+}  // extern "C"

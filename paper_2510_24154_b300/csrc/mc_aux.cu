@@ -1,0 +1,284 @@
+// Streaming kernels around the transport: HU -> density (a1), radiological
+// thickness ray sums (a9), dose statistics over the batch sub-tallies (a8) and
+// the k(t, s) dose-to-signal correction (a11), plus two diagnostics.
+#include "mc_aux.h"
+#include "mc_device.cuh"
+
+namespace mc {
+
+// ------------------------------------------------------------- a1 --------
+// HU-to-density curve (Sec. 2.1.2; the curve itself is a stated reading):
+// rho = 1 + HU/1000 for HU <= 0, 1 + 0.6 HU/1000 above, floored at air's
+// 0.001205, HU clamped to [-1024, 3071].  Material follows from density
+// thresholds evaluated with the same single-precision expression, which is
+// strictly increasing in HU, so the class boundaries -900 / -200 / 300 HU are
+// reproduced exactly.
+__device__ __forceinline__ float rho_of_hu(int hu) {
+    hu = min(max(hu, -1024), 3071);
+    const float h = static_cast<float>(hu);
+    const float r = (hu <= 0) ? fmaf(h, 1e-3f, 1.0f) : fmaf(h, 6e-4f, 1.0f);
+    return fmaxf(r, 0.001205f);
+}
+
+__global__ void k_hu_to_rho(const int16_t* __restrict__ hu, float* __restrict__ rho, size_t n,
+                            unsigned int* rho_max_bits, float* thr) {
+    __shared__ unsigned int s_max[4];
+    if (threadIdx.x < 4) s_max[threadIdx.x] = 0u;
+    __syncthreads();
+    const float t0 = rho_of_hu(-900), t1 = rho_of_hu(-200), t2 = rho_of_hu(300);
+    unsigned int lmax[4] = {0u, 0u, 0u, 0u};
+    const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+    // eight voxels per 16-byte load
+    const size_t n8 = n / 8;
+    const int4* hu8 = reinterpret_cast<const int4*>(hu);
+    for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n8; i += stride) {
+        const int4 q = __ldg(&hu8[i]);
+        const int32_t w[4] = {q.x, q.y, q.z, q.w};
+        float r[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            r[2 * k] = rho_of_hu(static_cast<int16_t>(w[k] & 0xffff));
+            r[2 * k + 1] = rho_of_hu(static_cast<int16_t>(static_cast<uint32_t>(w[k]) >> 16));
+        }
+        float4* out = reinterpret_cast<float4*>(rho + 8 * i);
+        out[0] = make_float4(r[0], r[1], r[2], r[3]);
+        out[1] = make_float4(r[4], r[5], r[6], r[7]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int m = (r[k] >= t0) + (r[k] >= t1) + (r[k] >= t2);
+            const unsigned int b = __float_as_uint(r[k]);
+            lmax[0] = (m == 0) ? max(lmax[0], b) : lmax[0];
+            lmax[1] = (m == 1) ? max(lmax[1], b) : lmax[1];
+            lmax[2] = (m == 2) ? max(lmax[2], b) : lmax[2];
+            lmax[3] = (m == 3) ? max(lmax[3], b) : lmax[3];
+        }
+    }
+    for (size_t i = 8 * n8 + static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float r = rho_of_hu(hu[i]);
+        rho[i] = r;
+        const int m = (r >= t0) + (r >= t1) + (r >= t2);
+        lmax[m] = max(lmax[m], __float_as_uint(r));
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        unsigned int v = lmax[m];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(kFull, v, o));
+        if ((threadIdx.x & 31) == 0 && v) atomicMax(&s_max[m], v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 4 && s_max[threadIdx.x]) atomicMax(&rho_max_bits[threadIdx.x], s_max[threadIdx.x]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) { thr[0] = t0; thr[1] = t1; thr[2] = t2; }
+}
+
+// ------------------------------------------------------------- a9 --------
+// Radiological thickness (Sec. 2.2, item 1): t = sum_v rho_v l_v along the
+// ray from the source to each pixel centre on the sensitive layer's
+// mid-plane.  Incremental voxel traversal (the Siddon parametrisation walked
+// plane by plane); crossings in single precision relative to the source,
+// products accumulated in double.
+__global__ void k_tmap(TmapArgs A, double* __restrict__ t) {
+    const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= A.npx * A.npy) return;
+    const int ix = pix % A.npx, iy = pix / A.npx;
+    const float X = -A.hwx + (ix + 0.5f) * A.pitch, Y = -A.hwy + (iy + 0.5f) * A.pitch, Z = A.zs;
+    float d[3], S[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        S[k] = A.src[k];
+        d[k] = A.iso[k] + X * A.ex[k] + Y * A.ey[k] + Z * A.ez[k] - S[k];
+    }
+    const float len = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const int n[3] = {A.nx, A.ny, A.nz};
+    const float o[3] = {A.ox, A.oy, A.oz}, v[3] = {A.vx, A.vy, A.vz};
+    float amin = 0.0f, amax = 1.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float lo = o[k], hi = o[k] + n[k] * v[k];
+        if (d[k] != 0.0f) {
+            const float a0 = (lo - S[k]) / d[k], a1 = (hi - S[k]) / d[k];
+            amin = fmaxf(amin, fminf(a0, a1));
+            amax = fminf(amax, fmaxf(a0, a1));
+        } else if (S[k] <= lo || S[k] >= hi) {
+            amax = -1.0f;
+        }
+    }
+    double acc = 0.0;
+    if (amin < amax) {
+        int idx[3], stp[3], plane[3];
+        float anext[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float pk = S[k] + amin * d[k];
+            idx[k] = min(max(__float2int_rd((pk - o[k]) / v[k]), 0), n[k] - 1);
+            stp[k] = (d[k] > 0.0f) ? 1 : (d[k] < 0.0f ? -1 : 0);
+            plane[k] = idx[k] + (stp[k] > 0 ? 1 : 0);
+            anext[k] = (stp[k] != 0) ? (o[k] + plane[k] * v[k] - S[k]) / d[k] : INFINITY;
+        }
+        float acur = amin;
+        const int maxit = n[0] + n[1] + n[2] + 3;
+        for (int it = 0; it < maxit; ++it) {
+            int k = 0;
+            if (anext[1] < anext[k]) k = 1;
+            if (anext[2] < anext[k]) k = 2;
+            const float aend = fminf(anext[k], amax);
+            const float rho = __ldg(&A.rho[(static_cast<size_t>(idx[2]) * A.ny + idx[1]) * A.nx + idx[0]]);
+            acc += static_cast<double>(rho) * static_cast<double>((aend - acur) * len);
+            if (anext[k] >= amax) break;
+            acur = anext[k];
+            idx[k] += stp[k];
+            if (idx[k] < 0 || idx[k] >= n[k]) break;
+            plane[k] += stp[k];
+            anext[k] = (o[k] + plane[k] * v[k] - S[k]) / d[k];
+        }
+    }
+    t[pix] = acc + A.t_offset;
+}
+
+// ------------------------------------------------------------- a8 --------
+// Per pixel: dose per history D = sum_b E_b / N, batch doses D_b = E_b / N_b,
+// sigma = sqrt(sum_b (D_b - D)^2 / (B (B - 1))).  Also the image maximum.
+__global__ void k_dose(const unsigned long long* __restrict__ tally, int npix, int B, const double* __restrict__ nb,
+                       double n_hist, double conv, double* __restrict__ dose, double* __restrict__ sigma,
+                       unsigned long long* max_bits) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double dm = 0.0;
+    if (i < npix) {
+        const double per_q = 1.0 / 2.56e8;          // MeV per tally unit
+        double sum = 0.0;
+        for (int b = 0; b < B; ++b) sum += static_cast<double>(tally[static_cast<size_t>(b) * npix + i]);
+        dm = sum * per_q / n_hist * conv;
+        double ss = 0.0;
+        for (int b = 0; b < B; ++b) {
+            const double db = static_cast<double>(tally[static_cast<size_t>(b) * npix + i]) * per_q / nb[b] * conv;
+            ss += (db - dm) * (db - dm);
+        }
+        dose[i] = dm;
+        if (sigma) sigma[i] = sqrt(ss / (static_cast<double>(B) * (B - 1)));
+    }
+    unsigned long long bits = __double_as_longlong(dm);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_down_sync(kFull, bits, o);
+        bits = ob > bits ? ob : bits;
+    }
+    if ((threadIdx.x & 31) == 0 && bits) atomicMax(max_bits, bits);
+}
+
+// Mean relative uncertainty over pixels above half the maximum: per-block
+// partial sums (fixed order), then a single-block final sum.
+__global__ void k_u_partial(const double* __restrict__ dose, const double* __restrict__ sigma, int npix,
+                            const unsigned long long* max_bits, double* part_sum, unsigned int* part_cnt) {
+    __shared__ double s_sum[256];
+    __shared__ unsigned int s_cnt[256];
+    const double half = 0.5 * __longlong_as_double(static_cast<long long>(*max_bits));
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    unsigned int c = 0u;
+    if (i < npix && dose[i] > half) { v = sigma[i] / dose[i]; c = 1u; }
+    s_sum[threadIdx.x] = v;
+    s_cnt[threadIdx.x] = c;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) { s_sum[threadIdx.x] += s_sum[threadIdx.x + s]; s_cnt[threadIdx.x] += s_cnt[threadIdx.x + s]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { part_sum[blockIdx.x] = s_sum[0]; part_cnt[blockIdx.x] = s_cnt[0]; }
+}
+
+__global__ void k_u_final(const double* part_sum, const unsigned int* part_cnt, int nparts, double* u) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        unsigned long long c = 0ull;
+        for (int i = 0; i < nparts; ++i) { s += part_sum[i]; c += part_cnt[i]; }
+        *u = c ? s / static_cast<double>(c) : __longlong_as_double(0x7ff8000000000000ll);
+    }
+}
+
+// ------------------------------------------------------------ a11 --------
+// signal = k_scale * k(t, s) * dose.  ks holds the table's column already
+// interpolated at the field's s (the bilinear rule taken one axis at a time);
+// here the per-pixel linear step along t, clamped at the end nodes.
+__global__ void k_lut(const double* __restrict__ dose, const double* __restrict__ t, int npix,
+                      const double* __restrict__ tn, const double* __restrict__ ks, int nt, double k_scale,
+                      float* __restrict__ signal) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npix) return;
+    double tt = fmin(fmax(t[i], tn[0]), tn[nt - 1]);
+    int lo = 0, hi = nt - 1;                       // largest node index with tn <= tt
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (tn[mid] <= tt) lo = mid; else hi = mid;
+    }
+    lo = min(lo, nt - 2);
+    const double f = (tt - tn[lo]) / (tn[lo + 1] - tn[lo]);
+    const double k = ks[lo] + f * (ks[lo + 1] - ks[lo]);
+    signal[i] = static_cast<float>(k_scale * k * dose[i]);
+}
+
+// ---------------------------------------------------------- diagnostics --
+__global__ void k_test_philox(const uint32_t* in, uint32_t* out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 r = philox4x32_10(make_uint4(in[6 * i], in[6 * i + 1], in[6 * i + 2], in[6 * i + 3]), in[6 * i + 4],
+                                  in[6 * i + 5]);
+    out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
+}
+
+__global__ void k_test_uniforms(unsigned long long seed, unsigned long long hist, uint32_t ord, int n, float* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Rng r;
+    r.setup(seed, hist, ord, 0u);
+    for (int i = 0; i < n; ++i) out[i] = r.u();
+}
+
+// ----------------------------------------------------------- launchers ---
+cudaError_t launch_hu_to_rho(const int16_t* hu, float* rho, size_t n, unsigned int* rho_max_bits, float* thr,
+                             int sm_count, cudaStream_t s) {
+    const int block = 256;
+    size_t want = (n / 8 + block - 1) / block;
+    int grid = static_cast<int>(want < static_cast<size_t>(sm_count) * 8 ? want : static_cast<size_t>(sm_count) * 8);
+    if (grid < 1) grid = 1;
+    k_hu_to_rho<<<grid, block, 0, s>>>(hu, rho, n, rho_max_bits, thr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tmap(const TmapArgs& A, double* t, cudaStream_t s) {
+    const int npix = A.npx * A.npy, block = 128;
+    k_tmap<<<(npix + block - 1) / block, block, 0, s>>>(A, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dose(const unsigned long long* tally, int npix, int B, const double* nb, double n_hist,
+                        double conv, double* dose, double* sigma, unsigned long long* max_bits, double* part_sum,
+                        unsigned int* part_cnt, double* u, cudaStream_t s) {
+    const int block = 256, grid = (npix + block - 1) / block;
+    cudaError_t e = cudaMemsetAsync(max_bits, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_dose<<<grid, block, 0, s>>>(tally, npix, B, nb, n_hist, conv, dose, sigma, max_bits);
+    if (u && sigma) {
+        k_u_partial<<<grid, block, 0, s>>>(dose, sigma, npix, max_bits, part_sum, part_cnt);
+        k_u_final<<<1, 32, 0, s>>>(part_sum, part_cnt, grid, u);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lut(const double* dose, const double* t, int npix, const double* tn, const double* ks, int nt,
+                       double k_scale, float* signal, cudaStream_t s) {
+    const int block = 256;
+    k_lut<<<(npix + block - 1) / block, block, 0, s>>>(dose, t, npix, tn, ks, nt, k_scale, signal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_test_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t s) {
+    k_test_philox<<<(n + 127) / 128, 128, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_test_uniforms(unsigned long long seed, unsigned long long hist, uint32_t ord, int n, float* out,
+                                 cudaStream_t s) {
+    k_test_uniforms<<<1, 32, 0, s>>>(seed, hist, ord, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace mc

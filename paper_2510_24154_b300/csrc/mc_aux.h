@@ -1,0 +1,42 @@
+// Host-callable launchers of the library's kernels (internal header).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mc {
+
+struct Params;
+struct Ctl;
+
+// Ray-sum arguments for the radiological thickness map.
+struct TmapArgs {
+    int nx, ny, nz;
+    float ox, oy, oz, vx, vy, vz;
+    const float* rho;
+    float src[3], iso[3], ex[3], ey[3], ez[3];
+    int npx, npy;
+    float pitch, hwx, hwy, zs;
+    double t_offset;
+};
+
+size_t transport_smem(int type);
+cudaError_t transport_occupancy(int type, int block, int* blocks_per_sm);
+cudaError_t launch_transport(int type, const Params& P, int grid, int block, cudaStream_t s);
+cudaError_t launch_swap(Ctl* c, int t, cudaStream_t s);
+cudaError_t launch_wave_begin(Ctl* c, unsigned long long per_wave, cudaStream_t s);
+
+cudaError_t launch_hu_to_rho(const int16_t* hu, float* rho, size_t n, unsigned int* rho_max_bits, float* thr,
+                             int sm_count, cudaStream_t s);
+cudaError_t launch_tmap(const TmapArgs& A, double* t, cudaStream_t s);
+cudaError_t launch_dose(const unsigned long long* tally, int npix, int B, const double* nb, double n_hist,
+                        double conv, double* dose, double* sigma, unsigned long long* max_bits, double* part_sum,
+                        unsigned int* part_cnt, double* u, cudaStream_t s);
+cudaError_t launch_lut(const double* dose, const double* t, int npix, const double* tn, const double* ks, int nt,
+                       double k_scale, float* signal, cudaStream_t s);
+cudaError_t launch_test_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t s);
+cudaError_t launch_test_uniforms(unsigned long long seed, unsigned long long hist, uint32_t ord, int n, float* out,
+                                 cudaStream_t s);
+
+}  // namespace mc

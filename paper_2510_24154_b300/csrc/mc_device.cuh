@@ -1,0 +1,370 @@
+// Device-side building blocks of the EPID transit Monte Carlo kernels.
+//
+// Particles live in structure-of-arrays banks, one pair of banks (input and
+// carry) per event type: photons in the CT, electrons in the CT, photons in
+// the EPID, electrons in the EPID.  Each transport kernel is persistent: a
+// warp keeps one particle per lane, advances every live lane by one event per
+// iteration and refills dead lanes from its input bank with one atomic per
+// warp, so the warp stays full while work remains.  Secondaries are compacted
+// into the banks of their event type with a warp ballot and a prefix count.
+//
+// Random numbers: draw d of the particle with history id h and ordinal o is
+// word d mod 4 of Philox4x32-10 (Salmon et al., SC'11) at counter
+// (d div 4, o, h_lo, h_hi) under key (seed_lo, seed_hi), mapped to
+// ((u >> 9) + 0.5) 2^-23.  Secondaries take the ordinal
+// fmix32(parent * 0x85EBCA6B + 8 d + slot + 1) (MurmurHash3 finaliser), with d
+// the parent's draw count when it creates them, so a history's random
+// numbers do not depend on the order in which the GPU processes events.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mc {
+
+constexpr float kMec2 = 0.51099895f;
+constexpr float kTwoMec2 = 1.0219979f;
+constexpr int kPhotonNodes = 2048;
+constexpr int kElectronNodes = 512;
+constexpr int kNumMat = 7;
+constexpr int kMaxLayers = 8;
+constexpr float kQuantaPerMeV = 2.56e8f;      // tally unit 2^-8 eV
+constexpr float kStopMargin = 1e-6f;          // electrons stop at T <= cutoff + this
+constexpr unsigned kFull = 0xffffffffu;
+
+enum BankType { kPhotonCT = 0, kElectronCT = 1, kPhotonEPID = 2, kElectronEPID = 3, kNumBanks = 4 };
+enum EnergyCounter { kESrc = 0, kECT = 1, kEEsc = 2, kELost = 3, kEEpid0 = 4, kNumEnergy = 12 };
+enum EventCounter {
+    kCFlightsCT = 0, kCRealCT, kCCompton, kCPhoto, kCPair, kCEStepsCT, kCEStepsEPID, kCMoller, kCBrem,
+    kCPrimAtEPID, kCUncollided, kCLost, kCFlightsEPID, kCElectrons, kCPositrons, kCPhotons2, kNumEvents
+};
+enum Flags : uint32_t { kPositron = 1u, kCollided = 2u };
+enum ErrorBits : uint32_t { kErrOverflow = 1u, kErrNonFinite = 2u };
+
+struct MatC {
+    float ne, pe_above, pe_below, pair, brem, msc;
+};
+
+struct BankPtr {
+    float *x, *y, *z, *u, *v, *w, *E;
+    uint32_t *hist, *ord, *draws, *cell, *flags;
+};
+
+// Run control shared by the kernels of one run (device memory).
+struct Ctl {
+    unsigned long long next_prim;   // next history (run-local index) to start
+    unsigned long long prim_limit;  // histories may start below this in the current wave
+    unsigned long long n_total;
+    uint32_t count[kNumBanks][2];
+    uint32_t head[kNumBanks];
+    uint32_t cur[kNumBanks];        // input parity per bank type
+    uint32_t allow_flush;           // more primaries follow: warps may hand low-occupancy work on
+    uint32_t error;
+};
+
+struct Params {
+    // CT (patient frame)
+    int nx, ny, nz;
+    float ox, oy, oz, vx, vy, vz, ivx, ivy, ivz;
+    const float* rho;
+    float rho_max[4];
+    float thr[3];                   // density thresholds lung / water / bone
+    // beam frame axes in patient coordinates, isocentre, source distance
+    float ex[3], ey[3], ez[3], iso[3];
+    float sad;
+    // EPID (beam frame)
+    int nl, sens, npx, npy;
+    float pitch, ipitch, hwx, hwy;
+    float zp[kMaxLayers + 1];
+    int lmat[kMaxLayers];
+    float lrho[kMaxLayers];
+    // source
+    int n_rect;
+    const float4* rect;
+    const double* cdf;
+    float e_max, mono_e;
+    // physics
+    float pcut, ecut, tstop, wcc, wcb, ln_wcb, step_frac;
+    int max_steps, coupled, nbatch;
+    MatC mat[kNumMat];
+    const float2* ptab;
+    float p_lnE0, p_idx;
+    const float2* etab;             // [kNumMat][kElectronNodes]
+    float e_lnT0, e_idx;
+    // run
+    unsigned long long seed, hist_base;
+    unsigned long long* tally;      // [B][npy][npx]
+    unsigned long long* energy;     // [kNumEnergy]
+    unsigned long long* events;     // [kNumEvents]
+    Ctl* ctl;
+    BankPtr bank[kNumBanks][2];
+    uint32_t cap;
+    int flush_lanes;
+};
+
+// ------------------------------------------------------------------ RNG ---
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16; h *= 0x85EBCA6Bu; h ^= h >> 13; h *= 0xC2B2AE35u; h ^= h >> 16;
+    return h;
+}
+
+__device__ __forceinline__ uint32_t child_ordinal(uint32_t parent, uint32_t draws, uint32_t slot) {
+    return fmix32(parent * 0x85EBCA6Bu + (draws * 8u + slot + 1u));
+}
+
+struct Rng {
+    uint32_t ord, hlo, hhi, d;
+    uint32_t w0, w1, w2, w3;
+    uint32_t k0, k1;
+
+    __device__ __forceinline__ void setup(unsigned long long seed, unsigned long long hist, uint32_t o, uint32_t draws) {
+        k0 = static_cast<uint32_t>(seed);
+        k1 = static_cast<uint32_t>(seed >> 32);
+        hlo = static_cast<uint32_t>(hist);
+        hhi = static_cast<uint32_t>(hist >> 32);
+        ord = o;
+        d = draws;
+        if (d & 3u) refill();
+    }
+    __device__ __forceinline__ void refill() {
+        const uint4 r = philox4x32_10(make_uint4(d >> 2, ord, hlo, hhi), k0, k1);
+        w0 = r.x; w1 = r.y; w2 = r.z; w3 = r.w;
+    }
+    __device__ __forceinline__ float u() {
+        if ((d & 3u) == 0u) refill();
+        const uint32_t j = d & 3u;
+        const uint32_t w = (j == 0u) ? w0 : (j == 1u) ? w1 : (j == 2u) ? w2 : w3;
+        ++d;
+        return (static_cast<float>(w >> 9) + 0.5f) * 1.1920928955078125e-07f;
+    }
+};
+
+// ------------------------------------------------------ fixed point -------
+
+__device__ __forceinline__ unsigned long long quanta(float e_mev) {
+    return __float2ull_rn(e_mev * kQuantaPerMeV);
+}
+
+// ------------------------------------------------------ warp helpers ------
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
+
+// Warp-aggregated reservation of slots in a queue counter: every lane of the
+// warp must call it; lanes with want=false get no slot.  One atomic per warp.
+__device__ __forceinline__ uint32_t warp_reserve(bool want, uint32_t* counter) {
+    const unsigned m = __ballot_sync(kFull, want);
+    if (m == 0u) return 0u;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane_id() == leader) base = atomicAdd(counter, static_cast<uint32_t>(__popc(m)));
+    base = __shfl_sync(kFull, base, leader);
+    return base + __popc(m & lanemask_lt());
+}
+
+// --------------------------------------------------------- bank I/O -------
+
+struct Part {
+    float x, y, z, u, v, w, E;
+    uint32_t hist, cell, flags;
+    Rng rng;
+};
+
+__device__ __forceinline__ void load_part(const BankPtr& b, uint32_t i, Part& p, const Params& P) {
+    p.x = b.x[i]; p.y = b.y[i]; p.z = b.z[i];
+    p.u = b.u[i]; p.v = b.v[i]; p.w = b.w[i];
+    p.E = b.E[i];
+    p.hist = b.hist[i];
+    p.cell = b.cell[i];
+    p.flags = b.flags[i];
+    p.rng.setup(P.seed, P.hist_base + p.hist, b.ord[i], b.draws[i]);
+}
+
+__device__ __forceinline__ void store_part(const BankPtr& b, uint32_t i, const Part& p) {
+    b.x[i] = p.x; b.y[i] = p.y; b.z[i] = p.z;
+    b.u[i] = p.u; b.v[i] = p.v; b.w[i] = p.w;
+    b.E[i] = p.E;
+    b.hist[i] = p.hist;
+    b.ord[i] = p.rng.ord;
+    b.draws[i] = p.rng.d;
+    b.cell[i] = p.cell;
+    b.flags[i] = p.flags;
+}
+
+// A secondary waiting to be written to a bank at the end of an iteration; it
+// starts at its parent's position and cell.
+struct Emit {
+    int dest;        // bank type, -1 = none
+    float E, u, v, w;
+    uint32_t ord, flags;
+};
+
+__device__ __forceinline__ void emit_none(Emit& e) { e.dest = -1; }
+
+// Writes the lane's pending emission into its destination bank (input parity
+// of that type, or the carry parity when it is the kernel's own type).
+// Convergent: all lanes call it.
+__device__ __forceinline__ void flush_emit(const Params& P, const Emit& e, const Part& parent, int own_type,
+                                           uint32_t own_in) {
+#pragma unroll
+    for (int t = 0; t < kNumBanks; ++t) {
+        const bool want = (e.dest == t);
+        if (__ballot_sync(kFull, want) == 0u) continue;
+        const uint32_t par = (t == own_type) ? (own_in ^ 1u) : P.ctl->cur[t];
+        const uint32_t slot = warp_reserve(want, &P.ctl->count[t][par]);
+        if (want) {
+            if (slot < P.cap) {
+                const BankPtr& b = P.bank[t][par];
+                b.x[slot] = parent.x; b.y[slot] = parent.y; b.z[slot] = parent.z;
+                b.u[slot] = e.u; b.v[slot] = e.v; b.w[slot] = e.w;
+                b.E[slot] = e.E;
+                b.hist[slot] = parent.hist;
+                b.ord[slot] = e.ord;
+                b.draws[slot] = 0u;
+                b.cell[slot] = parent.cell;
+                b.flags[slot] = e.flags;
+            } else {
+                atomicOr(&P.ctl->error, kErrOverflow);
+                atomicAdd(&P.energy[kELost], quanta(e.E + ((e.flags & kPositron) ? kTwoMec2 : 0.0f)));
+            }
+        }
+    }
+}
+
+// Moves the lane's own particle into bank `t` (input parity of t).
+__device__ __forceinline__ void flush_self(const Params& P, bool want, int t, uint32_t par, const Part& p) {
+    if (__ballot_sync(kFull, want) == 0u) return;
+    const uint32_t slot = warp_reserve(want, &P.ctl->count[t][par]);
+    if (want) {
+        if (slot < P.cap) {
+            store_part(P.bank[t][par], slot, p);
+        } else {
+            atomicOr(&P.ctl->error, kErrOverflow);
+            atomicAdd(&P.energy[kELost], quanta(p.E + ((p.flags & kPositron) ? kTwoMec2 : 0.0f)));
+        }
+    }
+}
+
+// -------------------------------------------------------- geometry --------
+
+__device__ __forceinline__ void to_beam(const Params& P, float px, float py, float pz, float& bx, float& by,
+                                        float& bz) {
+    const float dx = px - P.iso[0], dy = py - P.iso[1], dz = pz - P.iso[2];
+    bx = dx * P.ex[0] + dy * P.ex[1] + dz * P.ex[2];
+    by = dx * P.ey[0] + dy * P.ey[1] + dz * P.ey[2];
+    bz = dx * P.ez[0] + dy * P.ez[1] + dz * P.ez[2];
+}
+
+__device__ __forceinline__ void to_beam_dir(const Params& P, float u, float v, float w, float& bu, float& bv,
+                                            float& bw) {
+    bu = u * P.ex[0] + v * P.ex[1] + w * P.ex[2];
+    bv = u * P.ey[0] + v * P.ey[1] + w * P.ey[2];
+    bw = u * P.ez[0] + v * P.ez[1] + w * P.ez[2];
+}
+
+__device__ __forceinline__ uint32_t pack_cell(int ix, int iy, int iz) {
+    return static_cast<uint32_t>(ix) | (static_cast<uint32_t>(iy) << 10) | (static_cast<uint32_t>(iz) << 20);
+}
+__device__ __forceinline__ int cell_x(uint32_t c) { return c & 1023u; }
+__device__ __forceinline__ int cell_y(uint32_t c) { return (c >> 10) & 1023u; }
+__device__ __forceinline__ int cell_z(uint32_t c) { return (c >> 20) & 1023u; }
+
+__device__ __forceinline__ int material_of(const Params& P, float rho) {
+    return (rho >= P.thr[0]) + (rho >= P.thr[1]) + (rho >= P.thr[2]);
+}
+
+// Unit direction rotated by polar cosine ct and azimuth (cp, sp); the polar
+// frame is used within 0.99999 of the z axis.
+__device__ __forceinline__ void rotate_dir(float& u, float& v, float& w, float ct, float cp, float sp) {
+    const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+    if (fabsf(w) > 0.99999f) {
+        const float sg = (w > 0.0f) ? 1.0f : -1.0f;
+        u = st * cp; v = st * sp; w = sg * ct;
+    } else {
+        const float tmp = sqrtf(1.0f - w * w);
+        const float nu = u * ct + st * (u * w * cp - v * sp) / tmp;
+        const float nv = v * ct + st * (v * w * cp + u * sp) / tmp;
+        const float nw = w * ct - tmp * st * cp;
+        u = nu; v = nv; w = nw;
+    }
+    const float inv = 1.0f / sqrtf(u * u + v * v + w * w);
+    u *= inv; v *= inv; w *= inv;
+}
+
+// ------------------------------------------------------- physics ----------
+
+// Photon cross-section components at energy E from the shared-memory table.
+struct PhotonXS { float skn, pair, epow; bool below_edge; };
+
+__device__ __forceinline__ PhotonXS photon_xs(const float2* tab, const Params& P, float E) {
+    const float lnE = logf(E);
+    const float x = (lnE - P.p_lnE0) * P.p_idx;
+    const int i = min(max(__float2int_rd(x), 0), kPhotonNodes - 2);
+    const float f = x - static_cast<float>(i);
+    const float2 a = tab[i], b = tab[i + 1];
+    PhotonXS r;
+    r.skn = fmaf(f, b.x - a.x, a.x);
+    r.pair = fmaf(f, b.y - a.y, a.y);
+    r.epow = expf(-3.2f * lnE);
+    r.below_edge = E < 0.05024f;
+    return r;
+}
+
+// Per-gram partial coefficients (Compton, photoelectric, pair) of material m.
+__device__ __forceinline__ void photon_mu(const Params& P, int m, const PhotonXS& x, float& mc, float& mp,
+                                          float& mq) {
+    const MatC& c = P.mat[m];
+    mc = c.ne * x.skn;
+    mp = (x.below_edge ? c.pe_below : c.pe_above) * x.epow;
+    mq = c.pair * x.pair;
+}
+
+// Electron table lookup: (soft stopping power, hard Moller) per gram.
+__device__ __forceinline__ float2 electron_tab(const float2* tab, const Params& P, int m, float lnT) {
+    const float x = (lnT - P.e_lnT0) * P.e_idx;
+    const int i = min(max(__float2int_rd(x), 0), kElectronNodes - 2);
+    const float f = x - static_cast<float>(i);
+    const float2 a = tab[m * kElectronNodes + i], b = tab[m * kElectronNodes + i + 1];
+    return make_float2(fmaf(f, b.x - a.x, a.x), fmaf(f, b.y - a.y, a.y));
+}
+
+// Screening parameter A of the screened-Rutherford (Wentzel) law whose mean
+// <1 - cos> equals 1 - exp(-G); -1 means isotropic.  Newton on ln A.
+__device__ __forceinline__ float wentzel_A(float G) {
+    const float m = -0.5f * expm1f(-G);
+    if (0.5f - m < 1e-6f) return -1.0f;
+    float y = (m < 0.3f) ? logf(m / fmaxf(logf(1.0f / m) - 1.0f, 1.0f)) : logf(1.0f / (6.0f * (0.5f - m)));
+    for (int it = 0; it < 12; ++it) {
+        const float A = expf(y);
+        float mean, dm;
+        if (A > 100.0f) {
+            const float x = 1.0f / A;
+            mean = 0.5f - x * (1.0f / 6.0f - x * (1.0f / 12.0f - x * (1.0f / 20.0f)));
+            dm = x * x * (1.0f / 6.0f - x * (1.0f / 6.0f));
+        } else {
+            const float l = log1pf(1.0f / A);
+            mean = A * ((1.0f + A) * l - 1.0f);
+            dm = (1.0f + 2.0f * A) * l - 2.0f;
+        }
+        float step = (mean - m) / (A * dm);
+        step = fminf(fmaxf(step, -2.0f), 2.0f);
+        y -= step;
+        if (fabsf(step) < 2e-7f) break;
+    }
+    return expf(y);
+}
+
+}  // namespace mc

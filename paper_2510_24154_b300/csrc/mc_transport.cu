@@ -1,0 +1,731 @@
+// Transport kernels of the EPID transit Monte Carlo (paper Sec. 2.1).
+//
+// Four persistent kernels, one per event type, run in waves:
+//   photons in the CT    Woodcock (delta) tracking against the majorant
+//                        max_m rho_max,m mu_m(E); real interactions sampled as
+//                        Compton (Klein-Nishina), photoelectric or pair (Sec. 2.1.2).
+//                        Fuses the source (Sec. 2.1.1): dead lanes start new
+//                        histories once the input bank is drained.
+//   electrons in the CT  Class II condensed history: CSDA soft losses, hard
+//                        Moller and bremsstrahlung by delta tracking against
+//                        the start-of-step value, a random-hinge Wentzel
+//                        deflection, steps limited by voxel faces.
+//   photons in the EPID  exact optical-depth tracking through the layer stack.
+//   electrons in the EPID the same condensed history in the layers; energy in
+//                        the sensitive layer goes to the pixel tally.
+// Each kernel follows, draw for draw, the sampling order of the written model,
+// so a history fed the same Philox keys replays on another implementation.
+#include "mc_device.cuh"
+
+namespace mc {
+
+namespace {
+
+// Per-block accumulators and lane-private counters.
+struct Acc {
+    unsigned long long ct, src, esc, lost;
+    uint32_t flights, steps;
+};
+
+__device__ __forceinline__ void acc_flush(const Params& P, Acc& a, unsigned long long* s_energy,
+                                          unsigned long long* s_events, int flights_idx, int steps_idx) {
+    // warp reduction of the lane-private values, then one shared atomic per warp
+    unsigned long long v[4] = {a.ct, a.src, a.esc, a.lost};
+    uint32_t f = a.flights, s = a.steps;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] += __shfl_down_sync(kFull, v[k], o);
+        f += __shfl_down_sync(kFull, f, o);
+        s += __shfl_down_sync(kFull, s, o);
+    }
+    if (lane_id() == 0) {
+        if (v[0]) atomicAdd(&s_energy[kECT], v[0]);
+        if (v[1]) atomicAdd(&s_energy[kESrc], v[1]);
+        if (v[2]) atomicAdd(&s_energy[kEEsc], v[2]);
+        if (v[3]) atomicAdd(&s_energy[kELost], v[3]);
+        if (f) atomicAdd(&s_events[flights_idx], static_cast<unsigned long long>(f));
+        if (s) atomicAdd(&s_events[steps_idx], static_cast<unsigned long long>(s));
+    }
+}
+
+__device__ __forceinline__ float rest_extra(uint32_t flags) { return (flags & kPositron) ? kTwoMec2 : 0.0f; }
+
+// Energy deposited at beam-frame position (x, y) in EPID layer `layer`.
+__device__ __forceinline__ void deposit_epid(const Params& P, unsigned long long* s_energy, int layer, float x,
+                                             float y, uint32_t hist, float dE) {
+    if (!(dE > 0.0f)) return;
+    const unsigned long long q = quanta(dE);
+    atomicAdd(&s_energy[kEEpid0 + layer], q);
+    if (layer != P.sens) return;
+    int ix = __float2int_rd((x + P.hwx) / P.pitch);
+    int iy = __float2int_rd((y + P.hwy) / P.pitch);
+    ix = min(max(ix, 0), P.npx - 1);
+    iy = min(max(iy, 0), P.npy - 1);
+    const unsigned long long b = (P.hist_base + hist) % static_cast<unsigned long long>(P.nbatch);
+    atomicAdd(&P.tally[(b * P.npy + iy) * P.npx + ix], q);
+}
+
+template <bool EPID>
+__device__ __forceinline__ void deposit(const Params& P, Acc& a, unsigned long long* s_energy, uint32_t cell,
+                                        float x, float y, uint32_t hist, float dE) {
+    if (EPID) deposit_epid(P, s_energy, static_cast<int>(cell), x, y, hist, dE);
+    else if (dE > 0.0f) a.ct += quanta(dE);
+}
+
+// Sends a particle that leaves the CT across the vacuum gap: onto the EPID's
+// top plane if its line meets the detector face, else out of the world.
+// Any point of the line will do: the CT lies wholly above the detector.
+__device__ __forceinline__ bool transfer_to_epid(const Params& P, Part& p, Acc& a, unsigned long long* s_events,
+                                                 bool is_photon) {
+    float bx, by, bz, bu, bv, bw;
+    to_beam(P, p.x, p.y, p.z, bx, by, bz);
+    to_beam_dir(P, p.u, p.v, p.w, bu, bv, bw);
+    const float eexit = p.E + rest_extra(p.flags);
+    if (bw >= 0.0f) { a.esc += quanta(eexit); return false; }
+    const float t = (P.zp[0] - bz) / bw;
+    const float X = bx + t * bu, Y = by + t * bv;
+    if (!(fabsf(X) < P.hwx && fabsf(Y) < P.hwy)) { a.esc += quanta(eexit); return false; }
+    p.x = X; p.y = Y; p.z = P.zp[0];
+    p.u = bu; p.v = bv; p.w = bw;
+    p.cell = 0u;
+    if (is_photon && p.rng.ord == 0u) {
+        atomicAdd(&s_events[kCPrimAtEPID], 1ull);
+        if (!(p.flags & kCollided)) atomicAdd(&s_events[kCUncollided], 1ull);
+    }
+    return true;
+}
+
+// A secondary charged particle created by `p` (slot `slot`): queued when
+// electrons are transported and above the cutoff, otherwise deposited.
+template <bool EPID>
+__device__ __forceinline__ void charged(const Params& P, Acc& a, unsigned long long* s_energy,
+                                        unsigned long long* s_events, const Part& p, Emit& e, float T, float du,
+                                        float dv, float dw, uint32_t slot, bool positron) {
+    if (P.coupled && T > P.ecut + kStopMargin) {
+        e.dest = EPID ? kElectronEPID : kElectronCT;
+        e.E = T; e.u = du; e.v = dv; e.w = dw;
+        e.ord = child_ordinal(p.rng.ord, p.rng.d, slot);
+        e.flags = kCollided | (positron ? kPositron : 0u);
+        atomicAdd(&s_events[positron ? kCPositrons : kCElectrons], 1ull);
+    } else {
+        deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, T);
+    }
+}
+
+// Annihilation at rest of a stopped positron (or a pair positron born at the
+// cutoff): two mc^2 photons, isotropic, back to back; slots 0 and 1 after the
+// two direction draws.  Encoded as one emission record of count 2.
+template <bool EPID>
+__device__ __forceinline__ void annihilate(const Params& P, unsigned long long* s_events, Part& p, Emit& e) {
+    const float ct = 2.0f * p.rng.u() - 1.0f;
+    float sp, cp;
+    sincospif(2.0f * p.rng.u(), &sp, &cp);
+    const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+    e.dest = EPID ? kPhotonEPID : kPhotonCT;
+    e.E = kMec2;
+    e.u = st * cp; e.v = st * sp; e.w = ct;
+    e.ord = p.rng.ord;          // both children derive from (ord, d) at write time
+    // bit 31 marks a back-to-back pair; bits 2..30 hold the parent's draw count
+    e.flags = kCollided | 0x80000000u | ((p.rng.d & 0x1fffffffu) << 2);
+    atomicAdd(&s_events[kCPhotons2], 2ull);
+}
+
+// Klein-Nishina composition-rejection; returns eps = E'/E and cos(theta).
+__device__ __forceinline__ void sample_kn(Rng& r, float E, float& eps, float& ct) {
+    const float k = E / kMec2;
+    const float e0 = 1.0f / (1.0f + 2.0f * k);
+    const float a1 = logf(1.0f + 2.0f * k);
+    const float a2 = 0.5f * (1.0f - e0 * e0);
+    for (int it = 0; it < 4096; ++it) {
+        const float r1 = r.u(), r2 = r.u(), r3 = r.u();
+        float e;
+        if (r1 * (a1 + a2) < a1) e = expf(-a1 * r2);
+        else e = sqrtf(e0 * e0 + (1.0f - e0 * e0) * r2);
+        const float t = (1.0f - e) / (k * e);
+        const float s2 = t * (2.0f - t);
+        const float g = 1.0f - e * s2 / (1.0f + e * e);
+        if (r3 < g) { eps = e; ct = 1.0f - t; return; }
+    }
+    eps = 1.0f; ct = 1.0f;
+}
+
+// Moller energy fraction on [wcc/T, 1/2]: 1/eps^2 proposal, rejection on the bracket.
+__device__ __forceinline__ float sample_moller(Rng& r, float T, float wcc) {
+    const float tau = T / kMec2, g = tau + 1.0f;
+    const float ec = wcc / T, c = tau / g, bb = (2.0f * tau + 1.0f) / (g * g);
+    const float gmax = 2.0f - bb + 0.25f * c * c;
+    for (int it = 0; it < 4096; ++it) {
+        const float r1 = r.u(), r2 = r.u();
+        const float eps = ec / (1.0f - r1 * (1.0f - 2.0f * ec));
+        const float x = eps / (1.0f - eps);
+        const float gv = 1.0f + x * x + c * c * eps * eps - bb * x;
+        if (r2 * gmax < gv) return eps;
+    }
+    return ec;
+}
+
+// Source spectrum E = Emax X, X ~ Beta(3/2, 7/2) as G1/(G1+G2) with
+// G1 = Exp + N^2/2 and G2 = 3 Exp + N'^2/2 (one Box-Muller pair), redrawn
+// below the photon cutoff.  Six draws per attempt.
+__device__ __forceinline__ float sample_spectrum(Rng& r, float emax, float pcut) {
+    for (int it = 0; it < 4096; ++it) {
+        const float ua = r.u(), ub = r.u(), uc = r.u(), ud = r.u(), u1 = r.u(), u2 = r.u();
+        const float L = -logf(u1);
+        const float c = cospif(2.0f * u2);
+        const float g1 = -logf(ua) + L * c * c;
+        const float g2 = -logf(ub * uc * ud) + L * (1.0f - c * c);
+        const float E = emax * g1 / (g1 + g2);
+        if (E >= pcut) return E;
+    }
+    return emax * 0.3f;
+}
+
+// A real photon interaction of p in material m (per-gram partials mc, mp, mq).
+// Returns false when the photon is absorbed.
+template <bool EPID>
+__device__ __forceinline__ bool photon_interact(const Params& P, Acc& a, unsigned long long* s_energy,
+                                                unsigned long long* s_events, Part& p, float mc, float mp,
+                                                float mq, Emit& e0, Emit& e1) {
+    const float tot = mc + mp + mq;
+    const float xi = p.rng.u();
+    p.flags |= kCollided;
+    if (xi * tot < mc) {
+        atomicAdd(&s_events[kCCompton], 1ull);
+        float eps, ct;
+        sample_kn(p.rng, p.E, eps, ct);
+        float sp, cp;
+        sincospif(2.0f * p.rng.u(), &sp, &cp);
+        const float E0 = p.E, E1 = eps * E0;
+        const float u0 = p.u, v0 = p.v, w0 = p.w;
+        rotate_dir(p.u, p.v, p.w, ct, cp, sp);
+        const float T = E0 - E1;
+        float eu = E0 * u0 - E1 * p.u, ev = E0 * v0 - E1 * p.v, ew = E0 * w0 - E1 * p.w;
+        const float n = sqrtf(eu * eu + ev * ev + ew * ew);
+        if (n > 0.0f) { eu /= n; ev /= n; ew /= n; } else { eu = u0; ev = v0; ew = w0; }
+        charged<EPID>(P, a, s_energy, s_events, p, e0, T, eu, ev, ew, 0u, false);
+        p.E = E1;
+        if (p.E < P.pcut) {
+            deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, p.E);
+            return false;
+        }
+        return true;
+    }
+    if (xi * tot < mc + mp) {
+        atomicAdd(&s_events[kCPhoto], 1ull);
+        charged<EPID>(P, a, s_energy, s_events, p, e0, p.E, p.u, p.v, p.w, 0u, false);
+        return false;
+    }
+    atomicAdd(&s_events[kCPair], 1ull);
+    const float avail = p.E - kTwoMec2;
+    const float xu = p.rng.u();
+    const float Tm = xu * avail, Tp = avail - Tm;
+    if (P.coupled) {
+        charged<EPID>(P, a, s_energy, s_events, p, e0, Tm, p.u, p.v, p.w, 0u, false);
+        if (Tp > P.ecut + kStopMargin) {
+            charged<EPID>(P, a, s_energy, s_events, p, e1, Tp, p.u, p.v, p.w, 1u, true);
+        } else {
+            deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, Tp);
+            annihilate<EPID>(P, s_events, p, e1);
+        }
+    } else {
+        deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, Tm + Tp);
+        annihilate<EPID>(P, s_events, p, e0);
+    }
+    return false;
+}
+
+// Distance to leave EPID layer l; which = 0 (layer plane), 1 (x edge), 2 (y edge).
+__device__ __forceinline__ float epid_dist(const Params& P, const Part& p, int l, int& which) {
+    float dz = INFINITY, dx = INFINITY, dy = INFINITY;
+    if (p.w < 0.0f) dz = (P.zp[l + 1] - p.z) / p.w;
+    else if (p.w > 0.0f) dz = (P.zp[l] - p.z) / p.w;
+    if (p.u > 0.0f) dx = (P.hwx - p.x) / p.u;
+    else if (p.u < 0.0f) dx = (-P.hwx - p.x) / p.u;
+    if (p.v > 0.0f) dy = (P.hwy - p.y) / p.v;
+    else if (p.v < 0.0f) dy = (-P.hwy - p.y) / p.v;
+    float d = dz; which = 0;
+    if (dx < d) { d = dx; which = 1; }
+    if (dy < d) { d = dy; which = 2; }
+    return fmaxf(d, 0.0f);
+}
+
+// Distance to the faces of CT voxel `cell`; axis = 0, 1, 2.
+__device__ __forceinline__ float ct_dist(const Params& P, const Part& p, uint32_t cell, int& axis) {
+    const int ix = cell_x(cell), iy = cell_y(cell), iz = cell_z(cell);
+    float dx = INFINITY, dy = INFINITY, dz = INFINITY;
+    if (p.u > 0.0f) dx = (P.ox + (ix + 1) * P.vx - p.x) / p.u;
+    else if (p.u < 0.0f) dx = (P.ox + ix * P.vx - p.x) / p.u;
+    if (p.v > 0.0f) dy = (P.oy + (iy + 1) * P.vy - p.y) / p.v;
+    else if (p.v < 0.0f) dy = (P.oy + iy * P.vy - p.y) / p.v;
+    if (p.w > 0.0f) dz = (P.oz + (iz + 1) * P.vz - p.z) / p.w;
+    else if (p.w < 0.0f) dz = (P.oz + iz * P.vz - p.z) / p.w;
+    float d = dx; axis = 0;
+    if (dy < d) { d = dy; axis = 1; }
+    if (dz < d) { d = dz; axis = 2; }
+    return fmaxf(d, 0.0f);
+}
+
+// ---------------------------------------------------------------------------
+// One Woodcock flight of a CT photon.  Returns false when the photon leaves
+// the event type (absorbed, escaped, or moved to the EPID: `move`).
+__device__ __forceinline__ bool photon_ct_event(const Params& P, const float2* tab, Acc& a,
+                                                unsigned long long* s_energy, unsigned long long* s_events,
+                                                Part& p, Emit& e0, Emit& e1, bool& move) {
+    const PhotonXS xs = photon_xs(tab, P, p.E);
+    float tot[4];
+    float smax = 0.0f;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        float c, q, r;
+        photon_mu(P, m, xs, c, q, r);
+        tot[m] = c + q + r;
+        smax = fmaxf(smax, P.rho_max[m] * tot[m]);
+    }
+    const float s = -logf(p.rng.u()) / smax;
+    p.x += s * p.u; p.y += s * p.v; p.z += s * p.w;
+    ++a.flights;
+    const int ix = __float2int_rd((p.x - P.ox) / P.vx);
+    const int iy = __float2int_rd((p.y - P.oy) / P.vy);
+    const int iz = __float2int_rd((p.z - P.oz) / P.vz);
+    if (ix < 0 || ix >= P.nx || iy < 0 || iy >= P.ny || iz < 0 || iz >= P.nz) {
+        move = transfer_to_epid(P, p, a, s_events, true);
+        return false;
+    }
+    const float rho = __ldg(&P.rho[(static_cast<size_t>(iz) * P.ny + iy) * P.nx + ix]);
+    const int m = material_of(P, rho);
+    const float tm = (m == 0) ? tot[0] : (m == 1) ? tot[1] : (m == 2) ? tot[2] : tot[3];
+    if (!(p.rng.u() * smax < rho * tm)) return true;          // virtual
+    atomicAdd(&s_events[kCRealCT], 1ull);
+    p.cell = pack_cell(ix, iy, iz);
+    float mc, mp, mq;
+    photon_mu(P, m, xs, mc, mp, mq);
+    return photon_interact<false>(P, a, s_energy, s_events, p, mc, mp, mq, e0, e1);
+}
+
+// One optical-depth flight of an EPID photon through the layer stack.
+__device__ __forceinline__ bool photon_epid_event(const Params& P, const float2* tab, Acc& a,
+                                                  unsigned long long* s_energy, unsigned long long* s_events,
+                                                  Part& p, Emit& e0, Emit& e1) {
+    const PhotonXS xs = photon_xs(tab, P, p.E);
+    float tau = -logf(p.rng.u());
+    ++a.flights;
+    for (int guard = 0; guard < 4 * kMaxLayers + 8; ++guard) {
+        const int l = static_cast<int>(p.cell);
+        float c, q, r;
+        photon_mu(P, P.lmat[l], xs, c, q, r);
+        const float mu = P.lrho[l] * (c + q + r);
+        int which;
+        const float d = epid_dist(P, p, l, which);
+        if (tau < mu * d) {
+            const float s = tau / mu;
+            p.x += s * p.u; p.y += s * p.v; p.z += s * p.w;
+            return photon_interact<true>(P, a, s_energy, s_events, p, c, q, r, e0, e1);
+        }
+        tau -= mu * d;
+        p.x += d * p.u; p.y += d * p.v; p.z += d * p.w;
+        if (which != 0) { a.esc += quanta(p.E); return false; }
+        const int nl = l + (p.w < 0.0f ? 1 : -1);
+        if (nl < 0 || nl >= P.nl) { a.esc += quanta(p.E); return false; }
+        p.cell = static_cast<uint32_t>(nl);
+    }
+    a.lost += quanta(p.E);
+    atomicAdd(&s_events[kCLost], 1ull);
+    return false;
+}
+
+// One condensed-history step of an electron or positron.
+template <bool EPID>
+__device__ __forceinline__ bool electron_event(const Params& P, const float2* tab, Acc& a,
+                                               unsigned long long* s_energy, unsigned long long* s_events,
+                                               Part& p, Emit& e0, Emit& e1, bool& move) {
+    float rho;
+    int m, layer = 0;
+    if (EPID) {
+        layer = static_cast<int>(p.cell);
+        rho = P.lrho[layer];
+        m = P.lmat[layer];
+    } else {
+        rho = __ldg(&P.rho[(static_cast<size_t>(cell_z(p.cell)) * P.ny + cell_y(p.cell)) * P.nx + cell_x(p.cell)]);
+        m = material_of(P, rho);
+    }
+    ++a.steps;
+    const MatC& mcst = P.mat[m];
+    const float T = p.E;
+    // (a) energy-loss step with the midpoint stopping power
+    float dEt = P.step_frac * T;
+    if (T - dEt < P.tstop) dEt = T - P.ecut;
+    const float Tm = T - 0.5f * dEt;
+    const float L = rho * electron_tab(tab, P, m, logf(Tm)).x;
+    const float sE = dEt / L;
+    // (b) hard-event distance against the start-of-step cross section
+    const float lnT = logf(T);
+    const float Sh = rho * (electron_tab(tab, P, m, lnT).y + mcst.brem * (lnT - P.ln_wcb));
+    const float sh = -logf(p.rng.u()) / Sh;
+    // (c) cell boundary
+    int ax;
+    const float sb = EPID ? epid_dist(P, p, layer, ax) : ct_dist(P, p, p.cell, ax);
+    float s = sE;
+    int lim = 0;
+    if (sh < s) { s = sh; lim = 1; }
+    if (sb < s) { s = sb; lim = 2; }
+    const float xh = p.rng.u(), xmu = p.rng.u(), xph = p.rng.u();
+    const float s1 = xh * s;
+    p.x += s1 * p.u; p.y += s1 * p.v; p.z += s1 * p.w;
+    const float hx = p.x, hy = p.y, hz = p.z;
+    const uint32_t hcell = p.cell;
+    // random-hinge deflection for the whole step
+    const float pc2 = T * (T + 2.0f * kMec2);
+    const float pb2 = pc2 * pc2 / ((T + kMec2) * (T + kMec2));
+    const float G = s * rho * mcst.msc / pb2;
+    float mu = 0.0f;
+    if (G > 0.0f) {
+        const float A = wentzel_A(G);
+        mu = (A < 0.0f) ? xmu : A * xmu / (1.0f - xmu + A);
+    }
+    float sp, cp;
+    sincospif(2.0f * xph, &sp, &cp);
+    rotate_dir(p.u, p.v, p.w, 1.0f - 2.0f * mu, cp, sp);
+    float s2 = s - s1;
+    int ax2;
+    const float sb2 = EPID ? epid_dist(P, p, layer, ax2) : ct_dist(P, p, p.cell, ax2);
+    bool crossed = false;
+    if (s2 >= sb2) { s2 = sb2; crossed = true; }
+    p.x += s2 * p.u; p.y += s2 * p.v; p.z += s2 * p.w;
+    const float dE = dEt * ((s1 + s2) / sE);
+    const float Tn = T - dE;
+    if (Tn <= P.tstop) {
+        deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, dE + Tn);
+        if (p.flags & kPositron) {
+            p.x = hx; p.y = hy; p.z = hz; p.cell = hcell;
+            annihilate<EPID>(P, s_events, p, e0);
+        }
+        return false;
+    }
+    deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, dE);
+    p.E = Tn;
+    if (crossed) {
+        if (EPID) {
+            if (ax2 != 0) { a.esc += quanta(p.E + rest_extra(p.flags)); return false; }
+            const int nl = layer + (p.w < 0.0f ? 1 : -1);
+            if (nl < 0 || nl >= P.nl) { a.esc += quanta(p.E + rest_extra(p.flags)); return false; }
+            p.cell = static_cast<uint32_t>(nl);
+        } else {
+            int ix = cell_x(p.cell), iy = cell_y(p.cell), iz = cell_z(p.cell);
+            const float dirc = (ax2 == 0) ? p.u : (ax2 == 1) ? p.v : p.w;
+            const int stp = (dirc > 0.0f) ? 1 : -1;
+            if (ax2 == 0) ix += stp; else if (ax2 == 1) iy += stp; else iz += stp;
+            if (ix < 0 || ix >= P.nx || iy < 0 || iy >= P.ny || iz < 0 || iz >= P.nz) {
+                move = transfer_to_epid(P, p, a, s_events, false);
+                return false;
+            }
+            p.cell = pack_cell(ix, iy, iz);
+        }
+        return true;
+    }
+    if (lim != 1) return true;
+    const float lnTn = logf(Tn);
+    const float snm = rho * electron_tab(tab, P, m, lnTn).y;
+    const float snb = rho * mcst.brem * (lnTn - P.ln_wcb);
+    if (!(p.rng.u() * Sh < snm + snb)) return true;             // delta event
+    if (p.rng.u() * (snm + snb) < snm) {
+        atomicAdd(&s_events[kCMoller], 1ull);
+        const float eps = sample_moller(p.rng, Tn, P.wcc);
+        float sph, cph;
+        sincospif(2.0f * p.rng.u(), &sph, &cph);
+        const float W = eps * Tn, Tp = Tn - W;
+        const float cs = sqrtf(W * (Tn + 2.0f * kMec2) / (Tn * (W + 2.0f * kMec2)));
+        const float cpr = sqrtf(Tp * (Tn + 2.0f * kMec2) / (Tn * (Tp + 2.0f * kMec2)));
+        float su = p.u, sv = p.v, sw = p.w;
+        rotate_dir(su, sv, sw, cs, cph, sph);
+        rotate_dir(p.u, p.v, p.w, cpr, -cph, -sph);
+        charged<EPID>(P, a, s_energy, s_events, p, e0, W, su, sv, sw, 0u, false);
+        p.E = Tp;
+    } else {
+        atomicAdd(&s_events[kCBrem], 1ull);
+        const float k = P.wcb * expf(p.rng.u() * logf(Tn / P.wcb));
+        e0.dest = EPID ? kPhotonEPID : kPhotonCT;
+        e0.E = k; e0.u = p.u; e0.v = p.v; e0.w = p.w;
+        e0.ord = child_ordinal(p.rng.ord, p.rng.d, 0u);
+        e0.flags = kCollided;
+        atomicAdd(&s_events[kCPhotons2], 1ull);
+        p.E = Tn - k;
+    }
+    if (p.E <= P.tstop) {
+        deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, p.E);
+        if (p.flags & kPositron) annihilate<EPID>(P, s_events, p, e1);
+        return false;
+    }
+    return true;
+}
+
+// Writes an emission record; a count-2 record (annihilation) becomes two
+// back-to-back photons with the ordinals of slots 0 and 1.
+__device__ __forceinline__ void flush_emission(const Params& P, const Emit& e, const Part& parent, int own_type,
+                                               uint32_t own_in) {
+    const bool pairrec = (e.dest >= 0) && (e.flags & 0x80000000u);
+    const uint32_t n = (e.dest >= 0) ? (pairrec ? 2u : 1u) : 0u;
+#pragma unroll
+    for (int t = 0; t < kNumBanks; ++t) {
+        const bool want = (e.dest == t);
+        const unsigned m = __ballot_sync(kFull, want);
+        if (m == 0u) continue;
+        // warp prefix sum of the per-lane counts
+        uint32_t cnt = want ? n : 0u, incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane_id() >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        const uint32_t par = (t == own_type) ? (own_in ^ 1u) : P.ctl->cur[t];
+        uint32_t base = 0;
+        if (lane_id() == 0) base = atomicAdd(&P.ctl->count[t][par], total);
+        base = __shfl_sync(kFull, base, 0);
+        if (!want) continue;
+        const uint32_t first = base + incl - cnt;
+        const BankPtr b = P.bank[t][par];
+        for (uint32_t k = 0; k < n; ++k) {
+            const uint32_t slot = first + k;
+            const float sg = (k == 0u) ? 1.0f : -1.0f;
+            const uint32_t ord = pairrec ? child_ordinal(e.ord, (e.flags >> 2) & 0x1fffffffu, k) : e.ord;
+            const uint32_t fl = pairrec ? kCollided : e.flags;
+            if (slot < P.cap) {
+                b.x[slot] = parent.x; b.y[slot] = parent.y; b.z[slot] = parent.z;
+                b.u[slot] = sg * e.u; b.v[slot] = sg * e.v; b.w[slot] = sg * e.w;
+                b.E[slot] = e.E;
+                b.hist[slot] = parent.hist;
+                b.ord[slot] = ord;
+                b.draws[slot] = 0u;
+                b.cell[slot] = parent.cell;
+                b.flags[slot] = fl;
+            } else {
+                atomicOr(&P.ctl->error, kErrOverflow);
+                atomicAdd(&P.energy[kELost], quanta(e.E + rest_extra(fl)));
+            }
+        }
+    }
+}
+
+}  // namespace
+
+// Samples the primary of run-local history `idx` into p (patient frame, at the
+// CT entry point) and returns whether it enters the CT; otherwise `move`
+// tells whether it reached the EPID face.
+__device__ __forceinline__ bool start_primary(const Params& P, uint32_t idx, Part& p, Acc& a,
+                                              unsigned long long* s_events, bool& move) {
+    p.hist = idx;
+    p.cell = 0u;
+    p.flags = 0u;
+    p.rng.setup(P.seed, P.hist_base + idx, 0u, 0u);
+    const double xi = static_cast<double>(p.rng.u());
+    int lo = 0, hi = P.n_rect - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (xi < __ldg(&P.cdf[mid])) hi = mid; else lo = mid + 1;
+    }
+    const float4 r = __ldg(&P.rect[lo]);
+    const float X = r.x + (r.y - r.x) * p.rng.u();
+    const float Y = r.z + (r.w - r.z) * p.rng.u();
+    p.E = (P.mono_e > 0.0f) ? P.mono_e : sample_spectrum(p.rng, P.e_max, P.pcut);
+    a.src += quanta(p.E);
+    const float nb = sqrtf(X * X + Y * Y + P.sad * P.sad);
+    const float bu = X / nb, bv = Y / nb, bw = -P.sad / nb;
+    p.x = P.iso[0] + P.sad * P.ez[0];
+    p.y = P.iso[1] + P.sad * P.ez[1];
+    p.z = P.iso[2] + P.sad * P.ez[2];
+    p.u = bu * P.ex[0] + bv * P.ey[0] + bw * P.ez[0];
+    p.v = bu * P.ex[1] + bv * P.ey[1] + bw * P.ez[1];
+    p.w = bu * P.ex[2] + bv * P.ey[2] + bw * P.ez[2];
+    // slab test against the CT box
+    const float lo3[3] = {P.ox, P.oy, P.oz};
+    const float hi3[3] = {P.ox + P.nx * P.vx, P.oy + P.ny * P.vy, P.oz + P.nz * P.vz};
+    const float x3[3] = {p.x, p.y, p.z}, d3[3] = {p.u, p.v, p.w};
+    float t0 = -INFINITY, t1 = INFINITY;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (d3[k] != 0.0f) {
+            float ta = (lo3[k] - x3[k]) / d3[k], tb = (hi3[k] - x3[k]) / d3[k];
+            if (ta > tb) { const float t = ta; ta = tb; tb = t; }
+            t0 = fmaxf(t0, ta);
+            t1 = fminf(t1, tb);
+        } else if (x3[k] < lo3[k] || x3[k] > hi3[k]) {
+            t0 = INFINITY;
+        }
+    }
+    if (t0 < t1 && t1 > 0.0f) {
+        const float t = fmaxf(t0, 0.0f);
+        p.x += t * p.u; p.y += t * p.v; p.z += t * p.w;
+        return true;
+    }
+    move = transfer_to_epid(P, p, a, s_events, true);
+    return false;
+}
+
+// The persistent transport kernel for one event type.
+template <int TYPE>
+__global__ void __launch_bounds__(256) k_transport(const Params P) {
+    constexpr bool kPhoton = (TYPE == kPhotonCT || TYPE == kPhotonEPID);
+    constexpr bool kEpid = (TYPE == kPhotonEPID || TYPE == kElectronEPID);
+    constexpr int kTabN = kPhoton ? kPhotonNodes : kNumMat * kElectronNodes;
+    constexpr int kMoveTo = kPhoton ? kPhotonEPID : kElectronEPID;
+    extern __shared__ float2 s_tab[];
+    __shared__ unsigned long long s_energy[kNumEnergy];
+    __shared__ unsigned long long s_events[kNumEvents];
+
+    const float2* gtab = kPhoton ? P.ptab : P.etab;
+    for (int i = threadIdx.x; i < kTabN; i += blockDim.x) s_tab[i] = __ldg(&gtab[i]);
+    for (int i = threadIdx.x; i < kNumEnergy; i += blockDim.x) s_energy[i] = 0ull;
+    for (int i = threadIdx.x; i < kNumEvents; i += blockDim.x) s_events[i] = 0ull;
+    __syncthreads();
+
+    const uint32_t in = P.ctl->cur[TYPE];
+    const BankPtr bin = P.bank[TYPE][in];
+    // a recorded overflow can leave the count above the capacity: never read past the bank
+    const uint32_t n_in = min(P.ctl->count[TYPE][in], P.cap);
+    const unsigned long long prim_limit = P.ctl->prim_limit;
+    const bool may_flush = P.ctl->allow_flush != 0u;
+    const uint32_t move_par = kEpid ? 0u : P.ctl->cur[kMoveTo];
+
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0u, 0u};
+    Part p;
+    bool alive = false;
+    bool in_open = true;
+    bool src_open = (TYPE == kPhotonCT);
+    int steps_here = 0;
+
+    for (;;) {
+        bool move = false;
+        // refill dead lanes from the input bank
+        if (in_open && __any_sync(kFull, !alive)) {
+            const bool need = !alive;
+            const uint32_t slot = warp_reserve(need, &P.ctl->head[TYPE]);
+            const bool got = need && slot < n_in;
+            if (got) { load_part(bin, slot, p, P); alive = true; steps_here = 0; }
+            if (__any_sync(kFull, need && !got)) in_open = false;
+        }
+        // then start new histories (photons in the CT only)
+        if (TYPE == kPhotonCT && src_open && __any_sync(kFull, !alive)) {
+            const bool need = !alive;
+            const unsigned m = __ballot_sync(kFull, need);
+            const int leader = __ffs(m) - 1;
+            unsigned long long base = 0ull;
+            if (lane_id() == leader) base = atomicAdd(&P.ctl->next_prim, static_cast<unsigned long long>(__popc(m)));
+            base = __shfl_sync(kFull, base, leader);
+            const unsigned long long idx = base + __popc(m & lanemask_lt());
+            if (need && idx < prim_limit) {
+                alive = start_primary(P, static_cast<uint32_t>(idx), p, acc, s_events, move);
+                steps_here = 0;
+            }
+            if (base + __popc(m) >= prim_limit) src_open = false;
+            // keep the electron bank from filling: stop admitting new histories
+            // (one lane reads the live fill count so the decision is warp-uniform)
+            uint32_t fill = 0u;
+            if (lane_id() == 0)
+                fill = *reinterpret_cast<volatile uint32_t*>(&P.ctl->count[kElectronCT][P.ctl->cur[kElectronCT]]);
+            fill = __shfl_sync(kFull, fill, 0);
+            if (fill > P.cap / 2u) src_open = false;
+        }
+        flush_self(P, move, kMoveTo, move_par, p);
+        move = false;
+        const unsigned live = __ballot_sync(kFull, alive);
+        if (live == 0u) {
+            if (!in_open && !src_open) break;
+            continue;
+        }
+        if (may_flush && !in_open && !src_open && __popc(live) <= P.flush_lanes) {
+            flush_self(P, alive, TYPE, in ^ 1u, p);
+            alive = false;
+            break;
+        }
+        Emit e0, e1;
+        emit_none(e0);
+        emit_none(e1);
+        if (alive) {
+            bool keep;
+            if (TYPE == kPhotonCT) keep = photon_ct_event(P, s_tab, acc, s_energy, s_events, p, e0, e1, move);
+            else if (TYPE == kPhotonEPID) keep = photon_epid_event(P, s_tab, acc, s_energy, s_events, p, e0, e1);
+            else keep = electron_event<kEpid>(P, s_tab, acc, s_energy, s_events, p, e0, e1, move);
+            if (keep && ++steps_here > P.max_steps) {
+                acc.lost += quanta(p.E + rest_extra(p.flags));
+                atomicAdd(&s_events[kCLost], 1ull);
+                keep = false;
+            }
+            alive = keep;
+        }
+        flush_emission(P, e0, p, TYPE, in);
+        flush_emission(P, e1, p, TYPE, in);
+        if (!kEpid) flush_self(P, move, kMoveTo, move_par, p);
+    }
+
+    acc_flush(P, acc, s_energy, s_events, kPhoton ? (kEpid ? kCFlightsEPID : kCFlightsCT) : kCFlightsCT,
+              kEpid ? kCEStepsEPID : kCEStepsCT);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kNumEnergy; i += blockDim.x)
+        if (s_energy[i]) atomicAdd(&P.energy[i], s_energy[i]);
+    for (int i = threadIdx.x; i < kNumEvents; i += blockDim.x)
+        if (s_events[i]) atomicAdd(&P.events[i], s_events[i]);
+}
+
+
+// Closes a consumer pass of bank type t: the drained input parity is emptied
+// and the carry parity becomes the next input.
+__global__ void k_swap(Ctl* c, int t) {
+    const uint32_t in = c->cur[t];
+    c->count[t][in] = 0u;
+    c->head[t] = 0u;
+    c->cur[t] = in ^ 1u;
+    if (t == kPhotonCT && c->next_prim > c->prim_limit) c->next_prim = c->prim_limit;
+}
+
+// Opens a wave: admits up to `per_wave` more histories.
+__global__ void k_wave_begin(Ctl* c, unsigned long long per_wave) {
+    unsigned long long lim = c->next_prim + per_wave;
+    if (lim > c->n_total) lim = c->n_total;
+    c->prim_limit = lim;
+    c->allow_flush = (lim < c->n_total) ? 1u : 0u;
+}
+
+// ----------------------------------------------------------- launchers ---
+
+size_t transport_smem(int type) {
+    const bool photon = (type == kPhotonCT || type == kPhotonEPID);
+    return sizeof(float2) * (photon ? kPhotonNodes : kNumMat * kElectronNodes);
+}
+
+static const void* transport_fn(int type) {
+    switch (type) {
+        case kPhotonCT: return reinterpret_cast<const void*>(&k_transport<kPhotonCT>);
+        case kElectronCT: return reinterpret_cast<const void*>(&k_transport<kElectronCT>);
+        case kPhotonEPID: return reinterpret_cast<const void*>(&k_transport<kPhotonEPID>);
+        default: return reinterpret_cast<const void*>(&k_transport<kElectronEPID>);
+    }
+}
+
+cudaError_t transport_occupancy(int type, int block, int* blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_fn(type), block,
+                                                         transport_smem(type));
+}
+
+cudaError_t launch_transport(int type, const Params& P, int grid, int block, cudaStream_t s) {
+    const size_t smem = transport_smem(type);
+    switch (type) {
+        case kPhotonCT: k_transport<kPhotonCT><<<grid, block, smem, s>>>(P); break;
+        case kElectronCT: k_transport<kElectronCT><<<grid, block, smem, s>>>(P); break;
+        case kPhotonEPID: k_transport<kPhotonEPID><<<grid, block, smem, s>>>(P); break;
+        default: k_transport<kElectronEPID><<<grid, block, smem, s>>>(P); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_swap(Ctl* c, int t, cudaStream_t s) {
+    k_swap<<<1, 1, 0, s>>>(c, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wave_begin(Ctl* c, unsigned long long per_wave, cudaStream_t s) {
+    k_wave_begin<<<1, 1, 0, s>>>(c, per_wave);
+    return cudaGetLastError();
+}
+
+}  // namespace mc

@@ -1,0 +1,220 @@
+"""GPU parity tests: the CUDA path through the C-ABI against the FP64 oracle on
+the same seeded inputs.
+
+Transport is a stochastic estimator, so parity is checked in two tiers:
+  replay       both sides use the same Philox keys and draw order, so each
+               history is the same up to single- vs double-precision rounding;
+               the images must pass a 1 %/1 mm global gamma (10 % threshold)
+               with the oracle as reference at >= 99.5 % of pixels;
+  independent  different seeds; per-pixel |D_gpu - D_orc| <= 3 sqrt(s_g^2 + s_o^2)
+               for >= 99 % of pixels above 10 % of the maximum.
+Integer and closed-form steps (Philox, the uniform stream, Eq. 1, dose
+statistics from the integer tallies) are compared exactly or to FP64 rounding.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import gpu_cases as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2510_24154_b300 import binding  # noqa: E402
+
+
+# ------------------------------------------------------------ RNG -------
+
+def test_philox_bit_exact():
+    rng = np.random.default_rng(0)
+    rows = rng.integers(0, 2 ** 32, size=(20000, 6), dtype=np.uint64).astype(np.uint32)
+    rows[0] = 0
+    rows[1] = 0xFFFFFFFF
+    got = binding.test_philox(rows)
+    lib = oracle.lib()
+    for i in range(rows.shape[0]):
+        out = (C.c_uint32 * 4)()
+        lib.orc_philox((C.c_uint32 * 4)(*rows[i, :4]), (C.c_uint32 * 2)(*rows[i, 4:]), out)
+        assert list(got[i]) == list(out)
+
+
+@pytest.mark.parametrize("seed,hist,ord_", [(0, 0, 0), (1, 12345, 7), (2 ** 40 + 3, 2 ** 33 + 5, 0xDEADBEEF)])
+def test_uniform_stream_bit_exact(seed, hist, ord_):
+    n = 67
+    g = binding.test_uniforms(seed, hist, ord_, n).astype(np.float64)
+    o = np.empty(n)
+    oracle.lib().orc_uniforms(seed, hist, ord_, n, o.ctypes.data_as(C.POINTER(C.c_double)))
+    assert np.array_equal(g, o)
+
+
+# ------------------------------------------------- closed-form steps ----
+
+def test_eq1_field_size_and_tmap_small():
+    p = G.thorax_case(scale=4, epid_scale=8)
+    sim = G.make_sim(p)
+    s, a, b = sim.field_size()
+    oa, ob = oracle.aperture_bbox(p.field)
+    assert (a, b) == pytest.approx((oa, ob), rel=1e-12)
+    assert s == pytest.approx(oracle.effective_field_size(p.field), rel=1e-12)
+    t_gpu = sim.tmap()
+    t_orc = oracle.tmap(p)
+    assert np.allclose(t_gpu, t_orc, rtol=1e-5, atol=1e-5)
+    assert t_orc.max() > 10.0
+
+
+@pytest.mark.parametrize("gantry", [0.0, 37.0, 90.0, 211.5])
+def test_tmap_gantry_angles(gantry):
+    p = G.thorax_case(scale=4, epid_scale=8, gantry=gantry)
+    sim = G.make_sim(p)
+    assert np.allclose(sim.tmap(), oracle.tmap(p), rtol=1e-5, atol=1e-5)
+
+
+def test_tmap_full_size_sampled_pixels():
+    p = G.thorax_case(scale=1, epid_scale=1)
+    sim = G.make_sim(p)
+    t_gpu = sim.tmap()
+    rng = np.random.default_rng(3)
+    iy = rng.integers(0, p.epid.npy, 600)
+    ix = rng.integers(0, p.epid.npx, 600)
+    t_orc = oracle.tmap(p, ix, iy)
+    assert np.allclose(t_gpu[iy, ix], t_orc, rtol=1e-5, atol=1e-5)
+
+
+def test_dose_stats_and_lut_from_gpu_tally():
+    """a8 and a11 on the GPU's own integer tally: dose and sigma to FP64
+    rounding, signal to float32 rounding of k(t, s) * dose."""
+    for lut in (G.W.lut_bilinear(), G.W.lut_wavy(), G.W.lut_table1()):
+        p = G.thorax_case(n=20_000, scale=4, epid_scale=8)
+        p.lut = lut
+        sim, st, tally = G.gpu_run(p)
+        d, s, u = sim.dose()
+        od, os_, ou = oracle.dose_stats(tally, st["histories"], p.epid)
+        assert np.allclose(d, od, rtol=1e-12, atol=0)
+        assert np.allclose(s, os_, rtol=1e-9, atol=1e-30)
+        assert u == pytest.approx(ou, rel=1e-9)
+        sig = sim.epid_image()
+        want = oracle.lut_k(lut, oracle.tmap(p), oracle.effective_field_size(p.field)) * od
+        assert np.allclose(sig, want, rtol=2e-6, atol=1e-30)
+
+
+# ------------------------------------------------------- transport ------
+
+def _compare_replay(p, n, gpu_seed=None):
+    sim, st, gt = G.gpu_run(p, n=n, seed=gpu_seed)
+    orc = oracle.run(p, n_histories=n)
+    ot = orc["tally"]
+    assert G.energy_closure(st) < 2e-6, st
+    assert st["counters"]["lost"] == 0 and st["error_flags"] == 0
+    e_g, e_o = gt.sum(), ot.sum()
+    gd, gs, _ = sim.dose()
+    od, os_, _ = oracle.dose_stats(ot, n, p.epid)
+    return sim, st, orc, gt, ot, (e_g, e_o), (gd, gs, od, os_)
+
+
+def test_replay_photon_only_water():
+    p = G.water_case(n=1_000_000, coupled=False)
+    sim, st, orc, gt, ot, (e_g, e_o), (gd, gs, od, os_) = _compare_replay(p, p.n_histories)
+    assert abs(e_g / e_o - 1) < 1e-4
+    for k in ("flights_ct", "real_ct", "compton", "photo", "pair", "primaries_at_epid", "uncollided_at_epid"):
+        assert st["counters"][k] == pytest.approx(orc["counters"][k], rel=1e-4), k
+    assert G.gamma_rate(od, gd, p.epid.pitch) >= 0.995
+    frac, npx_sel = G.three_sigma_fraction(gd, gs, od, os_)
+    assert frac >= 0.99 and npx_sel > 100
+
+
+def test_replay_coupled_thorax():
+    p = G.thorax_case(n=200_000, scale=4, epid_scale=8)
+    sim, st, orc, gt, ot, (e_g, e_o), (gd, gs, od, os_) = _compare_replay(p, p.n_histories)
+    assert abs(e_g / e_o - 1) < 2e-3
+    for k in ("flights_ct", "real_ct", "compton", "esteps_ct", "esteps_epid", "electrons", "moller", "brem"):
+        assert st["counters"][k] == pytest.approx(orc["counters"][k], rel=2e-3), k
+    assert G.gamma_rate(od, gd, p.epid.pitch) >= 0.995
+    frac, _ = G.three_sigma_fraction(gd, gs, od, os_)
+    assert frac >= 0.99
+
+
+@pytest.mark.parametrize("case", ["water_photon", "water_coupled", "thorax"])
+def test_independent_streams_three_sigma(case):
+    if case == "water_photon":
+        p = G.water_case(n=2_000_000, coupled=False, batches=64)
+    elif case == "water_coupled":
+        p = G.water_case(n=400_000, coupled=True, batches=64)
+    else:
+        p = G.thorax_case(n=400_000, scale=4, epid_scale=8, batches=64)
+    sim, st, gt = G.gpu_run(p, seed=p.seed + 1000)
+    orc = oracle.run(p)
+    gd, gs, _ = sim.dose()
+    od, os_, _ = oracle.dose_stats(orc["tally"], p.n_histories, p.epid)
+    frac, nsel = G.three_sigma_fraction(gd, gs, od, os_)
+    assert nsel > 200
+    assert frac >= 0.99, (frac, nsel)
+
+
+def test_full_size_geometry_replay():
+    """The full thorax CT (256x256x128 at 2 mm) and EPID (1024x768 at 0.39 mm)
+    in the default launch configuration: energy balance, replay of the
+    sensitive-layer energy and of the event counts."""
+    p = G.thorax_case(n=20_000, scale=1, epid_scale=1)
+    sim, st, gt = G.gpu_run(p)
+    orc = oracle.run(p)
+    assert G.energy_closure(st) < 2e-6
+    assert gt.sum() == pytest.approx(orc["tally"].sum(), rel=5e-3)
+    for k in ("real_ct", "compton", "electrons", "primaries_at_epid"):
+        assert st["counters"][k] == pytest.approx(orc["counters"][k], rel=2e-3), k
+
+
+# --------------------------------------------------- determinism --------
+
+def test_bitwise_reproducible_across_runs_and_launch_shapes():
+    p = G.thorax_case(n=100_000, scale=4, epid_scale=8)
+    _, st1, t1 = G.gpu_run(p)
+    _, st2, t2 = G.gpu_run(p)
+    _, st3, t3 = G.gpu_run(p, block_size=128, bank_capacity=1 << 18, primaries_per_wave=1 << 14)
+    assert np.array_equal(t1, t2) and np.array_equal(t1, t3)
+    assert st1["counters"] == st3["counters"]
+    assert st1["e_src"] == st3["e_src"] and st1["e_ct"] == st3["e_ct"]
+
+
+def test_checkpoint_resume_is_bitwise_identical():
+    p = G.thorax_case(n=60_000, scale=4, epid_scale=8)
+    sim_a = G.make_sim(p)
+    sim_a.run(60_000, p.seed)
+    whole = sim_a.tally()
+    sim_b = G.make_sim(p)
+    sim_b.run(25_000, p.seed)
+    blob = sim_b.get_state()
+    sim_c = G.make_sim(p)
+    sim_c.set_state(blob)
+    sim_c.run(35_000, p.seed)
+    assert np.array_equal(sim_c.tally(), whole)
+    assert sim_c.stats()["histories"] == 60_000
+
+
+def test_split_runs_equal_one_run():
+    p = G.water_case(n=300_000, coupled=True)
+    sim = G.make_sim(p)
+    sim.run(100_000, p.seed)
+    sim.run(200_000, p.seed)
+    _, _, t_one = G.gpu_run(p)
+    assert np.array_equal(sim.tally().astype(np.float64) / G.QUANTA_PER_MEV, t_one)
+
+
+def test_input_errors_are_reported():
+    p = G.water_case(n=10)
+    from paper_2510_24154_b300.binding import MCError, Simulator
+    sim = Simulator(p.physics)
+    with pytest.raises(MCError):
+        sim.run(10, 0)                       # no geometry / field yet
+    sim.init_geometry(p.phantom, p.epid)
+    bad = G.W.open_field(10, 10)
+    bad.mu = np.array([0.0])
+    with pytest.raises(MCError):
+        sim.set_field(bad)
+    closed = G.W.open_field(10, 10)
+    closed.sid = 60.0                         # detector inside the CT
+    with pytest.raises(MCError):
+        sim.set_field(closed)
