@@ -726,14 +726,49 @@ static void electron(o_ctx* c, o_part* p) {
         if (sh < s) { s = sh; lim = 1; }
         if (sb < s) { s = sb; lim = 2; }
         double xh = rng_u(&p->rng), xmu = rng_u(&p->rng), xph = rng_u(&p->rng);
+        /* multiple-scattering deflection for the whole step */
+        double G = s * rho * orc_lambda1_inv(m, T);
+        double A = orc_wentzel_A(G);
+        double mu = (G > 0.0) ? sample_ms_mu(A, xmu) : 0.0;
+        if (lim == 2) {
+            /* Boundary-limited step: straight to the face, energy deposited at the
+             * segment midpoint, the face crossed, then the deflection applied.
+             * (A random hinge here would leave the particle just short of the
+             * face after a small deflection, and the next, ever-shorter steps
+             * would end where rounding decides the crossing.) */
+            double mid[3], hc[3] = {p->cell[0], p->cell[1], p->cell[2]};
+            for (int a = 0; a < 3; a++) { mid[a] = p->x[a] + 0.5 * s * p->u[a]; p->x[a] += s * p->u[a]; }
+            double dE = dEt * (s / sE);
+            double Tn = T - dE;
+            o_part here = *p;
+            if (Tn <= tstop) {
+                deposit(c, &here, mid, (int)hc[0], dE + Tn);
+                if (p->type == P_POSITRON) {
+                    p->x[0] = mid[0]; p->x[1] = mid[1]; p->x[2] = mid[2];
+                    annihilate(c, p);
+                }
+                return;
+            }
+            deposit(c, &here, mid, (int)hc[0], dE);
+            p->E = Tn;
+            if (p->zone == Z_CT) {
+                p->cell[ax] += (p->u[ax] > 0.0) ? 1 : -1;
+                int n[3] = {P->nx, P->ny, P->nz};
+                if (p->cell[ax] < 0 || p->cell[ax] >= n[ax]) { transfer_to_epid(c, p); return; }
+            } else {
+                if (ax != 0) { c->e_esc += p->E + rest_extra(p); return; }
+                int nl = layer + (p->u[2] < 0.0 ? 1 : -1);
+                if (nl < 0 || nl >= P->n_layers) { c->e_esc += p->E + rest_extra(p); return; }
+                p->cell[0] = nl;
+            }
+            rotate(p->u, 1.0 - 2.0 * mu, 2.0 * O_PI * xph);
+            continue;
+        }
+        /* random hinge: first segment, deflection, second segment */
         double s1 = xh * s;
         for (int a = 0; a < 3; a++) p->x[a] += s1 * p->u[a];
         double hinge[3] = {p->x[0], p->x[1], p->x[2]};
         int hcell[3] = {p->cell[0], p->cell[1], p->cell[2]};
-        /* random-hinge deflection for the whole step */
-        double G = s * rho * orc_lambda1_inv(m, T);
-        double A = orc_wentzel_A(G);
-        double mu = (G > 0.0) ? sample_ms_mu(A, xmu) : 0.0;
         rotate(p->u, 1.0 - 2.0 * mu, 2.0 * O_PI * xph);
         double s2 = s - s1;
         int ax2;

@@ -178,7 +178,8 @@ void make_params(const mc_ctx* c, Params& P, uint64_t seed) {
     P.ipitch = 1.0f / P.pitch;
     P.hwx = static_cast<float>(0.5 * E.npx * E.pitch_cm);
     P.hwy = static_cast<float>(0.5 * E.npy * E.pitch_cm);
-    for (int l = 0; l <= E.n_layers; ++l) P.zp[l] = static_cast<float>(c->zp[l]);
+    for (int l = 0; l <= E.n_layers; ++l) P.zp[l] = static_cast<float>(c->zp[l] - c->zp[0]);
+    P.zface = static_cast<float>(c->zp[0]);
     for (int l = 0; l < E.n_layers; ++l) {
         P.lmat[l] = E.material[l];
         P.lrho[l] = static_cast<float>(E.density[l]);

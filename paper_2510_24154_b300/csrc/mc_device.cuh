@@ -75,7 +75,8 @@ struct Params {
     // EPID (beam frame)
     int nl, sens, npx, npy;
     float pitch, ipitch, hwx, hwy;
-    float zp[kMaxLayers + 1];
+    float zp[kMaxLayers + 1];       // layer planes relative to the detector face (EPID particles keep z there)
+    float zface;                    // beam-frame Z of the detector face
     int lmat[kMaxLayers];
     float lrho[kMaxLayers];
     // source

@@ -83,10 +83,12 @@ __device__ __forceinline__ bool transfer_to_epid(const Params& P, Part& p, Acc& 
     to_beam_dir(P, p.u, p.v, p.w, bu, bv, bw);
     const float eexit = p.E + rest_extra(p.flags);
     if (bw >= 0.0f) { a.esc += quanta(eexit); return false; }
-    const float t = (P.zp[0] - bz) / bw;
+    const float t = (P.zface - bz) / bw;
     const float X = bx + t * bu, Y = by + t * bv;
     if (!(fabsf(X) < P.hwx && fabsf(Y) < P.hwy)) { a.esc += quanta(eexit); return false; }
-    p.x = X; p.y = Y; p.z = P.zp[0];
+    // inside the detector z is measured from its face, where single precision
+    // resolves the 0.29 mm phosphor to ~1e-8 cm (at Z = -50 cm it would be 4e-6 cm)
+    p.x = X; p.y = Y; p.z = 0.0f;
     p.u = bu; p.v = bv; p.w = bw;
     p.cell = 0u;
     if (is_photon && p.rng.ord == 0u) {
@@ -360,7 +362,8 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     const float sE = dEt / L;
     // (b) hard-event distance against the start-of-step cross section
     const float lnT = logf(T);
-    const float Sh = rho * (electron_tab(tab, P, m, lnT).y + mcst.brem * (lnT - P.ln_wcb));
+    // hard bremsstrahlung exists only above wcb: A ln(T / wcb) for T > wcb
+    const float Sh = rho * (electron_tab(tab, P, m, lnT).y + mcst.brem * fmaxf(lnT - P.ln_wcb, 0.0f));
     const float sh = -logf(p.rng.u()) / Sh;
     // (c) cell boundary
     int ax;
@@ -370,11 +373,7 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     if (sh < s) { s = sh; lim = 1; }
     if (sb < s) { s = sb; lim = 2; }
     const float xh = p.rng.u(), xmu = p.rng.u(), xph = p.rng.u();
-    const float s1 = xh * s;
-    p.x += s1 * p.u; p.y += s1 * p.v; p.z += s1 * p.w;
-    const float hx = p.x, hy = p.y, hz = p.z;
-    const uint32_t hcell = p.cell;
-    // random-hinge deflection for the whole step
+    // multiple-scattering deflection for the whole step
     const float pc2 = T * (T + 2.0f * kMec2);
     const float pb2 = pc2 * pc2 / ((T + kMec2) * (T + kMec2));
     const float G = s * rho * mcst.msc / pb2;
@@ -385,6 +384,50 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     }
     float sp, cp;
     sincospif(2.0f * xph, &sp, &cp);
+    if (lim == 2) {
+        // Boundary-limited step: straight to the face, deposit at the segment
+        // midpoint, cross, then deflect.  (A hinge here would stop the particle
+        // just short of the face and start a run of ever-shorter steps whose
+        // crossing is decided by rounding.)
+        const float mx = p.x + 0.5f * s * p.u, my = p.y + 0.5f * s * p.v, mz = p.z + 0.5f * s * p.w;
+        const uint32_t c0 = p.cell;
+        p.x += s * p.u; p.y += s * p.v; p.z += s * p.w;
+        const float dE = dEt * (s / sE);
+        const float Tn = T - dE;
+        if (Tn <= P.tstop) {
+            deposit<EPID>(P, a, s_energy, c0, mx, my, p.hist, dE + Tn);
+            if (p.flags & kPositron) {
+                p.x = mx; p.y = my; p.z = mz;
+                annihilate<EPID>(P, s_events, p, e0);
+            }
+            return false;
+        }
+        deposit<EPID>(P, a, s_energy, c0, mx, my, p.hist, dE);
+        p.E = Tn;
+        if (EPID) {
+            if (ax != 0) { a.esc += quanta(p.E + rest_extra(p.flags)); return false; }
+            const int nl = layer + (p.w < 0.0f ? 1 : -1);
+            if (nl < 0 || nl >= P.nl) { a.esc += quanta(p.E + rest_extra(p.flags)); return false; }
+            p.cell = static_cast<uint32_t>(nl);
+        } else {
+            int ix = cell_x(p.cell), iy = cell_y(p.cell), iz = cell_z(p.cell);
+            const float dirc = (ax == 0) ? p.u : (ax == 1) ? p.v : p.w;
+            const int stp = (dirc > 0.0f) ? 1 : -1;
+            if (ax == 0) ix += stp; else if (ax == 1) iy += stp; else iz += stp;
+            if (ix < 0 || ix >= P.nx || iy < 0 || iy >= P.ny || iz < 0 || iz >= P.nz) {
+                move = transfer_to_epid(P, p, a, s_events, false);
+                return false;
+            }
+            p.cell = pack_cell(ix, iy, iz);
+        }
+        rotate_dir(p.u, p.v, p.w, 1.0f - 2.0f * mu, cp, sp);
+        return true;
+    }
+    // random hinge: first segment, deflection, second segment
+    const float s1 = xh * s;
+    p.x += s1 * p.u; p.y += s1 * p.v; p.z += s1 * p.w;
+    const float hx = p.x, hy = p.y, hz = p.z;
+    const uint32_t hcell = p.cell;
     rotate_dir(p.u, p.v, p.w, 1.0f - 2.0f * mu, cp, sp);
     float s2 = s - s1;
     int ax2;
@@ -426,7 +469,7 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     if (lim != 1) return true;
     const float lnTn = logf(Tn);
     const float snm = rho * electron_tab(tab, P, m, lnTn).y;
-    const float snb = rho * mcst.brem * (lnTn - P.ln_wcb);
+    const float snb = rho * mcst.brem * fmaxf(lnTn - P.ln_wcb, 0.0f);
     if (!(p.rng.u() * Sh < snm + snb)) return true;             // delta event
     if (p.rng.u() * (snm + snb) < snm) {
         atomicAdd(&s_events[kCMoller], 1ull);
