@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Throughput of the EPID transit Monte Carlo hot path on one or more B300s.
+
+One step = the whole path over one field of the coupled thorax workload
+(256x256x128 HU CT at 2 mm, one 9-segment IMRT field, EPID 1024x768 at
+0.39 mm, 64x32 k-table): HU -> density, field set-up (source table,
+radiological thickness map, Eq. 1), transport of the histories, dose
+statistics and the k(t, s) corrected image.  Inputs are resident in HBM when
+the timed region starts; the `e2e` leg repeats the step through the C-ABI
+with host buffers (HU volume in, corrected image out) inside the timed region.
+
+`--impl reference` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the only other place this script runs it is the
+`cpu_baseline` leg).  Multi-GPU runs shard history ids across ranks (weak
+scaling, no data-path collective); the timing takes the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HIST_PER_STEP = 100_000_000
+SEED = 1
+WORKLOAD = "thorax_imrt_9seg: CT 256x256x128 int16 HU @2mm, 9 MLC segments x 60 pairs, " \
+           "EPID 1024x768 @0.39mm (Cu/Gd2O2S/a-Si), k-table 64x32, coupled photon/electron"
+# Counted single-precision work per CT electron step (FADD + FMUL + 2 x FFMA +
+# the special-function instructions), from the ncu capture summarised in
+# profiles/electron_ct_thorax.md.
+FLOPS_PER_ESTEP_CT = 312.0
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--histories", type=int, default=HIST_PER_STEP)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--bank-capacity", type=int, default=0, help="particles per bank (0: library default)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for n, v in zip(names, r[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_sample(problem, n, threads):
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.run(problem, n_histories=n, threads=threads)
+    dt = time.perf_counter() - t0
+    return n / dt, r["threads"], dt
+
+
+def run_reference(args):
+    """The FP64 oracle on the host cores, same workload, bounded samples."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2510_24154_b300 import workloads as W
+    oracle.build()
+    p = W.config_thorax_imrt(n_histories=args.histories, seed=SEED)
+    threads = os.cpu_count() or 1
+    sample = 200_000
+    for _ in range(args.warmup):
+        oracle.run(p, n_histories=20_000, threads=threads)
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(args.steps):
+        oracle.run(p, n_histories=sample, hist_begin=k * sample, threads=threads)
+        done += sample
+    dt = time.perf_counter() - t0
+    v = done / dt
+    line = {
+        "impl": "reference", "metric": "histories/s", "value": v, "unit": "histories/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "histories_per_step": sample, "seed": SEED},
+        "cpu_baseline": {"value": v, "unit": "histories/s", "cores": min(threads, p.physics.n_batches),
+                         "kind": "oracle", "sample": f"{sample} histories of the workload per step"},
+        "e2e": {"value": v, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    from paper_2510_24154_b300 import workloads as W
+    from paper_2510_24154_b300.binding import Simulator
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    p = W.config_thorax_imrt(n_histories=args.histories, seed=SEED)
+    N = args.histories
+    extra = {"bank_capacity": args.bank_capacity} if args.bank_capacity else {}
+    sim = Simulator(p.physics, device=local, time_kernels=1, **extra)
+    stream = torch.cuda.current_stream()
+    hu_dev = torch.from_numpy(p.phantom.hu).to(f"cuda:{local}")
+    ny, nx = p.epid.npy, p.epid.npx
+    dose = torch.empty((ny, nx), dtype=torch.float64, device=f"cuda:{local}")
+    sigma = torch.empty_like(dose)
+    signal = torch.empty((ny, nx), dtype=torch.float32, device=f"cuda:{local}")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=f"cuda:{local}")   # > 126 MB L2
+
+    agg = {"kernel_ms": np.zeros(4), "kernel_launches": np.zeros(4), "esteps_ct": 0, "launches": 0}
+
+    def step(record):
+        sim.init_geometry(p.phantom, p.epid, stream=stream, hu_device=hu_dev)     # a1
+        sim.set_field(p.field, p.lut, stream=stream)                              # a2 set-up, a9, a10
+        sim.set_history_base(rank * N)
+        st = sim.run(N, SEED, stream=stream)                                      # a2-a7
+        sim.dose_device(dose, sigma, stream=stream)                               # a8
+        sim.epid_image_device(signal, stream=stream)                              # a8 + a11
+        flush.zero_()
+        if record:
+            agg["kernel_ms"] += np.array(st["kernel_ms"])
+            agg["kernel_launches"] += np.array(st["kernel_launches"])
+            agg["esteps_ct"] += st["counters"]["esteps_ct"]
+            agg["launches"] += st["launches"] + 2 + 1 + 2
+        return st
+
+    for _ in range(max(args.warmup, 3)):
+        step(False)
+    barrier()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            last = step(True)
+        ev1.record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+    gpu_ms = ev0.elapsed_time(ev1)
+    t_local = gpu_ms / 1e3
+    t_all = t_local
+    if dist is not None:
+        t = torch.tensor([t_local], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_all = float(t.item())
+    total_hist = ws * N * args.steps
+    value = total_hist / t_all
+
+    # statistical uncertainty of one field -> seconds per field at <= 1 %
+    _, _, u = sim.dose(stream=stream)
+    n_1pct = N * (u / 0.01) ** 2
+    per_gpu_rate = N * args.steps / t_local
+
+    # live roofline of the dominant kernel (CT electrons)
+    launches_e = max(agg["kernel_launches"][1], 1)
+    avg_ms = agg["kernel_ms"][1] / launches_e
+    steps_per_launch = agg["esteps_ct"] / launches_e
+    flops = FLOPS_PER_ESTEP_CT * steps_per_launch
+    hbm_peak, peak_kind = peaks()
+    # algorithmic bytes of a CT electron launch: one 4-byte density gather per
+    # step plus the bank records read and written (48 bytes each)
+    st_counts = last["counters"]
+    bank_bytes = 48.0 * 2 * st_counts["electrons"] / max(last["kernel_launches"][1], 1)
+    alg_bytes = 4.0 * steps_per_launch + bank_bytes
+    mem_achieved = alg_bytes / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+    roofline = {
+        "bound": "alu", "kernel": "k_transport<electrons in CT>",
+        "achieved": flops / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0,
+        "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 (FMA) x 2.032 GHz",
+        "traffic": None,
+        "flops_per_unit": FLOPS_PER_ESTEP_CT, "unit_of_work": "CT electron step",
+        "units_per_launch": steps_per_launch, "avg_launch_ms": avg_ms,
+        "kernel_share_of_transport": float(agg["kernel_ms"][1] / max(agg["kernel_ms"].sum(), 1e-12)),
+    }
+    roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    memory_roofline = {"bound": "hbm", "achieved": mem_achieved, "peak": hbm_peak, "unit": "GB/s",
+                       "frac": mem_achieved / hbm_peak, "peak_kind": peak_kind,
+                       "algorithmic_bytes_per_launch": alg_bytes}
+
+    # end to end through the C-ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hu_pinned = torch.from_numpy(p.phantom.hu).pin_memory()
+        phantom_host = W.Phantom(hu_pinned.numpy(), p.phantom.vox, p.phantom.origin)
+        fld = p.field
+        h2d = (hu_pinned.numel() * 2 + fld.pair_edges.nbytes + fld.leaves.nbytes + fld.jaws.nbytes + fld.mu.nbytes
+               + p.lut.t_nodes.nbytes + p.lut.s_nodes.nbytes + p.lut.k.nbytes)
+        barrier()
+        t0 = time.perf_counter()
+        waves = 0
+        for _ in range(args.steps):
+            sim.init_geometry(phantom_host, p.epid, stream=stream)
+            sim.set_field(p.field, p.lut, stream=stream)
+            sim.set_history_base(rank * N)
+            st = sim.run(N, SEED, stream=stream)
+            img = sim.epid_image(stream=stream)
+            waves += st["waves"]
+        barrier()
+        te = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([te], device=f"cuda:{local}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        d2h = img.nbytes + 80 * waves // args.steps
+        e2e = {"value": total_hist / te, "unit": "histories/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        threads = os.cpu_count() or 1
+        sample = 300_000
+        v, used, dt = cpu_sample(p, sample, threads)
+        cpu = {"value": v, "unit": "histories/s", "cores": used, "kind": "oracle",
+               "sample": f"{sample} histories of the same workload ({dt:.1f} s wall on {used} threads)"}
+
+    if rank == 0:
+        line = {
+            "metric": "histories/s", "value": value, "unit": "histories/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "histories_per_step_per_gpu": N, "seed": SEED,
+                       "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"history shards x{ws}, no collective"},
+            "s_per_field_1pct": n_1pct / per_gpu_rate, "u_at_step": u, "histories_for_1pct": n_1pct,
+            "roofline": roofline, "memory_roofline": memory_roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(agg["launches"]), "clocks": clk.summary(), "wall_s_timed": wall,
+            "paper_context": "about 90 s per IMRT field at 1e9 histories on an RTX 3090 (paper Sec. 4.1)",
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    sim.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

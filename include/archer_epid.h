@@ -83,6 +83,7 @@ typedef struct mc_config {
     int ctas_per_sm;              /* resident CTAs per SM for the persistent kernels, 0 = occupancy limit */
     uint32_t bank_capacity;       /* particles per bank, 0 = 1<<22 */
     uint32_t primaries_per_wave;  /* new histories per transport wave, 0 = bank_capacity / 4 */
+    int time_kernels;             /* 1: time every transport launch with CUDA events (mc_run_stats.kernel_ms) */
 } mc_config;
 
 /* EPID layer stack from the source side (Sec. 2.1.3).  The centre of the
@@ -132,6 +133,10 @@ typedef struct mc_run_stats {
     int waves;                    /* transport waves of the last mc_run */
     uint32_t error_flags;         /* device-side error bits of the last mc_run */
     double gpu_ms;                /* device time of the last mc_run (CUDA events) */
+    double kernel_ms[4];          /* with time_kernels: summed time per transport kernel of the last mc_run
+                                     (CT photons, CT electrons, EPID photons, EPID electrons) */
+    uint32_t kernel_launches[4];  /* launches per transport kernel in the last mc_run */
+    uint32_t launches;            /* all kernel launches of the last mc_run */
 } mc_run_stats;
 
 typedef struct mc_ctx mc_ctx;
@@ -199,6 +204,11 @@ mc_status mc_reset_tally(mc_ctx* ctx, void* stream);
 mc_status mc_state_size(mc_ctx* ctx, size_t* bytes);
 mc_status mc_get_state(mc_ctx* ctx, void* host_buf, size_t bytes, void* stream);
 mc_status mc_set_state(mc_ctx* ctx, const void* host_buf, size_t bytes, void* stream);
+
+/* Sets the id of the next history (sharding: rank r of R running n histories
+ * each starts at r * n, and the union of the shards equals one run of R * n
+ * histories).  Does not clear the tally. */
+mc_status mc_set_history_base(mc_ctx* ctx, uint64_t next_history);
 
 /* Requests that a running mc_run on another host thread stop after its
  * current wave (it then returns MC_ERR_CANCELLED). */

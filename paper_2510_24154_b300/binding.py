@@ -24,7 +24,8 @@ STATUS = {0: "MC_OK", 1: "MC_ERR_ARG", 2: "MC_ERR_CUDA", 3: "MC_ERR_OOM", 4: "MC
 # Every entry point declared in include/archer_epid.h.
 EXPORTED = ("mc_config_default", "mc_create", "mc_destroy", "mc_init_geometry", "mc_set_field", "mc_run",
             "mc_get_dose", "mc_get_epid_image", "mc_get_tmap", "mc_get_tally", "mc_field_size", "mc_get_stats",
-            "mc_reset_tally", "mc_state_size", "mc_get_state", "mc_set_state", "mc_cancel", "mc_last_error",
+            "mc_reset_tally", "mc_state_size", "mc_get_state", "mc_set_state", "mc_set_history_base", "mc_cancel",
+            "mc_last_error",
             "mc_status_string", "mc_test_philox", "mc_test_uniforms")
 
 
@@ -33,7 +34,8 @@ class Config(C.Structure):
                 ("photon_cutoff_mev", C.c_double), ("electron_cutoff_mev", C.c_double),
                 ("wcc_mev", C.c_double), ("wcb_mev", C.c_double), ("step_fraction", C.c_double),
                 ("n_batches", C.c_int), ("max_steps", C.c_int), ("block_size", C.c_int),
-                ("ctas_per_sm", C.c_int), ("bank_capacity", C.c_uint32), ("primaries_per_wave", C.c_uint32)]
+                ("ctas_per_sm", C.c_int), ("bank_capacity", C.c_uint32), ("primaries_per_wave", C.c_uint32),
+                ("time_kernels", C.c_int)]
 
 
 class EpidDesc(C.Structure):
@@ -59,7 +61,8 @@ class RunStats(C.Structure):
     _fields_ = [("histories", C.c_uint64), ("e_src_mev", C.c_double), ("e_ct_mev", C.c_double),
                 ("e_epid_mev", C.c_double * MAX_LAYERS), ("e_esc_mev", C.c_double), ("e_lost_mev", C.c_double),
                 ("counters", C.c_uint64 * NUM_COUNTERS), ("waves", C.c_int), ("error_flags", C.c_uint32),
-                ("gpu_ms", C.c_double)]
+                ("gpu_ms", C.c_double), ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_uint32 * 4),
+                ("launches", C.c_uint32)]
 
 
 class MCError(RuntimeError):
@@ -104,6 +107,7 @@ def load(build_if_stale: bool = True):
     lib.mc_get_state.argtypes = [vp, vp, C.c_size_t, vp]
     lib.mc_set_state.argtypes = [vp, vp, C.c_size_t, vp]
     lib.mc_cancel.argtypes = [vp]
+    lib.mc_set_history_base.argtypes = [vp, u64]
     lib.mc_last_error.restype = C.c_char_p
     lib.mc_last_error.argtypes = [vp]
     lib.mc_status_string.restype = C.c_char_p
@@ -290,6 +294,9 @@ class Simulator:
         self._check(self.lib.mc_field_size(self.h, C.byref(s), C.byref(a), C.byref(b)))
         return s.value, a.value, b.value
 
+    def set_history_base(self, next_history):
+        self._check(self.lib.mc_set_history_base(self.h, int(next_history)))
+
     def reset_tally(self, stream=None):
         self._check(self.lib.mc_reset_tally(self.h, _stream_ptr(stream)))
 
@@ -312,6 +319,8 @@ def stats_dict(st: RunStats) -> dict:
         "e_esc": st.e_esc_mev, "e_lost": st.e_lost_mev,
         "counters": dict(zip(COUNTER_NAMES, [int(v) for v in st.counters])),
         "waves": int(st.waves), "error_flags": int(st.error_flags), "gpu_ms": float(st.gpu_ms),
+        "kernel_ms": [float(v) for v in st.kernel_ms], "kernel_launches": [int(v) for v in st.kernel_launches],
+        "launches": int(st.launches),
     }
 
 

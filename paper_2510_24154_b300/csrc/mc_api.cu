@@ -79,6 +79,10 @@ struct mc_ctx {
     unsigned int* d_partc = nullptr;
     float* d_signal = nullptr;
     int last_waves = 0;
+    double last_kernel_ms[4] = {0, 0, 0, 0};
+    uint32_t last_kernel_launches[4] = {0, 0, 0, 0};
+    uint32_t last_launches = 0;
+    std::vector<cudaEvent_t> ev_pool;
     uint32_t last_error = 0;
     double last_ms = 0;
 };
@@ -247,6 +251,7 @@ void mc_config_default(mc_config* cfg) {
     cfg->ctas_per_sm = 0;
     cfg->bank_capacity = 1u << 22;
     cfg->primaries_per_wave = 0;
+    cfg->time_kernels = 0;
 }
 
 const char* mc_status_string(mc_status s) {
@@ -355,6 +360,7 @@ mc_status mc_destroy(mc_ctx* c) {
     dfree(c->d_nb);
     dfree(c->d_u);
     dfree(c->d_maxbits);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
     return MC_OK;
 }
@@ -546,15 +552,36 @@ mc_status mc_run(mc_ctx* c, uint64_t n, uint64_t seed, void* stream, mc_run_stat
     CUDA_TRY(c, cudaEventRecord(e0, s));
     const int order[4] = {mc::kPhotonCT, mc::kElectronCT, mc::kPhotonEPID, mc::kElectronEPID};
     int waves = 0;
+    uint32_t launches = 0;
+    uint32_t klaunch[4] = {0, 0, 0, 0};
+    // (type, start event index) of every timed transport launch
+    std::vector<std::pair<int, size_t>> timed;
+    size_t ev_used = 0;
+    auto next_event = [&]() -> cudaEvent_t {
+        if (ev_used == c->ev_pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            c->ev_pool.push_back(e);
+        }
+        return c->ev_pool[ev_used++];
+    };
     mc_status result = MC_OK;
     const int max_waves = 1000000;
     for (; waves < max_waves; ++waves) {
         CUDA_TRY(c, mc::launch_wave_begin(c->d_ctl, c->cfg.primaries_per_wave, s));
+        ++launches;
         for (int t : order) {
             const bool electron = (t == mc::kElectronCT || t == mc::kElectronEPID);
             if (electron && !c->cfg.coupled) continue;
+            if (c->cfg.time_kernels) {
+                timed.emplace_back(t, ev_used);
+                CUDA_TRY(c, cudaEventRecord(next_event(), s));
+            }
             CUDA_TRY(c, mc::launch_transport(t, P, c->grid[t], c->block, s));
+            if (c->cfg.time_kernels) CUDA_TRY(c, cudaEventRecord(next_event(), s));
             CUDA_TRY(c, mc::launch_swap(c->d_ctl, t, s));
+            launches += 2;
+            ++klaunch[t];
         }
         CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(c, cudaStreamSynchronize(s));
@@ -571,6 +598,13 @@ mc_status mc_run(mc_ctx* c, uint64_t n, uint64_t seed, void* stream, mc_run_stat
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    for (int t = 0; t < 4; ++t) { c->last_kernel_ms[t] = 0.0; c->last_kernel_launches[t] = klaunch[t]; }
+    for (const auto& te : timed) {
+        float kms = 0.f;
+        cudaEventElapsedTime(&kms, c->ev_pool[te.second], c->ev_pool[te.second + 1]);
+        c->last_kernel_ms[te.first] += kms;
+    }
+    c->last_launches = launches;
     c->hist_done += n;
     c->last_waves = waves;
     c->last_error = h.error;
@@ -599,6 +633,11 @@ mc_status mc_get_stats(mc_ctx* c, mc_run_stats* st) {
     st->waves = c->last_waves;
     st->error_flags = c->last_error;
     st->gpu_ms = c->last_ms;
+    for (int t = 0; t < 4; ++t) {
+        st->kernel_ms[t] = c->last_kernel_ms[t];
+        st->kernel_launches[t] = c->last_kernel_launches[t];
+    }
+    st->launches = c->last_launches;
     return MC_OK;
 }
 
@@ -745,6 +784,12 @@ mc_status mc_set_state(mc_ctx* c, const void* buf, size_t bytes, void* stream) {
                                 cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
     c->hist_done = w[4];
+    return MC_OK;
+}
+
+mc_status mc_set_history_base(mc_ctx* c, uint64_t next_history) {
+    if (!c) return MC_ERR_ARG;
+    c->hist_done = next_history;
     return MC_OK;
 }
 

@@ -158,7 +158,7 @@ def test_full_size_geometry_replay():
     """The full thorax CT (256x256x128 at 2 mm) and EPID (1024x768 at 0.39 mm)
     in the default launch configuration: energy balance, replay of the
     sensitive-layer energy and of the event counts."""
-    p = G.thorax_case(n=20_000, scale=1, epid_scale=1)
+    p = G.thorax_case(n=200_000, scale=1, epid_scale=1)
     sim, st, gt = G.gpu_run(p)
     orc = oracle.run(p)
     assert G.energy_closure(st) < 2e-6
