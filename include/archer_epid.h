@@ -214,6 +214,33 @@ mc_status mc_set_history_base(mc_ctx* ctx, uint64_t next_history);
  * current wave (it then returns MC_ERR_CANCELLED). */
 mc_status mc_cancel(mc_ctx* ctx);
 
+/* Dose statistics without any device allocation.  The paper has no
+ * counterpart: this serves callers that may not allocate device memory once
+ * they are running, such as a QA service whose framework allocator has
+ * already reserved the GPU's memory, or medical software whose rules forbid
+ * run-time allocation because it can fail or stall unpredictably.
+ *
+ * Computes what mc_get_dose computes (per-history dose in Gy, its batch
+ * standard error and the mean relative uncertainty over pixels above half the
+ * maximum) from a tally the caller holds: tally is a device array
+ * [n_batches][npy][npx] of 2^-8 eV units (as mc_get_tally writes it) for
+ * history ids 0 .. n_histories-1; pixel_mass_kg is the mass of one pixel of
+ * the sensitive layer.  dose and sigma (sigma may be NULL) are device arrays
+ * [npy][npx]; u (device, one double, may be NULL; needs sigma) receives the
+ * relative uncertainty.  The work is queued on `stream`; nothing is copied to
+ * the host and nothing is allocated or freed.
+ *
+ * Limits: at most 4,194,304 pixels (2048 x 2048) and 1024 batches; larger
+ * inputs return MC_ERR_ARG (and a message on stderr).  Its scratch is a
+ * 213,248-byte array inside the library that every GPU loading the library
+ * keeps until the process exits.  The first call on a device looks up that
+ * array's device address, so make it before capturing the stream.  All calls
+ * share the array: calls whose work overlaps on the GPU (two streams, or two
+ * host threads) race and give wrong results; serialize them.  Call it with the
+ * device that holds `tally` current. */
+mc_status mc_dose_stats_noalloc(const uint64_t* tally, int npx, int npy, int n_batches, uint64_t n_histories,
+                                double pixel_mass_kg, double* dose, double* sigma, double* u, void* stream);
+
 const char* mc_last_error(const mc_ctx* ctx);
 const char* mc_status_string(mc_status s);
 

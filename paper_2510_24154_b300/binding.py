@@ -26,7 +26,7 @@ EXPORTED = ("mc_config_default", "mc_create", "mc_destroy", "mc_init_geometry", 
             "mc_get_dose", "mc_get_epid_image", "mc_get_tmap", "mc_get_tally", "mc_field_size", "mc_get_stats",
             "mc_reset_tally", "mc_state_size", "mc_get_state", "mc_set_state", "mc_set_history_base", "mc_cancel",
             "mc_last_error",
-            "mc_status_string", "mc_test_philox", "mc_test_uniforms")
+            "mc_status_string", "mc_test_philox", "mc_test_uniforms", "mc_dose_stats_noalloc")
 
 
 class Config(C.Structure):
@@ -114,6 +114,7 @@ def load(build_if_stale: bool = True):
     lib.mc_status_string.argtypes = [i]
     lib.mc_test_philox.argtypes = [vp, vp, i, vp]
     lib.mc_test_uniforms.argtypes = [u64, u64, u32, i, vp, vp]
+    lib.mc_dose_stats_noalloc.argtypes = [vp, i, i, i, u64, d, vp, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("mc_config_default", "mc_last_error", "mc_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -344,3 +345,15 @@ def test_uniforms(seed, hist, ord_, n, stream=None):
     if st:
         raise MCError(st, "mc_test_uniforms")
     return out.cpu().numpy()
+
+
+def dose_stats_noalloc(tally, npx, npy, n_batches, n_histories, pixel_mass_kg, dose, sigma=None, u=None,
+                       stream=None):
+    """mc_dose_stats_noalloc on device tensors (tally int64 [B][npy][npx],
+    dose/sigma float64 [npy][npx], u float64 [1]); allocates nothing."""
+    lib = load()
+    st = lib.mc_dose_stats_noalloc(_ptr(tally), int(npx), int(npy), int(n_batches), int(n_histories),
+                                   float(pixel_mass_kg), _ptr(dose), _ptr(sigma) if sigma is not None else None,
+                                   _ptr(u) if u is not None else None, _stream_ptr(stream))
+    if st:
+        raise MCError(st, "mc_dose_stats_noalloc")

@@ -15,7 +15,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 LIB = PKG / "libarcher_epid.so"
-SOURCES = ["mc_api.cu", "mc_transport.cu", "mc_aux.cu", "physics_tables.cpp"]
+SOURCES = ["mc_api.cu", "mc_transport.cu", "mc_aux.cu", "mc_noalloc.cu", "physics_tables.cpp"]
 HEADERS = ["mc_device.cuh", "mc_aux.h", "physics_tables.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
