@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--bank-capacity", type=int, default=0, help="particles per bank (0: library default)")
+    ap.add_argument("--regs-variant", default="", help="CTAs/SM build per transport kernel, e.g. 3,3,3,3")
     return ap.parse_args()
 
 
@@ -183,6 +184,8 @@ def main():
     p = W.config_thorax_imrt(n_histories=args.histories, seed=SEED)
     N = args.histories
     extra = {"bank_capacity": args.bank_capacity} if args.bank_capacity else {}
+    if args.regs_variant:
+        extra["regs_variant"] = [int(v) for v in args.regs_variant.split(",")]
     sim = Simulator(p.physics, device=local, time_kernels=1, **extra)
     stream = torch.cuda.current_stream()
     hu_dev = torch.from_numpy(p.phantom.hu).to(f"cuda:{local}")
@@ -257,6 +260,9 @@ def main():
         "flops_per_unit": FLOPS_PER_ESTEP_CT, "unit_of_work": "CT electron step",
         "units_per_launch": steps_per_launch, "avg_launch_ms": avg_ms,
         "kernel_share_of_transport": float(agg["kernel_ms"][1] / max(agg["kernel_ms"].sum(), 1e-12)),
+        "transport_ms_per_step": {k: float(v / args.steps) for k, v in
+                                  zip(("photons_ct", "electrons_ct", "photons_epid", "electrons_epid"),
+                                      agg["kernel_ms"])},
     }
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
     memory_roofline = {"bound": "hbm", "achieved": mem_achieved, "peak": hbm_peak, "unit": "GB/s",

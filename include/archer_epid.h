@@ -81,9 +81,12 @@ typedef struct mc_config {
     int max_steps;                /* per-particle step cap; beyond it the energy is counted as lost */
     int block_size;               /* threads per CTA of the transport kernels (multiple of 32), 0 = 256 */
     int ctas_per_sm;              /* resident CTAs per SM for the persistent kernels, 0 = occupancy limit */
-    uint32_t bank_capacity;       /* particles per bank, 0 = 1<<22 */
+    uint32_t bank_capacity;       /* particles per bank, 0 = 1<<23 */
     uint32_t primaries_per_wave;  /* new histories per transport wave, 0 = bank_capacity / 4 */
     int time_kernels;             /* 1: time every transport launch with CUDA events (mc_run_stats.kernel_ms) */
+    int regs_variant[4];          /* per transport kernel (CT photons, CT electrons, EPID photons, EPID
+                                     electrons): build for 2, 3 or 4 CTAs of 256 threads per SM
+                                     (register caps 128 / 85 / 64); 0 = 4 */
 } mc_config;
 
 /* EPID layer stack from the source side (Sec. 2.1.3).  The centre of the

@@ -35,7 +35,7 @@ class Config(C.Structure):
                 ("wcc_mev", C.c_double), ("wcb_mev", C.c_double), ("step_fraction", C.c_double),
                 ("n_batches", C.c_int), ("max_steps", C.c_int), ("block_size", C.c_int),
                 ("ctas_per_sm", C.c_int), ("bank_capacity", C.c_uint32), ("primaries_per_wave", C.c_uint32),
-                ("time_kernels", C.c_int)]
+                ("time_kernels", C.c_int), ("regs_variant", C.c_int * 4)]
 
 
 class EpidDesc(C.Structure):
@@ -138,7 +138,10 @@ def default_config(physics=None, **overrides) -> Config:
         cfg.n_batches = physics.n_batches
         cfg.max_steps = physics.max_steps
     for k, v in overrides.items():
-        setattr(cfg, k, v)
+        if k == "regs_variant":
+            cfg.regs_variant[:] = list(v)
+        else:
+            setattr(cfg, k, v)
     return cfg
 
 

@@ -31,6 +31,7 @@ struct mc_ctx {
     // transport launch shape per bank type
     int block = 256;
     int grid[mc::kNumBanks] = {0, 0, 0, 0};
+    int minb[mc::kNumBanks] = {4, 4, 4, 4};
     // banks
     void* bank_mem = nullptr;
     BankPtr bank[mc::kNumBanks][2];
@@ -212,6 +213,8 @@ void make_params(const mc_ctx* c, Params& P, uint64_t seed) {
     P.etab = c->d_etab;
     P.e_lnT0 = static_cast<float>(c->tabs.e_lnT0);
     P.e_idx = static_cast<float>(c->tabs.e_inv_dlnT);
+    P.w_lnG0 = static_cast<float>(c->tabs.w_lnG0);
+    P.w_idx = static_cast<float>(c->tabs.w_inv_dlnG);
     P.seed = seed;
     P.hist_base = c->hist_done;
     P.tally = c->d_tally;
@@ -249,9 +252,10 @@ void mc_config_default(mc_config* cfg) {
     cfg->max_steps = 10000;
     cfg->block_size = 256;
     cfg->ctas_per_sm = 0;
-    cfg->bank_capacity = 1u << 22;
+    cfg->bank_capacity = 1u << 23;
     cfg->primaries_per_wave = 0;
     cfg->time_kernels = 0;
+    for (int t = 0; t < 4; ++t) cfg->regs_variant[t] = 4;
 }
 
 const char* mc_status_string(mc_status s) {
@@ -277,7 +281,11 @@ mc_status mc_create(const mc_config* cfg_in, int device, mc_ctx** out) {
     mc_config cfg;
     if (cfg_in) cfg = *cfg_in; else mc_config_default(&cfg);
     if (cfg.block_size == 0) cfg.block_size = 256;
-    if (cfg.bank_capacity == 0) cfg.bank_capacity = 1u << 22;
+    if (cfg.bank_capacity == 0) cfg.bank_capacity = 1u << 23;
+    for (int t = 0; t < 4; ++t) {
+        if (cfg.regs_variant[t] == 0) cfg.regs_variant[t] = 4;
+        if (cfg.regs_variant[t] < 2 || cfg.regs_variant[t] > 4) return MC_ERR_ARG;
+    }
     if (cfg.primaries_per_wave == 0) cfg.primaries_per_wave = cfg.bank_capacity / 4;
     if (cfg.block_size % 32 != 0 || cfg.block_size < 32 || cfg.block_size > 256) return MC_ERR_ARG;
     if (cfg.n_batches < 2 || cfg.n_batches > 1024 || cfg.max_steps < 1) return MC_ERR_ARG;
@@ -297,11 +305,13 @@ mc_status mc_create(const mc_config* cfg_in, int device, mc_ctx** out) {
     const double emax = std::fmax(cfg.e_max_mev, cfg.mono_energy_mev);
     c->tabs = mcphys::build_tables(0.95 * std::fmin(cfg.photon_cutoff_mev, cfg.wcb_mev), 1.02 * emax,
                                    0.99 * cfg.electron_cutoff_mev, 1.02 * emax, cfg.wcc_mev, cfg.wcb_mev);
+    std::vector<float> etab(c->tabs.electron);
+    etab.insert(etab.end(), c->tabs.wentzel.begin(), c->tabs.wentzel.end());   // electron kernels stage both
     if (cudaMalloc(&c->d_ptab, sizeof(float) * c->tabs.photon.size()) != cudaSuccess ||
-        cudaMalloc(&c->d_etab, sizeof(float) * c->tabs.electron.size()) != cudaSuccess)
+        cudaMalloc(&c->d_etab, sizeof(float) * etab.size()) != cudaSuccess)
         return bail(MC_ERR_OOM);
     cudaMemcpy(c->d_ptab, c->tabs.photon.data(), sizeof(float) * c->tabs.photon.size(), cudaMemcpyHostToDevice);
-    cudaMemcpy(c->d_etab, c->tabs.electron.data(), sizeof(float) * c->tabs.electron.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_etab, etab.data(), sizeof(float) * etab.size(), cudaMemcpyHostToDevice);
 
     c->cap = cfg.bank_capacity;
     const size_t per = static_cast<size_t>(c->cap) * 4;
@@ -333,7 +343,8 @@ mc_status mc_create(const mc_config* cfg_in, int device, mc_ctx** out) {
     c->block = cfg.block_size;
     for (int t = 0; t < mc::kNumBanks; ++t) {
         int occ = 0;
-        if (mc::transport_occupancy(t, c->block, &occ) != cudaSuccess || occ < 1) return bail(MC_ERR_CUDA);
+        c->minb[t] = cfg.regs_variant[t];
+        if (mc::transport_occupancy(t, c->minb[t], c->block, &occ) != cudaSuccess || occ < 1) return bail(MC_ERR_CUDA);
         const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, occ) : occ;
         c->grid[t] = c->sm_count * per_sm;
     }
@@ -577,7 +588,7 @@ mc_status mc_run(mc_ctx* c, uint64_t n, uint64_t seed, void* stream, mc_run_stat
                 timed.emplace_back(t, ev_used);
                 CUDA_TRY(c, cudaEventRecord(next_event(), s));
             }
-            CUDA_TRY(c, mc::launch_transport(t, P, c->grid[t], c->block, s));
+            CUDA_TRY(c, mc::launch_transport(t, c->minb[t], P, c->grid[t], c->block, s));
             if (c->cfg.time_kernels) CUDA_TRY(c, cudaEventRecord(next_event(), s));
             CUDA_TRY(c, mc::launch_swap(c->d_ctl, t, s));
             launches += 2;

@@ -22,8 +22,8 @@ struct TmapArgs {
 };
 
 size_t transport_smem(int type);
-cudaError_t transport_occupancy(int type, int block, int* blocks_per_sm);
-cudaError_t launch_transport(int type, const Params& P, int grid, int block, cudaStream_t s);
+cudaError_t transport_occupancy(int type, int minb, int block, int* blocks_per_sm);
+cudaError_t launch_transport(int type, int minb, const Params& P, int grid, int block, cudaStream_t s);
 cudaError_t launch_swap(Ctl* c, int t, cudaStream_t s);
 cudaError_t launch_wave_begin(Ctl* c, unsigned long long per_wave, cudaStream_t s);
 

@@ -26,6 +26,7 @@ constexpr float kMec2 = 0.51099895f;
 constexpr float kTwoMec2 = 1.0219979f;
 constexpr int kPhotonNodes = 2048;
 constexpr int kElectronNodes = 512;
+constexpr int kWentzelNodes = 128;
 constexpr int kNumMat = 7;
 constexpr int kMaxLayers = 8;
 constexpr float kQuantaPerMeV = 2.56e8f;      // tally unit 2^-8 eV
@@ -90,8 +91,9 @@ struct Params {
     MatC mat[kNumMat];
     const float2* ptab;
     float p_lnE0, p_idx;
-    const float2* etab;             // [kNumMat][kElectronNodes]
+    const float2* etab;             // [kNumMat][kElectronNodes], then kWentzelNodes/2 float2 of ln A
     float e_lnT0, e_idx;
+    float w_lnG0, w_idx;
     // run
     unsigned long long seed, hist_base;
     unsigned long long* tally;      // [B][npy][npx]
@@ -343,27 +345,30 @@ __device__ __forceinline__ float2 electron_tab(const float2* tab, const Params& 
 }
 
 // Screening parameter A of the screened-Rutherford (Wentzel) law whose mean
-// <1 - cos> equals 1 - exp(-G); -1 means isotropic.  Newton on ln A.
-__device__ __forceinline__ float wentzel_A(float G) {
+// <1 - cos> equals 1 - exp(-G); -1 means isotropic.  Start from the ln A(ln G)
+// table (shared memory, after the electron tables) and take two Newton steps
+// on ln A; the same fixed work on every lane.
+__device__ __forceinline__ float wentzel_A(const float* wtab, const Params& P, float G) {
     const float m = -0.5f * expm1f(-G);
     if (0.5f - m < 1e-6f) return -1.0f;
-    float y = (m < 0.3f) ? logf(m / fmaxf(logf(1.0f / m) - 1.0f, 1.0f)) : logf(1.0f / (6.0f * (0.5f - m)));
-    for (int it = 0; it < 12; ++it) {
+    const float x = (logf(G) - P.w_lnG0) * P.w_idx;
+    const int i = min(max(__float2int_rd(x), 0), kWentzelNodes - 2);
+    const float f = x - static_cast<float>(i);
+    float y = fmaf(f, wtab[i + 1] - wtab[i], wtab[i]);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
         const float A = expf(y);
         float mean, dm;
         if (A > 100.0f) {
-            const float x = 1.0f / A;
-            mean = 0.5f - x * (1.0f / 6.0f - x * (1.0f / 12.0f - x * (1.0f / 20.0f)));
-            dm = x * x * (1.0f / 6.0f - x * (1.0f / 6.0f));
+            const float xa = 1.0f / A;
+            mean = 0.5f - xa * (1.0f / 6.0f - xa * (1.0f / 12.0f - xa * (1.0f / 20.0f)));
+            dm = xa * xa * (1.0f / 6.0f - xa * (1.0f / 6.0f));
         } else {
             const float l = log1pf(1.0f / A);
             mean = A * ((1.0f + A) * l - 1.0f);
             dm = (1.0f + 2.0f * A) * l - 2.0f;
         }
-        float step = (mean - m) / (A * dm);
-        step = fminf(fmaxf(step, -2.0f), 2.0f);
-        y -= step;
-        if (fabsf(step) < 2e-7f) break;
+        y -= fminf(fmaxf((mean - m) / (A * dm), -2.0f), 2.0f);
     }
     return expf(y);
 }

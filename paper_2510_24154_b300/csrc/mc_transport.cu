@@ -337,6 +337,16 @@ __device__ __forceinline__ bool photon_epid_event(const Params& P, const float2*
 }
 
 // One condensed-history step of an electron or positron.
+//
+// Step length: the least of the 5 % energy-loss step (midpoint stopping
+// power), the distance to a hard event (delta tracking against the
+// start-of-step cross section) and the distance to the cell face.  The
+// deflection for the whole step is drawn once.  An energy-loss or hard-event
+// limited step is a random hinge (first segment, deflection, second segment
+// clipped at a face); a face-limited step goes straight to the face, deposits
+// at its midpoint, crosses and keeps the deflection only if it stays inside.
+// Both kinds run through one code path, selecting where they differ, so the
+// warp diverges as little as possible.
 template <bool EPID>
 __device__ __forceinline__ bool electron_event(const Params& P, const float2* tab, Acc& a,
                                                unsigned long long* s_energy, unsigned long long* s_events,
@@ -365,7 +375,7 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     // hard bremsstrahlung exists only above wcb: A ln(T / wcb) for T > wcb
     const float Sh = rho * (electron_tab(tab, P, m, lnT).y + mcst.brem * fmaxf(lnT - P.ln_wcb, 0.0f));
     const float sh = -logf(p.rng.u()) / Sh;
-    // (c) cell boundary
+    // (c) cell face
     int ax;
     const float sb = EPID ? epid_dist(P, p, layer, ax) : ct_dist(P, p, p.cell, ax);
     float s = sE;
@@ -379,62 +389,39 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     const float G = s * rho * mcst.msc / pb2;
     float mu = 0.0f;
     if (G > 0.0f) {
-        const float A = wentzel_A(G);
+        const float A = wentzel_A(reinterpret_cast<const float*>(tab + kNumMat * kElectronNodes), P, G);
         mu = (A < 0.0f) ? xmu : A * xmu / (1.0f - xmu + A);
     }
     float sp, cp;
     sincospif(2.0f * xph, &sp, &cp);
-    if (lim == 2) {
-        // Boundary-limited step: straight to the face, deposit at the segment
-        // midpoint, cross, then deflect.  (A hinge here would stop the particle
-        // just short of the face and start a run of ever-shorter steps whose
-        // crossing is decided by rounding.)
-        const float mx = p.x + 0.5f * s * p.u, my = p.y + 0.5f * s * p.v, mz = p.z + 0.5f * s * p.w;
-        const uint32_t c0 = p.cell;
-        p.x += s * p.u; p.y += s * p.v; p.z += s * p.w;
-        const float dE = dEt * (s / sE);
-        const float Tn = T - dE;
-        if (Tn <= P.tstop) {
-            deposit<EPID>(P, a, s_energy, c0, mx, my, p.hist, dE + Tn);
-            if (p.flags & kPositron) {
-                p.x = mx; p.y = my; p.z = mz;
-                annihilate<EPID>(P, s_events, p, e0);
-            }
-            return false;
-        }
-        deposit<EPID>(P, a, s_energy, c0, mx, my, p.hist, dE);
-        p.E = Tn;
-        if (EPID) {
-            if (ax != 0) { a.esc += quanta(p.E + rest_extra(p.flags)); return false; }
-            const int nl = layer + (p.w < 0.0f ? 1 : -1);
-            if (nl < 0 || nl >= P.nl) { a.esc += quanta(p.E + rest_extra(p.flags)); return false; }
-            p.cell = static_cast<uint32_t>(nl);
-        } else {
-            int ix = cell_x(p.cell), iy = cell_y(p.cell), iz = cell_z(p.cell);
-            const float dirc = (ax == 0) ? p.u : (ax == 1) ? p.v : p.w;
-            const int stp = (dirc > 0.0f) ? 1 : -1;
-            if (ax == 0) ix += stp; else if (ax == 1) iy += stp; else iz += stp;
-            if (ix < 0 || ix >= P.nx || iy < 0 || iy >= P.ny || iz < 0 || iz >= P.nz) {
-                move = transfer_to_epid(P, p, a, s_events, false);
-                return false;
-            }
-            p.cell = pack_cell(ix, iy, iz);
-        }
-        rotate_dir(p.u, p.v, p.w, 1.0f - 2.0f * mu, cp, sp);
-        return true;
-    }
-    // random hinge: first segment, deflection, second segment
-    const float s1 = xh * s;
+    const bool face = (lim == 2);
+    // first segment: the whole step for a face-limited step, else up to the hinge
+    const float s1 = face ? s : xh * s;
+    const float sd = face ? 0.5f * s : s1;                     // deposit (and stop) point
+    const float hx = p.x + sd * p.u, hy = p.y + sd * p.v, hz = p.z + sd * p.w;
     p.x += s1 * p.u; p.y += s1 * p.v; p.z += s1 * p.w;
-    const float hx = p.x, hy = p.y, hz = p.z;
     const uint32_t hcell = p.cell;
+    const float u0 = p.u, v0 = p.v, w0 = p.w;                  // direction before the deflection
     rotate_dir(p.u, p.v, p.w, 1.0f - 2.0f * mu, cp, sp);
-    float s2 = s - s1;
-    int ax2;
-    const float sb2 = EPID ? epid_dist(P, p, layer, ax2) : ct_dist(P, p, p.cell, ax2);
-    bool crossed = false;
-    if (s2 >= sb2) { s2 = sb2; crossed = true; }
-    p.x += s2 * p.u; p.y += s2 * p.v; p.z += s2 * p.w;
+    // second segment (hinge steps only), clipped at the first face it meets
+    float s2 = 0.0f;
+    bool crossed = face;
+    int cax = ax;
+    // direction component across the crossed face: in the EPID face 0 is a layer
+    // plane (z) and faces 1, 2 are the lateral edges; in the CT faces 0, 1, 2 are x, y, z
+    float cdir = EPID ? w0 : (ax == 0) ? u0 : (ax == 1) ? v0 : w0;
+    if (!face) {
+        int ax2;
+        const float sb2 = EPID ? epid_dist(P, p, layer, ax2) : ct_dist(P, p, p.cell, ax2);
+        s2 = s - s1;
+        if (s2 >= sb2) {
+            s2 = sb2;
+            crossed = true;
+            cax = ax2;
+            cdir = EPID ? p.w : (ax2 == 0) ? p.u : (ax2 == 1) ? p.v : p.w;
+        }
+        p.x += s2 * p.u; p.y += s2 * p.v; p.z += s2 * p.w;
+    }
     const float dE = dEt * ((s1 + s2) / sE);
     const float Tn = T - dE;
     if (Tn <= P.tstop) {
@@ -448,21 +435,24 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, dE);
     p.E = Tn;
     if (crossed) {
+        bool out;
         if (EPID) {
-            if (ax2 != 0) { a.esc += quanta(p.E + rest_extra(p.flags)); return false; }
-            const int nl = layer + (p.w < 0.0f ? 1 : -1);
-            if (nl < 0 || nl >= P.nl) { a.esc += quanta(p.E + rest_extra(p.flags)); return false; }
-            p.cell = static_cast<uint32_t>(nl);
+            const int nl = layer + (cdir < 0.0f ? 1 : -1);      // layers are numbered down the beam (-z)
+            out = (cax != 0) || nl < 0 || nl >= P.nl;
+            if (!out) p.cell = static_cast<uint32_t>(nl);
         } else {
             int ix = cell_x(p.cell), iy = cell_y(p.cell), iz = cell_z(p.cell);
-            const float dirc = (ax2 == 0) ? p.u : (ax2 == 1) ? p.v : p.w;
-            const int stp = (dirc > 0.0f) ? 1 : -1;
-            if (ax2 == 0) ix += stp; else if (ax2 == 1) iy += stp; else iz += stp;
-            if (ix < 0 || ix >= P.nx || iy < 0 || iy >= P.ny || iz < 0 || iz >= P.nz) {
-                move = transfer_to_epid(P, p, a, s_events, false);
-                return false;
-            }
-            p.cell = pack_cell(ix, iy, iz);
+            const int stp = (cdir > 0.0f) ? 1 : -1;
+            if (cax == 0) ix += stp; else if (cax == 1) iy += stp; else iz += stp;
+            out = ix < 0 || ix >= P.nx || iy < 0 || iy >= P.ny || iz < 0 || iz >= P.nz;
+            if (!out) p.cell = pack_cell(ix, iy, iz);
+        }
+        if (out) {
+            // a face-limited step leaves undeflected
+            if (face) { p.u = u0; p.v = v0; p.w = w0; }
+            if (EPID) { a.esc += quanta(p.E + rest_extra(p.flags)); }
+            else { move = transfer_to_epid(P, p, a, s_events, false); }
+            return false;
         }
         return true;
     }
@@ -606,11 +596,11 @@ __device__ __forceinline__ bool start_primary(const Params& P, uint32_t idx, Par
 }
 
 // The persistent transport kernel for one event type.
-template <int TYPE>
-__global__ void __launch_bounds__(256) k_transport(const Params P) {
+template <int TYPE, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
     constexpr bool kPhoton = (TYPE == kPhotonCT || TYPE == kPhotonEPID);
     constexpr bool kEpid = (TYPE == kPhotonEPID || TYPE == kElectronEPID);
-    constexpr int kTabN = kPhoton ? kPhotonNodes : kNumMat * kElectronNodes;
+    constexpr int kTabN = kPhoton ? kPhotonNodes : kNumMat * kElectronNodes + kWentzelNodes / 2;
     constexpr int kMoveTo = kPhoton ? kPhotonEPID : kElectronEPID;
     extern __shared__ float2 s_tab[];
     __shared__ unsigned long long s_energy[kNumEnergy];
@@ -733,32 +723,38 @@ __global__ void k_wave_begin(Ctl* c, unsigned long long per_wave) {
 
 size_t transport_smem(int type) {
     const bool photon = (type == kPhotonCT || type == kPhotonEPID);
-    return sizeof(float2) * (photon ? kPhotonNodes : kNumMat * kElectronNodes);
+    return sizeof(float2) * (photon ? kPhotonNodes : kNumMat * kElectronNodes + kWentzelNodes / 2);
 }
 
-static const void* transport_fn(int type) {
-    switch (type) {
-        case kPhotonCT: return reinterpret_cast<const void*>(&k_transport<kPhotonCT>);
-        case kElectronCT: return reinterpret_cast<const void*>(&k_transport<kElectronCT>);
-        case kPhotonEPID: return reinterpret_cast<const void*>(&k_transport<kPhotonEPID>);
-        default: return reinterpret_cast<const void*>(&k_transport<kElectronEPID>);
+// Each event type is built for 2, 3 and 4 resident CTAs of 256 threads per SM
+// (register caps 128, 85 and 64); the launch picks one per type.
+template <int TYPE>
+static const void* fn_for(int minb) {
+    switch (minb) {
+        case 2: return reinterpret_cast<const void*>(&k_transport<TYPE, 2>);
+        case 4: return reinterpret_cast<const void*>(&k_transport<TYPE, 4>);
+        default: return reinterpret_cast<const void*>(&k_transport<TYPE, 3>);
     }
 }
 
-cudaError_t transport_occupancy(int type, int block, int* blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_fn(type), block,
+static const void* transport_fn(int type, int minb) {
+    switch (type) {
+        case kPhotonCT: return fn_for<kPhotonCT>(minb);
+        case kElectronCT: return fn_for<kElectronCT>(minb);
+        case kPhotonEPID: return fn_for<kPhotonEPID>(minb);
+        default: return fn_for<kElectronEPID>(minb);
+    }
+}
+
+cudaError_t transport_occupancy(int type, int minb, int block, int* blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_fn(type, minb), block,
                                                          transport_smem(type));
 }
 
-cudaError_t launch_transport(int type, const Params& P, int grid, int block, cudaStream_t s) {
+cudaError_t launch_transport(int type, int minb, const Params& P, int grid, int block, cudaStream_t s) {
     const size_t smem = transport_smem(type);
-    switch (type) {
-        case kPhotonCT: k_transport<kPhotonCT><<<grid, block, smem, s>>>(P); break;
-        case kElectronCT: k_transport<kElectronCT><<<grid, block, smem, s>>>(P); break;
-        case kPhotonEPID: k_transport<kPhotonEPID><<<grid, block, smem, s>>>(P); break;
-        default: k_transport<kElectronEPID><<<grid, block, smem, s>>>(P); break;
-    }
-    return cudaGetLastError();
+    void* args[] = {const_cast<Params*>(&P)};
+    return cudaLaunchKernel(transport_fn(type, minb), dim3(grid), dim3(block), args, smem, s);
 }
 
 cudaError_t launch_swap(Ctl* c, int t, cudaStream_t s) {

@@ -108,6 +108,26 @@ double moller_hard(int m, double T, double wcc) {
     return kAvogadro * mc.zA * 2.0 * kPi * kRe * kRe * kMec2 / (beta2 * T) * integral;
 }
 
+// Screened-Rutherford law p(mu) = A(1+A)/(mu+A)^2 on mu = (1-cos)/2 has mean
+// A[(1+A) ln(1+1/A) - 1]; A(G) solves mean = (1 - exp(-G))/2, by bisection on
+// ln A (the mean increases monotonically with A).
+double wentzel_screening(double G) {
+    const double target = 0.5 * -std::expm1(-G);
+    auto mean = [](double A) {
+        if (A > 1e3) {   // series in 1/A: 1/2 - 1/(6A) + 1/(12A^2) - 1/(20A^3)
+            const double x = 1.0 / A;
+            return 0.5 - x / 6.0 + x * x / 12.0 - x * x * x / 20.0;
+        }
+        return A * ((1.0 + A) * std::log1p(1.0 / A) - 1.0);
+    };
+    double lo = -80.0, hi = 40.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mean(std::exp(mid)) < target) lo = mid; else hi = mid;
+    }
+    return std::exp(0.5 * (lo + hi));
+}
+
 Tables build_tables(double e_lo, double e_hi, double t_lo, double t_hi, double wcc, double wcb) {
     Tables t;
     for (int m = 0; m < kNumMaterials; ++m) t.mat[m] = material_coefs(m);
@@ -135,6 +155,12 @@ Tables build_tables(double e_lo, double e_hi, double t_lo, double t_hi, double w
             row[1] = static_cast<float>(moller_hard(m, T, wcc));
         }
     }
+    const double lg0 = std::log(1e-12), lg1 = std::log(13.0);
+    t.w_lnG0 = lg0;
+    t.w_inv_dlnG = (kWentzelNodes - 1) / (lg1 - lg0);
+    t.wentzel.resize(kWentzelNodes);
+    for (int i = 0; i < kWentzelNodes; ++i)
+        t.wentzel[i] = static_cast<float>(std::log(wentzel_screening(std::exp(lg0 + i / t.w_inv_dlnG))));
     return t;
 }
 

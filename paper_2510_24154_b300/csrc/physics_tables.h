@@ -15,6 +15,7 @@ namespace mcphys {
 constexpr int kNumMaterials = 7;
 constexpr int kPhotonNodes = 2048;     // ln-uniform photon table nodes
 constexpr int kElectronNodes = 512;    // ln-uniform electron table nodes per material
+constexpr int kWentzelNodes = 128;     // ln A of the screening parameter on a ln G grid
 
 constexpr double kMec2 = 0.51099895;   // MeV
 constexpr double kRe = 2.8179403262e-13;
@@ -42,6 +43,7 @@ double klein_nishina_barn(double E);
 double pair_shape(double E);
 double collision_stopping_restricted(int m, double T, double wcc);
 double moller_hard(int m, double T, double wcc);
+double wentzel_screening(double G);
 
 struct Tables {
     // photon: (sigma_KN in barn, pair shape) at E_i = exp(lnE0 + i / inv_dlnE)
@@ -50,6 +52,10 @@ struct Tables {
     // electron, per material: (soft stopping power MeV cm^2/g, hard Moller cm^2/g)
     std::vector<float> electron;        // kNumMaterials * 2 * kElectronNodes
     double e_lnT0 = 0, e_inv_dlnT = 0;
+    // ln of the Wentzel screening parameter A(G) with <1-cos> = 1 - exp(-G),
+    // on ln G from ln(1e-12) to ln(13) (beyond ~13.1 the law is isotropic)
+    std::vector<float> wentzel;         // kWentzelNodes
+    double w_lnG0 = 0, w_inv_dlnG = 0;
     MaterialCoefs mat[kNumMaterials];
 };
 
