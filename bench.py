@@ -31,10 +31,11 @@ HIST_PER_STEP = 100_000_000
 SEED = 1
 WORKLOAD = "thorax_imrt_9seg: CT 256x256x128 int16 HU @2mm, 9 MLC segments x 60 pairs, " \
            "EPID 1024x768 @0.39mm (Cu/Gd2O2S/a-Si), k-table 64x32, coupled photon/electron"
-# Counted single-precision work per CT electron step (FADD + FMUL + 2 x FFMA +
-# the special-function instructions), from the ncu capture summarised in
-# profiles/electron_ct_thorax.md.
-FLOPS_PER_ESTEP_CT = 312.0
+# Counted single-precision work per CT electron step: FADD + FMUL + 2 FFMA
+# (+ 2 x the packed forms, none issued) summed over every CT-electron launch of
+# the small thorax case, divided by its CT electron steps; ncu capture in
+# profiles/electron_ct_small_case.md.
+FLOPS_PER_ESTEP_CT = 555.4
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
 
 
@@ -47,7 +48,7 @@ def parse():
     ap.add_argument("--histories", type=int, default=HIST_PER_STEP)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--bank-capacity", type=int, default=0, help="particles per bank (0: library default)")
+    ap.add_argument("--bank-capacity", type=int, default=1 << 24, help="particles per bank (0: library default)")
     ap.add_argument("--regs-variant", default="", help="CTAs/SM build per transport kernel, e.g. 3,3,3,3")
     return ap.parse_args()
 
@@ -260,6 +261,9 @@ def main():
         "flops_per_unit": FLOPS_PER_ESTEP_CT, "unit_of_work": "CT electron step",
         "units_per_launch": steps_per_launch, "avg_launch_ms": avg_ms,
         "kernel_share_of_transport": float(agg["kernel_ms"][1] / max(agg["kernel_ms"].sum(), 1e-12)),
+        "lane_utilisation": {
+            "photons_ct": last["counters"]["live_lanes_photon_ct"] / max(32 * last["counters"]["warp_iters_photon_ct"], 1),
+            "electrons_ct": last["counters"]["live_lanes_electron_ct"] / max(32 * last["counters"]["warp_iters_electron_ct"], 1)},
         "transport_ms_per_step": {k: float(v / args.steps) for k, v in
                                   zip(("photons_ct", "electrons_ct", "photons_epid", "electrons_epid"),
                                       agg["kernel_ms"])},

@@ -55,14 +55,18 @@ enum {
 };
 
 #define MC_MAX_LAYERS 8
-#define MC_NUM_COUNTERS 16
+#define MC_NUM_COUNTERS 20
 
 /* Event counters, in the order of mc_run_stats.counters. */
 enum {
     MC_CNT_FLIGHTS_CT = 0, MC_CNT_REAL_CT, MC_CNT_COMPTON, MC_CNT_PHOTO, MC_CNT_PAIR,
     MC_CNT_ESTEPS_CT, MC_CNT_ESTEPS_EPID, MC_CNT_MOLLER, MC_CNT_BREM, MC_CNT_PRIMARIES_AT_EPID,
     MC_CNT_UNCOLLIDED_AT_EPID, MC_CNT_LOST, MC_CNT_FLIGHTS_EPID, MC_CNT_ELECTRONS, MC_CNT_POSITRONS,
-    MC_CNT_SECONDARY_PHOTONS
+    MC_CNT_SECONDARY_PHOTONS,
+    /* execution: warp iterations and live lanes summed over them, for the CT
+     * photon and CT electron kernels (live / (32 iterations) = lane utilisation) */
+    MC_CNT_WARP_ITERS_PHOTON_CT, MC_CNT_LIVE_LANES_PHOTON_CT, MC_CNT_WARP_ITERS_ELECTRON_CT,
+    MC_CNT_LIVE_LANES_ELECTRON_CT
 };
 
 /* Transport and execution settings.  Physics fields follow Sec. 2.1.2

@@ -180,7 +180,8 @@ double orc_lambda1_inv(int m, double T) {
 /* draw stream.  Draw d of particle (hist h, ordinal o) is word d mod 4 of   */
 /* Philox(counter = (d div 4, o, h_lo, h_hi), key = (seed_lo, seed_hi)),     */
 /* mapped to ((u >> 9) + 0.5) 2^-23, a value exact in single and double      */
-/* precision and strictly inside (0, 1).                                     */
+/* precision and strictly inside (0, 1).  Electron steps and photon flights  */
+/* start at the next multiple of 4 (rng_align).                              */
 /* ------------------------------------------------------------------------ */
 void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
     uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
@@ -214,6 +215,10 @@ typedef struct {
     uint32_t d;
     uint32_t cblk; int cvalid; uint32_t cbuf[4];
 } o_rng;
+
+/* Every electron step and every photon flight starts on a fresh Philox block:
+ * the draw counter is rounded up to a multiple of 4. */
+static void rng_align(o_rng* r) { r->d = (r->d + 3u) & ~3u; }
 
 static double rng_u(o_rng* r) {
     uint32_t blk = r->d >> 2, w = r->d & 3u;
@@ -376,6 +381,9 @@ typedef struct {
     double half_w[2];                 /* EPID lateral half widths */
     double rho_max[4];                /* per CT material */
     int mat_present[4];
+    int mgM, mg[3];                   /* macro-cells: M voxels per side, count per axis */
+    double* mg_low;                   /* per macro-cell max density of air, lung, water voxels */
+    double* mg_bone;                  /* per macro-cell max density of bone voxels */
     double* rect;                     /* source rectangles: x0,x1,y0,y1 */
     double* cdf;                      /* cumulative weight */
     int n_rect;
@@ -438,23 +446,6 @@ static void deposit(o_ctx* c, const o_part* p, const double pos[3], int layer, d
     if (iy >= P->npy) iy = P->npy - 1;
     int b = (int)(c->hist % (uint64_t)P->n_batches);
     c->tally[((size_t)b * P->npy + iy) * P->npx + ix] += dE;
-}
-
-static double sigma_max_ct(const o_ctx* c, double E) {
-    double s = 0.0;
-    for (int m = 0; m < 4; m++)
-        if (c->mat_present[m]) s = fmax(s, c->rho_max[m] * mu_total(m, E));
-    return s;
-}
-
-static int ct_voxel(const o_ctx* c, const double x[3], int idx[3]) {
-    const orc_problem* P = c->P;
-    int n[3] = {P->nx, P->ny, P->nz};
-    for (int a = 0; a < 3; a++) {
-        idx[a] = (int)floor((x[a] - P->origin[a]) / P->vox[a]);
-        if (idx[a] < 0 || idx[a] >= n[a]) return 0;
-    }
-    return 1;
 }
 
 static void ct_props(const o_ctx* c, const int idx[3], double* rho, int* mat) {
@@ -618,19 +609,77 @@ static int photon_interact(o_ctx* c, o_part* p, int m, int layer) {
     }
 }
 
+/* Largest per-gram attenuation of the non-bone CT materials and of bone. */
+static void mu_groups(double E, double* mu_low, double* mu_bone) {
+    *mu_low = fmax(mu_total(0, E), fmax(mu_total(1, E), mu_total(2, E)));
+    *mu_bone = mu_total(3, E);
+}
+
+/* One Woodcock flight with a piecewise-constant majorant: an optical depth
+ * tau = -ln(xi) is spent along the ray across macro-cells, each with majorant
+ * Sigma_c = max(rho_low,c mu_low(E), rho_bone,c mu_bone(E)).  Returns 1 with
+ * the tentative collision's voxel (kept inside its macro-cell) and Sigma_c, or
+ * 0 when the ray leaves the CT (x is then on the box's face). */
+static int ct_flight(const o_ctx* c, double x[3], const double u[3], double E, o_rng* r, int idx[3], double* Sc_out) {
+    const orc_problem* P = c->P;
+    const int n[3] = {P->nx, P->ny, P->nz};
+    const int M = c->mgM;
+    double mul, mub;
+    mu_groups(E, &mul, &mub);
+    rng_align(r);
+    double tau = -log(rng_u(r));
+    int cm[3];
+    for (int a = 0; a < 3; a++) {
+        int k = (int)floor((x[a] - P->origin[a]) / (M * P->vox[a]));
+        cm[a] = k < 0 ? 0 : (k >= c->mg[a] ? c->mg[a] - 1 : k);
+    }
+    for (;;) {
+        size_t cc = ((size_t)cm[2] * c->mg[1] + cm[1]) * c->mg[0] + cm[0];
+        double Sc = fmax(c->mg_low[cc] * mul, c->mg_bone[cc] * mub);
+        double d = INFINITY;
+        int ax = 0;
+        for (int a = 0; a < 3; a++) {
+            double da = INFINITY;
+            if (u[a] > 0.0) {
+                int hi = (cm[a] + 1) * M < n[a] ? (cm[a] + 1) * M : n[a];
+                da = (P->origin[a] + hi * P->vox[a] - x[a]) / u[a];
+            } else if (u[a] < 0.0) {
+                da = (P->origin[a] + cm[a] * M * P->vox[a] - x[a]) / u[a];
+            }
+            if (da < d) { d = da; ax = a; }
+        }
+        if (d < 0.0) d = 0.0;
+        if (tau < Sc * d) {
+            double s = tau / Sc;
+            for (int a = 0; a < 3; a++) x[a] += s * u[a];
+            for (int a = 0; a < 3; a++) {
+                int k = (int)floor((x[a] - P->origin[a]) / P->vox[a]);
+                int lo = cm[a] * M, hi = ((cm[a] + 1) * M < n[a] ? (cm[a] + 1) * M : n[a]) - 1;
+                idx[a] = k < lo ? lo : (k > hi ? hi : k);
+            }
+            *Sc_out = Sc;
+            return 1;
+        }
+        tau -= Sc * d;
+        for (int a = 0; a < 3; a++) x[a] += d * u[a];
+        cm[ax] += (u[ax] > 0.0) ? 1 : -1;
+        if (cm[ax] < 0 || cm[ax] >= c->mg[ax]) return 0;
+    }
+}
+
+/* Photon transport in the CT: flights until a tentative collision is real
+ * (probability Sigma_voxel / Sigma_c) or the photon leaves the CT. */
 static void photon_ct(o_ctx* c, o_part* p) {
     const orc_problem* P = c->P;
     for (int f = 0; f < P->max_steps; f++) {
-        double smax = sigma_max_ct(c, p->E);
-        double s = -log(rng_u(&p->rng)) / smax;
-        for (int a = 0; a < 3; a++) p->x[a] += s * p->u[a];
-        c->cnt[C_FLIGHTS_CT]++;
         int idx[3];
-        if (!ct_voxel(c, p->x, idx)) { transfer_to_epid(c, p); return; }
+        double Sc;
+        c->cnt[C_FLIGHTS_CT]++;
+        if (!ct_flight(c, p->x, p->u, p->E, &p->rng, idx, &Sc)) { transfer_to_epid(c, p); return; }
         double rho; int m;
         ct_props(c, idx, &rho, &m);
         double sig = rho * mu_total(m, p->E);
-        if (!(rng_u(&p->rng) * smax < sig)) continue;      /* virtual */
+        if (!(rng_u(&p->rng) * Sc < sig)) continue;      /* virtual */
         c->cnt[C_REAL_CT]++;
         p->cell[0] = idx[0]; p->cell[1] = idx[1]; p->cell[2] = idx[2];
         if (!photon_interact(c, p, m, 0)) return;
@@ -657,6 +706,7 @@ static double epid_dist(const o_ctx* c, const double x[3], const double u[3], in
 static void photon_epid(o_ctx* c, o_part* p) {
     const orc_problem* P = c->P;
     for (int f = 0; f < P->max_steps; f++) {
+        rng_align(&p->rng);
         double tau = -log(rng_u(&p->rng));
         c->cnt[C_FLIGHTS_EPID]++;
         for (;;) {
@@ -710,6 +760,7 @@ static void electron(o_ctx* c, o_part* p) {
             c->cnt[C_ESTEP_EPID]++;
         }
         double T = p->E;
+        rng_align(&p->rng);
         /* (a) energy-loss limited step with midpoint stopping power */
         double dEt = P->step_frac * T;
         if (T - dEt < tstop) dEt = T - tcut;
@@ -947,6 +998,37 @@ static void ctx_geometry(o_ctx* c, const orc_problem* P) {
         c->mat_present[m] = 1;
         if (rho > c->rho_max[m]) c->rho_max[m] = rho;
     }
+    /* macro-cells of M^3 voxels, M the smallest power of two >= 4 giving at
+     * most 4096 cells; each keeps the largest density of its non-bone and of
+     * its bone voxels (the local Woodcock majorant) */
+    int n[3] = {P->nx, P->ny, P->nz};
+    int M = 4;
+    for (;;) {
+        long cells = 1;
+        for (int a = 0; a < 3; a++) cells *= (n[a] + M - 1) / M;
+        if (cells <= 4096) break;
+        M *= 2;
+    }
+    c->mgM = M;
+    for (int a = 0; a < 3; a++) c->mg[a] = (n[a] + M - 1) / M;
+    size_t ncell = (size_t)c->mg[0] * c->mg[1] * c->mg[2];
+    c->mg_low = (double*)calloc(ncell, sizeof(double));
+    c->mg_bone = (double*)calloc(ncell, sizeof(double));
+    for (int iz = 0; iz < P->nz; iz++)
+        for (int iy = 0; iy < P->ny; iy++)
+            for (int ix = 0; ix < P->nx; ix++) {
+                double rho; int m;
+                orc_hu_to_rho_mat(P->hu[((size_t)iz * P->ny + iy) * P->nx + ix], &rho, &m);
+                size_t cc = ((size_t)(iz / M) * c->mg[1] + iy / M) * c->mg[0] + ix / M;
+                double* tgt = (m == 3) ? &c->mg_bone[cc] : &c->mg_low[cc];
+                if (rho > *tgt) *tgt = rho;
+            }
+}
+
+static void ctx_free(o_ctx* c) {
+    free(c->mg_low);
+    free(c->mg_bone);
+    c->mg_low = c->mg_bone = NULL;
 }
 
 static void* worker(void* arg) {
@@ -966,7 +1048,7 @@ int orc_run(const orc_problem* P, uint64_t seed, uint64_t hist_begin, uint64_t n
     if (!P || !R || !R->tally || P->n_layers < 1 || P->n_layers > O_MAXL || P->n_batches < 1) return 1;
     o_ctx base;
     ctx_geometry(&base, P);
-    if (!build_source(&base)) { free(base.rect); free(base.cdf); return 2; }
+    if (!build_source(&base)) { free(base.rect); free(base.cdf); ctx_free(&base); return 2; }
     if (n_threads < 1) n_threads = 1;
     if (n_threads > P->n_batches) n_threads = P->n_batches;
     o_job* jobs = (o_job*)calloc((size_t)n_threads, sizeof(o_job));
@@ -989,6 +1071,7 @@ int orc_run(const orc_problem* P, uint64_t seed, uint64_t hist_begin, uint64_t n
         free(l->stack);
     }
     free(jobs); free(th); free(base.rect); free(base.cdf);
+    ctx_free(&base);
     return 0;
 }
 
@@ -1065,23 +1148,22 @@ void orc_first_interaction(const orc_problem* P, double E, const double start[3]
         double x[3] = {start[0], start[1], start[2]};
         vox[i] = -1; type[i] = -1;
         for (int f = 0; f < 100000; f++) {
-            double smax = sigma_max_ct(&c, E);
-            double s = -log(rng_u(&r)) / smax;
-            for (int a = 0; a < 3; a++) x[a] += s * dir[a];
             int idx[3];
-            if (!ct_voxel(&c, x, idx)) break;
+            double Sc;
+            if (!ct_flight(&c, x, dir, E, &r, idx, &Sc)) break;
             double rho; int m;
             ct_props(&c, idx, &rho, &m);
             double mu[3];
             orc_mu_photon(m, E, mu);
             double tot = mu[0] + mu[1] + mu[2];
-            if (!(rng_u(&r) * smax < rho * tot)) continue;
+            if (!(rng_u(&r) * Sc < rho * tot)) continue;
             double xi = rng_u(&r);
             vox[i] = ((int64_t)idx[2] * P->ny + idx[1]) * P->nx + idx[0];
             type[i] = (xi * tot < mu[0]) ? 0 : (xi * tot < mu[0] + mu[1]) ? 1 : 2;
             break;
         }
     }
+    ctx_free(&c);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1153,6 +1235,7 @@ void orc_tmap(const orc_problem* P, const int32_t* ix, const int32_t* iy, int64_
         to_patient(&c, pb, pp);
         t[i] = orc_siddon_ray(P, src, pp);
     }
+    ctx_free(&c);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1213,11 +1296,12 @@ int orc_sample_source_many(const orc_problem* P, uint64_t seed, uint64_t h0, uin
                            double* E) {
     o_ctx c;
     ctx_geometry(&c, P);
-    if (!build_source(&c)) { free(c.rect); free(c.cdf); return 2; }
+    if (!build_source(&c)) { free(c.rect); free(c.cdf); ctx_free(&c); return 2; }
     for (uint64_t i = 0; i < n; i++) {
         o_rng r; hook_rng(&r, seed, h0 + i);
         sample_source(&c, &r, &X[i], &Y[i], &E[i]);
     }
     free(c.rect); free(c.cdf);
+    ctx_free(&c);
     return 0;
 }

@@ -14,10 +14,11 @@ import numpy as np
 from . import build as _build
 
 MAX_LAYERS = 8
-NUM_COUNTERS = 16
+NUM_COUNTERS = 20
 COUNTER_NAMES = ("flights_ct", "real_ct", "compton", "photo", "pair", "esteps_ct", "esteps_epid",
                  "moller", "brem", "primaries_at_epid", "uncollided_at_epid", "lost", "flights_epid",
-                 "electrons", "positrons", "secondary_photons")
+                 "electrons", "positrons", "secondary_photons", "warp_iters_photon_ct", "live_lanes_photon_ct",
+                 "warp_iters_electron_ct", "live_lanes_electron_ct")
 STATUS = {0: "MC_OK", 1: "MC_ERR_ARG", 2: "MC_ERR_CUDA", 3: "MC_ERR_OOM", 4: "MC_ERR_STATE",
           5: "MC_ERR_TIMEOUT", 6: "MC_ERR_CANCELLED", 7: "MC_ERR_NUMERIC", 8: "MC_ERR_OVERFLOW"}
 

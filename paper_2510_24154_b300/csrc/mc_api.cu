@@ -49,6 +49,8 @@ struct mc_ctx {
     float* d_thr = nullptr;
     float rho_max[4] = {0, 0, 0, 0};
     float thr[3] = {0, 0, 0};
+    int mgM = 4, mg[3] = {1, 1, 1};
+    float2* d_mgrid = nullptr;
     mc_epid_desc epid{};
     double zp[MC_MAX_LAYERS + 1] = {};
     // field
@@ -169,6 +171,8 @@ void make_params(const mc_ctx* c, Params& P, uint64_t seed) {
     P.ivx = 1.0f / P.vx; P.ivy = 1.0f / P.vy; P.ivz = 1.0f / P.vz;
     P.rho = c->d_rho;
     for (int m = 0; m < 4; ++m) P.rho_max[m] = c->rho_max[m];
+    P.mgM = c->mgM; P.mgx = c->mg[0]; P.mgy = c->mg[1]; P.mgz = c->mg[2];
+    P.mgrid = c->d_mgrid;
     for (int k = 0; k < 3; ++k) {
         P.thr[k] = c->thr[k];
         P.ex[k] = static_cast<float>(c->ex[k]);
@@ -341,6 +345,7 @@ mc_status mc_create(const mc_config* cfg_in, int device, mc_ctx** out) {
     cudaMemset(c->d_events, 0, sizeof(unsigned long long) * mc::kNumEvents);
 
     c->block = cfg.block_size;
+    if (mc::transport_prepare() != cudaSuccess) return bail(MC_ERR_CUDA);
     for (int t = 0; t < mc::kNumBanks; ++t) {
         int occ = 0;
         c->minb[t] = cfg.regs_variant[t];
@@ -366,6 +371,7 @@ mc_status mc_destroy(mc_ctx* c) {
     dfree(c->d_rho);
     dfree(c->d_rho_max);
     dfree(c->d_thr);
+    dfree(c->d_mgrid);
     dfree(c->d_energy);
     dfree(c->d_events);
     dfree(c->d_nb);
@@ -412,6 +418,19 @@ mc_status mc_init_geometry(mc_ctx* c, const int16_t* hu, int nx, int ny, int nz,
     CUDA_TRY(c, cudaMemcpyAsync(c->thr, c->d_thr, sizeof(c->thr), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
     for (int m = 0; m < 4; ++m) std::memcpy(&c->rho_max[m], &bits[m], sizeof(float));
+    // macro-cells: M the smallest power of two >= 4 giving at most 4096 cells
+    int M = 4;
+    for (;;) {
+        const long cells = static_cast<long>((nx + M - 1) / M) * ((ny + M - 1) / M) * ((nz + M - 1) / M);
+        if (cells <= mc::kMaxMacroCells) break;
+        M *= 2;
+    }
+    c->mgM = M;
+    c->mg[0] = (nx + M - 1) / M; c->mg[1] = (ny + M - 1) / M; c->mg[2] = (nz + M - 1) / M;
+    if (!c->d_mgrid) CUDA_TRY(c, cudaMalloc(&c->d_mgrid, sizeof(float2) * mc::kMaxMacroCells));
+    CUDA_TRY(c, mc::launch_macro_grid(c->d_rho, nx, ny, nz, M, c->mg[0], c->mg[1], c->mg[2], c->thr[2], c->d_mgrid,
+                                      c->sm_count, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
     c->nx = nx; c->ny = ny; c->nz = nz;
     for (int k = 0; k < 3; ++k) { c->vox[k] = vox_cm[k]; c->origin[k] = origin_cm[k]; }
     c->epid = E;

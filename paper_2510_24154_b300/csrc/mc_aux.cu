@@ -20,6 +20,20 @@ __device__ __forceinline__ float rho_of_hu(int hu) {
     return fmaxf(r, 0.001205f);
 }
 
+// Per macro-cell (M^3 voxels) maxima of the non-bone and the bone densities:
+// the local Woodcock majorants.  Positive floats order like their bit patterns.
+__global__ void k_macro_grid(const float* __restrict__ rho, int nx, int ny, int nz, int M, int mgx, int mgy,
+                             float thr_bone, unsigned int* __restrict__ grid) {
+    const size_t n = static_cast<size_t>(nx) * ny * nz;
+    const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+    for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int ix = static_cast<int>(i % nx), iy = static_cast<int>((i / nx) % ny), iz = static_cast<int>(i / (static_cast<size_t>(nx) * ny));
+        const float r = rho[i];
+        const size_t cc = (static_cast<size_t>(iz / M) * mgy + iy / M) * mgx + ix / M;
+        atomicMax(&grid[2 * cc + (r >= thr_bone ? 1 : 0)], __float_as_uint(r));
+    }
+}
+
 __global__ void k_hu_to_rho(const int16_t* __restrict__ hu, float* __restrict__ rho, size_t n,
                             unsigned int* rho_max_bits, float* thr) {
     __shared__ unsigned int s_max[4];
@@ -240,6 +254,15 @@ cudaError_t launch_hu_to_rho(const int16_t* hu, float* rho, size_t n, unsigned i
     int grid = static_cast<int>(want < static_cast<size_t>(sm_count) * 8 ? want : static_cast<size_t>(sm_count) * 8);
     if (grid < 1) grid = 1;
     k_hu_to_rho<<<grid, block, 0, s>>>(hu, rho, n, rho_max_bits, thr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro_grid(const float* rho, int nx, int ny, int nz, int M, int mgx, int mgy, int mgz,
+                              float thr_bone, float2* grid, int sm_count, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(grid, 0, sizeof(float2) * static_cast<size_t>(mgx) * mgy * mgz, s);
+    if (e != cudaSuccess) return e;
+    k_macro_grid<<<sm_count * 8, 256, 0, s>>>(rho, nx, ny, nz, M, mgx, mgy, thr_bone,
+                                              reinterpret_cast<unsigned int*>(grid));
     return cudaGetLastError();
 }
 

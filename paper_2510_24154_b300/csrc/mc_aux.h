@@ -22,6 +22,7 @@ struct TmapArgs {
 };
 
 size_t transport_smem(int type);
+cudaError_t transport_prepare();
 cudaError_t transport_occupancy(int type, int minb, int block, int* blocks_per_sm);
 cudaError_t launch_transport(int type, int minb, const Params& P, int grid, int block, cudaStream_t s);
 cudaError_t launch_swap(Ctl* c, int t, cudaStream_t s);
@@ -29,6 +30,8 @@ cudaError_t launch_wave_begin(Ctl* c, unsigned long long per_wave, cudaStream_t 
 
 cudaError_t launch_hu_to_rho(const int16_t* hu, float* rho, size_t n, unsigned int* rho_max_bits, float* thr,
                              int sm_count, cudaStream_t s);
+cudaError_t launch_macro_grid(const float* rho, int nx, int ny, int nz, int M, int mgx, int mgy, int mgz,
+                              float thr_bone, float2* grid, int sm_count, cudaStream_t s);
 cudaError_t launch_tmap(const TmapArgs& A, double* t, cudaStream_t s);
 cudaError_t launch_dose(const unsigned long long* tally, int npix, int B, const double* nb, double n_hist,
                         double conv, double* dose, double* sigma, unsigned long long* max_bits, double* part_sum,

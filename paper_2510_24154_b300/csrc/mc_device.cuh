@@ -11,7 +11,8 @@
 // Random numbers: draw d of the particle with history id h and ordinal o is
 // word d mod 4 of Philox4x32-10 (Salmon et al., SC'11) at counter
 // (d div 4, o, h_lo, h_hi) under key (seed_lo, seed_hi), mapped to
-// ((u >> 9) + 0.5) 2^-23.  Secondaries take the ordinal
+// ((u >> 9) + 0.5) 2^-23; every electron step and photon flight starts at the
+// next multiple of 4.  Secondaries take the ordinal
 // fmix32(parent * 0x85EBCA6B + 8 d + slot + 1) (MurmurHash3 finaliser), with d
 // the parent's draw count when it creates them, so a history's random
 // numbers do not depend on the order in which the GPU processes events.
@@ -27,6 +28,7 @@ constexpr float kTwoMec2 = 1.0219979f;
 constexpr int kPhotonNodes = 2048;
 constexpr int kElectronNodes = 512;
 constexpr int kWentzelNodes = 128;
+constexpr int kMaxMacroCells = 4096;
 constexpr int kNumMat = 7;
 constexpr int kMaxLayers = 8;
 constexpr float kQuantaPerMeV = 2.56e8f;      // tally unit 2^-8 eV
@@ -37,7 +39,8 @@ enum BankType { kPhotonCT = 0, kElectronCT = 1, kPhotonEPID = 2, kElectronEPID =
 enum EnergyCounter { kESrc = 0, kECT = 1, kEEsc = 2, kELost = 3, kEEpid0 = 4, kNumEnergy = 12 };
 enum EventCounter {
     kCFlightsCT = 0, kCRealCT, kCCompton, kCPhoto, kCPair, kCEStepsCT, kCEStepsEPID, kCMoller, kCBrem,
-    kCPrimAtEPID, kCUncollided, kCLost, kCFlightsEPID, kCElectrons, kCPositrons, kCPhotons2, kNumEvents
+    kCPrimAtEPID, kCUncollided, kCLost, kCFlightsEPID, kCElectrons, kCPositrons, kCPhotons2,
+    kCItersPCT, kCLivePCT, kCItersECT, kCLiveECT, kNumEvents
 };
 enum Flags : uint32_t { kPositron = 1u, kCollided = 2u };
 enum ErrorBits : uint32_t { kErrOverflow = 1u, kErrNonFinite = 2u };
@@ -70,6 +73,8 @@ struct Params {
     const float* rho;
     float rho_max[4];
     float thr[3];                   // density thresholds lung / water / bone
+    int mgM, mgx, mgy, mgz;         // macro-cells: M voxels per side, cells per axis (<= 4096 cells)
+    const float2* mgrid;            // per macro-cell (max density of non-bone voxels, of bone voxels)
     // beam frame axes in patient coordinates, isocentre, source distance
     float ex[3], ey[3], ez[3], iso[3];
     float sad;
@@ -146,6 +151,9 @@ struct Rng {
         const uint4 r = philox4x32_10(make_uint4(d >> 2, ord, hlo, hhi), k0, k1);
         w0 = r.x; w1 = r.y; w2 = r.z; w3 = r.w;
     }
+    // Electron steps and photon flights start on a fresh Philox block, so the
+    // lanes of a warp refill together.
+    __device__ __forceinline__ void align() { d = (d + 3u) & ~3u; }
     __device__ __forceinline__ float u() {
         if ((d & 3u) == 0u) refill();
         const uint32_t j = d & 3u;

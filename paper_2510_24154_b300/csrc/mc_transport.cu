@@ -25,6 +25,7 @@ namespace {
 struct Acc {
     unsigned long long ct, src, esc, lost;
     uint32_t flights, steps;
+    uint32_t iters, live;       // warp iterations and live lanes (lane 0 counts)
 };
 
 __device__ __forceinline__ void acc_flush(const Params& P, Acc& a, unsigned long long* s_energy,
@@ -269,35 +270,76 @@ __device__ __forceinline__ float ct_dist(const Params& P, const Part& p, uint32_
 }
 
 // ---------------------------------------------------------------------------
-// One Woodcock flight of a CT photon.  Returns false when the photon leaves
-// the event type (absorbed, escaped, or moved to the EPID: `move`).
-__device__ __forceinline__ bool photon_ct_event(const Params& P, const float2* tab, Acc& a,
+// One Woodcock flight of a CT photon with a piecewise-constant majorant: an
+// optical depth tau = -ln(xi) is spent across macro-cells, each with majorant
+// max(rho_low,c mu_low(E), rho_bone,c mu_bone(E)) (3D-DDA over the cells); where
+// it runs out, the tentative collision in the voxel below (kept inside the
+// cell) is real with probability Sigma_voxel / Sigma_c.  Returns false when the
+// photon leaves the event type (absorbed, escaped, or moved to the EPID: `move`).
+__device__ __forceinline__ bool photon_ct_event(const Params& P, const float2* tab, const float2* grid, Acc& a,
                                                 unsigned long long* s_energy, unsigned long long* s_events,
                                                 Part& p, Emit& e0, Emit& e1, bool& move) {
     const PhotonXS xs = photon_xs(tab, P, p.E);
     float tot[4];
-    float smax = 0.0f;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         float c, q, r;
         photon_mu(P, m, xs, c, q, r);
         tot[m] = c + q + r;
-        smax = fmaxf(smax, P.rho_max[m] * tot[m]);
     }
-    const float s = -logf(p.rng.u()) / smax;
-    p.x += s * p.u; p.y += s * p.v; p.z += s * p.w;
+    const float mul = fmaxf(tot[0], fmaxf(tot[1], tot[2])), mub = tot[3];
+    p.rng.align();
+    float tau = -logf(p.rng.u());
     ++a.flights;
-    const int ix = __float2int_rd((p.x - P.ox) / P.vx);
-    const int iy = __float2int_rd((p.y - P.oy) / P.vy);
-    const int iz = __float2int_rd((p.z - P.oz) / P.vz);
-    if (ix < 0 || ix >= P.nx || iy < 0 || iy >= P.ny || iz < 0 || iz >= P.nz) {
+    const int M = P.mgM;
+    const float iu = 1.0f / p.u, iv = 1.0f / p.v, iw = 1.0f / p.w;
+    int cx = min(max(__float2int_rd((p.x - P.ox) / (M * P.vx)), 0), P.mgx - 1);
+    int cy = min(max(__float2int_rd((p.y - P.oy) / (M * P.vy)), 0), P.mgy - 1);
+    int cz = min(max(__float2int_rd((p.z - P.oz) / (M * P.vz)), 0), P.mgz - 1);
+    float Sc = 0.0f;
+    const int guard = P.mgx + P.mgy + P.mgz + 3;
+    bool inside = false;
+    for (int it = 0; it < guard; ++it) {
+        const float2 g = grid[(cz * P.mgy + cy) * P.mgx + cx];
+        Sc = fmaxf(g.x * mul, g.y * mub);
+        float dx = INFINITY, dy = INFINITY, dz = INFINITY;
+        if (p.u > 0.0f) dx = (P.ox + min((cx + 1) * M, P.nx) * P.vx - p.x) * iu;
+        else if (p.u < 0.0f) dx = (P.ox + cx * M * P.vx - p.x) * iu;
+        if (p.v > 0.0f) dy = (P.oy + min((cy + 1) * M, P.ny) * P.vy - p.y) * iv;
+        else if (p.v < 0.0f) dy = (P.oy + cy * M * P.vy - p.y) * iv;
+        if (p.w > 0.0f) dz = (P.oz + min((cz + 1) * M, P.nz) * P.vz - p.z) * iw;
+        else if (p.w < 0.0f) dz = (P.oz + cz * M * P.vz - p.z) * iw;
+        float d = dx;
+        int ax = 0;
+        if (dy < d) { d = dy; ax = 1; }
+        if (dz < d) { d = dz; ax = 2; }
+        d = fmaxf(d, 0.0f);
+        if (tau < Sc * d) {
+            const float s = tau / Sc;
+            p.x += s * p.u; p.y += s * p.v; p.z += s * p.w;
+            inside = true;
+            break;
+        }
+        tau -= Sc * d;
+        p.x += d * p.u; p.y += d * p.v; p.z += d * p.w;
+        bool out;
+        if (ax == 0) { cx += (p.u > 0.0f) ? 1 : -1; out = cx < 0 || cx >= P.mgx; }
+        else if (ax == 1) { cy += (p.v > 0.0f) ? 1 : -1; out = cy < 0 || cy >= P.mgy; }
+        else { cz += (p.w > 0.0f) ? 1 : -1; out = cz < 0 || cz >= P.mgz; }
+        if (out) break;
+    }
+    if (!inside) {
         move = transfer_to_epid(P, p, a, s_events, true);
         return false;
     }
+    // the voxel under the tentative collision, kept inside its macro-cell
+    const int ix = min(max(__float2int_rd((p.x - P.ox) / P.vx), cx * M), min((cx + 1) * M, P.nx) - 1);
+    const int iy = min(max(__float2int_rd((p.y - P.oy) / P.vy), cy * M), min((cy + 1) * M, P.ny) - 1);
+    const int iz = min(max(__float2int_rd((p.z - P.oz) / P.vz), cz * M), min((cz + 1) * M, P.nz) - 1);
     const float rho = __ldg(&P.rho[(static_cast<size_t>(iz) * P.ny + iy) * P.nx + ix]);
     const int m = material_of(P, rho);
     const float tm = (m == 0) ? tot[0] : (m == 1) ? tot[1] : (m == 2) ? tot[2] : tot[3];
-    if (!(p.rng.u() * smax < rho * tm)) return true;          // virtual
+    if (!(p.rng.u() * Sc < rho * tm)) return true;            // virtual
     atomicAdd(&s_events[kCRealCT], 1ull);
     p.cell = pack_cell(ix, iy, iz);
     float mc, mp, mq;
@@ -310,6 +352,7 @@ __device__ __forceinline__ bool photon_epid_event(const Params& P, const float2*
                                                   unsigned long long* s_energy, unsigned long long* s_events,
                                                   Part& p, Emit& e0, Emit& e1) {
     const PhotonXS xs = photon_xs(tab, P, p.E);
+    p.rng.align();
     float tau = -logf(p.rng.u());
     ++a.flights;
     for (int guard = 0; guard < 4 * kMaxLayers + 8; ++guard) {
@@ -362,6 +405,7 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
         m = material_of(P, rho);
     }
     ++a.steps;
+    p.rng.align();
     const MatC& mcst = P.mat[m];
     const float T = p.E;
     // (a) energy-loss step with the midpoint stopping power
@@ -496,6 +540,7 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
 // back-to-back photons with the ordinals of slots 0 and 1.
 __device__ __forceinline__ void flush_emission(const Params& P, const Emit& e, const Part& parent, int own_type,
                                                uint32_t own_in) {
+    if (__ballot_sync(kFull, e.dest >= 0) == 0u) return;        // the common case: nothing to write
     const bool pairrec = (e.dest >= 0) && (e.flags & 0x80000000u);
     const uint32_t n = (e.dest >= 0) ? (pairrec ? 2u : 1u) : 0u;
 #pragma unroll
@@ -608,6 +653,11 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
 
     const float2* gtab = kPhoton ? P.ptab : P.etab;
     for (int i = threadIdx.x; i < kTabN; i += blockDim.x) s_tab[i] = __ldg(&gtab[i]);
+    float2* s_grid = s_tab + kTabN;                 // macro-cell majorants (CT photons only)
+    if (TYPE == kPhotonCT) {
+        const int ncell = P.mgx * P.mgy * P.mgz;
+        for (int i = threadIdx.x; i < ncell; i += blockDim.x) s_grid[i] = __ldg(&P.mgrid[i]);
+    }
     for (int i = threadIdx.x; i < kNumEnergy; i += blockDim.x) s_energy[i] = 0ull;
     for (int i = threadIdx.x; i < kNumEvents; i += blockDim.x) s_events[i] = 0ull;
     __syncthreads();
@@ -620,7 +670,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
     const bool may_flush = P.ctl->allow_flush != 0u;
     const uint32_t move_par = kEpid ? 0u : P.ctl->cur[kMoveTo];
 
-    Acc acc = {0ull, 0ull, 0ull, 0ull, 0u, 0u};
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0u, 0u, 0u, 0u};
     Part p;
     bool alive = false;
     bool in_open = true;
@@ -671,12 +721,13 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
             alive = false;
             break;
         }
+        if (lane_id() == 0) { ++acc.iters; acc.live += __popc(live); }
         Emit e0, e1;
         emit_none(e0);
         emit_none(e1);
         if (alive) {
             bool keep;
-            if (TYPE == kPhotonCT) keep = photon_ct_event(P, s_tab, acc, s_energy, s_events, p, e0, e1, move);
+            if (TYPE == kPhotonCT) keep = photon_ct_event(P, s_tab, s_grid, acc, s_energy, s_events, p, e0, e1, move);
             else if (TYPE == kPhotonEPID) keep = photon_epid_event(P, s_tab, acc, s_energy, s_events, p, e0, e1);
             else keep = electron_event<kEpid>(P, s_tab, acc, s_energy, s_events, p, e0, e1, move);
             if (keep && ++steps_here > P.max_steps) {
@@ -693,6 +744,10 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
 
     acc_flush(P, acc, s_energy, s_events, kPhoton ? (kEpid ? kCFlightsEPID : kCFlightsCT) : kCFlightsCT,
               kEpid ? kCEStepsEPID : kCEStepsCT);
+    if (!kEpid && lane_id() == 0 && acc.iters) {
+        atomicAdd(&s_events[kPhoton ? kCItersPCT : kCItersECT], static_cast<unsigned long long>(acc.iters));
+        atomicAdd(&s_events[kPhoton ? kCLivePCT : kCLiveECT], static_cast<unsigned long long>(acc.live));
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < kNumEnergy; i += blockDim.x)
         if (s_energy[i]) atomicAdd(&P.energy[i], s_energy[i]);
@@ -723,7 +778,9 @@ __global__ void k_wave_begin(Ctl* c, unsigned long long per_wave) {
 
 size_t transport_smem(int type) {
     const bool photon = (type == kPhotonCT || type == kPhotonEPID);
-    return sizeof(float2) * (photon ? kPhotonNodes : kNumMat * kElectronNodes + kWentzelNodes / 2);
+    size_t n = photon ? kPhotonNodes : kNumMat * kElectronNodes + kWentzelNodes / 2;
+    if (type == kPhotonCT) n += kMaxMacroCells;
+    return sizeof(float2) * n;
 }
 
 // Each event type is built for 2, 3 and 4 resident CTAs of 256 threads per SM
@@ -744,6 +801,18 @@ static const void* transport_fn(int type, int minb) {
         case kPhotonEPID: return fn_for<kPhotonEPID>(minb);
         default: return fn_for<kElectronEPID>(minb);
     }
+}
+
+// Allows each transport kernel its full dynamic shared memory (the CT-photon
+// kernel stages 48 KB: photon table and macro-cell majorants).
+cudaError_t transport_prepare() {
+    for (int t = 0; t < kNumBanks; ++t)
+        for (int mb = 2; mb <= 4; ++mb) {
+            const cudaError_t e = cudaFuncSetAttribute(transport_fn(t, mb), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       static_cast<int>(transport_smem(t)));
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
 }
 
 cudaError_t transport_occupancy(int type, int minb, int block, int* blocks_per_sm) {

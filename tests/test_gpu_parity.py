@@ -159,7 +159,7 @@ def test_full_size_geometry_replay():
     in the default launch configuration: energy balance, replay of the
     sensitive-layer energy and of the event counts."""
     p = G.thorax_case(n=200_000, scale=1, epid_scale=1)
-    sim, st, gt = G.gpu_run(p)
+    sim, st, gt = G.gpu_run(p, bank_capacity=1 << 24)       # bench.py's launch configuration
     orc = oracle.run(p)
     assert G.energy_closure(st) < 2e-6
     assert gt.sum() == pytest.approx(orc["tally"].sum(), rel=5e-3)
@@ -175,7 +175,8 @@ def test_bitwise_reproducible_across_runs_and_launch_shapes():
     _, st2, t2 = G.gpu_run(p)
     _, st3, t3 = G.gpu_run(p, block_size=128, bank_capacity=1 << 18, primaries_per_wave=1 << 14)
     assert np.array_equal(t1, t2) and np.array_equal(t1, t3)
-    assert st1["counters"] == st3["counters"]
+    physics = oracle.COUNTER_NAMES          # the execution counters depend on the launch shape
+    assert all(st1["counters"][k] == st3["counters"][k] for k in physics)
     assert st1["e_src"] == st3["e_src"] and st1["e_ct"] == st3["e_ct"]
 
 
