@@ -88,6 +88,8 @@ typedef struct mc_config {
     uint32_t bank_capacity;       /* particles per bank, 0 = 1<<23 */
     uint32_t primaries_per_wave;  /* new histories per transport wave, 0 = bank_capacity / 4 */
     int time_kernels;             /* 1: time every transport launch with CUDA events (mc_run_stats.kernel_ms) */
+    int use_graph;                /* 1: each run is one CUDA-graph launch whose waves loop on the device
+                                     (a conditional while-node); 0: waves are driven from the host */
     int regs_variant[4];          /* per transport kernel (CT photons, CT electrons, EPID photons, EPID
                                      electrons): build for 2, 3 or 4 CTAs of 256 threads per SM
                                      (register caps 128 / 85 / 64); 0 = 4 */
@@ -174,28 +176,53 @@ mc_status mc_init_geometry(mc_ctx* ctx, const int16_t* hu, int nx, int ny, int n
  * (then mc_get_epid_image is unavailable). */
 mc_status mc_set_field(mc_ctx* ctx, const mc_field_desc* field, const mc_lut_desc* lut, void* stream);
 
-/* Steps a2-a7: transports n_histories histories (ids continue from the
- * previous run, so repeated calls equal one longer run) with Philox keyed by
- * seed, adding to the tally.  Synchronizes `stream`.  stats may be NULL. */
+/* Steps a2-a7: transports n_histories histories of every field set on the
+ * context (ids continue from the previous run, so repeated calls equal one
+ * longer run) with Philox keyed by seed, adding to the tally.  Synchronizes
+ * `stream`.  stats may be NULL. */
 mc_status mc_run(mc_ctx* ctx, uint64_t n_histories, uint64_t seed, void* stream, mc_run_stats* stats);
 
-/* Step a8: per-history dose (Gy) in the sensitive layer and its batch
+/* Batching (several static fields of one plan on one phantom, Sec. 2.3's 25
+ * IMRT fields): sets n_fields fields (1 .. 256) at once, each with its own
+ * source, beam frame (gantry angle), radiological-thickness map and Eq. 1
+ * field size, sharing the CT, the EPID and the k-table.  Each field keeps its
+ * own tally; field f draws from the same random streams as a single-field run
+ * whose history ids start at f * 2^40 (so a batch equals its fields run one
+ * by one).  Resets the tallies. */
+mc_status mc_set_fields(mc_ctx* ctx, const mc_field_desc* fields, int n_fields, const mc_lut_desc* lut,
+                        void* stream);
+
+/* Transports n_histories[f] histories of every field f in one wave sequence
+ * (one graph launch with use_graph), so fields of uneven sizes share the GPU.
+ * Synchronizes `stream`. */
+mc_status mc_run_batch(mc_ctx* ctx, const uint64_t* n_histories, uint64_t seed, void* stream,
+                       mc_run_stats* stats);
+
+/* Per-field read-outs: as mc_get_dose, mc_get_epid_image, mc_get_tmap and
+ * mc_field_size for field `field` (0 .. n_fields-1). */
+mc_status mc_get_field_dose(mc_ctx* ctx, int field, double* dose, double* sigma, double* u_out, int on_device,
+                            void* stream);
+mc_status mc_get_field_image(mc_ctx* ctx, int field, float* signal, int on_device, void* stream);
+mc_status mc_get_field_tmap(mc_ctx* ctx, int field, double* t, int on_device, void* stream);
+mc_status mc_get_field_size(mc_ctx* ctx, int field, double* s, double* a, double* b);
+
+/* Step a8 (field 0): per-history dose (Gy) in the sensitive layer and its batch
  * standard error, [npy][npx] doubles (host or device per on_device); sigma
  * may be NULL.  u_out (host, may be NULL) receives the mean relative
  * uncertainty over pixels above half the maximum dose. */
 mc_status mc_get_dose(mc_ctx* ctx, double* dose, double* sigma, double* u_out, int on_device, void* stream);
 
-/* Step a11 (Sec. 3.1): signal = k_scale * k(t, s) * dose per pixel, float32
+/* Step a11 (Sec. 3.1, field 0): signal = k_scale * k(t, s) * dose per pixel, float32
  * [npy][npx] (host or device per on_device). */
 mc_status mc_get_epid_image(mc_ctx* ctx, float* signal, int on_device, void* stream);
 
-/* The radiological thickness map t (cm, FP64) of the current field. */
+/* The radiological thickness map t (cm, FP64) of field 0. */
 mc_status mc_get_tmap(mc_ctx* ctx, double* t, int on_device, void* stream);
 
-/* Raw integer sub-tallies [B][npy][npx], unit 2^-8 eV. */
+/* Raw integer sub-tallies [n_fields][B][npy][npx], unit 2^-8 eV. */
 mc_status mc_get_tally(mc_ctx* ctx, uint64_t* tally, int on_device, void* stream);
 
-/* Equivalent square s (Eq. 1 reading) and bounding rectangle sides a, b (cm). */
+/* Equivalent square s (Eq. 1 reading) and bounding rectangle sides a, b (cm) of field 0. */
 mc_status mc_field_size(mc_ctx* ctx, double* s, double* a, double* b);
 
 /* Cumulative statistics (energy balance from the fixed-point counters). */
@@ -212,7 +239,7 @@ mc_status mc_state_size(mc_ctx* ctx, size_t* bytes);
 mc_status mc_get_state(mc_ctx* ctx, void* host_buf, size_t bytes, void* stream);
 mc_status mc_set_state(mc_ctx* ctx, const void* host_buf, size_t bytes, void* stream);
 
-/* Sets the id of the next history (sharding: rank r of R running n histories
+/* Sets the id of the next history of every field (sharding: rank r of R running n histories
  * each starts at r * n, and the union of the shards equals one run of R * n
  * histories).  Does not clear the tally. */
 mc_status mc_set_history_base(mc_ctx* ctx, uint64_t next_history);

@@ -24,7 +24,8 @@ STATUS = {0: "MC_OK", 1: "MC_ERR_ARG", 2: "MC_ERR_CUDA", 3: "MC_ERR_OOM", 4: "MC
 
 # Every entry point declared in include/archer_epid.h.
 EXPORTED = ("mc_config_default", "mc_create", "mc_destroy", "mc_init_geometry", "mc_set_field", "mc_run",
-            "mc_get_dose", "mc_get_epid_image", "mc_get_tmap", "mc_get_tally", "mc_field_size", "mc_get_stats",
+            "mc_set_fields", "mc_run_batch", "mc_get_field_dose", "mc_get_field_image", "mc_get_field_tmap",
+            "mc_get_field_size", "mc_get_dose", "mc_get_epid_image", "mc_get_tmap", "mc_get_tally", "mc_field_size", "mc_get_stats",
             "mc_reset_tally", "mc_state_size", "mc_get_state", "mc_set_state", "mc_set_history_base", "mc_cancel",
             "mc_last_error",
             "mc_status_string", "mc_test_philox", "mc_test_uniforms", "mc_dose_stats_noalloc")
@@ -36,7 +37,7 @@ class Config(C.Structure):
                 ("wcc_mev", C.c_double), ("wcb_mev", C.c_double), ("step_fraction", C.c_double),
                 ("n_batches", C.c_int), ("max_steps", C.c_int), ("block_size", C.c_int),
                 ("ctas_per_sm", C.c_int), ("bank_capacity", C.c_uint32), ("primaries_per_wave", C.c_uint32),
-                ("time_kernels", C.c_int), ("regs_variant", C.c_int * 4)]
+                ("time_kernels", C.c_int), ("use_graph", C.c_int), ("regs_variant", C.c_int * 4)]
 
 
 class EpidDesc(C.Structure):
@@ -97,6 +98,12 @@ def load(build_if_stale: bool = True):
     lib.mc_init_geometry.argtypes = [vp, vp, i, i, i, P(d), P(d), P(EpidDesc), i, vp]
     lib.mc_set_field.argtypes = [vp, P(FieldDesc), P(LutDesc), vp]
     lib.mc_run.argtypes = [vp, u64, u64, vp, P(RunStats)]
+    lib.mc_set_fields.argtypes = [vp, P(FieldDesc), i, P(LutDesc), vp]
+    lib.mc_run_batch.argtypes = [vp, P(u64), u64, vp, P(RunStats)]
+    lib.mc_get_field_dose.argtypes = [vp, i, vp, vp, P(d), i, vp]
+    lib.mc_get_field_image.argtypes = [vp, i, vp, i, vp]
+    lib.mc_get_field_tmap.argtypes = [vp, i, vp, i, vp]
+    lib.mc_get_field_size.argtypes = [vp, i, P(d), P(d), P(d)]
     lib.mc_get_dose.argtypes = [vp, vp, vp, P(d), i, vp]
     lib.mc_get_epid_image.argtypes = [vp, vp, i, vp]
     lib.mc_get_tmap.argtypes = [vp, vp, i, vp]
@@ -177,6 +184,7 @@ class Simulator:
         self.h = h
         self.device = device
         self.epid = None
+        self.n_fields = 0
         self._keep = []
 
     def _check(self, st, h="self"):
@@ -217,35 +225,64 @@ class Simulator:
                                               _stream_ptr(stream)))
         self.epid = epid
 
-    def set_field(self, field, lut=None, stream=None):
-        """a2 set-up, a9 t-map, a10 Eq. 1, k-table upload; resets the tally."""
+    @staticmethod
+    def _field_desc(field, lut, keep):
         edges = np.ascontiguousarray(field.pair_edges, dtype=np.float64)
         leaves = np.ascontiguousarray(field.leaves, dtype=np.float64)
         jaws = np.ascontiguousarray(field.jaws, dtype=np.float64)
         mu = np.ascontiguousarray(field.mu, dtype=np.float64)
+        keep += [edges, leaves, jaws, mu]
         f = FieldDesc()
         f.n_segments, f.n_pairs = leaves.shape[0], leaves.shape[1]
         f.pair_edges_cm, f.leaves_cm, f.jaws_cm, f.mu = _dp(edges), _dp(leaves), _dp(jaws), _dp(mu)
         f.gantry_deg, f.sad_cm, f.sid_cm = field.gantry_deg, field.sad, field.sid
         f.iso_cm[:] = [float(v) for v in field.iso]
         f.eq1_literal = int(lut.eq1_literal) if lut is not None else 0
-        lp = None
-        if lut is not None:
-            tn = np.ascontiguousarray(lut.t_nodes, dtype=np.float64)
-            sn = np.ascontiguousarray(lut.s_nodes, dtype=np.float64)
-            k = np.ascontiguousarray(lut.k, dtype=np.float64)
-            L = LutDesc()
-            L.nt, L.ns = tn.size, sn.size
-            L.t_nodes, L.s_nodes, L.k = _dp(tn), _dp(sn), _dp(k)
-            L.k_scale, L.t_offset_cm = lut.k_scale, lut.t_offset
-            lp = C.byref(L)
+        return f
+
+    @staticmethod
+    def _lut_desc(lut, keep):
+        if lut is None:
+            return None
+        tn = np.ascontiguousarray(lut.t_nodes, dtype=np.float64)
+        sn = np.ascontiguousarray(lut.s_nodes, dtype=np.float64)
+        k = np.ascontiguousarray(lut.k, dtype=np.float64)
+        keep += [tn, sn, k]
+        L = LutDesc()
+        L.nt, L.ns = tn.size, sn.size
+        L.t_nodes, L.s_nodes, L.k = _dp(tn), _dp(sn), _dp(k)
+        L.k_scale, L.t_offset_cm = lut.k_scale, lut.t_offset
+        keep.append(L)
+        return C.byref(L)
+
+    def set_field(self, field, lut=None, stream=None):
+        """a2 set-up, a9 t-map, a10 Eq. 1, k-table upload; resets the tally."""
+        keep = []
+        f = self._field_desc(field, lut, keep)
+        lp = self._lut_desc(lut, keep)
         self._check(self.lib.mc_set_field(self.h, C.byref(f), lp, _stream_ptr(stream)))
+        self.n_fields = 1
+
+    def set_fields(self, fields, lut=None, stream=None):
+        """a12: several fields of one plan (own source, gantry angle, t-map, s and tally each)."""
+        keep = []
+        arr = (FieldDesc * len(fields))(*[self._field_desc(f, lut, keep) for f in fields])
+        lp = self._lut_desc(lut, keep)
+        self._check(self.lib.mc_set_fields(self.h, arr, len(fields), lp, _stream_ptr(stream)))
+        self.n_fields = len(fields)
 
     # -- transport ------------------------------------------------------------
     def run(self, n_histories, seed, stream=None) -> dict:
         """a2-a7: transport n_histories more histories."""
         st = RunStats()
         self._check(self.lib.mc_run(self.h, int(n_histories), int(seed), _stream_ptr(stream), C.byref(st)))
+        return stats_dict(st)
+
+    def run_batch(self, n_histories, seed, stream=None) -> dict:
+        """a12: n_histories[f] more histories of every field f, in one wave sequence."""
+        n = (C.c_uint64 * self.n_fields)(*[int(v) for v in n_histories])
+        st = RunStats()
+        self._check(self.lib.mc_run_batch(self.h, n, int(seed), _stream_ptr(stream), C.byref(st)))
         return stats_dict(st)
 
     def stats(self) -> dict:
@@ -257,46 +294,54 @@ class Simulator:
     def _npix(self):
         return self.epid.npy, self.epid.npx
 
-    def dose(self, stream=None, with_sigma=True):
+    def dose(self, stream=None, with_sigma=True, field=0):
         """a8: (dose, sigma, u) as numpy arrays (Gy per history) and the scalar u."""
         ny, nx = self._npix()
         d = np.empty((ny, nx))
         s = np.empty((ny, nx)) if with_sigma else None
         u = C.c_double()
-        self._check(self.lib.mc_get_dose(self.h, C.c_void_p(d.ctypes.data),
-                                         C.c_void_p(s.ctypes.data) if s is not None else None,
-                                         C.byref(u) if with_sigma else None, 0, _stream_ptr(stream)))
+        self._check(self.lib.mc_get_field_dose(self.h, int(field), C.c_void_p(d.ctypes.data),
+                                               C.c_void_p(s.ctypes.data) if s is not None else None,
+                                               C.byref(u) if with_sigma else None, 0, _stream_ptr(stream)))
         return d, s, u.value
 
-    def dose_device(self, dose, sigma=None, stream=None):
-        self._check(self.lib.mc_get_dose(self.h, _ptr(dose), _ptr(sigma) if sigma is not None else None, None, 1,
-                                         _stream_ptr(stream)))
+    def dose_device(self, dose, sigma=None, stream=None, field=0):
+        self._check(self.lib.mc_get_field_dose(self.h, int(field), _ptr(dose),
+                                               _ptr(sigma) if sigma is not None else None, None, 1,
+                                               _stream_ptr(stream)))
 
-    def epid_image(self, stream=None):
+    def epid_image(self, stream=None, field=0):
         """a11: k(t, s)-corrected signal, float32 numpy [npy][npx]."""
         ny, nx = self._npix()
         out = np.empty((ny, nx), dtype=np.float32)
-        self._check(self.lib.mc_get_epid_image(self.h, C.c_void_p(out.ctypes.data), 0, _stream_ptr(stream)))
+        self._check(self.lib.mc_get_field_image(self.h, int(field), C.c_void_p(out.ctypes.data), 0,
+                                                _stream_ptr(stream)))
         return out
 
-    def epid_image_device(self, out, stream=None):
-        self._check(self.lib.mc_get_epid_image(self.h, _ptr(out), 1, _stream_ptr(stream)))
+    def epid_image_device(self, out, stream=None, field=0):
+        self._check(self.lib.mc_get_field_image(self.h, int(field), _ptr(out), 1, _stream_ptr(stream)))
 
-    def tmap(self, stream=None):
+    def tmap(self, stream=None, field=0):
         ny, nx = self._npix()
         out = np.empty((ny, nx))
-        self._check(self.lib.mc_get_tmap(self.h, C.c_void_p(out.ctypes.data), 0, _stream_ptr(stream)))
+        self._check(self.lib.mc_get_field_tmap(self.h, int(field), C.c_void_p(out.ctypes.data), 0,
+                                               _stream_ptr(stream)))
         return out
 
-    def tally(self, stream=None):
+    def tally_all(self, stream=None):
+        """Raw sub-tallies of every field, uint64 [n_fields][B][npy][npx] (unit 2^-8 eV)."""
         ny, nx = self._npix()
-        out = np.empty((self.cfg.n_batches, ny, nx), dtype=np.uint64)
+        out = np.empty((self.n_fields, self.cfg.n_batches, ny, nx), dtype=np.uint64)
         self._check(self.lib.mc_get_tally(self.h, C.c_void_p(out.ctypes.data), 0, _stream_ptr(stream)))
         return out
 
-    def field_size(self):
+    def tally(self, stream=None, field=0):
+        """Raw sub-tallies of one field, uint64 [B][npy][npx]."""
+        return self.tally_all(stream)[field]
+
+    def field_size(self, field=0):
         s, a, b = C.c_double(), C.c_double(), C.c_double()
-        self._check(self.lib.mc_field_size(self.h, C.byref(s), C.byref(a), C.byref(b)))
+        self._check(self.lib.mc_get_field_size(self.h, int(field), C.byref(s), C.byref(a), C.byref(b)))
         return s.value, a.value, b.value
 
     def set_history_base(self, next_history):

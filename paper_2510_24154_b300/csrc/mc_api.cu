@@ -1,5 +1,6 @@
 // C ABI of the EPID transit Monte Carlo library (declared in archer_epid.h):
-// context lifecycle, geometry and field set-up, the transport wave loop,
+// context lifecycle, geometry and field set-up, the transport wave loop
+// (driven from the host, or one CUDA graph whose waves loop on the device),
 // statistics, the dose-to-signal correction and checkpointing.
 #include <algorithm>
 #include <atomic>
@@ -7,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "archer_epid.h"
@@ -16,7 +18,28 @@
 
 using mc::BankPtr;
 using mc::Ctl;
+using mc::FieldDev;
 using mc::Params;
+
+namespace {
+
+// Host copy of one field: beam frame, source rectangles, Eq. 1 and how many
+// of its histories have run (the next history index of its stream).
+struct FieldHost {
+    double ex[3], ey[3], ez[3], iso[3];
+    double sad, sid, zface;
+    int rect_off, n_rect;
+    double s_eq, bbox_a, bbox_b;
+    uint64_t stream_base;     // random-stream id of the field's history 0 (f * 2^40)
+    uint64_t hist_done;
+};
+
+constexpr double kQuantaPerMeV = 2.56e8;
+constexpr double kJoulePerMeV = 1.602176634e-13;
+constexpr uint64_t kFieldStride = 1ull << 40;
+constexpr unsigned int kMaxWaves = 1000000u;
+
+}  // namespace
 
 struct mc_ctx {
     int device = 0;
@@ -52,26 +75,25 @@ struct mc_ctx {
     int mgM = 4, mg[3] = {1, 1, 1};
     float2* d_mgrid = nullptr;
     mc_epid_desc epid{};
-    double zp[MC_MAX_LAYERS + 1] = {};
-    // field
+    double zp[MC_MAX_LAYERS + 1] = {};   // layer planes, beam frame, sensitive-layer centre at 0
+    // fields
+    std::vector<FieldHost> fields;
     bool has_field = false;
-    double ex[3], ey[3], ez[3], iso[3], sad = 100, sid = 150;
-    int n_rect = 0;
+    FieldDev* d_fields = nullptr;
+    unsigned long long* d_first = nullptr;
     float4* d_rect = nullptr;
     double* d_cdf = nullptr;
-    double s_eq = 0, bbox_a = 0, bbox_b = 0;
-    double* d_tmap = nullptr;
+    double* d_tmap = nullptr;    // [F][npix]
     bool has_lut = false;
     int lut_nt = 0;
     double* d_lut_t = nullptr;
-    double* d_lut_ks = nullptr;
+    double* d_lut_ks = nullptr;  // [F][nt]: the k-table column at each field's s
     double k_scale = 1.0, t_offset = 0.0;
     // tallies
-    unsigned long long* d_tally = nullptr;
+    unsigned long long* d_tally = nullptr;   // [F][B][npix]
     size_t tally_n = 0;
     unsigned long long* d_energy = nullptr;
     unsigned long long* d_events = nullptr;
-    uint64_t hist_done = 0;
     // statistics scratch
     double* d_dose = nullptr;
     double* d_sigma = nullptr;
@@ -82,12 +104,13 @@ struct mc_ctx {
     unsigned int* d_partc = nullptr;
     float* d_signal = nullptr;
     int last_waves = 0;
+    uint32_t last_error = 0;
+    double last_ms = 0;
     double last_kernel_ms[4] = {0, 0, 0, 0};
     uint32_t last_kernel_launches[4] = {0, 0, 0, 0};
     uint32_t last_launches = 0;
     std::vector<cudaEvent_t> ev_pool;
-    uint32_t last_error = 0;
-    double last_ms = 0;
+    cudaStream_t capture_stream = nullptr;
 };
 
 namespace {
@@ -113,8 +136,8 @@ void dfree(T*& p) {
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
-constexpr double kQuantaPerMeV = 2.56e8;
-constexpr double kJoulePerMeV = 1.602176634e-13;
+int npix(const mc_ctx* c) { return c->epid.npx * c->epid.npy; }
+int nfields(const mc_ctx* c) { return static_cast<int>(c->fields.size()); }
 
 void free_field(mc_ctx* c) {
     dfree(c->d_rect);
@@ -128,37 +151,17 @@ void free_field(mc_ctx* c) {
     dfree(c->d_partc);
     dfree(c->d_signal);
     dfree(c->d_tally);
+    c->tally_n = 0;
+    c->fields.clear();
     c->has_field = false;
     c->has_lut = false;
-}
-
-int npix(const mc_ctx* c) { return c->epid.npx * c->epid.npy; }
-
-mc_status ensure_tally(mc_ctx* c) {
-    const size_t n = static_cast<size_t>(c->cfg.n_batches) * npix(c);
-    if (c->d_tally && c->tally_n == n) return MC_OK;
-    dfree(c->d_tally);
-    CUDA_TRY(c, cudaMalloc(&c->d_tally, n * sizeof(unsigned long long)));
-    c->tally_n = n;
-    const int parts = (npix(c) + 255) / 256;
-    dfree(c->d_dose);
-    dfree(c->d_sigma);
-    dfree(c->d_part);
-    dfree(c->d_partc);
-    dfree(c->d_signal);
-    CUDA_TRY(c, cudaMalloc(&c->d_dose, sizeof(double) * npix(c)));
-    CUDA_TRY(c, cudaMalloc(&c->d_sigma, sizeof(double) * npix(c)));
-    CUDA_TRY(c, cudaMalloc(&c->d_part, sizeof(double) * parts));
-    CUDA_TRY(c, cudaMalloc(&c->d_partc, sizeof(unsigned int) * parts));
-    CUDA_TRY(c, cudaMalloc(&c->d_signal, sizeof(float) * npix(c)));
-    return MC_OK;
 }
 
 mc_status clear_tally(mc_ctx* c, cudaStream_t s) {
     if (c->d_tally) CUDA_TRY(c, cudaMemsetAsync(c->d_tally, 0, c->tally_n * sizeof(unsigned long long), s));
     CUDA_TRY(c, cudaMemsetAsync(c->d_energy, 0, sizeof(unsigned long long) * mc::kNumEnergy, s));
     CUDA_TRY(c, cudaMemsetAsync(c->d_events, 0, sizeof(unsigned long long) * mc::kNumEvents, s));
-    c->hist_done = 0;
+    for (FieldHost& f : c->fields) f.hist_done = 0;
     return MC_OK;
 }
 
@@ -173,14 +176,10 @@ void make_params(const mc_ctx* c, Params& P, uint64_t seed) {
     for (int m = 0; m < 4; ++m) P.rho_max[m] = c->rho_max[m];
     P.mgM = c->mgM; P.mgx = c->mg[0]; P.mgy = c->mg[1]; P.mgz = c->mg[2];
     P.mgrid = c->d_mgrid;
-    for (int k = 0; k < 3; ++k) {
-        P.thr[k] = c->thr[k];
-        P.ex[k] = static_cast<float>(c->ex[k]);
-        P.ey[k] = static_cast<float>(c->ey[k]);
-        P.ez[k] = static_cast<float>(c->ez[k]);
-        P.iso[k] = static_cast<float>(c->iso[k]);
-    }
-    P.sad = static_cast<float>(c->sad);
+    for (int k = 0; k < 3; ++k) P.thr[k] = c->thr[k];
+    P.fields = c->d_fields;
+    P.n_fields = nfields(c);
+    P.first = c->d_first;
     const mc_epid_desc& E = c->epid;
     P.nl = E.n_layers; P.sens = E.sensitive_layer; P.npx = E.npx; P.npy = E.npy;
     P.pitch = static_cast<float>(E.pitch_cm);
@@ -188,12 +187,11 @@ void make_params(const mc_ctx* c, Params& P, uint64_t seed) {
     P.hwx = static_cast<float>(0.5 * E.npx * E.pitch_cm);
     P.hwy = static_cast<float>(0.5 * E.npy * E.pitch_cm);
     for (int l = 0; l <= E.n_layers; ++l) P.zp[l] = static_cast<float>(c->zp[l] - c->zp[0]);
-    P.zface = static_cast<float>(c->zp[0]);
     for (int l = 0; l < E.n_layers; ++l) {
         P.lmat[l] = E.material[l];
         P.lrho[l] = static_cast<float>(E.density[l]);
     }
-    P.n_rect = c->n_rect; P.rect = c->d_rect; P.cdf = c->d_cdf;
+    P.rect = c->d_rect; P.cdf = c->d_cdf;
     P.e_max = static_cast<float>(c->cfg.e_max_mev);
     P.mono_e = static_cast<float>(c->cfg.mono_energy_mev);
     P.pcut = static_cast<float>(c->cfg.photon_cutoff_mev);
@@ -220,7 +218,6 @@ void make_params(const mc_ctx* c, Params& P, uint64_t seed) {
     P.w_lnG0 = static_cast<float>(c->tabs.w_lnG0);
     P.w_idx = static_cast<float>(c->tabs.w_inv_dlnG);
     P.seed = seed;
-    P.hist_base = c->hist_done;
     P.tally = c->d_tally;
     P.energy = c->d_energy;
     P.events = c->d_events;
@@ -236,6 +233,383 @@ bool increasing(const double* a, int n) {
         if (!(a[i] > a[i - 1])) return false;
     return true;
 }
+
+// Source rectangles of one field (weight MU x open area, cumulative in
+// double, appended to rect / cdf), its bounding box, Eq. 1 and beam frame.
+mc_status build_field(mc_ctx* c, const mc_field_desc* f, int index, std::vector<float4>& rect,
+                      std::vector<double>& cdf, FieldHost& out) {
+    const std::string which = " (field " + std::to_string(index) + ")";
+    if (!f->pair_edges_cm || !f->leaves_cm || !f->jaws_cm || !f->mu) return fail(c, MC_ERR_ARG, "null field" + which);
+    if (f->n_segments < 1 || f->n_pairs < 1 || f->n_segments * f->n_pairs > (1 << 20))
+        return fail(c, MC_ERR_ARG, "bad segment / pair count" + which);
+    if (!(f->sad_cm > 0) || !(f->sid_cm > f->sad_cm)) return fail(c, MC_ERR_ARG, "need 0 < SAD < SID" + which);
+    if (!increasing(f->pair_edges_cm, f->n_pairs + 1)) return fail(c, MC_ERR_ARG, "pair edges must increase" + which);
+    const size_t off = rect.size();
+    double acc = 0.0, X0 = INFINITY, X1 = -INFINITY, Y0 = INFINITY, Y1 = -INFINITY;
+    for (int k = 0; k < f->n_segments; ++k) {
+        const double* jw = f->jaws_cm + 4 * k;
+        const double mu = f->mu[k];
+        if (!(mu >= 0.0)) return fail(c, MC_ERR_ARG, "MU weights must be >= 0" + which);
+        for (int j = 0; j < f->n_pairs; ++j) {
+            const double* lf = f->leaves_cm + 2 * (static_cast<size_t>(k) * f->n_pairs + j);
+            const double x0 = std::fmax(lf[0], jw[0]), x1 = std::fmin(lf[1], jw[1]);
+            const double y0 = std::fmax(f->pair_edges_cm[j], jw[2]), y1 = std::fmin(f->pair_edges_cm[j + 1], jw[3]);
+            if (x1 > x0 && y1 > y0 && mu > 0.0) {
+                acc += mu * (x1 - x0) * (y1 - y0);
+                rect.push_back(make_float4(static_cast<float>(x0), static_cast<float>(x1), static_cast<float>(y0),
+                                           static_cast<float>(y1)));
+                cdf.push_back(acc);
+                X0 = std::fmin(X0, x0); X1 = std::fmax(X1, x1); Y0 = std::fmin(Y0, y0); Y1 = std::fmax(Y1, y1);
+            }
+        }
+    }
+    if (rect.size() == off) return fail(c, MC_ERR_ARG, "field has no open aperture" + which);
+    for (size_t i = off; i < cdf.size(); ++i) cdf[i] /= acc;
+    out.rect_off = static_cast<int>(off);
+    out.n_rect = static_cast<int>(rect.size() - off);
+    out.bbox_a = X1 - X0;
+    out.bbox_b = Y1 - Y0;
+    // Eq. 1 as printed gives ab / (2(a+b)) (2.5 cm for 10 x 10), which cannot index
+    // Table 1; the default reading is the equivalent square 2ab / (a+b).
+    out.s_eq = f->eq1_literal ? out.bbox_a * out.bbox_b / (2.0 * (out.bbox_a + out.bbox_b))
+                              : 2.0 * out.bbox_a * out.bbox_b / (out.bbox_a + out.bbox_b);
+    const double g = f->gantry_deg * 3.14159265358979323846 / 180.0;
+    out.ex[0] = std::cos(g); out.ex[1] = std::sin(g); out.ex[2] = 0.0;
+    out.ey[0] = 0.0; out.ey[1] = 0.0; out.ey[2] = 1.0;
+    out.ez[0] = std::sin(g); out.ez[1] = -std::cos(g); out.ez[2] = 0.0;
+    for (int k = 0; k < 3; ++k) out.iso[k] = f->iso_cm[k];
+    out.sad = f->sad_cm;
+    out.sid = f->sid_cm;
+    out.zface = (out.sad - out.sid) + c->zp[0];
+    // the vacuum transfer needs the whole CT above the detector face and below the source
+    for (int corner = 0; corner < 8; ++corner) {
+        double p[3];
+        const int n[3] = {c->nx, c->ny, c->nz};
+        for (int k = 0; k < 3; ++k) p[k] = c->origin[k] + ((corner >> k) & 1) * n[k] * c->vox[k] - out.iso[k];
+        const double Z = p[0] * out.ez[0] + p[1] * out.ez[1] + p[2] * out.ez[2];
+        if (!(Z > out.zface + 1e-3) || !(Z < out.sad))
+            return fail(c, MC_ERR_ARG, "CT box must lie between the source and the EPID face" + which);
+    }
+    out.stream_base = static_cast<uint64_t>(index) * kFieldStride;
+    out.hist_done = 0;
+    return MC_OK;
+}
+
+// Per-field device records for a run; `first` is the prefix sum of the
+// histories each field runs in it.
+mc_status upload_fields(mc_ctx* c, const std::vector<uint64_t>& first, cudaStream_t s) {
+    std::vector<FieldDev> fd(c->fields.size());
+    const size_t per_field = static_cast<size_t>(c->cfg.n_batches) * npix(c);
+    for (size_t i = 0; i < c->fields.size(); ++i) {
+        const FieldHost& h = c->fields[i];
+        FieldDev& d = fd[i];
+        for (int k = 0; k < 3; ++k) {
+            d.ex[k] = static_cast<float>(h.ex[k]);
+            d.ey[k] = static_cast<float>(h.ey[k]);
+            d.ez[k] = static_cast<float>(h.ez[k]);
+            d.iso[k] = static_cast<float>(h.iso[k]);
+        }
+        d.sad = static_cast<float>(h.sad);
+        d.zface = static_cast<float>(h.zface);
+        d.rect_off = h.rect_off;
+        d.n_rect = h.n_rect;
+        d.hist_base = h.stream_base + h.hist_done;
+        d.batch_base = h.hist_done;
+        d.tally_off = i * per_field;
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_fields, fd.data(), sizeof(FieldDev) * fd.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_first, first.data(), sizeof(unsigned long long) * first.size(),
+                                cudaMemcpyHostToDevice, s));
+    // the copies read host vectors that die on return
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
+struct WaveResult {
+    int waves = 0;
+    uint32_t launches = 0;
+    uint32_t klaunch[4] = {0, 0, 0, 0};
+    double kms[4] = {0, 0, 0, 0};
+};
+
+bool is_electron(int t) { return t == mc::kElectronCT || t == mc::kElectronEPID; }
+
+const int kOrder[4] = {mc::kPhotonCT, mc::kElectronCT, mc::kPhotonEPID, mc::kElectronEPID};
+
+// Graph-driven waves: one wave (wave-begin, the transport kernels with their
+// bank swaps, wave-end) is captured into the body of a conditional while-node;
+// the wave-end kernel sets the condition, so the whole run is one launch and
+// the host waits once.  `e0` is recorded just before the launch.
+mc_status run_waves_graph(mc_ctx* c, const Params& P, cudaStream_t s, cudaEvent_t e0, WaveResult& r) {
+    if (!c->capture_stream) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    };
+    CUDA_TRY(c, cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle handle;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np{};
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = handle;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    }
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(c, MC_ERR_CUDA, std::string("conditional node: ") + cudaGetErrorString(e));
+    }
+    cudaStream_t cs = c->capture_stream;
+    e = cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(c, MC_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+    }
+    uint32_t per_wave = 2;   // wave-begin and wave-end
+    e = mc::launch_wave_begin(c->d_ctl, c->cfg.primaries_per_wave, cs);
+    for (int t : kOrder) {
+        if (is_electron(t) && !c->cfg.coupled) continue;
+        if (e == cudaSuccess) e = mc::launch_transport(t, c->minb[t], P, c->grid[t], c->block, cs);
+        if (e == cudaSuccess) e = mc::launch_swap(c->d_ctl, t, cs);
+        per_wave += 2;
+    }
+    if (e == cudaSuccess) e = mc::launch_wave_end(c->d_ctl, handle, kMaxWaves, cs);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(cs, &captured);
+    if (e == cudaSuccess) e = e_end;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+    Ctl& h = *c->h_ctl;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) return fail(c, MC_ERR_CUDA, std::string("graph-driven run: ") + cudaGetErrorString(e));
+    r.waves = static_cast<int>(h.waves);
+    r.launches = per_wave * h.waves;
+    for (int t : kOrder)
+        if (!(is_electron(t) && !c->cfg.coupled)) r.klaunch[t] = h.waves;
+    if (h.error) return fail(c, MC_ERR_OVERFLOW, "particle bank overflow");
+    if (h.waves >= kMaxWaves) return fail(c, MC_ERR_TIMEOUT, "wave limit reached");
+    return MC_OK;
+}
+
+// Host-driven waves: the host reads the run control after every wave and
+// stops when all banks are empty; it can time every transport launch.
+mc_status run_waves_host(mc_ctx* c, const Params& P, cudaStream_t s, cudaEvent_t e0, WaveResult& r) {
+    Ctl& h = *c->h_ctl;
+    std::vector<std::pair<int, size_t>> timed;   // (type, index of its start event)
+    size_t ev_used = 0;
+    auto next_event = [&]() -> cudaEvent_t {
+        if (ev_used == c->ev_pool.size()) {
+            cudaEvent_t ev;
+            cudaEventCreate(&ev);
+            c->ev_pool.push_back(ev);
+        }
+        return c->ev_pool[ev_used++];
+    };
+    CUDA_TRY(c, cudaEventRecord(e0, s));
+    mc_status result = MC_OK;
+    int& waves = r.waves;
+    for (; waves < static_cast<int>(kMaxWaves); ++waves) {
+        CUDA_TRY(c, mc::launch_wave_begin(c->d_ctl, c->cfg.primaries_per_wave, s));
+        ++r.launches;
+        for (int t : kOrder) {
+            if (is_electron(t) && !c->cfg.coupled) continue;
+            if (c->cfg.time_kernels) {
+                timed.emplace_back(t, ev_used);
+                CUDA_TRY(c, cudaEventRecord(next_event(), s));
+            }
+            CUDA_TRY(c, mc::launch_transport(t, c->minb[t], P, c->grid[t], c->block, s));
+            if (c->cfg.time_kernels) CUDA_TRY(c, cudaEventRecord(next_event(), s));
+            CUDA_TRY(c, mc::launch_swap(c->d_ctl, t, s));
+            r.launches += 2;
+            ++r.klaunch[t];
+        }
+        CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        if (h.error) { result = fail(c, MC_ERR_OVERFLOW, "particle bank overflow"); ++waves; break; }
+        bool empty = h.next_prim >= h.n_total;
+        for (int t = 0; t < mc::kNumBanks; ++t) empty = empty && h.count[t][h.cur[t]] == 0u;
+        if (empty) { ++waves; break; }
+        if (c->cancel.load()) { result = fail(c, MC_ERR_CANCELLED, "cancelled"); ++waves; break; }
+    }
+    if (waves >= static_cast<int>(kMaxWaves) && result == MC_OK) result = fail(c, MC_ERR_TIMEOUT, "wave limit reached");
+    for (const auto& te : timed) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev_pool[te.second], c->ev_pool[te.second + 1]);
+        r.kms[te.first] += ms;
+    }
+    return result;
+}
+
+mc_status set_fields_impl(mc_ctx* c, const mc_field_desc* f, int n, const mc_lut_desc* lut, cudaStream_t s) {
+    if (!c->has_geom) return fail(c, MC_ERR_STATE, "mc_init_geometry must come first");
+    if (!f || n < 1 || n > mc::kMaxFields) return fail(c, MC_ERR_ARG, "need 1..256 fields");
+    if (lut) {
+        if (lut->nt < 2 || lut->ns < 2 || lut->nt > 1024 || lut->ns > 1024 || !lut->t_nodes || !lut->s_nodes || !lut->k)
+            return fail(c, MC_ERR_ARG, "bad k-table");
+        if (!increasing(lut->t_nodes, lut->nt) || !increasing(lut->s_nodes, lut->ns))
+            return fail(c, MC_ERR_ARG, "k-table nodes must increase");
+    }
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    free_field(c);
+    std::vector<float4> rect;
+    std::vector<double> cdf;
+    std::vector<FieldHost> fh(n);
+    for (int i = 0; i < n; ++i) {
+        const mc_status st = build_field(c, &f[i], i, rect, cdf, fh[i]);
+        if (st != MC_OK) return st;
+    }
+    const int np = npix(c);
+    const size_t tally_n = static_cast<size_t>(n) * c->cfg.n_batches * np;
+    const int parts = (np + 255) / 256;
+    CUDA_TRY(c, cudaMalloc(&c->d_tally, tally_n * sizeof(unsigned long long)));
+    c->tally_n = tally_n;
+    CUDA_TRY(c, cudaMalloc(&c->d_dose, sizeof(double) * np));
+    CUDA_TRY(c, cudaMalloc(&c->d_sigma, sizeof(double) * np));
+    CUDA_TRY(c, cudaMalloc(&c->d_part, sizeof(double) * parts));
+    CUDA_TRY(c, cudaMalloc(&c->d_partc, sizeof(unsigned int) * parts));
+    CUDA_TRY(c, cudaMalloc(&c->d_signal, sizeof(float) * np));
+    CUDA_TRY(c, cudaMalloc(&c->d_rect, sizeof(float4) * rect.size()));
+    CUDA_TRY(c, cudaMalloc(&c->d_cdf, sizeof(double) * cdf.size()));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_rect, rect.data(), sizeof(float4) * rect.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_cdf, cdf.data(), sizeof(double) * cdf.size(), cudaMemcpyHostToDevice, s));
+
+    // radiological thickness map of every field (a9)
+    c->t_offset = lut ? lut->t_offset_cm : 0.0;
+    CUDA_TRY(c, cudaMalloc(&c->d_tmap, sizeof(double) * static_cast<size_t>(n) * np));
+    const mc_epid_desc& E = c->epid;
+    for (int i = 0; i < n; ++i) {
+        const FieldHost& h = fh[i];
+        mc::TmapArgs A;
+        A.nx = c->nx; A.ny = c->ny; A.nz = c->nz;
+        A.ox = static_cast<float>(c->origin[0]); A.oy = static_cast<float>(c->origin[1]);
+        A.oz = static_cast<float>(c->origin[2]);
+        A.vx = static_cast<float>(c->vox[0]); A.vy = static_cast<float>(c->vox[1]);
+        A.vz = static_cast<float>(c->vox[2]);
+        A.rho = c->d_rho;
+        for (int k = 0; k < 3; ++k) {
+            A.src[k] = static_cast<float>(h.iso[k] + h.sad * h.ez[k]);
+            A.iso[k] = static_cast<float>(h.iso[k]);
+            A.ex[k] = static_cast<float>(h.ex[k]);
+            A.ey[k] = static_cast<float>(h.ey[k]);
+            A.ez[k] = static_cast<float>(h.ez[k]);
+        }
+        A.npx = E.npx; A.npy = E.npy;
+        A.pitch = static_cast<float>(E.pitch_cm);
+        A.hwx = static_cast<float>(0.5 * E.npx * E.pitch_cm);
+        A.hwy = static_cast<float>(0.5 * E.npy * E.pitch_cm);
+        A.zs = static_cast<float>(h.sad - h.sid);
+        A.t_offset = c->t_offset;
+        CUDA_TRY(c, mc::launch_tmap(A, c->d_tmap + static_cast<size_t>(i) * np, s));
+    }
+
+    // k-table: the column at each field's s, for the per-pixel step along t
+    std::vector<double> ks;
+    if (lut) {
+        ks.resize(static_cast<size_t>(n) * lut->nt);
+        for (int i = 0; i < n; ++i) {
+            const double sc = std::fmin(std::fmax(fh[i].s_eq, lut->s_nodes[0]), lut->s_nodes[lut->ns - 1]);
+            int js = 0;
+            while (js + 1 < lut->ns - 1 && lut->s_nodes[js + 1] <= sc) ++js;
+            const double fs = (sc - lut->s_nodes[js]) / (lut->s_nodes[js + 1] - lut->s_nodes[js]);
+            for (int it = 0; it < lut->nt; ++it)
+                ks[static_cast<size_t>(i) * lut->nt + it] = (1.0 - fs) * lut->k[static_cast<size_t>(js) * lut->nt + it] +
+                                                             fs * lut->k[static_cast<size_t>(js + 1) * lut->nt + it];
+        }
+        CUDA_TRY(c, cudaMalloc(&c->d_lut_t, sizeof(double) * lut->nt));
+        CUDA_TRY(c, cudaMalloc(&c->d_lut_ks, sizeof(double) * ks.size()));
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_lut_t, lut->t_nodes, sizeof(double) * lut->nt, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_lut_ks, ks.data(), sizeof(double) * ks.size(), cudaMemcpyHostToDevice, s));
+        c->lut_nt = lut->nt;
+        c->k_scale = lut->k_scale;
+        c->has_lut = true;
+    }
+    c->fields = fh;
+    const mc_status st = clear_tally(c, s);
+    if (st != MC_OK) return st;
+    // rect, cdf and ks are host vectors: finish their copies before returning
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    c->has_field = true;
+    return MC_OK;
+}
+
+mc_status run_impl(mc_ctx* c, const uint64_t* n, uint64_t seed, cudaStream_t s, mc_run_stats* stats) {
+    if (!c->has_field) return fail(c, MC_ERR_STATE, "mc_set_field must come first");
+    std::vector<uint64_t> first(c->fields.size() + 1, 0);
+    for (size_t i = 0; i < c->fields.size(); ++i) {
+        if (n[i] > 0xffffffffull) return fail(c, MC_ERR_ARG, "at most 2^32-1 histories per field and call");
+        first[i + 1] = first[i] + n[i];
+    }
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    c->cancel.store(0);
+    mc_status st = upload_fields(c, first, s);
+    if (st != MC_OK) return st;
+    Params P;
+    make_params(c, P, seed);
+    Ctl& h = *c->h_ctl;
+    std::memset(&h, 0, sizeof(h));
+    h.n_total = first.back();
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    CUDA_TRY(c, cudaEventCreate(&e1));
+    WaveResult r;
+    const mc_status result = c->cfg.use_graph ? run_waves_graph(c, P, s, e0, r) : run_waves_host(c, P, s, e0, r);
+    float ms = 0.f;
+    if (cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess)
+        cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (size_t i = 0; i < c->fields.size(); ++i) c->fields[i].hist_done += n[i];
+    c->last_waves = r.waves;
+    c->last_error = h.error;
+    c->last_ms = ms;
+    c->last_launches = r.launches;
+    for (int t = 0; t < 4; ++t) { c->last_kernel_ms[t] = r.kms[t]; c->last_kernel_launches[t] = r.klaunch[t]; }
+    if (stats) {
+        const mc_status s2 = mc_get_stats(c, stats);
+        if (s2 != MC_OK) return s2;
+    }
+    return result;
+}
+
+mc_status compute_dose(mc_ctx* c, int field, double* dose, double* sigma, double* u_dev, cudaStream_t s) {
+    const int B = c->cfg.n_batches;
+    const uint64_t N = c->fields[field].hist_done;
+    if (N == 0) return fail(c, MC_ERR_STATE, "no histories run");
+    std::vector<double> nb(B);
+    for (int b = 0; b < B; ++b) nb[b] = static_cast<double>(N / B + (static_cast<uint64_t>(b) < N % B ? 1 : 0));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_nb, nb.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+    const mc_epid_desc& E = c->epid;
+    const int l = E.sensitive_layer;
+    const double mass_kg = E.density[l] * E.pitch_cm * E.pitch_cm * E.thickness_cm[l] * 1e-3;
+    const unsigned long long* tally = c->d_tally + static_cast<size_t>(field) * B * npix(c);
+    CUDA_TRY(c, mc::launch_dose(tally, npix(c), B, c->d_nb, static_cast<double>(N), kJoulePerMeV / mass_kg, dose,
+                                sigma, c->d_maxbits, c->d_part, c->d_partc, u_dev, s));
+    // nb is a host vector: finish its copy before returning
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
+mc_status check_field(mc_ctx* c, int field) {
+    if (!c->has_field) return fail(c, MC_ERR_STATE, "no field");
+    if (field < 0 || field >= nfields(c)) return fail(c, MC_ERR_ARG, "field index out of range");
+    return MC_OK;
+}
+
+// State layout (uint64 words): magic, B, npx, npy, number of fields, the
+// next history index of each field, energy counters, event counters,
+// sub-tallies.
+const uint64_t kStateMagic = 0x4550494453543032ull;   // "EPIDST02"
+size_t state_words(const mc_ctx* c) { return 5 + c->fields.size() + mc::kNumEnergy + mc::kNumEvents + c->tally_n; }
 
 }  // namespace
 
@@ -259,6 +633,7 @@ void mc_config_default(mc_config* cfg) {
     cfg->bank_capacity = 1u << 23;
     cfg->primaries_per_wave = 0;
     cfg->time_kernels = 0;
+    cfg->use_graph = 0;
     for (int t = 0; t < 4; ++t) cfg->regs_variant[t] = 4;
 }
 
@@ -297,6 +672,7 @@ mc_status mc_create(const mc_config* cfg_in, int device, mc_ctx** out) {
         !(cfg.wcc_mev > 0) || !(cfg.step_fraction > 0 && cfg.step_fraction < 1) || !(cfg.e_max_mev > 0))
         return MC_ERR_ARG;
     if (cfg.bank_capacity < 1024 || cfg.primaries_per_wave < 32) return MC_ERR_ARG;
+    if (cfg.use_graph != 0 && cfg.use_graph != 1) return MC_ERR_ARG;
 
     mc_ctx* c = new mc_ctx();
     c->cfg = cfg;
@@ -339,7 +715,9 @@ mc_status mc_create(const mc_config* cfg_in, int device, mc_ctx** out) {
         cudaMalloc(&c->d_thr, sizeof(float) * 3) != cudaSuccess ||
         cudaMalloc(&c->d_nb, sizeof(double) * cfg.n_batches) != cudaSuccess ||
         cudaMalloc(&c->d_u, sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->d_maxbits, sizeof(unsigned long long)) != cudaSuccess)
+        cudaMalloc(&c->d_maxbits, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_fields, sizeof(FieldDev) * mc::kMaxFields) != cudaSuccess ||
+        cudaMalloc(&c->d_first, sizeof(unsigned long long) * (mc::kMaxFields + 1)) != cudaSuccess)
         return bail(MC_ERR_OOM);
     cudaMemset(c->d_energy, 0, sizeof(unsigned long long) * mc::kNumEnergy);
     cudaMemset(c->d_events, 0, sizeof(unsigned long long) * mc::kNumEvents);
@@ -377,7 +755,10 @@ mc_status mc_destroy(mc_ctx* c) {
     dfree(c->d_nb);
     dfree(c->d_u);
     dfree(c->d_maxbits);
+    dfree(c->d_fields);
+    dfree(c->d_first);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     delete c;
     return MC_OK;
 }
@@ -434,216 +815,38 @@ mc_status mc_init_geometry(mc_ctx* c, const int16_t* hu, int nx, int ny, int nz,
     c->nx = nx; c->ny = ny; c->nz = nz;
     for (int k = 0; k < 3; ++k) { c->vox[k] = vox_cm[k]; c->origin[k] = origin_cm[k]; }
     c->epid = E;
+    // layer planes with the sensitive layer's centre at 0; each field puts
+    // that centre at its SID
+    double z = 0.5 * E.thickness_cm[E.sensitive_layer];
+    for (int l = E.sensitive_layer - 1; l >= 0; --l) z += E.thickness_cm[l];
+    c->zp[0] = z;
+    for (int l = 0; l < E.n_layers; ++l) c->zp[l + 1] = c->zp[l] - E.thickness_cm[l];
     c->has_geom = true;
     return MC_OK;
 }
 
 mc_status mc_set_field(mc_ctx* c, const mc_field_desc* f, const mc_lut_desc* lut, void* stream) {
     if (!c) return MC_ERR_ARG;
-    if (!c->has_geom) return fail(c, MC_ERR_STATE, "mc_init_geometry must come first");
-    if (!f || !f->pair_edges_cm || !f->leaves_cm || !f->jaws_cm || !f->mu) return fail(c, MC_ERR_ARG, "null field");
-    if (f->n_segments < 1 || f->n_pairs < 1 || f->n_segments * f->n_pairs > (1 << 20))
-        return fail(c, MC_ERR_ARG, "bad segment / pair count");
-    if (!(f->sad_cm > 0) || !(f->sid_cm > f->sad_cm)) return fail(c, MC_ERR_ARG, "need 0 < SAD < SID");
-    if (!increasing(f->pair_edges_cm, f->n_pairs + 1)) return fail(c, MC_ERR_ARG, "pair edges must increase");
-    CUDA_TRY(c, cudaSetDevice(c->device));
-    cudaStream_t s = as_stream(stream);
-    free_field(c);
+    if (!f) return fail(c, MC_ERR_ARG, "null field");
+    return set_fields_impl(c, f, 1, lut, as_stream(stream));
+}
 
-    // source rectangles with weight MU x area, cumulative in double
-    std::vector<float4> rect;
-    std::vector<double> cdf;
-    double acc = 0.0, X0 = INFINITY, X1 = -INFINITY, Y0 = INFINITY, Y1 = -INFINITY;
-    for (int k = 0; k < f->n_segments; ++k) {
-        const double* jw = f->jaws_cm + 4 * k;
-        const double mu = f->mu[k];
-        if (!(mu >= 0.0)) return fail(c, MC_ERR_ARG, "MU weights must be >= 0");
-        for (int j = 0; j < f->n_pairs; ++j) {
-            const double* lf = f->leaves_cm + 2 * (static_cast<size_t>(k) * f->n_pairs + j);
-            const double x0 = std::fmax(lf[0], jw[0]), x1 = std::fmin(lf[1], jw[1]);
-            const double y0 = std::fmax(f->pair_edges_cm[j], jw[2]), y1 = std::fmin(f->pair_edges_cm[j + 1], jw[3]);
-            if (x1 > x0 && y1 > y0 && mu > 0.0) {
-                acc += mu * (x1 - x0) * (y1 - y0);
-                rect.push_back(make_float4(static_cast<float>(x0), static_cast<float>(x1), static_cast<float>(y0),
-                                           static_cast<float>(y1)));
-                cdf.push_back(acc);
-                X0 = std::fmin(X0, x0); X1 = std::fmax(X1, x1); Y0 = std::fmin(Y0, y0); Y1 = std::fmax(Y1, y1);
-            }
-        }
-    }
-    if (rect.empty()) return fail(c, MC_ERR_ARG, "field has no open aperture");
-    for (double& v : cdf) v /= acc;
-    c->bbox_a = X1 - X0;
-    c->bbox_b = Y1 - Y0;
-    // Eq. 1 as printed gives ab / (2(a+b)) (2.5 cm for 10 x 10), which cannot index
-    // Table 1; the default reading is the equivalent square 2ab / (a+b).
-    c->s_eq = f->eq1_literal ? c->bbox_a * c->bbox_b / (2.0 * (c->bbox_a + c->bbox_b))
-                             : 2.0 * c->bbox_a * c->bbox_b / (c->bbox_a + c->bbox_b);
-
-    const double g = f->gantry_deg * 3.14159265358979323846 / 180.0;
-    c->ex[0] = std::cos(g); c->ex[1] = std::sin(g); c->ex[2] = 0.0;
-    c->ey[0] = 0.0; c->ey[1] = 0.0; c->ey[2] = 1.0;
-    c->ez[0] = std::sin(g); c->ez[1] = -std::cos(g); c->ez[2] = 0.0;
-    for (int k = 0; k < 3; ++k) c->iso[k] = f->iso_cm[k];
-    c->sad = f->sad_cm;
-    c->sid = f->sid_cm;
-    const mc_epid_desc& E = c->epid;
-    double z = (c->sad - c->sid) + 0.5 * E.thickness_cm[E.sensitive_layer];
-    for (int l = E.sensitive_layer - 1; l >= 0; --l) z += E.thickness_cm[l];
-    c->zp[0] = z;
-    for (int l = 0; l < E.n_layers; ++l) c->zp[l + 1] = c->zp[l] - E.thickness_cm[l];
-    // the vacuum transfer needs the whole CT above the detector face and below the source
-    for (int corner = 0; corner < 8; ++corner) {
-        double p[3];
-        const int n[3] = {c->nx, c->ny, c->nz};
-        for (int k = 0; k < 3; ++k) p[k] = c->origin[k] + ((corner >> k) & 1) * n[k] * c->vox[k] - c->iso[k];
-        const double Z = p[0] * c->ez[0] + p[1] * c->ez[1] + p[2] * c->ez[2];
-        if (!(Z > c->zp[0] + 1e-3) || !(Z < c->sad))
-            return fail(c, MC_ERR_ARG, "CT box must lie between the source and the EPID face");
-    }
-
-    mc_status st = ensure_tally(c);
-    if (st != MC_OK) return st;
-    c->n_rect = static_cast<int>(rect.size());
-    CUDA_TRY(c, cudaMalloc(&c->d_rect, sizeof(float4) * rect.size()));
-    CUDA_TRY(c, cudaMalloc(&c->d_cdf, sizeof(double) * cdf.size()));
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_rect, rect.data(), sizeof(float4) * rect.size(), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_cdf, cdf.data(), sizeof(double) * cdf.size(), cudaMemcpyHostToDevice, s));
-
-    // radiological thickness map (a9)
-    c->t_offset = lut ? lut->t_offset_cm : 0.0;
-    CUDA_TRY(c, cudaMalloc(&c->d_tmap, sizeof(double) * npix(c)));
-    mc::TmapArgs A;
-    A.nx = c->nx; A.ny = c->ny; A.nz = c->nz;
-    A.ox = static_cast<float>(c->origin[0]); A.oy = static_cast<float>(c->origin[1]);
-    A.oz = static_cast<float>(c->origin[2]);
-    A.vx = static_cast<float>(c->vox[0]); A.vy = static_cast<float>(c->vox[1]); A.vz = static_cast<float>(c->vox[2]);
-    A.rho = c->d_rho;
-    for (int k = 0; k < 3; ++k) {
-        A.src[k] = static_cast<float>(c->iso[k] + c->sad * c->ez[k]);
-        A.iso[k] = static_cast<float>(c->iso[k]);
-        A.ex[k] = static_cast<float>(c->ex[k]);
-        A.ey[k] = static_cast<float>(c->ey[k]);
-        A.ez[k] = static_cast<float>(c->ez[k]);
-    }
-    A.npx = E.npx; A.npy = E.npy;
-    A.pitch = static_cast<float>(E.pitch_cm);
-    A.hwx = static_cast<float>(0.5 * E.npx * E.pitch_cm);
-    A.hwy = static_cast<float>(0.5 * E.npy * E.pitch_cm);
-    A.zs = static_cast<float>(c->sad - c->sid);
-    A.t_offset = c->t_offset;
-    CUDA_TRY(c, mc::launch_tmap(A, c->d_tmap, s));
-
-    // k-table: the column at this field's s, for the per-pixel step along t
-    if (lut) {
-        if (lut->nt < 2 || lut->ns < 2 || lut->nt > 1024 || lut->ns > 1024 || !lut->t_nodes || !lut->s_nodes || !lut->k)
-            return fail(c, MC_ERR_ARG, "bad k-table");
-        if (!increasing(lut->t_nodes, lut->nt) || !increasing(lut->s_nodes, lut->ns))
-            return fail(c, MC_ERR_ARG, "k-table nodes must increase");
-        const double sc = std::fmin(std::fmax(c->s_eq, lut->s_nodes[0]), lut->s_nodes[lut->ns - 1]);
-        int js = 0;
-        while (js + 1 < lut->ns - 1 && lut->s_nodes[js + 1] <= sc) ++js;
-        const double fs = (sc - lut->s_nodes[js]) / (lut->s_nodes[js + 1] - lut->s_nodes[js]);
-        std::vector<double> ks(lut->nt);
-        for (int it = 0; it < lut->nt; ++it)
-            ks[it] = (1.0 - fs) * lut->k[static_cast<size_t>(js) * lut->nt + it] +
-                     fs * lut->k[static_cast<size_t>(js + 1) * lut->nt + it];
-        CUDA_TRY(c, cudaMalloc(&c->d_lut_t, sizeof(double) * lut->nt));
-        CUDA_TRY(c, cudaMalloc(&c->d_lut_ks, sizeof(double) * lut->nt));
-        CUDA_TRY(c, cudaMemcpyAsync(c->d_lut_t, lut->t_nodes, sizeof(double) * lut->nt, cudaMemcpyHostToDevice, s));
-        CUDA_TRY(c, cudaMemcpyAsync(c->d_lut_ks, ks.data(), sizeof(double) * lut->nt, cudaMemcpyHostToDevice, s));
-        c->lut_nt = lut->nt;
-        c->k_scale = lut->k_scale;
-        c->has_lut = true;
-    }
-    st = clear_tally(c, s);
-    if (st != MC_OK) return st;
-    CUDA_TRY(c, cudaStreamSynchronize(s));
-    c->has_field = true;
-    return MC_OK;
+mc_status mc_set_fields(mc_ctx* c, const mc_field_desc* f, int n, const mc_lut_desc* lut, void* stream) {
+    if (!c) return MC_ERR_ARG;
+    return set_fields_impl(c, f, n, lut, as_stream(stream));
 }
 
 mc_status mc_run(mc_ctx* c, uint64_t n, uint64_t seed, void* stream, mc_run_stats* stats) {
     if (!c) return MC_ERR_ARG;
     if (!c->has_field) return fail(c, MC_ERR_STATE, "mc_set_field must come first");
-    if (n > 0xffffffffull) return fail(c, MC_ERR_ARG, "at most 2^32-1 histories per call");
-    CUDA_TRY(c, cudaSetDevice(c->device));
-    cudaStream_t s = as_stream(stream);
-    c->cancel.store(0);
-    Params P;
-    make_params(c, P, seed);
-    Ctl& h = *c->h_ctl;
-    std::memset(&h, 0, sizeof(h));
-    h.n_total = n;
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-    cudaEvent_t e0, e1;
-    CUDA_TRY(c, cudaEventCreate(&e0));
-    CUDA_TRY(c, cudaEventCreate(&e1));
-    CUDA_TRY(c, cudaEventRecord(e0, s));
-    const int order[4] = {mc::kPhotonCT, mc::kElectronCT, mc::kPhotonEPID, mc::kElectronEPID};
-    int waves = 0;
-    uint32_t launches = 0;
-    uint32_t klaunch[4] = {0, 0, 0, 0};
-    // (type, start event index) of every timed transport launch
-    std::vector<std::pair<int, size_t>> timed;
-    size_t ev_used = 0;
-    auto next_event = [&]() -> cudaEvent_t {
-        if (ev_used == c->ev_pool.size()) {
-            cudaEvent_t e;
-            cudaEventCreate(&e);
-            c->ev_pool.push_back(e);
-        }
-        return c->ev_pool[ev_used++];
-    };
-    mc_status result = MC_OK;
-    const int max_waves = 1000000;
-    for (; waves < max_waves; ++waves) {
-        CUDA_TRY(c, mc::launch_wave_begin(c->d_ctl, c->cfg.primaries_per_wave, s));
-        ++launches;
-        for (int t : order) {
-            const bool electron = (t == mc::kElectronCT || t == mc::kElectronEPID);
-            if (electron && !c->cfg.coupled) continue;
-            if (c->cfg.time_kernels) {
-                timed.emplace_back(t, ev_used);
-                CUDA_TRY(c, cudaEventRecord(next_event(), s));
-            }
-            CUDA_TRY(c, mc::launch_transport(t, c->minb[t], P, c->grid[t], c->block, s));
-            if (c->cfg.time_kernels) CUDA_TRY(c, cudaEventRecord(next_event(), s));
-            CUDA_TRY(c, mc::launch_swap(c->d_ctl, t, s));
-            launches += 2;
-            ++klaunch[t];
-        }
-        CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(c, cudaStreamSynchronize(s));
-        if (h.error) { result = fail(c, MC_ERR_OVERFLOW, "particle bank overflow"); ++waves; break; }
-        bool empty = h.next_prim >= h.n_total;
-        for (int t = 0; t < mc::kNumBanks; ++t) empty = empty && h.count[t][h.cur[t]] == 0u;
-        if (empty) { ++waves; break; }
-        if (c->cancel.load()) { result = fail(c, MC_ERR_CANCELLED, "cancelled"); ++waves; break; }
-    }
-    if (waves >= max_waves && result == MC_OK) result = fail(c, MC_ERR_TIMEOUT, "wave limit reached");
-    CUDA_TRY(c, cudaEventRecord(e1, s));
-    CUDA_TRY(c, cudaEventSynchronize(e1));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    for (int t = 0; t < 4; ++t) { c->last_kernel_ms[t] = 0.0; c->last_kernel_launches[t] = klaunch[t]; }
-    for (const auto& te : timed) {
-        float kms = 0.f;
-        cudaEventElapsedTime(&kms, c->ev_pool[te.second], c->ev_pool[te.second + 1]);
-        c->last_kernel_ms[te.first] += kms;
-    }
-    c->last_launches = launches;
-    c->hist_done += n;
-    c->last_waves = waves;
-    c->last_error = h.error;
-    c->last_ms = ms;
-    if (stats) {
-        mc_status st = mc_get_stats(c, stats);
-        if (st != MC_OK) return st;
-    }
-    return result;
+    const std::vector<uint64_t> per(c->fields.size(), n);
+    return run_impl(c, per.data(), seed, as_stream(stream), stats);
+}
+
+mc_status mc_run_batch(mc_ctx* c, const uint64_t* n, uint64_t seed, void* stream, mc_run_stats* stats) {
+    if (!c) return MC_ERR_ARG;
+    if (!n) return fail(c, MC_ERR_ARG, "null history counts");
+    return run_impl(c, n, seed, as_stream(stream), stats);
 }
 
 mc_status mc_get_stats(mc_ctx* c, mc_run_stats* st) {
@@ -653,7 +856,7 @@ mc_status mc_get_stats(mc_ctx* c, mc_run_stats* st) {
     CUDA_TRY(c, cudaMemcpy(en, c->d_energy, sizeof(en), cudaMemcpyDeviceToHost));
     CUDA_TRY(c, cudaMemcpy(ev, c->d_events, sizeof(ev), cudaMemcpyDeviceToHost));
     std::memset(st, 0, sizeof(*st));
-    st->histories = c->hist_done;
+    for (const FieldHost& f : c->fields) st->histories += f.hist_done;
     st->e_src_mev = en[mc::kESrc] / kQuantaPerMeV;
     st->e_ct_mev = en[mc::kECT] / kQuantaPerMeV;
     st->e_esc_mev = en[mc::kEEsc] / kQuantaPerMeV;
@@ -671,30 +874,17 @@ mc_status mc_get_stats(mc_ctx* c, mc_run_stats* st) {
     return MC_OK;
 }
 
-static mc_status compute_dose(mc_ctx* c, double* dose, double* sigma, double* u_dev, cudaStream_t s) {
-    const int B = c->cfg.n_batches;
-    const uint64_t N = c->hist_done;
-    if (N == 0) return fail(c, MC_ERR_STATE, "no histories run");
-    std::vector<double> nb(B);
-    for (int b = 0; b < B; ++b) nb[b] = static_cast<double>(N / B + (static_cast<uint64_t>(b) < N % B ? 1 : 0));
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_nb, nb.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
-    const mc_epid_desc& E = c->epid;
-    const int l = E.sensitive_layer;
-    const double mass_kg = E.density[l] * E.pitch_cm * E.pitch_cm * E.thickness_cm[l] * 1e-3;
-    CUDA_TRY(c, mc::launch_dose(c->d_tally, npix(c), B, c->d_nb, static_cast<double>(N), kJoulePerMeV / mass_kg,
-                                dose, sigma, c->d_maxbits, c->d_part, c->d_partc, u_dev, s));
-    return MC_OK;
-}
-
-mc_status mc_get_dose(mc_ctx* c, double* dose, double* sigma, double* u_out, int on_device, void* stream) {
+mc_status mc_get_field_dose(mc_ctx* c, int field, double* dose, double* sigma, double* u_out, int on_device,
+                            void* stream) {
     if (!c) return MC_ERR_ARG;
-    if (!c->has_field) return fail(c, MC_ERR_STATE, "no field");
+    mc_status st = check_field(c, field);
+    if (st != MC_OK) return st;
     if (!dose) return fail(c, MC_ERR_ARG, "null dose");
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
     double* dd = on_device ? dose : c->d_dose;
     double* ds = on_device ? (sigma ? sigma : c->d_sigma) : c->d_sigma;
-    mc_status st = compute_dose(c, dd, ds, u_out ? c->d_u : nullptr, s);
+    st = compute_dose(c, field, dd, ds, u_out ? c->d_u : nullptr, s);
     if (st != MC_OK) return st;
     const size_t bytes = sizeof(double) * npix(c);
     if (!on_device) {
@@ -706,16 +896,23 @@ mc_status mc_get_dose(mc_ctx* c, double* dose, double* sigma, double* u_out, int
     return MC_OK;
 }
 
-mc_status mc_get_epid_image(mc_ctx* c, float* signal, int on_device, void* stream) {
+mc_status mc_get_dose(mc_ctx* c, double* dose, double* sigma, double* u_out, int on_device, void* stream) {
+    return mc_get_field_dose(c, 0, dose, sigma, u_out, on_device, stream);
+}
+
+mc_status mc_get_field_image(mc_ctx* c, int field, float* signal, int on_device, void* stream) {
     if (!c) return MC_ERR_ARG;
-    if (!c->has_field || !c->has_lut) return fail(c, MC_ERR_STATE, "no field or no k-table");
+    mc_status st = check_field(c, field);
+    if (st != MC_OK) return st;
+    if (!c->has_lut) return fail(c, MC_ERR_STATE, "no k-table");
     if (!signal) return fail(c, MC_ERR_ARG, "null signal");
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
-    mc_status st = compute_dose(c, c->d_dose, c->d_sigma, nullptr, s);
+    st = compute_dose(c, field, c->d_dose, c->d_sigma, nullptr, s);
     if (st != MC_OK) return st;
     float* out = on_device ? signal : c->d_signal;
-    CUDA_TRY(c, mc::launch_lut(c->d_dose, c->d_tmap, npix(c), c->d_lut_t, c->d_lut_ks, c->lut_nt, c->k_scale, out, s));
+    CUDA_TRY(c, mc::launch_lut(c->d_dose, c->d_tmap + static_cast<size_t>(field) * npix(c), npix(c), c->d_lut_t,
+                               c->d_lut_ks + static_cast<size_t>(field) * c->lut_nt, c->lut_nt, c->k_scale, out, s));
     if (!on_device) {
         CUDA_TRY(c, cudaMemcpyAsync(signal, c->d_signal, sizeof(float) * npix(c), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(c, cudaStreamSynchronize(s));
@@ -723,16 +920,25 @@ mc_status mc_get_epid_image(mc_ctx* c, float* signal, int on_device, void* strea
     return MC_OK;
 }
 
-mc_status mc_get_tmap(mc_ctx* c, double* t, int on_device, void* stream) {
+mc_status mc_get_epid_image(mc_ctx* c, float* signal, int on_device, void* stream) {
+    return mc_get_field_image(c, 0, signal, on_device, stream);
+}
+
+mc_status mc_get_field_tmap(mc_ctx* c, int field, double* t, int on_device, void* stream) {
     if (!c) return MC_ERR_ARG;
-    if (!c->has_field) return fail(c, MC_ERR_STATE, "no field");
+    mc_status st = check_field(c, field);
+    if (st != MC_OK) return st;
     if (!t) return fail(c, MC_ERR_ARG, "null output");
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
-    CUDA_TRY(c, cudaMemcpyAsync(t, c->d_tmap, sizeof(double) * npix(c),
+    CUDA_TRY(c, cudaMemcpyAsync(t, c->d_tmap + static_cast<size_t>(field) * npix(c), sizeof(double) * npix(c),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(s));
     return MC_OK;
+}
+
+mc_status mc_get_tmap(mc_ctx* c, double* t, int on_device, void* stream) {
+    return mc_get_field_tmap(c, 0, t, on_device, stream);
 }
 
 mc_status mc_get_tally(mc_ctx* c, uint64_t* tally, int on_device, void* stream) {
@@ -747,31 +953,27 @@ mc_status mc_get_tally(mc_ctx* c, uint64_t* tally, int on_device, void* stream) 
     return MC_OK;
 }
 
-mc_status mc_field_size(mc_ctx* c, double* sz, double* a, double* b) {
+mc_status mc_get_field_size(mc_ctx* c, int field, double* sz, double* a, double* b) {
     if (!c) return MC_ERR_ARG;
-    if (!c->has_field) return fail(c, MC_ERR_STATE, "no field");
-    if (sz) *sz = c->s_eq;
-    if (a) *a = c->bbox_a;
-    if (b) *b = c->bbox_b;
+    const mc_status st = check_field(c, field);
+    if (st != MC_OK) return st;
+    if (sz) *sz = c->fields[field].s_eq;
+    if (a) *a = c->fields[field].bbox_a;
+    if (b) *b = c->fields[field].bbox_b;
     return MC_OK;
 }
+
+mc_status mc_field_size(mc_ctx* c, double* sz, double* a, double* b) { return mc_get_field_size(c, 0, sz, a, b); }
 
 mc_status mc_reset_tally(mc_ctx* c, void* stream) {
     if (!c) return MC_ERR_ARG;
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
-    mc_status st = clear_tally(c, s);
+    const mc_status st = clear_tally(c, s);
     if (st != MC_OK) return st;
     CUDA_TRY(c, cudaStreamSynchronize(s));
     return MC_OK;
 }
-
-// State layout: magic, B, npx, npy, next history id, energy counters,
-// event counters, sub-tallies (all uint64).
-static size_t state_words(const mc_ctx* c) {
-    return 5 + mc::kNumEnergy + mc::kNumEvents + c->tally_n;
-}
-static const uint64_t kStateMagic = 0x4550494453543031ull;   // "EPIDST01"
 
 mc_status mc_state_size(mc_ctx* c, size_t* bytes) {
     if (!c || !bytes) return MC_ERR_ARG;
@@ -787,11 +989,14 @@ mc_status mc_get_state(mc_ctx* c, void* buf, size_t bytes, void* stream) {
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
     uint64_t* w = static_cast<uint64_t*>(buf);
-    w[0] = kStateMagic; w[1] = c->cfg.n_batches; w[2] = c->epid.npx; w[3] = c->epid.npy; w[4] = c->hist_done;
-    CUDA_TRY(c, cudaMemcpyAsync(w + 5, c->d_energy, sizeof(uint64_t) * mc::kNumEnergy, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(c, cudaMemcpyAsync(w + 5 + mc::kNumEnergy, c->d_events, sizeof(uint64_t) * mc::kNumEvents,
+    const size_t F = c->fields.size();
+    w[0] = kStateMagic; w[1] = c->cfg.n_batches; w[2] = c->epid.npx; w[3] = c->epid.npy; w[4] = F;
+    for (size_t i = 0; i < F; ++i) w[5 + i] = c->fields[i].hist_done;
+    uint64_t* q = w + 5 + F;
+    CUDA_TRY(c, cudaMemcpyAsync(q, c->d_energy, sizeof(uint64_t) * mc::kNumEnergy, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaMemcpyAsync(q + mc::kNumEnergy, c->d_events, sizeof(uint64_t) * mc::kNumEvents,
                                 cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(c, cudaMemcpyAsync(w + 5 + mc::kNumEnergy + mc::kNumEvents, c->d_tally, sizeof(uint64_t) * c->tally_n,
+    CUDA_TRY(c, cudaMemcpyAsync(q + mc::kNumEnergy + mc::kNumEvents, c->d_tally, sizeof(uint64_t) * c->tally_n,
                                 cudaMemcpyDeviceToHost, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
     return MC_OK;
@@ -802,24 +1007,26 @@ mc_status mc_set_state(mc_ctx* c, const void* buf, size_t bytes, void* stream) {
     if (!c->has_field) return fail(c, MC_ERR_STATE, "no field");
     if (bytes < state_words(c) * sizeof(uint64_t)) return fail(c, MC_ERR_ARG, "state buffer too small");
     const uint64_t* w = static_cast<const uint64_t*>(buf);
+    const size_t F = c->fields.size();
     if (w[0] != kStateMagic || w[1] != static_cast<uint64_t>(c->cfg.n_batches) ||
-        w[2] != static_cast<uint64_t>(c->epid.npx) || w[3] != static_cast<uint64_t>(c->epid.npy))
+        w[2] != static_cast<uint64_t>(c->epid.npx) || w[3] != static_cast<uint64_t>(c->epid.npy) || w[4] != F)
         return fail(c, MC_ERR_ARG, "state does not match this context");
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_energy, w + 5, sizeof(uint64_t) * mc::kNumEnergy, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_events, w + 5 + mc::kNumEnergy, sizeof(uint64_t) * mc::kNumEvents,
+    const uint64_t* q = w + 5 + F;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_energy, q, sizeof(uint64_t) * mc::kNumEnergy, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_events, q + mc::kNumEnergy, sizeof(uint64_t) * mc::kNumEvents,
                                 cudaMemcpyHostToDevice, s));
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_tally, w + 5 + mc::kNumEnergy + mc::kNumEvents, sizeof(uint64_t) * c->tally_n,
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_tally, q + mc::kNumEnergy + mc::kNumEvents, sizeof(uint64_t) * c->tally_n,
                                 cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
-    c->hist_done = w[4];
+    for (size_t i = 0; i < F; ++i) c->fields[i].hist_done = w[5 + i];
     return MC_OK;
 }
 
 mc_status mc_set_history_base(mc_ctx* c, uint64_t next_history) {
     if (!c) return MC_ERR_ARG;
-    c->hist_done = next_history;
+    for (FieldHost& f : c->fields) f.hist_done = next_history;
     return MC_OK;
 }
 

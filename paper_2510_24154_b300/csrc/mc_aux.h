@@ -27,6 +27,7 @@ cudaError_t transport_occupancy(int type, int minb, int block, int* blocks_per_s
 cudaError_t launch_transport(int type, int minb, const Params& P, int grid, int block, cudaStream_t s);
 cudaError_t launch_swap(Ctl* c, int t, cudaStream_t s);
 cudaError_t launch_wave_begin(Ctl* c, unsigned long long per_wave, cudaStream_t s);
+cudaError_t launch_wave_end(Ctl* c, cudaGraphConditionalHandle h, unsigned int max_waves, cudaStream_t s);
 
 cudaError_t launch_hu_to_rho(const int16_t* hu, float* rho, size_t n, unsigned int* rho_max_bits, float* thr,
                              int sm_count, cudaStream_t s);

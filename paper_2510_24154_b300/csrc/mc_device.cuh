@@ -64,7 +64,27 @@ struct Ctl {
     uint32_t cur[kNumBanks];        // input parity per bank type
     uint32_t allow_flush;           // more primaries follow: warps may hand low-occupancy work on
     uint32_t error;
+    uint32_t waves;                 // waves completed (graph-driven runs)
+    uint32_t more;                  // 1 while work remains (set by the wave-end kernel)
 };
+
+// One field of a run: beam frame (axes and isocentre in patient coordinates),
+// source distance, beam-frame Z of the detector face, its source rectangles,
+// the random-stream id of its first history in this run (hist_base), that
+// history's index within the field (batch_base: sub-tally = index mod B) and
+// the field's tally offset.
+struct FieldDev {
+    float ex[3], ey[3], ez[3], iso[3];
+    float sad, zface;
+    int rect_off, n_rect;
+    unsigned long long hist_base;
+    unsigned long long batch_base;
+    unsigned long long tally_off;
+};
+
+constexpr uint32_t kFieldShift = 8;             // particle flags bits 8..15: field index
+constexpr uint32_t kFieldMask = 0xff00u;
+constexpr int kMaxFields = 256;
 
 struct Params {
     // CT (patient frame)
@@ -75,18 +95,18 @@ struct Params {
     float thr[3];                   // density thresholds lung / water / bone
     int mgM, mgx, mgy, mgz;         // macro-cells: M voxels per side, cells per axis (<= 4096 cells)
     const float2* mgrid;            // per macro-cell (max density of non-bone voxels, of bone voxels)
-    // beam frame axes in patient coordinates, isocentre, source distance
-    float ex[3], ey[3], ez[3], iso[3];
-    float sad;
+    // fields: per-field beam frames, sources and tallies; a batch enumerates the
+    // histories of all fields one after the other (first[f] .. first[f+1])
+    const struct FieldDev* fields;
+    int n_fields;
+    const unsigned long long* first;    // [n_fields + 1]
     // EPID (beam frame)
     int nl, sens, npx, npy;
     float pitch, ipitch, hwx, hwy;
     float zp[kMaxLayers + 1];       // layer planes relative to the detector face (EPID particles keep z there)
-    float zface;                    // beam-frame Z of the detector face
     int lmat[kMaxLayers];
     float lrho[kMaxLayers];
-    // source
-    int n_rect;
+    // source: rectangles and cumulative weights of all fields, concatenated
     const float4* rect;
     const double* cdf;
     float e_max, mono_e;
@@ -100,8 +120,8 @@ struct Params {
     float e_lnT0, e_idx;
     float w_lnG0, w_idx;
     // run
-    unsigned long long seed, hist_base;
-    unsigned long long* tally;      // [B][npy][npx]
+    unsigned long long seed;
+    unsigned long long* tally;      // [n_fields][B][npy][npx]
     unsigned long long* energy;     // [kNumEnergy]
     unsigned long long* events;     // [kNumEvents]
     Ctl* ctl;
@@ -201,7 +221,8 @@ __device__ __forceinline__ void load_part(const BankPtr& b, uint32_t i, Part& p,
     p.hist = b.hist[i];
     p.cell = b.cell[i];
     p.flags = b.flags[i];
-    p.rng.setup(P.seed, P.hist_base + p.hist, b.ord[i], b.draws[i]);
+    const int f = static_cast<int>((p.flags & kFieldMask) >> kFieldShift);
+    p.rng.setup(P.seed, __ldg(&P.fields[f].hist_base) + p.hist, b.ord[i], b.draws[i]);
 }
 
 __device__ __forceinline__ void store_part(const BankPtr& b, uint32_t i, const Part& p) {
@@ -271,20 +292,22 @@ __device__ __forceinline__ void flush_self(const Params& P, bool want, int t, ui
 
 // -------------------------------------------------------- geometry --------
 
-__device__ __forceinline__ void to_beam(const Params& P, float px, float py, float pz, float& bx, float& by,
+__device__ __forceinline__ void to_beam(const FieldDev& F, float px, float py, float pz, float& bx, float& by,
                                         float& bz) {
-    const float dx = px - P.iso[0], dy = py - P.iso[1], dz = pz - P.iso[2];
-    bx = dx * P.ex[0] + dy * P.ex[1] + dz * P.ex[2];
-    by = dx * P.ey[0] + dy * P.ey[1] + dz * P.ey[2];
-    bz = dx * P.ez[0] + dy * P.ez[1] + dz * P.ez[2];
+    const float dx = px - F.iso[0], dy = py - F.iso[1], dz = pz - F.iso[2];
+    bx = dx * F.ex[0] + dy * F.ex[1] + dz * F.ex[2];
+    by = dx * F.ey[0] + dy * F.ey[1] + dz * F.ey[2];
+    bz = dx * F.ez[0] + dy * F.ez[1] + dz * F.ez[2];
 }
 
-__device__ __forceinline__ void to_beam_dir(const Params& P, float u, float v, float w, float& bu, float& bv,
+__device__ __forceinline__ void to_beam_dir(const FieldDev& F, float u, float v, float w, float& bu, float& bv,
                                             float& bw) {
-    bu = u * P.ex[0] + v * P.ex[1] + w * P.ex[2];
-    bv = u * P.ey[0] + v * P.ey[1] + w * P.ey[2];
-    bw = u * P.ez[0] + v * P.ez[1] + w * P.ez[2];
+    bu = u * F.ex[0] + v * F.ex[1] + w * F.ex[2];
+    bv = u * F.ey[0] + v * F.ey[1] + w * F.ey[2];
+    bw = u * F.ez[0] + v * F.ez[1] + w * F.ez[2];
 }
+
+__device__ __forceinline__ int field_of(uint32_t flags) { return static_cast<int>((flags & kFieldMask) >> kFieldShift); }
 
 __device__ __forceinline__ uint32_t pack_cell(int ix, int iy, int iz) {
     return static_cast<uint32_t>(ix) | (static_cast<uint32_t>(iy) << 10) | (static_cast<uint32_t>(iz) << 20);

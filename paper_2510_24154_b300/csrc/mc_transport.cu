@@ -52,9 +52,10 @@ __device__ __forceinline__ void acc_flush(const Params& P, Acc& a, unsigned long
 
 __device__ __forceinline__ float rest_extra(uint32_t flags) { return (flags & kPositron) ? kTwoMec2 : 0.0f; }
 
-// Energy deposited at beam-frame position (x, y) in EPID layer `layer`.
+// Energy deposited at beam-frame position (x, y) in EPID layer `layer` by a
+// particle of history `hist` of field `f`: into sub-tally (history index within the field mod B).
 __device__ __forceinline__ void deposit_epid(const Params& P, unsigned long long* s_energy, int layer, float x,
-                                             float y, uint32_t hist, float dE) {
+                                             float y, uint32_t hist, uint32_t flags, float dE) {
     if (!(dE > 0.0f)) return;
     const unsigned long long q = quanta(dE);
     atomicAdd(&s_energy[kEEpid0 + layer], q);
@@ -63,14 +64,15 @@ __device__ __forceinline__ void deposit_epid(const Params& P, unsigned long long
     int iy = __float2int_rd((y + P.hwy) / P.pitch);
     ix = min(max(ix, 0), P.npx - 1);
     iy = min(max(iy, 0), P.npy - 1);
-    const unsigned long long b = (P.hist_base + hist) % static_cast<unsigned long long>(P.nbatch);
-    atomicAdd(&P.tally[(b * P.npy + iy) * P.npx + ix], q);
+    const FieldDev& F = P.fields[field_of(flags)];
+    const unsigned long long b = (F.batch_base + hist) % static_cast<unsigned long long>(P.nbatch);
+    atomicAdd(&P.tally[F.tally_off + (b * P.npy + iy) * P.npx + ix], q);
 }
 
 template <bool EPID>
 __device__ __forceinline__ void deposit(const Params& P, Acc& a, unsigned long long* s_energy, uint32_t cell,
-                                        float x, float y, uint32_t hist, float dE) {
-    if (EPID) deposit_epid(P, s_energy, static_cast<int>(cell), x, y, hist, dE);
+                                        float x, float y, uint32_t hist, uint32_t flags, float dE) {
+    if (EPID) deposit_epid(P, s_energy, static_cast<int>(cell), x, y, hist, flags, dE);
     else if (dE > 0.0f) a.ct += quanta(dE);
 }
 
@@ -79,12 +81,13 @@ __device__ __forceinline__ void deposit(const Params& P, Acc& a, unsigned long l
 // Any point of the line will do: the CT lies wholly above the detector.
 __device__ __forceinline__ bool transfer_to_epid(const Params& P, Part& p, Acc& a, unsigned long long* s_events,
                                                  bool is_photon) {
+    const FieldDev& F = P.fields[field_of(p.flags)];
     float bx, by, bz, bu, bv, bw;
-    to_beam(P, p.x, p.y, p.z, bx, by, bz);
-    to_beam_dir(P, p.u, p.v, p.w, bu, bv, bw);
+    to_beam(F, p.x, p.y, p.z, bx, by, bz);
+    to_beam_dir(F, p.u, p.v, p.w, bu, bv, bw);
     const float eexit = p.E + rest_extra(p.flags);
     if (bw >= 0.0f) { a.esc += quanta(eexit); return false; }
-    const float t = (P.zface - bz) / bw;
+    const float t = (F.zface - bz) / bw;
     const float X = bx + t * bu, Y = by + t * bv;
     if (!(fabsf(X) < P.hwx && fabsf(Y) < P.hwy)) { a.esc += quanta(eexit); return false; }
     // inside the detector z is measured from its face, where single precision
@@ -112,7 +115,7 @@ __device__ __forceinline__ void charged(const Params& P, Acc& a, unsigned long l
         e.flags = kCollided | (positron ? kPositron : 0u);
         atomicAdd(&s_events[positron ? kCPositrons : kCElectrons], 1ull);
     } else {
-        deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, T);
+        deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, p.flags, T);
     }
 }
 
@@ -209,7 +212,7 @@ __device__ __forceinline__ bool photon_interact(const Params& P, Acc& a, unsigne
         charged<EPID>(P, a, s_energy, s_events, p, e0, T, eu, ev, ew, 0u, false);
         p.E = E1;
         if (p.E < P.pcut) {
-            deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, p.E);
+            deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, p.flags, p.E);
             return false;
         }
         return true;
@@ -228,11 +231,11 @@ __device__ __forceinline__ bool photon_interact(const Params& P, Acc& a, unsigne
         if (Tp > P.ecut + kStopMargin) {
             charged<EPID>(P, a, s_energy, s_events, p, e1, Tp, p.u, p.v, p.w, 1u, true);
         } else {
-            deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, Tp);
+            deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, p.flags, Tp);
             annihilate<EPID>(P, s_events, p, e1);
         }
     } else {
-        deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, Tm + Tp);
+        deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, p.flags, Tm + Tp);
         annihilate<EPID>(P, s_events, p, e0);
     }
     return false;
@@ -469,14 +472,14 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     const float dE = dEt * ((s1 + s2) / sE);
     const float Tn = T - dE;
     if (Tn <= P.tstop) {
-        deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, dE + Tn);
+        deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, p.flags, dE + Tn);
         if (p.flags & kPositron) {
             p.x = hx; p.y = hy; p.z = hz; p.cell = hcell;
             annihilate<EPID>(P, s_events, p, e0);
         }
         return false;
     }
-    deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, dE);
+    deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, p.flags, dE);
     p.E = Tn;
     if (crossed) {
         bool out;
@@ -529,7 +532,7 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
         p.E = Tn - k;
     }
     if (p.E <= P.tstop) {
-        deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, p.E);
+        deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, p.flags, p.E);
         if (p.flags & kPositron) annihilate<EPID>(P, s_events, p, e1);
         return false;
     }
@@ -567,7 +570,7 @@ __device__ __forceinline__ void flush_emission(const Params& P, const Emit& e, c
             const uint32_t slot = first + k;
             const float sg = (k == 0u) ? 1.0f : -1.0f;
             const uint32_t ord = pairrec ? child_ordinal(e.ord, (e.flags >> 2) & 0x1fffffffu, k) : e.ord;
-            const uint32_t fl = pairrec ? kCollided : e.flags;
+            const uint32_t fl = (pairrec ? kCollided : e.flags) | (parent.flags & kFieldMask);
             if (slot < P.cap) {
                 b.x[slot] = parent.x; b.y[slot] = parent.y; b.z[slot] = parent.z;
                 b.u[slot] = sg * e.u; b.v[slot] = sg * e.v; b.w[slot] = sg * e.w;
@@ -587,34 +590,47 @@ __device__ __forceinline__ void flush_emission(const Params& P, const Emit& e, c
 
 }  // namespace
 
-// Samples the primary of run-local history `idx` into p (patient frame, at the
-// CT entry point) and returns whether it enters the CT; otherwise `move`
-// tells whether it reached the EPID face.
-__device__ __forceinline__ bool start_primary(const Params& P, uint32_t idx, Part& p, Acc& a,
+// Samples the primary of batch history `k` into p (patient frame, at the CT
+// entry point) and returns whether it enters the CT; otherwise `move` tells
+// whether it reached the EPID face.  The field is the one whose history range
+// [first[f], first[f+1]) holds k; the history id within its stream is
+// hist_base + k - first[f].
+__device__ __forceinline__ bool start_primary(const Params& P, unsigned long long k, Part& p, Acc& a,
                                               unsigned long long* s_events, bool& move) {
+    int f = 0;
+    {
+        int lo = 0, hi = P.n_fields - 1;            // last f with first[f] <= k
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&P.first[mid]) <= k) lo = mid; else hi = mid - 1;
+        }
+        f = lo;
+    }
+    const FieldDev& F = P.fields[f];
+    const uint32_t idx = static_cast<uint32_t>(k - __ldg(&P.first[f]));
     p.hist = idx;
     p.cell = 0u;
-    p.flags = 0u;
-    p.rng.setup(P.seed, P.hist_base + idx, 0u, 0u);
+    p.flags = static_cast<uint32_t>(f) << kFieldShift;
+    p.rng.setup(P.seed, F.hist_base + idx, 0u, 0u);
     const double xi = static_cast<double>(p.rng.u());
-    int lo = 0, hi = P.n_rect - 1;
+    int lo = 0, hi = F.n_rect - 1;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (xi < __ldg(&P.cdf[mid])) hi = mid; else lo = mid + 1;
+        if (xi < __ldg(&P.cdf[F.rect_off + mid])) hi = mid; else lo = mid + 1;
     }
-    const float4 r = __ldg(&P.rect[lo]);
+    const float4 r = __ldg(&P.rect[F.rect_off + lo]);
     const float X = r.x + (r.y - r.x) * p.rng.u();
     const float Y = r.z + (r.w - r.z) * p.rng.u();
     p.E = (P.mono_e > 0.0f) ? P.mono_e : sample_spectrum(p.rng, P.e_max, P.pcut);
     a.src += quanta(p.E);
-    const float nb = sqrtf(X * X + Y * Y + P.sad * P.sad);
-    const float bu = X / nb, bv = Y / nb, bw = -P.sad / nb;
-    p.x = P.iso[0] + P.sad * P.ez[0];
-    p.y = P.iso[1] + P.sad * P.ez[1];
-    p.z = P.iso[2] + P.sad * P.ez[2];
-    p.u = bu * P.ex[0] + bv * P.ey[0] + bw * P.ez[0];
-    p.v = bu * P.ex[1] + bv * P.ey[1] + bw * P.ez[1];
-    p.w = bu * P.ex[2] + bv * P.ey[2] + bw * P.ez[2];
+    const float nb = sqrtf(X * X + Y * Y + F.sad * F.sad);
+    const float bu = X / nb, bv = Y / nb, bw = -F.sad / nb;
+    p.x = F.iso[0] + F.sad * F.ez[0];
+    p.y = F.iso[1] + F.sad * F.ez[1];
+    p.z = F.iso[2] + F.sad * F.ez[2];
+    p.u = bu * F.ex[0] + bv * F.ey[0] + bw * F.ez[0];
+    p.v = bu * F.ex[1] + bv * F.ey[1] + bw * F.ez[1];
+    p.w = bu * F.ex[2] + bv * F.ey[2] + bw * F.ez[2];
     // slab test against the CT box
     const float lo3[3] = {P.ox, P.oy, P.oz};
     const float hi3[3] = {P.ox + P.nx * P.vx, P.oy + P.ny * P.vy, P.oz + P.nz * P.vz};
@@ -697,7 +713,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
             base = __shfl_sync(kFull, base, leader);
             const unsigned long long idx = base + __popc(m & lanemask_lt());
             if (need && idx < prim_limit) {
-                alive = start_primary(P, static_cast<uint32_t>(idx), p, acc, s_events, move);
+                alive = start_primary(P, idx, p, acc, s_events, move);
                 steps_here = 0;
             }
             if (base + __popc(m) >= prim_limit) src_open = false;
@@ -774,6 +790,19 @@ __global__ void k_wave_begin(Ctl* c, unsigned long long per_wave) {
     c->allow_flush = (lim < c->n_total) ? 1u : 0u;
 }
 
+// Closes a wave of a graph-driven run: counts it and tells the enclosing
+// conditional while-node whether another wave is needed (work left, no error,
+// under the wave cap), so the loop ends on the device without a host sync.
+__global__ void k_wave_end(Ctl* c, cudaGraphConditionalHandle h, unsigned int max_waves) {
+    bool empty = c->next_prim >= c->n_total;
+#pragma unroll
+    for (int t = 0; t < kNumBanks; ++t) empty = empty && (c->count[t][c->cur[t]] == 0u);
+    c->waves += 1u;
+    const unsigned int more = (!empty && c->error == 0u && c->waves < max_waves) ? 1u : 0u;
+    c->more = more;
+    cudaGraphSetConditional(h, more);
+}
+
 // ----------------------------------------------------------- launchers ---
 
 size_t transport_smem(int type) {
@@ -828,6 +857,11 @@ cudaError_t launch_transport(int type, int minb, const Params& P, int grid, int 
 
 cudaError_t launch_swap(Ctl* c, int t, cudaStream_t s) {
     k_swap<<<1, 1, 0, s>>>(c, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wave_end(Ctl* c, cudaGraphConditionalHandle h, unsigned int max_waves, cudaStream_t s) {
+    k_wave_end<<<1, 1, 0, s>>>(c, h, max_waves);
     return cudaGetLastError();
 }
 
