@@ -15,8 +15,9 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 LIB = PKG / "libarcher_epid.so"
-SOURCES = ["mc_api.cu", "mc_transport.cu", "mc_aux.cu", "mc_noalloc.cu", "physics_tables.cpp"]
-HEADERS = ["mc_device.cuh", "mc_aux.h", "physics_tables.h"]
+SOURCES = ["mc_api.cu", "mc_transport.cu", "mc_aux.cu", "mc_noalloc.cu", "physics_tables.cpp", "dn_kernels.cu",
+           "dn_api.cu"]
+HEADERS = ["mc_device.cuh", "mc_aux.h", "physics_tables.h", "dn_tc.cuh", "dn_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,7 +30,7 @@ def stale() -> bool:
     if not LIB.exists():
         return True
     t = LIB.stat().st_mtime
-    deps = [CSRC / s for s in SOURCES + HEADERS] + [INCLUDE / "archer_epid.h"]
+    deps = [CSRC / s for s in SOURCES + HEADERS] + [INCLUDE / "archer_epid.h", INCLUDE / "archer_denoise.h"]
     return any(d.stat().st_mtime > t for d in deps)
 
 

@@ -1,0 +1,671 @@
+// Kernels of the EPID-image denoiser (a 2D U-Net trained on pairs of
+// low- and high-count Monte Carlo images).
+//
+// Convolutions run on the fifth-generation tensor cores as implicit GEMMs:
+//   forward / input gradient: M = 128 pixels of one image row (a TMA box of
+//     the NHWC activation shifted by the tap offset; zero fill supplies the
+//     padding), N = output channels, K = taps x input channels.  A producer
+//     thread streams (activation, weight) tile pairs through a ring of
+//     shared-memory stages with TMA; one thread issues tcgen05.mma into a TMEM
+//     accumulator; four warps read the accumulator back (tcgen05.ld) and apply
+//     the epilogue (bias, ReLU, the ReLU mask of the layer below, the split of
+//     a concatenated input, bf16 rounding).
+//   weight gradient: M = 128 output channels, N = 64 input channels, K =
+//     pixels; both operands are read channel-contiguous (MN-major) straight
+//     from the NHWC tensors, one tap row per CTA with its three column taps
+//     in three TMEM accumulators, split over pixel ranges and reduced with
+//     f32 atomics.
+// Everything else (pooling, upsampling, loss, Adam, weight packing) is
+// HBM-bound pointwise work on CUDA cores.
+#include "dn_kernels.cuh"
+#include "dn_tc.cuh"
+
+namespace dn {
+
+namespace {
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+    const uint32_t a = smem_u32(p);
+    return p + ((1024u - (a & 1023u)) & 1023u);
+}
+
+struct KStep {
+    int tap, s, ch;
+};
+
+__device__ __forceinline__ KStep kstep(const ConvArgs& a, int i) {
+    const int chunks = a.src[0].nch + (a.nsrc > 1 ? a.src[1].nch : 0);
+    KStep k;
+    k.tap = i / chunks;
+    const int r = i - k.tap * chunks;
+    k.s = (r < a.src[0].nch) ? 0 : 1;
+    k.ch = k.s ? r - a.src[0].nch : r;
+    return k;
+}
+
+}  // namespace
+
+// ------------------------------------------------------- convolution ------
+
+__global__ void __launch_bounds__(128) k_conv(const __grid_constant__ CUtensorMap ta0,
+                                              const __grid_constant__ CUtensorMap ta1,
+                                              const __grid_constant__ CUtensorMap tb0,
+                                              const __grid_constant__ CUtensorMap tb1, const ConvArgs a) {
+    extern __shared__ uint8_t dsm[];
+    uint8_t* tiles = align1024(dsm);
+    const int S = a.stages;
+    uint64_t* full = reinterpret_cast<uint64_t*>(tiles + S * a.stage_bytes);
+    uint64_t* empty = full + S;
+    uint64_t* done = empty + S;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const int segs = (a.W + 127) >> 7;
+    int t = blockIdx.x;
+    const int xs = t % segs;
+    t /= segs;
+    const int y = t % a.H;
+    const int n = t / a.H;
+    const int x0 = xs << 7;
+    const int n0 = blockIdx.y * a.N_tile;
+    const int p = a.k >> 1;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(done, 1);
+        mbar_fence_init();
+        tma_prefetch(&ta0);
+        tma_prefetch(&tb0);
+        if (a.nsrc > 1) {
+            tma_prefetch(&ta1);
+            tma_prefetch(&tb1);
+        }
+    }
+    if (warp == 1) tmem_alloc(tslot, a.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0 && lane == 0) {
+        // producer: one (activation, weight) tile pair per K step
+        int issued = 0;
+        for (int i = 0; i < a.nk; ++i) {
+            const int st = i % S;
+            if (i >= S && !mbar_wait(&empty[st], ((i / S) - 1) & 1, a.err, kErrWaitEmpty)) break;
+            const KStep ks = kstep(a, i);
+            const ConvSrc& src = a.src[ks.s];
+            uint8_t* sa = tiles + st * a.stage_bytes;
+            uint8_t* sb = sa + a.a_region;
+            const uint32_t bytes = (128u + static_cast<uint32_t>(a.N_tile)) * static_cast<uint32_t>(src.CW) * 2u;
+            mbar_expect_tx(&full[st], bytes);
+            const int dy = ks.tap / a.k, dx = ks.tap - dy * a.k;
+            tma_load_4d(sa, ks.s ? &ta1 : &ta0, &full[st], ks.ch * src.CW, x0 + dx - p, y + dy - p, n);
+            tma_load_2d(sb, ks.s ? &tb1 : &tb0, &full[st], (ks.tap * src.nch + ks.ch) * src.CW, n0);
+            issued = i + 1;
+        }
+        // every copy this CTA started has landed before it may exit
+        for (int st = 0; st < S && st < issued; ++st) {
+            const int last = st + ((issued - 1 - st) / S) * S;
+            mbar_wait(&full[st], (last / S) & 1, a.err, kErrWaitTail);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        for (int i = 0; i < a.nk; ++i) {
+            const int st = i % S;
+            if (!mbar_wait(&full[st], (i / S) & 1, a.err, kErrWaitFull)) break;
+            tc_fence_after();
+            const KStep ks = kstep(a, i);
+            const int CW = a.src[ks.s].CW;
+            const uint32_t sa = smem_u32(tiles + st * a.stage_bytes);
+            const uint32_t sb = sa + a.a_region;
+            const uint32_t row = static_cast<uint32_t>(CW) * 2u;
+            const uint32_t swz = swz_for_row(row);
+            for (int kk = 0; kk < CW / 16; ++kk) {
+                const uint64_t da = smem_desc(sa + kk * 32u, 16u, 8u * row, swz);
+                const uint64_t db = smem_desc(sb + kk * 32u, 16u, 8u * row, swz);
+                tc_mma(tmem, da, db, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc_commit(&empty[st]);
+        }
+        tc_commit(done);
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(done, 0, a.err, kErrWaitDone);
+    tc_fence_after();
+    __syncwarp();
+
+    // epilogue: thread = pixel (TMEM lane), 16 channels per TMEM load
+    const int row = warp * 32 + lane;
+    const int x = x0 + row;
+    const bool valid = ok && x < a.W;
+    const size_t pix = (static_cast<size_t>(n) * a.H + y) * a.W + x;
+    const uint32_t tbase = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    for (int c = 0; c < a.N_tile; c += 16) {
+        float v[16];
+        tmem_ld16(tbase + static_cast<uint32_t>(c), v);
+        if (!valid) continue;
+        const int co0 = n0 + c;
+        if (co0 >= a.N) continue;
+        const int d = (a.ndst > 1 && co0 >= a.dst_split) ? 1 : 0;
+        const int cc0 = co0 - (d ? a.dst_split : 0);
+        const int dC = a.dst_C[d];
+        const int dend = d ? a.N : (a.ndst > 1 ? a.dst_split : a.N);
+        __nv_bfloat16* out = a.dst[d] + pix * dC;
+        const __nv_bfloat16* mk = a.mask[d] ? a.mask[d] + pix * dC : nullptr;
+        if (co0 + 16 <= dend && (dC & 7) == 0 && (cc0 & 7) == 0) {
+            // two 16-byte stores
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint4 mv = make_uint4(0, 0, 0, 0);
+                if (mk) mv = *reinterpret_cast<const uint4*>(mk + cc0 + 8 * h);
+                const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mv);
+                __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float val = v[8 * h + j];
+                    if (a.bias) val += __ldg(&a.bias[co0 + 8 * h + j]);
+                    if (a.relu) val = fmaxf(val, 0.0f);
+                    if (mk && !(__bfloat162float(mb[j]) > 0.0f)) val = 0.0f;
+                    o[j] = __float2bfloat16_rn(val);
+                }
+                *reinterpret_cast<uint4*>(out + cc0 + 8 * h) = *reinterpret_cast<const uint4*>(o);
+            }
+        } else {
+            for (int j = 0; j < 16; ++j) {
+                const int co = co0 + j;
+                if (co >= a.N) break;
+                const int dd = (a.ndst > 1 && co >= a.dst_split) ? 1 : 0;
+                const int cc = co - (dd ? a.dst_split : 0);
+                float val = v[j];
+                if (a.bias) val += __ldg(&a.bias[co]);
+                if (a.relu) val = fmaxf(val, 0.0f);
+                const size_t o = pix * a.dst_C[dd] + cc;
+                if (a.mask[dd] && !(__bfloat162float(a.mask[dd][o]) > 0.0f)) val = 0.0f;
+                a.dst[dd][o] = __float2bfloat16_rn(val);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, a.tmem_cols);
+}
+
+// ----------------------------------------------------- weight gradient -----
+
+__global__ void __launch_bounds__(128) k_wgrad(const __grid_constant__ CUtensorMap tz,
+                                               const __grid_constant__ CUtensorMap tx0,
+                                               const __grid_constant__ CUtensorMap tx1, const WgradArgs a) {
+    extern __shared__ uint8_t dsm[];
+    uint8_t* tiles = align1024(dsm);
+    const int S = a.stages;
+    uint64_t* full = reinterpret_cast<uint64_t*>(tiles + S * a.stage_bytes);
+    uint64_t* empty = full + S;
+    uint64_t* done = empty + S;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // blockIdx.x = ((co_tile * chunks) + chunk) * k + dy
+    const int chunks = a.src_chunks[0] + (a.nsrc > 1 ? a.src_chunks[1] : 0);
+    int b = blockIdx.x;
+    const int dy = b % a.k;
+    b /= a.k;
+    const int chunk = b % chunks;
+    const int co_tile = b / chunks;
+    const int s = chunk < a.src_chunks[0] ? 0 : 1;
+    const int ch = s ? chunk - a.src_chunks[0] : chunk;
+    const int p = a.k >> 1;
+    const int per = (a.ksteps + a.splits - 1) / a.splits;
+    const int j0 = blockIdx.y * per;
+    const int j1 = min(a.ksteps, j0 + per);
+    const int nk = max(j1 - j0, 0);
+    const int segs = (a.W + 127) >> 7;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(done, 1);
+        mbar_fence_init();
+        tma_prefetch(&tz);
+        tma_prefetch(s ? &tx1 : &tx0);
+    }
+    if (warp == 1) tmem_alloc(tslot, a.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const CUtensorMap* tx = s ? &tx1 : &tx0;
+
+    if (warp == 0 && lane == 0) {
+        int issued = 0;
+        for (int i = 0; i < nk; ++i) {
+            const int st = i % S;
+            if (i >= S && !mbar_wait(&empty[st], ((i / S) - 1) & 1, a.err, kErrWaitEmpty)) break;
+            const int j = j0 + i;
+            const int xs = j % segs;
+            const int yy = (j / segs) % a.H;
+            const int n = j / (segs * a.H);
+            const int x0 = xs << 7;
+            uint8_t* sa = tiles + st * a.stage_bytes;
+            uint8_t* sb = sa + a.b_region;
+            mbar_expect_tx(&full[st], (2u + static_cast<uint32_t>(a.k)) * 16384u);
+            const int co0 = co_tile * 128;
+            tma_load_4d(sa, &tz, &full[st], co0, x0, yy, n);
+            tma_load_4d(sa + 16384, &tz, &full[st], co0 + 64, x0, yy, n);
+            for (int dx = 0; dx < a.k; ++dx)
+                tma_load_4d(sb + dx * 16384, tx, &full[st], ch * 64, x0 + dx - p, yy + dy - p, n);
+            issued = i + 1;
+        }
+        for (int st = 0; st < S && st < issued; ++st) {
+            const int last = st + ((issued - 1 - st) / S) * S;
+            mbar_wait(&full[st], (last / S) & 1, a.err, kErrWaitTail);
+        }
+    } else if (warp == 1 && lane == 0) {
+        for (int i = 0; i < nk; ++i) {
+            const int st = i % S;
+            if (!mbar_wait(&full[st], (i / S) & 1, a.err, kErrWaitFull)) break;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(tiles + st * a.stage_bytes);
+            const uint32_t sb = sa + a.b_region;
+            for (int dx = 0; dx < a.k; ++dx) {
+                for (int kk = 0; kk < 8; ++kk) {
+                    // 16 pixels = two 8-row groups of 1024 bytes
+                    const uint64_t da = smem_desc(sa + kk * 2048u, 16384u, 1024u, kSw128);
+                    const uint64_t db = smem_desc(sb + dx * 16384u + kk * 2048u, 16384u, 1024u, kSw128);
+                    tc_mma(tmem + static_cast<uint32_t>(dx * 64), da, db, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                }
+            }
+            tc_commit(&empty[st]);
+        }
+        tc_commit(done);
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(done, 0, a.err, kErrWaitDone) && nk > 0;
+    tc_fence_after();
+    __syncwarp();
+
+    const int co = co_tile * 128 + warp * 32 + lane;
+    const uint32_t tbase = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    const int Cs = a.src_C[s];
+    for (int dx = 0; dx < a.k; ++dx) {
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            tmem_ld16(tbase + static_cast<uint32_t>(dx * 64 + c), v);
+            if (!ok || co >= a.Co) continue;
+            float* dst = a.dW + ((static_cast<size_t>(co) * a.k + dy) * a.k + dx) * a.ci_total + a.src_coff[s];
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+                const int ci = ch * 64 + c + jj;
+                if (ci < Cs) atomicAdd(dst + ci, v[jj]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, a.tmem_cols);
+}
+
+// ---------------------------------------------------------- pointwise -----
+
+namespace {
+
+constexpr int kThreads = 256;
+
+int blocks_for(long long n) {
+    long long b = (n + kThreads - 1) / kThreads;
+    if (b < 1) b = 1;
+    if (b > 148 * 64) b = 148 * 64;
+    return static_cast<int>(b);
+}
+
+__device__ __forceinline__ void load8(const __nv_bfloat16* p, float* f) {
+    const uint4 u = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat16* b = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) f[i] = __bfloat162float(b[i]);
+}
+
+__device__ __forceinline__ void store8(__nv_bfloat16* p, const float* f) {
+    __align__(16) __nv_bfloat16 b[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) b[i] = __float2bfloat16_rn(f[i]);
+    *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(b);
+}
+
+}  // namespace
+
+// one thread per (pooled pixel, 8 channels)
+__global__ void k_maxpool(const __nv_bfloat16* __restrict__ x, __nv_bfloat16* __restrict__ y, int Nb, int H, int W,
+                          int C) {
+    const int h = H >> 1, w = W >> 1, c8 = C >> 3;
+    const long long total = static_cast<long long>(Nb) * h * w * c8;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(i % c8) * 8;
+        long long r = i / c8;
+        const int xo = static_cast<int>(r % w);
+        r /= w;
+        const int yo = static_cast<int>(r % h);
+        const int n = static_cast<int>(r / h);
+        float m[8], f[8];
+        load8(x + ((static_cast<size_t>(n) * H + 2 * yo) * W + 2 * xo) * C + c, m);
+        for (int q = 1; q < 4; ++q) {
+            load8(x + ((static_cast<size_t>(n) * H + 2 * yo + (q >> 1)) * W + 2 * xo + (q & 1)) * C + c, f);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) m[k] = fmaxf(m[k], f[k]);
+        }
+        store8(y + ((static_cast<size_t>(n) * h + yo) * w + xo) * C + c, m);
+    }
+}
+
+// dx = (gradient routed to the first maximum of each 2x2 window) + add
+__global__ void k_maxpool_bwd(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ dy,
+                              const __nv_bfloat16* __restrict__ add, __nv_bfloat16* __restrict__ dx, int Nb, int H,
+                              int W, int C) {
+    const int h = H >> 1, w = W >> 1, c8 = C >> 3;
+    const long long total = static_cast<long long>(Nb) * h * w * c8;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(i % c8) * 8;
+        long long r = i / c8;
+        const int xo = static_cast<int>(r % w);
+        r /= w;
+        const int yo = static_cast<int>(r % h);
+        const int n = static_cast<int>(r / h);
+        float v[4][8], g[8], best[8];
+        int arg[8];
+        for (int q = 0; q < 4; ++q)
+            load8(x + ((static_cast<size_t>(n) * H + 2 * yo + (q >> 1)) * W + 2 * xo + (q & 1)) * C + c, v[q]);
+        load8(dy + ((static_cast<size_t>(n) * h + yo) * w + xo) * C + c, g);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            best[k] = v[0][k];
+            arg[k] = 0;
+        }
+        for (int q = 1; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (v[q][k] > best[k]) {
+                    best[k] = v[q][k];
+                    arg[k] = q;
+                }
+        for (int q = 0; q < 4; ++q) {
+            const size_t o = ((static_cast<size_t>(n) * H + 2 * yo + (q >> 1)) * W + 2 * xo + (q & 1)) * C + c;
+            float out[8], ad[8];
+            if (add) load8(add + o, ad);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) out[k] = (arg[k] == q ? g[k] : 0.0f) + (add ? ad[k] : 0.0f);
+            store8(dx + o, out);
+        }
+    }
+}
+
+__global__ void k_upsample(const __nv_bfloat16* __restrict__ x, __nv_bfloat16* __restrict__ y, int Nb, int h, int w,
+                           int C) {
+    const int H = 2 * h, W = 2 * w, c8 = C >> 3;
+    const long long total = static_cast<long long>(Nb) * H * W * c8;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(i % c8) * 8;
+        long long r = i / c8;
+        const int xx = static_cast<int>(r % W);
+        r /= W;
+        const int yy = static_cast<int>(r % H);
+        const int n = static_cast<int>(r / H);
+        const uint4 u = *reinterpret_cast<const uint4*>(x + ((static_cast<size_t>(n) * h + (yy >> 1)) * w + (xx >> 1)) * C + c);
+        *reinterpret_cast<uint4*>(y + ((static_cast<size_t>(n) * H + yy) * W + xx) * C + c) = u;
+    }
+}
+
+__global__ void k_upsample_bwd(const __nv_bfloat16* __restrict__ dy, __nv_bfloat16* __restrict__ dx, int Nb, int h,
+                               int w, int C) {
+    const int H = 2 * h, W = 2 * w, c8 = C >> 3;
+    const long long total = static_cast<long long>(Nb) * h * w * c8;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(i % c8) * 8;
+        long long r = i / c8;
+        const int xo = static_cast<int>(r % w);
+        r /= w;
+        const int yo = static_cast<int>(r % h);
+        const int n = static_cast<int>(r / h);
+        float s[8] = {0, 0, 0, 0, 0, 0, 0, 0}, f[8];
+        for (int q = 0; q < 4; ++q) {
+            load8(dy + ((static_cast<size_t>(n) * H + 2 * yo + (q >> 1)) * W + 2 * xo + (q & 1)) * C + c, f);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s[k] += f[k];
+        }
+        store8(dx + ((static_cast<size_t>(n) * h + yo) * w + xo) * C + c, s);
+    }
+}
+
+// db[co] += sum over pixels of dz[p][co]; block = 256 threads over (pixel
+// lane, channel) pairs, one f32 atomic per channel per block.
+__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dz, int Cz, int Co, long long npix, float* db) {
+    __shared__ float acc[256];
+    const int lanes = 256 / Co;              // Co divides 256 or is 1
+    const int c = threadIdx.x % Co;
+    const int l = threadIdx.x / Co;
+    float s = 0.0f;
+    if (l < lanes)
+        for (long long q = static_cast<long long>(blockIdx.x) * lanes + l; q < npix;
+             q += static_cast<long long>(gridDim.x) * lanes)
+            s += __bfloat162float(dz[q * Cz + c]);
+    acc[threadIdx.x] = (l < lanes) ? s : 0.0f;
+    __syncthreads();
+    if (threadIdx.x < Co) {
+        float t = 0.0f;
+        for (int k = 0; k < lanes; ++k) t += acc[k * Co + threadIdx.x];
+        atomicAdd(&db[threadIdx.x], t);
+    }
+}
+
+// Mean squared error of y against t (n values) and its gradient 2 (y - t) / n
+// (bf16, written with stride dy_stride; other channels of dy stay zero).
+// Per-block partial sums in FP64, then one block adds them in a fixed order.
+__global__ void k_mse(const __nv_bfloat16* __restrict__ y, int ys, const __nv_bfloat16* __restrict__ t, long long n,
+                      __nv_bfloat16* __restrict__ dy, int ds, double* partials) {
+    __shared__ double red[kThreads];
+    double s = 0.0;
+    const float scale = 2.0f / static_cast<float>(n);
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const float d = __bfloat162float(y[i * ys]) - __bfloat162float(t[i]);
+        s += static_cast<double>(d) * d;
+        dy[i * ds] = __float2bfloat16_rn(scale * d);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+__global__ void k_mse_final(const double* partials, int nparts, long long n, double* loss) {
+    __shared__ double red[kThreads];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partials[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = red[0] / static_cast<double>(n);
+}
+
+// Adam (Kingma and Ba, Algorithm 1); c1 = 1 - beta1^t, c2 = 1 - beta2^t.
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+                       float c2) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+__global__ void k_pack_fwd(const float* __restrict__ w, int Co, int rows, int k, int ci_total, int coff, int C,
+                           int CW, int nch, __nv_bfloat16* __restrict__ out) {
+    const int kk = k * k, row = kk * nch * CW;
+    const long long total = static_cast<long long>(rows) * row;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int co = static_cast<int>(i / row);
+        const int r = static_cast<int>(i % row);
+        const int tap = r / (nch * CW);
+        const int c = r % (nch * CW);
+        const float val =
+            (co < Co && c < C) ? w[(static_cast<size_t>(co) * kk + tap) * ci_total + coff + c] : 0.0f;
+        out[i] = __float2bfloat16_rn(val);
+    }
+}
+
+// Input-gradient operand: out[ci][t'][co] = w[co][k*k-1-t'][ci]
+__global__ void k_pack_dgrad(const float* __restrict__ w, int Co, int k, int ci_total, int rows, int CWz, int nchz,
+                             __nv_bfloat16* __restrict__ out) {
+    const int kk = k * k, row = kk * nchz * CWz;
+    const long long total = static_cast<long long>(rows) * row;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int ci = static_cast<int>(i / row);
+        const int r = static_cast<int>(i % row);
+        const int tp = r / (nchz * CWz);
+        const int co = r % (nchz * CWz);
+        const float val =
+            (co < Co && ci < ci_total) ? w[(static_cast<size_t>(co) * kk + (kk - 1 - tp)) * ci_total + ci] : 0.0f;
+        out[i] = __float2bfloat16_rn(val);
+    }
+}
+
+__global__ void k_prep(const float* __restrict__ img, float scale, long long npix, __nv_bfloat16* __restrict__ out,
+                       int out_C) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < npix;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        out[i * out_C] = __float2bfloat16_rn(img[i] * scale);
+        for (int c = 1; c < out_C; ++c) out[i * out_C + c] = __float2bfloat16_rn(0.0f);
+    }
+}
+
+__global__ void k_to_f32(const __nv_bfloat16* __restrict__ x, int stride, long long npix, float scale,
+                         float* __restrict__ out) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < npix;
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+        out[i] = __bfloat162float(x[i * stride]) * scale;
+}
+
+// ----------------------------------------------------------- launchers ----
+
+cudaError_t conv_prepare() {
+    cudaError_t e = cudaFuncSetAttribute(k_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    return e;
+}
+
+static size_t conv_smem(int stages, uint32_t stage_bytes) {
+    return 1024 + static_cast<size_t>(stages) * stage_bytes + (2 * stages + 1) * 8 + 16;
+}
+
+cudaError_t launch_conv(const CUtensorMap* ta, const CUtensorMap* tb, const ConvArgs& a, cudaStream_t s) {
+    const int segs = (a.W + 127) / 128;
+    const dim3 grid(segs * a.H * a.Nb, (a.N + a.N_tile - 1) / a.N_tile);
+    k_conv<<<grid, 128, conv_smem(a.stages, a.stage_bytes), s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0],
+                                                                 tb[a.nsrc > 1 ? 1 : 0], a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wgrad(const CUtensorMap* tz, const CUtensorMap* tx, const WgradArgs& a, cudaStream_t s) {
+    const int chunks = a.src_chunks[0] + (a.nsrc > 1 ? a.src_chunks[1] : 0);
+    const dim3 grid(a.co_tiles * chunks * a.k, a.splits);
+    k_wgrad<<<grid, 128, conv_smem(a.stages, a.stage_bytes), s>>>(*tz, tx[0], tx[a.nsrc > 1 ? 1 : 0], a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxpool(const __nv_bfloat16* x, __nv_bfloat16* y, int Nb, int H, int W, int C, cudaStream_t s) {
+    k_maxpool<<<blocks_for(static_cast<long long>(Nb) * (H / 2) * (W / 2) * (C / 8)), kThreads, 0, s>>>(x, y, Nb, H,
+                                                                                                      W, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxpool_bwd(const __nv_bfloat16* x, const __nv_bfloat16* dy, const __nv_bfloat16* add,
+                               __nv_bfloat16* dx, int Nb, int H, int W, int C, cudaStream_t s) {
+    k_maxpool_bwd<<<blocks_for(static_cast<long long>(Nb) * (H / 2) * (W / 2) * (C / 8)), kThreads, 0, s>>>(
+        x, dy, add, dx, Nb, H, W, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_upsample(const __nv_bfloat16* x, __nv_bfloat16* y, int Nb, int h, int w, int C, cudaStream_t s) {
+    k_upsample<<<blocks_for(static_cast<long long>(Nb) * 4 * h * w * (C / 8)), kThreads, 0, s>>>(x, y, Nb, h, w, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_upsample_bwd(const __nv_bfloat16* dy, __nv_bfloat16* dx, int Nb, int h, int w, int C,
+                                cudaStream_t s) {
+    k_upsample_bwd<<<blocks_for(static_cast<long long>(Nb) * h * w * (C / 8)), kThreads, 0, s>>>(dy, dx, Nb, h, w,
+                                                                                                 C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bias_grad(const __nv_bfloat16* dz, int Cz, int Co, long long npix, float* db, cudaStream_t s) {
+    const int lanes = 256 / Co;
+    long long b = (npix + lanes - 1) / lanes;
+    if (b > 148 * 8) b = 148 * 8;
+    if (b < 1) b = 1;
+    k_bias_grad<<<static_cast<int>(b), 256, 0, s>>>(dz, Cz, Co, npix, db);
+    return cudaGetLastError();
+}
+
+int mse_parts() { return 148 * 4; }
+
+cudaError_t launch_mse(const __nv_bfloat16* y, int ys, const __nv_bfloat16* t, long long n, __nv_bfloat16* dy,
+                       int ds, double* partials, int nparts, double* loss, cudaStream_t s) {
+    k_mse<<<nparts, kThreads, 0, s>>>(y, ys, t, n, dy, ds, partials);
+    k_mse_final<<<1, kThreads, 0, s>>>(partials, nparts, n, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
+                        float eps, float c1, float c2, cudaStream_t s) {
+    k_adam<<<blocks_for(n), kThreads, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_fwd(const float* w, int Co, int rows, int k, int ci_total, int coff, int C, int CW, int nch,
+                            __nv_bfloat16* out, cudaStream_t s) {
+    k_pack_fwd<<<blocks_for(static_cast<long long>(rows) * k * k * nch * CW), kThreads, 0, s>>>(
+        w, Co, rows, k, ci_total, coff, C, CW, nch, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_dgrad(const float* w, int Co, int k, int ci_total, int rows, int CWz, int nchz,
+                              __nv_bfloat16* out, cudaStream_t s) {
+    k_pack_dgrad<<<blocks_for(static_cast<long long>(rows) * k * k * nchz * CWz), kThreads, 0, s>>>(
+        w, Co, k, ci_total, rows, CWz, nchz, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const float* img, float scale, long long npix, __nv_bfloat16* out, int out_C,
+                        cudaStream_t s) {
+    k_prep<<<blocks_for(npix), kThreads, 0, s>>>(img, scale, npix, out, out_C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const __nv_bfloat16* x, int stride, long long npix, float scale, float* out,
+                          cudaStream_t s) {
+    k_to_f32<<<blocks_for(npix), kThreads, 0, s>>>(x, stride, npix, scale, out);
+    return cudaGetLastError();
+}
+
+}  // namespace dn

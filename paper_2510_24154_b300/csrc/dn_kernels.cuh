@@ -1,0 +1,88 @@
+// Argument blocks and launchers of the denoiser's kernels (internal header).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace dn {
+
+// One activation source of a convolution (two for a concatenated input):
+// channels stored (a multiple of 8) and the chunk of channels one K step
+// loads (16, 32 or 64: the tile row is 32, 64 or 128 bytes).
+struct ConvSrc {
+    int C, CW, nch;
+};
+
+// Implicit-GEMM convolution (forward, or input gradient with transposed
+// weights): out[n,y,x,j] = epilogue(sum over taps t, sources s, channels c of
+// src_s[n, y+dy_t-p, x+dx_t-p, c] * Wop_s[j][t][c]).
+struct ConvArgs {
+    int nsrc;
+    ConvSrc src[2];
+    int k;                      // 1 or 3 (p = k / 2)
+    int Nb, H, W;
+    int N;                      // output channels (GEMM N)
+    int N_tile, tmem_cols;
+    int nk;                     // K steps = k*k * (chunks of all sources)
+    int stages;
+    uint32_t stage_bytes, a_region;
+    uint32_t idesc;
+    const float* bias;          // [N] or null
+    int relu;
+    int ndst, dst_split;        // channels [0, split) -> dst[0], [split, N) -> dst[1]
+    __nv_bfloat16* dst[2];
+    int dst_C[2];
+    const __nv_bfloat16* mask[2];   // if set: zero where mask <= 0 (same layout as dst)
+    unsigned* err;
+};
+
+// Weight gradient: dW[co][dy][dx][coff_s + c] += sum over pixels of
+// dz[n,y,x,co] * src_s[n, y+dy-p, x+dx-p, c].
+struct WgradArgs {
+    int Nb, H, W, k;
+    int Co, co_tiles;
+    int nsrc;
+    int src_C[2], src_coff[2], src_chunks[2];
+    int ci_total;
+    int ksteps, splits;
+    int stages;
+    uint32_t stage_bytes, b_region;
+    uint32_t idesc;
+    int tmem_cols;
+    float* dW;
+    unsigned* err;
+};
+
+cudaError_t conv_prepare();
+cudaError_t launch_conv(const CUtensorMap* ta, const CUtensorMap* tb, const ConvArgs& a, cudaStream_t s);
+cudaError_t launch_wgrad(const CUtensorMap* tz, const CUtensorMap* tx, const WgradArgs& a, cudaStream_t s);
+
+// Pointwise and reduction kernels.
+cudaError_t launch_maxpool(const __nv_bfloat16* x, __nv_bfloat16* y, int Nb, int H, int W, int C, cudaStream_t s);
+cudaError_t launch_maxpool_bwd(const __nv_bfloat16* x, const __nv_bfloat16* dy, const __nv_bfloat16* add,
+                               __nv_bfloat16* dx, int Nb, int H, int W, int C, cudaStream_t s);
+cudaError_t launch_upsample(const __nv_bfloat16* x, __nv_bfloat16* y, int Nb, int h, int w, int C, cudaStream_t s);
+cudaError_t launch_upsample_bwd(const __nv_bfloat16* dy, __nv_bfloat16* dx, int Nb, int h, int w, int C,
+                                cudaStream_t s);
+cudaError_t launch_bias_grad(const __nv_bfloat16* dz, int Cz, int Co, long long npix, float* db, cudaStream_t s);
+cudaError_t launch_mse(const __nv_bfloat16* y, int y_stride, const __nv_bfloat16* t, long long n,
+                       __nv_bfloat16* dy, int dy_stride, double* partials, int nparts, double* loss, cudaStream_t s);
+int mse_parts();
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
+                        float eps, float c1, float c2, cudaStream_t s);
+// fp32 master weights [Co][k][k][Ci_total] -> bf16 operand of one source,
+// [rows >= Co][k*k][nch*CW] (forward) or the flipped transpose
+// [rows >= Ci_total][k*k][nchz*CWz] (input gradient); padding is zero.
+cudaError_t launch_pack_fwd(const float* w, int Co, int rows, int k, int ci_total, int coff, int C, int CW, int nch,
+                            __nv_bfloat16* out, cudaStream_t s);
+cudaError_t launch_pack_dgrad(const float* w, int Co, int k, int ci_total, int rows, int CWz, int nchz,
+                              __nv_bfloat16* out, cudaStream_t s);
+cudaError_t launch_prep(const float* img, float scale, long long npix, __nv_bfloat16* out, int out_C,
+                        cudaStream_t s);
+cudaError_t launch_to_f32(const __nv_bfloat16* x, int stride, long long npix, float scale, float* out,
+                          cudaStream_t s);
+
+}  // namespace dn

@@ -340,3 +340,26 @@ def config_anthropomorphic(n_histories=1_000_000_000, seed=4) -> Problem:
         phantom=ph, epid=epid_default(1190, 1190, 0.0336), field=fld,
         lut=lut_bilinear(), physics=Physics(coupled=True),
         n_histories=n_histories, seed=seed)
+
+
+# ------------------------------------------------------------ denoiser ----
+
+def unet_params(layer_shapes, seed=0, bias_sd=0.05):
+    """Seeded parameter vector for a network given as (name, Co, k, Ci)
+    tuples: per layer He-normal weights [Co][k][k][Ci] (sd sqrt(2 / (k k Ci)))
+    then biases N(0, bias_sd), float32."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for _, co, k, ci in layer_shapes:
+        parts.append(rng.normal(size=co * k * k * ci) * np.sqrt(2.0 / (k * k * ci)))
+        parts.append(rng.normal(size=co) * bias_sd)
+    return np.concatenate(parts).astype(np.float32)
+
+
+def bf16_values(rng, shape, scale=1.0, nonneg=False):
+    """Random float32 values that are exactly representable in bfloat16."""
+    a = rng.normal(size=shape) * scale
+    if nonneg:
+        a = np.abs(a)
+    u = a.astype(np.float32).view(np.uint32) & np.uint32(0xFFFF0000)
+    return u.view(np.float32)
