@@ -248,6 +248,20 @@ mc_status mc_set_history_base(mc_ctx* ctx, uint64_t next_history);
  * current wave (it then returns MC_ERR_CANCELLED). */
 mc_status mc_cancel(mc_ctx* ctx);
 
+/* Global gamma index (Low et al. 1998), the image comparison of Sec. 2.3.3:
+ * for each pixel of the reference image `ref` at or above threshold * max(ref),
+ * gamma = min over offsets r (a square sub-grid of step step_mm within
+ * radius_mm) of sqrt(|r|^2 / dta_mm^2 + (ev(x + r) - ref(x))^2 / (dd_frac *
+ * max(ref))^2), with `ev` bilinearly interpolated and clamped at the border.
+ * ref, ev: device double [ny][nx] (non-negative), pixel pitch pixel_mm;
+ * gamma: device double [ny][nx] (NaN below the threshold) or NULL;
+ * pass_rate (host) receives the fraction of evaluated pixels with gamma <= 1
+ * (1 if none is evaluated).  step_mm <= 0 selects min(pixel_mm, dta_mm / 10),
+ * radius_mm <= 0 selects 3 dta_mm.  Synchronizes `stream`. */
+mc_status mc_gamma(const double* ref, const double* ev, int nx, int ny, double pixel_mm, double dd_frac,
+                   double dta_mm, double threshold, double step_mm, double radius_mm, double* gamma,
+                   double* pass_rate, void* stream);
+
 /* Dose statistics without any device allocation.  The paper has no
  * counterpart: this serves callers that may not allocate device memory once
  * they are running, such as a QA service whose framework allocator has

@@ -28,7 +28,7 @@ EXPORTED = ("mc_config_default", "mc_create", "mc_destroy", "mc_init_geometry", 
             "mc_get_field_size", "mc_get_dose", "mc_get_epid_image", "mc_get_tmap", "mc_get_tally", "mc_field_size", "mc_get_stats",
             "mc_reset_tally", "mc_state_size", "mc_get_state", "mc_set_state", "mc_set_history_base", "mc_cancel",
             "mc_last_error",
-            "mc_status_string", "mc_test_philox", "mc_test_uniforms", "mc_dose_stats_noalloc")
+            "mc_status_string", "mc_test_philox", "mc_test_uniforms", "mc_dose_stats_noalloc", "mc_gamma")
 
 
 class Config(C.Structure):
@@ -123,6 +123,7 @@ def load(build_if_stale: bool = True):
     lib.mc_test_philox.argtypes = [vp, vp, i, vp]
     lib.mc_test_uniforms.argtypes = [u64, u64, u32, i, vp, vp]
     lib.mc_dose_stats_noalloc.argtypes = [vp, i, i, i, u64, d, vp, vp, vp, vp]
+    lib.mc_gamma.argtypes = [vp, vp, i, i, d, d, d, d, d, d, vp, P(d), vp]
     for name in EXPORTED:
         if name not in ("mc_config_default", "mc_last_error", "mc_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -406,3 +407,18 @@ def dose_stats_noalloc(tally, npx, npy, n_batches, n_histories, pixel_mass_kg, d
                                    _ptr(u) if u is not None else None, _stream_ptr(stream))
     if st:
         raise MCError(st, "mc_dose_stats_noalloc")
+
+
+def gamma(ref, ev, pixel_mm, dd=0.01, dta_mm=1.0, threshold=0.10, step_mm=0.0, radius_mm=0.0, out=None,
+          stream=None):
+    """Global gamma pass rate of `ev` against `ref` (CUDA float64 tensors
+    [ny][nx]); per-pixel values go to `out` (same shape) when given."""
+    lib = load()
+    ny, nx = ref.shape
+    rate = C.c_double()
+    st = lib.mc_gamma(_ptr(ref), _ptr(ev), nx, ny, float(pixel_mm), float(dd), float(dta_mm), float(threshold),
+                      float(step_mm), float(radius_mm), _ptr(out) if out is not None else None, C.byref(rate),
+                      _stream_ptr(stream))
+    if st != 0:
+        raise MCError(st, "mc_gamma failed")
+    return rate.value

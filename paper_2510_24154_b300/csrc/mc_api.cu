@@ -1036,6 +1036,28 @@ mc_status mc_cancel(mc_ctx* c) {
     return MC_OK;
 }
 
+mc_status mc_gamma(const double* ref, const double* ev, int nx, int ny, double pixel_mm, double dd_frac,
+                   double dta_mm, double threshold, double step_mm, double radius_mm, double* gamma,
+                   double* pass_rate, void* stream) {
+    if (!ref || !ev || !pass_rate || nx < 1 || ny < 1 || static_cast<long long>(nx) * ny > (1ll << 28) ||
+        !(pixel_mm > 0) || !(dd_frac > 0) || !(dta_mm > 0) || !(threshold >= 0))
+        return MC_ERR_ARG;
+    const double h = step_mm > 0 ? step_mm : std::fmin(pixel_mm, dta_mm / 10.0);
+    const double rad = radius_mm > 0 ? radius_mm : 3.0 * dta_mm;
+    if (rad / h > 4096.0) return MC_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    unsigned long long* scratch = nullptr;
+    if (cudaMalloc(&scratch, 3 * sizeof(unsigned long long)) != cudaSuccess) return MC_ERR_OOM;
+    unsigned long long counts[3] = {0, 0, 0};
+    cudaError_t e = mc::launch_gamma(ref, ev, nx, ny, pixel_mm, dd_frac, dta_mm, threshold, h, rad, gamma, scratch, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counts, scratch, sizeof(counts), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(scratch);
+    if (e != cudaSuccess) return MC_ERR_CUDA;
+    *pass_rate = counts[1] ? static_cast<double>(counts[2]) / static_cast<double>(counts[1]) : 1.0;
+    return MC_OK;
+}
+
 mc_status mc_test_philox(const uint32_t* in, uint32_t* out, int n, void* stream) {
     if (!in || !out || n < 0) return MC_ERR_ARG;
     if (n == 0) return MC_OK;

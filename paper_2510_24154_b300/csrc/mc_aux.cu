@@ -2,6 +2,8 @@
 // thickness ray sums (a9), dose statistics over the batch sub-tallies (a8) and
 // the k(t, s) dose-to-signal correction (a11), plus two diagnostics.
 #include "mc_aux.h"
+
+#include <algorithm>
 #include "mc_device.cuh"
 
 namespace mc {
@@ -283,6 +285,75 @@ cudaError_t launch_dose(const unsigned long long* tally, int npix, int B, const 
         k_u_partial<<<grid, block, 0, s>>>(dose, sigma, npix, max_bits, part_sum, part_cnt);
         k_u_final<<<1, 32, 0, s>>>(part_sum, part_cnt, grid, u);
     }
+    return cudaGetLastError();
+}
+
+// Global gamma index (Low et al. 1998) of `ev` against `ref`, one thread per
+// reference pixel: above the low-dose threshold, the least
+// sqrt(r^2 / dta^2 + (ev(x + r) - ref(x))^2 / dd^2) over sub-grid offsets r
+// of step h within the search radius, ev bilinearly interpolated (clamped at
+// the border); dd = dd_frac * max(ref).  FP64 throughout.
+__device__ double bilin_clamped(const double* img, int nx, int ny, double fx, double fy) {
+    fx = fmin(fmax(fx, 0.0), static_cast<double>(nx - 1));
+    fy = fmin(fmax(fy, 0.0), static_cast<double>(ny - 1));
+    const int x0 = static_cast<int>(floor(fx)), y0 = static_cast<int>(floor(fy));
+    const int x1 = x0 + 1 < nx ? x0 + 1 : x0, y1 = y0 + 1 < ny ? y0 + 1 : y0;
+    const double ax = fx - x0, ay = fy - y0;
+    return (1 - ay) * ((1 - ax) * img[static_cast<size_t>(y0) * nx + x0] + ax * img[static_cast<size_t>(y0) * nx + x1]) +
+           ay * ((1 - ax) * img[static_cast<size_t>(y1) * nx + x0] + ax * img[static_cast<size_t>(y1) * nx + x1]);
+}
+
+__global__ void k_max_f64(const double* __restrict__ a, size_t n, unsigned long long* max_bits) {
+    double m = 0.0;
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x)
+        m = fmax(m, a[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(max_bits, static_cast<unsigned long long>(__double_as_longlong(m)));
+}
+
+__global__ void k_gamma(const double* __restrict__ ref, const double* __restrict__ ev, int nx, int ny, double pix,
+                        double dd_frac, double dta, double thr_frac, double h, double rad,
+                        const unsigned long long* max_bits, double* gam, unsigned long long* counts) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx * ny) return;
+    const double rmax = __longlong_as_double(static_cast<long long>(*max_bits));
+    const double ddabs = dd_frac * rmax;
+    const int x = i % nx, y = i / nx;
+    if (ref[i] < thr_frac * rmax) {
+        if (gam) gam[i] = nan("");
+        return;
+    }
+    const int nsub = static_cast<int>(ceil(rad / h));
+    double best = INFINITY;
+    for (int sy = -nsub; sy <= nsub && best > 0.0; ++sy) {
+        for (int sx = -nsub; sx <= nsub; ++sx) {
+            const double dx = sx * h, dy = sy * h;
+            const double r2 = dx * dx + dy * dy;
+            if (r2 > rad * rad) continue;
+            const double dist2 = r2 / (dta * dta);
+            if (dist2 >= best) continue;
+            const double v = bilin_clamped(ev, nx, ny, x + dx / pix, y + dy / pix);
+            const double dv = (v - ref[i]) / ddabs;
+            const double g2 = dist2 + dv * dv;
+            if (g2 < best) best = g2;
+        }
+    }
+    const double gv = sqrt(best);
+    if (gam) gam[i] = gv;
+    atomicAdd(&counts[0], 1ull);
+    if (gv <= 1.0) atomicAdd(&counts[1], 1ull);
+}
+
+cudaError_t launch_gamma(const double* ref, const double* ev, int nx, int ny, double pix, double dd_frac, double dta,
+                         double thr_frac, double h, double rad, double* gam, unsigned long long* scratch,
+                         cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 3 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const size_t n = static_cast<size_t>(nx) * ny;
+    k_max_f64<<<static_cast<unsigned>(std::min<size_t>((n + 255) / 256, 1184)), 256, 0, s>>>(ref, n, scratch);
+    k_gamma<<<static_cast<unsigned>((n + 127) / 128), 128, 0, s>>>(ref, ev, nx, ny, pix, dd_frac, dta, thr_frac, h,
+                                                                   rad, scratch, gam, scratch + 1);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,77 @@
+"""Train and evaluate the denoiser on Monte Carlo pairs; prints one JSON line.
+
+    python -m paper_2510_24154_b300.denoise_experiment --pairs 128 --n-input 1e6 \
+        --n-target 1e9 --eval 8 --n-ref 1e10 --steps 3000
+
+The default sizes are the reduced data set (128 training pairs instead of
+2000, 8 held-out cases instead of 100) that one GPU session affords: the
+targets alone are 1.3e11 histories.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--pairs", type=int, default=128)
+    ap.add_argument("--n-input", type=float, default=1e6)
+    ap.add_argument("--n-target", type=float, default=1e9)
+    ap.add_argument("--eval", type=int, default=8)
+    ap.add_argument("--n-ref", type=float, default=1e10)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr-final", type=float, default=5e-5)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--bin", type=int, default=8)
+    args = ap.parse_args()
+    import torch
+    from .denoise import UNet
+    from .denoise_data import DoseSource, evaluate, make_pairs, train
+
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    src = DoseSource()
+    X, T, _ = make_pairs(src, range(args.pairs), int(args.n_input), int(args.n_target), args.seed)
+    t_pairs = time.perf_counter() - t0
+    mc_hist, mc_s = src.histories, src.seconds
+    net = UNet(768, 1024, batch=args.batch, levels=4, base_channels=32, seed=args.seed)
+    t1 = time.perf_counter()
+    losses = train(net, X, T, args.steps, args.lr, args.batch, seed=args.seed, log_every=max(args.steps // 20, 1),
+                   lr_final=args.lr_final)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    del X, T
+    # evaluation network: batch 1
+    params = net.params()
+    net.close()
+    ev_net = UNet(768, 1024, batch=1, levels=4, base_channels=32, seed=args.seed)
+    ev_net.set_params(params)
+    cases = range(100000, 100000 + args.eval)
+    t2 = time.perf_counter()
+    res = evaluate(ev_net, src, cases, int(args.n_input), int(args.n_ref), seed=args.seed, b=args.bin)
+    t_eval = time.perf_counter() - t2
+    line = {
+        "pairs": args.pairs, "n_input": args.n_input, "n_target": args.n_target, "eval_cases": args.eval,
+        "n_ref": args.n_ref, "steps": args.steps, "batch": args.batch, "lr": args.lr, "lr_final": args.lr_final, "bin": args.bin,
+        "gamma": f"2 %/2 mm global, 10 % threshold, binned {args.bin}x{args.bin} ({0.39 * args.bin:.2f} mm)",
+        "loss_first": losses[0][1], "loss_last": losses[-1][1], "losses": losses,
+        "gamma_raw_mean": float(np.mean([r["gamma_raw"] for r in res])),
+        "gamma_denoised_mean": float(np.mean([r["gamma_denoised"] for r in res])),
+        "rms_raw_mean": float(np.mean([r["rms_raw"] for r in res])),
+        "rms_denoised_mean": float(np.mean([r["rms_denoised"] for r in res])),
+        "cases": res, "seconds": {"pairs": t_pairs, "train": t_train, "eval": t_eval},
+        "mc_histories_for_pairs": mc_hist, "mc_seconds_for_pairs": mc_s,
+    }
+    print(json.dumps(line), flush=True)
+    ev_net.close()
+    src.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -228,3 +228,42 @@ def test_unet_full_size_forward_runs():
     loss = net.train_step(x, x, lr=1e-4)
     assert np.isfinite(loss)
     net.close()
+
+
+def test_gamma_kernel_matches_oracle():
+    """mc_gamma (GPU, FP64) against the oracle's gamma on the same images."""
+    import oracle
+    from paper_2510_24154_b300.binding import gamma
+    r = np.random.default_rng(9)
+    yy, xx = np.mgrid[0:60, 0:80]
+    ref = np.exp(-((yy - 30) ** 2 + (xx - 40) ** 2) / 300.0) + 0.05
+    for sig, shift in ((0.01, 0.0), (0.03, 0.7), (0.0, 1.6)):
+        ev = np.exp(-((yy - 30 - shift) ** 2 + (xx - 40) ** 2) / 300.0) + 0.05 + sig * r.normal(size=ref.shape)
+        for dd, dta, pix in ((0.02, 2.0, 2.5), (0.01, 1.0, 0.39 * 8)):
+            rate_o, g_o = oracle.gamma(ref, ev, pix, dd=dd, dta_mm=dta, threshold=0.10)
+            out = torch.empty((60, 80), dtype=torch.float64, device=DEV)
+            rate_g = gamma(torch.tensor(ref, device=DEV), torch.tensor(ev, device=DEV), pix, dd, dta, 0.10, out=out)
+            g_g = out.cpu().numpy()
+            assert np.array_equal(np.isnan(g_g), np.isnan(g_o))
+            ok = ~np.isnan(g_o)
+            assert np.allclose(g_g[ok], g_o[ok], rtol=1e-9, atol=1e-12)
+            near = np.abs(g_o[ok] - 1.0) < 1e-9          # decisions only differ within rounding of 1
+            assert abs(rate_g - rate_o) <= near.sum() / ok.sum() + 1e-15
+
+
+def test_denoiser_pipeline_on_mc_pairs_small():
+    """Pairs from the transport, a few training steps, gamma evaluation: the
+    pipeline runs end to end and the training loss falls."""
+    from paper_2510_24154_b300.denoise_data import DoseSource, evaluate, make_pairs, train
+    src = DoseSource()
+    X, T, s = make_pairs(src, range(4), 100_000, 10_000_000, seed=3)
+    assert X.shape == (4, 768, 1024) and torch.isfinite(X).all() and torch.isfinite(T).all()
+    assert abs(float(X.mean()) - 1.0) < 1e-3
+    net = D.UNet(768, 1024, batch=2, levels=4, base_channels=32, seed=3)
+    losses = train(net, X, T, 60, 1e-3, 2, log_every=10)
+    assert losses[-1][1] < losses[0][1]
+    ev = D.UNet(768, 1024, batch=1, levels=4, base_channels=32)
+    ev.set_params(net.params())
+    res = evaluate(ev, src, [1000], 100_000, 30_000_000, seed=3)
+    assert 0.0 <= res[0]["gamma_raw"] <= 1.0 and 0.0 <= res[0]["gamma_denoised"] <= 1.0
+    net.close(); ev.close(); src.close()
