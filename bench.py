@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--regs-variant", default="", help="CTAs/SM build per transport kernel, e.g. 3,3,3,3")
     ap.add_argument("--no-batched", action="store_true", help="skip the 25-field batched-plan leg")
     ap.add_argument("--batched-scale", type=float, default=1.0, help="scale of the batched plan's history counts")
+    ap.add_argument("--no-denoiser", action="store_true", help="skip the U-Net denoiser leg")
+    ap.add_argument("--dn-batch", type=int, default=4, help="images per denoiser training step")
     return ap.parse_args()
 
 
@@ -161,6 +163,76 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def unet_flops(H=768, W=1024, levels=4, c0=32):
+    """Algorithmic FLOPs of one image: forward, and forward + input gradients
+    + weight gradients (a training step), from the layer shapes (2 per MAC)."""
+    layers = []
+    ci = 1
+    for l in range(levels):
+        c = c0 << l
+        layers += [(l, c, 3, ci, l > 0), (l, c, 3, c, True)]
+        ci = c
+    for l in range(levels - 2, -1, -1):
+        c = c0 << l
+        layers += [(l, c, 3, (c0 << (l + 1)) + c, True), (l, c, 3, c, True)]
+    layers.append((0, 1, 1, c0, True))
+    fwd = dgrad = 0.0
+    for l, co, k, ci, has_dgrad in layers:
+        f = 2.0 * (H >> l) * (W >> l) * co * k * k * ci
+        fwd += f
+        dgrad += f if has_dgrad else 0.0
+    return fwd, 2.0 * fwd + dgrad
+
+
+def denoiser_leg(args, local, barrier):
+    """U-Net (768 x 1024, 4 levels, 32-256 channels) training and inference
+    throughput on the tensor-core kernels, against the measured bf16 peak."""
+    import torch
+    from paper_2510_24154_b300.denoise import UNet
+    B = args.dn_batch
+    net = UNet(768, 1024, batch=B, levels=4, base_channels=32, seed=1, device=local)
+    g = torch.Generator(device=f"cuda:{local}").manual_seed(5)
+    x = torch.rand((B, 768, 1024), device=f"cuda:{local}", generator=g)
+    t = torch.rand((B, 768, 1024), device=f"cuda:{local}", generator=g)
+    out = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        net.train_step(x, t, 1e-4, stream=stream, want_loss=False)
+    barrier()
+    steps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        net.train_step(x, t, 1e-4, stream=stream, want_loss=False)
+    e1.record(stream)
+    barrier()
+    train_ms = e0.elapsed_time(e1) / steps
+    for _ in range(3):
+        net.forward(x, out, stream=stream)
+    barrier()
+    e0.record(stream)
+    for _ in range(steps):
+        net.forward(x, out, stream=stream)
+    e1.record(stream)
+    barrier()
+    fwd_ms = e0.elapsed_time(e1) / steps
+    net.close()
+    f_fwd, f_train = unet_flops()
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, kind = float(json.load(f)["bf16_tflops_sustained"]), "measured (sustained bf16)"
+    except Exception:
+        peak, kind = 1400.0, "fallback (sustained bf16)"
+    ach = B * f_train / (train_ms / 1e3) / 1e12
+    return {"workload": f"U-Net 768x1024, 4 levels 32-256 channels, bf16 operands / f32 accumulate, batch {B}",
+            "train_step_ms": train_ms, "train_images_per_s": B * 1e3 / train_ms,
+            "forward_ms": fwd_ms, "infer_images_per_s": B * 1e3 / fwd_ms,
+            "flops_per_image": {"forward": f_fwd, "train": f_train},
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "peak_kind": kind, "scope": "whole training step (all kernels)"},
+            "forward_tflops": B * f_fwd / (fwd_ms / 1e3) / 1e12}
 
 
 def batched_plan(args, Simulator, W, p, extra, stream, local, rank, dist, barrier):
@@ -349,6 +421,9 @@ def main():
     batched = None
     if not args.no_batched:
         batched = batched_plan(args, Simulator, W, p, extra, stream, local, rank, dist, barrier)
+    denoiser = None
+    if not args.no_denoiser:
+        denoiser = denoiser_leg(args, local, barrier)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -370,7 +445,7 @@ def main():
                        "parallelism": f"history shards x{ws}, no collective"},
             "s_per_field_1pct": n_1pct / per_gpu_rate, "u_at_step": u, "histories_for_1pct": n_1pct,
             "roofline": roofline, "memory_roofline": memory_roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "batched_plan": batched,
+            "batched_plan": batched, "denoiser": denoiser,
             "gpu_launches": int(agg["launches"]), "clocks": clk.summary(), "wall_s_timed": wall,
             "paper_context": "about 90 s per IMRT field at 1e9 histories on an RTX 3090 (paper Sec. 4.1)",
         }

@@ -99,7 +99,7 @@ struct ConvPlan {
 // sources; wop[s]: packed bf16 operand [wrows][k*k*nch_s*CW_s].
 bool plan_conv(ConvPlan& P, int nsrc, const bf16* const src[2], const int srcC[2], int Nb, int H, int W, int k,
                const bf16* const wop[2], int wrows, int N, const float* bias, int relu, int ndst, int split,
-               bf16* const dst[2], const int dstC[2], const bf16* const mask[2], unsigned* err) {
+               bf16* const dst[2], const int dstC[2], const bf16* const mask[2], unsigned* err, int sm_count) {
     ConvArgs& a = P.a;
     std::memset(&a, 0, sizeof(a));
     a.nsrc = nsrc;
@@ -128,7 +128,8 @@ bool plan_conv(ConvPlan& P, int nsrc, const bf16* const src[2], const int srcC[2
     a.a_region = 128u * cwmax * 2u;
     const uint32_t b_bytes = ((static_cast<uint32_t>(a.N_tile) * cwmax * 2u + 1023u) / 1024u) * 1024u;
     a.stage_bytes = a.a_region + b_bytes;
-    a.stages = std::max(2, std::min(8, static_cast<int>((200u * 1024u) / a.stage_bytes)));
+    a.stages = std::max(2, std::min(16, static_cast<int>((200u * 1024u) / a.stage_bytes)));
+    a.grid = sm_count;
     a.idesc = dn::idesc_bf16(128, static_cast<uint32_t>(a.N_tile), 0, 0);
     a.bias = bias;
     a.relu = relu;
@@ -155,6 +156,10 @@ bool plan_wgrad(WgradPlan& P, const bf16* dz, int Cz, int Co, int nsrc, const bf
     a.Nb = Nb; a.H = H; a.W = W; a.k = k;
     a.Co = Co;
     a.co_tiles = (Co + 127) / 128;
+    // narrow layers put several taps into the 128 GEMM rows (dz must hold
+    // exactly Co channels so that one box is one tap)
+    a.mode = (k == 3 && (Co == 32 || Co == 64) && Cz == Co) ? 1 : 0;
+    a.G = a.mode ? 128 / Co : 1;
     a.nsrc = nsrc;
     int coff = 0, nch = 0;
     for (int s = 0; s < nsrc; ++s) {
@@ -166,18 +171,26 @@ bool plan_wgrad(WgradPlan& P, const bf16* dz, int Cz, int Co, int nsrc, const bf
         if (!act_map(&P.tx[s], src[s], Nb, H, W, srcC[s], 64)) return false;
     }
     if (nsrc == 1) P.tx[1] = P.tx[0];
-    if (!act_map(&P.tz, dz, Nb, H, W, Cz, 64)) return false;
+    if (!act_map(&P.tz, dz, Nb, H, W, Cz, a.mode ? Co : 64)) return false;
     a.ci_total = coff;
     a.ksteps = Nb * H * ((W + 127) / 128);
-    const int base = a.co_tiles * nch * k;
+    const int rows = a.mode == 0 ? a.co_tiles * k : (k * k + a.G - 1) / a.G;
+    const int base = rows * nch;
     int splits = (2 * sm_count + base - 1) / base;
     splits = std::max(1, std::min(splits, a.ksteps));
     a.splits = splits;
-    a.b_region = 32768u;
-    a.stage_bytes = 32768u + static_cast<uint32_t>(k) * 16384u;
+    if (a.mode == 0) {
+        a.b_region = 32768u;
+        a.stage_bytes = 32768u + static_cast<uint32_t>(k) * 16384u;
+        a.tmem_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(k * 64)));
+        a.idesc = dn::idesc_bf16(128, 64, 1, 1);
+    } else {
+        a.b_region = static_cast<uint32_t>(a.G) * 128u * Co * 2u;     // G dz boxes = 32 KB
+        a.stage_bytes = a.b_region + 16384u;
+        a.tmem_cols = 64;
+        a.idesc = dn::idesc_bf16(128, 64, 1, 1);
+    }
     a.stages = std::max(2, std::min(6, static_cast<int>((200u * 1024u) / a.stage_bytes)));
-    a.idesc = dn::idesc_bf16(128, 64, 1, 1);
-    a.tmem_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(k * 64)));
     a.dW = dW;
     a.err = err;
     return true;
@@ -493,7 +506,7 @@ mc_status build(dn_ctx* c) {
         bf16* dsts[2] = {o->p, nullptr};
         const int dC[2] = {o->C, 0};
         if (!plan_conv(ly.fwd, ly.nsrc, srcs, ly.srcC, o->Nb, o->H, o->W, ly.k, wops, ly.wf_rows, ly.Co,
-                       c->d_params + ly.b_off, ly.relu, 1, ly.Co, dsts, dC, nullptr, c->d_err))
+                       c->d_params + ly.b_off, ly.relu, 1, ly.Co, dsts, dC, nullptr, c->d_err, c->sm_count))
             return fail(c, MC_ERR_CUDA, "tensor map encoding failed (" + ly.name + ")");
         if (ly.has_dgrad) {
             const bf16* zs[2] = {ly.gout->p, nullptr};
@@ -503,7 +516,7 @@ mc_status build(dn_ctx* c) {
             const int gC[2] = {ly.srcC[0], ly.srcC[1]};
             const bf16* mk[2] = {ly.in[0]->p, ly.in[1] ? ly.in[1]->p : nullptr};
             if (!plan_conv(ly.bwd, 1, zs, zC, o->Nb, o->H, o->W, ly.k, wd2, ly.wd_rows, ly.srcC[0] + ly.srcC[1],
-                           nullptr, 0, ly.nsrc, ly.srcC[0], gd, gC, mk, c->d_err))
+                           nullptr, 0, ly.nsrc, ly.srcC[0], gd, gC, mk, c->d_err, c->sm_count))
                 return fail(c, MC_ERR_CUDA, "tensor map encoding failed (" + ly.name + " dgrad)");
         }
         if (!plan_wgrad(ly.wg, ly.gout->p, Cz, ly.Co, ly.nsrc, srcs, ly.srcC, o->Nb, o->H, o->W, ly.k,
@@ -701,6 +714,13 @@ mc_status prim_check(cudaStream_t s, unsigned* err) {
 
 bool chan_ok(int c) { return c > 0 && c % 8 == 0 && (c < 64 || c % 64 == 0) && c <= 1024; }
 
+int device_sms() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
 }  // namespace
 
 extern "C" {
@@ -738,7 +758,7 @@ mc_status dn_conv2d_forward(const uint16_t* x0, int c0, const uint16_t* x1, int 
     bf16* dst[2] = {reinterpret_cast<bf16*>(y), nullptr};
     const int dC[2] = {y_stride, 0};
     if (!plan_conv(P, nsrc, srcs, C, batch, height, width, k, wops, rows, co, bias, relu, 1, co, dst, dC, nullptr,
-                   err))
+                   err, device_sms()))
         return MC_ERR_CUDA;
     if (dn::launch_conv(P.ta, P.tb, P.a, s) != cudaSuccess) return MC_ERR_CUDA;
     return prim_check(s, err);
@@ -771,7 +791,8 @@ mc_status dn_conv2d_backward_data(const uint16_t* dz, int dz_stride, int co, int
     bf16* dst[2] = {reinterpret_cast<bf16*>(dx0), reinterpret_cast<bf16*>(dx1)};
     const int dC[2] = {c0, dx1 ? c1 : 0};
     const bf16* mk[2] = {reinterpret_cast<const bf16*>(mask0), reinterpret_cast<const bf16*>(mask1)};
-    if (!plan_conv(P, 1, zs, zC, batch, height, width, k, w2, rows, ci_total, nullptr, 0, ndst, c0, dst, dC, mk, err))
+    if (!plan_conv(P, 1, zs, zC, batch, height, width, k, w2, rows, ci_total, nullptr, 0, ndst, c0, dst, dC, mk, err,
+                   device_sms()))
         return MC_ERR_CUDA;
     if (dn::launch_conv(P.ta, P.tb, P.a, s) != cudaSuccess) return MC_ERR_CUDA;
     return prim_check(s, err);

@@ -18,6 +18,8 @@
 // Everything else (pooling, upsampling, loss, Adam, weight packing) is
 // HBM-bound pointwise work on CUDA cores.
 #include "dn_kernels.cuh"
+
+#include <algorithm>
 #include "dn_tc.cuh"
 
 namespace dn {
@@ -47,7 +49,14 @@ __device__ __forceinline__ KStep kstep(const ConvArgs& a, int i) {
 
 // ------------------------------------------------------- convolution ------
 
-__global__ void __launch_bounds__(128) k_conv(const __grid_constant__ CUtensorMap ta0,
+// Persistent: CTA b takes output tiles b, b + grid, ...; a tile is 128
+// pixels of one image row x N_tile output channels.  Warp 0 (one lane)
+// streams the (activation, weight) tile pairs of every K step of every tile
+// through a ring of `stages` shared-memory slots; warp 1 (one lane) issues the
+// MMAs of a tile into one of two TMEM accumulators; warps 2-5 drain the other
+// accumulator (tcgen05.ld), so a tile's epilogue overlaps the next tile's
+// MMAs.
+__global__ void __launch_bounds__(192) k_conv(const __grid_constant__ CUtensorMap ta0,
                                               const __grid_constant__ CUtensorMap ta1,
                                               const __grid_constant__ CUtensorMap tb0,
                                               const __grid_constant__ CUtensorMap tb1, const ConvArgs a) {
@@ -56,18 +65,15 @@ __global__ void __launch_bounds__(128) k_conv(const __grid_constant__ CUtensorMa
     const int S = a.stages;
     uint64_t* full = reinterpret_cast<uint64_t*>(tiles + S * a.stage_bytes);
     uint64_t* empty = full + S;
-    uint64_t* done = empty + S;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    uint64_t* accf = empty + S;      // [2] accumulator ready (MMA -> epilogue)
+    uint64_t* acce = accf + 2;       // [2] accumulator drained (epilogue -> MMA)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
+    volatile uint32_t* abort_flag = tslot + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const int segs = (a.W + 127) >> 7;
-    int t = blockIdx.x;
-    const int xs = t % segs;
-    t /= segs;
-    const int y = t % a.H;
-    const int n = t / a.H;
-    const int x0 = xs << 7;
-    const int n0 = blockIdx.y * a.N_tile;
+    const int n_tiles = (a.N + a.N_tile - 1) / a.N_tile;
+    const int total = segs * a.H * a.Nb * n_tiles;
     const int p = a.k >> 1;
 
     if (threadIdx.x == 0) {
@@ -75,7 +81,11 @@ __global__ void __launch_bounds__(128) k_conv(const __grid_constant__ CUtensorMa
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
-        mbar_init(done, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&acce[i], 4);
+        }
+        *abort_flag = 0u;
         mbar_fence_init();
         tma_prefetch(&ta0);
         tma_prefetch(&tb0);
@@ -84,118 +94,182 @@ __global__ void __launch_bounds__(128) k_conv(const __grid_constant__ CUtensorMa
             tma_prefetch(&tb1);
         }
     }
-    if (warp == 1) tmem_alloc(tslot, a.tmem_cols);
+    if (warp == 1) tmem_alloc(tslot, static_cast<uint32_t>(2 * a.tmem_cols));
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    if (warp == 0 && lane == 0) {
-        // producer: one (activation, weight) tile pair per K step
-        int issued = 0;
-        for (int i = 0; i < a.nk; ++i) {
-            const int st = i % S;
-            if (i >= S && !mbar_wait(&empty[st], ((i / S) - 1) & 1, a.err, kErrWaitEmpty)) break;
-            const KStep ks = kstep(a, i);
-            const ConvSrc& src = a.src[ks.s];
-            uint8_t* sa = tiles + st * a.stage_bytes;
-            uint8_t* sb = sa + a.a_region;
-            const uint32_t bytes = (128u + static_cast<uint32_t>(a.N_tile)) * static_cast<uint32_t>(src.CW) * 2u;
-            mbar_expect_tx(&full[st], bytes);
-            const int dy = ks.tap / a.k, dx = ks.tap - dy * a.k;
-            tma_load_4d(sa, ks.s ? &ta1 : &ta0, &full[st], ks.ch * src.CW, x0 + dx - p, y + dy - p, n);
-            tma_load_2d(sb, ks.s ? &tb1 : &tb0, &full[st], (ks.tap * src.nch + ks.ch) * src.CW, n0);
-            issued = i + 1;
-        }
-        // every copy this CTA started has landed before it may exit
-        for (int st = 0; st < S && st < issued; ++st) {
-            const int last = st + ((issued - 1 - st) / S) * S;
-            mbar_wait(&full[st], (last / S) & 1, a.err, kErrWaitTail);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        for (int i = 0; i < a.nk; ++i) {
-            const int st = i % S;
-            if (!mbar_wait(&full[st], (i / S) & 1, a.err, kErrWaitFull)) break;
-            tc_fence_after();
-            const KStep ks = kstep(a, i);
-            const int CW = a.src[ks.s].CW;
-            const uint32_t sa = smem_u32(tiles + st * a.stage_bytes);
-            const uint32_t sb = sa + a.a_region;
-            const uint32_t row = static_cast<uint32_t>(CW) * 2u;
-            const uint32_t swz = swz_for_row(row);
-            for (int kk = 0; kk < CW / 16; ++kk) {
-                const uint64_t da = smem_desc(sa + kk * 32u, 16u, 8u * row, swz);
-                const uint64_t db = smem_desc(sb + kk * 32u, 16u, 8u * row, swz);
-                tc_mma(tmem, da, db, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
-            }
-            tc_commit(&empty[st]);
-        }
-        tc_commit(done);
-    }
-    __syncwarp();
-    const bool ok = mbar_wait(done, 0, a.err, kErrWaitDone);
-    tc_fence_after();
-    __syncwarp();
+    // tile t -> (x segment, row, image, N tile); N tiles outermost so that
+    // neighbouring CTAs share input rows in L2
+    auto decode = [&](int t, int& x0, int& y, int& n, int& n0) {
+        const int per = segs * a.H * a.Nb;
+        const int nt = t / per;
+        int r = t - nt * per;
+        const int xs = r % segs;
+        r /= segs;
+        y = r % a.H;
+        n = r / a.H;
+        x0 = xs << 7;
+        n0 = nt * a.N_tile;
+    };
 
-    // epilogue: thread = pixel (TMEM lane), 16 channels per TMEM load
-    const int row = warp * 32 + lane;
-    const int x = x0 + row;
-    const bool valid = ok && x < a.W;
-    const size_t pix = (static_cast<size_t>(n) * a.H + y) * a.W + x;
-    const uint32_t tbase = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    for (int c = 0; c < a.N_tile; c += 16) {
-        float v[16];
-        tmem_ld16(tbase + static_cast<uint32_t>(c), v);
-        if (!valid) continue;
-        const int co0 = n0 + c;
-        if (co0 >= a.N) continue;
-        const int d = (a.ndst > 1 && co0 >= a.dst_split) ? 1 : 0;
-        const int cc0 = co0 - (d ? a.dst_split : 0);
-        const int dC = a.dst_C[d];
-        const int dend = d ? a.N : (a.ndst > 1 ? a.dst_split : a.N);
-        __nv_bfloat16* out = a.dst[d] + pix * dC;
-        const __nv_bfloat16* mk = a.mask[d] ? a.mask[d] + pix * dC : nullptr;
-        if (co0 + 16 <= dend && (dC & 7) == 0 && (cc0 & 7) == 0) {
-            // two 16-byte stores
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                uint4 mv = make_uint4(0, 0, 0, 0);
-                if (mk) mv = *reinterpret_cast<const uint4*>(mk + cc0 + 8 * h);
-                const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mv);
-                __align__(16) __nv_bfloat16 o[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    float val = v[8 * h + j];
-                    if (a.bias) val += __ldg(&a.bias[co0 + 8 * h + j]);
-                    if (a.relu) val = fmaxf(val, 0.0f);
-                    if (mk && !(__bfloat162float(mb[j]) > 0.0f)) val = 0.0f;
-                    o[j] = __float2bfloat16_rn(val);
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+                int x0, y, n, n0;
+                decode(t, x0, y, n, n0);
+                for (int i = 0; i < a.nk; ++i, ++it) {
+                    const uint32_t st = it % S;
+                    if (it >= static_cast<uint32_t>(S) &&
+                        !mbar_wait(&empty[st], ((it / S) - 1) & 1, a.err, kErrWaitEmpty)) {
+                        *abort_flag = 1u;
+                        break;
+                    }
+                    const KStep ks = kstep(a, i);
+                    const ConvSrc& src = a.src[ks.s];
+                    uint8_t* sa = tiles + st * a.stage_bytes;
+                    uint8_t* sb = sa + a.a_region;
+                    const uint32_t bytes =
+                        (128u + static_cast<uint32_t>(a.N_tile)) * static_cast<uint32_t>(src.CW) * 2u;
+                    mbar_expect_tx(&full[st], bytes);
+                    const int dy = ks.tap / a.k, dx = ks.tap - dy * a.k;
+                    tma_load_4d(sa, ks.s ? &ta1 : &ta0, &full[st], ks.ch * src.CW, x0 + dx - p, y + dy - p, n);
+                    tma_load_2d(sb, ks.s ? &tb1 : &tb0, &full[st], (ks.tap * src.nch + ks.ch) * src.CW, n0);
                 }
-                *reinterpret_cast<uint4*>(out + cc0 + 8 * h) = *reinterpret_cast<const uint4*>(o);
+                if (*abort_flag) break;
             }
-        } else {
-            for (int j = 0; j < 16; ++j) {
-                const int co = co0 + j;
-                if (co >= a.N) break;
-                const int dd = (a.ndst > 1 && co >= a.dst_split) ? 1 : 0;
-                const int cc = co - (dd ? a.dst_split : 0);
-                float val = v[j];
-                if (a.bias) val += __ldg(&a.bias[co]);
-                if (a.relu) val = fmaxf(val, 0.0f);
-                const size_t o = pix * a.dst_C[dd] + cc;
-                if (a.mask[dd] && !(__bfloat162float(a.mask[dd][o]) > 0.0f)) val = 0.0f;
-                a.dst[dd][o] = __float2bfloat16_rn(val);
+            // every copy this CTA started has landed before it may exit
+            const uint32_t issued = it;
+            for (uint32_t st = 0; st < static_cast<uint32_t>(S) && st < issued; ++st) {
+                const uint32_t last = st + ((issued - 1 - st) / S) * S;
+                mbar_wait(&full[st], (last / S) & 1, a.err, kErrWaitTail);
             }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t it = 0, lt = 0;
+            uint32_t commits[2] = {0u, 0u};
+            for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++lt) {
+                const uint32_t buf = lt & 1u;
+                if (lt >= 2 && !mbar_wait(&acce[buf], ((lt >> 1) - 1) & 1, a.err, kErrWaitEmpty)) {
+                    *abort_flag = 1u;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + buf * static_cast<uint32_t>(a.tmem_cols);
+                for (int i = 0; i < a.nk; ++i, ++it) {
+                    const uint32_t st = it % S;
+                    if (!mbar_wait(&full[st], (it / S) & 1, a.err, kErrWaitFull)) {
+                        *abort_flag = 1u;
+                        break;
+                    }
+                    tc_fence_after();
+                    const KStep ks = kstep(a, i);
+                    const int CW = a.src[ks.s].CW;
+                    const uint32_t sa = smem_u32(tiles + st * a.stage_bytes);
+                    const uint32_t sb = sa + a.a_region;
+                    const uint32_t row = static_cast<uint32_t>(CW) * 2u;
+                    const uint32_t swz = swz_for_row(row);
+                    for (int kk = 0; kk < CW / 16; ++kk) {
+                        const uint64_t da = smem_desc(sa + kk * 32u, 16u, 8u * row, swz);
+                        const uint64_t db = smem_desc(sb + kk * 32u, 16u, 8u * row, swz);
+                        tc_mma(d, da, db, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    tc_commit(&empty[st]);
+                }
+                tc_commit(&accf[buf]);   // also covers a tile cut short by an abort
+                ++commits[buf];
+                if (*abort_flag) break;
+            }
+            // no MMA of this CTA may still run when its TMEM is freed
+            for (int b = 0; b < 2; ++b)
+                if (commits[b]) mbar_wait(&accf[b], (commits[b] - 1) & 1, a.err, kErrWaitTail);
+        }
+    } else {
+        // epilogue warps 2-5: TMEM lane quarter q = warp % 4
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        uint32_t lt = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++lt) {
+            const uint32_t buf = lt & 1u;
+            const bool ok = mbar_wait(&accf[buf], (lt >> 1) & 1, a.err, kErrWaitDone);
+            tc_fence_after();
+            __syncwarp();
+            if (!ok || *abort_flag) {
+                *abort_flag = 1u;
+                break;
+            }
+            int x0, y, n, n0;
+            decode(t, x0, y, n, n0);
+            const int x = x0 + row;
+            const bool valid = x < a.W;
+            const size_t pix = (static_cast<size_t>(n) * a.H + y) * a.W + x;
+            const uint32_t tbase = tmem + buf * static_cast<uint32_t>(a.tmem_cols) + (static_cast<uint32_t>(q * 32) << 16);
+            for (int c = 0; c < a.N_tile; c += 16) {
+                float v[16];
+                tmem_ld16(tbase + static_cast<uint32_t>(c), v);
+                const int co0 = n0 + c;
+                if (!valid || co0 >= a.N) continue;
+                const int d = (a.ndst > 1 && co0 >= a.dst_split) ? 1 : 0;
+                const int cc0 = co0 - (d ? a.dst_split : 0);
+                const int dC = a.dst_C[d];
+                const int dend = d ? a.N : (a.ndst > 1 ? a.dst_split : a.N);
+                __nv_bfloat16* out = a.dst[d] + pix * dC;
+                const __nv_bfloat16* mk = a.mask[d] ? a.mask[d] + pix * dC : nullptr;
+                if (co0 + 16 <= dend && (dC & 7) == 0 && (cc0 & 7) == 0) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        uint4 mv = make_uint4(0, 0, 0, 0);
+                        if (mk) mv = *reinterpret_cast<const uint4*>(mk + cc0 + 8 * h);
+                        const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mv);
+                        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            float val = v[8 * h + j];
+                            if (a.bias) val += __ldg(&a.bias[co0 + 8 * h + j]);
+                            if (a.relu) val = fmaxf(val, 0.0f);
+                            if (mk && !(__bfloat162float(mb[j]) > 0.0f)) val = 0.0f;
+                            o[j] = __float2bfloat16_rn(val);
+                        }
+                        *reinterpret_cast<uint4*>(out + cc0 + 8 * h) = *reinterpret_cast<const uint4*>(o);
+                    }
+                } else {
+                    for (int j = 0; j < 16; ++j) {
+                        const int co = co0 + j;
+                        if (co >= a.N) break;
+                        const int dd = (a.ndst > 1 && co >= a.dst_split) ? 1 : 0;
+                        const int cc = co - (dd ? a.dst_split : 0);
+                        float val = v[j];
+                        if (a.bias) val += __ldg(&a.bias[co]);
+                        if (a.relu) val = fmaxf(val, 0.0f);
+                        const size_t o = pix * a.dst_C[dd] + cc;
+                        if (a.mask[dd] && !(__bfloat162float(a.mask[dd][o]) > 0.0f)) val = 0.0f;
+                        a.dst[dd][o] = __float2bfloat16_rn(val);
+                    }
+                }
+            }
+            // this warp's TMEM reads are complete (tcgen05.wait::ld): hand the buffer back
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[buf]);
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) tmem_dealloc(tmem, a.tmem_cols);
+    if (warp == 1) tmem_dealloc(tmem, static_cast<uint32_t>(2 * a.tmem_cols));
 }
 
 // ----------------------------------------------------- weight gradient -----
 
+// Two layouts of the product, both with K = 128 pixels of one row per step:
+//  mode 0 (Co >= 128 or k = 1): M = 128 output channels (two 64-channel TMA
+//    boxes of dz), N = 64 input channels of one source, one tap row dy per
+//    CTA and its k column taps as k accumulators (k shifted boxes of x);
+//  mode 1 (Co = 32 or 64, k = 3): M = G = 128 / Co taps x Co channels: the
+//    taps are moved onto dz, sum_p dz[p] x[p + o_t] = sum_q dz[q - o_t] x[q],
+//    so one unshifted box of x serves G shifted boxes of dz.
 __global__ void __launch_bounds__(128) k_wgrad(const __grid_constant__ CUtensorMap tz,
                                                const __grid_constant__ CUtensorMap tx0,
                                                const __grid_constant__ CUtensorMap tx1, const WgradArgs a) {
@@ -208,13 +282,15 @@ __global__ void __launch_bounds__(128) k_wgrad(const __grid_constant__ CUtensorM
     uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // blockIdx.x = ((co_tile * chunks) + chunk) * k + dy
     const int chunks = a.src_chunks[0] + (a.nsrc > 1 ? a.src_chunks[1] : 0);
     int b = blockIdx.x;
-    const int dy = b % a.k;
-    b /= a.k;
+    int dy = 0, co_tile = 0, group = 0;
+    if (a.mode == 0) {            // blockIdx.x = ((co_tile * chunks) + chunk) * k + dy
+        dy = b % a.k;
+        b /= a.k;
+    }
     const int chunk = b % chunks;
-    const int co_tile = b / chunks;
+    if (a.mode == 0) co_tile = b / chunks; else group = b / chunks;   // mode 1: (group * chunks) + chunk
     const int s = chunk < a.src_chunks[0] ? 0 : 1;
     const int ch = s ? chunk - a.src_chunks[0] : chunk;
     const int p = a.k >> 1;
@@ -223,6 +299,8 @@ __global__ void __launch_bounds__(128) k_wgrad(const __grid_constant__ CUtensorM
     const int j1 = min(a.ksteps, j0 + per);
     const int nk = max(j1 - j0, 0);
     const int segs = (a.W + 127) >> 7;
+    const int G = a.G;                                   // mode 1: taps per CTA
+    const uint32_t slice = 128u * static_cast<uint32_t>(a.Co) * 2u;   // mode 1: bytes of one dz box
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
@@ -253,12 +331,24 @@ __global__ void __launch_bounds__(128) k_wgrad(const __grid_constant__ CUtensorM
             const int x0 = xs << 7;
             uint8_t* sa = tiles + st * a.stage_bytes;
             uint8_t* sb = sa + a.b_region;
-            mbar_expect_tx(&full[st], (2u + static_cast<uint32_t>(a.k)) * 16384u);
-            const int co0 = co_tile * 128;
-            tma_load_4d(sa, &tz, &full[st], co0, x0, yy, n);
-            tma_load_4d(sa + 16384, &tz, &full[st], co0 + 64, x0, yy, n);
-            for (int dx = 0; dx < a.k; ++dx)
-                tma_load_4d(sb + dx * 16384, tx, &full[st], ch * 64, x0 + dx - p, yy + dy - p, n);
+            if (a.mode == 0) {
+                mbar_expect_tx(&full[st], (2u + static_cast<uint32_t>(a.k)) * 16384u);
+                const int co0 = co_tile * 128;
+                tma_load_4d(sa, &tz, &full[st], co0, x0, yy, n);
+                tma_load_4d(sa + 16384, &tz, &full[st], co0 + 64, x0, yy, n);
+                for (int dx = 0; dx < a.k; ++dx)
+                    tma_load_4d(sb + dx * 16384, tx, &full[st], ch * 64, x0 + dx - p, yy + dy - p, n);
+            } else {
+                mbar_expect_tx(&full[st], static_cast<uint32_t>(G) * slice + 16384u);
+                for (int g = 0; g < G; ++g) {
+                    const int t = group * G + g;
+                    // a tap past the last one loads a box wholly outside the image: zeros
+                    const int ty = t < a.k * a.k ? t / a.k : 0, tx_ = t < a.k * a.k ? t % a.k : 0;
+                    const int ycoord = t < a.k * a.k ? yy - ty + p : -1000000;
+                    tma_load_4d(sa + g * slice, &tz, &full[st], 0, x0 - tx_ + p, ycoord, n);
+                }
+                tma_load_4d(sb, tx, &full[st], ch * 64, x0, yy, n);
+            }
             issued = i + 1;
         }
         for (int st = 0; st < S && st < issued; ++st) {
@@ -266,16 +356,20 @@ __global__ void __launch_bounds__(128) k_wgrad(const __grid_constant__ CUtensorM
             mbar_wait(&full[st], (last / S) & 1, a.err, kErrWaitTail);
         }
     } else if (warp == 1 && lane == 0) {
+        const uint32_t a_row = a.mode == 0 ? 128u : static_cast<uint32_t>(a.Co) * 2u;   // bytes per pixel row of A
+        const uint32_t a_swz = a_row == 128u ? kSw128 : kSw64;
+        const uint32_t a_lbo = a.mode == 0 ? 16384u : slice;
         for (int i = 0; i < nk; ++i) {
             const int st = i % S;
             if (!mbar_wait(&full[st], (i / S) & 1, a.err, kErrWaitFull)) break;
             tc_fence_after();
             const uint32_t sa = smem_u32(tiles + st * a.stage_bytes);
             const uint32_t sb = sa + a.b_region;
-            for (int dx = 0; dx < a.k; ++dx) {
+            const int nacc = a.mode == 0 ? a.k : 1;
+            for (int dx = 0; dx < nacc; ++dx) {
                 for (int kk = 0; kk < 8; ++kk) {
-                    // 16 pixels = two 8-row groups of 1024 bytes
-                    const uint64_t da = smem_desc(sa + kk * 2048u, 16384u, 1024u, kSw128);
+                    // 16 pixels = two 8-row groups
+                    const uint64_t da = smem_desc(sa + kk * 16u * a_row, a_lbo, 8u * a_row, a_swz);
                     const uint64_t db = smem_desc(sb + dx * 16384u + kk * 2048u, 16384u, 1024u, kSw128);
                     tc_mma(tmem + static_cast<uint32_t>(dx * 64), da, db, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
                 }
@@ -289,15 +383,30 @@ __global__ void __launch_bounds__(128) k_wgrad(const __grid_constant__ CUtensorM
     tc_fence_after();
     __syncwarp();
 
-    const int co = co_tile * 128 + warp * 32 + lane;
+    const int r = warp * 32 + lane;                      // TMEM lane = GEMM row
     const uint32_t tbase = tmem + (static_cast<uint32_t>(warp * 32) << 16);
     const int Cs = a.src_C[s];
-    for (int dx = 0; dx < a.k; ++dx) {
+    int co, tap_y, tap_x0, ntap;
+    if (a.mode == 0) {
+        co = co_tile * 128 + r;
+        tap_y = dy;
+        tap_x0 = 0;
+        ntap = a.k;
+    } else {
+        co = r % a.Co;
+        const int t = group * G + r / a.Co;
+        tap_y = t / a.k;
+        tap_x0 = t % a.k;
+        ntap = (t < a.k * a.k) ? 1 : 0;
+    }
+    const int nacc = a.mode == 0 ? a.k : 1;
+    for (int dx = 0; dx < nacc; ++dx) {
         for (int c = 0; c < 64; c += 16) {
             float v[16];
             tmem_ld16(tbase + static_cast<uint32_t>(dx * 64 + c), v);
-            if (!ok || co >= a.Co) continue;
-            float* dst = a.dW + ((static_cast<size_t>(co) * a.k + dy) * a.k + dx) * a.ci_total + a.src_coff[s];
+            if (!ok || co >= a.Co || ntap == 0) continue;
+            const int tx_ = a.mode == 0 ? dx : tap_x0;
+            float* dst = a.dW + ((static_cast<size_t>(co) * a.k + tap_y) * a.k + tx_) * a.ci_total + a.src_coff[s];
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) {
                 const int ci = ch * 64 + c + jj;
@@ -575,20 +684,22 @@ cudaError_t conv_prepare() {
 }
 
 static size_t conv_smem(int stages, uint32_t stage_bytes) {
-    return 1024 + static_cast<size_t>(stages) * stage_bytes + (2 * stages + 1) * 8 + 16;
+    return 1024 + static_cast<size_t>(stages) * stage_bytes + (2 * stages + 4) * 8 + 16;
 }
 
 cudaError_t launch_conv(const CUtensorMap* ta, const CUtensorMap* tb, const ConvArgs& a, cudaStream_t s) {
     const int segs = (a.W + 127) / 128;
-    const dim3 grid(segs * a.H * a.Nb, (a.N + a.N_tile - 1) / a.N_tile);
-    k_conv<<<grid, 128, conv_smem(a.stages, a.stage_bytes), s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0],
+    const long long total = static_cast<long long>(segs) * a.H * a.Nb * ((a.N + a.N_tile - 1) / a.N_tile);
+    const int grid = static_cast<int>(std::min<long long>(total, a.grid));
+    k_conv<<<grid, 192, conv_smem(a.stages, a.stage_bytes), s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0],
                                                                  tb[a.nsrc > 1 ? 1 : 0], a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_wgrad(const CUtensorMap* tz, const CUtensorMap* tx, const WgradArgs& a, cudaStream_t s) {
     const int chunks = a.src_chunks[0] + (a.nsrc > 1 ? a.src_chunks[1] : 0);
-    const dim3 grid(a.co_tiles * chunks * a.k, a.splits);
+    const int rows = a.mode == 0 ? a.co_tiles * a.k : (a.k * a.k + a.G - 1) / a.G;
+    const dim3 grid(rows * chunks, a.splits);
     k_wgrad<<<grid, 128, conv_smem(a.stages, a.stage_bytes), s>>>(*tz, tx[0], tx[a.nsrc > 1 ? 1 : 0], a);
     return cudaGetLastError();
 }

@@ -28,6 +28,7 @@ struct ConvArgs {
     int N_tile, tmem_cols;
     int nk;                     // K steps = k*k * (chunks of all sources)
     int stages;
+    int grid;                   // persistent CTAs (one per SM)
     uint32_t stage_bytes, a_region;
     uint32_t idesc;
     const float* bias;          // [N] or null
@@ -40,9 +41,11 @@ struct ConvArgs {
 };
 
 // Weight gradient: dW[co][dy][dx][coff_s + c] += sum over pixels of
-// dz[n,y,x,co] * src_s[n, y+dy-p, x+dx-p, c].
+// dz[n,y,x,co] * src_s[n, y+dy-p, x+dx-p, c].  mode 0: M = 128 output
+// channels; mode 1 (Co = 32 or 64, k = 3): M = G = 128 / Co taps x Co.
 struct WgradArgs {
     int Nb, H, W, k;
+    int mode, G;
     int Co, co_tiles;
     int nsrc;
     int src_C[2], src_coff[2], src_chunks[2];

@@ -1,6 +1,7 @@
 """CPU checks of the C-ABI boundary: the library builds for sm_103a, loads, and
-exports every entry point include/archer_epid.h declares; the ctypes struct
-mirrors match the C layout.  No compute call is made (no GPU here)."""
+exports every entry point include/archer_epid.h and include/archer_denoise.h
+declare; the ctypes struct mirrors match the C layout.  No compute call is
+made (no GPU here)."""
 import ctypes as C
 import re
 import subprocess
@@ -9,20 +10,22 @@ from pathlib import Path
 
 import pytest
 
-from paper_2510_24154_b300 import binding, build
+from paper_2510_24154_b300 import binding, build, denoise
 
 ROOT = Path(__file__).resolve().parents[1]
 HEADER = ROOT / "include" / "archer_epid.h"
+DN_HEADER = ROOT / "include" / "archer_denoise.h"
 
 
-def declared_entry_points():
-    text = HEADER.read_text()
+def declared_entry_points(header=HEADER, prefix="mc_"):
+    text = header.read_text()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(mc_[a-z_0-9]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(" + prefix + r"[a-z_0-9]+)\s*\(", text)))
 
 
 def test_header_and_binding_agree():
     assert declared_entry_points() == sorted(binding.EXPORTED)
+    assert declared_entry_points(DN_HEADER, "dn_") == sorted(denoise.EXPORTED)
 
 
 def test_library_builds_and_exports_every_symbol():
@@ -30,11 +33,12 @@ def test_library_builds_and_exports_every_symbol():
     assert lib_path.exists()
     out = subprocess.run(["nm", "-D", "--defined-only", str(lib_path)], capture_output=True, text=True,
                          check=True).stdout
-    exported = set(re.findall(r"\bT\s+(mc_\w+)", out))
-    missing = set(declared_entry_points()) - exported
+    exported = set(re.findall(r"\bT\s+((?:mc|dn)_\w+)", out))
+    declared = set(declared_entry_points()) | set(declared_entry_points(DN_HEADER, "dn_"))
+    missing = declared - exported
     assert not missing, f"missing exports: {missing}"
     lib = C.CDLL(str(lib_path))
-    for name in declared_entry_points():
+    for name in declared:
         assert hasattr(lib, name)
 
 
@@ -83,3 +87,16 @@ def test_struct_layouts_match_c(tmp_path):
     assert offs == [binding.Config.use_graph.offset, binding.Config.regs_variant.offset, binding.EpidDesc.pitch_cm.offset,
                     binding.FieldDesc.eq1_literal.offset, binding.RunStats.gpu_ms.offset,
                     binding.RunStats.launches.offset]
+
+
+def test_denoise_config_layout_and_errors_without_gpu():
+    probe_ok = denoise.DnConfig()
+    lib = denoise.lib()
+    lib.dn_config_default(C.byref(probe_ok))
+    assert (probe_ok.height, probe_ok.width, probe_ok.levels, probe_ok.base_channels) == (768, 1024, 4, 32)
+    assert lib.dn_create(None, 0, None) == 1
+    bad = denoise.DnConfig(height=100, width=1024, batch=1, levels=4, base_channels=32, seed=0)   # not a multiple of 8
+    h = C.c_void_p()
+    assert lib.dn_create(C.byref(bad), 0, C.byref(h)) == 1 and not h.value
+    assert lib.dn_destroy(None) == 0
+    assert lib.dn_conv2d_forward(None, 32, None, 0, 1, 8, 8, None, None, 3, 32, 1, None, 32, None) == 1
