@@ -97,9 +97,21 @@ struct ConvPlan {
 
 // A convolution launch (forward or input gradient).  src/srcC: activation
 // sources; wop[s]: packed bf16 operand [wrows][k*k*nch_s*CW_s].
+// Column-taps-in-N variant: 3x3, 32 or 64 output channels, resident weights.
+bool dxn_fits(int k, int N, int nsrc, const int srcC[2]) {
+    if (k != 3 || !(N == 32 || N == 64)) return false;
+    size_t bytes = 0;
+    for (int s = 0; s < nsrc; ++s) {
+        const int CW = cw_for(srcC[s]);
+        bytes = (bytes + 1023) / 1024 * 1024 + static_cast<size_t>(3 * chunks(srcC[s], CW)) * 3 * N * CW * 2;
+    }
+    return bytes <= 150u * 1024u;
+}
+
 bool plan_conv(ConvPlan& P, int nsrc, const bf16* const src[2], const int srcC[2], int Nb, int H, int W, int k,
                const bf16* const wop[2], int wrows, int N, const float* bias, int relu, int ndst, int split,
-               bf16* const dst[2], const int dstC[2], const bf16* const mask[2], unsigned* err, int sm_count) {
+               bf16* const dst[2], const int dstC[2], const bf16* const mask[2], unsigned* err, int sm_count,
+               bool resident_ok = true, bool dxn = false) {
     ConvArgs& a = P.a;
     std::memset(&a, 0, sizeof(a));
     a.nsrc = nsrc;
@@ -117,8 +129,11 @@ bool plan_conv(ConvPlan& P, int nsrc, const bf16* const src[2], const int srcC[2
         cwmax = std::max(cwmax, a.src[s].CW);
         nch_total += a.src[s].nch;
         if (!act_map(&P.ta[s], src[s], Nb, H, W, srcC[s], a.src[s].CW)) return false;
-        if (!mat_map(&P.tb[s], wop[s], wrows, k * k * a.src[s].nch * a.src[s].CW, a.src[s].CW, a.N_tile))
+        if (dxn) {
+            if (!mat_map(&P.tb[s], wop[s], 3 * N, 3 * a.src[s].nch * a.src[s].CW, a.src[s].CW, 3 * N)) return false;
+        } else if (!mat_map(&P.tb[s], wop[s], wrows, k * k * a.src[s].nch * a.src[s].CW, a.src[s].CW, a.N_tile)) {
             return false;
+        }
     }
     if (nsrc == 1) {
         P.ta[1] = P.ta[0];
@@ -130,7 +145,52 @@ bool plan_conv(ConvPlan& P, int nsrc, const bf16* const src[2], const int srcC[2
     a.stage_bytes = a.a_region + b_bytes;
     a.stages = std::max(2, std::min(16, static_cast<int>((200u * 1024u) / a.stage_bytes)));
     a.grid = sm_count;
-    a.idesc = dn::idesc_bf16(128, static_cast<uint32_t>(a.N_tile), 0, 0);
+    // resident weights when they fit: R output rows per tile (TMEM holds two
+    // sets of R accumulators of N_tile columns)
+    uint32_t wb = 0, w_off1 = 0;
+    for (int s = 0; s < nsrc; ++s) {
+        if (s == 1) {
+            wb = (wb + 1023u) / 1024u * 1024u;
+            w_off1 = wb;
+        }
+        wb += static_cast<uint32_t>(k * k * a.src[s].nch) * a.N_tile * a.src[s].CW * 2u;
+    }
+    const uint32_t w_region = (wb + 1023u) / 1024u * 1024u;
+    if (dxn) {
+        uint32_t wbx = 0, off1 = 0;
+        for (int s = 0; s < nsrc; ++s) {
+            if (s == 1) {
+                wbx = (wbx + 1023u) / 1024u * 1024u;
+                off1 = wbx;
+            }
+            wbx += static_cast<uint32_t>(3 * a.src[s].nch) * 3u * N * a.src[s].CW * 2u;
+        }
+        a.dxn = 1;
+        a.rows_per_tile = 0;
+        a.w_off[0] = 0;
+        a.w_off[1] = off1;
+        a.w_bytes_real = wbx;
+        a.w_bytes = (wbx + 1023u) / 1024u * 1024u;
+        a.stage_bytes = a.a_region;
+        a.stages = std::max(2, std::min(16, static_cast<int>((205u * 1024u - a.w_bytes) / a.stage_bytes)));
+        a.N_tile = N;
+        a.tmem_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(6 * N)));
+        a.idesc = dn::idesc_bf16(128, static_cast<uint32_t>(3 * N), 0, 0);
+    } else if (n_tiles == 1 && w_region <= 150u * 1024u && resident_ok) {
+        int R = 4;
+        while (R > 1 && (2 * R * a.N_tile > 512 || R > H)) R >>= 1;
+        a.rows_per_tile = R;
+        a.w_off[0] = 0;
+        a.w_off[1] = w_off1;
+        a.w_bytes_real = wb;
+        a.w_bytes = w_region;
+        a.stage_bytes = a.a_region;
+        a.stages = std::max(2, std::min(16, static_cast<int>((205u * 1024u - w_region) / a.stage_bytes)));
+        a.tmem_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(2 * R * a.N_tile)));
+    } else {
+        a.rows_per_tile = 0;
+    }
+    if (!a.dxn) a.idesc = dn::idesc_bf16(128, static_cast<uint32_t>(a.N_tile), 0, 0);
     a.bias = bias;
     a.relu = relu;
     a.ndst = ndst;
@@ -221,6 +281,7 @@ struct ConvLayer {
     bf16* wd = nullptr;
     int wd_rows = 0, CWz = 16, nchz = 0;
     bool has_dgrad = true;
+    bool fwd_dxn = false, bwd_dxn = false;   // column-taps-in-N operands
     ConvPlan fwd, bwd;
     WgradPlan wg;
 };
@@ -299,11 +360,17 @@ mc_status pack_weights(dn_ctx* c, cudaStream_t s) {
         const float* w = c->d_params + ly.w_off;
         int coff = 0;
         for (int q = 0; q < ly.nsrc; ++q) {
-            DN_TRY(c, dn::launch_pack_fwd(w, ly.Co, ly.wf_rows, ly.k, ly.ci_total, coff, ly.realC[q], ly.CW[q],
-                                          ly.nch[q], ly.wf[q], s));
+            if (ly.fwd_dxn)
+                DN_TRY(c, dn::launch_pack_dxn(w, ly.Co, ly.ci_total, coff, ly.realC[q], ly.CW[q], ly.nch[q], 0, ly.Co,
+                                              ly.wf[q], s));
+            else
+                DN_TRY(c, dn::launch_pack_fwd(w, ly.Co, ly.wf_rows, ly.k, ly.ci_total, coff, ly.realC[q], ly.CW[q],
+                                              ly.nch[q], ly.wf[q], s));
             coff += ly.realC[q];
         }
-        if (ly.has_dgrad)
+        if (ly.has_dgrad && ly.bwd_dxn)
+            DN_TRY(c, dn::launch_pack_dxn(w, ly.Co, ly.ci_total, 0, ly.Co, ly.CWz, ly.nchz, 1, ly.ci_total, ly.wd, s));
+        else if (ly.has_dgrad)
             DN_TRY(c, dn::launch_pack_dgrad(w, ly.Co, ly.k, ly.ci_total, ly.wd_rows, ly.CWz, ly.nchz, ly.wd, s));
     }
     return MC_OK;
@@ -481,14 +548,15 @@ mc_status build(dn_ctx* c) {
         int nt_f, tiles_f;
         n_tiling(ly.Co, nt_f, tiles_f);
         ly.wf_rows = nt_f * tiles_f;
+        ly.fwd_dxn = dxn_fits(ly.k, ly.Co, ly.nsrc, ly.srcC);
         for (int q = 0; q < ly.nsrc; ++q) {
             // the network input's 8 stored channels hold 1 real one: its weight
             // operand has zeros for the other 7
             ly.CW[q] = cw_for(ly.srcC[q]);
             ly.nch[q] = chunks(ly.srcC[q], ly.CW[q]);
-            if ((st = dalloc(c, &ly.wf[q], static_cast<size_t>(ly.wf_rows) * ly.k * ly.k * ly.nch[q] * ly.CW[q])) !=
-                MC_OK)
-                return st;
+            const size_t n_op = ly.fwd_dxn ? static_cast<size_t>(3 * ly.Co) * 3 * ly.nch[q] * ly.CW[q]
+                                           : static_cast<size_t>(ly.wf_rows) * ly.k * ly.k * ly.nch[q] * ly.CW[q];
+            if ((st = dalloc(c, &ly.wf[q], n_op)) != MC_OK) return st;
         }
         ly.has_dgrad = ly.gin[0] != nullptr;
         const int Cz = ly.gout->C;
@@ -497,16 +565,19 @@ mc_status build(dn_ctx* c) {
         int nt_d, tiles_d;
         n_tiling(ly.srcC[0] + ly.srcC[1], nt_d, tiles_d);
         ly.wd_rows = nt_d * tiles_d;
-        if (ly.has_dgrad &&
-            (st = dalloc(c, &ly.wd, static_cast<size_t>(ly.wd_rows) * ly.k * ly.k * ly.nchz * ly.CWz)) != MC_OK)
-            return st;
+        const int zC1[2] = {Cz, 0};
+        ly.bwd_dxn = ly.has_dgrad && dxn_fits(ly.k, ly.srcC[0] + ly.srcC[1], 1, zC1);
+        const size_t n_wd = ly.bwd_dxn ? static_cast<size_t>(3 * (ly.srcC[0] + ly.srcC[1])) * 3 * ly.nchz * ly.CWz
+                                       : static_cast<size_t>(ly.wd_rows) * ly.k * ly.k * ly.nchz * ly.CWz;
+        if (ly.has_dgrad && (st = dalloc(c, &ly.wd, n_wd)) != MC_OK) return st;
         const Buf* o = ly.out;
         const bf16* srcs[2] = {ly.in[0]->p, ly.in[1] ? ly.in[1]->p : nullptr};
         const bf16* wops[2] = {ly.wf[0], ly.wf[1]};
         bf16* dsts[2] = {o->p, nullptr};
         const int dC[2] = {o->C, 0};
         if (!plan_conv(ly.fwd, ly.nsrc, srcs, ly.srcC, o->Nb, o->H, o->W, ly.k, wops, ly.wf_rows, ly.Co,
-                       c->d_params + ly.b_off, ly.relu, 1, ly.Co, dsts, dC, nullptr, c->d_err, c->sm_count))
+                       c->d_params + ly.b_off, ly.relu, 1, ly.Co, dsts, dC, nullptr, c->d_err, c->sm_count, true,
+                       ly.fwd_dxn))
             return fail(c, MC_ERR_CUDA, "tensor map encoding failed (" + ly.name + ")");
         if (ly.has_dgrad) {
             const bf16* zs[2] = {ly.gout->p, nullptr};
@@ -516,7 +587,7 @@ mc_status build(dn_ctx* c) {
             const int gC[2] = {ly.srcC[0], ly.srcC[1]};
             const bf16* mk[2] = {ly.in[0]->p, ly.in[1] ? ly.in[1]->p : nullptr};
             if (!plan_conv(ly.bwd, 1, zs, zC, o->Nb, o->H, o->W, ly.k, wd2, ly.wd_rows, ly.srcC[0] + ly.srcC[1],
-                           nullptr, 0, ly.nsrc, ly.srcC[0], gd, gC, mk, c->d_err, c->sm_count))
+                           nullptr, 0, ly.nsrc, ly.srcC[0], gd, gC, mk, c->d_err, c->sm_count, true, ly.bwd_dxn))
                 return fail(c, MC_ERR_CUDA, "tensor map encoding failed (" + ly.name + " dgrad)");
         }
         if (!plan_wgrad(ly.wg, ly.gout->p, Cz, ly.Co, ly.nsrc, srcs, ly.srcC, o->Nb, o->H, o->W, ly.k,
@@ -744,12 +815,15 @@ mc_status dn_conv2d_forward(const uint16_t* x0, int c0, const uint16_t* x1, int 
     unsigned* err = sc.get<unsigned>(1);
     if (!err || cudaMemsetAsync(err, 0, sizeof(unsigned), s) != cudaSuccess) return MC_ERR_CUDA;
     int coff = 0;
+    const bool dxn = dxn_fits(k, co, nsrc, C);
     for (int q = 0; q < nsrc; ++q) {
         const int CW = cw_for(C[q]), nch = chunks(C[q], CW);
-        wop[q] = sc.get<bf16>(static_cast<size_t>(rows) * k * k * nch * CW);
+        wop[q] = sc.get<bf16>(dxn ? static_cast<size_t>(3 * co) * 3 * nch * CW
+                                  : static_cast<size_t>(rows) * k * k * nch * CW);
         if (!wop[q]) return MC_ERR_OOM;
-        if (dn::launch_pack_fwd(weight, co, rows, k, C[0] + C[1], coff, C[q], CW, nch, wop[q], s) != cudaSuccess)
-            return MC_ERR_CUDA;
+        const cudaError_t e = dxn ? dn::launch_pack_dxn(weight, co, C[0] + C[1], coff, C[q], CW, nch, 0, co, wop[q], s)
+                                  : dn::launch_pack_fwd(weight, co, rows, k, C[0] + C[1], coff, C[q], CW, nch, wop[q], s);
+        if (e != cudaSuccess) return MC_ERR_CUDA;
         coff += C[q];
     }
     ConvPlan P;
@@ -758,7 +832,7 @@ mc_status dn_conv2d_forward(const uint16_t* x0, int c0, const uint16_t* x1, int 
     bf16* dst[2] = {reinterpret_cast<bf16*>(y), nullptr};
     const int dC[2] = {y_stride, 0};
     if (!plan_conv(P, nsrc, srcs, C, batch, height, width, k, wops, rows, co, bias, relu, 1, co, dst, dC, nullptr,
-                   err, device_sms()))
+                   err, device_sms(), true, dxn))
         return MC_ERR_CUDA;
     if (dn::launch_conv(P.ta, P.tb, P.a, s) != cudaSuccess) return MC_ERR_CUDA;
     return prim_check(s, err);
@@ -779,11 +853,16 @@ mc_status dn_conv2d_backward_data(const uint16_t* dz, int dz_stride, int co, int
     int nt, tiles;
     n_tiling(ci_total, nt, tiles);
     const int rows = nt * tiles;
+    const int zC1[2] = {dz_stride, 0};
+    const bool dxn = dxn_fits(k, ci_total, 1, zC1);
     unsigned* err = sc.get<unsigned>(1);
-    bf16* wd = sc.get<bf16>(static_cast<size_t>(rows) * k * k * nchz * CWz);
+    bf16* wd = sc.get<bf16>(dxn ? static_cast<size_t>(3 * ci_total) * 3 * nchz * CWz
+                                : static_cast<size_t>(rows) * k * k * nchz * CWz);
     if (!err || !wd) return MC_ERR_OOM;
     if (cudaMemsetAsync(err, 0, sizeof(unsigned), s) != cudaSuccess) return MC_ERR_CUDA;
-    if (dn::launch_pack_dgrad(weight, co, k, ci_total, rows, CWz, nchz, wd, s) != cudaSuccess) return MC_ERR_CUDA;
+    const cudaError_t pe = dxn ? dn::launch_pack_dxn(weight, co, ci_total, 0, co, CWz, nchz, 1, ci_total, wd, s)
+                               : dn::launch_pack_dgrad(weight, co, k, ci_total, rows, CWz, nchz, wd, s);
+    if (pe != cudaSuccess) return MC_ERR_CUDA;
     ConvPlan P;
     const bf16* zs[2] = {reinterpret_cast<const bf16*>(dz), nullptr};
     const bf16* w2[2] = {wd, nullptr};
@@ -792,7 +871,7 @@ mc_status dn_conv2d_backward_data(const uint16_t* dz, int dz_stride, int co, int
     const int dC[2] = {c0, dx1 ? c1 : 0};
     const bf16* mk[2] = {reinterpret_cast<const bf16*>(mask0), reinterpret_cast<const bf16*>(mask1)};
     if (!plan_conv(P, 1, zs, zC, batch, height, width, k, w2, rows, ci_total, nullptr, 0, ndst, c0, dst, dC, mk, err,
-                   device_sms()))
+                   device_sms(), true, dxn))
         return MC_ERR_CUDA;
     if (dn::launch_conv(P.ta, P.tb, P.a, s) != cudaSuccess) return MC_ERR_CUDA;
     return prim_check(s, err);

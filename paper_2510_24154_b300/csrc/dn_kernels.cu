@@ -45,6 +45,50 @@ __device__ __forceinline__ KStep kstep(const ConvArgs& a, int i) {
     return k;
 }
 
+
+// Epilogue of 16 accumulator columns (output channels co0 .. co0+15) of one
+// pixel: bias, ReLU, the mask of the source layer, the split of a
+// concatenated input, bf16 rounding; 16-byte stores where aligned.
+__device__ __forceinline__ void epilogue16(const ConvArgs& a, const float* v, int co0, size_t pix) {
+    const int d = (a.ndst > 1 && co0 >= a.dst_split) ? 1 : 0;
+    const int cc0 = co0 - (d ? a.dst_split : 0);
+    const int dC = a.dst_C[d];
+    const int dend = d ? a.N : (a.ndst > 1 ? a.dst_split : a.N);
+    __nv_bfloat16* out = a.dst[d] + pix * dC;
+    const __nv_bfloat16* mk = a.mask[d] ? a.mask[d] + pix * dC : nullptr;
+    if (co0 + 16 <= dend && (dC & 7) == 0 && (cc0 & 7) == 0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint4 mv = make_uint4(0, 0, 0, 0);
+            if (mk) mv = *reinterpret_cast<const uint4*>(mk + cc0 + 8 * h);
+            const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mv);
+            __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float val = v[8 * h + j];
+                if (a.bias) val += __ldg(&a.bias[co0 + 8 * h + j]);
+                if (a.relu) val = fmaxf(val, 0.0f);
+                if (mk && !(__bfloat162float(mb[j]) > 0.0f)) val = 0.0f;
+                o[j] = __float2bfloat16_rn(val);
+            }
+            *reinterpret_cast<uint4*>(out + cc0 + 8 * h) = *reinterpret_cast<const uint4*>(o);
+        }
+    } else {
+        for (int j = 0; j < 16; ++j) {
+            const int co = co0 + j;
+            if (co >= a.N) break;
+            const int dd = (a.ndst > 1 && co >= a.dst_split) ? 1 : 0;
+            const int cc = co - (dd ? a.dst_split : 0);
+            float val = v[j];
+            if (a.bias) val += __ldg(&a.bias[co]);
+            if (a.relu) val = fmaxf(val, 0.0f);
+            const size_t o = pix * a.dst_C[dd] + cc;
+            if (a.mask[dd] && !(__bfloat162float(a.mask[dd][o]) > 0.0f)) val = 0.0f;
+            a.dst[dd][o] = __float2bfloat16_rn(val);
+        }
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------- convolution ------
@@ -56,7 +100,7 @@ __device__ __forceinline__ KStep kstep(const ConvArgs& a, int i) {
 // MMAs of a tile into one of two TMEM accumulators; warps 2-5 drain the other
 // accumulator (tcgen05.ld), so a tile's epilogue overlaps the next tile's
 // MMAs.
-__global__ void __launch_bounds__(192) k_conv(const __grid_constant__ CUtensorMap ta0,
+__global__ void __launch_bounds__(320) k_conv(const __grid_constant__ CUtensorMap ta0,
                                               const __grid_constant__ CUtensorMap ta1,
                                               const __grid_constant__ CUtensorMap tb0,
                                               const __grid_constant__ CUtensorMap tb1, const ConvArgs a) {
@@ -188,11 +232,13 @@ __global__ void __launch_bounds__(192) k_conv(const __grid_constant__ CUtensorMa
                 if (commits[b]) mbar_wait(&accf[b], (commits[b] - 1) & 1, a.err, kErrWaitTail);
         }
     } else {
-        // epilogue warps 2-5: TMEM lane quarter q = warp % 4
+        // epilogue: warps 2-5 drain buffer 0 (even tiles), warps 6-9 buffer 1
+        // (odd tiles); TMEM lane quarter q = warp % 4
+        const int g = (warp - 2) >> 2;
         const int q = warp & 3;
         const int row = q * 32 + lane;
-        uint32_t lt = 0;
-        for (int t = blockIdx.x; t < total; t += gridDim.x, ++lt) {
+        uint32_t lt = static_cast<uint32_t>(g);
+        for (int t = blockIdx.x + g * gridDim.x; t < total; t += 2 * gridDim.x, lt += 2) {
             const uint32_t buf = lt & 1u;
             const bool ok = mbar_wait(&accf[buf], (lt >> 1) & 1, a.err, kErrWaitDone);
             tc_fence_after();
@@ -212,43 +258,7 @@ __global__ void __launch_bounds__(192) k_conv(const __grid_constant__ CUtensorMa
                 tmem_ld16(tbase + static_cast<uint32_t>(c), v);
                 const int co0 = n0 + c;
                 if (!valid || co0 >= a.N) continue;
-                const int d = (a.ndst > 1 && co0 >= a.dst_split) ? 1 : 0;
-                const int cc0 = co0 - (d ? a.dst_split : 0);
-                const int dC = a.dst_C[d];
-                const int dend = d ? a.N : (a.ndst > 1 ? a.dst_split : a.N);
-                __nv_bfloat16* out = a.dst[d] + pix * dC;
-                const __nv_bfloat16* mk = a.mask[d] ? a.mask[d] + pix * dC : nullptr;
-                if (co0 + 16 <= dend && (dC & 7) == 0 && (cc0 & 7) == 0) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        uint4 mv = make_uint4(0, 0, 0, 0);
-                        if (mk) mv = *reinterpret_cast<const uint4*>(mk + cc0 + 8 * h);
-                        const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mv);
-                        __align__(16) __nv_bfloat16 o[8];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            float val = v[8 * h + j];
-                            if (a.bias) val += __ldg(&a.bias[co0 + 8 * h + j]);
-                            if (a.relu) val = fmaxf(val, 0.0f);
-                            if (mk && !(__bfloat162float(mb[j]) > 0.0f)) val = 0.0f;
-                            o[j] = __float2bfloat16_rn(val);
-                        }
-                        *reinterpret_cast<uint4*>(out + cc0 + 8 * h) = *reinterpret_cast<const uint4*>(o);
-                    }
-                } else {
-                    for (int j = 0; j < 16; ++j) {
-                        const int co = co0 + j;
-                        if (co >= a.N) break;
-                        const int dd = (a.ndst > 1 && co >= a.dst_split) ? 1 : 0;
-                        const int cc = co - (dd ? a.dst_split : 0);
-                        float val = v[j];
-                        if (a.bias) val += __ldg(&a.bias[co]);
-                        if (a.relu) val = fmaxf(val, 0.0f);
-                        const size_t o = pix * a.dst_C[dd] + cc;
-                        if (a.mask[dd] && !(__bfloat162float(a.mask[dd][o]) > 0.0f)) val = 0.0f;
-                        a.dst[dd][o] = __float2bfloat16_rn(val);
-                    }
-                }
+                epilogue16(a, v, co0, pix);
             }
             // this warp's TMEM reads are complete (tcgen05.wait::ld): hand the buffer back
             tc_fence_before();
@@ -259,6 +269,447 @@ __global__ void __launch_bounds__(192) k_conv(const __grid_constant__ CUtensorMa
     tc_fence_before();
     __syncthreads();
     if (warp == 1) tmem_dealloc(tmem, static_cast<uint32_t>(2 * a.tmem_cols));
+}
+
+// Resident-weight variant for layers whose packed weights fit in shared
+// memory (N <= 256): the weights are loaded once per CTA; a tile is R output
+// rows x 128 pixels, and each K step is one activation box (input row j,
+// column shift dx, channel chunk) that feeds the up to k accumulators of the
+// output rows it touches (row r = j - dy with weight tap (dy, dx)), so an
+// input row is fetched (R + k - 1) / R times per output row instead of k.
+__global__ void __launch_bounds__(320) k_conv_res(const __grid_constant__ CUtensorMap ta0,
+                                                  const __grid_constant__ CUtensorMap ta1,
+                                                  const __grid_constant__ CUtensorMap tb0,
+                                                  const __grid_constant__ CUtensorMap tb1, const ConvArgs a) {
+    extern __shared__ uint8_t dsm[];
+    uint8_t* wsm = align1024(dsm);                        // resident weights
+    uint8_t* tiles = wsm + a.w_bytes;                     // ring of activation boxes
+    const int S = a.stages;
+    uint64_t* full = reinterpret_cast<uint64_t*>(tiles + S * a.stage_bytes);
+    uint64_t* empty = full + S;
+    uint64_t* accf = empty + S;
+    uint64_t* acce = accf + 2;
+    uint64_t* wbar = acce + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(wbar + 1);
+    volatile uint32_t* abort_flag = tslot + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const int R = a.rows_per_tile, k = a.k, p = k >> 1;
+    const int segs = (a.W + 127) >> 7;
+    const int groups = (a.H + R - 1) / R;
+    const int total = segs * groups * a.Nb;
+    const int chunks = a.src[0].nch + (a.nsrc > 1 ? a.src[1].nch : 0);
+    const int in_rows = R + k - 1;
+    const int steps = in_rows * k * chunks;               // K steps per tile
+    const uint32_t acc_cols = static_cast<uint32_t>(a.N_tile);
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&acce[i], 4);
+        }
+        mbar_init(wbar, 1);
+        *abort_flag = 0u;
+        mbar_fence_init();
+        tma_prefetch(&ta0);
+        tma_prefetch(&tb0);
+        if (a.nsrc > 1) {
+            tma_prefetch(&ta1);
+            tma_prefetch(&tb1);
+        }
+    }
+    if (warp == 1) tmem_alloc(tslot, static_cast<uint32_t>(a.tmem_cols));
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    auto decode = [&](int t, int& x0, int& y0, int& n) {
+        const int xs = t % segs;
+        int r = t / segs;
+        y0 = (r % groups) * R;
+        n = r / groups;
+        x0 = xs << 7;
+    };
+    // K step i of a tile -> (input row j, column shift dx, source s, chunk c)
+    auto step = [&](int i, int& j, int& dx, int& s_, int& c) {
+        const int r = i % chunks;
+        const int jd = i / chunks;
+        j = jd / k;
+        dx = jd - j * k;
+        s_ = r < a.src[0].nch ? 0 : 1;
+        c = s_ ? r - a.src[0].nch : r;
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // resident weights: one box per (source, tap, chunk)
+            mbar_expect_tx(wbar, a.w_bytes_real);
+            for (int s_ = 0; s_ < a.nsrc; ++s_) {
+                const ConvSrc& src = a.src[s_];
+                const uint32_t tile_bytes = static_cast<uint32_t>(a.N_tile) * src.CW * 2u;
+                for (int t = 0; t < k * k; ++t)
+                    for (int c = 0; c < src.nch; ++c)
+                        tma_load_2d(wsm + a.w_off[s_] + (t * src.nch + c) * tile_bytes, s_ ? &tb1 : &tb0, wbar,
+                                    (t * src.nch + c) * src.CW, 0);
+            }
+            uint32_t it = 0;
+            for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+                int x0, y0, n;
+                decode(t, x0, y0, n);
+                for (int i = 0; i < steps; ++i, ++it) {
+                    const uint32_t st = it % S;
+                    if (it >= static_cast<uint32_t>(S) &&
+                        !mbar_wait(&empty[st], ((it / S) - 1) & 1, a.err, kErrWaitEmpty)) {
+                        *abort_flag = 1u;
+                        break;
+                    }
+                    int j, dx, s_, c;
+                    step(i, j, dx, s_, c);
+                    const ConvSrc& src = a.src[s_];
+                    mbar_expect_tx(&full[st], 128u * static_cast<uint32_t>(src.CW) * 2u);
+                    tma_load_4d(tiles + st * a.stage_bytes, s_ ? &ta1 : &ta0, &full[st], c * src.CW, x0 + dx - p,
+                                y0 - p + j, n);
+                }
+                if (*abort_flag) break;
+            }
+            const uint32_t issued = it;
+            for (uint32_t st = 0; st < static_cast<uint32_t>(S) && st < issued; ++st) {
+                const uint32_t last = st + ((issued - 1 - st) / S) * S;
+                mbar_wait(&full[st], (last / S) & 1, a.err, kErrWaitTail);
+            }
+            mbar_wait(wbar, 0, a.err, kErrWaitTail);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const bool wok = mbar_wait(wbar, 0, a.err, kErrWaitFull);
+            if (!wok) *abort_flag = 1u;
+            tc_fence_after();
+            uint32_t it = 0, lt = 0;
+            uint32_t commits[2] = {0u, 0u};
+            const uint32_t wbase = smem_u32(wsm);
+            for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++lt) {
+                const uint32_t buf = lt & 1u;
+                if (lt >= 2 && !mbar_wait(&acce[buf], ((lt >> 1) - 1) & 1, a.err, kErrWaitEmpty)) {
+                    *abort_flag = 1u;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d0 = tmem + buf * static_cast<uint32_t>(R) * acc_cols;
+                for (int i = 0; i < steps; ++i, ++it) {
+                    const uint32_t st = it % S;
+                    if (!mbar_wait(&full[st], (it / S) & 1, a.err, kErrWaitFull)) {
+                        *abort_flag = 1u;
+                        break;
+                    }
+                    tc_fence_after();
+                    int j, dx, s_, c;
+                    step(i, j, dx, s_, c);
+                    const ConvSrc& src = a.src[s_];
+                    const uint32_t row = static_cast<uint32_t>(src.CW) * 2u;
+                    const uint32_t swz = swz_for_row(row);
+                    const uint32_t sa = smem_u32(tiles + st * a.stage_bytes);
+                    const uint32_t tile_bytes = static_cast<uint32_t>(a.N_tile) * row;
+                    for (int dy = 0; dy < k; ++dy) {
+                        const int r = j - dy;
+                        if (r < 0 || r >= R) continue;
+                        const uint32_t wt = wbase + a.w_off[s_] + ((dy * k + dx) * src.nch + c) * tile_bytes;
+                        const bool first = (dy == 0 && dx == 0 && s_ == 0 && c == 0);
+                        for (int kk = 0; kk < src.CW / 16; ++kk) {
+                            const uint64_t da = smem_desc(sa + kk * 32u, 16u, 8u * row, swz);
+                            const uint64_t db = smem_desc(wt + kk * 32u, 16u, 8u * row, swz);
+                            tc_mma(d0 + static_cast<uint32_t>(r) * acc_cols, da, db, a.idesc,
+                                   (first && kk == 0) ? 0u : 1u);
+                        }
+                    }
+                    tc_commit(&empty[st]);
+                }
+                tc_commit(&accf[buf]);
+                ++commits[buf];
+                if (*abort_flag) break;
+            }
+            for (int b = 0; b < 2; ++b)
+                if (commits[b]) mbar_wait(&accf[b], (commits[b] - 1) & 1, a.err, kErrWaitTail);
+        }
+    } else {
+        const int g = (warp - 2) >> 2;             // epilogue group = accumulator buffer
+        const int q = warp & 3;
+        const int prow = q * 32 + lane;
+        uint32_t lt = static_cast<uint32_t>(g);
+        for (int t = blockIdx.x + g * gridDim.x; t < total; t += 2 * gridDim.x, lt += 2) {
+            const uint32_t buf = lt & 1u;
+            const bool ok = mbar_wait(&accf[buf], (lt >> 1) & 1, a.err, kErrWaitDone);
+            tc_fence_after();
+            __syncwarp();
+            if (!ok || *abort_flag) {
+                *abort_flag = 1u;
+                break;
+            }
+            int x0, y0, n;
+            decode(t, x0, y0, n);
+            const int x = x0 + prow;
+            for (int r = 0; r < R; ++r) {
+                const int y = y0 + r;
+                const bool valid = x < a.W && y < a.H;
+                const size_t pix = (static_cast<size_t>(n) * a.H + y) * a.W + x;
+                const uint32_t tbase = tmem + (buf * static_cast<uint32_t>(R) + r) * acc_cols +
+                                       (static_cast<uint32_t>(q * 32) << 16);
+                for (int c = 0; c < a.N_tile; c += 16) {
+                    float v[16];
+                    tmem_ld16(tbase + static_cast<uint32_t>(c), v);
+                    if (!valid || c >= a.N) continue;
+                    epilogue16(a, v, c, pix);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[buf]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, static_cast<uint32_t>(a.tmem_cols));
+}
+
+// Column taps in N (3x3 layers with N <= 64 output channels): tcgen05.mma
+// costs about the same per instruction whatever its N, so for narrow layers
+// one MMA computes, for the 128 pixels of one input row segment, the products
+// with all three column taps at once: D[r][(dx, o)] = sum over (dy, c) of
+// in[y + dy - 1][x0 - 1 + r][c] W[o][dy][dx][c] (N = 3 x channels; the three
+// row taps accumulate along K).  The output pixel x0 - 1 + r is then
+// D[r-1][(0, o)] + D[r][(1, o)] + D[r+1][(2, o)]: the epilogue combines
+// neighbouring TMEM lanes with warp shuffles (and a shared-memory exchange
+// across warps), and tiles advance by 126 pixels.  Weights are resident in
+// shared memory as [dy][chunk][(dx, o)][c].
+__global__ void __launch_bounds__(320) k_conv_dxn(const __grid_constant__ CUtensorMap ta0,
+                                                  const __grid_constant__ CUtensorMap ta1,
+                                                  const __grid_constant__ CUtensorMap tb0,
+                                                  const __grid_constant__ CUtensorMap tb1, const ConvArgs a) {
+    extern __shared__ uint8_t dsm[];
+    uint8_t* wsm = align1024(dsm);
+    uint8_t* tiles = wsm + a.w_bytes;
+    const int S = a.stages;
+    uint64_t* full = reinterpret_cast<uint64_t*>(tiles + S * a.stage_bytes);
+    uint64_t* empty = full + S;
+    uint64_t* accf = empty + S;
+    uint64_t* acce = accf + 2;
+    uint64_t* wbar = acce + 2;
+    float* xch = reinterpret_cast<float*>(wbar + 1);     // [2 groups][2 sides][4 warps][16]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(xch + 2 * 2 * 4 * 16);
+    volatile uint32_t* abort_flag = tslot + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const int N = a.N;                      // output channels
+    const int N3 = 3 * N;                   // MMA N
+    const int segs = (a.W + 125) / 126;
+    const int total = segs * a.H * a.Nb;
+    const int chunks = a.src[0].nch + (a.nsrc > 1 ? a.src[1].nch : 0);
+    const int steps = 3 * chunks;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&acce[i], 4);
+        }
+        mbar_init(wbar, 1);
+        *abort_flag = 0u;
+        mbar_fence_init();
+        tma_prefetch(&ta0);
+        tma_prefetch(&tb0);
+        if (a.nsrc > 1) {
+            tma_prefetch(&ta1);
+            tma_prefetch(&tb1);
+        }
+    }
+    if (warp == 1) tmem_alloc(tslot, static_cast<uint32_t>(a.tmem_cols));
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    auto decode = [&](int t, int& x0, int& y, int& n) {
+        const int xs = t % segs;
+        int r = t / segs;
+        y = r % a.H;
+        n = r / a.H;
+        x0 = xs * 126;
+    };
+    auto step = [&](int i, int& dy, int& s_, int& c) {
+        dy = i / chunks;
+        const int r = i - dy * chunks;
+        s_ = r < a.src[0].nch ? 0 : 1;
+        c = s_ ? r - a.src[0].nch : r;
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_expect_tx(wbar, a.w_bytes_real);
+            for (int s_ = 0; s_ < a.nsrc; ++s_) {
+                const ConvSrc& src = a.src[s_];
+                const uint32_t tile_bytes = static_cast<uint32_t>(N3) * src.CW * 2u;
+                for (int dy = 0; dy < 3; ++dy)
+                    for (int c = 0; c < src.nch; ++c)
+                        tma_load_2d(wsm + a.w_off[s_] + (dy * src.nch + c) * tile_bytes, s_ ? &tb1 : &tb0, wbar,
+                                    (dy * src.nch + c) * src.CW, 0);
+            }
+            uint32_t it = 0;
+            for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+                int x0, y, n;
+                decode(t, x0, y, n);
+                for (int i = 0; i < steps; ++i, ++it) {
+                    const uint32_t st = it % S;
+                    if (it >= static_cast<uint32_t>(S) &&
+                        !mbar_wait(&empty[st], ((it / S) - 1) & 1, a.err, kErrWaitEmpty)) {
+                        *abort_flag = 1u;
+                        break;
+                    }
+                    int dy, s_, c;
+                    step(i, dy, s_, c);
+                    const ConvSrc& src = a.src[s_];
+                    mbar_expect_tx(&full[st], 128u * static_cast<uint32_t>(src.CW) * 2u);
+                    tma_load_4d(tiles + st * a.stage_bytes, s_ ? &ta1 : &ta0, &full[st], c * src.CW, x0 - 1,
+                                y + dy - 1, n);
+                }
+                if (*abort_flag) break;
+            }
+            const uint32_t issued = it;
+            for (uint32_t st = 0; st < static_cast<uint32_t>(S) && st < issued; ++st) {
+                const uint32_t last = st + ((issued - 1 - st) / S) * S;
+                mbar_wait(&full[st], (last / S) & 1, a.err, kErrWaitTail);
+            }
+            mbar_wait(wbar, 0, a.err, kErrWaitTail);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            if (!mbar_wait(wbar, 0, a.err, kErrWaitFull)) *abort_flag = 1u;
+            tc_fence_after();
+            uint32_t it = 0, lt = 0;
+            uint32_t commits[2] = {0u, 0u};
+            const uint32_t wbase = smem_u32(wsm);
+            for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++lt) {
+                const uint32_t buf = lt & 1u;
+                if (lt >= 2 && !mbar_wait(&acce[buf], ((lt >> 1) - 1) & 1, a.err, kErrWaitEmpty)) {
+                    *abort_flag = 1u;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + buf * static_cast<uint32_t>(a.tmem_cols / 2);
+                for (int i = 0; i < steps; ++i, ++it) {
+                    const uint32_t st = it % S;
+                    if (!mbar_wait(&full[st], (it / S) & 1, a.err, kErrWaitFull)) {
+                        *abort_flag = 1u;
+                        break;
+                    }
+                    tc_fence_after();
+                    int dy, s_, c;
+                    step(i, dy, s_, c);
+                    const ConvSrc& src = a.src[s_];
+                    const uint32_t row = static_cast<uint32_t>(src.CW) * 2u;
+                    const uint32_t swz = swz_for_row(row);
+                    const uint32_t sa = smem_u32(tiles + st * a.stage_bytes);
+                    const uint32_t wt = wbase + a.w_off[s_] + (dy * src.nch + c) * (static_cast<uint32_t>(N3) * row);
+                    for (int kk = 0; kk < src.CW / 16; ++kk) {
+                        const uint64_t da = smem_desc(sa + kk * 32u, 16u, 8u * row, swz);
+                        const uint64_t db = smem_desc(wt + kk * 32u, 16u, 8u * row, swz);
+                        tc_mma(d, da, db, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    tc_commit(&empty[st]);
+                }
+                tc_commit(&accf[buf]);
+                ++commits[buf];
+                if (*abort_flag) break;
+            }
+            for (int b = 0; b < 2; ++b)
+                if (commits[b]) mbar_wait(&accf[b], (commits[b] - 1) & 1, a.err, kErrWaitTail);
+        }
+    } else {
+        const int g = (warp - 2) >> 2;          // epilogue group = accumulator buffer
+        const int q = warp & 3;                 // TMEM lane quarter: rows 32q .. 32q+31
+        const int r = q * 32 + lane;
+        float* gx = xch + g * 128;
+        uint32_t lt = static_cast<uint32_t>(g);
+        for (int t = blockIdx.x + g * gridDim.x; t < total; t += 2 * gridDim.x, lt += 2) {
+            const uint32_t buf = lt & 1u;
+            const bool ok = mbar_wait(&accf[buf], (lt >> 1) & 1, a.err, kErrWaitDone);
+            tc_fence_after();
+            __syncwarp();
+            if (!ok || *abort_flag) {
+                *abort_flag = 1u;
+                break;
+            }
+            int x0, y, n;
+            decode(t, x0, y, n);
+            const int x = x0 - 1 + r;
+            const bool valid = r >= 1 && r <= 126 && x < a.W;
+            const size_t pix = (static_cast<size_t>(n) * a.H + y) * a.W + (valid ? x : 0);
+            const uint32_t tbase = tmem + buf * static_cast<uint32_t>(a.tmem_cols / 2) +
+                                   (static_cast<uint32_t>(q * 32) << 16);
+            for (int c = 0; c < N; c += 16) {
+                float v0[16], v1[16], v2[16], o[16];
+                tmem_ld16(tbase + static_cast<uint32_t>(c), v0);
+                tmem_ld16(tbase + static_cast<uint32_t>(N + c), v1);
+                tmem_ld16(tbase + static_cast<uint32_t>(2 * N + c), v2);
+                // rows 32q-1 and 32q+32 live in the neighbouring warps
+                if (lane == 31)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) gx[(0 * 4 + q) * 16 + j] = v0[j];
+                if (lane == 0)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) gx[(1 * 4 + q) * 16 + j] = v2[j];
+                asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float left = __shfl_up_sync(0xffffffffu, v0[j], 1);
+                    float right = __shfl_down_sync(0xffffffffu, v2[j], 1);
+                    if (lane == 0) left = q > 0 ? gx[(0 * 4 + q - 1) * 16 + j] : 0.0f;
+                    if (lane == 31) right = q < 3 ? gx[(1 * 4 + q + 1) * 16 + j] : 0.0f;
+                    o[j] = left + v1[j] + right;
+                }
+                asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+                if (valid) epilogue16(a, o, c, pix);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[buf]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, static_cast<uint32_t>(a.tmem_cols));
+}
+
+// fp32 master weights -> the column-taps-in-N operand of one source:
+// out[(dx, o)][(dy, chunk, c)] = w[o][dy][dx][coff + chunk * CW + c]
+// (forward; o < Co) or, for the input gradient, w'[ci][flipped tap][co] with
+// (dx, ci) rows.
+__global__ void k_pack_dxn(const float* __restrict__ w, int Co, int ci_total, int coff, int C, int CW, int nch,
+                           int dgrad, int Nout, __nv_bfloat16* __restrict__ out) {
+    const int cols = 3 * nch * CW;
+    const long long total = static_cast<long long>(3 * Nout) * cols;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int rr = static_cast<int>(i / cols);
+        const int cc = static_cast<int>(i % cols);
+        const int dx = rr / Nout, o = rr % Nout;
+        const int dy = cc / (nch * CW);
+        const int c = cc % (nch * CW);
+        float val = 0.0f;
+        if (!dgrad) {
+            if (c < C) val = w[(static_cast<size_t>(o) * 9 + dy * 3 + dx) * ci_total + coff + c];
+        } else {
+            // input gradient: rows are input channels o, columns output channels c
+            if (c < Co) val = w[(static_cast<size_t>(c) * 9 + (8 - (dy * 3 + dx))) * ci_total + o];
+        }
+        out[i] = __float2bfloat16_rn(val);
+    }
 }
 
 // ----------------------------------------------------- weight gradient -----
@@ -679,6 +1130,10 @@ __global__ void k_to_f32(const __nv_bfloat16* __restrict__ x, int stride, long l
 cudaError_t conv_prepare() {
     cudaError_t e = cudaFuncSetAttribute(k_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_conv_res, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_conv_dxn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     return e;
 }
@@ -689,9 +1144,24 @@ static size_t conv_smem(int stages, uint32_t stage_bytes) {
 
 cudaError_t launch_conv(const CUtensorMap* ta, const CUtensorMap* tb, const ConvArgs& a, cudaStream_t s) {
     const int segs = (a.W + 127) / 128;
+    if (a.dxn) {
+        const long long total = static_cast<long long>((a.W + 125) / 126) * a.H * a.Nb;
+        const int grid = static_cast<int>(std::min<long long>(total, a.grid));
+        const size_t smem =
+            1024 + a.w_bytes + static_cast<size_t>(a.stages) * a.stage_bytes + (2 * a.stages + 5) * 8 + 2 * 2 * 4 * 16 * 4 + 16;
+        k_conv_dxn<<<grid, 320, smem, s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0], tb[a.nsrc > 1 ? 1 : 0], a);
+        return cudaGetLastError();
+    }
+    if (a.rows_per_tile > 0) {
+        const long long total = static_cast<long long>(segs) * ((a.H + a.rows_per_tile - 1) / a.rows_per_tile) * a.Nb;
+        const int grid = static_cast<int>(std::min<long long>(total, a.grid));
+        const size_t smem = 1024 + a.w_bytes + static_cast<size_t>(a.stages) * a.stage_bytes + (2 * a.stages + 5) * 8 + 16;
+        k_conv_res<<<grid, 320, smem, s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0], tb[a.nsrc > 1 ? 1 : 0], a);
+        return cudaGetLastError();
+    }
     const long long total = static_cast<long long>(segs) * a.H * a.Nb * ((a.N + a.N_tile - 1) / a.N_tile);
     const int grid = static_cast<int>(std::min<long long>(total, a.grid));
-    k_conv<<<grid, 192, conv_smem(a.stages, a.stage_bytes), s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0],
+    k_conv<<<grid, 320, conv_smem(a.stages, a.stage_bytes), s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0],
                                                                  tb[a.nsrc > 1 ? 1 : 0], a);
     return cudaGetLastError();
 }
@@ -764,6 +1234,13 @@ cudaError_t launch_pack_dgrad(const float* w, int Co, int k, int ci_total, int r
                               __nv_bfloat16* out, cudaStream_t s) {
     k_pack_dgrad<<<blocks_for(static_cast<long long>(rows) * k * k * nchz * CWz), kThreads, 0, s>>>(
         w, Co, k, ci_total, rows, CWz, nchz, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_dxn(const float* w, int Co, int ci_total, int coff, int C, int CW, int nch, int dgrad,
+                            int Nout, __nv_bfloat16* out, cudaStream_t s) {
+    k_pack_dxn<<<blocks_for(static_cast<long long>(3 * Nout) * 3 * nch * CW), kThreads, 0, s>>>(
+        w, Co, ci_total, coff, C, CW, nch, dgrad, Nout, out);
     return cudaGetLastError();
 }
 

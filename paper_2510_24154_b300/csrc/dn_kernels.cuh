@@ -29,6 +29,11 @@ struct ConvArgs {
     int nk;                     // K steps = k*k * (chunks of all sources)
     int stages;
     int grid;                   // persistent CTAs (one per SM)
+    // resident-weight variant (rows_per_tile > 0): R output rows per tile,
+    // packed weights of source s at byte w_off[s] of a w_bytes region
+    int rows_per_tile;
+    int dxn;                    // column taps in N (3x3, N <= 64): tiles of 126 pixels
+    uint32_t w_bytes, w_bytes_real, w_off[2];
     uint32_t stage_bytes, a_region;
     uint32_t idesc;
     const float* bias;          // [N] or null
@@ -83,6 +88,9 @@ cudaError_t launch_pack_fwd(const float* w, int Co, int rows, int k, int ci_tota
                             __nv_bfloat16* out, cudaStream_t s);
 cudaError_t launch_pack_dgrad(const float* w, int Co, int k, int ci_total, int rows, int CWz, int nchz,
                               __nv_bfloat16* out, cudaStream_t s);
+// Column-taps-in-N operand [(dx, o)][(dy, chunk, c)], o < Nout (3 * Nout rows).
+cudaError_t launch_pack_dxn(const float* w, int Co, int ci_total, int coff, int C, int CW, int nch, int dgrad,
+                            int Nout, __nv_bfloat16* out, cudaStream_t s);
 cudaError_t launch_prep(const float* img, float scale, long long npix, __nv_bfloat16* out, int out_C,
                         cudaStream_t s);
 cudaError_t launch_to_f32(const __nv_bfloat16* x, int stride, long long npix, float scale, float* out,

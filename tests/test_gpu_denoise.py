@@ -53,6 +53,8 @@ def _within(gpu, ref, bound):
     dict(N=1, H=3, W=40, c0=8, c1=0, co=32, k=3, relu=0),        # narrow input, W < 128
     dict(N=1, H=2, W=136, c0=32, c1=0, co=1, k=1, relu=0),       # 1x1 to one channel
     dict(N=1, H=2, W=128, c0=128, c1=256, co=320, k=3, relu=1),  # two N tiles, 384 input channels
+    dict(N=1, H=3, W=260, c0=64, c1=32, co=32, k=3, relu=1),     # column taps in N, two sources, 3 tiles
+    dict(N=2, H=4, W=126, c0=64, c1=0, co=64, k=3, relu=0),      # column taps in N, one exact tile
 ])
 def test_conv_forward_parity(case):
     r = np.random.default_rng(1)
@@ -79,6 +81,7 @@ def test_conv_forward_parity(case):
     dict(N=1, H=4, W=256, c0=64, c1=32, co=32, k=3),
     dict(N=1, H=3, W=64, c0=32, c1=0, co=1, k=1),
     dict(N=1, H=2, W=128, c0=256, c1=128, co=128, k=3),
+    dict(N=1, H=3, W=300, c0=64, c1=0, co=64, k=3),              # column taps in N (N = 64)
 ])
 def test_conv_backward_data_parity(case):
     r = np.random.default_rng(2)
