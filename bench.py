@@ -446,6 +446,9 @@ def main():
             "s_per_field_1pct": n_1pct / per_gpu_rate, "u_at_step": u, "histories_for_1pct": n_1pct,
             "roofline": roofline, "memory_roofline": memory_roofline, "cpu_baseline": cpu, "e2e": e2e,
             "batched_plan": batched, "denoiser": denoiser,
+            "events_per_history": {k: last["counters"][k] / N for k in
+                                   ("flights_ct", "real_ct", "compton", "photo", "pair", "esteps_ct", "esteps_epid",
+                                    "moller", "brem", "electrons", "primaries_at_epid")},
             "gpu_launches": int(agg["launches"]), "clocks": clk.summary(), "wall_s_timed": wall,
             "paper_context": "about 90 s per IMRT field at 1e9 histories on an RTX 3090 (paper Sec. 4.1)",
         }
