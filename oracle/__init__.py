@@ -63,7 +63,7 @@ class _Result(C.Structure):
     _fields_ = [
         ("tally", C.POINTER(C.c_double)), ("e_src", C.c_double), ("e_ct", C.c_double),
         ("e_epid", C.c_double * MAXL), ("e_esc", C.c_double), ("e_lost", C.c_double),
-        ("counters", C.c_uint64 * len(COUNTER_NAMES)),
+        ("counters", C.c_uint64 * len(COUNTER_NAMES)), ("vox", C.POINTER(C.c_double)),
     ]
 
 
@@ -150,9 +150,12 @@ class _Marshalled:
         self.s = s
 
 
-def run(problem, n_histories=None, seed=None, hist_begin=0, threads=None, physics=None, field=None):
+def run(problem, n_histories=None, seed=None, hist_begin=0, threads=None, physics=None, field=None,
+        patient_dose=False):
     """Transport `n_histories` histories (ids hist_begin..) and return the tally
-    [B][npy][npx] in MeV, the energy balance and the event counters."""
+    [B][npy][npx] in MeV, the energy balance and the event counters; with
+    patient_dose, also "vox": the energy (MeV) deposited in each CT voxel,
+    [nz][ny][nx]."""
     m = _Marshalled(problem, physics, field)
     n = int(problem.n_histories if n_histories is None else n_histories)
     sd = int(problem.seed if seed is None else seed)
@@ -160,6 +163,9 @@ def run(problem, n_histories=None, seed=None, hist_begin=0, threads=None, physic
     tally = np.zeros((B, m.s.npy, m.s.npx), dtype=np.float64)
     r = _Result()
     r.tally = _dp(tally)
+    vox = np.zeros(problem.phantom.hu.shape, dtype=np.float64) if patient_dose else None
+    if vox is not None:
+        r.vox = _dp(vox)
     nthr = int(threads if threads is not None else (os.cpu_count() or 1))
     rc = lib().orc_run(C.byref(m.s), sd, int(hist_begin), n, nthr, C.byref(r))
     if rc != 0:
@@ -169,7 +175,7 @@ def run(problem, n_histories=None, seed=None, hist_begin=0, threads=None, physic
         "e_src": r.e_src, "e_ct": r.e_ct, "e_epid": np.array(r.e_epid[:len(problem.epid.layers)]),
         "e_esc": r.e_esc, "e_lost": r.e_lost,
         "counters": dict(zip(COUNTER_NAMES, [int(v) for v in r.counters])),
-        "threads": min(nthr, B),
+        "threads": min(nthr, B), "vox": vox,
     }
 
 
@@ -284,6 +290,15 @@ def lut_k(lut, t, s):
     k00, k01 = K[js, it], K[js, it + 1]
     k10, k11 = K[js + 1, it], K[js + 1, it + 1]
     return (1 - fs) * ((1 - ft) * k00 + ft * k01) + fs * ((1 - ft) * k10 + ft * k11)
+
+
+def patient_dose(vox_mev, phantom, n_hist):
+    """Per-history dose (Gy) of each CT voxel from its deposited energy (MeV):
+    E / (rho V), rho from the HU curve, V the voxel volume."""
+    rho, _ = hu_to_rho_mat(phantom.hu)
+    vol = phantom.vox[0] * phantom.vox[1] * phantom.vox[2]
+    vox_mev = np.asarray(vox_mev, dtype=np.float64)
+    return vox_mev * 1.602176634e-13 / (rho.reshape(vox_mev.shape) * vol * 1e-3) / float(n_hist)
 
 
 def batch_counts(n_hist, B, hist_begin=0):

@@ -358,6 +358,7 @@ typedef struct {
     double* tally;               /* [B][npy][npx] MeV */
     double e_src, e_ct, e_epid[O_MAXL], e_esc, e_lost;
     uint64_t counters[C_NCOUNT];
+    double* vox;                 /* [nz][ny][nx] MeV deposited per CT voxel, or NULL (patient dose off) */
 } orc_result;
 
 /* ------------------------------------------------------------------------ */
@@ -389,6 +390,7 @@ typedef struct {
     int n_rect;
     /* per worker */
     double* tally; double e_src, e_ct, e_epid[O_MAXL], e_esc, e_lost;
+    double* vox;                      /* this worker's voxel tally (patient dose), or NULL */
     uint64_t cnt[C_NCOUNT];
     uint64_t hist;
     o_part* stack; int sp, cap;
@@ -434,7 +436,12 @@ static double rest_extra(const o_part* p) { return (p->type == P_POSITRON) ? 2.0
 
 static void deposit(o_ctx* c, const o_part* p, const double pos[3], int layer, double dE) {
     if (dE == 0.0) return;
-    if (p->zone == Z_CT) { c->e_ct += dE; return; }
+    if (p->zone == Z_CT) {
+        c->e_ct += dE;
+        /* patient dose: the energy goes to the voxel the particle is in */
+        if (c->vox) c->vox[((size_t)p->cell[2] * c->P->ny + p->cell[1]) * c->P->nx + p->cell[0]] += dE;
+        return;
+    }
     c->e_epid[layer] += dE;
     const orc_problem* P = c->P;
     if (layer != P->sens_layer) return;
@@ -1053,9 +1060,11 @@ int orc_run(const orc_problem* P, uint64_t seed, uint64_t hist_begin, uint64_t n
     if (n_threads > P->n_batches) n_threads = P->n_batches;
     o_job* jobs = (o_job*)calloc((size_t)n_threads, sizeof(o_job));
     pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+    const size_t nvox = (size_t)P->nx * P->ny * P->nz;
     for (int t = 0; t < n_threads; t++) {
         jobs[t].local = base;
         jobs[t].local.tally = R->tally;
+        jobs[t].local.vox = R->vox ? (double*)calloc(nvox, sizeof(double)) : NULL;
         jobs[t].local.stack = NULL; jobs[t].local.sp = 0; jobs[t].local.cap = 0;
         jobs[t].seed = seed; jobs[t].h0 = hist_begin; jobs[t].n = n_hist;
         jobs[t].tid = t; jobs[t].nthreads = n_threads;
@@ -1068,6 +1077,10 @@ int orc_run(const orc_problem* P, uint64_t seed, uint64_t hist_begin, uint64_t n
         R->e_src += l->e_src; R->e_ct += l->e_ct; R->e_esc += l->e_esc; R->e_lost += l->e_lost;
         for (int k = 0; k < O_MAXL; k++) R->e_epid[k] += l->e_epid[k];
         for (int k = 0; k < C_NCOUNT; k++) R->counters[k] += l->cnt[k];
+        if (l->vox) {
+            for (size_t v = 0; v < nvox; v++) R->vox[v] += l->vox[v];
+            free(l->vox);
+        }
         free(l->stack);
     }
     free(jobs); free(th); free(base.rect); free(base.cdf);

@@ -573,3 +573,28 @@ def test_batch_counts_ragged():
     for n, h0 in ((0, 0), (5, 0), (37, 3), (1000, 15)):
         ids = np.arange(h0, h0 + n) % 16
         assert np.array_equal(oracle.batch_counts(n, 16, h0), np.bincount(ids, minlength=16))
+
+
+def test_patient_voxel_tally_first_collision_profile():
+    """Patient dose (the voxel tally): a 1 MeV pencil beam, photon-only, with
+    the photon cutoff just below 1 MeV, leaves all its energy at its first
+    interaction, so the energy per depth slab is E (exp(-mu y0) - exp(-mu y1))
+    per history; the voxel tally also sums to the CT energy."""
+    n = 200_000
+    prob = W.config_water_open(n_histories=n, field_cm=0.1)
+    phys = W.Physics(coupled=False, mono_energy=1.0, photon_cutoff=0.999)
+    r = oracle.run(prob, physics=phys, patient_dose=True, threads=8)
+    vox = r["vox"]
+    assert vox.shape == prob.phantom.hu.shape
+    assert vox.sum() == pytest.approx(r["e_ct"], rel=1e-12)
+    depth = vox.sum(axis=(0, 2))            # [ny]: the beam runs along +y at gantry 0
+    mu = _mu(W.MAT_WATER, 1.0).sum() * 1.0
+    dy = prob.phantom.vox[1]
+    y = np.arange(depth.size + 1) * dy
+    want = n * 1.0 * (np.exp(-mu * y[:-1]) - np.exp(-mu * y[1:]))
+    sd = np.sqrt(want * (1.0 - want / n))
+    assert np.all(np.abs(depth - want) <= 4.0 * sd + 1e-9), np.max(np.abs(depth - want) / sd)
+    d = oracle.patient_dose(vox, prob.phantom, n)
+    rho, _ = oracle.hu_to_rho_mat(prob.phantom.hu)
+    back = d * rho.reshape(vox.shape) * np.prod(prob.phantom.vox) * 1e-3 / 1.602176634e-13 * n
+    assert np.allclose(back, vox, rtol=1e-12, atol=0)
