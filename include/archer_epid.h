@@ -93,6 +93,8 @@ typedef struct mc_config {
     int regs_variant[4];          /* per transport kernel (CT photons, CT electrons, EPID photons, EPID
                                      electrons): build for 2, 3 or 4 CTAs of 256 threads per SM
                                      (register caps 128 / 85 / 64); 0 = 4 */
+    int patient_dose;             /* 1: also tally the energy deposited in every CT voxel (the patient
+                                     dose of the same histories; mc_get_patient_dose) */
 } mc_config;
 
 /* EPID layer stack from the source side (Sec. 2.1.3).  The centre of the
@@ -224,6 +226,15 @@ mc_status mc_get_tally(mc_ctx* ctx, uint64_t* tally, int on_device, void* stream
 
 /* Equivalent square s (Eq. 1 reading) and bounding rectangle sides a, b (cm) of field 0. */
 mc_status mc_field_size(mc_ctx* ctx, double* s, double* a, double* b);
+
+/* Patient dose (the dose engine the method builds on, Sec. 2.1):
+ * with mc_config.patient_dose, every energy deposit in the CT also goes, in
+ * the same 2^-8 eV units, to the voxel the particle is in, for all fields
+ * and runs since the tally was last reset.  dose (host or device per
+ * on_device) receives [nz][ny][nx] doubles: Gy per source history =
+ * E / (rho V) / N, rho from the HU curve, V the voxel volume, N the histories
+ * of all fields.  MC_ERR_STATE when patient dose is off or nothing has run. */
+mc_status mc_get_patient_dose(mc_ctx* ctx, double* dose, int on_device, void* stream);
 
 /* Cumulative statistics (energy balance from the fixed-point counters). */
 mc_status mc_get_stats(mc_ctx* ctx, mc_run_stats* stats);

@@ -28,7 +28,8 @@ EXPORTED = ("mc_config_default", "mc_create", "mc_destroy", "mc_init_geometry", 
             "mc_get_field_size", "mc_get_dose", "mc_get_epid_image", "mc_get_tmap", "mc_get_tally", "mc_field_size", "mc_get_stats",
             "mc_reset_tally", "mc_state_size", "mc_get_state", "mc_set_state", "mc_set_history_base", "mc_cancel",
             "mc_last_error",
-            "mc_status_string", "mc_test_philox", "mc_test_uniforms", "mc_dose_stats_noalloc", "mc_gamma")
+            "mc_status_string", "mc_test_philox", "mc_test_uniforms", "mc_dose_stats_noalloc", "mc_gamma",
+            "mc_get_patient_dose")
 
 
 class Config(C.Structure):
@@ -37,7 +38,8 @@ class Config(C.Structure):
                 ("wcc_mev", C.c_double), ("wcb_mev", C.c_double), ("step_fraction", C.c_double),
                 ("n_batches", C.c_int), ("max_steps", C.c_int), ("block_size", C.c_int),
                 ("ctas_per_sm", C.c_int), ("bank_capacity", C.c_uint32), ("primaries_per_wave", C.c_uint32),
-                ("time_kernels", C.c_int), ("use_graph", C.c_int), ("regs_variant", C.c_int * 4)]
+                ("time_kernels", C.c_int), ("use_graph", C.c_int), ("regs_variant", C.c_int * 4),
+                ("patient_dose", C.c_int)]
 
 
 class EpidDesc(C.Structure):
@@ -124,6 +126,7 @@ def load(build_if_stale: bool = True):
     lib.mc_test_uniforms.argtypes = [u64, u64, u32, i, vp, vp]
     lib.mc_dose_stats_noalloc.argtypes = [vp, i, i, i, u64, d, vp, vp, vp, vp]
     lib.mc_gamma.argtypes = [vp, vp, i, i, d, d, d, d, d, d, vp, P(d), vp]
+    lib.mc_get_patient_dose.argtypes = [vp, vp, i, vp]
     for name in EXPORTED:
         if name not in ("mc_config_default", "mc_last_error", "mc_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -225,6 +228,7 @@ class Simulator:
         self._check(self.lib.mc_init_geometry(self.h, ptr, nx, ny, nz, vox, org, C.byref(e), on_dev,
                                               _stream_ptr(stream)))
         self.epid = epid
+        self._ct_shape = (nz, ny, nx)
 
     @staticmethod
     def _field_desc(field, lut, keep):
@@ -339,6 +343,13 @@ class Simulator:
     def tally(self, stream=None, field=0):
         """Raw sub-tallies of one field, uint64 [B][npy][npx]."""
         return self.tally_all(stream)[field]
+
+    def patient_dose(self, stream=None):
+        """Per-history dose (Gy) of every CT voxel [nz][ny][nx] (needs patient_dose=1)."""
+        nz, ny, nx = self._ct_shape
+        out = np.empty((nz, ny, nx))
+        self._check(self.lib.mc_get_patient_dose(self.h, C.c_void_p(out.ctypes.data), 0, _stream_ptr(stream)))
+        return out
 
     def field_size(self, field=0):
         s, a, b = C.c_double(), C.c_double(), C.c_double()

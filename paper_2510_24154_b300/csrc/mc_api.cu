@@ -94,6 +94,8 @@ struct mc_ctx {
     size_t tally_n = 0;
     unsigned long long* d_energy = nullptr;
     unsigned long long* d_events = nullptr;
+    unsigned long long* d_vox = nullptr;     // patient dose: [nz][ny][nx], 2^-8 eV
+    size_t vox_n = 0;
     // statistics scratch
     double* d_dose = nullptr;
     double* d_sigma = nullptr;
@@ -161,6 +163,7 @@ mc_status clear_tally(mc_ctx* c, cudaStream_t s) {
     if (c->d_tally) CUDA_TRY(c, cudaMemsetAsync(c->d_tally, 0, c->tally_n * sizeof(unsigned long long), s));
     CUDA_TRY(c, cudaMemsetAsync(c->d_energy, 0, sizeof(unsigned long long) * mc::kNumEnergy, s));
     CUDA_TRY(c, cudaMemsetAsync(c->d_events, 0, sizeof(unsigned long long) * mc::kNumEvents, s));
+    if (c->d_vox) CUDA_TRY(c, cudaMemsetAsync(c->d_vox, 0, c->vox_n * sizeof(unsigned long long), s));
     for (FieldHost& f : c->fields) f.hist_done = 0;
     return MC_OK;
 }
@@ -221,6 +224,7 @@ void make_params(const mc_ctx* c, Params& P, uint64_t seed) {
     P.tally = c->d_tally;
     P.energy = c->d_energy;
     P.events = c->d_events;
+    P.vox = c->cfg.patient_dose ? c->d_vox : nullptr;
     P.ctl = c->d_ctl;
     for (int t = 0; t < mc::kNumBanks; ++t)
         for (int k = 0; k < 2; ++k) P.bank[t][k] = c->bank[t][k];
@@ -605,11 +609,15 @@ mc_status check_field(mc_ctx* c, int field) {
     return MC_OK;
 }
 
-// State layout (uint64 words): magic, B, npx, npy, number of fields, the
-// next history index of each field, energy counters, event counters,
-// sub-tallies.
-const uint64_t kStateMagic = 0x4550494453543032ull;   // "EPIDST02"
-size_t state_words(const mc_ctx* c) { return 5 + c->fields.size() + mc::kNumEnergy + mc::kNumEvents + c->tally_n; }
+// State layout (uint64 words): magic, B, npx, npy, number of fields, voxels
+// of the patient-dose tally (0 when off), the next history index of each
+// field, energy counters, event counters, sub-tallies, patient-dose tally.
+const uint64_t kStateMagic = 0x4550494453543033ull;   // "EPIDST03"
+constexpr size_t kStateHead = 6;
+size_t vox_words(const mc_ctx* c) { return c->cfg.patient_dose ? c->vox_n : 0; }
+size_t state_words(const mc_ctx* c) {
+    return kStateHead + c->fields.size() + mc::kNumEnergy + mc::kNumEvents + c->tally_n + vox_words(c);
+}
 
 }  // namespace
 
@@ -635,6 +643,7 @@ void mc_config_default(mc_config* cfg) {
     cfg->time_kernels = 0;
     cfg->use_graph = 0;
     for (int t = 0; t < 4; ++t) cfg->regs_variant[t] = 4;
+    cfg->patient_dose = 0;
 }
 
 const char* mc_status_string(mc_status s) {
@@ -673,6 +682,7 @@ mc_status mc_create(const mc_config* cfg_in, int device, mc_ctx** out) {
         return MC_ERR_ARG;
     if (cfg.bank_capacity < 1024 || cfg.primaries_per_wave < 32) return MC_ERR_ARG;
     if (cfg.use_graph != 0 && cfg.use_graph != 1) return MC_ERR_ARG;
+    if (cfg.patient_dose != 0 && cfg.patient_dose != 1) return MC_ERR_ARG;
 
     mc_ctx* c = new mc_ctx();
     c->cfg = cfg;
@@ -757,6 +767,7 @@ mc_status mc_destroy(mc_ctx* c) {
     dfree(c->d_maxbits);
     dfree(c->d_fields);
     dfree(c->d_first);
+    dfree(c->d_vox);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     delete c;
@@ -812,6 +823,13 @@ mc_status mc_init_geometry(mc_ctx* c, const int16_t* hu, int nx, int ny, int nz,
     CUDA_TRY(c, mc::launch_macro_grid(c->d_rho, nx, ny, nz, M, c->mg[0], c->mg[1], c->mg[2], c->thr[2], c->d_mgrid,
                                       c->sm_count, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (c->cfg.patient_dose && c->vox_n != nvox) {
+        dfree(c->d_vox);
+        c->vox_n = 0;
+        CUDA_TRY(c, cudaMalloc(&c->d_vox, nvox * sizeof(unsigned long long)));
+        c->vox_n = nvox;
+    }
+    if (c->d_vox) CUDA_TRY(c, cudaMemset(c->d_vox, 0, c->vox_n * sizeof(unsigned long long)));
     c->nx = nx; c->ny = ny; c->nz = nz;
     for (int k = 0; k < 3; ++k) { c->vox[k] = vox_cm[k]; c->origin[k] = origin_cm[k]; }
     c->epid = E;
@@ -953,6 +971,33 @@ mc_status mc_get_tally(mc_ctx* c, uint64_t* tally, int on_device, void* stream) 
     return MC_OK;
 }
 
+mc_status mc_get_patient_dose(mc_ctx* c, double* dose, int on_device, void* stream) {
+    if (!c) return MC_ERR_ARG;
+    if (!dose) return fail(c, MC_ERR_ARG, "null output");
+    if (!c->cfg.patient_dose || !c->d_vox || !c->has_geom) return fail(c, MC_ERR_STATE, "patient dose is off");
+    uint64_t N = 0;
+    for (const FieldHost& f : c->fields) N += f.hist_done;
+    if (N == 0) return fail(c, MC_ERR_STATE, "no histories run");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaStream_t s = as_stream(stream);
+    const double vol = c->vox[0] * c->vox[1] * c->vox[2];
+    // Gy per history = E[MeV] * J/MeV / (rho[g/cm^3] V[cm^3] 1e-3 kg/g) / N
+    const double conv = kJoulePerMeV / (kQuantaPerMeV * vol * 1e-3 * static_cast<double>(N));
+    double* out = dose;
+    double* tmp = nullptr;
+    if (!on_device) {
+        CUDA_TRY(c, cudaMalloc(&tmp, sizeof(double) * c->vox_n));
+        out = tmp;
+    }
+    cudaError_t e = mc::launch_vox_dose(c->d_vox, c->d_rho, c->vox_n, conv, out, s);
+    if (e == cudaSuccess && !on_device)
+        e = cudaMemcpyAsync(dose, tmp, sizeof(double) * c->vox_n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(s);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return fail(c, MC_ERR_CUDA, std::string("patient dose: ") + cudaGetErrorString(e));
+    return MC_OK;
+}
+
 mc_status mc_get_field_size(mc_ctx* c, int field, double* sz, double* a, double* b) {
     if (!c) return MC_ERR_ARG;
     const mc_status st = check_field(c, field);
@@ -991,13 +1036,17 @@ mc_status mc_get_state(mc_ctx* c, void* buf, size_t bytes, void* stream) {
     uint64_t* w = static_cast<uint64_t*>(buf);
     const size_t F = c->fields.size();
     w[0] = kStateMagic; w[1] = c->cfg.n_batches; w[2] = c->epid.npx; w[3] = c->epid.npy; w[4] = F;
-    for (size_t i = 0; i < F; ++i) w[5 + i] = c->fields[i].hist_done;
-    uint64_t* q = w + 5 + F;
+    w[5] = vox_words(c);
+    for (size_t i = 0; i < F; ++i) w[kStateHead + i] = c->fields[i].hist_done;
+    uint64_t* q = w + kStateHead + F;
     CUDA_TRY(c, cudaMemcpyAsync(q, c->d_energy, sizeof(uint64_t) * mc::kNumEnergy, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(c, cudaMemcpyAsync(q + mc::kNumEnergy, c->d_events, sizeof(uint64_t) * mc::kNumEvents,
                                 cudaMemcpyDeviceToHost, s));
     CUDA_TRY(c, cudaMemcpyAsync(q + mc::kNumEnergy + mc::kNumEvents, c->d_tally, sizeof(uint64_t) * c->tally_n,
                                 cudaMemcpyDeviceToHost, s));
+    if (vox_words(c))
+        CUDA_TRY(c, cudaMemcpyAsync(q + mc::kNumEnergy + mc::kNumEvents + c->tally_n, c->d_vox,
+                                    sizeof(uint64_t) * c->vox_n, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
     return MC_OK;
 }
@@ -1009,18 +1058,22 @@ mc_status mc_set_state(mc_ctx* c, const void* buf, size_t bytes, void* stream) {
     const uint64_t* w = static_cast<const uint64_t*>(buf);
     const size_t F = c->fields.size();
     if (w[0] != kStateMagic || w[1] != static_cast<uint64_t>(c->cfg.n_batches) ||
-        w[2] != static_cast<uint64_t>(c->epid.npx) || w[3] != static_cast<uint64_t>(c->epid.npy) || w[4] != F)
+        w[2] != static_cast<uint64_t>(c->epid.npx) || w[3] != static_cast<uint64_t>(c->epid.npy) || w[4] != F ||
+        w[5] != vox_words(c))
         return fail(c, MC_ERR_ARG, "state does not match this context");
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
-    const uint64_t* q = w + 5 + F;
+    const uint64_t* q = w + kStateHead + F;
     CUDA_TRY(c, cudaMemcpyAsync(c->d_energy, q, sizeof(uint64_t) * mc::kNumEnergy, cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_events, q + mc::kNumEnergy, sizeof(uint64_t) * mc::kNumEvents,
                                 cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_tally, q + mc::kNumEnergy + mc::kNumEvents, sizeof(uint64_t) * c->tally_n,
                                 cudaMemcpyHostToDevice, s));
+    if (vox_words(c))
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_vox, q + mc::kNumEnergy + mc::kNumEvents + c->tally_n,
+                                    sizeof(uint64_t) * c->vox_n, cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
-    for (size_t i = 0; i < F; ++i) c->fields[i].hist_done = w[5 + i];
+    for (size_t i = 0; i < F; ++i) c->fields[i].hist_done = w[kStateHead + i];
     return MC_OK;
 }
 

@@ -345,6 +345,20 @@ __global__ void k_gamma(const double* __restrict__ ref, const double* __restrict
     if (gv <= 1.0) atomicAdd(&counts[1], 1ull);
 }
 
+__global__ void k_vox_dose(const unsigned long long* __restrict__ vox, const float* __restrict__ rho, size_t n,
+                           double conv, double* __restrict__ dose) {
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x)
+        dose[i] = static_cast<double>(vox[i]) * conv / static_cast<double>(rho[i]);
+}
+
+cudaError_t launch_vox_dose(const unsigned long long* vox, const float* rho, size_t n, double conv, double* dose,
+                            cudaStream_t s) {
+    k_vox_dose<<<static_cast<unsigned>(std::min<size_t>((n + 255) / 256, 148 * 32)), 256, 0, s>>>(vox, rho, n, conv,
+                                                                                                  dose);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gamma(const double* ref, const double* ev, int nx, int ny, double pix, double dd_frac, double dta,
                          double thr_frac, double h, double rad, double* gam, unsigned long long* scratch,
                          cudaStream_t s) {

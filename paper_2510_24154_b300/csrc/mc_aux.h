@@ -39,6 +39,9 @@ cudaError_t launch_dose(const unsigned long long* tally, int npix, int B, const 
                         unsigned int* part_cnt, double* u, cudaStream_t s);
 cudaError_t launch_lut(const double* dose, const double* t, int npix, const double* tn, const double* ks, int nt,
                        double k_scale, float* signal, cudaStream_t s);
+// dose[v] = vox[v] * conv / rho[v] (patient dose)
+cudaError_t launch_vox_dose(const unsigned long long* vox, const float* rho, size_t n, double conv, double* dose,
+                            cudaStream_t s);
 // scratch: 3 device u64 (max bits, evaluated count, passed count)
 cudaError_t launch_gamma(const double* ref, const double* ev, int nx, int ny, double pix, double dd_frac, double dta,
                          double thr_frac, double h, double rad, double* gam, unsigned long long* scratch,

@@ -124,6 +124,7 @@ struct Params {
     unsigned long long* tally;      // [n_fields][B][npy][npx]
     unsigned long long* energy;     // [kNumEnergy]
     unsigned long long* events;     // [kNumEvents]
+    unsigned long long* vox;        // patient dose: energy per CT voxel [nz][ny][nx] (2^-8 eV), or null
     Ctl* ctl;
     BankPtr bank[kNumBanks][2];
     uint32_t cap;

@@ -72,8 +72,16 @@ __device__ __forceinline__ void deposit_epid(const Params& P, unsigned long long
 template <bool EPID>
 __device__ __forceinline__ void deposit(const Params& P, Acc& a, unsigned long long* s_energy, uint32_t cell,
                                         float x, float y, uint32_t hist, uint32_t flags, float dE) {
-    if (EPID) deposit_epid(P, s_energy, static_cast<int>(cell), x, y, hist, flags, dE);
-    else if (dE > 0.0f) a.ct += quanta(dE);
+    if (EPID) {
+        deposit_epid(P, s_energy, static_cast<int>(cell), x, y, hist, flags, dE);
+    } else if (dE > 0.0f) {
+        const unsigned long long q = quanta(dE);
+        a.ct += q;
+        // patient dose: the same quanta into the particle's voxel, so the voxel
+        // tally sums to the CT energy exactly
+        if (P.vox)
+            atomicAdd(&P.vox[(static_cast<size_t>(cell_z(cell)) * P.ny + cell_y(cell)) * P.nx + cell_x(cell)], q);
+    }
 }
 
 // Sends a particle that leaves the CT across the vacuum gap: onto the EPID's
