@@ -29,8 +29,9 @@ def test_voxel_tally_closes_with_ct_energy():
     p = G.thorax_case(n=50_000, scale=4, epid_scale=8)
     sim, st, _ = G.gpu_run(p, patient_dose=1)
     e = _energy_mev(sim.patient_dose(), p.phantom, st["histories"])
-    # both are sums of the same 2^-8 eV quanta; only the float conversion differs
-    assert e.sum() == pytest.approx(st["e_ct"], rel=1e-9)
+    # both are sums of the same 2^-8 eV quanta; the dose divides by the
+    # float32 density the transport uses (relative rounding <= 6e-8)
+    assert e.sum() == pytest.approx(st["e_ct"], rel=1e-7)
     assert (e >= 0).all()
 
 
