@@ -227,6 +227,25 @@ mc_status mc_get_tally(mc_ctx* ctx, uint64_t* tally, int on_device, void* stream
 /* Equivalent square s (Eq. 1 reading) and bounding rectangle sides a, b (cm) of field 0. */
 mc_status mc_field_size(mc_ctx* ctx, double* s, double* a, double* b);
 
+/* Plan image (VMAT arcs and multi-field plans): with the fields of a batch
+ * as control points, dose = sum_f w_f D_f and signal = sum_f w_f k(t_f, s_f)
+ * D_f over the fields, D_f the per-history dose of field f, t_f its
+ * radiological-thickness map and s_f its Eq. 1 size -- what an EPID
+ * integrating over the arc records per unit weight.  weights: host array of
+ * n_fields (e.g. MU fractions) or NULL for equal weights 1/n_fields.  dose
+ * and signal: [npy][npx] doubles (host or device per on_device); either may
+ * be NULL; signal needs the k-table. */
+mc_status mc_get_plan_image(mc_ctx* ctx, const double* weights, double* dose, double* signal, int on_device,
+                            void* stream);
+
+/* Bilinear resampling of an image between pixel grids centred on the same
+ * axis (pixel centres at ((i + 1/2) - n/2) pitch; the border value is held
+ * beyond the outer centres), e.g. a 2.5 mm dose image onto the detector's
+ * 1190 x 1190 grid at 0.336 mm (Sec. 2.3).  src [sny][snx], dst [dny][dnx]:
+ * device doubles.  Synchronizes `stream`. */
+mc_status mc_resample_image(const double* src, int snx, int sny, double src_pitch, double* dst, int dnx, int dny,
+                            double dst_pitch, void* stream);
+
 /* Patient dose (the dose engine the method builds on, Sec. 2.1):
  * with mc_config.patient_dose, every energy deposit in the CT also goes, in
  * the same 2^-8 eV units, to the voxel the particle is in, for all fields

@@ -301,6 +301,36 @@ def patient_dose(vox_mev, phantom, n_hist):
     return vox_mev * 1.602176634e-13 / (rho.reshape(vox_mev.shape) * vol * 1e-3) / float(n_hist)
 
 
+def resample(src, src_pitch, dnx, dny, dst_pitch):
+    """Bilinear resampling onto another pixel grid centred on the same axis:
+    destination centre X = ((i + 1/2) - n/2) pitch is looked up at source
+    index X / src_pitch + snx/2 - 1/2, clamped to the outer source centres."""
+    src = np.asarray(src, dtype=np.float64)
+    sny, snx = src.shape
+    X = ((np.arange(dnx) + 0.5) - 0.5 * dnx) * dst_pitch
+    Y = ((np.arange(dny) + 0.5) - 0.5 * dny) * dst_pitch
+    fx = np.clip(X / src_pitch + 0.5 * snx - 0.5, 0, snx - 1)
+    fy = np.clip(Y / src_pitch + 0.5 * sny - 0.5, 0, sny - 1)
+    x0 = np.floor(fx).astype(int)
+    y0 = np.floor(fy).astype(int)
+    x1 = np.minimum(x0 + 1, snx - 1)
+    y1 = np.minimum(y0 + 1, sny - 1)
+    ax = (fx - x0)[None, :]
+    ay = (fy - y0)[:, None]
+    return ((1 - ay) * ((1 - ax) * src[y0][:, x0] + ax * src[y0][:, x1]) +
+            ay * ((1 - ax) * src[y1][:, x0] + ax * src[y1][:, x1]))
+
+
+def plan_image(doses, tmaps, fields, lut, weights=None):
+    """Weighted sums over control points / fields: sum_f w_f D_f and
+    sum_f w_f k(t_f, s_f) D_f (Sec. 3.1 per field)."""
+    F = len(doses)
+    w = np.full(F, 1.0 / F) if weights is None else np.asarray(weights, dtype=np.float64)
+    dose = sum(w[f] * np.asarray(doses[f]) for f in range(F))
+    sig = sum(w[f] * lut_k(lut, tmaps[f], effective_field_size(fields[f])) * np.asarray(doses[f]) for f in range(F))
+    return dose, sig
+
+
 def batch_counts(n_hist, B, hist_begin=0):
     """Number of history ids h in [hist_begin, hist_begin+n) with h mod B == b."""
     ids = np.arange(B)

@@ -29,7 +29,7 @@ EXPORTED = ("mc_config_default", "mc_create", "mc_destroy", "mc_init_geometry", 
             "mc_reset_tally", "mc_state_size", "mc_get_state", "mc_set_state", "mc_set_history_base", "mc_cancel",
             "mc_last_error",
             "mc_status_string", "mc_test_philox", "mc_test_uniforms", "mc_dose_stats_noalloc", "mc_gamma",
-            "mc_get_patient_dose")
+            "mc_get_patient_dose", "mc_get_plan_image", "mc_resample_image")
 
 
 class Config(C.Structure):
@@ -127,6 +127,8 @@ def load(build_if_stale: bool = True):
     lib.mc_dose_stats_noalloc.argtypes = [vp, i, i, i, u64, d, vp, vp, vp, vp]
     lib.mc_gamma.argtypes = [vp, vp, i, i, d, d, d, d, d, d, vp, P(d), vp]
     lib.mc_get_patient_dose.argtypes = [vp, vp, i, vp]
+    lib.mc_get_plan_image.argtypes = [vp, vp, vp, vp, i, vp]
+    lib.mc_resample_image.argtypes = [vp, i, i, d, vp, i, i, d, vp]
     for name in EXPORTED:
         if name not in ("mc_config_default", "mc_last_error", "mc_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -344,6 +346,17 @@ class Simulator:
         """Raw sub-tallies of one field, uint64 [B][npy][npx]."""
         return self.tally_all(stream)[field]
 
+    def plan_image(self, weights=None, stream=None):
+        """Weighted sums over the fields: (dose, signal) [npy][npx] (signal None without a k-table)."""
+        ny, nx = self._npix()
+        d = np.empty((ny, nx))
+        sg = np.empty((ny, nx))
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+        self._check(self.lib.mc_get_plan_image(self.h, C.c_void_p(w.ctypes.data) if w is not None else None,
+                                               C.c_void_p(d.ctypes.data), C.c_void_p(sg.ctypes.data), 0,
+                                               _stream_ptr(stream)))
+        return d, sg
+
     def patient_dose(self, stream=None):
         """Per-history dose (Gy) of every CT voxel [nz][ny][nx] (needs patient_dose=1)."""
         nz, ny, nx = self._ct_shape
@@ -433,3 +446,14 @@ def gamma(ref, ev, pixel_mm, dd=0.01, dta_mm=1.0, threshold=0.10, step_mm=0.0, r
     if st != 0:
         raise MCError(st, "mc_gamma failed")
     return rate.value
+
+
+def resample_image(src, src_pitch, dst, dst_pitch, stream=None):
+    """Bilinear resampling of a CUDA float64 image onto `dst`'s grid (same centre)."""
+    lib = load()
+    sny, snx = src.shape
+    dny, dnx = dst.shape
+    st = lib.mc_resample_image(_ptr(src), snx, sny, float(src_pitch), _ptr(dst), dnx, dny, float(dst_pitch),
+                               _stream_ptr(stream))
+    if st != 0:
+        raise MCError(st, "mc_resample_image failed")

@@ -971,6 +971,40 @@ mc_status mc_get_tally(mc_ctx* c, uint64_t* tally, int on_device, void* stream) 
     return MC_OK;
 }
 
+mc_status mc_get_plan_image(mc_ctx* c, const double* weights, double* dose, double* signal, int on_device,
+                            void* stream) {
+    if (!c) return MC_ERR_ARG;
+    if (!c->has_field) return fail(c, MC_ERR_STATE, "no field");
+    if (signal && !c->has_lut) return fail(c, MC_ERR_STATE, "no k-table");
+    const int F = nfields(c), np = npix(c);
+    for (int f = 0; f < F; ++f)
+        if (c->fields[f].hist_done == 0) return fail(c, MC_ERR_STATE, "a field has no histories");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaStream_t s = as_stream(stream);
+    double *acc_d = nullptr, *acc_s = nullptr;
+    CUDA_TRY(c, cudaMalloc(&acc_d, sizeof(double) * np * 2));
+    acc_s = acc_d + np;
+    cudaError_t e = cudaMemsetAsync(acc_d, 0, sizeof(double) * np * 2, s);
+    for (int f = 0; f < F && e == cudaSuccess; ++f) {
+        const mc_status st = compute_dose(c, f, c->d_dose, c->d_sigma, nullptr, s);
+        if (st != MC_OK) {
+            cudaFree(acc_d);
+            return st;
+        }
+        const double w = weights ? weights[f] : 1.0 / F;
+        e = mc::launch_plan_accum(c->d_dose, c->d_tmap + static_cast<size_t>(f) * np, np, c->d_lut_t,
+                                  c->has_lut ? c->d_lut_ks + static_cast<size_t>(f) * c->lut_nt : nullptr, c->lut_nt,
+                                  c->k_scale, w, acc_d, c->has_lut ? acc_s : nullptr, s);
+    }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (e == cudaSuccess && dose) e = cudaMemcpyAsync(dose, acc_d, sizeof(double) * np, kind, s);
+    if (e == cudaSuccess && signal) e = cudaMemcpyAsync(signal, acc_s, sizeof(double) * np, kind, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(acc_d);
+    if (e != cudaSuccess) return fail(c, MC_ERR_CUDA, std::string("plan image: ") + cudaGetErrorString(e));
+    return MC_OK;
+}
+
 mc_status mc_get_patient_dose(mc_ctx* c, double* dose, int on_device, void* stream) {
     if (!c) return MC_ERR_ARG;
     if (!dose) return fail(c, MC_ERR_ARG, "null output");
@@ -1109,6 +1143,16 @@ mc_status mc_gamma(const double* ref, const double* ev, int nx, int ny, double p
     if (e != cudaSuccess) return MC_ERR_CUDA;
     *pass_rate = counts[1] ? static_cast<double>(counts[2]) / static_cast<double>(counts[1]) : 1.0;
     return MC_OK;
+}
+
+mc_status mc_resample_image(const double* src, int snx, int sny, double src_pitch, double* dst, int dnx, int dny,
+                            double dst_pitch, void* stream) {
+    if (!src || !dst || snx < 1 || sny < 1 || dnx < 1 || dny < 1 || !(src_pitch > 0) || !(dst_pitch > 0) ||
+        static_cast<long long>(dnx) * dny > (1ll << 28))
+        return MC_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    if (mc::launch_resample(src, snx, sny, src_pitch, dst, dnx, dny, dst_pitch, s) != cudaSuccess) return MC_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? MC_OK : MC_ERR_CUDA;
 }
 
 mc_status mc_test_philox(const uint32_t* in, uint32_t* out, int n, void* stream) {

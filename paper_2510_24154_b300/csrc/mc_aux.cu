@@ -345,6 +345,53 @@ __global__ void k_gamma(const double* __restrict__ ref, const double* __restrict
     if (gv <= 1.0) atomicAdd(&counts[1], 1ull);
 }
 
+__device__ double bilin_clamped(const double* img, int nx, int ny, double fx, double fy);
+
+// Plan image: acc_dose += w dose, acc_signal += w k(t, s) dose (FP64 sums
+// over the fields of a batch).
+__global__ void k_plan_accum(const double* __restrict__ dose, const double* __restrict__ t, int npix,
+                             const double* __restrict__ tn, const double* __restrict__ ks, int nt, double k_scale,
+                             double w, double* __restrict__ acc_dose, double* __restrict__ acc_signal) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npix) return;
+    acc_dose[i] += w * dose[i];
+    if (!acc_signal) return;
+    double tt = fmin(fmax(t[i], tn[0]), tn[nt - 1]);
+    int lo = 0, hi = nt - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (tn[mid] <= tt) lo = mid; else hi = mid;
+    }
+    lo = min(lo, nt - 2);
+    const double f = (tt - tn[lo]) / (tn[lo + 1] - tn[lo]);
+    acc_signal[i] += w * k_scale * (ks[lo] + f * (ks[lo + 1] - ks[lo])) * dose[i];
+}
+
+cudaError_t launch_plan_accum(const double* dose, const double* t, int npix, const double* tn, const double* ks,
+                              int nt, double k_scale, double w, double* acc_dose, double* acc_signal,
+                              cudaStream_t s) {
+    k_plan_accum<<<(npix + 255) / 256, 256, 0, s>>>(dose, t, npix, tn, ks, nt, k_scale, w, acc_dose, acc_signal);
+    return cudaGetLastError();
+}
+
+// Bilinear resampling between two pixel grids centred on the same axis
+// (pixel centres at ((i + 0.5) - n / 2) pitch), clamped at the border.
+__global__ void k_resample(const double* __restrict__ src, int snx, int sny, double sp, double* __restrict__ dst,
+                           int dnx, int dny, double dp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dnx * dny) return;
+    const int x = i % dnx, y = i / dnx;
+    const double X = ((x + 0.5) - 0.5 * dnx) * dp, Y = ((y + 0.5) - 0.5 * dny) * dp;
+    dst[i] = bilin_clamped(src, snx, sny, X / sp + 0.5 * snx - 0.5, Y / sp + 0.5 * sny - 0.5);
+}
+
+cudaError_t launch_resample(const double* src, int snx, int sny, double sp, double* dst, int dnx, int dny, double dp,
+                            cudaStream_t s) {
+    const int n = dnx * dny;
+    k_resample<<<(n + 255) / 256, 256, 0, s>>>(src, snx, sny, sp, dst, dnx, dny, dp);
+    return cudaGetLastError();
+}
+
 __global__ void k_vox_dose(const unsigned long long* __restrict__ vox, const float* __restrict__ rho, size_t n,
                            double conv, double* __restrict__ dose) {
     for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;

@@ -39,6 +39,10 @@ cudaError_t launch_dose(const unsigned long long* tally, int npix, int B, const 
                         unsigned int* part_cnt, double* u, cudaStream_t s);
 cudaError_t launch_lut(const double* dose, const double* t, int npix, const double* tn, const double* ks, int nt,
                        double k_scale, float* signal, cudaStream_t s);
+cudaError_t launch_plan_accum(const double* dose, const double* t, int npix, const double* tn, const double* ks,
+                              int nt, double k_scale, double w, double* acc_dose, double* acc_signal, cudaStream_t s);
+cudaError_t launch_resample(const double* src, int snx, int sny, double sp, double* dst, int dnx, int dny, double dp,
+                            cudaStream_t s);
 // dose[v] = vox[v] * conv / rho[v] (patient dose)
 cudaError_t launch_vox_dose(const unsigned long long* vox, const float* rho, size_t n, double conv, double* dose,
                             cudaStream_t s);

@@ -330,6 +330,39 @@ def config_batched_plan(seed=2, n_fields=25, scale=1, epid_scale=1,
     return ph, ep, fields, hist
 
 
+def vmat_arc(rng: np.random.Generator, n_cp: int = 64, start_deg: float = 181.0, arc_deg: float = 358.0,
+             leaf_range: float = 8.0, jaw_y: float = 8.0, step_cm: float = 0.5):
+    """A VMAT arc: n_cp control points, gantry from start_deg over arc_deg
+    (clockwise), one aperture each whose leaf tips follow a bounded random
+    walk (steps N(0, step_cm)) so that neighbouring apertures are alike;
+    MU per control point ~ 0.5 + U(0, 1), normalised.  Returns the control
+    points as single-segment fields and their MU fractions."""
+    edges = millennium_pair_edges()
+    n_pairs = edges.size - 1
+    tips = np.sort(rng.uniform(-leaf_range / 2, leaf_range / 2, size=(n_pairs, 2)), axis=1)
+    mu = 0.5 + rng.uniform(0.0, 1.0, size=n_cp)
+    mu /= mu.sum()
+    fields = []
+    for k in range(n_cp):
+        tips = np.clip(tips + rng.normal(0.0, step_cm, size=tips.shape), -leaf_range, leaf_range)
+        tips.sort(axis=1)
+        tips[:, 1] = np.maximum(tips[:, 1], tips[:, 0] + 0.2)       # keep every pair open
+        g = (start_deg + arc_deg * k / max(n_cp - 1, 1)) % 360.0
+        jaws = np.array([[-leaf_range, leaf_range, -jaw_y, jaw_y]])
+        fields.append(Field(edges, tips[None].copy(), jaws, np.ones(1), g))
+    return fields, mu
+
+
+def config_vmat(n_cp: int = 64, seed: int = 5, scale: int = 1, epid_npx: int = 1190, epid_pitch: float = 0.0336):
+    """VMAT arc on the thorax CT, imaged by the 1190 x 1190 EPID at 0.336 mm
+    (the paper's detector, Sec. 2.3)."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = 256 // scale, 256 // scale, 128 // scale
+    ph = thorax_ct(np.random.default_rng(1), nx, ny, nz, 0.2 * scale)
+    fields, mu = vmat_arc(rng, n_cp)
+    return ph, epid_default(epid_npx, epid_npx, epid_pitch), fields, mu
+
+
 def config_anthropomorphic(n_histories=1_000_000_000, seed=4) -> Problem:
     """512x512x200 at 1 mm, one 40-segment field, EPID 1190x1190 at 0.336 mm."""
     rng = np.random.default_rng(seed)

@@ -598,3 +598,39 @@ def test_patient_voxel_tally_first_collision_profile():
     rho, _ = oracle.hu_to_rho_mat(prob.phantom.hu)
     back = d * rho.reshape(vox.shape) * np.prod(prob.phantom.vox) * 1e-3 / 1.602176634e-13 * n
     assert np.allclose(back, vox, rtol=1e-12, atol=0)
+
+
+def test_resample_pins():
+    """Bilinear resampling: identity on the same grid, constants stay
+    constant, a linear ramp is reproduced inside the source's centre hull."""
+    r = np.random.default_rng(10)
+    img = r.normal(size=(12, 16))
+    assert np.allclose(oracle.resample(img, 2.5, 16, 12, 2.5), img, rtol=0, atol=1e-14)
+    assert np.allclose(oracle.resample(np.full((8, 8), 3.25), 2.5, 37, 29, 0.336), 3.25)
+    sny, snx, sp = 20, 24, 2.5
+    Xs = ((np.arange(snx) + 0.5) - snx / 2) * sp
+    Ys = ((np.arange(sny) + 0.5) - sny / 2) * sp
+    ramp = 0.7 * Xs[None, :] - 1.3 * Ys[:, None] + 5.0
+    dnx = dny = 101
+    dp = 0.336
+    out = oracle.resample(ramp, sp, dnx, dny, dp)
+    Xd = ((np.arange(dnx) + 0.5) - dnx / 2) * dp
+    Yd = ((np.arange(dny) + 0.5) - dny / 2) * dp
+    want = 0.7 * Xd[None, :] - 1.3 * Yd[:, None] + 5.0
+    inside = (np.abs(Xd)[None, :] <= Xs.max()) & (np.abs(Yd)[:, None] <= Ys.max())
+    assert np.allclose(out[inside], want[inside], rtol=0, atol=1e-12)
+
+
+def test_plan_image_is_the_weighted_sum():
+    lut = W.lut_bilinear()
+    r = np.random.default_rng(11)
+    fields, mu = W.vmat_arc(r, 5)
+    doses = [r.uniform(size=(6, 7)) for _ in fields]
+    tmaps = [r.uniform(0, 30, size=(6, 7)) for _ in fields]
+    d, s = oracle.plan_image(doses, tmaps, fields, lut, mu)
+    assert np.allclose(d, sum(m * x for m, x in zip(mu, doses)))
+    one = [oracle.lut_k(lut, t, oracle.effective_field_size(f)) * x for f, t, x in zip(fields, tmaps, doses)]
+    assert np.allclose(s, sum(m * x for m, x in zip(mu, one)))
+    assert len(fields) == 5 and np.isclose(mu.sum(), 1.0)
+    g = [f.gantry_deg for f in fields]
+    assert g[0] == pytest.approx(181.0) and g[-1] == pytest.approx((181.0 + 358.0) % 360.0)
