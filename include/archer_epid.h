@@ -123,6 +123,8 @@ typedef struct mc_field_desc {
     double sad_cm, sid_cm;
     double iso_cm[3];             /* isocentre in CT coordinates */
     int eq1_literal;              /* 0: s = 2ab/(a+b); 1: s = ab/(2(a+b)) exactly as Eq. 1 is printed */
+    double leaf_transmission;     /* fraction of the open fluence passing closed leaves inside the jaws,
+                                     0 <= T < 1 (0: ideal MLC; the jaws stay opaque) */
 } mc_field_desc;
 
 /* k(t, s) table of Sec. 3.1 (Eq. 2, Table 1): k[is * nt + it] on strictly

@@ -55,7 +55,7 @@ class _Problem(C.Structure):
         ("gantry_deg", C.c_double), ("sad", C.c_double), ("sid", C.c_double), ("iso", C.c_double * 3),
         ("coupled", C.c_int), ("e_max", C.c_double), ("mono_e", C.c_double), ("pcut", C.c_double),
         ("ecut", C.c_double), ("wcc", C.c_double), ("wcb", C.c_double), ("step_frac", C.c_double),
-        ("n_batches", C.c_int), ("max_steps", C.c_int),
+        ("n_batches", C.c_int), ("max_steps", C.c_int), ("leaf_trans", C.c_double),
     ]
 
 
@@ -147,6 +147,7 @@ class _Marshalled:
         s.e_max, s.mono_e = phy.e_max, phy.mono_energy
         s.pcut, s.ecut, s.wcc, s.wcb = phy.photon_cutoff, phy.electron_cutoff, phy.wcc, phy.wcb
         s.step_frac, s.n_batches, s.max_steps = phy.step_fraction, phy.n_batches, phy.max_steps
+        s.leaf_trans = float(getattr(fld, "leaf_transmission", 0.0))
         self.s = s
 
 

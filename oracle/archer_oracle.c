@@ -349,6 +349,7 @@ typedef struct {
     int n_seg, n_pairs; const double* pair_edges; const double* leaves; const double* jaws; const double* mu;
     double gantry_deg, sad, sid; double iso[3];
     int coupled; double e_max, mono_e, pcut, ecut, wcc, wcb, step_frac; int n_batches; int max_steps;
+    double leaf_trans;           /* fluence fraction through closed leaves inside the jaws (0: ideal MLC) */
 } orc_problem;
 
 enum { C_FLIGHTS_CT, C_REAL_CT, C_COMPTON, C_PHOTO, C_PAIR, C_ESTEP_CT, C_ESTEP_EPID, C_MOLLER, C_BREM,
@@ -906,30 +907,49 @@ static void electron(o_ctx* c, o_part* p) {
 /* aperture): rectangle chosen with weight MU_k x area, point uniform in it  */
 /* at the isocentre plane, direction from the point source.                  */
 /* ------------------------------------------------------------------------ */
+/* Source rectangles at the isocentre plane: per segment and leaf pair (in
+ * that order), within the jaws, the part of the pair left of the opening,
+ * the opening, the part right of it (a closed pair is one part).  Openings
+ * weigh MU x area; closed parts MU x T x area with T the leaf transmission
+ * (absent when T = 0).  Returns whether any opening exists. */
+static void add_rect(o_ctx* c, int* n, double* acc, double x0, double x1, double y0, double y1, double w) {
+    if (!(x1 > x0) || !(w > 0.0)) return;
+    *acc += w * (x1 - x0) * (y1 - y0);
+    c->rect[4 * *n] = x0; c->rect[4 * *n + 1] = x1; c->rect[4 * *n + 2] = y0; c->rect[4 * *n + 3] = y1;
+    c->cdf[*n] = *acc;
+    (*n)++;
+}
+
 static int build_source(o_ctx* c) {
     const orc_problem* P = c->P;
-    int nmax = P->n_seg * P->n_pairs;
+    int nmax = 3 * P->n_seg * P->n_pairs;
     c->rect = (double*)malloc(sizeof(double) * 4 * (size_t)(nmax > 0 ? nmax : 1));
     c->cdf = (double*)malloc(sizeof(double) * (size_t)(nmax > 0 ? nmax : 1));
     double acc = 0.0;
-    int n = 0;
+    int n = 0, open = 0;
+    const double T = P->leaf_trans;
     for (int k = 0; k < P->n_seg; k++) {
         const double* jw = P->jaws + 4 * k;
+        const double mu = P->mu[k];
+        if (!(mu > 0.0)) continue;
         for (int j = 0; j < P->n_pairs; j++) {
             const double* lf = P->leaves + 2 * ((size_t)k * P->n_pairs + j);
-            double x0 = fmax(lf[0], jw[0]), x1 = fmin(lf[1], jw[1]);
-            double y0 = fmax(P->pair_edges[j], jw[2]), y1 = fmin(P->pair_edges[j + 1], jw[3]);
-            if (x1 > x0 && y1 > y0 && P->mu[k] > 0.0) {
-                acc += P->mu[k] * (x1 - x0) * (y1 - y0);
-                c->rect[4 * n] = x0; c->rect[4 * n + 1] = x1; c->rect[4 * n + 2] = y0; c->rect[4 * n + 3] = y1;
-                c->cdf[n] = acc;
-                n++;
+            const double y0 = fmax(P->pair_edges[j], jw[2]), y1 = fmin(P->pair_edges[j + 1], jw[3]);
+            if (!(y1 > y0)) continue;
+            const double a = fmax(lf[0], jw[0]), b = fmin(lf[1], jw[1]);
+            if (b > a) {
+                add_rect(c, &n, &acc, jw[0], a, y0, y1, T * mu);
+                add_rect(c, &n, &acc, a, b, y0, y1, mu);
+                add_rect(c, &n, &acc, b, jw[1], y0, y1, T * mu);
+                open = 1;
+            } else {
+                add_rect(c, &n, &acc, jw[0], jw[1], y0, y1, T * mu);
             }
         }
     }
     c->n_rect = n;
     for (int i = 0; i < n; i++) c->cdf[i] /= acc;
-    return n > 0;
+    return open;
 }
 
 /* Draws of a primary: rectangle (1), X (1), Y (1), then the spectrum. */

@@ -52,7 +52,8 @@ class FieldDesc(C.Structure):
     _fields_ = [("n_segments", C.c_int), ("n_pairs", C.c_int), ("pair_edges_cm", C.POINTER(C.c_double)),
                 ("leaves_cm", C.POINTER(C.c_double)), ("jaws_cm", C.POINTER(C.c_double)),
                 ("mu", C.POINTER(C.c_double)), ("gantry_deg", C.c_double), ("sad_cm", C.c_double),
-                ("sid_cm", C.c_double), ("iso_cm", C.c_double * 3), ("eq1_literal", C.c_int)]
+                ("sid_cm", C.c_double), ("iso_cm", C.c_double * 3), ("eq1_literal", C.c_int),
+                ("leaf_transmission", C.c_double)]
 
 
 class LutDesc(C.Structure):
@@ -245,6 +246,7 @@ class Simulator:
         f.gantry_deg, f.sad_cm, f.sid_cm = field.gantry_deg, field.sad, field.sid
         f.iso_cm[:] = [float(v) for v in field.iso]
         f.eq1_literal = int(lut.eq1_literal) if lut is not None else 0
+        f.leaf_transmission = float(getattr(field, "leaf_transmission", 0.0))
         return f
 
     @staticmethod

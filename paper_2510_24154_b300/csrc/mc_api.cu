@@ -248,26 +248,42 @@ mc_status build_field(mc_ctx* c, const mc_field_desc* f, int index, std::vector<
         return fail(c, MC_ERR_ARG, "bad segment / pair count" + which);
     if (!(f->sad_cm > 0) || !(f->sid_cm > f->sad_cm)) return fail(c, MC_ERR_ARG, "need 0 < SAD < SID" + which);
     if (!increasing(f->pair_edges_cm, f->n_pairs + 1)) return fail(c, MC_ERR_ARG, "pair edges must increase" + which);
+    const double T = f->leaf_transmission;
+    if (!(T >= 0.0 && T < 1.0)) return fail(c, MC_ERR_ARG, "leaf transmission must be in [0, 1)" + which);
     const size_t off = rect.size();
     double acc = 0.0, X0 = INFINITY, X1 = -INFINITY, Y0 = INFINITY, Y1 = -INFINITY;
+    bool open = false;
+    // per segment and pair, left to right inside the jaws: the closed part
+    // before the opening (weight T MU), the opening (MU), the closed part after
+    auto add = [&](double x0, double x1, double y0, double y1, double w) {
+        if (!(x1 > x0) || !(w > 0.0)) return;
+        acc += w * (x1 - x0) * (y1 - y0);
+        rect.push_back(make_float4(static_cast<float>(x0), static_cast<float>(x1), static_cast<float>(y0),
+                                   static_cast<float>(y1)));
+        cdf.push_back(acc);
+    };
     for (int k = 0; k < f->n_segments; ++k) {
         const double* jw = f->jaws_cm + 4 * k;
         const double mu = f->mu[k];
         if (!(mu >= 0.0)) return fail(c, MC_ERR_ARG, "MU weights must be >= 0" + which);
+        if (!(mu > 0.0)) continue;
         for (int j = 0; j < f->n_pairs; ++j) {
             const double* lf = f->leaves_cm + 2 * (static_cast<size_t>(k) * f->n_pairs + j);
-            const double x0 = std::fmax(lf[0], jw[0]), x1 = std::fmin(lf[1], jw[1]);
             const double y0 = std::fmax(f->pair_edges_cm[j], jw[2]), y1 = std::fmin(f->pair_edges_cm[j + 1], jw[3]);
-            if (x1 > x0 && y1 > y0 && mu > 0.0) {
-                acc += mu * (x1 - x0) * (y1 - y0);
-                rect.push_back(make_float4(static_cast<float>(x0), static_cast<float>(x1), static_cast<float>(y0),
-                                           static_cast<float>(y1)));
-                cdf.push_back(acc);
+            if (!(y1 > y0)) continue;
+            const double x0 = std::fmax(lf[0], jw[0]), x1 = std::fmin(lf[1], jw[1]);
+            if (x1 > x0) {
+                add(jw[0], x0, y0, y1, T * mu);
+                add(x0, x1, y0, y1, mu);
+                add(x1, jw[1], y0, y1, T * mu);
+                open = true;
                 X0 = std::fmin(X0, x0); X1 = std::fmax(X1, x1); Y0 = std::fmin(Y0, y0); Y1 = std::fmax(Y1, y1);
+            } else {
+                add(jw[0], jw[1], y0, y1, T * mu);
             }
         }
     }
-    if (rect.size() == off) return fail(c, MC_ERR_ARG, "field has no open aperture" + which);
+    if (!open) return fail(c, MC_ERR_ARG, "field has no open aperture" + which);
     for (size_t i = off; i < cdf.size(); ++i) cdf[i] /= acc;
     out.rect_off = static_cast<int>(off);
     out.n_rect = static_cast<int>(rect.size() - off);

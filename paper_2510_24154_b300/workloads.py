@@ -64,6 +64,8 @@ class Field:
     leaves:     [n_seg][n_pairs][2] (left, right) leaf tips along X.
     jaws:       [n_seg][4] (x1, x2, y1, y2).
     mu:         [n_seg] monitor-unit weights.
+    leaf_transmission: fraction of the open fluence that passes closed
+                leaves inside the jaw opening (0 = ideal MLC).
     """
     pair_edges: np.ndarray
     leaves: np.ndarray
@@ -73,6 +75,7 @@ class Field:
     sad: float = 100.0
     sid: float = 150.0
     iso: tuple = (0.0, 0.0, 0.0)
+    leaf_transmission: float = 0.0
 
 
 @dataclass

@@ -219,3 +219,18 @@ def test_input_errors_are_reported():
     closed.sid = 60.0                         # detector inside the CT
     with pytest.raises(MCError):
         sim.set_field(closed)
+
+
+def test_replay_with_leaf_transmission():
+    """Leaf transmission (1.5 %) in both source models: the primaries behind
+    closed leaves replay like the others."""
+    p = G.thorax_case(n=200_000, scale=4, epid_scale=8)
+    p.field.leaf_transmission = 0.015
+    sim, st, orc, gt, ot, (e_g, e_o), (gd, gs, od, os_) = _compare_replay(p, p.n_histories)
+    assert abs(e_g / e_o - 1) < 2e-3
+    assert G.gamma_rate(od, gd, p.epid.pitch) >= 0.995
+    frac, _ = G.three_sigma_fraction(gd, gs, od, os_)
+    assert frac >= 0.99
+    q = G.thorax_case(n=200_000, scale=4, epid_scale=8)
+    _, _, g0 = G.gpu_run(q)
+    assert gt.sum() > g0.sum()                     # transmission adds signal behind the leaves

@@ -634,3 +634,36 @@ def test_plan_image_is_the_weighted_sum():
     assert len(fields) == 5 and np.isclose(mu.sum(), 1.0)
     g = [f.gantry_deg for f in fields]
     assert g[0] == pytest.approx(181.0) and g[-1] == pytest.approx((181.0 + 358.0) % 360.0)
+
+
+def test_leaf_transmission_source_density():
+    """With leaf transmission T, the source density inside the jaws is T times
+    the open density behind closed leaves: the fraction of primaries outside
+    the opening is T A_closed / (A_open + T A_closed); T = 0 is the ideal MLC."""
+    edges = np.linspace(-5.0, 5.0, 11)                 # 10 pairs of 1 cm
+    leaves = np.zeros((1, 10, 2))
+    leaves[0, :, 0], leaves[0, :, 1] = -2.0, 2.0        # every pair open over 4 cm
+    leaves[0, 0] = (1.0, 1.0)                          # one pair closed
+    jaws = np.array([[-5.0, 5.0, -5.0, 5.0]])
+    for T in (0.0, 0.015, 0.2):
+        fld = W.Field(edges, leaves, jaws, np.ones(1), leaf_transmission=T)
+        prob = W.config_water_open(n_histories=1)
+        prob.field = fld
+        n = 400_000
+        X, Y, _ = oracle.sample_source(prob, n, seed=3)
+        assert np.all(np.abs(X) <= 5.0) and np.all(np.abs(Y) <= 5.0)
+        in_open = (np.abs(X) < 2.0) & (Y > -4.0)
+        a_open = 4.0 * 9.0
+        a_closed = 100.0 - a_open
+        want = T * a_closed / (a_open + T * a_closed)
+        got = 1.0 - in_open.mean()
+        sd = np.sqrt(max(want * (1 - want), 1e-12) / n)
+        assert abs(got - want) <= 4 * sd + 1e-12, (T, got, want)
+        if T > 0:
+            # closed-pair density equals the other closed regions' density
+            dens_closed_pair = np.mean(Y < -4.0) / 10.0
+            dens_closed_rest = np.mean((~in_open) & (Y >= -4.0)) / (a_closed - 10.0)
+            assert dens_closed_pair == pytest.approx(dens_closed_rest, rel=0.1)
+    # Eq. 1 sees the openings only
+    a, b = oracle.aperture_bbox(W.Field(edges, leaves, jaws, np.ones(1), leaf_transmission=0.2))
+    assert (a, b) == (4.0, 9.0)
