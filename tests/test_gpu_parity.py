@@ -233,4 +233,9 @@ def test_replay_with_leaf_transmission():
     assert frac >= 0.99
     q = G.thorax_case(n=200_000, scale=4, epid_scale=8)
     _, _, g0 = G.gpu_run(q)
-    assert gt.sum() > g0.sum()                     # transmission adds signal behind the leaves
+    # behind the leaves (pixels below 2 % of the open-field maximum without
+    # transmission) the signal grows; histories are redistributed, so the
+    # total need not
+    img0, img1 = g0.sum(axis=0), gt.sum(axis=0)
+    low = img0 < 0.02 * img0.max()
+    assert low.sum() > 100 and img1[low].sum() > 1.5 * img0[low].sum()
