@@ -1,0 +1,49 @@
+"""GPU S(t, s) sweep: the trends of beam attenuation and phantom scatter, and
+parity of one calibration point with the FP64 oracle (same histories)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_24154_b300 import calibration as CAL
+from paper_2510_24154_b300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+def test_s_table_trends():
+    ep = W.epid_default(256, 192, 0.156)
+    S, U = CAL.s_table(4_000_000, epid=ep)
+    assert S.shape == (4, 5) and (S > 0).all() and (U > 0).all()
+    assert (U / S < 0.02).all()
+    # attenuation: S falls with thickness for every field size
+    assert (np.diff(S, axis=1) < 0).all()
+    # phantom scatter: behind 10-20 cm, larger fields give more central signal
+    assert (np.diff(S[:, 2:], axis=0) > -3 * np.hypot(U[1:, 2:], U[:-1, 2:])).all()
+    assert S[3, 4] > S[0, 4]
+    # effective attenuation of a 6 MV beam through 20 cm of water (small field)
+    mu_eff = -np.log(S[0, 4] / S[0, 0]) / 20.0
+    assert 0.03 < mu_eff < 0.06
+
+
+def test_calibration_point_matches_oracle():
+    ep = W.epid_default(128, 96, 0.312)
+    t, s, n = 10.0, 10.0, 400_000
+    mask = CAL.central_region(ep)
+    S, U = CAL.s_table(n, t_nodes=(t,), s_nodes=(s,), epid=ep, seed=21)
+    prob = W.Problem(name="calib", phantom=CAL.slab_phantom(t), epid=ep, field=W.open_field(s, s),
+                     lut=W.lut_table1(), physics=W.Physics(coupled=True), n_histories=n, seed=21)
+    orc = oracle.run(prob)
+    od, osd, _ = oracle.dose_stats(orc["tally"], n, ep)
+    o_mean = od[mask].mean()
+    # the oracle's region error from its own batches
+    B = orc["tally"].shape[0]
+    nb = oracle.batch_counts(n, B).astype(float)
+    _, thick, rho = ep.layers[ep.sensitive]
+    conv = 1.602176634e-13 / (rho * ep.pitch ** 2 * thick * 1e-3)
+    per = orc["tally"][:, mask].mean(axis=1) * conv / nb
+    o_sd = per.std(ddof=1) / np.sqrt(B)
+    assert abs(S[0, 0] - o_mean) <= 3.0 * np.hypot(U[0, 0], o_sd)
+    assert S[0, 0] == pytest.approx(o_mean, rel=0.01)         # same histories: replay
