@@ -10,7 +10,12 @@ on the isocentre with the beam along its thickness (gantry 0); t = 0 is an
 empty (air) geometry -- the paper's t = 0 includes the treatment couch, which
 is not modelled; the field is an open s x s square at the isocentre; the
 region is the pixels whose centres lie within 0.5 cm of the image centre.
-The uncertainty of each S is the batch standard error of the region mean.
+S is expressed per unit primary fluence at the isocentre plane (the
+per-history dose times the field area s^2, in Gy cm^2), as a fixed number of
+monitor units delivers a fixed fluence whatever the field size; each point
+runs histories_per_cm2 x s^2 histories, so all points carry similar
+statistics.  The uncertainty of each S is the batch standard error of the
+region mean.
 """
 from __future__ import annotations
 
@@ -54,10 +59,11 @@ def region_signal(tally_mev: np.ndarray, n_hist: int, epid: W.Epid, mask: np.nda
     return float(mean), float(sigma)
 
 
-def s_table(n_histories: int = 100_000_000, t_nodes=T_NODES, s_nodes=S_NODES, epid: W.Epid | None = None,
+def s_table(histories_per_cm2: float = 1e6, t_nodes=T_NODES, s_nodes=S_NODES, epid: W.Epid | None = None,
             seed: int = 11, device: int = 0, physics: W.Physics | None = None):
-    """S(t, s) and its uncertainty, arrays [len(s_nodes)][len(t_nodes)] in Gy
-    per history (the layout of Table 1: rows field sizes, columns thicknesses)."""
+    """S(t, s) and its uncertainty, arrays [len(s_nodes)][len(t_nodes)] in
+    Gy cm^2 per history (the layout of Table 1: rows field sizes, columns
+    thicknesses)."""
     from .binding import Simulator
     epid = epid or W.epid_default(1024, 768, 0.039)
     physics = physics or W.Physics(coupled=True)
@@ -69,10 +75,16 @@ def s_table(n_histories: int = 100_000_000, t_nodes=T_NODES, s_nodes=S_NODES, ep
         for j, t in enumerate(t_nodes):
             sim.init_geometry(slab_phantom(t), epid)
             for i, s in enumerate(s_nodes):
+                n = int(round(histories_per_cm2 * s * s))
                 sim.set_field(W.open_field(s, s))
-                sim.run(n_histories, seed + 1000 * j + i)
+                done = 0
+                while done < n:
+                    k = min(n - done, 1 << 31)
+                    sim.run(k, seed + 1000 * j + i)
+                    done += k
                 tally = sim.tally().astype(np.float64) / 2.56e8
-                S[i, j], U[i, j] = region_signal(tally, n_histories, epid, mask)
+                m, u = region_signal(tally, n, epid, mask)
+                S[i, j], U[i, j] = m * s * s, u * s * s
     finally:
         sim.close()
     return S, U

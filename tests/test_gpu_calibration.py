@@ -15,9 +15,9 @@ if not torch.cuda.is_available():
 
 def test_s_table_trends():
     ep = W.epid_default(256, 192, 0.156)
-    S, U = CAL.s_table(4_000_000, epid=ep)
+    S, U = CAL.s_table(1e6, epid=ep)
     assert S.shape == (4, 5) and (S > 0).all() and (U > 0).all()
-    assert (U / S < 0.02).all()
+    assert (U / S < 0.035).all()          # about 1.5-2.5 %; the batch estimate itself varies ~20 %
     # attenuation: S falls with thickness for every field size
     assert (np.diff(S, axis=1) < 0).all()
     # phantom scatter: behind 10-20 cm, larger fields give more central signal
@@ -32,7 +32,8 @@ def test_calibration_point_matches_oracle():
     ep = W.epid_default(128, 96, 0.312)
     t, s, n = 10.0, 10.0, 400_000
     mask = CAL.central_region(ep)
-    S, U = CAL.s_table(n, t_nodes=(t,), s_nodes=(s,), epid=ep, seed=21)
+    S, U = CAL.s_table(n / (s * s), t_nodes=(t,), s_nodes=(s,), epid=ep, seed=21)
+    S, U = S / (s * s), U / (s * s)                 # back to per history
     prob = W.Problem(name="calib", phantom=CAL.slab_phantom(t), epid=ep, field=W.open_field(s, s),
                      lut=W.lut_table1(), physics=W.Physics(coupled=True), n_histories=n, seed=21)
     orc = oracle.run(prob)
