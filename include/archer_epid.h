@@ -123,8 +123,19 @@ typedef struct mc_field_desc {
     double sad_cm, sid_cm;
     double iso_cm[3];             /* isocentre in CT coordinates */
     int eq1_literal;              /* 0: s = 2ab/(a+b); 1: s = ab/(2(a+b)) exactly as Eq. 1 is printed */
-    double leaf_transmission;     /* fraction of the open fluence passing closed leaves inside the jaws,
-                                     0 <= T < 1 (0: ideal MLC; the jaws stay opaque) */
+    /* Collimation (Sec. 2.1.1 transports the beam through jaws and MLC; this
+     * library models them as fluence filters on the isocentre plane, inside
+     * the largest field |X|, |Y| <= 20 cm and the MLC's extent).  Per MU the
+     * fluence is (leaf factor) x (jaw factor): 1 inside the effective opening
+     * of the point's leaf pair, else leaf_transmission; 1 inside the segment's
+     * jaws, else jaw_transmission.  All zero: the ideal aperture. */
+    double leaf_transmission;     /* 0 <= T < 1 */
+    double jaw_transmission;      /* 0 <= Tj < 1 */
+    double tg_width_cm;           /* tongue and groove: within half this width of a pair boundary the
+                                     opening is the intersection of both pairs' openings;
+                                     0 <= w < narrowest pair */
+    double leaf_gap_cm;           /* dosimetric leaf gap: an open pair's tips move apart by g/2 each
+                                     (rounded leaf ends); a pair whose tips meet stays closed; 0 <= g < 2 */
 } mc_field_desc;
 
 /* k(t, s) table of Sec. 3.1 (Eq. 2, Table 1): k[is * nt + it] on strictly

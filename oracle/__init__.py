@@ -56,6 +56,7 @@ class _Problem(C.Structure):
         ("coupled", C.c_int), ("e_max", C.c_double), ("mono_e", C.c_double), ("pcut", C.c_double),
         ("ecut", C.c_double), ("wcc", C.c_double), ("wcb", C.c_double), ("step_frac", C.c_double),
         ("n_batches", C.c_int), ("max_steps", C.c_int), ("leaf_trans", C.c_double),
+        ("jaw_trans", C.c_double), ("tg_width", C.c_double), ("leaf_gap", C.c_double),
     ]
 
 
@@ -148,6 +149,14 @@ class _Marshalled:
         s.pcut, s.ecut, s.wcc, s.wcb = phy.photon_cutoff, phy.electron_cutoff, phy.wcc, phy.wcb
         s.step_frac, s.n_batches, s.max_steps = phy.step_fraction, phy.n_batches, phy.max_steps
         s.leaf_trans = float(getattr(fld, "leaf_transmission", 0.0))
+        s.jaw_trans = float(getattr(fld, "jaw_transmission", 0.0))
+        s.tg_width = float(getattr(fld, "tg_width", 0.0))
+        s.leaf_gap = float(getattr(fld, "leaf_gap", 0.0))
+        edges = np.asarray(fld.pair_edges, dtype=np.float64)
+        if not (0.0 <= s.leaf_trans < 1.0 and 0.0 <= s.jaw_trans < 1.0):
+            raise ValueError("transmissions must lie in [0, 1)")
+        if not (0.0 <= s.tg_width < np.diff(edges).min()) or not (0.0 <= s.leaf_gap < 2.0):
+            raise ValueError("need 0 <= tongue-and-groove width < narrowest pair and 0 <= leaf gap < 2 cm")
         self.s = s
 
 

@@ -349,7 +349,10 @@ typedef struct {
     int n_seg, n_pairs; const double* pair_edges; const double* leaves; const double* jaws; const double* mu;
     double gantry_deg, sad, sid; double iso[3];
     int coupled; double e_max, mono_e, pcut, ecut, wcc, wcb, step_frac; int n_batches; int max_steps;
-    double leaf_trans;           /* fluence fraction through closed leaves inside the jaws (0: ideal MLC) */
+    double leaf_trans;           /* fluence fraction through closed leaves (0: ideal MLC) */
+    double jaw_trans;            /* fluence fraction through the jaws (0: opaque) */
+    double tg_width;             /* tongue-and-groove strip width at the isocentre plane, cm */
+    double leaf_gap;             /* dosimetric leaf gap of an open pair, cm */
 } orc_problem;
 
 enum { C_FLIGHTS_CT, C_REAL_CT, C_COMPTON, C_PHOTO, C_PAIR, C_ESTEP_CT, C_ESTEP_EPID, C_MOLLER, C_BREM,
@@ -913,41 +916,113 @@ static void electron(o_ctx* c, o_part* p) {
  * weigh MU x area; closed parts MU x T x area with T the leaf transmission
  * (absent when T = 0).  Returns whether any opening exists. */
 static void add_rect(o_ctx* c, int* n, double* acc, double x0, double x1, double y0, double y1, double w) {
-    if (!(x1 > x0) || !(w > 0.0)) return;
+    if (!(x1 > x0) || !(y1 > y0) || !(w > 0.0)) return;
     *acc += w * (x1 - x0) * (y1 - y0);
     c->rect[4 * *n] = x0; c->rect[4 * *n + 1] = x1; c->rect[4 * *n + 2] = y0; c->rect[4 * *n + 3] = y1;
     c->cdf[*n] = *acc;
     (*n)++;
 }
 
+/* Half-width of the largest field at the isocentre plane (40 x 40 cm). */
+#define O_FIELD_HALF 20.0
+
+/* Effective opening [lo, hi] of pair j in segment k: the leaf tips moved
+ * apart by half the leaf gap each, for a pair whose leaves are apart; a pair
+ * whose tips meet or cross is closed (returns 0). */
+static int pair_opening(const orc_problem* P, int k, int j, double* lo, double* hi) {
+    const double* lf = P->leaves + 2 * ((size_t)k * P->n_pairs + j);
+    if (!(lf[1] > lf[0])) return 0;
+    *lo = lf[0] - 0.5 * P->leaf_gap;
+    *hi = lf[1] + 0.5 * P->leaf_gap;
+    return 1;
+}
+
+static int cmp_double(const void* a, const void* b) {
+    const double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/* Sorted distinct values of v[0..n) that lie strictly inside (lo, hi),
+ * framed by lo and hi; returns the count. */
+static int breakpoints(double lo, double hi, const double* v, int n, double* out) {
+    int m = 0;
+    out[m++] = lo;
+    for (int i = 0; i < n; i++)
+        if (v[i] > lo && v[i] < hi) out[m++] = v[i];
+    out[m++] = hi;
+    qsort(out + 1, (size_t)(m - 2), sizeof(double), cmp_double);
+    int u = 1;
+    for (int i = 1; i < m; i++)
+        if (out[i] != out[u - 1]) out[u++] = out[i];
+    return u;
+}
+
+/* Source of Sec. 2.1.1 with the collimators as fluence filters (the paper
+ * transports the beam through jaws and MLC; no head model is available, so
+ * this is the stated reading).  Per MU, the fluence at a point (X, Y) of the
+ * isocentre plane inside the largest field and the MLC's extent is
+ *   (leaf factor) x (jaw factor),
+ * leaf factor = 1 inside the effective opening of the point's pair, else the
+ * leaf transmission; within half the tongue-and-groove width of the boundary
+ * between two pairs the opening is the intersection of both pairs' openings;
+ * jaw factor = 1 inside the segment's jaws, else the jaw transmission.  Each
+ * segment, pair, band of Y and interval of X on which both factors are
+ * constant is one rectangle, weighted by MU x factors x area, in that order
+ * (segments, pairs, increasing Y, increasing X). */
 static int build_source(o_ctx* c) {
     const orc_problem* P = c->P;
-    int nmax = 3 * P->n_seg * P->n_pairs;
+    const double C = O_FIELD_HALF, w = P->tg_width;
+    int nmax = 25 * P->n_seg * P->n_pairs;
     c->rect = (double*)malloc(sizeof(double) * 4 * (size_t)(nmax > 0 ? nmax : 1));
     c->cdf = (double*)malloc(sizeof(double) * (size_t)(nmax > 0 ? nmax : 1));
     double acc = 0.0;
     int n = 0, open = 0;
-    const double T = P->leaf_trans;
     for (int k = 0; k < P->n_seg; k++) {
         const double* jw = P->jaws + 4 * k;
         const double mu = P->mu[k];
         if (!(mu > 0.0)) continue;
+        const double jx0 = fmax(jw[0], -C), jx1 = fmin(jw[1], C);
+        const double jy0 = fmax(jw[2], -C), jy1 = fmin(jw[3], C);
         for (int j = 0; j < P->n_pairs; j++) {
+            const double e0 = P->pair_edges[j], e1 = P->pair_edges[j + 1];
             const double* lf = P->leaves + 2 * ((size_t)k * P->n_pairs + j);
-            const double y0 = fmax(P->pair_edges[j], jw[2]), y1 = fmin(P->pair_edges[j + 1], jw[3]);
-            if (!(y1 > y0)) continue;
-            const double a = fmax(lf[0], jw[0]), b = fmin(lf[1], jw[1]);
-            if (b > a) {
-                add_rect(c, &n, &acc, jw[0], a, y0, y1, T * mu);
-                add_rect(c, &n, &acc, a, b, y0, y1, mu);
-                add_rect(c, &n, &acc, b, jw[1], y0, y1, T * mu);
-                open = 1;
-            } else {
-                add_rect(c, &n, &acc, jw[0], jw[1], y0, y1, T * mu);
+            /* the physical aperture, for the field size of Eq. 1 */
+            if (fmin(lf[1], jw[1]) > fmax(lf[0], jw[0]) && fmin(e1, jw[3]) > fmax(e0, jw[2])) open = 1;
+            const double ya = fmax(e0, -C), yb = fmin(e1, C);
+            if (!(yb > ya)) continue;
+            double ycut[4] = {jy0, jy1, e0 + 0.5 * w, e1 - 0.5 * w}, yb_[6];
+            const int ny = breakpoints(ya, yb, ycut, (w > 0.0) ? 4 : 2, yb_);
+            for (int b = 0; b + 1 < ny; b++) {
+                const double y0 = yb_[b], y1 = yb_[b + 1], ym = 0.5 * (y0 + y1);
+                double lo = 0.0, hi = 0.0;
+                int has = pair_opening(P, k, j, &lo, &hi);
+                int nb = -1;                      /* the neighbour sharing a tongue-and-groove strip */
+                if (w > 0.0 && j > 0 && ym < e0 + 0.5 * w) nb = j - 1;
+                if (w > 0.0 && j + 1 < P->n_pairs && ym > e1 - 0.5 * w) nb = j + 1;
+                if (has && nb >= 0) {
+                    double lo2, hi2;
+                    if (pair_opening(P, k, nb, &lo2, &hi2)) {
+                        lo = fmax(lo, lo2);
+                        hi = fmin(hi, hi2);
+                        has = hi > lo;
+                    } else {
+                        has = 0;
+                    }
+                }
+                const int in_jaw_y = ym >= jy0 && ym <= jy1;
+                double xcut[4] = {jx0, jx1, lo, hi}, xb[6];
+                const int nx = breakpoints(-C, C, xcut, has ? 4 : 2, xb);
+                for (int a = 0; a + 1 < nx; a++) {
+                    const double x0 = xb[a], x1 = xb[a + 1], xm = 0.5 * (x0 + x1);
+                    const double leaf = (has && xm >= lo && xm <= hi) ? 1.0 : P->leaf_trans;
+                    const double jaw = (in_jaw_y && xm >= jx0 && xm <= jx1) ? 1.0 : P->jaw_trans;
+                    add_rect(c, &n, &acc, x0, x1, y0, y1, mu * leaf * jaw);
+                }
             }
         }
     }
     c->n_rect = n;
+    if (!(acc > 0.0)) return 0;
     for (int i = 0; i < n; i++) c->cdf[i] /= acc;
     return open;
 }

@@ -53,7 +53,8 @@ class FieldDesc(C.Structure):
                 ("leaves_cm", C.POINTER(C.c_double)), ("jaws_cm", C.POINTER(C.c_double)),
                 ("mu", C.POINTER(C.c_double)), ("gantry_deg", C.c_double), ("sad_cm", C.c_double),
                 ("sid_cm", C.c_double), ("iso_cm", C.c_double * 3), ("eq1_literal", C.c_int),
-                ("leaf_transmission", C.c_double)]
+                ("leaf_transmission", C.c_double), ("jaw_transmission", C.c_double),
+                ("tg_width_cm", C.c_double), ("leaf_gap_cm", C.c_double)]
 
 
 class LutDesc(C.Structure):
@@ -247,6 +248,9 @@ class Simulator:
         f.iso_cm[:] = [float(v) for v in field.iso]
         f.eq1_literal = int(lut.eq1_literal) if lut is not None else 0
         f.leaf_transmission = float(getattr(field, "leaf_transmission", 0.0))
+        f.jaw_transmission = float(getattr(field, "jaw_transmission", 0.0))
+        f.tg_width_cm = float(getattr(field, "tg_width", 0.0))
+        f.leaf_gap_cm = float(getattr(field, "leaf_gap", 0.0))
         return f
 
     @staticmethod

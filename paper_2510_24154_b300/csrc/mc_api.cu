@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <utility>
 #include <vector>
@@ -248,41 +249,96 @@ mc_status build_field(mc_ctx* c, const mc_field_desc* f, int index, std::vector<
         return fail(c, MC_ERR_ARG, "bad segment / pair count" + which);
     if (!(f->sad_cm > 0) || !(f->sid_cm > f->sad_cm)) return fail(c, MC_ERR_ARG, "need 0 < SAD < SID" + which);
     if (!increasing(f->pair_edges_cm, f->n_pairs + 1)) return fail(c, MC_ERR_ARG, "pair edges must increase" + which);
-    const double T = f->leaf_transmission;
-    if (!(T >= 0.0 && T < 1.0)) return fail(c, MC_ERR_ARG, "leaf transmission must be in [0, 1)" + which);
+    const double T = f->leaf_transmission, Tj = f->jaw_transmission;
+    const double w = f->tg_width_cm, gap = f->leaf_gap_cm;
+    if (!(T >= 0.0 && T < 1.0) || !(Tj >= 0.0 && Tj < 1.0))
+        return fail(c, MC_ERR_ARG, "leaf and jaw transmission must be in [0, 1)" + which);
+    double narrowest = INFINITY;
+    for (int j = 0; j < f->n_pairs; ++j)
+        narrowest = std::fmin(narrowest, f->pair_edges_cm[j + 1] - f->pair_edges_cm[j]);
+    if (!(w >= 0.0 && w < narrowest)) return fail(c, MC_ERR_ARG, "tongue-and-groove width must be in [0, narrowest pair)" + which);
+    if (!(gap >= 0.0 && gap < 2.0)) return fail(c, MC_ERR_ARG, "leaf gap must be in [0, 2) cm" + which);
     const size_t off = rect.size();
     double acc = 0.0, X0 = INFINITY, X1 = -INFINITY, Y0 = INFINITY, Y1 = -INFINITY;
     bool open = false;
-    // per segment and pair, left to right inside the jaws: the closed part
-    // before the opening (weight T MU), the opening (MU), the closed part after
-    auto add = [&](double x0, double x1, double y0, double y1, double w) {
-        if (!(x1 > x0) || !(w > 0.0)) return;
-        acc += w * (x1 - x0) * (y1 - y0);
+    auto add = [&](double x0, double x1, double y0, double y1, double wt) {
+        if (!(x1 > x0) || !(y1 > y0) || !(wt > 0.0)) return;
+        acc += wt * (x1 - x0) * (y1 - y0);
         rect.push_back(make_float4(static_cast<float>(x0), static_cast<float>(x1), static_cast<float>(y0),
                                    static_cast<float>(y1)));
         cdf.push_back(acc);
     };
+    // [lo, hi] framed and split at the cuts strictly inside it, ascending, distinct
+    auto split = [](double lo, double hi, std::initializer_list<double> cuts) {
+        std::vector<double> v{lo};
+        for (double x : cuts)
+            if (x > lo && x < hi) v.push_back(x);
+        std::sort(v.begin() + 1, v.end());
+        v.push_back(hi);
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        return v;
+    };
+    constexpr double kHalf = 20.0;            // the largest field, 40 x 40 cm at the isocentre
+    // Every (segment, pair, Y band, X interval) on which the leaf and jaw
+    // factors are constant is one source rectangle of weight MU x factors,
+    // in that order; the same order as the oracle, so replay keys match.
     for (int k = 0; k < f->n_segments; ++k) {
         const double* jw = f->jaws_cm + 4 * k;
         const double mu = f->mu[k];
         if (!(mu >= 0.0)) return fail(c, MC_ERR_ARG, "MU weights must be >= 0" + which);
         if (!(mu > 0.0)) continue;
+        const double jx0 = std::fmax(jw[0], -kHalf), jx1 = std::fmin(jw[1], kHalf);
+        const double jy0 = std::fmax(jw[2], -kHalf), jy1 = std::fmin(jw[3], kHalf);
+        const double* lv = f->leaves_cm + 2 * static_cast<size_t>(k) * f->n_pairs;
+        // effective opening of pair j: tips apart by the leaf gap, if open at all
+        auto opening = [&](int j, double& lo, double& hi) {
+            if (!(lv[2 * j + 1] > lv[2 * j])) return false;
+            lo = lv[2 * j] - 0.5 * gap;
+            hi = lv[2 * j + 1] + 0.5 * gap;
+            return true;
+        };
         for (int j = 0; j < f->n_pairs; ++j) {
-            const double* lf = f->leaves_cm + 2 * (static_cast<size_t>(k) * f->n_pairs + j);
-            const double y0 = std::fmax(f->pair_edges_cm[j], jw[2]), y1 = std::fmin(f->pair_edges_cm[j + 1], jw[3]);
-            if (!(y1 > y0)) continue;
-            const double x0 = std::fmax(lf[0], jw[0]), x1 = std::fmin(lf[1], jw[1]);
-            if (x1 > x0) {
-                add(jw[0], x0, y0, y1, T * mu);
-                add(x0, x1, y0, y1, mu);
-                add(x1, jw[1], y0, y1, T * mu);
+            const double e0 = f->pair_edges_cm[j], e1 = f->pair_edges_cm[j + 1];
+            // the physical aperture sets the field size of Eq. 1
+            const double ax0 = std::fmax(lv[2 * j], jw[0]), ax1 = std::fmin(lv[2 * j + 1], jw[1]);
+            const double ay0 = std::fmax(e0, jw[2]), ay1 = std::fmin(e1, jw[3]);
+            if (ax1 > ax0 && ay1 > ay0) {
                 open = true;
-                X0 = std::fmin(X0, x0); X1 = std::fmax(X1, x1); Y0 = std::fmin(Y0, y0); Y1 = std::fmax(Y1, y1);
-            } else {
-                add(jw[0], jw[1], y0, y1, T * mu);
+                X0 = std::fmin(X0, ax0); X1 = std::fmax(X1, ax1); Y0 = std::fmin(Y0, ay0); Y1 = std::fmax(Y1, ay1);
+            }
+            const double ya = std::fmax(e0, -kHalf), yb = std::fmin(e1, kHalf);
+            if (!(yb > ya)) continue;
+            const std::vector<double> ys = w > 0.0 ? split(ya, yb, {jy0, jy1, e0 + 0.5 * w, e1 - 0.5 * w})
+                                                   : split(ya, yb, {jy0, jy1});
+            for (size_t b = 0; b + 1 < ys.size(); ++b) {
+                const double y0 = ys[b], y1 = ys[b + 1], ym = 0.5 * (y0 + y1);
+                double lo = 0.0, hi = 0.0;
+                bool has = opening(j, lo, hi);
+                int nb = -1;                      // pair sharing this tongue-and-groove strip
+                if (w > 0.0 && j > 0 && ym < e0 + 0.5 * w) nb = j - 1;
+                if (w > 0.0 && j + 1 < f->n_pairs && ym > e1 - 0.5 * w) nb = j + 1;
+                if (has && nb >= 0) {
+                    double lo2, hi2;
+                    has = opening(nb, lo2, hi2);
+                    if (has) {
+                        lo = std::fmax(lo, lo2);
+                        hi = std::fmin(hi, hi2);
+                        has = hi > lo;
+                    }
+                }
+                const bool jaw_y = ym >= jy0 && ym <= jy1;
+                const std::vector<double> xs = has ? split(-kHalf, kHalf, {jx0, jx1, lo, hi})
+                                                   : split(-kHalf, kHalf, {jx0, jx1});
+                for (size_t a2 = 0; a2 + 1 < xs.size(); ++a2) {
+                    const double x0 = xs[a2], x1 = xs[a2 + 1], xm = 0.5 * (x0 + x1);
+                    const double leaf = (has && xm >= lo && xm <= hi) ? 1.0 : T;
+                    const double jaw = (jaw_y && xm >= jx0 && xm <= jx1) ? 1.0 : Tj;
+                    add(x0, x1, y0, y1, mu * leaf * jaw);
+                }
             }
         }
     }
+    if (!(acc > 0.0)) open = false;
     if (!open) return fail(c, MC_ERR_ARG, "field has no open aperture" + which);
     for (size_t i = off; i < cdf.size(); ++i) cdf[i] /= acc;
     out.rect_off = static_cast<int>(off);

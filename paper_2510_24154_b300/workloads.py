@@ -65,7 +65,13 @@ class Field:
     jaws:       [n_seg][4] (x1, x2, y1, y2).
     mu:         [n_seg] monitor-unit weights.
     leaf_transmission: fraction of the open fluence that passes closed
-                leaves inside the jaw opening (0 = ideal MLC).
+                leaves (0 = ideal MLC).
+    jaw_transmission: fraction that passes the jaws (0 = opaque).
+    tg_width:   tongue-and-groove strip width at the isocentre plane (cm):
+                within half of it from a pair boundary, the opening is the
+                intersection of both pairs' openings.
+    leaf_gap:   dosimetric leaf gap (cm): an open pair's effective opening
+                is wider by this much (rounded leaf ends).
     """
     pair_edges: np.ndarray
     leaves: np.ndarray
@@ -76,6 +82,9 @@ class Field:
     sid: float = 150.0
     iso: tuple = (0.0, 0.0, 0.0)
     leaf_transmission: float = 0.0
+    jaw_transmission: float = 0.0
+    tg_width: float = 0.0
+    leaf_gap: float = 0.0
 
 
 @dataclass

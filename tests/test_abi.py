@@ -70,9 +70,10 @@ def test_struct_layouts_match_c(tmp_path):
         int main(void) {
           printf("%zu %zu %zu %zu %zu\\n", sizeof(mc_config), sizeof(mc_epid_desc), sizeof(mc_field_desc),
                  sizeof(mc_lut_desc), sizeof(mc_run_stats));
-          printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(mc_config, use_graph), offsetof(mc_config, regs_variant), offsetof(mc_config, patient_dose),
+          printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(mc_config, use_graph), offsetof(mc_config, regs_variant), offsetof(mc_config, patient_dose),
                  offsetof(mc_epid_desc, pitch_cm),
-                 offsetof(mc_field_desc, eq1_literal), offsetof(mc_run_stats, gpu_ms),
+                 offsetof(mc_field_desc, eq1_literal), offsetof(mc_field_desc, leaf_transmission),
+                 offsetof(mc_field_desc, leaf_gap_cm), offsetof(mc_run_stats, gpu_ms),
                  offsetof(mc_run_stats, launches));
           return 0;
         }""")
@@ -85,7 +86,8 @@ def test_struct_layouts_match_c(tmp_path):
     assert sizes == [C.sizeof(binding.Config), C.sizeof(binding.EpidDesc), C.sizeof(binding.FieldDesc),
                      C.sizeof(binding.LutDesc), C.sizeof(binding.RunStats)]
     assert offs == [binding.Config.use_graph.offset, binding.Config.regs_variant.offset, binding.Config.patient_dose.offset, binding.EpidDesc.pitch_cm.offset,
-                    binding.FieldDesc.eq1_literal.offset, binding.RunStats.gpu_ms.offset,
+                    binding.FieldDesc.eq1_literal.offset, binding.FieldDesc.leaf_transmission.offset,
+                    binding.FieldDesc.leaf_gap_cm.offset, binding.RunStats.gpu_ms.offset,
                     binding.RunStats.launches.offset]
 
 

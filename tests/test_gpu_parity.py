@@ -239,3 +239,30 @@ def test_replay_with_leaf_transmission():
     img0, img1 = g0.sum(axis=0), gt.sum(axis=0)
     low = img0 < 0.02 * img0.max()
     assert low.sum() > 100 and img1[low].sum() > 1.5 * img0[low].sum()
+
+
+def test_replay_with_collimation():
+    """Leaf and jaw transmission, tongue and groove, leaf gap: both source
+    builders must produce the same rectangles in the same order, so a
+    photon-only run replays the oracle pixel by pixel (an independent stream
+    would differ by its full noise, tens of per cent per pixel)."""
+    p = G.thorax_case(n=400_000, scale=4, epid_scale=8)
+    p.physics.coupled = False
+    f = p.field
+    f.leaf_transmission, f.jaw_transmission, f.tg_width, f.leaf_gap = 0.015, 0.005, 0.1, 0.15
+    sim, st, orc, gt, ot, (e_g, e_o), (gd, gs, od, os_) = _compare_replay(p, p.n_histories)
+    assert abs(e_g / e_o - 1) < 1e-3
+    for k in ("flights_ct", "real_ct", "compton", "primaries_at_epid", "uncollided_at_epid"):
+        assert st["counters"][k] == pytest.approx(orc["counters"][k], rel=5e-4), k
+    img_g, img_o = gt.sum(axis=0), ot.sum(axis=0)
+    assert np.abs(img_g - img_o).sum() / img_o.sum() < 0.02
+
+
+def test_collimation_arguments_rejected():
+    p = G.thorax_case(n=1000, scale=4, epid_scale=8)
+    for name, v in (("jaw_transmission", 1.0), ("tg_width", 0.6), ("leaf_gap", 2.0), ("leaf_transmission", -0.1)):
+        q = G.thorax_case(n=1000, scale=4, epid_scale=8)
+        setattr(q.field, name, v)
+        with pytest.raises(binding.MCError):
+            G.make_sim(q)
+    G.make_sim(p).close()

@@ -667,3 +667,83 @@ def test_leaf_transmission_source_density():
     # Eq. 1 sees the openings only
     a, b = oracle.aperture_bbox(W.Field(edges, leaves, jaws, np.ones(1), leaf_transmission=0.2))
     assert (a, b) == (4.0, 9.0)
+
+
+def _frac_check(got_mask, want, n):
+    sd = np.sqrt(max(want * (1 - want), 1e-12) / n)
+    got = float(np.mean(got_mask))
+    assert abs(got - want) <= 4 * sd + 1e-12, (got, want)
+
+
+def _sample(fld, n=400_000, seed=5):
+    prob = W.config_water_open(n_histories=1)
+    prob.field = fld
+    X, Y, _ = oracle.sample_source(prob, n, seed=seed)
+    return X, Y
+
+
+def test_tongue_and_groove_strip():
+    """Two 1 cm pairs with complementary openings [-3, 0] and [0, 3]: within
+    w/2 of their boundary the opening is the (empty) intersection, so with
+    opaque leaves no primary starts there and each pair keeps 2.7 cm^2; with
+    leaf transmission T the strip (10 cm x w inside the jaws) emits at T:
+    fraction 2 T / (2 (2.7 + 6.3 T) + 2 T) for w = 0.2 (strip area 2 cm^2)."""
+    edges = np.array([-1.0, 0.0, 1.0])
+    leaves = np.array([[[-3.0, 0.0], [0.0, 3.0]]])
+    jaws = np.array([[-5.0, 5.0, -1.0, 1.0]])
+    n = 400_000
+    X, Y = _sample(W.Field(edges, leaves, jaws, np.ones(1), tg_width=0.2), n)
+    assert not np.any(np.abs(Y) < 0.1)
+    _frac_check(Y > 0, 0.5, n)
+    assert np.all((Y < 0) == (X < 0))
+    T = 0.1
+    X, Y = _sample(W.Field(edges, leaves, jaws, np.ones(1), leaf_transmission=T, tg_width=0.2), n)
+    _frac_check(np.abs(Y) < 0.1, 2.0 * T / (2 * (2.7 + 0.9 * 7.0 * T) + 2.0 * T), n)
+    # without the strip the same field has no gap at the boundary
+    X, Y = _sample(W.Field(edges, leaves, jaws, np.ones(1)), n)
+    _frac_check(np.abs(Y) < 0.1, 0.1, n)
+
+
+def test_leaf_gap_widens_open_pairs_only():
+    """Dosimetric leaf gap g: an open pair [-2, 2] emits uniformly over
+    [-2 - g/2, 2 + g/2]; a closed pair stays closed."""
+    edges = np.array([-1.0, 0.0, 1.0])
+    leaves = np.array([[[-2.0, 2.0], [0.5, 0.5]]])
+    jaws = np.array([[-5.0, 5.0, -1.0, 1.0]])
+    n = 200_000
+    X, Y = _sample(W.Field(edges, leaves, jaws, np.ones(1), leaf_gap=0.4), n)
+    assert np.all(Y < 0.0) and np.abs(X).max() <= 2.2 and np.abs(X).max() > 2.19
+    _frac_check(np.abs(X) > 2.0, 0.4 / 4.4, n)
+    a, b = oracle.aperture_bbox(W.Field(edges, leaves, jaws, np.ones(1), leaf_gap=0.4))
+    assert (a, b) == (4.0, 1.0)                      # Eq. 1 uses the physical aperture
+
+
+def test_jaw_transmission():
+    """MLC of 20 pairs over [-10, 10] fully open to |X| <= 10, jaws 4 x 6 cm:
+    with jaw transmission Tj and leaf transmission T the density is 1 inside
+    the jaws, Tj in the rest of the leaf openings (376 cm^2) and T Tj beyond
+    the leaves inside the 40 cm field (400 cm^2); nothing beyond the MLC."""
+    edges = np.linspace(-10.0, 10.0, 21)
+    leaves = np.zeros((1, 20, 2))
+    leaves[0, :, 0], leaves[0, :, 1] = -10.0, 10.0
+    jaws = np.array([[-2.0, 2.0, -3.0, 3.0]])
+    Tj, T = 0.01, 0.02
+    n = 400_000
+    X, Y = _sample(W.Field(edges, leaves, jaws, np.ones(1), leaf_transmission=T, jaw_transmission=Tj), n)
+    tot = 24.0 + 376.0 * Tj + 400.0 * T * Tj
+    assert np.abs(Y).max() <= 10.0 and np.abs(X).max() <= 20.0
+    inside = (np.abs(X) < 2.0) & (np.abs(Y) < 3.0)
+    _frac_check(inside, 24.0 / tot, n)
+    _frac_check(np.abs(X) > 10.0, 400.0 * T * Tj / tot, n)
+    X, Y = _sample(W.Field(edges, leaves, jaws, np.ones(1), jaw_transmission=Tj), n)
+    assert np.abs(X).max() <= 10.0
+    _frac_check((np.abs(X) < 2.0) & (np.abs(Y) < 3.0), 24.0 / (24.0 + 376.0 * Tj), n)
+
+
+def test_collimation_arguments_checked():
+    edges = np.array([-1.0, 0.0, 1.0])
+    leaves = np.array([[[-2.0, 2.0], [-2.0, 2.0]]])
+    jaws = np.array([[-5.0, 5.0, -1.0, 1.0]])
+    for kw in (dict(tg_width=1.0), dict(jaw_transmission=1.0), dict(leaf_gap=-0.1), dict(leaf_transmission=-0.1)):
+        with pytest.raises(ValueError):
+            _sample(W.Field(edges, leaves, jaws, np.ones(1), **kw), 10)
