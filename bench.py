@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 25-field batched-plan leg")
     ap.add_argument("--batched-scale", type=float, default=1.0, help="scale of the batched plan's history counts")
     ap.add_argument("--no-denoiser", action="store_true", help="skip the U-Net denoiser leg")
+    ap.add_argument("--no-anthro", action="store_true", help="skip the anthropomorphic-phantom leg")
+    ap.add_argument("--anthro-histories", type=int, default=1_000_000_000)
     ap.add_argument("--dn-batch", type=int, default=4, help="images per denoiser training step")
     return ap.parse_args()
 
@@ -278,6 +280,44 @@ def batched_plan(args, Simulator, W, p, extra, stream, local, rank, dist, barrie
             "s_per_field_1pct_max": max(s_1pct), "s_plan_1pct_all_fields": sum(s_1pct)}
 
 
+def anthropomorphic_leg(args, Simulator, W, extra, stream, local, rank, dist, barrier):
+    """The 512 x 512 x 200 phantom at 1 mm, one 40-segment field, the
+    1190 x 1190 EPID at 0.336 mm: one graph-driven run of the full history
+    count, its rate and the time to 1 % at that rate."""
+    import torch
+    N = args.anthro_histories
+    p = W.config_anthropomorphic(n_histories=N)
+    sim = Simulator(p.physics, device=local, use_graph=1, **extra)
+    sim.init_geometry(p.phantom, p.epid, stream=stream)
+    sim.set_field(p.field, p.lut, stream=stream)
+    sim.set_history_base(rank * N)
+    sim.run(max(N // 100, 1000), SEED, stream=stream)                              # warm-up
+    sim.reset_tally(stream=stream)
+    sim.set_history_base(rank * N)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    st = sim.run(N, SEED, stream=stream)
+    ev1.record(stream)
+    barrier()
+    t = ev0.elapsed_time(ev1) / 1e3
+    if dist is not None:
+        tt = torch.tensor([t], device=f"cuda:{local}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    ws = 1 if dist is None else dist.get_world_size()
+    _, _, u = sim.dose(stream=stream)
+    sim.close()
+    rate = N / t
+    return {"workload": "anthropomorphic_40seg: CT 512x512x200 int16 HU @1mm (body, lungs, spine, ribs, organs), "
+                        "one 40-segment IMRT field, EPID 1190x1190 @0.336mm, coupled",
+            "histories": N * ws, "seconds": t, "histories_per_s": ws * rate, "waves": st["waves"],
+            "u_at_run": u, "histories_for_1pct": N * (u / 0.01) ** 2,
+            "s_per_field_1pct": N * (u / 0.01) ** 2 / rate,
+            "energy_closure": abs(st["e_ct"] + sum(st["e_epid"]) + st["e_esc"] + st["e_lost"] - st["e_src"])
+            / st["e_src"]}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -424,6 +464,9 @@ def main():
     denoiser = None
     if not args.no_denoiser:
         denoiser = denoiser_leg(args, local, barrier)
+    anthro = None
+    if not args.no_anthro:
+        anthro = anthropomorphic_leg(args, Simulator, W, extra, stream, local, rank, dist, barrier)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -445,7 +488,7 @@ def main():
                        "parallelism": f"history shards x{ws}, no collective"},
             "s_per_field_1pct": n_1pct / per_gpu_rate, "u_at_step": u, "histories_for_1pct": n_1pct,
             "roofline": roofline, "memory_roofline": memory_roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "batched_plan": batched, "denoiser": denoiser,
+            "batched_plan": batched, "denoiser": denoiser, "anthropomorphic": anthro,
             "events_per_history": {k: last["counters"][k] / N for k in
                                    ("flights_ct", "real_ct", "compton", "photo", "pair", "esteps_ct", "esteps_epid",
                                     "moller", "brem", "electrons", "primaries_at_epid")},
