@@ -35,6 +35,9 @@ struct FieldHost {
     uint64_t hist_done;
 };
 
+// CTAs of 256 threads per SM each transport kernel is built for, measured
+// best on the thorax workload: photons 4 (64 registers), electrons 3 (80).
+constexpr int kDefaultRegsVariant[4] = {4, 3, 4, 3};
 constexpr double kQuantaPerMeV = 2.56e8;
 constexpr double kJoulePerMeV = 1.602176634e-13;
 constexpr uint64_t kFieldStride = 1ull << 40;
@@ -56,6 +59,7 @@ struct mc_ctx {
     int block = 256;
     int grid[mc::kNumBanks] = {0, 0, 0, 0};
     int minb[mc::kNumBanks] = {4, 4, 4, 4};
+    int src_grid = 0;            // source kernel: 8 CTAs of 256 per SM, grid-stride
     // banks
     void* bank_mem = nullptr;
     BankPtr bank[mc::kNumBanks][2];
@@ -447,8 +451,9 @@ mc_status run_waves_graph(mc_ctx* c, const Params& P, cudaStream_t s, cudaEvent_
         cleanup();
         return fail(c, MC_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
     }
-    uint32_t per_wave = 2;   // wave-begin and wave-end
-    e = mc::launch_wave_begin(c->d_ctl, c->cfg.primaries_per_wave, cs);
+    uint32_t per_wave = 3;   // wave-begin, source and wave-end
+    e = mc::launch_wave_begin(c->d_ctl, c->cfg.primaries_per_wave, c->cfg.bank_capacity, cs);
+    if (e == cudaSuccess) e = mc::launch_source(P, c->src_grid, cs);
     for (int t : kOrder) {
         if (is_electron(t) && !c->cfg.coupled) continue;
         if (e == cudaSuccess) e = mc::launch_transport(t, c->minb[t], P, c->grid[t], c->block, cs);
@@ -494,8 +499,9 @@ mc_status run_waves_host(mc_ctx* c, const Params& P, cudaStream_t s, cudaEvent_t
     mc_status result = MC_OK;
     int& waves = r.waves;
     for (; waves < static_cast<int>(kMaxWaves); ++waves) {
-        CUDA_TRY(c, mc::launch_wave_begin(c->d_ctl, c->cfg.primaries_per_wave, s));
-        ++r.launches;
+        CUDA_TRY(c, mc::launch_wave_begin(c->d_ctl, c->cfg.primaries_per_wave, c->cfg.bank_capacity, s));
+        CUDA_TRY(c, mc::launch_source(P, c->src_grid, s));
+        r.launches += 2;
         for (int t : kOrder) {
             if (is_electron(t) && !c->cfg.coupled) continue;
             if (c->cfg.time_kernels) {
@@ -714,7 +720,7 @@ void mc_config_default(mc_config* cfg) {
     cfg->primaries_per_wave = 0;
     cfg->time_kernels = 0;
     cfg->use_graph = 0;
-    for (int t = 0; t < 4; ++t) cfg->regs_variant[t] = 4;
+    for (int t = 0; t < 4; ++t) cfg->regs_variant[t] = kDefaultRegsVariant[t];
     cfg->patient_dose = 0;
 }
 
@@ -743,7 +749,7 @@ mc_status mc_create(const mc_config* cfg_in, int device, mc_ctx** out) {
     if (cfg.block_size == 0) cfg.block_size = 256;
     if (cfg.bank_capacity == 0) cfg.bank_capacity = 1u << 23;
     for (int t = 0; t < 4; ++t) {
-        if (cfg.regs_variant[t] == 0) cfg.regs_variant[t] = 4;
+        if (cfg.regs_variant[t] == 0) cfg.regs_variant[t] = kDefaultRegsVariant[t];
         if (cfg.regs_variant[t] < 2 || cfg.regs_variant[t] > 4) return MC_ERR_ARG;
     }
     if (cfg.primaries_per_wave == 0) cfg.primaries_per_wave = cfg.bank_capacity / 4;
@@ -813,6 +819,7 @@ mc_status mc_create(const mc_config* cfg_in, int device, mc_ctx** out) {
         const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, occ) : occ;
         c->grid[t] = c->sm_count * per_sm;
     }
+    c->src_grid = c->sm_count * 8;
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(MC_ERR_CUDA);
     *out = c;
     return MC_OK;

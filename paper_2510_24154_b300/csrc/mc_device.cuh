@@ -57,7 +57,9 @@ struct BankPtr {
 // Run control shared by the kernels of one run (device memory).
 struct Ctl {
     unsigned long long next_prim;   // next history (run-local index) to start
-    unsigned long long prim_limit;  // histories may start below this in the current wave
+    unsigned long long prim_limit;  // histories started so far, through the current wave
+    unsigned long long src_begin;   // the source kernel of this wave starts [src_begin, src_end)
+    unsigned long long src_end;
     unsigned long long n_total;
     uint32_t count[kNumBanks][2];
     uint32_t head[kNumBanks];

@@ -4,8 +4,10 @@
 //   photons in the CT    Woodcock (delta) tracking against the majorant
 //                        max_m rho_max,m mu_m(E); real interactions sampled as
 //                        Compton (Klein-Nishina), photoelectric or pair (Sec. 2.1.2).
-//                        Fuses the source (Sec. 2.1.1): dead lanes start new
-//                        histories once the input bank is drained.
+// A source kernel opens each wave: it samples that wave's primaries (Sec.
+// 2.1.1) one per thread, with every lane doing the same work, and writes them
+// into the CT-photon bank (or the EPID-photon bank when they miss the CT), so
+// the transport kernels never branch into history start-up.
 //   electrons in the CT  Class II condensed history: CSDA soft losses, hard
 //                        Moller and bremsstrahlung by delta tracking against
 //                        the start-of-step value, a random-hinge Wentzel
@@ -690,7 +692,6 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
     const BankPtr bin = P.bank[TYPE][in];
     // a recorded overflow can leave the count above the capacity: never read past the bank
     const uint32_t n_in = min(P.ctl->count[TYPE][in], P.cap);
-    const unsigned long long prim_limit = P.ctl->prim_limit;
     const bool may_flush = P.ctl->allow_flush != 0u;
     const uint32_t move_par = kEpid ? 0u : P.ctl->cur[kMoveTo];
 
@@ -698,7 +699,6 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
     Part p;
     bool alive = false;
     bool in_open = true;
-    bool src_open = (TYPE == kPhotonCT);
     int steps_here = 0;
 
     for (;;) {
@@ -711,36 +711,12 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
             if (got) { load_part(bin, slot, p, P); alive = true; steps_here = 0; }
             if (__any_sync(kFull, need && !got)) in_open = false;
         }
-        // then start new histories (photons in the CT only)
-        if (TYPE == kPhotonCT && src_open && __any_sync(kFull, !alive)) {
-            const bool need = !alive;
-            const unsigned m = __ballot_sync(kFull, need);
-            const int leader = __ffs(m) - 1;
-            unsigned long long base = 0ull;
-            if (lane_id() == leader) base = atomicAdd(&P.ctl->next_prim, static_cast<unsigned long long>(__popc(m)));
-            base = __shfl_sync(kFull, base, leader);
-            const unsigned long long idx = base + __popc(m & lanemask_lt());
-            if (need && idx < prim_limit) {
-                alive = start_primary(P, idx, p, acc, s_events, move);
-                steps_here = 0;
-            }
-            if (base + __popc(m) >= prim_limit) src_open = false;
-            // keep the electron bank from filling: stop admitting new histories
-            // (one lane reads the live fill count so the decision is warp-uniform)
-            uint32_t fill = 0u;
-            if (lane_id() == 0)
-                fill = *reinterpret_cast<volatile uint32_t*>(&P.ctl->count[kElectronCT][P.ctl->cur[kElectronCT]]);
-            fill = __shfl_sync(kFull, fill, 0);
-            if (fill > P.cap / 2u) src_open = false;
-        }
-        flush_self(P, move, kMoveTo, move_par, p);
-        move = false;
         const unsigned live = __ballot_sync(kFull, alive);
         if (live == 0u) {
-            if (!in_open && !src_open) break;
+            if (!in_open) break;
             continue;
         }
-        if (may_flush && !in_open && !src_open && __popc(live) <= P.flush_lanes) {
+        if (may_flush && !in_open && __popc(live) <= P.flush_lanes) {
             flush_self(P, alive, TYPE, in ^ 1u, p);
             alive = false;
             break;
@@ -780,6 +756,38 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
 }
 
 
+// The source of one wave: thread-by-thread the primaries of run-local
+// histories [src_begin, src_end), each sampled as the transport would have
+// sampled it (same draws), written with its draw count into the CT-photon
+// bank, or the EPID-photon bank when its line misses the CT.  Grid-stride,
+// whole warps per iteration (the bank reservations are warp-aggregated).
+__global__ void __launch_bounds__(256) k_source(const Params P) {
+    __shared__ unsigned long long s_energy[kNumEnergy];
+    __shared__ unsigned long long s_events[kNumEvents];
+    for (int i = threadIdx.x; i < kNumEnergy; i += blockDim.x) s_energy[i] = 0ull;
+    for (int i = threadIdx.x; i < kNumEvents; i += blockDim.x) s_events[i] = 0ull;
+    __syncthreads();
+    const unsigned long long begin = P.ctl->src_begin, end = P.ctl->src_end;
+    const uint32_t par_ct = P.ctl->cur[kPhotonCT], par_epid = P.ctl->cur[kPhotonEPID];
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0u, 0u, 0u, 0u};
+    const unsigned long long warps = static_cast<unsigned long long>(gridDim.x) * (blockDim.x >> 5);
+    const unsigned long long w0 = static_cast<unsigned long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (unsigned long long base = begin + 32ull * w0; base < end; base += 32ull * warps) {
+        const unsigned long long idx = base + static_cast<unsigned long long>(lane_id());
+        Part p;
+        bool enter = false, move = false;
+        if (idx < end) enter = start_primary(P, idx, p, acc, s_events, move);
+        flush_self(P, enter, kPhotonCT, par_ct, p);
+        flush_self(P, move, kPhotonEPID, par_epid, p);
+    }
+    acc_flush(P, acc, s_energy, s_events, kCFlightsCT, kCEStepsCT);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kNumEnergy; i += blockDim.x)
+        if (s_energy[i]) atomicAdd(&P.energy[i], s_energy[i]);
+    for (int i = threadIdx.x; i < kNumEvents; i += blockDim.x)
+        if (s_events[i]) atomicAdd(&P.events[i], s_events[i]);
+}
+
 // Closes a consumer pass of bank type t: the drained input parity is emptied
 // and the carry parity becomes the next input.
 __global__ void k_swap(Ctl* c, int t) {
@@ -787,13 +795,20 @@ __global__ void k_swap(Ctl* c, int t) {
     c->count[t][in] = 0u;
     c->head[t] = 0u;
     c->cur[t] = in ^ 1u;
-    if (t == kPhotonCT && c->next_prim > c->prim_limit) c->next_prim = c->prim_limit;
 }
 
-// Opens a wave: admits up to `per_wave` more histories.
-__global__ void k_wave_begin(Ctl* c, unsigned long long per_wave) {
-    unsigned long long lim = c->next_prim + per_wave;
+// Opens a wave: the source kernel will start up to `per_wave` more histories,
+// no more than the CT-photon bank has room for beside the photons carried
+// over, and at most half a bank (their secondaries fill the electron bank).
+__global__ void k_wave_begin(Ctl* c, unsigned long long per_wave, uint32_t cap) {
+    const uint32_t carried = c->count[kPhotonCT][c->cur[kPhotonCT]];
+    unsigned long long room = (carried < cap) ? cap - carried : 0u;
+    room = min(room, static_cast<unsigned long long>(cap / 2u));
+    unsigned long long lim = c->next_prim + min(per_wave, room);
     if (lim > c->n_total) lim = c->n_total;
+    c->src_begin = c->next_prim;
+    c->src_end = lim;
+    c->next_prim = lim;
     c->prim_limit = lim;
     c->allow_flush = (lim < c->n_total) ? 1u : 0u;
 }
@@ -873,8 +888,13 @@ cudaError_t launch_wave_end(Ctl* c, cudaGraphConditionalHandle h, unsigned int m
     return cudaGetLastError();
 }
 
-cudaError_t launch_wave_begin(Ctl* c, unsigned long long per_wave, cudaStream_t s) {
-    k_wave_begin<<<1, 1, 0, s>>>(c, per_wave);
+cudaError_t launch_wave_begin(Ctl* c, unsigned long long per_wave, uint32_t cap, cudaStream_t s) {
+    k_wave_begin<<<1, 1, 0, s>>>(c, per_wave, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source(const Params& P, int grid, cudaStream_t s) {
+    k_source<<<grid, 256, 0, s>>>(P);
     return cudaGetLastError();
 }
 
