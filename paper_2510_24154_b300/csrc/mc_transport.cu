@@ -52,6 +52,14 @@ __device__ __forceinline__ void acc_flush(const Params& P, Acc& a, unsigned long
     }
 }
 
+// Adds n per calling lane to event counter idx: the converged lanes that
+// reach this call together are counted by one of them with a single shared
+// atomic (same-address atomics from many lanes would serialise).
+__device__ __forceinline__ void count_event(unsigned long long* s_events, int idx, unsigned n = 1u) {
+    const unsigned m = __activemask();
+    if (lane_id() == __ffs(m) - 1) atomicAdd(&s_events[idx], static_cast<unsigned long long>(__popc(m) * n));
+}
+
 __device__ __forceinline__ float rest_extra(uint32_t flags) { return (flags & kPositron) ? kTwoMec2 : 0.0f; }
 
 // Energy deposited at beam-frame position (x, y) in EPID layer `layer` by a
@@ -106,8 +114,8 @@ __device__ __forceinline__ bool transfer_to_epid(const Params& P, Part& p, Acc& 
     p.u = bu; p.v = bv; p.w = bw;
     p.cell = 0u;
     if (is_photon && p.rng.ord == 0u) {
-        atomicAdd(&s_events[kCPrimAtEPID], 1ull);
-        if (!(p.flags & kCollided)) atomicAdd(&s_events[kCUncollided], 1ull);
+        count_event(s_events, kCPrimAtEPID);
+        if (!(p.flags & kCollided)) count_event(s_events, kCUncollided);
     }
     return true;
 }
@@ -123,7 +131,8 @@ __device__ __forceinline__ void charged(const Params& P, Acc& a, unsigned long l
         e.E = T; e.u = du; e.v = dv; e.w = dw;
         e.ord = child_ordinal(p.rng.ord, p.rng.d, slot);
         e.flags = kCollided | (positron ? kPositron : 0u);
-        atomicAdd(&s_events[positron ? kCPositrons : kCElectrons], 1ull);
+        if (positron) count_event(s_events, kCPositrons);
+        else count_event(s_events, kCElectrons);
     } else {
         deposit<EPID>(P, a, s_energy, p.cell, p.x, p.y, p.hist, p.flags, T);
     }
@@ -144,7 +153,7 @@ __device__ __forceinline__ void annihilate(const Params& P, unsigned long long* 
     e.ord = p.rng.ord;          // both children derive from (ord, d) at write time
     // bit 31 marks a back-to-back pair; bits 2..30 hold the parent's draw count
     e.flags = kCollided | 0x80000000u | ((p.rng.d & 0x1fffffffu) << 2);
-    atomicAdd(&s_events[kCPhotons2], 2ull);
+    count_event(s_events, kCPhotons2, 2u);
 }
 
 // Klein-Nishina composition-rejection; returns eps = E'/E and cos(theta).
@@ -207,7 +216,7 @@ __device__ __forceinline__ bool photon_interact(const Params& P, Acc& a, unsigne
     const float xi = p.rng.u();
     p.flags |= kCollided;
     if (xi * tot < mc) {
-        atomicAdd(&s_events[kCCompton], 1ull);
+        count_event(s_events, kCCompton);
         float eps, ct;
         sample_kn(p.rng, p.E, eps, ct);
         float sp, cp;
@@ -228,11 +237,11 @@ __device__ __forceinline__ bool photon_interact(const Params& P, Acc& a, unsigne
         return true;
     }
     if (xi * tot < mc + mp) {
-        atomicAdd(&s_events[kCPhoto], 1ull);
+        count_event(s_events, kCPhoto);
         charged<EPID>(P, a, s_energy, s_events, p, e0, p.E, p.u, p.v, p.w, 0u, false);
         return false;
     }
-    atomicAdd(&s_events[kCPair], 1ull);
+    count_event(s_events, kCPair);
     const float avail = p.E - kTwoMec2;
     const float xu = p.rng.u();
     const float Tm = xu * avail, Tp = avail - Tm;
@@ -353,7 +362,7 @@ __device__ __forceinline__ bool photon_ct_event(const Params& P, const float2* t
     const int m = material_of(P, rho);
     const float tm = (m == 0) ? tot[0] : (m == 1) ? tot[1] : (m == 2) ? tot[2] : tot[3];
     if (!(p.rng.u() * Sc < rho * tm)) return true;            // virtual
-    atomicAdd(&s_events[kCRealCT], 1ull);
+    count_event(s_events, kCRealCT);
     p.cell = pack_cell(ix, iy, iz);
     float mc, mp, mq;
     photon_mu(P, m, xs, mc, mp, mq);
@@ -406,7 +415,7 @@ __device__ __forceinline__ bool photon_epid_event(const Params& P, const float2*
 template <bool EPID>
 __device__ __forceinline__ bool electron_event(const Params& P, const float2* tab, Acc& a,
                                                unsigned long long* s_energy, unsigned long long* s_events,
-                                               Part& p, Emit& e0, Emit& e1, bool& move) {
+                                               Part& p, Emit& e0, Emit& e1, bool& move, float& rho_c) {
     float rho;
     int m, layer = 0;
     if (EPID) {
@@ -414,7 +423,7 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
         rho = P.lrho[layer];
         m = P.lmat[layer];
     } else {
-        rho = __ldg(&P.rho[(static_cast<size_t>(cell_z(p.cell)) * P.ny + cell_y(p.cell)) * P.nx + cell_x(p.cell)]);
+        rho = rho_c;               // the density of p.cell, loaded when the electron entered it
         m = material_of(P, rho);
     }
     ++a.steps;
@@ -502,7 +511,10 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
             const int stp = (cdir > 0.0f) ? 1 : -1;
             if (cax == 0) ix += stp; else if (cax == 1) iy += stp; else iz += stp;
             out = ix < 0 || ix >= P.nx || iy < 0 || iy >= P.ny || iz < 0 || iz >= P.nz;
-            if (!out) p.cell = pack_cell(ix, iy, iz);
+            if (!out) {
+                p.cell = pack_cell(ix, iy, iz);
+                rho_c = __ldg(&P.rho[(static_cast<size_t>(iz) * P.ny + iy) * P.nx + ix]);   // used next step
+            }
         }
         if (out) {
             // a face-limited step leaves undeflected
@@ -519,7 +531,7 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     const float snb = rho * mcst.brem * fmaxf(lnTn - P.ln_wcb, 0.0f);
     if (!(p.rng.u() * Sh < snm + snb)) return true;             // delta event
     if (p.rng.u() * (snm + snb) < snm) {
-        atomicAdd(&s_events[kCMoller], 1ull);
+        count_event(s_events, kCMoller);
         const float eps = sample_moller(p.rng, Tn, P.wcc);
         float sph, cph;
         sincospif(2.0f * p.rng.u(), &sph, &cph);
@@ -532,13 +544,13 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
         charged<EPID>(P, a, s_energy, s_events, p, e0, W, su, sv, sw, 0u, false);
         p.E = Tp;
     } else {
-        atomicAdd(&s_events[kCBrem], 1ull);
+        count_event(s_events, kCBrem);
         const float k = P.wcb * expf(p.rng.u() * logf(Tn / P.wcb));
         e0.dest = EPID ? kPhotonEPID : kPhotonCT;
         e0.E = k; e0.u = p.u; e0.v = p.v; e0.w = p.w;
         e0.ord = child_ordinal(p.rng.ord, p.rng.d, 0u);
         e0.flags = kCollided;
-        atomicAdd(&s_events[kCPhotons2], 1ull);
+        count_event(s_events, kCPhotons2);
         p.E = Tn - k;
     }
     if (p.E <= P.tstop) {
@@ -700,6 +712,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
     bool alive = false;
     bool in_open = true;
     int steps_here = 0;
+    float rho_c = 0.0f;         // electrons in the CT: density of the current voxel
 
     for (;;) {
         bool move = false;
@@ -708,7 +721,14 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
             const bool need = !alive;
             const uint32_t slot = warp_reserve(need, &P.ctl->head[TYPE]);
             const bool got = need && slot < n_in;
-            if (got) { load_part(bin, slot, p, P); alive = true; steps_here = 0; }
+            if (got) {
+                load_part(bin, slot, p, P);
+                alive = true;
+                steps_here = 0;
+                if (TYPE == kElectronCT)
+                    rho_c = __ldg(&P.rho[(static_cast<size_t>(cell_z(p.cell)) * P.ny + cell_y(p.cell)) * P.nx +
+                                         cell_x(p.cell)]);
+            }
             if (__any_sync(kFull, need && !got)) in_open = false;
         }
         const unsigned live = __ballot_sync(kFull, alive);
@@ -729,7 +749,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
             bool keep;
             if (TYPE == kPhotonCT) keep = photon_ct_event(P, s_tab, s_grid, acc, s_energy, s_events, p, e0, e1, move);
             else if (TYPE == kPhotonEPID) keep = photon_epid_event(P, s_tab, acc, s_energy, s_events, p, e0, e1);
-            else keep = electron_event<kEpid>(P, s_tab, acc, s_energy, s_events, p, e0, e1, move);
+            else keep = electron_event<kEpid>(P, s_tab, acc, s_energy, s_events, p, e0, e1, move, rho_c);
             if (keep && ++steps_here > P.max_steps) {
                 acc.lost += quanta(p.E + rest_extra(p.flags));
                 atomicAdd(&s_events[kCLost], 1ull);
