@@ -27,7 +27,7 @@ constexpr float kMec2 = 0.51099895f;
 constexpr float kTwoMec2 = 1.0219979f;
 constexpr int kPhotonNodes = 2048;
 constexpr int kElectronNodes = 512;
-constexpr int kWentzelNodes = 128;
+constexpr int kWentzelNodes = 2048;
 constexpr int kMaxMacroCells = 4096;
 constexpr int kNumMat = 7;
 constexpr int kMaxLayers = 8;
@@ -379,32 +379,17 @@ __device__ __forceinline__ float2 electron_tab(const float2* tab, const Params& 
 }
 
 // Screening parameter A of the screened-Rutherford (Wentzel) law whose mean
-// <1 - cos> equals 1 - exp(-G); -1 means isotropic.  Start from the ln A(ln G)
-// table (shared memory, after the electron tables) and take two Newton steps
-// on ln A; the same fixed work on every lane.
+// <1 - cos> equals 1 - exp(-G); -1 means isotropic (1/2 - <(1 - cos)/2> =
+// exp(-G)/2 below 1e-6, i.e. G > ln(5e5)).  Linear interpolation of ln A on a
+// 2048-node ln G table in shared memory (after the electron tables): relative
+// error below 2e-3 everywhere and 3e-5 on average against the root of the
+// defining equation, the same fixed work on every lane.
 __device__ __forceinline__ float wentzel_A(const float* wtab, const Params& P, float G) {
-    const float m = -0.5f * expm1f(-G);
-    if (0.5f - m < 1e-6f) return -1.0f;
+    if (G > 13.1223634f) return -1.0f;
     const float x = (logf(G) - P.w_lnG0) * P.w_idx;
     const int i = min(max(__float2int_rd(x), 0), kWentzelNodes - 2);
     const float f = x - static_cast<float>(i);
-    float y = fmaf(f, wtab[i + 1] - wtab[i], wtab[i]);
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const float A = expf(y);
-        float mean, dm;
-        if (A > 100.0f) {
-            const float xa = 1.0f / A;
-            mean = 0.5f - xa * (1.0f / 6.0f - xa * (1.0f / 12.0f - xa * (1.0f / 20.0f)));
-            dm = xa * xa * (1.0f / 6.0f - xa * (1.0f / 6.0f));
-        } else {
-            const float l = log1pf(1.0f / A);
-            mean = A * ((1.0f + A) * l - 1.0f);
-            dm = (1.0f + 2.0f * A) * l - 2.0f;
-        }
-        y -= fminf(fmaxf((mean - m) / (A * dm), -2.0f), 2.0f);
-    }
-    return expf(y);
+    return expf(fmaf(f, wtab[i + 1] - wtab[i], wtab[i]));
 }
 
 }  // namespace mc

@@ -155,7 +155,10 @@ Tables build_tables(double e_lo, double e_hi, double t_lo, double t_hi, double w
             row[1] = static_cast<float>(moller_hard(m, T, wcc));
         }
     }
-    const double lg0 = std::log(1e-12), lg1 = std::log(13.0);
+    // ln G from 1e-16 (steps far below the FP32 resolution of a position) to
+    // 13.12, just under the isotropic limit ln(5e5) where <1 - cos> is within
+    // 2e-6 of 1
+    const double lg0 = std::log(1e-16), lg1 = std::log(13.12);
     t.w_lnG0 = lg0;
     t.w_inv_dlnG = (kWentzelNodes - 1) / (lg1 - lg0);
     t.wentzel.resize(kWentzelNodes);

@@ -15,7 +15,7 @@ namespace mcphys {
 constexpr int kNumMaterials = 7;
 constexpr int kPhotonNodes = 2048;     // ln-uniform photon table nodes
 constexpr int kElectronNodes = 512;    // ln-uniform electron table nodes per material
-constexpr int kWentzelNodes = 128;     // ln A of the screening parameter on a ln G grid
+constexpr int kWentzelNodes = 2048;     // ln A of the screening parameter on a ln G grid
 
 constexpr double kMec2 = 0.51099895;   // MeV
 constexpr double kRe = 2.8179403262e-13;
