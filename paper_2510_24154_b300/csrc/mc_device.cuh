@@ -249,36 +249,6 @@ struct Emit {
 
 __device__ __forceinline__ void emit_none(Emit& e) { e.dest = -1; }
 
-// Writes the lane's pending emission into its destination bank (input parity
-// of that type, or the carry parity when it is the kernel's own type).
-// Convergent: all lanes call it.
-__device__ __forceinline__ void flush_emit(const Params& P, const Emit& e, const Part& parent, int own_type,
-                                           uint32_t own_in) {
-#pragma unroll
-    for (int t = 0; t < kNumBanks; ++t) {
-        const bool want = (e.dest == t);
-        if (__ballot_sync(kFull, want) == 0u) continue;
-        const uint32_t par = (t == own_type) ? (own_in ^ 1u) : P.ctl->cur[t];
-        const uint32_t slot = warp_reserve(want, &P.ctl->count[t][par]);
-        if (want) {
-            if (slot < P.cap) {
-                const BankPtr& b = P.bank[t][par];
-                b.x[slot] = parent.x; b.y[slot] = parent.y; b.z[slot] = parent.z;
-                b.u[slot] = e.u; b.v[slot] = e.v; b.w[slot] = e.w;
-                b.E[slot] = e.E;
-                b.hist[slot] = parent.hist;
-                b.ord[slot] = e.ord;
-                b.draws[slot] = 0u;
-                b.cell[slot] = parent.cell;
-                b.flags[slot] = e.flags;
-            } else {
-                atomicOr(&P.ctl->error, kErrOverflow);
-                atomicAdd(&P.energy[kELost], quanta(e.E + ((e.flags & kPositron) ? kTwoMec2 : 0.0f)));
-            }
-        }
-    }
-}
-
 // Moves the lane's own particle into bank `t` (input parity of t).
 __device__ __forceinline__ void flush_self(const Params& P, bool want, int t, uint32_t par, const Part& p) {
     if (__ballot_sync(kFull, want) == 0u) return;

@@ -565,28 +565,25 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
 // back-to-back photons with the ordinals of slots 0 and 1.
 __device__ __forceinline__ void flush_emission(const Params& P, const Emit& e, const Part& parent, int own_type,
                                                uint32_t own_in) {
-    if (__ballot_sync(kFull, e.dest >= 0) == 0u) return;        // the common case: nothing to write
-    const bool pairrec = (e.dest >= 0) && (e.flags & 0x80000000u);
-    const uint32_t n = (e.dest >= 0) ? (pairrec ? 2u : 1u) : 0u;
+    const bool has = e.dest >= 0;
+    if (__ballot_sync(kFull, has) == 0u) return;                // the common case: nothing to write
+    const bool pairrec = has && (e.flags & 0x80000000u);
+    const unsigned types = __reduce_or_sync(kFull, has ? (1u << e.dest) : 0u);
+    const unsigned lt = lanemask_lt();
 #pragma unroll
     for (int t = 0; t < kNumBanks; ++t) {
+        if (!(types & (1u << t))) continue;                     // warp-uniform
         const bool want = (e.dest == t);
-        const unsigned m = __ballot_sync(kFull, want);
-        if (m == 0u) continue;
-        // warp prefix sum of the per-lane counts
-        uint32_t cnt = want ? n : 0u, incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, incl, o);
-            if (lane_id() >= o) incl += y;
-        }
-        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        // records per lane: one, or two for a back-to-back pair
+        const unsigned one = __ballot_sync(kFull, want), two = __ballot_sync(kFull, want && pairrec);
+        const uint32_t total = __popc(one) + __popc(two);
         const uint32_t par = (t == own_type) ? (own_in ^ 1u) : P.ctl->cur[t];
         uint32_t base = 0;
         if (lane_id() == 0) base = atomicAdd(&P.ctl->count[t][par], total);
         base = __shfl_sync(kFull, base, 0);
         if (!want) continue;
-        const uint32_t first = base + incl - cnt;
+        const uint32_t n = pairrec ? 2u : 1u;
+        const uint32_t first = base + __popc(one & lt) + __popc(two & lt);
         const BankPtr b = P.bank[t][par];
         for (uint32_t k = 0; k < n; ++k) {
             const uint32_t slot = first + k;
