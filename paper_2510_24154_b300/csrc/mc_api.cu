@@ -38,6 +38,7 @@ struct FieldHost {
 // CTAs of 256 threads per SM each transport kernel is built for, measured
 // best on the thorax workload: photons 4 (64 registers), electrons 3 (80).
 constexpr int kDefaultRegsVariant[4] = {4, 3, 4, 3};
+constexpr size_t kHeadsBytes = sizeof(uint32_t) * mc::kNumBanks * mc::kHeadShards * mc::kHeadStride;
 constexpr double kQuantaPerMeV = 2.56e8;
 constexpr double kJoulePerMeV = 1.602176634e-13;
 constexpr uint64_t kFieldStride = 1ull << 40;
@@ -65,6 +66,7 @@ struct mc_ctx {
     BankPtr bank[mc::kNumBanks][2];
     uint32_t cap = 0;
     Ctl* d_ctl = nullptr;
+    uint32_t* d_heads = nullptr;  // segment read counters of the input banks
     Ctl* h_ctl = nullptr;        // pinned
     // geometry
     bool has_geom = false;
@@ -231,6 +233,7 @@ void make_params(const mc_ctx* c, Params& P, uint64_t seed) {
     P.events = c->d_events;
     P.vox = c->cfg.patient_dose ? c->d_vox : nullptr;
     P.ctl = c->d_ctl;
+    P.heads = c->d_heads;
     for (int t = 0; t < mc::kNumBanks; ++t)
         for (int k = 0; k < 2; ++k) P.bank[t][k] = c->bank[t][k];
     P.cap = c->cap;
@@ -457,7 +460,7 @@ mc_status run_waves_graph(mc_ctx* c, const Params& P, cudaStream_t s, cudaEvent_
     for (int t : kOrder) {
         if (is_electron(t) && !c->cfg.coupled) continue;
         if (e == cudaSuccess) e = mc::launch_transport(t, c->minb[t], P, c->grid[t], c->block, cs);
-        if (e == cudaSuccess) e = mc::launch_swap(c->d_ctl, t, cs);
+        if (e == cudaSuccess) e = mc::launch_swap(c->d_ctl, c->d_heads, t, cs);
         per_wave += 2;
     }
     if (e == cudaSuccess) e = mc::launch_wave_end(c->d_ctl, handle, kMaxWaves, cs);
@@ -510,7 +513,7 @@ mc_status run_waves_host(mc_ctx* c, const Params& P, cudaStream_t s, cudaEvent_t
             }
             CUDA_TRY(c, mc::launch_transport(t, c->minb[t], P, c->grid[t], c->block, s));
             if (c->cfg.time_kernels) CUDA_TRY(c, cudaEventRecord(next_event(), s));
-            CUDA_TRY(c, mc::launch_swap(c->d_ctl, t, s));
+            CUDA_TRY(c, mc::launch_swap(c->d_ctl, c->d_heads, t, s));
             r.launches += 2;
             ++r.klaunch[t];
         }
@@ -640,6 +643,7 @@ mc_status run_impl(mc_ctx* c, const uint64_t* n, uint64_t seed, cudaStream_t s, 
     std::memset(&h, 0, sizeof(h));
     h.n_total = first.back();
     CUDA_TRY(c, cudaMemcpyAsync(c->d_ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_heads, 0, kHeadsBytes, s));
     cudaEvent_t e0, e1;
     CUDA_TRY(c, cudaEventCreate(&e0));
     CUDA_TRY(c, cudaEventCreate(&e1));
@@ -795,7 +799,8 @@ mc_status mc_create(const mc_config* cfg_in, int device, mc_ctx** out) {
             for (int i = 0; i < 5; ++i) { *q[i] = reinterpret_cast<uint32_t*>(base); base += per; }
         }
     }
-    if (cudaMalloc(&c->d_ctl, sizeof(Ctl)) != cudaSuccess || cudaMallocHost(&c->h_ctl, sizeof(Ctl)) != cudaSuccess)
+    if (cudaMalloc(&c->d_ctl, sizeof(Ctl)) != cudaSuccess || cudaMallocHost(&c->h_ctl, sizeof(Ctl)) != cudaSuccess ||
+        cudaMalloc(&c->d_heads, kHeadsBytes) != cudaSuccess)
         return bail(MC_ERR_OOM);
     if (cudaMalloc(&c->d_energy, sizeof(unsigned long long) * mc::kNumEnergy) != cudaSuccess ||
         cudaMalloc(&c->d_events, sizeof(unsigned long long) * mc::kNumEvents) != cudaSuccess ||
@@ -833,6 +838,7 @@ mc_status mc_destroy(mc_ctx* c) {
     dfree(c->d_etab);
     if (c->bank_mem) cudaFree(c->bank_mem);
     dfree(c->d_ctl);
+    dfree(c->d_heads);
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     dfree(c->d_hu);
     dfree(c->d_rho);

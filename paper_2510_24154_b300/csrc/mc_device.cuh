@@ -36,6 +36,11 @@ constexpr float kStopMargin = 1e-6f;          // electrons stop at T <= cutoff +
 constexpr unsigned kFull = 0xffffffffu;
 
 enum BankType { kPhotonCT = 0, kElectronCT = 1, kPhotonEPID = 2, kElectronEPID = 3, kNumBanks = 4 };
+// A consumer kernel reads its input bank as kHeadShards contiguous segments,
+// each with its own read counter on its own 128-byte line (kHeadStride
+// words), so the refills of thousands of warps do not all hit one address.
+constexpr int kHeadShards = 8;
+constexpr int kHeadStride = 32;
 enum EnergyCounter { kESrc = 0, kECT = 1, kEEsc = 2, kELost = 3, kEEpid0 = 4, kNumEnergy = 12 };
 enum EventCounter {
     kCFlightsCT = 0, kCRealCT, kCCompton, kCPhoto, kCPair, kCEStepsCT, kCEStepsEPID, kCMoller, kCBrem,
@@ -62,7 +67,6 @@ struct Ctl {
     unsigned long long src_end;
     unsigned long long n_total;
     uint32_t count[kNumBanks][2];
-    uint32_t head[kNumBanks];
     uint32_t cur[kNumBanks];        // input parity per bank type
     uint32_t allow_flush;           // more primaries follow: warps may hand low-occupancy work on
     uint32_t error;
@@ -128,6 +132,7 @@ struct Params {
     unsigned long long* events;     // [kNumEvents]
     unsigned long long* vox;        // patient dose: energy per CT voxel [nz][ny][nx] (2^-8 eV), or null
     Ctl* ctl;
+    uint32_t* heads;                // [kNumBanks][kHeadShards][kHeadStride]: read counters of the input segments
     BankPtr bank[kNumBanks][2];
     uint32_t cap;
     int flush_lanes;

@@ -710,14 +710,32 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
     bool in_open = true;
     int steps_here = 0;
     float rho_c = 0.0f;         // electrons in the CT: density of the current voxel
+    // input segment this warp reads first, and the segments found dry
+    int seg = static_cast<int>((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kHeadShards);
+    uint32_t dry = 0u;
 
     for (;;) {
         bool move = false;
         // refill dead lanes from the input bank
         if (in_open && __any_sync(kFull, !alive)) {
             const bool need = !alive;
-            const uint32_t slot = warp_reserve(need, &P.ctl->head[TYPE]);
-            const bool got = need && slot < n_in;
+            // reserve from the current segment; a segment that runs dry sends
+            // the warp on to the next one, and the input is closed for the
+            // warp once every segment is dry
+            const unsigned m = __ballot_sync(kFull, need);
+            const uint32_t lo = static_cast<uint32_t>(static_cast<unsigned long long>(n_in) * seg / kHeadShards);
+            const uint32_t hi = static_cast<uint32_t>(static_cast<unsigned long long>(n_in) * (seg + 1) / kHeadShards);
+            uint32_t base = 0;
+            if (lane_id() == __ffs(m) - 1)
+                base = atomicAdd(&P.heads[(TYPE * kHeadShards + seg) * kHeadStride], static_cast<uint32_t>(__popc(m)));
+            base = lo + __shfl_sync(kFull, base, __ffs(m) - 1);
+            const uint32_t slot = base + __popc(m & lanemask_lt());
+            const bool got = need && slot < hi;
+            if (base + __popc(m) >= hi) {              // this segment is dry (warp-uniform)
+                dry |= 1u << seg;
+                seg = (seg + 1) % kHeadShards;
+                if (dry == (1u << kHeadShards) - 1u) in_open = false;
+            }
             if (got) {
                 load_part(bin, slot, p, P);
                 alive = true;
@@ -726,7 +744,6 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
                     rho_c = __ldg(&P.rho[(static_cast<size_t>(cell_z(p.cell)) * P.ny + cell_y(p.cell)) * P.nx +
                                          cell_x(p.cell)]);
             }
-            if (__any_sync(kFull, need && !got)) in_open = false;
         }
         const unsigned live = __ballot_sync(kFull, alive);
         if (live == 0u) {
@@ -807,10 +824,10 @@ __global__ void __launch_bounds__(256) k_source(const Params P) {
 
 // Closes a consumer pass of bank type t: the drained input parity is emptied
 // and the carry parity becomes the next input.
-__global__ void k_swap(Ctl* c, int t) {
+__global__ void k_swap(Ctl* c, uint32_t* heads, int t) {
     const uint32_t in = c->cur[t];
     c->count[t][in] = 0u;
-    c->head[t] = 0u;
+    for (int k = 0; k < kHeadShards; ++k) heads[(t * kHeadShards + k) * kHeadStride] = 0u;
     c->cur[t] = in ^ 1u;
 }
 
@@ -895,8 +912,8 @@ cudaError_t launch_transport(int type, int minb, const Params& P, int grid, int 
     return cudaLaunchKernel(transport_fn(type, minb), dim3(grid), dim3(block), args, smem, s);
 }
 
-cudaError_t launch_swap(Ctl* c, int t, cudaStream_t s) {
-    k_swap<<<1, 1, 0, s>>>(c, t);
+cudaError_t launch_swap(Ctl* c, uint32_t* heads, int t, cudaStream_t s) {
+    k_swap<<<1, 1, 0, s>>>(c, heads, t);
     return cudaGetLastError();
 }
 
