@@ -31,11 +31,17 @@ HIST_PER_STEP = 100_000_000
 SEED = 1
 WORKLOAD = "thorax_imrt_9seg: CT 256x256x128 int16 HU @2mm, 9 MLC segments x 60 pairs, " \
            "EPID 1024x768 @0.39mm (Cu/Gd2O2S/a-Si), k-table 64x32, coupled photon/electron"
-# Counted single-precision work per CT electron step: FADD + FMUL + 2 FFMA
-# (+ 2 x the packed forms, none issued) summed over every CT-electron launch of
-# the small thorax case, divided by its CT electron steps; ncu capture in
-# profiles/electron_ct_small_case.md.
-FLOPS_PER_ESTEP_CT = 555.4
+# Per CT electron step, counted by ncu over every CT-electron launch of the
+# 2e6-history thorax case (profiles/electron_ct_small_case.md): executed
+# thread instructions, single-precision operations (FADD + FMUL + 2 FFMA; no
+# packed forms issued) and DRAM bytes read + written.
+INST_PER_ESTEP_CT = 596.1
+FLOPS_PER_ESTEP_CT = 162.3
+DRAM_BYTES_PER_ESTEP_CT = 3.38
+# instruction issue: 148 SMs x 4 schedulers x 32 lanes x 2.032 GHz
+ISSUE_PEAK_TINST = 148 * 4 * 32 * 2.032e9 / 1e12
+# run-control block read back after every wave of a host-driven run
+CTL_BYTES = 104
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
 
 
@@ -401,6 +407,7 @@ def main():
     launches_e = max(agg["kernel_launches"][1], 1)
     avg_ms = agg["kernel_ms"][1] / launches_e
     steps_per_launch = agg["esteps_ct"] / launches_e
+    insts = INST_PER_ESTEP_CT * steps_per_launch
     flops = FLOPS_PER_ESTEP_CT * steps_per_launch
     hbm_peak, peak_kind = peaks()
     # algorithmic bytes of a CT electron launch: one 4-byte density gather per
@@ -411,12 +418,18 @@ def main():
     mem_achieved = alg_bytes / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
     roofline = {
         "bound": "alu", "kernel": "k_transport<electrons in CT>",
-        "achieved": flops / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0,
-        "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 (FMA) x 2.032 GHz",
-        "traffic": None,
-        "flops_per_unit": FLOPS_PER_ESTEP_CT, "unit_of_work": "CT electron step",
+        "achieved": insts / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0,
+        "peak": ISSUE_PEAK_TINST, "unit": "T thread-instructions/s",
+        "peak_kind": "derived: 148 SMs x 4 schedulers x 32 lanes x 2.032 GHz (one warp instruction per "
+                     "scheduler per clock)",
+        "traffic": DRAM_BYTES_PER_ESTEP_CT * steps_per_launch,
+        "traffic_note": "ncu DRAM read+write per CT electron step on the 2e6-history case, scaled by the "
+                        "steps of one launch here",
+        "inst_per_unit": INST_PER_ESTEP_CT, "unit_of_work": "CT electron step",
         "units_per_launch": steps_per_launch, "avg_launch_ms": avg_ms,
+        "fp32": {"flops_per_unit": FLOPS_PER_ESTEP_CT,
+                 "achieved_tflops": flops / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0,
+                 "peak_tflops": FP32_PEAK_TFLOPS},
         "kernel_share_of_transport": float(agg["kernel_ms"][1] / max(agg["kernel_ms"].sum(), 1e-12)),
         "lane_utilisation": {
             "photons_ct": last["counters"]["live_lanes_photon_ct"] / max(32 * last["counters"]["warp_iters_photon_ct"], 1),
@@ -454,7 +467,7 @@ def main():
             t = torch.tensor([te], device=f"cuda:{local}")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             te = float(t.item())
-        d2h = img.nbytes + 80 * waves // args.steps
+        d2h = img.nbytes + CTL_BYTES * waves // args.steps
         e2e = {"value": total_hist / te, "unit": "histories/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
