@@ -150,9 +150,9 @@ def run_reference(args):
     oracle.build()
     p = W.config_thorax_imrt(n_histories=args.histories, seed=SEED)
     threads = os.cpu_count() or 1
-    sample = 200_000
+    sample = 2_000_000                 # about 3 s per step on 16 threads
     for _ in range(args.warmup):
-        oracle.run(p, n_histories=20_000, threads=threads)
+        oracle.run(p, n_histories=200_000, threads=threads)
     t0 = time.perf_counter()
     done = 0
     for k in range(args.steps):
@@ -486,7 +486,7 @@ def main():
         import oracle
         oracle.build()
         threads = os.cpu_count() or 1
-        sample = 300_000
+        sample = 6_000_000            # about 10 s on 16 threads
         v, used, dt = cpu_sample(p, sample, threads)
         cpu = {"value": v, "unit": "histories/s", "cores": used, "kind": "oracle",
                "sample": f"{sample} histories of the same workload ({dt:.1f} s wall on {used} threads)"}
