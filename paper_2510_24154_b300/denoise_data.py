@@ -126,9 +126,11 @@ def bin_image(a, b):
 
 
 def evaluate(net: UNet, src: DoseSource, cases, n_input, n_ref, seed=3, b=8, pixel_mm=0.39, dd=0.02,
-             dta_mm=2.0, threshold=0.10):
+             dta_mm=2.0, threshold=0.10, ladder=()):
     """Gamma pass rates of raw and denoised n_input-history images against
-    n_ref-history references, per case (binned b x b)."""
+    n_ref-history references, per case (binned b x b); with a ladder of
+    history counts, also the raw images' gamma and RMS error at each count
+    (plain Monte Carlo at matched quality)."""
     torch = src.torch
     out = []
     cache = {}
@@ -150,6 +152,27 @@ def evaluate(net: UNet, src: DoseSource, cases, n_input, n_ref, seed=3, b=8, pix
         g_den = gamma(R, torch.tensor(den, device=dev), pixel_mm * b, dd, dta_mm, threshold)
         mask = ref >= threshold * ref.max()
         rel = lambda e: float(np.sqrt(np.mean(((e - ref) / ref.max())[mask] ** 2)))
-        out.append({"case": int(c), "gamma_raw": g_raw, "gamma_denoised": g_den, "rms_raw": rel(raw),
-                    "rms_denoised": rel(den)})
+        row = {"case": int(c), "gamma_raw": g_raw, "gamma_denoised": g_den, "rms_raw": rel(raw),
+               "rms_denoised": rel(den), "ladder": []}
+        for n in ladder:
+            d_n = bin_image(src.image(prob, int(n), 0, seed + 1000).cpu().numpy(), b)
+            row["ladder"].append({"n": float(n), "rms": rel(d_n),
+                                  "gamma": gamma(R, torch.tensor(d_n, device=dev), pixel_mm * b, dd, dta_mm,
+                                                 threshold)})
+        out.append(row)
     return out
+
+
+def matched_histories(ladder_means, target):
+    """Histories at which the mean of a quality measure over the ladder reaches
+    `target`, interpolated in log N; None when the ladder never reaches it.
+    ladder_means: [(n, value)] with value increasing in n (gamma) -- pass
+    negated values for a measure that falls (RMS error)."""
+    pts = sorted(ladder_means)
+    if pts and pts[0][1] >= target:
+        return pts[0][0]
+    for (n0, v0), (n1, v1) in zip(pts, pts[1:]):
+        if v0 < target <= v1:
+            f = (target - v0) / (v1 - v0)
+            return float(np.exp(np.log(n0) + f * (np.log(n1) - np.log(n0))))
+    return None

@@ -29,10 +29,12 @@ def main():
     ap.add_argument("--lr-final", type=float, default=5e-5)
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--bin", type=int, default=8)
+    ap.add_argument("--ladder", type=str, default="1e7,3e7,1e8,3e8,1e9",
+                    help="history counts of plain Monte Carlo images evaluated beside the denoised ones")
     args = ap.parse_args()
     import torch
     from .denoise import UNet
-    from .denoise_data import DoseSource, evaluate, make_pairs, train
+    from .denoise_data import DoseSource, evaluate, make_pairs, matched_histories, train
 
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
@@ -54,8 +56,36 @@ def main():
     ev_net.set_params(params)
     cases = range(100000, 100000 + args.eval)
     t2 = time.perf_counter()
-    res = evaluate(ev_net, src, cases, int(args.n_input), int(args.n_ref), seed=args.seed, b=args.bin)
+    ladder = [float(v) for v in args.ladder.split(",")] if args.ladder else []
+    res = evaluate(ev_net, src, cases, int(args.n_input), int(args.n_ref), seed=args.seed, b=args.bin,
+                   ladder=ladder)
     t_eval = time.perf_counter() - t2
+    # plain Monte Carlo at the denoised image's quality, and the time of each
+    # route per field at the measured transport rate and inference time
+    g_den = float(np.mean([r["gamma_denoised"] for r in res]))
+    e_den = float(np.mean([r["rms_denoised"] for r in res]))
+    lad_g = [(n, float(np.mean([r["ladder"][i]["gamma"] for r in res]))) for i, n in enumerate(ladder)]
+    lad_e = [(n, -float(np.mean([r["ladder"][i]["rms"] for r in res]))) for i, n in enumerate(ladder)]
+    rate = src.histories / max(src.seconds, 1e-9)
+    x = torch.zeros((1, 768, 1024), dtype=torch.float32, device="cuda:0")
+    y = torch.empty_like(x)
+    ev_net.forward(x, y)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    for _ in range(10):
+        ev_net.forward(x, y)
+    torch.cuda.synchronize()
+    t_inf = (time.perf_counter() - t3) / 10
+    n_g, n_e = matched_histories(lad_g, g_den), matched_histories(lad_e, -e_den)
+    matched = {
+        "mc_histories_per_s": rate, "inference_s": t_inf,
+        "denoised_s_per_field": args.n_input / rate + t_inf,
+        "plain_histories_at_denoised_gamma": n_g,
+        "plain_s_per_field_at_denoised_gamma": None if n_g is None else n_g / rate,
+        "plain_histories_at_denoised_rms": n_e,
+        "plain_s_per_field_at_denoised_rms": None if n_e is None else n_e / rate,
+        "ladder_gamma_mean": lad_g, "ladder_rms_mean": [(n, -v) for n, v in lad_e],
+    }
     line = {
         "pairs": args.pairs, "n_input": args.n_input, "n_target": args.n_target, "eval_cases": args.eval,
         "n_ref": args.n_ref, "steps": args.steps, "batch": args.batch, "lr": args.lr, "lr_final": args.lr_final, "bin": args.bin,
@@ -65,6 +95,7 @@ def main():
         "gamma_denoised_mean": float(np.mean([r["gamma_denoised"] for r in res])),
         "rms_raw_mean": float(np.mean([r["rms_raw"] for r in res])),
         "rms_denoised_mean": float(np.mean([r["rms_denoised"] for r in res])),
+        "matched": matched,
         "cases": res, "seconds": {"pairs": t_pairs, "train": t_train, "eval": t_eval},
         "mc_histories_for_pairs": mc_hist, "mc_seconds_for_pairs": mc_s,
     }
