@@ -150,10 +150,16 @@ def evaluate(net: UNet, src: DoseSource, cases, n_input, n_ref, seed=3, b=8, pix
         R = torch.tensor(ref, device=dev)
         g_raw = gamma(R, torch.tensor(raw, device=dev), pixel_mm * b, dd, dta_mm, threshold)
         g_den = gamma(R, torch.tensor(den, device=dev), pixel_mm * b, dd, dta_mm, threshold)
+        # the network need not conserve the image's integral, which the raw
+        # image estimates without bias: the same output rescaled to it
+        den_c = den * (raw.sum() / max(den.sum(), 1e-300))
+        g_den_c = gamma(R, torch.tensor(den_c, device=dev), pixel_mm * b, dd, dta_mm, threshold)
         mask = ref >= threshold * ref.max()
         rel = lambda e: float(np.sqrt(np.mean(((e - ref) / ref.max())[mask] ** 2)))
+        bias = lambda e: float(e[mask].sum() / ref[mask].sum() - 1.0)
         row = {"case": int(c), "gamma_raw": g_raw, "gamma_denoised": g_den, "rms_raw": rel(raw),
-               "rms_denoised": rel(den), "ladder": []}
+               "rms_denoised": rel(den), "gamma_denoised_rescaled": g_den_c, "rms_denoised_rescaled": rel(den_c),
+               "bias_raw": bias(raw), "bias_denoised": bias(den), "ladder": []}
         for n in ladder:
             d_n = bin_image(src.image(prob, int(n), 0, seed + 1000).cpu().numpy(), b)
             row["ladder"].append({"n": float(n), "rms": rel(d_n),

@@ -95,6 +95,10 @@ def main():
         "gamma_denoised_mean": float(np.mean([r["gamma_denoised"] for r in res])),
         "rms_raw_mean": float(np.mean([r["rms_raw"] for r in res])),
         "rms_denoised_mean": float(np.mean([r["rms_denoised"] for r in res])),
+        "gamma_denoised_rescaled_mean": float(np.mean([r["gamma_denoised_rescaled"] for r in res])),
+        "rms_denoised_rescaled_mean": float(np.mean([r["rms_denoised_rescaled"] for r in res])),
+        "bias_raw_mean": float(np.mean([r["bias_raw"] for r in res])),
+        "bias_denoised_mean": float(np.mean([r["bias_denoised"] for r in res])),
         "matched": matched,
         "cases": res, "seconds": {"pairs": t_pairs, "train": t_train, "eval": t_eval},
         "mc_histories_for_pairs": mc_hist, "mc_seconds_for_pairs": mc_s,
