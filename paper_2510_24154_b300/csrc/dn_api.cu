@@ -175,7 +175,6 @@ bool plan_conv(ConvPlan& P, int nsrc, const bf16* const src[2], const int srcC[2
         a.stages = std::max(2, std::min(16, static_cast<int>((205u * 1024u - a.w_bytes) / a.stage_bytes)));
         a.N_tile = N;
         a.tmem_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(6 * N)));
-        a.idesc = dn::idesc_bf16(128, static_cast<uint32_t>(3 * N), 0, 0);
     } else if (n_tiles == 1 && w_region <= 150u * 1024u && resident_ok) {
         int R = 4;
         while (R > 1 && (2 * R * a.N_tile > 512 || R > H)) R >>= 1;
@@ -190,7 +189,15 @@ bool plan_conv(ConvPlan& P, int nsrc, const bf16* const src[2], const int srcC[2
     } else {
         a.rows_per_tile = 0;
     }
-    if (!a.dxn) a.idesc = dn::idesc_bf16(128, static_cast<uint32_t>(a.N_tile), 0, 0);
+    // column slices, one MMA warp each (up to three): a multiple of 16 wide
+    if (a.dxn) {
+        a.n_issue = 3;                          // one column tap per warp
+        a.n_slice = N;
+    } else {
+        a.n_issue = (a.N_tile % 48 == 0) ? 3 : (a.N_tile % 32 == 0) ? 2 : 1;
+        a.n_slice = a.N_tile / a.n_issue;
+    }
+    a.idesc = dn::idesc_bf16(128, static_cast<uint32_t>(a.n_slice), 0, 0);
     a.bias = bias;
     a.relu = relu;
     a.ndst = ndst;
@@ -242,14 +249,14 @@ bool plan_wgrad(WgradPlan& P, const bf16* dz, int Cz, int Co, int nsrc, const bf
     if (a.mode == 0) {
         a.b_region = 32768u;
         a.stage_bytes = 32768u + static_cast<uint32_t>(k) * 16384u;
-        a.tmem_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(k * 64)));
         a.idesc = dn::idesc_bf16(128, 64, 1, 1);
     } else {
         a.b_region = static_cast<uint32_t>(a.G) * 128u * Co * 2u;     // G dz boxes = 32 KB
         a.stage_bytes = a.b_region + 16384u;
-        a.tmem_cols = 64;
         a.idesc = dn::idesc_bf16(128, 64, 1, 1);
     }
+    // one 64-column accumulator per MMA warp: a column tap each, or a share of the K slices
+    a.tmem_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(dn::kWgradIssuers * 64)));
     a.stages = std::max(2, std::min(6, static_cast<int>((200u * 1024u) / a.stage_bytes)));
     a.dW = dW;
     a.err = err;

@@ -6,8 +6,9 @@
 //     the NHWC activation shifted by the tap offset; zero fill supplies the
 //     padding), N = output channels, K = taps x input channels.  A producer
 //     thread streams (activation, weight) tile pairs through a ring of
-//     shared-memory stages with TMA; one thread issues tcgen05.mma into a TMEM
-//     accumulator; four warps read the accumulator back (tcgen05.ld) and apply
+//     shared-memory stages with TMA; one thread per column slice issues
+//     tcgen05.mma into a TMEM accumulator; four warps read the accumulator
+//     back (tcgen05.ld) and apply
 //     the epilogue (bias, ReLU, the ReLU mask of the layer below, the split of
 //     a concatenated input, bf16 rounding).
 //   weight gradient: M = 128 output channels, N = 64 input channels, K =
@@ -96,11 +97,11 @@ __device__ __forceinline__ void epilogue16(const ConvArgs& a, const float* v, in
 // Persistent: CTA b takes output tiles b, b + grid, ...; a tile is 128
 // pixels of one image row x N_tile output channels.  Warp 0 (one lane)
 // streams the (activation, weight) tile pairs of every K step of every tile
-// through a ring of `stages` shared-memory slots; warp 1 (one lane) issues the
-// MMAs of a tile into one of two TMEM accumulators; warps 2-5 drain the other
-// accumulator (tcgen05.ld), so a tile's epilogue overlaps the next tile's
-// MMAs.
-__global__ void __launch_bounds__(320) k_conv(const __grid_constant__ CUtensorMap ta0,
+// through a ring of `stages` shared-memory slots; warps 1 .. n_issue (one lane
+// each) issue the MMAs of a tile, one column slice each, into one of two TMEM
+// accumulators; warps 4-7 and 8-11 drain the accumulators (tcgen05.ld), so a
+// tile's epilogue overlaps the next tile's MMAs.
+__global__ void __launch_bounds__(384) k_conv(const __grid_constant__ CUtensorMap ta0,
                                               const __grid_constant__ CUtensorMap ta1,
                                               const __grid_constant__ CUtensorMap tb0,
                                               const __grid_constant__ CUtensorMap tb1, const ConvArgs a) {
@@ -123,10 +124,10 @@ __global__ void __launch_bounds__(320) k_conv(const __grid_constant__ CUtensorMa
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+            mbar_init(&empty[i], a.n_issue);
         }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&accf[i], 1);
+            mbar_init(&accf[i], a.n_issue);
             mbar_init(&acce[i], 4);
         }
         *abort_flag = 0u;
@@ -191,8 +192,10 @@ __global__ void __launch_bounds__(320) k_conv(const __grid_constant__ CUtensorMa
                 mbar_wait(&full[st], (last / S) & 1, a.err, kErrWaitTail);
             }
         }
-    } else if (warp == 1) {
-        if (lane == 0) {
+    } else if (warp <= 3) {
+        // MMA warps 1 .. n_issue: warp 1 + js issues column slice js of every tile
+        const uint32_t js = static_cast<uint32_t>(warp - 1);
+        if (lane == 0 && warp <= a.n_issue) {
             uint32_t it = 0, lt = 0;
             uint32_t commits[2] = {0u, 0u};
             for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++lt) {
@@ -216,10 +219,12 @@ __global__ void __launch_bounds__(320) k_conv(const __grid_constant__ CUtensorMa
                     const uint32_t sb = sa + a.a_region;
                     const uint32_t row = static_cast<uint32_t>(CW) * 2u;
                     const uint32_t swz = swz_for_row(row);
+                    const uint32_t sbj = sb + js * static_cast<uint32_t>(a.n_slice) * row;
+                    const uint32_t dj = d + js * static_cast<uint32_t>(a.n_slice);
                     for (int kk = 0; kk < CW / 16; ++kk) {
                         const uint64_t da = smem_desc(sa + kk * 32u, 16u, 8u * row, swz);
-                        const uint64_t db = smem_desc(sb + kk * 32u, 16u, 8u * row, swz);
-                        tc_mma(d, da, db, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                        const uint64_t db = smem_desc(sbj + kk * 32u, 16u, 8u * row, swz);
+                        tc_mma(dj, da, db, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
                     }
                     tc_commit(&empty[st]);
                 }
@@ -232,9 +237,9 @@ __global__ void __launch_bounds__(320) k_conv(const __grid_constant__ CUtensorMa
                 if (commits[b]) mbar_wait(&accf[b], (commits[b] - 1) & 1, a.err, kErrWaitTail);
         }
     } else {
-        // epilogue: warps 2-5 drain buffer 0 (even tiles), warps 6-9 buffer 1
+        // epilogue: warps 4-7 drain buffer 0 (even tiles), warps 8-11 buffer 1
         // (odd tiles); TMEM lane quarter q = warp % 4
-        const int g = (warp - 2) >> 2;
+        const int g = (warp - 4) >> 2;
         const int q = warp & 3;
         const int row = q * 32 + lane;
         uint32_t lt = static_cast<uint32_t>(g);
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(320) k_conv(const __grid_constant__ CUtensorMa
 // column shift dx, channel chunk) that feeds the up to k accumulators of the
 // output rows it touches (row r = j - dy with weight tap (dy, dx)), so an
 // input row is fetched (R + k - 1) / R times per output row instead of k.
-__global__ void __launch_bounds__(320) k_conv_res(const __grid_constant__ CUtensorMap ta0,
+__global__ void __launch_bounds__(384) k_conv_res(const __grid_constant__ CUtensorMap ta0,
                                                   const __grid_constant__ CUtensorMap ta1,
                                                   const __grid_constant__ CUtensorMap tb0,
                                                   const __grid_constant__ CUtensorMap tb1, const ConvArgs a) {
@@ -306,10 +311,10 @@ __global__ void __launch_bounds__(320) k_conv_res(const __grid_constant__ CUtens
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+            mbar_init(&empty[i], a.n_issue);
         }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&accf[i], 1);
+            mbar_init(&accf[i], a.n_issue);
             mbar_init(&acce[i], 4);
         }
         mbar_init(wbar, 1);
@@ -384,8 +389,10 @@ __global__ void __launch_bounds__(320) k_conv_res(const __grid_constant__ CUtens
             }
             mbar_wait(wbar, 0, a.err, kErrWaitTail);
         }
-    } else if (warp == 1) {
-        if (lane == 0) {
+    } else if (warp <= 3) {
+        // MMA warps 1 .. n_issue: warp 1 + js issues column slice js of every tile
+        const uint32_t js = static_cast<uint32_t>(warp - 1);
+        if (lane == 0 && warp <= a.n_issue) {
             const bool wok = mbar_wait(wbar, 0, a.err, kErrWaitFull);
             if (!wok) *abort_flag = 1u;
             tc_fence_after();
@@ -417,13 +424,14 @@ __global__ void __launch_bounds__(320) k_conv_res(const __grid_constant__ CUtens
                     for (int dy = 0; dy < k; ++dy) {
                         const int r = j - dy;
                         if (r < 0 || r >= R) continue;
-                        const uint32_t wt = wbase + a.w_off[s_] + ((dy * k + dx) * src.nch + c) * tile_bytes;
+                        const uint32_t wt = wbase + a.w_off[s_] + ((dy * k + dx) * src.nch + c) * tile_bytes +
+                                            js * static_cast<uint32_t>(a.n_slice) * row;
                         const bool first = (dy == 0 && dx == 0 && s_ == 0 && c == 0);
+                        const uint32_t dr = d0 + static_cast<uint32_t>(r) * acc_cols + js * static_cast<uint32_t>(a.n_slice);
                         for (int kk = 0; kk < src.CW / 16; ++kk) {
                             const uint64_t da = smem_desc(sa + kk * 32u, 16u, 8u * row, swz);
                             const uint64_t db = smem_desc(wt + kk * 32u, 16u, 8u * row, swz);
-                            tc_mma(d0 + static_cast<uint32_t>(r) * acc_cols, da, db, a.idesc,
-                                   (first && kk == 0) ? 0u : 1u);
+                            tc_mma(dr, da, db, a.idesc, (first && kk == 0) ? 0u : 1u);
                         }
                     }
                     tc_commit(&empty[st]);
@@ -436,7 +444,7 @@ __global__ void __launch_bounds__(320) k_conv_res(const __grid_constant__ CUtens
                 if (commits[b]) mbar_wait(&accf[b], (commits[b] - 1) & 1, a.err, kErrWaitTail);
         }
     } else {
-        const int g = (warp - 2) >> 2;             // epilogue group = accumulator buffer
+        const int g = (warp - 4) >> 2;             // epilogue group = accumulator buffer
         const int q = warp & 3;
         const int prow = q * 32 + lane;
         uint32_t lt = static_cast<uint32_t>(g);
@@ -485,7 +493,7 @@ __global__ void __launch_bounds__(320) k_conv_res(const __grid_constant__ CUtens
 // neighbouring TMEM lanes with warp shuffles (and a shared-memory exchange
 // across warps), and tiles advance by 126 pixels.  Weights are resident in
 // shared memory as [dy][chunk][(dx, o)][c].
-__global__ void __launch_bounds__(320) k_conv_dxn(const __grid_constant__ CUtensorMap ta0,
+__global__ void __launch_bounds__(384) k_conv_dxn(const __grid_constant__ CUtensorMap ta0,
                                                   const __grid_constant__ CUtensorMap ta1,
                                                   const __grid_constant__ CUtensorMap tb0,
                                                   const __grid_constant__ CUtensorMap tb1, const ConvArgs a) {
@@ -513,10 +521,10 @@ __global__ void __launch_bounds__(320) k_conv_dxn(const __grid_constant__ CUtens
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+            mbar_init(&empty[i], a.n_issue);
         }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&accf[i], 1);
+            mbar_init(&accf[i], a.n_issue);
             mbar_init(&acce[i], 4);
         }
         mbar_init(wbar, 1);
@@ -587,8 +595,10 @@ __global__ void __launch_bounds__(320) k_conv_dxn(const __grid_constant__ CUtens
             }
             mbar_wait(wbar, 0, a.err, kErrWaitTail);
         }
-    } else if (warp == 1) {
-        if (lane == 0) {
+    } else if (warp <= 3) {
+        // MMA warps 1 .. n_issue: warp 1 + js issues column slice js of every tile
+        const uint32_t js = static_cast<uint32_t>(warp - 1);
+        if (lane == 0 && warp <= a.n_issue) {
             if (!mbar_wait(wbar, 0, a.err, kErrWaitFull)) *abort_flag = 1u;
             tc_fence_after();
             uint32_t it = 0, lt = 0;
@@ -615,11 +625,13 @@ __global__ void __launch_bounds__(320) k_conv_dxn(const __grid_constant__ CUtens
                     const uint32_t row = static_cast<uint32_t>(src.CW) * 2u;
                     const uint32_t swz = swz_for_row(row);
                     const uint32_t sa = smem_u32(tiles + st * a.stage_bytes);
-                    const uint32_t wt = wbase + a.w_off[s_] + (dy * src.nch + c) * (static_cast<uint32_t>(N3) * row);
+                    const uint32_t wt = wbase + a.w_off[s_] + (dy * src.nch + c) * (static_cast<uint32_t>(N3) * row) +
+                                        js * static_cast<uint32_t>(a.n_slice) * row;
+                    const uint32_t dj = d + js * static_cast<uint32_t>(a.n_slice);
                     for (int kk = 0; kk < src.CW / 16; ++kk) {
                         const uint64_t da = smem_desc(sa + kk * 32u, 16u, 8u * row, swz);
                         const uint64_t db = smem_desc(wt + kk * 32u, 16u, 8u * row, swz);
-                        tc_mma(d, da, db, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                        tc_mma(dj, da, db, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
                     }
                     tc_commit(&empty[st]);
                 }
@@ -631,7 +643,7 @@ __global__ void __launch_bounds__(320) k_conv_dxn(const __grid_constant__ CUtens
                 if (commits[b]) mbar_wait(&accf[b], (commits[b] - 1) & 1, a.err, kErrWaitTail);
         }
     } else {
-        const int g = (warp - 2) >> 2;          // epilogue group = accumulator buffer
+        const int g = (warp - 4) >> 2;          // epilogue group = accumulator buffer
         const int q = warp & 3;                 // TMEM lane quarter: rows 32q .. 32q+31
         const int r = q * 32 + lane;
         float* gx = xch + g * 128;
@@ -753,12 +765,16 @@ __global__ void __launch_bounds__(128) k_wgrad(const __grid_constant__ CUtensorM
     const int G = a.G;                                   // mode 1: taps per CTA
     const uint32_t slice = 128u * static_cast<uint32_t>(a.Co) * 2u;   // mode 1: bytes of one dz box
 
+    // MMA warps 1-3: with three column taps (mode 0, k = 3) warp 1 + dx owns
+    // accumulator dx; otherwise the 16-pixel K slices of a box are dealt
+    // round-robin to three accumulators that the epilogue adds
+    const bool per_dx = (a.mode == 0 && a.k > 1);
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+            mbar_init(&empty[i], kWgradIssuers);
         }
-        mbar_init(done, 1);
+        mbar_init(done, kWgradIssuers);
         mbar_fence_init();
         tma_prefetch(&tz);
         tma_prefetch(s ? &tx1 : &tx0);
@@ -806,7 +822,8 @@ __global__ void __launch_bounds__(128) k_wgrad(const __grid_constant__ CUtensorM
             const int last = st + ((issued - 1 - st) / S) * S;
             mbar_wait(&full[st], (last / S) & 1, a.err, kErrWaitTail);
         }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp >= 1 && warp <= kWgradIssuers && lane == 0) {
+        const int j = warp - 1;
         const uint32_t a_row = a.mode == 0 ? 128u : static_cast<uint32_t>(a.Co) * 2u;   // bytes per pixel row of A
         const uint32_t a_swz = a_row == 128u ? kSw128 : kSw64;
         const uint32_t a_lbo = a.mode == 0 ? 16384u : slice;
@@ -816,14 +833,15 @@ __global__ void __launch_bounds__(128) k_wgrad(const __grid_constant__ CUtensorM
             tc_fence_after();
             const uint32_t sa = smem_u32(tiles + st * a.stage_bytes);
             const uint32_t sb = sa + a.b_region;
-            const int nacc = a.mode == 0 ? a.k : 1;
-            for (int dx = 0; dx < nacc; ++dx) {
-                for (int kk = 0; kk < 8; ++kk) {
-                    // 16 pixels = two 8-row groups
-                    const uint64_t da = smem_desc(sa + kk * 16u * a_row, a_lbo, 8u * a_row, a_swz);
-                    const uint64_t db = smem_desc(sb + dx * 16384u + kk * 2048u, 16384u, 1024u, kSw128);
-                    tc_mma(tmem + static_cast<uint32_t>(dx * 64), da, db, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                }
+            // this warp's accumulator and K slices: all 8 of tap dx = j, or slices j, j + 3, ...
+            const int dx = per_dx ? j : 0;
+            const int kk0 = per_dx ? 0 : j, kstep = per_dx ? 1 : kWgradIssuers;
+            const uint32_t acc = tmem + static_cast<uint32_t>(j * 64);
+            for (int kk = kk0; kk < 8; kk += kstep) {
+                // 16 pixels = two 8-row groups
+                const uint64_t da = smem_desc(sa + kk * 16u * a_row, a_lbo, 8u * a_row, a_swz);
+                const uint64_t db = smem_desc(sb + dx * 16384u + kk * 2048u, 16384u, 1024u, kSw128);
+                tc_mma(acc, da, db, a.idesc, (i > 0 || kk > kk0) ? 1u : 0u);
             }
             tc_commit(&empty[st]);
         }
@@ -850,11 +868,20 @@ __global__ void __launch_bounds__(128) k_wgrad(const __grid_constant__ CUtensorM
         tap_x0 = t % a.k;
         ntap = (t < a.k * a.k) ? 1 : 0;
     }
-    const int nacc = a.mode == 0 ? a.k : 1;
+    const int nacc = per_dx ? a.k : 1;
     for (int dx = 0; dx < nacc; ++dx) {
         for (int c = 0; c < 64; c += 16) {
             float v[16];
             tmem_ld16(tbase + static_cast<uint32_t>(dx * 64 + c), v);
+            if (!per_dx) {
+                // the three K-slice accumulators of the single tap set
+                for (int q = 1; q < kWgradIssuers; ++q) {
+                    float w[16];
+                    tmem_ld16(tbase + static_cast<uint32_t>(q * 64 + c), w);
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) v[jj] += w[jj];
+                }
+            }
             if (!ok || co >= a.Co || ntap == 0) continue;
             const int tx_ = a.mode == 0 ? dx : tap_x0;
             float* dst = a.dW + ((static_cast<size_t>(co) * a.k + tap_y) * a.k + tx_) * a.ci_total + a.src_coff[s];
@@ -1149,19 +1176,19 @@ cudaError_t launch_conv(const CUtensorMap* ta, const CUtensorMap* tb, const Conv
         const int grid = static_cast<int>(std::min<long long>(total, a.grid));
         const size_t smem =
             1024 + a.w_bytes + static_cast<size_t>(a.stages) * a.stage_bytes + (2 * a.stages + 5) * 8 + 2 * 2 * 4 * 16 * 4 + 16;
-        k_conv_dxn<<<grid, 320, smem, s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0], tb[a.nsrc > 1 ? 1 : 0], a);
+        k_conv_dxn<<<grid, 384, smem, s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0], tb[a.nsrc > 1 ? 1 : 0], a);
         return cudaGetLastError();
     }
     if (a.rows_per_tile > 0) {
         const long long total = static_cast<long long>(segs) * ((a.H + a.rows_per_tile - 1) / a.rows_per_tile) * a.Nb;
         const int grid = static_cast<int>(std::min<long long>(total, a.grid));
         const size_t smem = 1024 + a.w_bytes + static_cast<size_t>(a.stages) * a.stage_bytes + (2 * a.stages + 5) * 8 + 16;
-        k_conv_res<<<grid, 320, smem, s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0], tb[a.nsrc > 1 ? 1 : 0], a);
+        k_conv_res<<<grid, 384, smem, s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0], tb[a.nsrc > 1 ? 1 : 0], a);
         return cudaGetLastError();
     }
     const long long total = static_cast<long long>(segs) * a.H * a.Nb * ((a.N + a.N_tile - 1) / a.N_tile);
     const int grid = static_cast<int>(std::min<long long>(total, a.grid));
-    k_conv<<<grid, 320, conv_smem(a.stages, a.stage_bytes), s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0],
+    k_conv<<<grid, 384, conv_smem(a.stages, a.stage_bytes), s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0],
                                                                  tb[a.nsrc > 1 ? 1 : 0], a);
     return cudaGetLastError();
 }

@@ -35,7 +35,12 @@ struct ConvArgs {
     int dxn;                    // column taps in N (3x3, N <= 64): tiles of 126 pixels
     uint32_t w_bytes, w_bytes_real, w_off[2];
     uint32_t stage_bytes, a_region;
-    uint32_t idesc;
+    uint32_t idesc;             // instruction descriptor of one MMA: M = 128, N = n_slice
+    // the N columns of a tile are split into n_issue slices of n_slice, each
+    // issued by its own warp: a warp issues one tcgen05.mma per ~170 cycles
+    // whatever its N, so narrow tiles need several issuers to keep the tensor
+    // core busy
+    int n_issue, n_slice;
     const float* bias;          // [N] or null
     int relu;
     int ndst, dst_split;        // channels [0, split) -> dst[0], [split, N) -> dst[1]
@@ -44,6 +49,9 @@ struct ConvArgs {
     const __nv_bfloat16* mask[2];   // if set: zero where mask <= 0 (same layout as dst)
     unsigned* err;
 };
+
+// MMA-issuing warps of the weight-gradient kernel (see k_wgrad).
+constexpr int kWgradIssuers = 3;
 
 // Weight gradient: dW[co][dy][dx][coff_s + c] += sum over pixels of
 // dz[n,y,x,co] * src_s[n, y+dy-p, x+dx-p, c].  mode 0: M = 128 output
