@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--histories", type=int, default=HIST_PER_STEP)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--bank-capacity", type=int, default=1 << 24, help="particles per bank (0: library default)")
+    ap.add_argument("--bank-capacity", type=int, default=1 << 26,
+                    help="particles per bank (0: library default); 2^26 = 25.8 GB of banks, 7 waves per step")
     ap.add_argument("--regs-variant", default="", help="CTAs/SM build per transport kernel, e.g. 3,3,3,3")
     ap.add_argument("--no-batched", action="store_true", help="skip the 25-field batched-plan leg")
     ap.add_argument("--batched-scale", type=float, default=1.0, help="scale of the batched plan's history counts")
