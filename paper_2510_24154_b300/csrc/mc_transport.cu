@@ -318,38 +318,56 @@ __device__ __forceinline__ bool photon_ct_event(const Params& P, const float2* t
     int cx = min(max(__float2int_rd((p.x - P.ox) / (M * P.vx)), 0), P.mgx - 1);
     int cy = min(max(__float2int_rd((p.y - P.oy) / (M * P.vy)), 0), P.mgy - 1);
     int cz = min(max(__float2int_rd((p.z - P.oz) / (M * P.vz)), 0), P.mgz - 1);
-    float Sc = 0.0f;
+    // 3D-DDA in the flight's path length t from its start: tx, ty, tz are the
+    // values of t at the current cell's exit plane on each axis (the last
+    // cell along an axis may be cut short by the CT edge)
+    const float x0 = p.x, y0 = p.y, z0 = p.z;
+    const int sx = (p.u > 0.0f) ? 1 : -1, sy = (p.v > 0.0f) ? 1 : -1, sz = (p.w > 0.0f) ? 1 : -1;
+    auto exit_t = [&](int c, int s, int n, float o, float v, float org, float dir, float inv) {
+        if (dir == 0.0f) return INFINITY;
+        const int face = (s > 0) ? min((c + 1) * M, n) : c * M;
+        return (o + face * v - org) * inv;
+    };
+    float tx = exit_t(cx, sx, P.nx, P.ox, P.vx, x0, p.u, iu);
+    float ty = exit_t(cy, sy, P.ny, P.oy, P.vy, y0, p.v, iv);
+    float tz = exit_t(cz, sz, P.nz, P.oz, P.vz, z0, p.w, iw);
+    float t = 0.0f, Sc = 0.0f;
     const int guard = P.mgx + P.mgy + P.mgz + 3;
     bool inside = false;
     for (int it = 0; it < guard; ++it) {
         const float2 g = grid[(cz * P.mgy + cy) * P.mgx + cx];
         Sc = fmaxf(g.x * mul, g.y * mub);
-        float dx = INFINITY, dy = INFINITY, dz = INFINITY;
-        if (p.u > 0.0f) dx = (P.ox + min((cx + 1) * M, P.nx) * P.vx - p.x) * iu;
-        else if (p.u < 0.0f) dx = (P.ox + cx * M * P.vx - p.x) * iu;
-        if (p.v > 0.0f) dy = (P.oy + min((cy + 1) * M, P.ny) * P.vy - p.y) * iv;
-        else if (p.v < 0.0f) dy = (P.oy + cy * M * P.vy - p.y) * iv;
-        if (p.w > 0.0f) dz = (P.oz + min((cz + 1) * M, P.nz) * P.vz - p.z) * iw;
-        else if (p.w < 0.0f) dz = (P.oz + cz * M * P.vz - p.z) * iw;
-        float d = dx;
+        float tn = tx;
         int ax = 0;
-        if (dy < d) { d = dy; ax = 1; }
-        if (dz < d) { d = dz; ax = 2; }
-        d = fmaxf(d, 0.0f);
+        if (ty < tn) { tn = ty; ax = 1; }
+        if (tz < tn) { tn = tz; ax = 2; }
+        const float d = fmaxf(tn - t, 0.0f);
         if (tau < Sc * d) {
-            const float s = tau / Sc;
-            p.x += s * p.u; p.y += s * p.v; p.z += s * p.w;
+            t += tau / Sc;
             inside = true;
             break;
         }
         tau -= Sc * d;
-        p.x += d * p.u; p.y += d * p.v; p.z += d * p.w;
+        t = fmaxf(tn, t);
         bool out;
-        if (ax == 0) { cx += (p.u > 0.0f) ? 1 : -1; out = cx < 0 || cx >= P.mgx; }
-        else if (ax == 1) { cy += (p.v > 0.0f) ? 1 : -1; out = cy < 0 || cy >= P.mgy; }
-        else { cz += (p.w > 0.0f) ? 1 : -1; out = cz < 0 || cz >= P.mgz; }
+        if (ax == 0) {
+            cx += sx;
+            out = cx < 0 || cx >= P.mgx;
+            tx = exit_t(cx, sx, P.nx, P.ox, P.vx, x0, p.u, iu);
+        } else if (ax == 1) {
+            cy += sy;
+            out = cy < 0 || cy >= P.mgy;
+            ty = exit_t(cy, sy, P.ny, P.oy, P.vy, y0, p.v, iv);
+        } else {
+            cz += sz;
+            out = cz < 0 || cz >= P.mgz;
+            tz = exit_t(cz, sz, P.nz, P.oz, P.vz, z0, p.w, iw);
+        }
         if (out) break;
     }
+    p.x = fmaf(t, p.u, x0);
+    p.y = fmaf(t, p.v, y0);
+    p.z = fmaf(t, p.w, z0);
     if (!inside) {
         move = transfer_to_epid(P, p, a, s_events, true);
         return false;
