@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--bank-capacity", type=int, default=1 << 26,
                     help="particles per bank (0: library default); 2^26 = 25.8 GB of banks, 7 waves per step")
     ap.add_argument("--regs-variant", default="", help="CTAs/SM build per transport kernel, e.g. 3,3,3,3")
+    ap.add_argument("--primaries-per-wave", type=int, default=0, help="new histories per wave (0: a quarter bank)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 25-field batched-plan leg")
     ap.add_argument("--batched-scale", type=float, default=1.0, help="scale of the batched plan's history counts")
     ap.add_argument("--no-denoiser", action="store_true", help="skip the U-Net denoiser leg")
@@ -349,6 +350,8 @@ def main():
     p = W.config_thorax_imrt(n_histories=args.histories, seed=SEED)
     N = args.histories
     extra = {"bank_capacity": args.bank_capacity} if args.bank_capacity else {}
+    if args.primaries_per_wave:
+        extra["primaries_per_wave"] = args.primaries_per_wave
     if args.regs_variant:
         extra["regs_variant"] = [int(v) for v in args.regs_variant.split(",")]
     sim = Simulator(p.physics, device=local, time_kernels=1, **extra)
