@@ -86,7 +86,8 @@ typedef struct mc_config {
     int block_size;               /* threads per CTA of the transport kernels (multiple of 32), 0 = 256 */
     int ctas_per_sm;              /* resident CTAs per SM for the persistent kernels, 0 = occupancy limit */
     uint32_t bank_capacity;       /* particles per bank, 0 = 1<<23 */
-    uint32_t primaries_per_wave;  /* new histories per transport wave, 0 = bank_capacity / 4 */
+    uint32_t primaries_per_wave;  /* new histories per transport wave, 0 = bank_capacity / 4; a wave admits
+                                     no more than half a bank or the room left in the CT-photon bank */
     int time_kernels;             /* 1: time every transport launch with CUDA events (mc_run_stats.kernel_ms) */
     int use_graph;                /* 1: each run is one CUDA-graph launch whose waves loop on the device
                                      (a conditional while-node); 0: waves are driven from the host */

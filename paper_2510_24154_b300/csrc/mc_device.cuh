@@ -5,8 +5,9 @@
 // the EPID, electrons in the EPID.  Each transport kernel is persistent: a
 // warp keeps one particle per lane, advances every live lane by one event per
 // iteration and refills dead lanes from its input bank with one atomic per
-// warp, so the warp stays full while work remains.  Secondaries are compacted
-// into the banks of their event type with a warp ballot and a prefix count.
+// warp on one of the bank's 8 segment counters, so the warp stays full while
+// work remains.  Secondaries are compacted into the banks of their event type
+// with warp ballots and a prefix count.
 //
 // Random numbers: draw d of the particle with history id h and ordinal o is
 // word d mod 4 of Philox4x32-10 (Salmon et al., SC'11) at counter
