@@ -99,9 +99,11 @@ def make_pairs(src: DoseSource, cases, n_input, n_target, seed=3):
     return torch.stack(xs), torch.stack(ts), np.array(scales)
 
 
-def train(net: UNet, X, T, steps, lr, batch, seed=0, log_every=0, lr_final=None):
+def train(net: UNet, X, T, steps, lr, batch, seed=0, log_every=0, lr_final=None, augment=False):
     """Adam on random mini-batches of the pairs, the learning rate decaying
-    from lr to lr_final on a half cosine; returns the loss history."""
+    from lr to lr_final on a half cosine; returns the loss history.  With
+    augment, each mini-batch is mirrored along rows and/or columns at random
+    (input and target alike: the noise has no preferred orientation)."""
     import math
     import torch
     lr_final = lr if lr_final is None else lr_final
@@ -110,8 +112,13 @@ def train(net: UNet, X, T, steps, lr, batch, seed=0, log_every=0, lr_final=None)
     losses = []
     for it in range(steps):
         idx = torch.as_tensor(rng.choice(n, size=batch, replace=n < batch), device=X.device)
-        xb = X.index_select(0, idx).contiguous()
-        tb = T.index_select(0, idx).contiguous()
+        xb = X.index_select(0, idx)
+        tb = T.index_select(0, idx)
+        if augment:
+            dims = [d for d, f in ((1, rng.random() < 0.5), (2, rng.random() < 0.5)) if f]
+            if dims:
+                xb, tb = torch.flip(xb, dims), torch.flip(tb, dims)
+        xb, tb = xb.contiguous(), tb.contiguous()
         want = log_every and (it % log_every == 0 or it == steps - 1)
         lr_t = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * it / max(steps - 1, 1)))
         loss = net.train_step(xb, tb, lr_t, want_loss=bool(want))

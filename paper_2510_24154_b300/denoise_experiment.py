@@ -29,6 +29,7 @@ def main():
     ap.add_argument("--lr-final", type=float, default=5e-5)
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--bin", type=int, default=8)
+    ap.add_argument("--augment", action="store_true", help="random row/column mirroring of the training pairs")
     ap.add_argument("--ladder", type=str, default="1e7,3e7,1e8,3e8,1e9",
                     help="history counts of plain Monte Carlo images evaluated beside the denoised ones")
     args = ap.parse_args()
@@ -45,7 +46,7 @@ def main():
     net = UNet(768, 1024, batch=args.batch, levels=4, base_channels=32, seed=args.seed)
     t1 = time.perf_counter()
     losses = train(net, X, T, args.steps, args.lr, args.batch, seed=args.seed, log_every=max(args.steps // 20, 1),
-                   lr_final=args.lr_final)
+                   lr_final=args.lr_final, augment=args.augment)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
     del X, T
@@ -88,7 +89,7 @@ def main():
     }
     line = {
         "pairs": args.pairs, "n_input": args.n_input, "n_target": args.n_target, "eval_cases": args.eval,
-        "n_ref": args.n_ref, "steps": args.steps, "batch": args.batch, "lr": args.lr, "lr_final": args.lr_final, "bin": args.bin,
+        "n_ref": args.n_ref, "steps": args.steps, "augment": args.augment, "batch": args.batch, "lr": args.lr, "lr_final": args.lr_final, "bin": args.bin,
         "gamma": f"2 %/2 mm global, 10 % threshold, binned {args.bin}x{args.bin} ({0.39 * args.bin:.2f} mm)",
         "loss_first": losses[0][1], "loss_last": losses[-1][1], "losses": losses,
         "gamma_raw_mean": float(np.mean([r["gamma_raw"] for r in res])),
