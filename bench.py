@@ -481,6 +481,22 @@ def main():
     denoiser = None
     if not args.no_denoiser:
         denoiser = denoiser_leg(args, local, barrier)
+    # the metric's two routes per field on this workload: plain Monte Carlo to
+    # 1 % per pixel, and a 1e7-history image plus one denoiser inference
+    # (both timed here); the image quality of the second route is the one
+    # measured by `python -m paper_2510_24154_b300.denoise_experiment
+    # --n-input 1e7` (8 held-out cases, 2 %/2 mm on 3.1 mm bins), quoted
+    denoised_vs_plain = None
+    if denoiser is not None:
+        denoised_vs_plain = {
+            "plain_s_per_field_1pct": n_1pct / per_gpu_rate,
+            "denoised_s_per_field": 1e7 / per_gpu_rate + denoiser["forward_ms"] / 1e3 / args.dn_batch,
+            "denoised_input_histories": 1e7,
+            "quality_quoted": {"gamma_2pct_2mm": {"raw_1e7": 0.815, "denoised": 0.58, "plain_1e9": 0.976},
+                               "rms_of_max": {"raw_1e7": 0.187, "denoised": 0.054},
+                               "plain_histories_matching_denoised_rms": 1.3e8,
+                               "plain_histories_matching_denoised_gamma": 1e7},
+        }
     anthro = None
     if not args.no_anthro:
         anthro = anthropomorphic_leg(args, Simulator, W, extra, stream, local, rank, dist, barrier)
@@ -505,7 +521,8 @@ def main():
                        "parallelism": f"history shards x{ws}, no collective"},
             "s_per_field_1pct": n_1pct / per_gpu_rate, "u_at_step": u, "histories_for_1pct": n_1pct,
             "roofline": roofline, "memory_roofline": memory_roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "batched_plan": batched, "denoiser": denoiser, "anthropomorphic": anthro,
+            "batched_plan": batched, "denoiser": denoiser, "denoised_vs_plain": denoised_vs_plain,
+            "anthropomorphic": anthro,
             "events_per_history": {k: last["counters"][k] / N for k in
                                    ("flights_ct", "real_ct", "compton", "photo", "pair", "esteps_ct", "esteps_epid",
                                     "moller", "brem", "electrons", "primaries_at_epid")},
