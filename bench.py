@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--bank-capacity", type=int, default=1 << 26,
-                    help="particles per bank (0: library default); 2^26 = 25.8 GB of banks, 7 waves per step")
+                    help="particles per bank (0: library default); 2^26 = 25.8 GB of banks, 9 waves per step")
     ap.add_argument("--regs-variant", default="", help="CTAs/SM build per transport kernel, e.g. 3,3,3,3")
     ap.add_argument("--primaries-per-wave", type=int, default=0, help="new histories per wave (0: a quarter bank)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 25-field batched-plan leg")
