@@ -174,10 +174,13 @@ def test_bitwise_reproducible_across_runs_and_launch_shapes():
     _, st1, t1 = G.gpu_run(p)
     _, st2, t2 = G.gpu_run(p)
     _, st3, t3 = G.gpu_run(p, block_size=128, bank_capacity=1 << 18, primaries_per_wave=1 << 14)
-    assert np.array_equal(t1, t2) and np.array_equal(t1, t3)
+    # a wave size far above the bank: each wave admits at most half a bank
+    _, st4, t4 = G.gpu_run(p, bank_capacity=1 << 14, primaries_per_wave=1 << 22)
+    assert np.array_equal(t1, t2) and np.array_equal(t1, t3) and np.array_equal(t1, t4)
+    assert st4["error_flags"] == 0 and st4["waves"] > st1["waves"]
     physics = oracle.COUNTER_NAMES          # the execution counters depend on the launch shape
-    assert all(st1["counters"][k] == st3["counters"][k] for k in physics)
-    assert st1["e_src"] == st3["e_src"] and st1["e_ct"] == st3["e_ct"]
+    assert all(st1["counters"][k] == st3["counters"][k] == st4["counters"][k] for k in physics)
+    assert st1["e_src"] == st3["e_src"] == st4["e_src"] and st1["e_ct"] == st3["e_ct"] == st4["e_ct"]
 
 
 def test_checkpoint_resume_is_bitwise_identical():
