@@ -506,7 +506,7 @@ def main():
         import oracle
         oracle.build()
         threads = os.cpu_count() or 1
-        sample = 6_000_000            # about 10 s on 16 threads
+        sample = 12_000_000           # about 11 s on 16 threads
         v, used, dt = cpu_sample(p, sample, threads)
         cpu = {"value": v, "unit": "histories/s", "cores": used, "kind": "oracle",
                "sample": f"{sample} histories of the same workload ({dt:.1f} s wall on {used} threads)"}
