@@ -174,7 +174,11 @@ bool plan_conv(ConvPlan& P, int nsrc, const bf16* const src[2], const int srcC[2
         a.stage_bytes = a.a_region;
         a.stages = std::max(2, std::min(16, static_cast<int>((205u * 1024u - a.w_bytes) / a.stage_bytes)));
         a.N_tile = N;
-        a.tmem_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(6 * N)));
+        // as many accumulator buffers (each with its own epilogue warpgroup)
+        // as TMEM holds: 4 of 128 columns for N = 32, 2 of 256 for N = 64
+        a.buf_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(3 * N)));
+        a.epi_groups = std::min(dn::kDxnMaxGroups, 512 / a.buf_cols);
+        a.tmem_cols = a.epi_groups * a.buf_cols;
     } else if (n_tiles == 1 && w_region <= 150u * 1024u && resident_ok) {
         int R = 4;
         while (R > 1 && (2 * R * a.N_tile > 512 || R > H)) R >>= 1;

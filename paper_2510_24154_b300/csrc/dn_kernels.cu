@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(384) k_conv_res(const __grid_constant__ CUtens
 // neighbouring TMEM lanes with warp shuffles (and a shared-memory exchange
 // across warps), and tiles advance by 126 pixels.  Weights are resident in
 // shared memory as [dy][chunk][(dx, o)][c].
-__global__ void __launch_bounds__(384) k_conv_dxn(const __grid_constant__ CUtensorMap ta0,
+__global__ void __launch_bounds__(kDxnMaxThreads) k_conv_dxn(const __grid_constant__ CUtensorMap ta0,
                                                   const __grid_constant__ CUtensorMap ta1,
                                                   const __grid_constant__ CUtensorMap tb0,
                                                   const __grid_constant__ CUtensorMap tb1, const ConvArgs a) {
@@ -503,11 +503,12 @@ __global__ void __launch_bounds__(384) k_conv_dxn(const __grid_constant__ CUtens
     const int S = a.stages;
     uint64_t* full = reinterpret_cast<uint64_t*>(tiles + S * a.stage_bytes);
     uint64_t* empty = full + S;
+    const int GE = a.epi_groups;                          // accumulator buffers = epilogue warpgroups
     uint64_t* accf = empty + S;
-    uint64_t* acce = accf + 2;
-    uint64_t* wbar = acce + 2;
-    float* xch = reinterpret_cast<float*>(wbar + 1);     // [2 groups][2 sides][4 warps][16]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(xch + 2 * 2 * 4 * 16);
+    uint64_t* acce = accf + GE;
+    uint64_t* wbar = acce + GE;
+    float* xch = reinterpret_cast<float*>(wbar + 1);     // [groups][2 sides][4 warps][16]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(xch + GE * 2 * 4 * 16);
     volatile uint32_t* abort_flag = tslot + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -523,7 +524,7 @@ __global__ void __launch_bounds__(384) k_conv_dxn(const __grid_constant__ CUtens
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], a.n_issue);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < GE; ++i) {
             mbar_init(&accf[i], a.n_issue);
             mbar_init(&acce[i], 4);
         }
@@ -602,16 +603,17 @@ __global__ void __launch_bounds__(384) k_conv_dxn(const __grid_constant__ CUtens
             if (!mbar_wait(wbar, 0, a.err, kErrWaitFull)) *abort_flag = 1u;
             tc_fence_after();
             uint32_t it = 0, lt = 0;
-            uint32_t commits[2] = {0u, 0u};
+            uint32_t commits[kDxnMaxGroups] = {0u, 0u, 0u, 0u};
             const uint32_t wbase = smem_u32(wsm);
+            const uint32_t ge = static_cast<uint32_t>(GE);
             for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++lt) {
-                const uint32_t buf = lt & 1u;
-                if (lt >= 2 && !mbar_wait(&acce[buf], ((lt >> 1) - 1) & 1, a.err, kErrWaitEmpty)) {
+                const uint32_t buf = lt % ge;
+                if (lt >= ge && !mbar_wait(&acce[buf], ((lt / ge) - 1) & 1, a.err, kErrWaitEmpty)) {
                     *abort_flag = 1u;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem + buf * static_cast<uint32_t>(a.tmem_cols / 2);
+                const uint32_t d = tmem + buf * static_cast<uint32_t>(a.buf_cols);
                 for (int i = 0; i < steps; ++i, ++it) {
                     const uint32_t st = it % S;
                     if (!mbar_wait(&full[st], (it / S) & 1, a.err, kErrWaitFull)) {
@@ -639,7 +641,7 @@ __global__ void __launch_bounds__(384) k_conv_dxn(const __grid_constant__ CUtens
                 ++commits[buf];
                 if (*abort_flag) break;
             }
-            for (int b = 0; b < 2; ++b)
+            for (int b = 0; b < GE; ++b)
                 if (commits[b]) mbar_wait(&accf[b], (commits[b] - 1) & 1, a.err, kErrWaitTail);
         }
     } else {
@@ -647,10 +649,11 @@ __global__ void __launch_bounds__(384) k_conv_dxn(const __grid_constant__ CUtens
         const int q = warp & 3;                 // TMEM lane quarter: rows 32q .. 32q+31
         const int r = q * 32 + lane;
         float* gx = xch + g * 128;
+        const uint32_t ge = static_cast<uint32_t>(GE);
         uint32_t lt = static_cast<uint32_t>(g);
-        for (int t = blockIdx.x + g * gridDim.x; t < total; t += 2 * gridDim.x, lt += 2) {
-            const uint32_t buf = lt & 1u;
-            const bool ok = mbar_wait(&accf[buf], (lt >> 1) & 1, a.err, kErrWaitDone);
+        for (int t = blockIdx.x + g * gridDim.x; t < total; t += GE * gridDim.x, lt += ge) {
+            const uint32_t buf = lt % ge;
+            const bool ok = mbar_wait(&accf[buf], (lt / ge) & 1, a.err, kErrWaitDone);
             tc_fence_after();
             __syncwarp();
             if (!ok || *abort_flag) {
@@ -662,7 +665,7 @@ __global__ void __launch_bounds__(384) k_conv_dxn(const __grid_constant__ CUtens
             const int x = x0 - 1 + r;
             const bool valid = r >= 1 && r <= 126 && x < a.W;
             const size_t pix = (static_cast<size_t>(n) * a.H + y) * a.W + (valid ? x : 0);
-            const uint32_t tbase = tmem + buf * static_cast<uint32_t>(a.tmem_cols / 2) +
+            const uint32_t tbase = tmem + buf * static_cast<uint32_t>(a.buf_cols) +
                                    (static_cast<uint32_t>(q * 32) << 16);
             for (int c = 0; c < N; c += 16) {
                 float v0[16], v1[16], v2[16], o[16];
@@ -1174,9 +1177,10 @@ cudaError_t launch_conv(const CUtensorMap* ta, const CUtensorMap* tb, const Conv
     if (a.dxn) {
         const long long total = static_cast<long long>((a.W + 125) / 126) * a.H * a.Nb;
         const int grid = static_cast<int>(std::min<long long>(total, a.grid));
-        const size_t smem =
-            1024 + a.w_bytes + static_cast<size_t>(a.stages) * a.stage_bytes + (2 * a.stages + 5) * 8 + 2 * 2 * 4 * 16 * 4 + 16;
-        k_conv_dxn<<<grid, 384, smem, s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0], tb[a.nsrc > 1 ? 1 : 0], a);
+        const size_t smem = 1024 + a.w_bytes + static_cast<size_t>(a.stages) * a.stage_bytes +
+                            (2 * a.stages + 2 * a.epi_groups + 1) * 8 + a.epi_groups * 2 * 4 * 16 * 4 + 16;
+        k_conv_dxn<<<grid, 32 * (4 + 4 * a.epi_groups), smem, s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0],
+                                                                 tb[a.nsrc > 1 ? 1 : 0], a);
         return cudaGetLastError();
     }
     if (a.rows_per_tile > 0) {
