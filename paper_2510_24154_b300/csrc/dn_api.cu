@@ -177,7 +177,7 @@ bool plan_conv(ConvPlan& P, int nsrc, const bf16* const src[2], const int srcC[2
         // as many accumulator buffers (each with its own epilogue warpgroup)
         // as TMEM holds: 4 of 128 columns for N = 32, 2 of 256 for N = 64
         a.buf_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(3 * N)));
-        a.epi_groups = std::min(dn::kDxnMaxGroups, 512 / a.buf_cols);
+        a.epi_groups = std::min(dn::kConvMaxGroups, 512 / a.buf_cols);
         a.tmem_cols = a.epi_groups * a.buf_cols;
     } else if (n_tiles == 1 && w_region <= 150u * 1024u && resident_ok) {
         int R = 4;
@@ -192,6 +192,9 @@ bool plan_conv(ConvPlan& P, int nsrc, const bf16* const src[2], const int srcC[2
         a.tmem_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(2 * R * a.N_tile)));
     } else {
         a.rows_per_tile = 0;
+        a.buf_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(a.N_tile)));
+        a.epi_groups = std::min(dn::kConvMaxGroups, 512 / a.buf_cols);
+        a.tmem_cols = a.epi_groups * a.buf_cols;
     }
     // column slices, one MMA warp each (up to three): a multiple of 16 wide
     if (a.dxn) {

@@ -101,7 +101,7 @@ __device__ __forceinline__ void epilogue16(const ConvArgs& a, const float* v, in
 // each) issue the MMAs of a tile, one column slice each, into one of two TMEM
 // accumulators; warps 4-7 and 8-11 drain the accumulators (tcgen05.ld), so a
 // tile's epilogue overlaps the next tile's MMAs.
-__global__ void __launch_bounds__(384) k_conv(const __grid_constant__ CUtensorMap ta0,
+__global__ void __launch_bounds__(kConvMaxThreads) k_conv(const __grid_constant__ CUtensorMap ta0,
                                               const __grid_constant__ CUtensorMap ta1,
                                               const __grid_constant__ CUtensorMap tb0,
                                               const __grid_constant__ CUtensorMap tb1, const ConvArgs a) {
@@ -110,9 +110,10 @@ __global__ void __launch_bounds__(384) k_conv(const __grid_constant__ CUtensorMa
     const int S = a.stages;
     uint64_t* full = reinterpret_cast<uint64_t*>(tiles + S * a.stage_bytes);
     uint64_t* empty = full + S;
-    uint64_t* accf = empty + S;      // [2] accumulator ready (MMA -> epilogue)
-    uint64_t* acce = accf + 2;       // [2] accumulator drained (epilogue -> MMA)
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
+    const int GE = a.epi_groups;     // accumulator buffers = epilogue warpgroups
+    uint64_t* accf = empty + S;      // [GE] accumulator ready (MMA -> epilogue)
+    uint64_t* acce = accf + GE;      // [GE] accumulator drained (epilogue -> MMA)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + GE);
     volatile uint32_t* abort_flag = tslot + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(384) k_conv(const __grid_constant__ CUtensorMa
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], a.n_issue);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < GE; ++i) {
             mbar_init(&accf[i], a.n_issue);
             mbar_init(&acce[i], 4);
         }
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(384) k_conv(const __grid_constant__ CUtensorMa
             tma_prefetch(&tb1);
         }
     }
-    if (warp == 1) tmem_alloc(tslot, static_cast<uint32_t>(2 * a.tmem_cols));
+    if (warp == 1) tmem_alloc(tslot, static_cast<uint32_t>(a.tmem_cols));
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -197,15 +198,16 @@ __global__ void __launch_bounds__(384) k_conv(const __grid_constant__ CUtensorMa
         const uint32_t js = static_cast<uint32_t>(warp - 1);
         if (lane == 0 && warp <= a.n_issue) {
             uint32_t it = 0, lt = 0;
-            uint32_t commits[2] = {0u, 0u};
+            uint32_t commits[kConvMaxGroups] = {0u, 0u, 0u, 0u};
+            const uint32_t ge = static_cast<uint32_t>(GE);
             for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++lt) {
-                const uint32_t buf = lt & 1u;
-                if (lt >= 2 && !mbar_wait(&acce[buf], ((lt >> 1) - 1) & 1, a.err, kErrWaitEmpty)) {
+                const uint32_t buf = lt % ge;
+                if (lt >= ge && !mbar_wait(&acce[buf], ((lt / ge) - 1) & 1, a.err, kErrWaitEmpty)) {
                     *abort_flag = 1u;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem + buf * static_cast<uint32_t>(a.tmem_cols);
+                const uint32_t d = tmem + buf * static_cast<uint32_t>(a.buf_cols);
                 for (int i = 0; i < a.nk; ++i, ++it) {
                     const uint32_t st = it % S;
                     if (!mbar_wait(&full[st], (it / S) & 1, a.err, kErrWaitFull)) {
@@ -233,19 +235,20 @@ __global__ void __launch_bounds__(384) k_conv(const __grid_constant__ CUtensorMa
                 if (*abort_flag) break;
             }
             // no MMA of this CTA may still run when its TMEM is freed
-            for (int b = 0; b < 2; ++b)
+            for (int b = 0; b < GE; ++b)
                 if (commits[b]) mbar_wait(&accf[b], (commits[b] - 1) & 1, a.err, kErrWaitTail);
         }
     } else {
-        // epilogue: warps 4-7 drain buffer 0 (even tiles), warps 8-11 buffer 1
-        // (odd tiles); TMEM lane quarter q = warp % 4
+        // epilogue: warps 4 + 4g .. 7 + 4g drain buffer g (the tiles lt with
+        // lt mod GE = g); TMEM lane quarter q = warp % 4
         const int g = (warp - 4) >> 2;
         const int q = warp & 3;
         const int row = q * 32 + lane;
+        const uint32_t ge = static_cast<uint32_t>(GE);
         uint32_t lt = static_cast<uint32_t>(g);
-        for (int t = blockIdx.x + g * gridDim.x; t < total; t += 2 * gridDim.x, lt += 2) {
-            const uint32_t buf = lt & 1u;
-            const bool ok = mbar_wait(&accf[buf], (lt >> 1) & 1, a.err, kErrWaitDone);
+        for (int t = blockIdx.x + g * gridDim.x; t < total; t += GE * gridDim.x, lt += ge) {
+            const uint32_t buf = lt % ge;
+            const bool ok = mbar_wait(&accf[buf], (lt / ge) & 1, a.err, kErrWaitDone);
             tc_fence_after();
             __syncwarp();
             if (!ok || *abort_flag) {
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(384) k_conv(const __grid_constant__ CUtensorMa
             const int x = x0 + row;
             const bool valid = x < a.W;
             const size_t pix = (static_cast<size_t>(n) * a.H + y) * a.W + x;
-            const uint32_t tbase = tmem + buf * static_cast<uint32_t>(a.tmem_cols) + (static_cast<uint32_t>(q * 32) << 16);
+            const uint32_t tbase = tmem + buf * static_cast<uint32_t>(a.buf_cols) + (static_cast<uint32_t>(q * 32) << 16);
             for (int c = 0; c < a.N_tile; c += 16) {
                 float v[16];
                 tmem_ld16(tbase + static_cast<uint32_t>(c), v);
@@ -273,7 +276,7 @@ __global__ void __launch_bounds__(384) k_conv(const __grid_constant__ CUtensorMa
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) tmem_dealloc(tmem, static_cast<uint32_t>(2 * a.tmem_cols));
+    if (warp == 1) tmem_dealloc(tmem, static_cast<uint32_t>(a.tmem_cols));
 }
 
 // Resident-weight variant for layers whose packed weights fit in shared
@@ -493,7 +496,7 @@ __global__ void __launch_bounds__(384) k_conv_res(const __grid_constant__ CUtens
 // neighbouring TMEM lanes with warp shuffles (and a shared-memory exchange
 // across warps), and tiles advance by 126 pixels.  Weights are resident in
 // shared memory as [dy][chunk][(dx, o)][c].
-__global__ void __launch_bounds__(kDxnMaxThreads) k_conv_dxn(const __grid_constant__ CUtensorMap ta0,
+__global__ void __launch_bounds__(kConvMaxThreads) k_conv_dxn(const __grid_constant__ CUtensorMap ta0,
                                                   const __grid_constant__ CUtensorMap ta1,
                                                   const __grid_constant__ CUtensorMap tb0,
                                                   const __grid_constant__ CUtensorMap tb1, const ConvArgs a) {
@@ -603,7 +606,7 @@ __global__ void __launch_bounds__(kDxnMaxThreads) k_conv_dxn(const __grid_consta
             if (!mbar_wait(wbar, 0, a.err, kErrWaitFull)) *abort_flag = 1u;
             tc_fence_after();
             uint32_t it = 0, lt = 0;
-            uint32_t commits[kDxnMaxGroups] = {0u, 0u, 0u, 0u};
+            uint32_t commits[kConvMaxGroups] = {0u, 0u, 0u, 0u};
             const uint32_t wbase = smem_u32(wsm);
             const uint32_t ge = static_cast<uint32_t>(GE);
             for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++lt) {
@@ -1168,8 +1171,8 @@ cudaError_t conv_prepare() {
     return e;
 }
 
-static size_t conv_smem(int stages, uint32_t stage_bytes) {
-    return 1024 + static_cast<size_t>(stages) * stage_bytes + (2 * stages + 4) * 8 + 16;
+static size_t conv_smem(int stages, uint32_t stage_bytes, int groups = 2) {
+    return 1024 + static_cast<size_t>(stages) * stage_bytes + (2 * stages + 2 * groups) * 8 + 16;
 }
 
 cudaError_t launch_conv(const CUtensorMap* ta, const CUtensorMap* tb, const ConvArgs& a, cudaStream_t s) {
@@ -1192,7 +1195,8 @@ cudaError_t launch_conv(const CUtensorMap* ta, const CUtensorMap* tb, const Conv
     }
     const long long total = static_cast<long long>(segs) * a.H * a.Nb * ((a.N + a.N_tile - 1) / a.N_tile);
     const int grid = static_cast<int>(std::min<long long>(total, a.grid));
-    k_conv<<<grid, 384, conv_smem(a.stages, a.stage_bytes), s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0],
+    k_conv<<<grid, 32 * (4 + 4 * a.epi_groups), conv_smem(a.stages, a.stage_bytes, a.epi_groups), s>>>(
+        ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0],
                                                                  tb[a.nsrc > 1 ? 1 : 0], a);
     return cudaGetLastError();
 }

@@ -33,8 +33,9 @@ struct ConvArgs {
     // packed weights of source s at byte w_off[s] of a w_bytes region
     int rows_per_tile;
     int dxn;                    // column taps in N (3x3, N <= 64): tiles of 126 pixels
-    int epi_groups;             // column-tap variant: TMEM accumulator buffers, one epilogue warpgroup each
-    int buf_cols;               // column-tap variant: TMEM columns per buffer
+    int epi_groups;             // streamed and column-tap variants: TMEM accumulator buffers, one
+                                // epilogue warpgroup each (resident variant: 2)
+    int buf_cols;               // TMEM columns per buffer (streamed and column-tap variants)
     uint32_t w_bytes, w_bytes_real, w_off[2];
     uint32_t stage_bytes, a_region;
     uint32_t idesc;             // instruction descriptor of one MMA: M = 128, N = n_slice
@@ -52,11 +53,11 @@ struct ConvArgs {
     unsigned* err;
 };
 
-// Column-tap convolution: at most 4 accumulator buffers, each drained by its
-// own epilogue warpgroup (warps 4 + 4g .. 7 + 4g), after the producer and the
-// three MMA warps.
-constexpr int kDxnMaxGroups = 4;
-constexpr int kDxnMaxThreads = 32 * (4 + 4 * kDxnMaxGroups);
+// Convolution kernels (streamed and column-tap): at most 4 accumulator
+// buffers, each drained by its own epilogue warpgroup (warps 4 + 4g ..
+// 7 + 4g), after the producer and the three MMA warps.
+constexpr int kConvMaxGroups = 4;
+constexpr int kConvMaxThreads = 32 * (4 + 4 * kConvMaxGroups);
 
 // MMA-issuing warps of the weight-gradient kernel (see k_wgrad).
 constexpr int kWgradIssuers = 3;
