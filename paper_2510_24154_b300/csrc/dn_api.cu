@@ -264,7 +264,10 @@ bool plan_wgrad(WgradPlan& P, const bf16* dz, int Cz, int Co, int nsrc, const bf
     }
     // one 64-column accumulator per MMA warp: a column tap each, or a share of the K slices
     a.tmem_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(dn::kWgradIssuers * 64)));
-    a.stages = std::max(2, std::min(6, static_cast<int>((200u * 1024u) / a.stage_bytes)));
+    // narrow layers (mode 1): two CTAs per SM of two stages each, so one CTA's
+    // start-up and epilogue overlap the other's main loop
+    const uint32_t budget = a.mode ? 100u * 1024u : 200u * 1024u;
+    a.stages = std::max(2, std::min(6, static_cast<int>(budget / a.stage_bytes)));
     a.dW = dW;
     a.err = err;
     return true;
