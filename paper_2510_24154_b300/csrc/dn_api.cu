@@ -180,8 +180,11 @@ bool plan_conv(ConvPlan& P, int nsrc, const bf16* const src[2], const int srcC[2
         a.epi_groups = std::min(dn::kConvMaxGroups, 512 / a.buf_cols);
         a.tmem_cols = a.epi_groups * a.buf_cols;
     } else if (n_tiles == 1 && w_region <= 150u * 1024u && resident_ok) {
+        // rows per tile first (input reuse), then as many accumulator buffers
+        // (epilogue warpgroups) of R rows as TMEM holds, at least two
         int R = 4;
         while (R > 1 && (2 * R * a.N_tile > 512 || R > H)) R >>= 1;
+        a.epi_groups = (4 * R * a.N_tile <= 512) ? 4 : 2;
         a.rows_per_tile = R;
         a.w_off[0] = 0;
         a.w_off[1] = w_off1;
@@ -189,7 +192,7 @@ bool plan_conv(ConvPlan& P, int nsrc, const bf16* const src[2], const int srcC[2
         a.w_bytes = w_region;
         a.stage_bytes = a.a_region;
         a.stages = std::max(2, std::min(16, static_cast<int>((205u * 1024u - w_region) / a.stage_bytes)));
-        a.tmem_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(2 * R * a.N_tile)));
+        a.tmem_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(a.epi_groups * R * a.N_tile)));
     } else {
         a.rows_per_tile = 0;
         a.buf_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(a.N_tile)));

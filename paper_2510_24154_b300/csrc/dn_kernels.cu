@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv(const __grid_constant_
 // column shift dx, channel chunk) that feeds the up to k accumulators of the
 // output rows it touches (row r = j - dy with weight tap (dy, dx)), so an
 // input row is fetched (R + k - 1) / R times per output row instead of k.
-__global__ void __launch_bounds__(384) k_conv_res(const __grid_constant__ CUtensorMap ta0,
+__global__ void __launch_bounds__(kConvMaxThreads) k_conv_res(const __grid_constant__ CUtensorMap ta0,
                                                   const __grid_constant__ CUtensorMap ta1,
                                                   const __grid_constant__ CUtensorMap tb0,
                                                   const __grid_constant__ CUtensorMap tb1, const ConvArgs a) {
@@ -295,9 +295,10 @@ __global__ void __launch_bounds__(384) k_conv_res(const __grid_constant__ CUtens
     const int S = a.stages;
     uint64_t* full = reinterpret_cast<uint64_t*>(tiles + S * a.stage_bytes);
     uint64_t* empty = full + S;
+    const int GE = a.epi_groups;                          // accumulator buffers = epilogue warpgroups
     uint64_t* accf = empty + S;
-    uint64_t* acce = accf + 2;
-    uint64_t* wbar = acce + 2;
+    uint64_t* acce = accf + GE;
+    uint64_t* wbar = acce + GE;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(wbar + 1);
     volatile uint32_t* abort_flag = tslot + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(384) k_conv_res(const __grid_constant__ CUtens
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], a.n_issue);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < GE; ++i) {
             mbar_init(&accf[i], a.n_issue);
             mbar_init(&acce[i], 4);
         }
@@ -400,11 +401,12 @@ __global__ void __launch_bounds__(384) k_conv_res(const __grid_constant__ CUtens
             if (!wok) *abort_flag = 1u;
             tc_fence_after();
             uint32_t it = 0, lt = 0;
-            uint32_t commits[2] = {0u, 0u};
+            uint32_t commits[kConvMaxGroups] = {0u, 0u, 0u, 0u};
             const uint32_t wbase = smem_u32(wsm);
+            const uint32_t ge = static_cast<uint32_t>(GE);
             for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++lt) {
-                const uint32_t buf = lt & 1u;
-                if (lt >= 2 && !mbar_wait(&acce[buf], ((lt >> 1) - 1) & 1, a.err, kErrWaitEmpty)) {
+                const uint32_t buf = lt % ge;
+                if (lt >= ge && !mbar_wait(&acce[buf], ((lt / ge) - 1) & 1, a.err, kErrWaitEmpty)) {
                     *abort_flag = 1u;
                     break;
                 }
@@ -443,17 +445,18 @@ __global__ void __launch_bounds__(384) k_conv_res(const __grid_constant__ CUtens
                 ++commits[buf];
                 if (*abort_flag) break;
             }
-            for (int b = 0; b < 2; ++b)
+            for (int b = 0; b < GE; ++b)
                 if (commits[b]) mbar_wait(&accf[b], (commits[b] - 1) & 1, a.err, kErrWaitTail);
         }
     } else {
         const int g = (warp - 4) >> 2;             // epilogue group = accumulator buffer
         const int q = warp & 3;
         const int prow = q * 32 + lane;
+        const uint32_t ge = static_cast<uint32_t>(GE);
         uint32_t lt = static_cast<uint32_t>(g);
-        for (int t = blockIdx.x + g * gridDim.x; t < total; t += 2 * gridDim.x, lt += 2) {
-            const uint32_t buf = lt & 1u;
-            const bool ok = mbar_wait(&accf[buf], (lt >> 1) & 1, a.err, kErrWaitDone);
+        for (int t = blockIdx.x + g * gridDim.x; t < total; t += GE * gridDim.x, lt += ge) {
+            const uint32_t buf = lt % ge;
+            const bool ok = mbar_wait(&accf[buf], (lt / ge) & 1, a.err, kErrWaitDone);
             tc_fence_after();
             __syncwarp();
             if (!ok || *abort_flag) {
@@ -1189,8 +1192,10 @@ cudaError_t launch_conv(const CUtensorMap* ta, const CUtensorMap* tb, const Conv
     if (a.rows_per_tile > 0) {
         const long long total = static_cast<long long>(segs) * ((a.H + a.rows_per_tile - 1) / a.rows_per_tile) * a.Nb;
         const int grid = static_cast<int>(std::min<long long>(total, a.grid));
-        const size_t smem = 1024 + a.w_bytes + static_cast<size_t>(a.stages) * a.stage_bytes + (2 * a.stages + 5) * 8 + 16;
-        k_conv_res<<<grid, 384, smem, s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0], tb[a.nsrc > 1 ? 1 : 0], a);
+        const size_t smem =
+            1024 + a.w_bytes + static_cast<size_t>(a.stages) * a.stage_bytes + (2 * a.stages + 2 * a.epi_groups + 1) * 8 + 16;
+        k_conv_res<<<grid, 32 * (4 + 4 * a.epi_groups), smem, s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0],
+                                                                 tb[a.nsrc > 1 ? 1 : 0], a);
         return cudaGetLastError();
     }
     const long long total = static_cast<long long>(segs) * a.H * a.Nb * ((a.N + a.N_tile - 1) / a.N_tile);
