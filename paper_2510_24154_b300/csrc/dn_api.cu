@@ -118,6 +118,7 @@ bool plan_conv(ConvPlan& P, int nsrc, const bf16* const src[2], const int srcC[2
     a.k = k;
     a.Nb = Nb; a.H = H; a.W = W;
     a.N = N;
+    if (N < 1 || N > dn::kConvMaxN) return false;
     int n_tiles;
     n_tiling(N, a.N_tile, n_tiles);
     a.tmem_cols = static_cast<int>(pow2_at_least(static_cast<uint32_t>(a.N_tile)));

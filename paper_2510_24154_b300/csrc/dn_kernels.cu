@@ -50,7 +50,7 @@ __device__ __forceinline__ KStep kstep(const ConvArgs& a, int i) {
 // Epilogue of 16 accumulator columns (output channels co0 .. co0+15) of one
 // pixel: bias, ReLU, the mask of the source layer, the split of a
 // concatenated input, bf16 rounding; 16-byte stores where aligned.
-__device__ __forceinline__ void epilogue16(const ConvArgs& a, const float* v, int co0, size_t pix) {
+__device__ __forceinline__ void epilogue16(const ConvArgs& a, const float* bias, const float* v, int co0, size_t pix) {
     const int d = (a.ndst > 1 && co0 >= a.dst_split) ? 1 : 0;
     const int cc0 = co0 - (d ? a.dst_split : 0);
     const int dC = a.dst_C[d];
@@ -67,7 +67,7 @@ __device__ __forceinline__ void epilogue16(const ConvArgs& a, const float* v, in
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 float val = v[8 * h + j];
-                if (a.bias) val += __ldg(&a.bias[co0 + 8 * h + j]);
+                if (a.bias) val += bias[co0 + 8 * h + j];
                 if (a.relu) val = fmaxf(val, 0.0f);
                 if (mk && !(__bfloat162float(mb[j]) > 0.0f)) val = 0.0f;
                 o[j] = __float2bfloat16_rn(val);
@@ -81,7 +81,7 @@ __device__ __forceinline__ void epilogue16(const ConvArgs& a, const float* v, in
             const int dd = (a.ndst > 1 && co >= a.dst_split) ? 1 : 0;
             const int cc = co - (dd ? a.dst_split : 0);
             float val = v[j];
-            if (a.bias) val += __ldg(&a.bias[co]);
+            if (a.bias) val += bias[co];
             if (a.relu) val = fmaxf(val, 0.0f);
             const size_t o = pix * a.dst_C[dd] + cc;
             if (a.mask[dd] && !(__bfloat162float(a.mask[dd][o]) > 0.0f)) val = 0.0f;
@@ -116,6 +116,9 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv(const __grid_constant_
     uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + GE);
     volatile uint32_t* abort_flag = tslot + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ float s_bias[kConvMaxN];                  // the epilogue's bias, read once
+    if (a.bias)
+        for (int i = threadIdx.x; i < a.N; i += blockDim.x) s_bias[i] = __ldg(&a.bias[i]);
 
     const int segs = (a.W + 127) >> 7;
     const int n_tiles = (a.N + a.N_tile - 1) / a.N_tile;
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv(const __grid_constant_
                 tmem_ld16(tbase + static_cast<uint32_t>(c), v);
                 const int co0 = n0 + c;
                 if (!valid || co0 >= a.N) continue;
-                epilogue16(a, v, co0, pix);
+                epilogue16(a, s_bias, v, co0, pix);
             }
             // this warp's TMEM reads are complete (tcgen05.wait::ld): hand the buffer back
             tc_fence_before();
@@ -302,6 +305,9 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_res(const __grid_const
     uint32_t* tslot = reinterpret_cast<uint32_t*>(wbar + 1);
     volatile uint32_t* abort_flag = tslot + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ float s_bias[kConvMaxN];                  // the epilogue's bias, read once
+    if (a.bias)
+        for (int i = threadIdx.x; i < a.N; i += blockDim.x) s_bias[i] = __ldg(&a.bias[i]);
 
     const int R = a.rows_per_tile, k = a.k, p = k >> 1;
     const int segs = (a.W + 127) >> 7;
@@ -476,7 +482,7 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_res(const __grid_const
                     float v[16];
                     tmem_ld16(tbase + static_cast<uint32_t>(c), v);
                     if (!valid || c >= a.N) continue;
-                    epilogue16(a, v, c, pix);
+                    epilogue16(a, s_bias, v, c, pix);
                 }
             }
             tc_fence_before();
@@ -517,6 +523,9 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_dxn(const __grid_const
     uint32_t* tslot = reinterpret_cast<uint32_t*>(xch + GE * 2 * 4 * 16);
     volatile uint32_t* abort_flag = tslot + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ float s_bias[kConvMaxN];                  // the epilogue's bias, read once
+    if (a.bias)
+        for (int i = threadIdx.x; i < a.N; i += blockDim.x) s_bias[i] = __ldg(&a.bias[i]);
 
     const int N = a.N;                      // output channels
     const int N3 = 3 * N;                   // MMA N
@@ -695,7 +704,7 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_dxn(const __grid_const
                     o[j] = left + v1[j] + right;
                 }
                 asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
-                if (valid) epilogue16(a, o, c, pix);
+                if (valid) epilogue16(a, s_bias, o, c, pix);
             }
             tc_fence_before();
             __syncwarp();
@@ -1163,14 +1172,22 @@ __global__ void k_to_f32(const __nv_bfloat16* __restrict__ x, int stride, long l
 
 // ----------------------------------------------------------- launchers ----
 
+// Each kernel may use the SM's opt-in shared memory (227 KB) less its static arrays.
+template <class K>
+static cudaError_t allow_dynamic_smem(K kernel) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const int total = 227 * 1024;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                total - static_cast<int>(fa.sharedSizeBytes));
+}
+
 cudaError_t conv_prepare() {
-    cudaError_t e = cudaFuncSetAttribute(k_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv_res, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv_dxn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaError_t e = allow_dynamic_smem(k_conv);
+    if (e == cudaSuccess) e = allow_dynamic_smem(k_conv_res);
+    if (e == cudaSuccess) e = allow_dynamic_smem(k_conv_dxn);
+    if (e == cudaSuccess) e = allow_dynamic_smem(k_wgrad);
     return e;
 }
 

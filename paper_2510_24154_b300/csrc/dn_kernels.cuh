@@ -57,6 +57,7 @@ struct ConvArgs {
 // buffers, each drained by its own epilogue warpgroup (warps 4 + 4g ..
 // 7 + 4g), after the producer and the three MMA warps.
 constexpr int kConvMaxGroups = 4;
+constexpr int kConvMaxN = 512;      // output channels of one convolution
 constexpr int kConvMaxThreads = 32 * (4 + 4 * kConvMaxGroups);
 
 // MMA-issuing warps of the weight-gradient kernel (see k_wgrad).
