@@ -778,14 +778,23 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
         emit_none(e0);
         emit_none(e1);
         if (alive) {
-            bool keep;
-            if (TYPE == kPhotonCT) keep = photon_ct_event(P, s_tab, s_grid, acc, s_energy, s_events, p, e0, e1, move);
-            else if (TYPE == kPhotonEPID) keep = photon_epid_event(P, s_tab, acc, s_energy, s_events, p, e0, e1);
-            else keep = electron_event<kEpid>(P, s_tab, acc, s_energy, s_events, p, e0, e1, move, rho_c);
-            if (keep && ++steps_here > P.max_steps) {
-                acc.lost += quanta(p.E + rest_extra(p.flags));
-                atomicAdd(&s_events[kCLost], 1ull);
-                keep = false;
+            bool keep = true;
+            // electrons in the CT take up to four steps per iteration, going on
+            // while a step emits nothing: the iteration's refill, votes and
+            // flushes are shared by several steps (measured best at four; the
+            // draws are the same as one step per iteration)
+            const int reps = (TYPE == kElectronCT) ? 4 : 1;
+#pragma unroll 1
+            for (int rep = 0; rep < reps; ++rep) {
+                if (rep > 0 && !(keep && e0.dest < 0 && e1.dest < 0)) break;
+                if (TYPE == kPhotonCT) keep = photon_ct_event(P, s_tab, s_grid, acc, s_energy, s_events, p, e0, e1, move);
+                else if (TYPE == kPhotonEPID) keep = photon_epid_event(P, s_tab, acc, s_energy, s_events, p, e0, e1);
+                else keep = electron_event<kEpid>(P, s_tab, acc, s_energy, s_events, p, e0, e1, move, rho_c);
+                if (keep && ++steps_here > P.max_steps) {
+                    acc.lost += quanta(p.E + rest_extra(p.flags));
+                    atomicAdd(&s_events[kCLost], 1ull);
+                    keep = false;
+                }
             }
             alive = keep;
         }
