@@ -93,7 +93,7 @@ typedef struct mc_config {
                                      (a conditional while-node); 0: waves are driven from the host */
     int regs_variant[4];          /* per transport kernel (CT photons, CT electrons, EPID photons, EPID
                                      electrons): build for 2, 3 or 4 CTAs of 256 threads per SM
-                                     (register caps 128 / 85 / 64); 0 = the default {4, 3, 4, 3} */
+                                     (register caps 128 / 85 / 64); 0 = the default 4 */
     int patient_dose;             /* 1: also tally the energy deposited in every CT voxel (the patient
                                      dose of the same histories; mc_get_patient_dose) */
 } mc_config;

@@ -23,11 +23,11 @@ import os
 from pathlib import Path
 from typing import Callable, Dict, Iterable, Optional
 
-DEFAULTS = {"regs_variant": (4, 3, 4, 3), "block_size": 256, "bank_capacity": 1 << 23, "primaries_per_wave": 0,
+DEFAULTS = {"regs_variant": (4, 4, 4, 4), "block_size": 256, "bank_capacity": 1 << 23, "primaries_per_wave": 0,
             "use_graph": 0}
 
 SEARCH = {
-    "regs_variant": [(4, 3, 4, 3), (4, 4, 4, 4), (3, 3, 4, 4), (3, 3, 3, 3), (4, 2, 4, 3), (2, 3, 4, 3)],
+    "regs_variant": [(4, 4, 4, 4), (4, 3, 4, 3), (4, 3, 4, 4), (3, 3, 4, 4), (3, 3, 3, 3), (4, 2, 4, 4)],
     "block_size": [256, 128],
     "bank_capacity": [1 << 23, 1 << 24],
     "primaries_per_wave": [0, 1 << 20, 1 << 22],

@@ -36,8 +36,8 @@ struct FieldHost {
 };
 
 // CTAs of 256 threads per SM each transport kernel is built for, measured
-// best on the thorax workload: photons 4 (64 registers), electrons 3 (80).
-constexpr int kDefaultRegsVariant[4] = {4, 3, 4, 3};
+// best on the thorax workload: 4 (64 registers) for every kernel.
+constexpr int kDefaultRegsVariant[4] = {4, 4, 4, 4};
 constexpr size_t kHeadsBytes = sizeof(uint32_t) * mc::kNumBanks * mc::kHeadShards * mc::kHeadStride;
 constexpr double kQuantaPerMeV = 2.56e8;
 constexpr double kJoulePerMeV = 1.602176634e-13;
