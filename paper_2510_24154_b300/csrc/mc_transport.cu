@@ -4,17 +4,18 @@
 //   photons in the CT    Woodcock (delta) tracking against the majorant
 //                        max_m rho_max,m mu_m(E); real interactions sampled as
 //                        Compton (Klein-Nishina), photoelectric or pair (Sec. 2.1.2).
+//   electrons in the CT  Class II condensed history: CSDA soft losses, hard
+//                        Moller and bremsstrahlung by delta tracking against
+//                        the start-of-step value, a random-hinge Wentzel
+//                        deflection, steps limited by voxel faces; up to four
+//                        steps per warp iteration while steps emit nothing.
+//   photons in the EPID  exact optical-depth tracking through the layer stack.
+//   electrons in the EPID the same condensed history in the layers; energy in
+//                        the sensitive layer goes to the pixel tally.
 // A source kernel opens each wave: it samples that wave's primaries (Sec.
 // 2.1.1) one per thread, with every lane doing the same work, and writes them
 // into the CT-photon bank (or the EPID-photon bank when they miss the CT), so
 // the transport kernels never branch into history start-up.
-//   electrons in the CT  Class II condensed history: CSDA soft losses, hard
-//                        Moller and bremsstrahlung by delta tracking against
-//                        the start-of-step value, a random-hinge Wentzel
-//                        deflection, steps limited by voxel faces.
-//   photons in the EPID  exact optical-depth tracking through the layer stack.
-//   electrons in the EPID the same condensed history in the layers; energy in
-//                        the sensitive layer goes to the pixel tally.
 // Each kernel follows, draw for draw, the sampling order of the written model,
 // so a history fed the same Philox keys replays on another implementation.
 #include "mc_device.cuh"
