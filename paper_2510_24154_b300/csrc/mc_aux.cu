@@ -157,28 +157,40 @@ __global__ void k_tmap(TmapArgs A, double* __restrict__ t) {
 __global__ void k_dose(const unsigned long long* __restrict__ tally, int npix, int B, const double* __restrict__ nb,
                        double n_hist, double conv, double* __restrict__ dose, double* __restrict__ sigma,
                        unsigned long long* max_bits) {
+    // per-batch factor from tally units to dose per history, once per block
+    __shared__ double s_w[1024];
+    __shared__ unsigned long long s_max[32];
+    const double per_q = 1.0 / 2.56e8;              // MeV per tally unit
+    for (int b = threadIdx.x; b < B; b += blockDim.x) s_w[b] = per_q / nb[b] * conv;
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double dm = 0.0;
     if (i < npix) {
-        const double per_q = 1.0 / 2.56e8;          // MeV per tally unit
         double sum = 0.0;
         for (int b = 0; b < B; ++b) sum += static_cast<double>(tally[static_cast<size_t>(b) * npix + i]);
         dm = sum * per_q / n_hist * conv;
         double ss = 0.0;
         for (int b = 0; b < B; ++b) {
-            const double db = static_cast<double>(tally[static_cast<size_t>(b) * npix + i]) * per_q / nb[b] * conv;
+            const double db = static_cast<double>(tally[static_cast<size_t>(b) * npix + i]) * s_w[b];
             ss += (db - dm) * (db - dm);
         }
         dose[i] = dm;
         if (sigma) sigma[i] = sqrt(ss / (static_cast<double>(B) * (B - 1)));
     }
+    // block maximum (doses are >= 0, so their bit patterns order like the values), one atomic per block
     unsigned long long bits = __double_as_longlong(dm);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long ob = __shfl_down_sync(kFull, bits, o);
         bits = ob > bits ? ob : bits;
     }
-    if ((threadIdx.x & 31) == 0 && bits) atomicMax(max_bits, bits);
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = bits;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long m = 0;
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) m = s_max[w] > m ? s_max[w] : m;
+        if (m) atomicMax(max_bits, m);
+    }
 }
 
 // Mean relative uncertainty over pixels above half the maximum: per-block
