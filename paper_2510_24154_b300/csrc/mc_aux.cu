@@ -122,14 +122,15 @@ __global__ void k_tmap(TmapArgs A, double* __restrict__ t) {
     double acc = 0.0;
     if (amin < amax) {
         int idx[3], stp[3], plane[3];
-        float anext[3];
+        float anext[3], inv[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const float pk = S[k] + amin * d[k];
             idx[k] = min(max(__float2int_rd((pk - o[k]) / v[k]), 0), n[k] - 1);
             stp[k] = (d[k] > 0.0f) ? 1 : (d[k] < 0.0f ? -1 : 0);
             plane[k] = idx[k] + (stp[k] > 0 ? 1 : 0);
-            anext[k] = (stp[k] != 0) ? (o[k] + plane[k] * v[k] - S[k]) / d[k] : INFINITY;
+            inv[k] = (stp[k] != 0) ? 1.0f / d[k] : 0.0f;
+            anext[k] = (stp[k] != 0) ? (o[k] + plane[k] * v[k] - S[k]) * inv[k] : INFINITY;
         }
         float acur = amin;
         const int maxit = n[0] + n[1] + n[2] + 3;
@@ -139,13 +140,14 @@ __global__ void k_tmap(TmapArgs A, double* __restrict__ t) {
             if (anext[2] < anext[k]) k = 2;
             const float aend = fminf(anext[k], amax);
             const float rho = __ldg(&A.rho[(static_cast<size_t>(idx[2]) * A.ny + idx[1]) * A.nx + idx[0]]);
-            acc += static_cast<double>(rho) * static_cast<double>((aend - acur) * len);
+            // the segment's product in single precision, the sum in double
+            acc += static_cast<double>(rho * ((aend - acur) * len));
             if (anext[k] >= amax) break;
             acur = anext[k];
             idx[k] += stp[k];
             if (idx[k] < 0 || idx[k] >= n[k]) break;
             plane[k] += stp[k];
-            anext[k] = (o[k] + plane[k] * v[k] - S[k]) / d[k];
+            anext[k] = (o[k] + plane[k] * v[k] - S[k]) * inv[k];
         }
     }
     t[pix] = acc + A.t_offset;
