@@ -27,12 +27,25 @@ __device__ __forceinline__ float rho_of_hu(int hu) {
 __global__ void k_macro_grid(const float* __restrict__ rho, int nx, int ny, int nz, int M, int mgx, int mgy,
                              float thr_bone, unsigned int* __restrict__ grid) {
     const size_t n = static_cast<size_t>(nx) * ny * nz;
-    const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
-    for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int ix = static_cast<int>(i % nx), iy = static_cast<int>((i / nx) % ny), iz = static_cast<int>(i / (static_cast<size_t>(nx) * ny));
-        const float r = rho[i];
-        const size_t cc = (static_cast<size_t>(iz / M) * mgy + iy / M) * mgx + ix / M;
-        atomicMax(&grid[2 * cc + (r >= thr_bone ? 1 : 0)], __float_as_uint(r));
+    const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;      // a multiple of 32
+    const unsigned lane = threadIdx.x & 31u;
+    // whole warps per pass: lanes with the same (cell, class) reduce their
+    // maximum first, and one of them updates the grid (32 consecutive voxels
+    // share at most a few cells)
+    for (size_t base = static_cast<size_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+        const size_t i = base + lane;
+        unsigned key = 0xffffffffu, bits = 0u;
+        if (i < n) {
+            const int ix = static_cast<int>(i % nx), iy = static_cast<int>((i / nx) % ny),
+                      iz = static_cast<int>(i / (static_cast<size_t>(nx) * ny));
+            const float r = rho[i];
+            const size_t cc = (static_cast<size_t>(iz / M) * mgy + iy / M) * mgx + ix / M;
+            key = static_cast<unsigned>(2 * cc + (r >= thr_bone ? 1 : 0));
+            bits = __float_as_uint(r);
+        }
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        const unsigned mx = __reduce_max_sync(grp, bits);
+        if (i < n && lane == static_cast<unsigned>(__ffs(grp) - 1)) atomicMax(&grid[key], mx);
     }
 }
 
