@@ -159,12 +159,35 @@ def test_full_size_geometry_replay():
     in the default launch configuration: energy balance, replay of the
     sensitive-layer energy and of the event counts."""
     p = G.thorax_case(n=200_000, scale=1, epid_scale=1)
-    sim, st, gt = G.gpu_run(p, bank_capacity=1 << 24)       # bench.py's launch configuration
+    sim, st, gt = G.gpu_run(p, bank_capacity=1 << 26)       # bench.py's launch configuration
     orc = oracle.run(p)
     assert G.energy_closure(st) < 2e-6
     assert gt.sum() == pytest.approx(orc["tally"].sum(), rel=5e-3)
     for k in ("real_ct", "compton", "electrons", "primaries_at_epid"):
         assert st["counters"][k] == pytest.approx(orc["counters"][k], rel=2e-3), k
+
+
+def test_bench_step_statistics_against_oracle_sample():
+    """The benchmark step itself (full thorax CT and EPID, 1e8 histories,
+    2^26-particle banks): energy balance, no lost particles, and the mean
+    sensitive-layer energy and event counts per history within 4 standard
+    errors of an independent oracle sample of 4e5 histories (its batch
+    spread gives the error; the GPU's own error is 16x smaller)."""
+    n_gpu, n_orc = 100_000_000, 400_000
+    p = G.thorax_case(n=n_gpu, scale=1, epid_scale=1, batches=16)
+    sim, st, gt = G.gpu_run(p, bank_capacity=1 << 26)
+    assert st["histories"] == n_gpu and st["error_flags"] == 0 and st["counters"]["lost"] == 0
+    assert G.energy_closure(st) < 2e-6
+    orc = oracle.run(p, n_histories=n_orc, hist_begin=1 << 40)     # streams disjoint from the GPU's
+    per_batch = orc["tally"].reshape(orc["tally"].shape[0], -1).sum(axis=1) / oracle.batch_counts(n_orc, 16)
+    mean_o = orc["tally"].sum() / n_orc
+    se_o = per_batch.std(ddof=1) / np.sqrt(per_batch.size)
+    mean_g = gt.sum() / n_gpu
+    assert abs(mean_g - mean_o) <= 4.0 * se_o, (mean_g, mean_o, se_o)
+    # event counts per history: Poisson-like errors of the oracle sample
+    for k in ("flights_ct", "real_ct", "compton", "esteps_ct", "electrons", "primaries_at_epid"):
+        g, o = st["counters"][k] / n_gpu, orc["counters"][k] / n_orc
+        assert abs(g - o) <= 4.0 * np.sqrt(max(orc["counters"][k], 1)) / n_orc * 3.0, (k, g, o)
 
 
 # --------------------------------------------------- determinism --------
