@@ -443,6 +443,15 @@ def main():
                                       agg["kernel_ms"])},
     }
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    # measured arithmetic peaks of this GPU (outside the timed region): the
+    # best issue rate any probe reached, and the FP32 FMA rate
+    from paper_2510_24154_b300.binding import probe_alu_peaks
+    probe = probe_alu_peaks(local)
+    issue_meas = max(probe["ffma_tflops"] / 2.0, probe["int_tinst"], probe["mix_tinst"])
+    roofline["probe"] = dict(probe, issue_tinst_measured=issue_meas)
+    roofline["frac_of_probe_issue"] = roofline["achieved"] / issue_meas
+    roofline["fp32"]["peak_tflops_measured"] = max(probe["ffma_tflops"], probe["ffma2_tflops"])
+    roofline["fp32"]["frac_of_measured"] = roofline["fp32"]["achieved_tflops"] / roofline["fp32"]["peak_tflops_measured"]
     memory_roofline = {"bound": "hbm", "achieved": mem_achieved, "peak": hbm_peak, "unit": "GB/s",
                        "frac": mem_achieved / hbm_peak, "peak_kind": peak_kind,
                        "algorithmic_bytes_per_launch": alg_bytes}

@@ -344,6 +344,31 @@ mc_status mc_test_philox(const uint32_t* in, uint32_t* out, int n, void* stream)
  * under seed, as the transport kernels draw them.  out: device float [n]. */
 mc_status mc_test_uniforms(uint64_t seed, uint64_t hist, uint32_t ord, int n, float* out, void* stream);
 
+/* Measured arithmetic peaks of this GPU: the denominators of the transport
+ * kernels' ALU roofline.  Each figure is the best of `repeats` launches of a
+ * full-occupancy kernel of independent dependency chains of one instruction
+ * class, counted from its source:
+ *   ffma_tflops   FP32 fused multiply-adds (2 flops each), scalar form
+ *   ffma2_tflops  FP32 fused multiply-adds issued as fma.rn.f32x2 pairs
+ *   mufu_tops     ex2.approx / lg2.approx results, T ops/s
+ *   int_tinst     32-bit integer xor and add, T thread-instructions/s
+ *   mix_tinst     FP32 FMA and integer ops interleaved, T thread-instructions/s
+ *   ms_total      summed best times of the five probes
+ * Takes about 0.1 s on device `device`; allocates and frees its own buffers.
+ * MC_ERR_ARG for a null result, repeats outside [1, 100] or a bad device. */
+typedef struct mc_alu_peaks {
+    double ffma_tflops;
+    double ffma2_tflops;
+    double mufu_tops;
+    double int_tinst;
+    double mix_tinst;
+    double ms_total;
+    int32_t sm_count;
+    int32_t _pad;
+} mc_alu_peaks;
+
+mc_status mc_probe_alu_peaks(int device, int repeats, mc_alu_peaks* res);
+
 #ifdef __cplusplus
 }
 #endif

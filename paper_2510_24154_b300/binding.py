@@ -29,7 +29,7 @@ EXPORTED = ("mc_config_default", "mc_create", "mc_destroy", "mc_init_geometry", 
             "mc_reset_tally", "mc_state_size", "mc_get_state", "mc_set_state", "mc_set_history_base", "mc_cancel",
             "mc_last_error",
             "mc_status_string", "mc_test_philox", "mc_test_uniforms", "mc_dose_stats_noalloc", "mc_gamma",
-            "mc_get_patient_dose", "mc_get_plan_image", "mc_resample_image")
+            "mc_get_patient_dose", "mc_get_plan_image", "mc_resample_image", "mc_probe_alu_peaks")
 
 
 class Config(C.Structure):
@@ -69,6 +69,12 @@ class RunStats(C.Structure):
                 ("counters", C.c_uint64 * NUM_COUNTERS), ("waves", C.c_int), ("error_flags", C.c_uint32),
                 ("gpu_ms", C.c_double), ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_uint32 * 4),
                 ("launches", C.c_uint32)]
+
+
+class AluPeaks(C.Structure):
+    _fields_ = [("ffma_tflops", C.c_double), ("ffma2_tflops", C.c_double), ("mufu_tops", C.c_double),
+                ("int_tinst", C.c_double), ("mix_tinst", C.c_double), ("ms_total", C.c_double),
+                ("sm_count", C.c_int32), ("_pad", C.c_int32)]
 
 
 class MCError(RuntimeError):
@@ -131,6 +137,7 @@ def load(build_if_stale: bool = True):
     lib.mc_get_patient_dose.argtypes = [vp, vp, i, vp]
     lib.mc_get_plan_image.argtypes = [vp, vp, vp, vp, i, vp]
     lib.mc_resample_image.argtypes = [vp, i, i, d, vp, i, i, d, vp]
+    lib.mc_probe_alu_peaks.argtypes = [i, i, P(AluPeaks)]
     for name in EXPORTED:
         if name not in ("mc_config_default", "mc_last_error", "mc_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -425,6 +432,17 @@ def test_uniforms(seed, hist, ord_, n, stream=None):
     if st:
         raise MCError(st, "mc_test_uniforms")
     return out.cpu().numpy()
+
+
+def probe_alu_peaks(device=0, repeats=3):
+    """mc_probe_alu_peaks: measured FP32 FMA (scalar and f32x2), ex2/lg2,
+    integer and mixed-issue rates of the GPU, as a dict."""
+    lib = load()
+    r = AluPeaks()
+    st = lib.mc_probe_alu_peaks(int(device), int(repeats), C.byref(r))
+    if st:
+        raise MCError(st, "mc_probe_alu_peaks")
+    return {k: getattr(r, k) for k, _ in AluPeaks._fields_ if not k.startswith("_")}
 
 
 def dose_stats_noalloc(tally, npx, npy, n_batches, n_histories, pixel_mass_kg, dose, sigma=None, u=None,

@@ -16,7 +16,7 @@ CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 LIB = PKG / "libarcher_epid.so"
 SOURCES = ["mc_api.cu", "mc_transport.cu", "mc_aux.cu", "mc_noalloc.cu", "physics_tables.cpp", "dn_kernels.cu",
-           "dn_api.cu"]
+           "dn_api.cu", "mc_probe.cu"]
 HEADERS = ["mc_device.cuh", "mc_aux.h", "physics_tables.h", "dn_tc.cuh", "dn_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
