@@ -299,6 +299,17 @@ __device__ __forceinline__ int material_of(const Params& P, float rho) {
     return (rho >= P.thr[0]) + (rho >= P.thr[1]) + (rho >= P.thr[2]);
 }
 
+// Sine and cosine of the azimuth 2 pi x of a uniform x in (0, 1), from the
+// hardware's approximate sine and cosine (absolute error below 2^-21 on
+// [-pi, pi]) of the argument shifted into that range: x - 1/2 is exact for
+// the generator's uniforms, and sin, cos of 2 pi x - pi are minus those of 2 pi x.
+__device__ __forceinline__ void azimuth_sincos(float x, float& s, float& c) {
+    float sn, cs;
+    __sincosf(6.28318530717958648f * (x - 0.5f), &sn, &cs);
+    s = -sn;
+    c = -cs;
+}
+
 // Unit direction rotated by polar cosine ct and azimuth (cp, sp); the polar
 // frame is used within 0.99999 of the z axis.
 __device__ __forceinline__ void rotate_dir(float& u, float& v, float& w, float ct, float cp, float sp) {
@@ -307,13 +318,15 @@ __device__ __forceinline__ void rotate_dir(float& u, float& v, float& w, float c
         const float sg = (w > 0.0f) ? 1.0f : -1.0f;
         u = st * cp; v = st * sp; w = sg * ct;
     } else {
-        const float tmp = sqrtf(1.0f - w * w);
-        const float nu = u * ct + st * (u * w * cp - v * sp) / tmp;
-        const float nv = v * ct + st * (v * w * cp + u * sp) / tmp;
-        const float nw = w * ct - tmp * st * cp;
+        const float q = 1.0f - w * w;                           // sin^2 of the polar angle of (u, v, w)
+        const float iq = rsqrtf(q);
+        const float sq = st * iq;
+        const float nu = u * ct + sq * (u * w * cp - v * sp);
+        const float nv = v * ct + sq * (v * w * cp + u * sp);
+        const float nw = w * ct - q * iq * st * cp;
         u = nu; v = nv; w = nw;
     }
-    const float inv = 1.0f / sqrtf(u * u + v * v + w * w);
+    const float inv = rsqrtf(u * u + v * v + w * w);
     u *= inv; v *= inv; w *= inv;
 }
 

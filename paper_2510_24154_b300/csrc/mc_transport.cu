@@ -146,7 +146,7 @@ template <bool EPID>
 __device__ __forceinline__ void annihilate(const Params& P, unsigned long long* s_events, Part& p, Emit& e) {
     const float ct = 2.0f * p.rng.u() - 1.0f;
     float sp, cp;
-    sincospif(2.0f * p.rng.u(), &sp, &cp);
+    azimuth_sincos(p.rng.u(), sp, cp);
     const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
     e.dest = EPID ? kPhotonEPID : kPhotonCT;
     e.E = kMec2;
@@ -221,7 +221,7 @@ __device__ __forceinline__ bool photon_interact(const Params& P, Acc& a, unsigne
         float eps, ct;
         sample_kn(p.rng, p.E, eps, ct);
         float sp, cp;
-        sincospif(2.0f * p.rng.u(), &sp, &cp);
+        azimuth_sincos(p.rng.u(), sp, cp);
         const float E0 = p.E, E1 = eps * E0;
         const float u0 = p.u, v0 = p.v, w0 = p.w;
         rotate_dir(p.u, p.v, p.w, ct, cp, sp);
@@ -478,7 +478,7 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
         mu = (A < 0.0f) ? xmu : A * xmu / (1.0f - xmu + A);
     }
     float sp, cp;
-    sincospif(2.0f * xph, &sp, &cp);
+    azimuth_sincos(xph, sp, cp);
     const bool face = (lim == 2);
     // first segment: the whole step for a face-limited step, else up to the hinge
     const float s1 = face ? s : xh * s;
@@ -553,7 +553,7 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
         count_event(s_events, kCMoller);
         const float eps = sample_moller(p.rng, Tn, P.wcc);
         float sph, cph;
-        sincospif(2.0f * p.rng.u(), &sph, &cph);
+        azimuth_sincos(p.rng.u(), sph, cph);
         const float W = eps * Tn, Tp = Tn - W;
         const float cs = sqrtf(W * (Tn + 2.0f * kMec2) / (Tn * (W + 2.0f * kMec2)));
         const float cpr = sqrtf(Tp * (Tn + 2.0f * kMec2) / (Tn * (Tp + 2.0f * kMec2)));
