@@ -460,7 +460,7 @@ mc_status run_waves_graph(mc_ctx* c, const Params& P, cudaStream_t s, cudaEvent_
     for (int t : kOrder) {
         if (is_electron(t) && !c->cfg.coupled) continue;
         if (e == cudaSuccess) e = mc::launch_transport(t, c->minb[t], P, c->grid[t], c->block, cs);
-        if (e == cudaSuccess) e = mc::launch_swap(c->d_ctl, c->d_heads, t, cs);
+        if (e == cudaSuccess) e = mc::launch_swap(c->d_ctl, c->d_heads, t, c->cap, cs);
         per_wave += 2;
     }
     if (e == cudaSuccess) e = mc::launch_wave_end(c->d_ctl, handle, kMaxWaves, cs);
@@ -513,7 +513,7 @@ mc_status run_waves_host(mc_ctx* c, const Params& P, cudaStream_t s, cudaEvent_t
             }
             CUDA_TRY(c, mc::launch_transport(t, c->minb[t], P, c->grid[t], c->block, s));
             if (c->cfg.time_kernels) CUDA_TRY(c, cudaEventRecord(next_event(), s));
-            CUDA_TRY(c, mc::launch_swap(c->d_ctl, c->d_heads, t, s));
+            CUDA_TRY(c, mc::launch_swap(c->d_ctl, c->d_heads, t, c->cap, s));
             r.launches += 2;
             ++r.klaunch[t];
         }

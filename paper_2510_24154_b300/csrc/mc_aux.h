@@ -25,7 +25,7 @@ size_t transport_smem(int type);
 cudaError_t transport_prepare();
 cudaError_t transport_occupancy(int type, int minb, int block, int* blocks_per_sm);
 cudaError_t launch_transport(int type, int minb, const Params& P, int grid, int block, cudaStream_t s);
-cudaError_t launch_swap(Ctl* c, uint32_t* heads, int t, cudaStream_t s);
+cudaError_t launch_swap(Ctl* c, uint32_t* heads, int t, uint32_t cap, cudaStream_t s);
 cudaError_t launch_wave_begin(Ctl* c, unsigned long long per_wave, uint32_t cap, cudaStream_t s);
 cudaError_t launch_source(const Params& P, int grid, cudaStream_t s);
 cudaError_t launch_wave_end(Ctl* c, cudaGraphConditionalHandle h, unsigned int max_waves, cudaStream_t s);

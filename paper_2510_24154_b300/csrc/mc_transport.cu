@@ -29,6 +29,10 @@ struct Acc {
     unsigned long long ct, src, esc, lost;
     uint32_t flights, steps;
     uint32_t iters, live;       // warp iterations and live lanes (lane 0 counts)
+    // EPID kernels: `ct` holds the lane's pending deposit in layer `lay`,
+    // added to the block's layer total when the layer changes and at the end
+    // (same-address shared atomics from a whole warp on every step would serialise)
+    uint32_t lay;
 };
 
 __device__ __forceinline__ void acc_flush(const Params& P, Acc& a, unsigned long long* s_energy,
@@ -65,11 +69,16 @@ __device__ __forceinline__ float rest_extra(uint32_t flags) { return (flags & kP
 
 // Energy deposited at beam-frame position (x, y) in EPID layer `layer` by a
 // particle of history `hist` of field `f`: into sub-tally (history index within the field mod B).
-__device__ __forceinline__ void deposit_epid(const Params& P, unsigned long long* s_energy, int layer, float x,
-                                             float y, uint32_t hist, uint32_t flags, float dE) {
+__device__ __forceinline__ void deposit_epid(const Params& P, Acc& a, unsigned long long* s_energy, int layer,
+                                             float x, float y, uint32_t hist, uint32_t flags, float dE) {
     if (!(dE > 0.0f)) return;
     const unsigned long long q = quanta(dE);
-    atomicAdd(&s_energy[kEEpid0 + layer], q);
+    if (static_cast<uint32_t>(layer) != a.lay) {
+        if (a.ct) atomicAdd(&s_energy[kEEpid0 + a.lay], a.ct);
+        a.lay = static_cast<uint32_t>(layer);
+        a.ct = 0ull;
+    }
+    a.ct += q;
     if (layer != P.sens) return;
     int ix = __float2int_rd((x + P.hwx) / P.pitch);
     int iy = __float2int_rd((y + P.hwy) / P.pitch);
@@ -84,7 +93,7 @@ template <bool EPID>
 __device__ __forceinline__ void deposit(const Params& P, Acc& a, unsigned long long* s_energy, uint32_t cell,
                                         float x, float y, uint32_t hist, uint32_t flags, float dE) {
     if (EPID) {
-        deposit_epid(P, s_energy, static_cast<int>(cell), x, y, hist, flags, dE);
+        deposit_epid(P, a, s_energy, static_cast<int>(cell), x, y, hist, flags, dE);
     } else if (dE > 0.0f) {
         const unsigned long long q = quanta(dE);
         a.ct += q;
@@ -695,8 +704,21 @@ __device__ __forceinline__ bool start_primary(const Params& P, unsigned long lon
 }
 
 // The persistent transport kernel for one event type.
+// EPID electrons are few per wave (about one per lane of the grid) and each
+// takes tens of dependent steps, so a launch costs the longest chain of steps
+// whatever its size.  While more source waves follow and the input holds less
+// than an eighth of a bank, the kernel leaves its input for a later wave (the
+// producers append to it) and the bank swap keeps it: the chain is paid once
+// for several waves.  Every particle still runs (the last source wave and the
+// waves that drain the banks never defer), in an order that changes no result
+// (per-particle random streams, integer tallies).
+__device__ __forceinline__ bool defer_epid_electrons(const Ctl* c, uint32_t cap) {
+    return c->allow_flush != 0u && c->count[kElectronEPID][c->cur[kElectronEPID]] < cap / 8u;
+}
+
 template <int TYPE, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
+    if (TYPE == kElectronEPID && defer_epid_electrons(P.ctl, P.cap)) return;
     constexpr bool kPhoton = (TYPE == kPhotonCT || TYPE == kPhotonEPID);
     constexpr bool kEpid = (TYPE == kPhotonEPID || TYPE == kElectronEPID);
     constexpr int kTabN = kPhoton ? kPhotonNodes : kNumMat * kElectronNodes + kWentzelNodes / 2;
@@ -723,7 +745,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
     const bool may_flush = P.ctl->allow_flush != 0u;
     const uint32_t move_par = kEpid ? 0u : P.ctl->cur[kMoveTo];
 
-    Acc acc = {0ull, 0ull, 0ull, 0ull, 0u, 0u, 0u, 0u};
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0u, 0u, 0u, 0u, 0u};
     Part p;
     bool alive = false;
     bool in_open = true;
@@ -804,6 +826,10 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
         if (!kEpid) flush_self(P, move, kMoveTo, move_par, p);
     }
 
+    if (kEpid && acc.ct) {
+        atomicAdd(&s_energy[kEEpid0 + acc.lay], acc.ct);
+        acc.ct = 0ull;
+    }
     acc_flush(P, acc, s_energy, s_events, kPhoton ? (kEpid ? kCFlightsEPID : kCFlightsCT) : kCFlightsCT,
               kEpid ? kCEStepsEPID : kCEStepsCT);
     if (!kEpid && lane_id() == 0 && acc.iters) {
@@ -831,7 +857,7 @@ __global__ void __launch_bounds__(256) k_source(const Params P) {
     __syncthreads();
     const unsigned long long begin = P.ctl->src_begin, end = P.ctl->src_end;
     const uint32_t par_ct = P.ctl->cur[kPhotonCT], par_epid = P.ctl->cur[kPhotonEPID];
-    Acc acc = {0ull, 0ull, 0ull, 0ull, 0u, 0u, 0u, 0u};
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0u, 0u, 0u, 0u, 0u};
     const unsigned long long warps = static_cast<unsigned long long>(gridDim.x) * (blockDim.x >> 5);
     const unsigned long long w0 = static_cast<unsigned long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
     for (unsigned long long base = begin + 32ull * w0; base < end; base += 32ull * warps) {
@@ -852,7 +878,8 @@ __global__ void __launch_bounds__(256) k_source(const Params P) {
 
 // Closes a consumer pass of bank type t: the drained input parity is emptied
 // and the carry parity becomes the next input.
-__global__ void k_swap(Ctl* c, uint32_t* heads, int t) {
+__global__ void k_swap(Ctl* c, uint32_t* heads, int t, uint32_t cap) {
+    if (t == kElectronEPID && defer_epid_electrons(c, cap)) return;       // input kept for a later wave
     const uint32_t in = c->cur[t];
     c->count[t][in] = 0u;
     for (int k = 0; k < kHeadShards; ++k) heads[(t * kHeadShards + k) * kHeadStride] = 0u;
@@ -940,8 +967,8 @@ cudaError_t launch_transport(int type, int minb, const Params& P, int grid, int 
     return cudaLaunchKernel(transport_fn(type, minb), dim3(grid), dim3(block), args, smem, s);
 }
 
-cudaError_t launch_swap(Ctl* c, uint32_t* heads, int t, cudaStream_t s) {
-    k_swap<<<1, 1, 0, s>>>(c, heads, t);
+cudaError_t launch_swap(Ctl* c, uint32_t* heads, int t, uint32_t cap, cudaStream_t s) {
+    k_swap<<<1, 1, 0, s>>>(c, heads, t, cap);
     return cudaGetLastError();
 }
 
