@@ -134,6 +134,18 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def cpu_model():
+    """The host CPU's model name (first processor in /proc/cpuinfo), or None."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def cpu_sample(problem, n, threads):
     import oracle
     t0 = time.perf_counter()
@@ -168,7 +180,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "histories_per_step": sample, "seed": SEED},
         "cpu_baseline": {"value": v, "unit": "histories/s", "cores": min(threads, p.physics.n_batches),
-                         "kind": "oracle", "sample": f"{sample} histories of the workload per step"},
+                         "kind": "oracle", "sample": f"{sample} histories of the workload per step",
+                         "host": {"cpu_model": cpu_model(), "logical_cpus": threads}},
         "e2e": {"value": v, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -517,8 +530,13 @@ def main():
         threads = os.cpu_count() or 1
         sample = 12_000_000           # about 11 s on 16 threads
         v, used, dt = cpu_sample(p, sample, threads)
+        sample1 = 400_000             # about 6 s on one thread
+        v1, _, dt1 = cpu_sample(p, sample1, 1)
         cpu = {"value": v, "unit": "histories/s", "cores": used, "kind": "oracle",
-               "sample": f"{sample} histories of the same workload ({dt:.1f} s wall on {used} threads)"}
+               "sample": f"{sample} histories of the same workload ({dt:.1f} s wall on {used} threads)",
+               "host": {"cpu_model": cpu_model(), "logical_cpus": threads},
+               "single_core": {"value": v1, "unit": "histories/s",
+                               "sample": f"{sample1} histories on 1 thread ({dt1:.1f} s wall)"}}
 
     if rank == 0:
         line = {
