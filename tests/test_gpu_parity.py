@@ -204,6 +204,9 @@ def test_bitwise_reproducible_across_runs_and_launch_shapes():
     physics = oracle.COUNTER_NAMES          # the execution counters depend on the launch shape
     assert all(st1["counters"][k] == st3["counters"][k] == st4["counters"][k] for k in physics)
     assert st1["e_src"] == st3["e_src"] == st4["e_src"] and st1["e_ct"] == st3["e_ct"] == st4["e_ct"]
+    # per-layer EPID energy (lanes hold pending deposits; the many-wave run
+    # defers its EPID electrons to the last source wave)
+    assert np.array_equal(st1["e_epid"], st3["e_epid"]) and np.array_equal(st1["e_epid"], st4["e_epid"])
 
 
 def test_checkpoint_resume_is_bitwise_identical():
