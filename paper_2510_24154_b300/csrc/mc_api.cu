@@ -238,6 +238,15 @@ void make_params(const mc_ctx* c, Params& P, uint64_t seed) {
         for (int k = 0; k < 2; ++k) P.bank[t][k] = c->bank[t][k];
     P.cap = c->cap;
     P.flush_lanes = 8;
+    // CT-photon slot pools: at most 1/16 of a bank can be left reserved but
+    // unused at the end of a launch (16 slots per warp for the benchmark's
+    // banks; 16 measured slightly better than 32)
+    {
+        const unsigned long long warps =
+            static_cast<unsigned long long>(c->grid[mc::kPhotonCT]) * static_cast<unsigned long long>(c->block) / 32u;
+        const unsigned long long per = warps ? static_cast<unsigned long long>(c->cap) / (16u * warps) : 1u;
+        P.pool_chunk = static_cast<uint32_t>(std::max<unsigned long long>(1u, std::min<unsigned long long>(16u, per)));
+    }
 }
 
 bool increasing(const double* a, int n) {
