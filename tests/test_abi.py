@@ -60,6 +60,13 @@ def test_argument_errors_need_no_gpu():
     assert lib.mc_create(None, 0, None) == 1            # MC_ERR_ARG on a null out-pointer
     assert lib.mc_destroy(None) == 0
     assert lib.mc_cancel(None) == 1
+    # the arithmetic peak probe checks its arguments before touching a device
+    import ctypes as C
+    r = binding.AluPeaks()
+    assert lib.mc_probe_alu_peaks(0, 1, None) == 1
+    assert lib.mc_probe_alu_peaks(0, 0, C.byref(r)) == 1
+    assert lib.mc_probe_alu_peaks(0, 101, C.byref(r)) == 1
+    assert lib.mc_probe_alu_peaks(-1, 1, C.byref(r)) == 1
 
 
 def test_struct_layouts_match_c(tmp_path):
@@ -68,8 +75,8 @@ def test_struct_layouts_match_c(tmp_path):
         #include <stddef.h>
         #include "archer_epid.h"
         int main(void) {
-          printf("%zu %zu %zu %zu %zu\\n", sizeof(mc_config), sizeof(mc_epid_desc), sizeof(mc_field_desc),
-                 sizeof(mc_lut_desc), sizeof(mc_run_stats));
+          printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mc_config), sizeof(mc_epid_desc), sizeof(mc_field_desc),
+                 sizeof(mc_lut_desc), sizeof(mc_run_stats), sizeof(mc_alu_peaks), offsetof(mc_alu_peaks, sm_count));
           printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(mc_config, use_graph), offsetof(mc_config, regs_variant), offsetof(mc_config, patient_dose),
                  offsetof(mc_epid_desc, pitch_cm),
                  offsetof(mc_field_desc, eq1_literal), offsetof(mc_field_desc, leaf_transmission),
@@ -84,7 +91,8 @@ def test_struct_layouts_match_c(tmp_path):
     sizes, offs = [list(map(int, l.split())) for l in
                    subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()]
     assert sizes == [C.sizeof(binding.Config), C.sizeof(binding.EpidDesc), C.sizeof(binding.FieldDesc),
-                     C.sizeof(binding.LutDesc), C.sizeof(binding.RunStats)]
+                     C.sizeof(binding.LutDesc), C.sizeof(binding.RunStats), C.sizeof(binding.AluPeaks),
+                     binding.AluPeaks.sm_count.offset]
     assert offs == [binding.Config.use_graph.offset, binding.Config.regs_variant.offset, binding.Config.patient_dose.offset, binding.EpidDesc.pitch_cm.offset,
                     binding.FieldDesc.eq1_literal.offset, binding.FieldDesc.leaf_transmission.offset,
                     binding.FieldDesc.leaf_gap_cm.offset, binding.RunStats.gpu_ms.offset,
