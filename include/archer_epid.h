@@ -323,10 +323,14 @@ mc_status mc_gamma(const double* ref, const double* ev, int nx, int ny, double p
  * the host and nothing is allocated or freed.
  *
  * Limits: at most 4,194,304 pixels (2048 x 2048) and 1024 batches; larger
- * inputs return MC_ERR_ARG (and a message on stderr).  Its scratch is a
- * 213,248-byte array inside the library that every GPU loading the library
- * keeps until the process exits.  The first call on a device looks up that
- * array's device address, so make it before capturing the stream.  All calls
+ * inputs return MC_ERR_ARG (and a message on stderr), and so does
+ * n_histories < n_batches (a batch without histories has no mean).  Its
+ * scratch is a 205,056-byte array inside the library that every GPU loading
+ * the library keeps until the process exits.  The first call on a device
+ * looks up that array's device address, so make it before capturing the
+ * stream; the address is kept for the life of the process, so do not call
+ * this again after cudaDeviceReset (or another destruction of the device's
+ * primary context).  All calls
  * share the array: calls whose work overlaps on the GPU (two streams, or two
  * host threads) race and give wrong results; serialize them.  Call it with the
  * device that holds `tally` current. */

@@ -24,11 +24,16 @@ constexpr size_t kOffNb = 0;                                        // double[kM
 constexpr size_t kOffMax = kOffNb + sizeof(double) * kMaxBatches;   // unsigned long long
 constexpr size_t kOffSum = kOffMax + 256;                           // double[kMaxParts]
 constexpr size_t kOffCnt = kOffSum + sizeof(double) * kMaxParts;    // unsigned int[kMaxParts]
-constexpr size_t kScratchBytes = kOffCnt + sizeof(unsigned int) * kMaxParts;   // 204,800 + 8,448 bytes
+constexpr size_t kScratchBytes = kOffCnt + sizeof(unsigned int) * kMaxParts;
+// 8,192 (batch counts) + 256 (maximum) + 131,072 (partial sums) + 65,536 (partial counts)
+static_assert(kScratchBytes == 205056, "the documented scratch size must follow the layout");
 
 // Every GPU that loads the library keeps this array until the process exits.
 // Host code may not use its name as an address; set-up below asks the runtime
-// for the device address.
+// for the device address.  The address is looked up once per device and kept:
+// after cudaDeviceReset (or anything else that destroys the device's primary
+// context) it is stale, so this entry point must not be called again in that
+// process after such a reset.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -54,6 +59,12 @@ extern "C" mc_status mc_dose_stats_noalloc(const uint64_t* tally, int npx, int n
         return MC_ERR_ARG;
     }
     if (u && !sigma) return MC_ERR_ARG;
+    if (n_histories < static_cast<uint64_t>(n_batches)) {
+        // a batch without histories has no mean: sigma and u would be NaN
+        std::fprintf(stderr, "mc_dose_stats_noalloc: %llu histories cannot fill %d batches (need at least one "
+                             "history per batch)\n", static_cast<unsigned long long>(n_histories), n_batches);
+        return MC_ERR_ARG;
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MC_ERR_CUDA;
     unsigned char* base;

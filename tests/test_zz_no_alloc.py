@@ -20,6 +20,8 @@ from paper_2510_24154_b300 import binding, workloads as W  # noqa: E402
 
 
 def _case(problem, n):
+    """Run `problem` through the context path; return its tally on the device,
+    the pixel mass and mc_get_dose's (dose, sigma, u)."""
     sim = binding.Simulator(problem.physics)
     sim.init_geometry(problem.phantom, problem.epid)
     sim.set_field(problem.field, problem.lut)
@@ -55,10 +57,32 @@ def test_noalloc_matches_mc_get_dose_on_two_calls_in_a_row():
         assert float(u.item()) == pytest.approx(u_ref, rel=1e-12)
 
 
-def test_noalloc_rejects_oversized_inputs():
-    t = torch.zeros(4, dtype=torch.int64, device="cuda")
+def test_noalloc_dose_only_and_the_batch_limit():
+    """A dose-only call (no sigma, no u) and a call at the largest batch count
+    (1024), each against mc_get_dose of the same tally."""
+    p = W.config_water_open(n_histories=100_000, npx=24, npy=16, pitch=1.0)
+    p.physics.n_batches = 1024
+    tally, mass, (d_ref, s_ref, u_ref) = _case(p, 100_000)
+    ny, nx = p.epid.npy, p.epid.npx
+    dose = torch.full((ny, nx), -1.0, dtype=torch.float64, device="cuda")
+    binding.dose_stats_noalloc(tally, nx, ny, 1024, 100_000, mass, dose)
+    torch.cuda.synchronize()
+    assert np.allclose(dose.cpu().numpy(), d_ref, rtol=1e-12, atol=0)
+    sigma = torch.full((ny, nx), -1.0, dtype=torch.float64, device="cuda")
+    u = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+    binding.dose_stats_noalloc(tally, nx, ny, 1024, 100_000, mass, dose, sigma, u)
+    torch.cuda.synchronize()
+    assert np.allclose(dose.cpu().numpy(), d_ref, rtol=1e-12, atol=0)
+    assert np.allclose(sigma.cpu().numpy(), s_ref, rtol=1e-12, atol=1e-300)
+    assert float(u.item()) == pytest.approx(u_ref, rel=1e-12)
+
+
+def test_noalloc_rejects_bad_inputs():
+    t = torch.zeros(64, dtype=torch.int64, device="cuda")
     out = torch.zeros(4, dtype=torch.float64, device="cuda")
-    with pytest.raises(binding.MCError):
+    with pytest.raises(binding.MCError):       # more pixels than the scratch holds
         binding.dose_stats_noalloc(t, 4096, 2048, 16, 100, 1e-6, out)
-    with pytest.raises(binding.MCError):
-        binding.dose_stats_noalloc(t, 2, 2, 2048, 100, 1e-6, out)
+    with pytest.raises(binding.MCError):       # more batches than the scratch holds
+        binding.dose_stats_noalloc(t, 2, 2, 2048, 100_000, 1e-6, out)
+    with pytest.raises(binding.MCError):       # fewer histories than batches: empty batches
+        binding.dose_stats_noalloc(t, 2, 2, 16, 15, 1e-6, out)
