@@ -68,6 +68,26 @@ class _Result(C.Structure):
     ]
 
 
+class _Probe(C.Structure):
+    _fields_ = [
+        ("type", C.c_int), ("E", C.c_double), ("x", C.c_double * 3), ("u", C.c_double * 3),
+        ("no_ms", C.c_int), ("no_hard", C.c_int), ("macro_M", C.c_int), ("cap", C.c_int64),
+        ("path", C.POINTER(C.c_double)), ("hard_T", C.POINTER(C.c_double)), ("hard_type", C.POINTER(C.c_int32)),
+        ("first_layer", C.POINTER(C.c_int32)), ("first_pos", C.POINTER(C.c_double)),
+        ("end_pos", C.POINTER(C.c_double)), ("first_pixel", C.POINTER(C.c_int64)),
+        ("pair_frac", C.POINTER(C.c_double)), ("annih_cos", C.POINTER(C.c_double)),
+        ("annih_phi", C.POINTER(C.c_double)), ("brem_x", C.POINTER(C.c_double)),
+        ("compton_phi", C.POINTER(C.c_double)),
+        ("n_exit_uncollided", C.c_uint64), ("n_compton", C.c_uint64), ("n_moller", C.c_uint64),
+        ("n_brem", C.c_uint64), ("n_pair", C.c_uint64), ("n_annih", C.c_uint64), ("n_pos_escape", C.c_uint64),
+        ("n_pos_born", C.c_uint64),
+        ("compton_dev", C.c_double), ("polar_dev", C.c_double), ("moller_dev", C.c_double),
+        ("brem_dev", C.c_double),
+        ("pair_dev", C.c_double), ("annih_dev", C.c_double), ("unit_dev", C.c_double),
+        ("hidx", C.c_int64), ("first_done", C.c_int), ("pix_done", C.c_int), ("hard_done", C.c_int),
+    ]
+
+
 _lib = None
 
 
@@ -100,8 +120,10 @@ def lib():
         _lib.orc_hu_to_rho_mat.argtypes = [i, P(d), P(i)]
         _lib.orc_run.restype = i
         _lib.orc_run.argtypes = [P(_Problem), u64, u64, u64, i, P(_Result)]
-        _lib.orc_first_interaction.argtypes = [P(_Problem), d, P(d), P(d), u64, u64, P(C.c_int64),
+        _lib.orc_first_interaction.argtypes = [P(_Problem), d, P(d), P(d), u64, u64, i, P(C.c_int64),
                                                P(C.c_int32)]
+        _lib.orc_pencil.restype = i
+        _lib.orc_pencil.argtypes = [P(_Problem), P(_Probe), u64, u64, u64, P(_Result)]
         _lib.orc_tmap.argtypes = [P(_Problem), P(C.c_int32), P(C.c_int32), C.c_int64, P(d)]
         _lib.orc_siddon_ray.restype = d
         _lib.orc_siddon_ray.argtypes = [P(_Problem), P(d), P(d)]
@@ -189,16 +211,104 @@ def run(problem, n_histories=None, seed=None, hist_begin=0, threads=None, physic
     }
 
 
-def first_interaction(problem, E, start, direction, n, seed=0):
+def first_interaction(problem, E, start, direction, n, seed=0, macro_M=0):
+    """First real interaction (flat voxel, type) of n photons along one ray;
+    macro_M > 0 overrides the macro-cell size of the Woodcock majorant."""
     m = _Marshalled(problem)
     st = np.ascontiguousarray(start, dtype=np.float64)
     dr = np.ascontiguousarray(direction, dtype=np.float64)
     vox = np.empty(n, dtype=np.int64)
     typ = np.empty(n, dtype=np.int32)
-    lib().orc_first_interaction(C.byref(m.s), float(E), _dp(st), _dp(dr), int(seed), int(n),
+    lib().orc_first_interaction(C.byref(m.s), float(E), _dp(st), _dp(dr), int(seed), int(n), int(macro_M),
                                 vox.ctypes.data_as(C.POINTER(C.c_int64)),
                                 typ.ctypes.data_as(C.POINTER(C.c_int32)))
     return vox, typ
+
+
+PARTICLE = {"photon": 0, "electron": 1, "positron": 2}
+_PROBE_SAMPLES = ("pair_frac", "annih_cos", "annih_phi", "brem_x", "compton_phi")
+_PROBE_COUNTS = ("n_exit_uncollided", "n_compton", "n_moller", "n_brem", "n_pair", "n_annih", "n_pos_escape",
+                 "n_pos_born")
+_PROBE_DEVS = ("compton_dev", "polar_dev", "moller_dev", "brem_dev", "pair_dev", "annih_dev", "unit_dev")
+
+
+def pencil(problem, particle, E, start, direction, n, seed=0, hist_begin=0, no_ms=False, no_hard=False,
+           macro_M=0, patient_dose=False, cap=200_000, threads=None, physics=None, field=None):
+    """Histories whose primary is one given particle (a pencil), transported
+    by the oracle's own transport with its test probe recording (orc_pencil).
+
+    particle: "photon", "electron" or "positron"; start/direction in the
+    patient frame (a charged primary starts inside the CT; a photon enters
+    the world along its line).  no_ms / no_hard switch off the deflections /
+    the hard events.  Returns the usual energy balance, tally and counters
+    plus, per history, "path" (charged primary's track length), "hard_T" /
+    "hard_type" (its first hard event), "first_layer", "first_pos" and
+    "first_pixel" (a photon primary's first real interaction and first
+    deposit), "end_pos" (where a charged primary stops), the kinematic deviations, event counts and up to `cap` samples
+    per thread of each kind.  Chunks of histories run on `threads` threads
+    (the C call releases the GIL); each history is independent."""
+    from concurrent.futures import ThreadPoolExecutor
+    m = _Marshalled(problem, physics, field)
+    n = int(n)
+    nthr = max(1, min(int(threads if threads is not None else (os.cpu_count() or 1)), n))
+    B = m.s.n_batches
+    bounds = np.linspace(0, n, nthr + 1).astype(np.int64)
+    out = {"path": np.zeros(n), "hard_T": np.zeros(n), "hard_type": np.zeros(n, np.int32),
+           "first_layer": np.zeros(n, np.int32), "first_pos": np.zeros((n, 3)), "end_pos": np.zeros((n, 3)),
+           "first_pixel": np.zeros(n, np.int64)}
+    st = np.ascontiguousarray(start, dtype=np.float64)
+    dr = np.ascontiguousarray(direction, dtype=np.float64)
+
+    def chunk(k):
+        a, b = int(bounds[k]), int(bounds[k + 1])
+        q = _Probe()
+        q.type, q.E = PARTICLE[particle], float(E)
+        q.x[:], q.u[:] = [float(v) for v in st], [float(v) for v in dr]
+        q.no_ms, q.no_hard, q.macro_M, q.cap = int(no_ms), int(no_hard), int(macro_M), int(cap)
+        views = {key: arr[a:b] for key, arr in out.items()}
+        keep = [views]
+        q.path, q.hard_T = _dp(views["path"]), _dp(views["hard_T"])
+        q.hard_type = views["hard_type"].ctypes.data_as(C.POINTER(C.c_int32))
+        q.first_layer = views["first_layer"].ctypes.data_as(C.POINTER(C.c_int32))
+        q.first_pos = _dp(views["first_pos"])
+        q.end_pos = _dp(views["end_pos"])
+        q.first_pixel = views["first_pixel"].ctypes.data_as(C.POINTER(C.c_int64))
+        samples = {key: np.full(int(cap), np.nan) for key in _PROBE_SAMPLES}
+        for key, arr in samples.items():
+            setattr(q, key, _dp(arr))
+        tally = np.zeros((B, m.s.npy, m.s.npx), dtype=np.float64)
+        r = _Result()
+        r.tally = _dp(tally)
+        vox = np.zeros(problem.phantom.hu.shape, dtype=np.float64) if patient_dose else None
+        if vox is not None:
+            r.vox = _dp(vox)
+        rc = lib().orc_pencil(C.byref(m.s), C.byref(q), int(seed), int(hist_begin) + a, b - a, C.byref(r))
+        if rc != 0:
+            raise RuntimeError(f"orc_pencil failed with code {rc}")
+        del keep
+        return q, r, tally, vox, samples
+
+    with ThreadPoolExecutor(nthr) as ex:
+        parts = list(ex.map(chunk, range(nthr)))
+    res = dict(out)
+    res["tally"] = sum(p[2] for p in parts)
+    res["vox"] = sum(p[3] for p in parts) if patient_dose else None
+    res["e_src"] = sum(p[1].e_src for p in parts)
+    res["e_ct"] = sum(p[1].e_ct for p in parts)
+    res["e_esc"] = sum(p[1].e_esc for p in parts)
+    res["e_lost"] = sum(p[1].e_lost for p in parts)
+    res["e_epid"] = sum(np.array(p[1].e_epid[:len(problem.epid.layers)]) for p in parts)
+    res["counters"] = {name: sum(int(p[1].counters[i]) for p in parts) for i, name in enumerate(COUNTER_NAMES)}
+    for key in _PROBE_COUNTS:
+        res[key] = sum(int(getattr(p[0], key)) for p in parts)
+    for key in _PROBE_DEVS:
+        res[key] = max(float(getattr(p[0], key)) for p in parts)
+    for key in _PROBE_SAMPLES:
+        vals = [p[4][key] for p in parts]
+        cnt = {"pair_frac": "n_pair", "annih_cos": "n_annih", "annih_phi": "n_annih", "brem_x": "n_brem",
+               "compton_phi": "n_compton"}[key]
+        res[key] = np.concatenate([v[:min(int(getattr(p[0], cnt)), int(cap))] for v, p in zip(vals, parts)])
+    return res
 
 
 def sample_source(problem, n, seed=0, hist_begin=0):

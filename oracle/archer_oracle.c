@@ -20,12 +20,18 @@
  *
  * Parity pins: each sampler and cross section has an external check in the
  * CPU test suite (closed forms, numerical integration, brute-force
- * enumeration).  The absolute values of the builder's photoelectric, pair and
- * bremsstrahlung fits are model definitions with no external data to compare
- * against ("parity unpinned" for their magnitudes; their structure is pinned).
+ * enumeration), and the transport loop itself is pinned through orc_pencil
+ * (the loop of orc_run with one fixed primary and a recording probe): CSDA
+ * track length and depth profile, Lewis' mean stopping depth, the hard-event
+ * survival law, EPID layer transmission, pixel mapping, pair and annihilation
+ * and interaction kinematics.  The absolute values of the builder's
+ * photoelectric, pair and bremsstrahlung fits are model definitions with no
+ * external data to compare against ("parity unpinned" for their magnitudes;
+ * their structure is pinned).
  */
 #include <math.h>
 #include <pthread.h>
+#include <stddef.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -46,6 +52,8 @@
 #define O_TSTOP 1e-6               /* an electron stops once T <= cutoff + this, MeV */
 #define O_NMAT 7
 #define O_MAXL 8
+#define O_HOM_R 2                  /* half-width of a homogeneous voxel's neighbourhood, voxels */
+#define O_HOM_SPAN 200             /* largest HU span within a homogeneous neighbourhood */
 
 /* ------------------------------------------------------------------------ */
 /* Materials: elemental mass fractions and mean excitation energies.         */
@@ -376,8 +384,56 @@ typedef struct {
     double x[3], u[3], E;
     int cell[3];                 /* CT voxel index, or [0] = EPID layer */
     int collided;                /* primaries only: has had a real interaction */
+    double tau;                  /* charged particles: optical depth left to the next tentative hard event
+                                    against the step majorants; <= 0: none drawn yet */
+    int prim;                    /* the probe's primary particle (test hook only; children are 0) */
     o_rng rng;
 } o_part;
+
+/* ------------------------------------------------------------------------ */
+/* Test probe (orc_pencil only): facts about one primary particle per history */
+/* and kinematic checks of each interaction, gathered for the CPU pins.  The  */
+/* transport below only reads `no_ms` / `no_hard` from it and otherwise       */
+/* records; with no probe (every orc_run) nothing changes.                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    /* inputs */
+    int type;                    /* primary: 0 photon, 1 electron, 2 positron */
+    double E;                    /* its kinetic energy, MeV */
+    double x[3], u[3];           /* start and direction, patient frame (a charged primary starts inside the CT) */
+    int no_ms, no_hard;          /* switches: no multiple-scattering deflection; no hard events */
+    int macro_M;                 /* macro-cell size override for the Woodcock majorant (0: default rule) */
+    int64_t cap;                 /* capacity of the sample arrays below */
+    /* per-history outputs (arrays of n, each may be NULL) */
+    double* path;                /* track length of a charged primary, cm */
+    double* hard_T;              /* primary's kinetic energy when its first hard event happens, or -1 */
+    int32_t* hard_type;          /* that event: 0 Moller, 1 bremsstrahlung, -1 none */
+    int32_t* first_layer;        /* primary photon's first real interaction: EPID layer, -1 CT, -2 none */
+    double* first_pos;           /* [n][3] its point, beam frame (EPID interactions only) */
+    double* end_pos;             /* [n][3] where a charged primary stops (patient frame), NaN if it never stops */
+    int64_t* first_pixel;        /* sensitive-layer pixel y*npx+x that its first deposit went to, or -1 */
+    /* samples (first `cap` events of each kind) */
+    double* pair_frac;           /* T- / (E - 2 mc^2) of each pair event */
+    double* annih_cos;           /* cos(polar angle) of the first photon of each annihilation */
+    double* annih_phi;           /* its azimuth, [0, 2 pi) */
+    double* brem_x;              /* ln(k / wcb) / ln(T / wcb) of each hard bremsstrahlung photon */
+    double* compton_phi;         /* azimuth of the scattered photon about the incident direction */
+    /* aggregate outputs */
+    uint64_t n_exit_uncollided;  /* primary photons leaving the EPID's far face with no real interaction */
+    uint64_t n_compton, n_moller, n_brem, n_pair, n_annih, n_pos_escape, n_pos_born;
+    double compton_dev;          /* max over Compton events with |w0| <= 0.99999 (the general rotation frame):
+                                    | |E0 u0 - E1 u1| - p_e | / E0 and |u0.u1 - cos| */
+    double polar_dev;            /* the Compton and Moller figures for events in the polar frame
+                                    (|w0| > 0.99999), which takes u0 as the z axis itself */
+    double moller_dev;           /* max | p0 u0 - pW uW - pT uT | / p0 (general frame; polar frame: polar_dev) */
+    double brem_dev;             /* max | photon direction - electron direction | */
+    double pair_dev;             /* max | T- + T+ - (E - 2 mc^2) | */
+    double annih_dev;            /* max |u1 + u2|, |E1 - mc^2|, |E2 - mc^2| */
+    double unit_dev;             /* max | |u| - 1 | of any direction set by an interaction */
+    /* working state */
+    int64_t hidx;                /* index of the current history in the per-history arrays */
+    int first_done, pix_done, hard_done;
+} orc_probe;
 
 typedef struct {
     const orc_problem* P;
@@ -389,6 +445,7 @@ typedef struct {
     int mgM, mg[3];                   /* macro-cells: M voxels per side, count per axis */
     double* mg_low;                   /* per macro-cell max density of air, lung, water voxels */
     double* mg_bone;                  /* per macro-cell max density of bone voxels */
+    unsigned char* hom;               /* per voxel: 1 if homogeneous (see ctx_homogeneity) */
     double* rect;                     /* source rectangles: x0,x1,y0,y1 */
     double* cdf;                      /* cumulative weight */
     int n_rect;
@@ -398,6 +455,7 @@ typedef struct {
     uint64_t cnt[C_NCOUNT];
     uint64_t hist;
     o_part* stack; int sp, cap;
+    orc_probe* probe;                 /* test hook, NULL in every orc_run */
 } o_ctx;
 
 /* HU -> density (g/cm^3) and material (stated reading of the curve in Sec. 2.1.2). */
@@ -438,26 +496,71 @@ static void push(o_ctx* c, const o_part* p) {
 
 static double rest_extra(const o_part* p) { return (p->type == P_POSITRON) ? 2.0 * O_MC2 : 0.0; }
 
+/* The probe's first-deposit record: the sensitive-layer pixel, or -1. */
+static void probe_first_deposit(o_ctx* c, const o_part* p, int64_t pixel) {
+    orc_probe* Q = c->probe;
+    if (!Q || !p->prim || Q->pix_done) return;
+    Q->pix_done = 1;
+    if (Q->first_pixel) Q->first_pixel[Q->hidx] = pixel;
+}
+
 static void deposit(o_ctx* c, const o_part* p, const double pos[3], int layer, double dE) {
     if (dE == 0.0) return;
     if (p->zone == Z_CT) {
         c->e_ct += dE;
         /* patient dose: the energy goes to the voxel the particle is in */
         if (c->vox) c->vox[((size_t)p->cell[2] * c->P->ny + p->cell[1]) * c->P->nx + p->cell[0]] += dE;
+        probe_first_deposit(c, p, -1);
         return;
     }
     c->e_epid[layer] += dE;
     const orc_problem* P = c->P;
-    if (layer != P->sens_layer) return;
+    if (layer != P->sens_layer) { probe_first_deposit(c, p, -1); return; }
     int ix = (int)floor((pos[0] + c->half_w[0]) / P->pitch);
     int iy = (int)floor((pos[1] + c->half_w[1]) / P->pitch);
     if (ix < 0) ix = 0;
     if (ix >= P->npx) ix = P->npx - 1;
     if (iy < 0) iy = 0;
     if (iy >= P->npy) iy = P->npy - 1;
+    probe_first_deposit(c, p, (int64_t)iy * P->npx + ix);
     int b = (int)(c->hist % (uint64_t)P->n_batches);
     c->tally[((size_t)b * P->npy + iy) * P->npx + ix] += dE;
 }
+
+/* Energy leaving the world (escape), with the probe's count of positrons
+ * that end this way instead of annihilating. */
+static void escape(o_ctx* c, const o_part* p, double E) {
+    c->e_esc += E;
+    if (c->probe && p->type == P_POSITRON) c->probe->n_pos_escape++;
+}
+
+static void probe_max(double* acc, double v) { if (v > *acc) *acc = v; }
+
+/* The probe's record of where a charged primary comes to rest. */
+static void probe_end(o_ctx* c, const o_part* p, const double pos[3]) {
+    orc_probe* Q = c->probe;
+    if (!Q || !p->prim || !Q->end_pos) return;
+    for (int a = 0; a < 3; a++) Q->end_pos[3 * Q->hidx + a] = pos[a];
+}
+
+static void probe_unit(o_ctx* c, const double u[3]) {
+    probe_max(&c->probe->unit_dev, fabs(sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) - 1.0));
+}
+
+/* Azimuth of direction v about axis a in a frame fixed by a alone. */
+static double azimuth_about(const double a[3], const double v[3]) {
+    double r[3] = {1.0, 0.0, 0.0};
+    if (fabs(a[0]) > 0.6) { r[0] = 0.0; r[1] = 1.0; }
+    double e1[3] = {a[1] * r[2] - a[2] * r[1], a[2] * r[0] - a[0] * r[2], a[0] * r[1] - a[1] * r[0]};
+    double n1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (int i = 0; i < 3; i++) e1[i] /= n1;
+    double e2[3] = {a[1] * e1[2] - a[2] * e1[1], a[2] * e1[0] - a[0] * e1[2], a[0] * e1[1] - a[1] * e1[0]};
+    double ph = atan2(v[0] * e2[0] + v[1] * e2[1] + v[2] * e2[2], v[0] * e1[0] + v[1] * e1[1] + v[2] * e1[2]);
+    return ph < 0.0 ? ph + 2.0 * O_PI : ph;
+}
+
+/* Momentum |p| of an electron of kinetic energy T, MeV/c. */
+static double p_of_T(double T) { return sqrt(T * (T + 2.0 * O_MC2)); }
 
 static void ct_props(const o_ctx* c, const int idx[3], double* rho, int* mat) {
     const orc_problem* P = c->P;
@@ -473,14 +576,14 @@ static void transfer_to_epid(o_ctx* c, o_part* p) {
     to_beam(c, p->x, b);
     to_beam_dir(c, p->u, ub);
     double Eexit = p->E + rest_extra(p);
-    if (ub[2] >= 0.0) { c->e_esc += Eexit; return; }
+    if (ub[2] >= 0.0) { escape(c, p, Eexit); return; }
     /* Any point of the vacuum line will do: a Woodcock flight may have carried
      * the photon past the detector plane, but the CT lies wholly above it, so
      * the line's crossing of the detector face is always downstream of the
      * true exit point. */
     double t = (c->zplane[0] - b[2]) / ub[2];
     double X = b[0] + t * ub[0], Y = b[1] + t * ub[1];
-    if (!(fabs(X) < c->half_w[0] && fabs(Y) < c->half_w[1])) { c->e_esc += Eexit; return; }
+    if (!(fabs(X) < c->half_w[0] && fabs(Y) < c->half_w[1])) { escape(c, p, Eexit); return; }
     p->zone = Z_EPID;
     p->x[0] = X; p->x[1] = Y; p->x[2] = c->zplane[0];
     p->u[0] = ub[0]; p->u[1] = ub[1]; p->u[2] = ub[2];
@@ -539,18 +642,44 @@ static void annihilate(o_ctx* c, o_part* parent) {
     double ph = 2.0 * O_PI * rng_u(&parent->rng);
     double st = sqrt(fmax(0.0, 1.0 - ct * ct));
     double d[3] = {st * cos(ph), st * sin(ph), ct};
+    double gu[2][3], gE[2];
     for (int k = 0; k < 2; k++) {
         o_part g;
         make_child(parent, &g, P_PHOTON, (uint32_t)k);
         double sg = k ? -1.0 : 1.0;
         g.u[0] = sg * d[0]; g.u[1] = sg * d[1]; g.u[2] = sg * d[2];
         g.E = O_MC2;
+        for (int a = 0; a < 3; a++) gu[k][a] = g.u[a];
+        gE[k] = g.E;
         c->cnt[C_PHOTONS2]++;
         push(c, &g);
+    }
+    orc_probe* Q = c->probe;
+    if (Q) {
+        double sum = sqrt((gu[0][0] + gu[1][0]) * (gu[0][0] + gu[1][0]) + (gu[0][1] + gu[1][1]) * (gu[0][1] + gu[1][1]) +
+                          (gu[0][2] + gu[1][2]) * (gu[0][2] + gu[1][2]));
+        probe_max(&Q->annih_dev, fmax(sum, fmax(fabs(gE[0] - O_MC2), fabs(gE[1] - O_MC2))));
+        probe_unit(c, gu[0]);
+        if ((int64_t)Q->n_annih < Q->cap) {
+            if (Q->annih_cos) Q->annih_cos[Q->n_annih] = gu[0][2];
+            if (Q->annih_phi) { double a = atan2(gu[0][1], gu[0][0]); Q->annih_phi[Q->n_annih] = a < 0 ? a + 2.0 * O_PI : a; }
+        }
+        Q->n_annih++;
     }
 }
 
 static int layer_mat(const o_ctx* c, int l) { return c->P->layer_mat[l]; }
+
+/* The probe's record of the primary photon's first real interaction: the
+ * EPID layer (or -1 in the CT) and, in the EPID, the beam-frame point. */
+static void probe_first_interaction(o_ctx* c, const o_part* p, int layer) {
+    orc_probe* Q = c->probe;
+    if (!Q || !p->prim || Q->first_done) return;
+    Q->first_done = 1;
+    if (Q->first_layer) Q->first_layer[Q->hidx] = layer;
+    if (Q->first_pos && layer >= 0)
+        for (int a = 0; a < 3; a++) Q->first_pos[3 * Q->hidx + a] = p->x[a];
+}
 
 /* Emit an electron or positron of kinetic energy T created by `parent`, or
  * deposit it when transport is off or T is at the cutoff. */
@@ -589,6 +718,16 @@ static int photon_interact(o_ctx* c, o_part* p, int m, int layer) {
         double T = E0 - E1;
         double pe[3] = {E0 * u0[0] - E1 * p->u[0], E0 * u0[1] - E1 * p->u[1], E0 * u0[2] - E1 * p->u[2]};
         double n = sqrt(pe[0] * pe[0] + pe[1] * pe[1] + pe[2] * pe[2]);
+        orc_probe* Q = c->probe;
+        if (Q) {
+            /* momentum balance with the electron's |p| from its kinetic energy, and the scattering angle */
+            double* dev = (fabs(u0[2]) > 0.99999) ? &Q->polar_dev : &Q->compton_dev;
+            probe_max(dev, fabs(n - p_of_T(T)) / E0);
+            probe_max(dev, fabs(u0[0] * p->u[0] + u0[1] * p->u[1] + u0[2] * p->u[2] - ct));
+            probe_unit(c, p->u);
+            if ((int64_t)Q->n_compton < Q->cap && Q->compton_phi) Q->compton_phi[Q->n_compton] = azimuth_about(u0, p->u);
+            Q->n_compton++;
+        }
         if (n > 0.0) { pe[0] /= n; pe[1] /= n; pe[2] /= n; } else { pe[0] = u0[0]; pe[1] = u0[1]; pe[2] = u0[2]; }
         emit_charged(c, p, P_ELECTRON, T, pe, 0, layer);
         p->E = E1;
@@ -603,6 +742,13 @@ static int photon_interact(o_ctx* c, o_part* p, int m, int layer) {
         double avail = p->E - 2.0 * O_MC2;
         double xu = rng_u(&p->rng);
         double Tm = xu * avail, Tp = avail - Tm;
+        orc_probe* Q = c->probe;
+        if (Q) {
+            probe_max(&Q->pair_dev, fabs(Tm + Tp - (p->E - 2.0 * O_MC2)));
+            if ((int64_t)Q->n_pair < Q->cap && Q->pair_frac) Q->pair_frac[Q->n_pair] = Tm / avail;
+            Q->n_pair++;
+            Q->n_pos_born++;
+        }
         if (P->coupled) {
             emit_charged(c, p, P_ELECTRON, Tm, p->u, 0, layer);
             if (Tp > P->ecut + O_TSTOP) {
@@ -693,6 +839,7 @@ static void photon_ct(o_ctx* c, o_part* p) {
         if (!(rng_u(&p->rng) * Sc < sig)) continue;      /* virtual */
         c->cnt[C_REAL_CT]++;
         p->cell[0] = idx[0]; p->cell[1] = idx[1]; p->cell[2] = idx[2];
+        probe_first_interaction(c, p, -1);
         if (!photon_interact(c, p, m, 0)) return;
     }
     c->e_lost += p->E;
@@ -732,11 +879,16 @@ static void photon_epid(o_ctx* c, o_part* p) {
             }
             tau -= mu * d;
             for (int a = 0; a < 3; a++) p->x[a] += d * p->u[a];
-            if (which != 0) { c->e_esc += p->E; return; }
+            if (which != 0) { escape(c, p, p->E); return; }
             int nl = l + (p->u[2] < 0.0 ? 1 : -1);
-            if (nl < 0 || nl >= P->n_layers) { c->e_esc += p->E; return; }
+            if (nl < 0 || nl >= P->n_layers) {
+                if (c->probe && p->prim && !p->collided && nl >= P->n_layers) c->probe->n_exit_uncollided++;
+                escape(c, p, p->E);
+                return;
+            }
             p->cell[0] = nl;
         }
+        probe_first_interaction(c, p, p->cell[0]);
         if (!photon_interact(c, p, layer_mat(c, p->cell[0]), p->cell[0])) return;
     }
     c->e_lost += p->E;
@@ -754,6 +906,44 @@ static double ct_dist(const o_ctx* c, const double x[3], const double u[3], cons
         if (d < best) { best = d; *axis = a; }
     }
     return fmax(best, 0.0);
+}
+
+/* Where the second segment of a CT hinge step may run through faces: from x
+ * along u for length len, starting in voxel cell, it ends in voxel end (by
+ * floor of the end point).  It runs through if cell is homogeneous (c->hom)
+ * and end lies within O_HOM_R voxels of it along every axis. */
+static int leg_through(const o_ctx* c, const double x[3], const double u[3], const int cell[3], double len,
+                       int end[3]) {
+    const orc_problem* P = c->P;
+    if (!c->hom[((size_t)cell[2] * P->ny + cell[1]) * P->nx + cell[0]]) return 0;
+    for (int a = 0; a < 3; a++) {
+        end[a] = (int)floor((x[a] + len * u[a] - P->origin[a]) / P->vox[a]);
+        if (abs(end[a] - cell[a]) > O_HOM_R) return 0;
+    }
+    return 1;
+}
+
+/* Walk a straight segment of length len from x along u, starting in voxel
+ * cell, face by face (crossing at most O_MAXFACES faces): the voxels it
+ * passes (cells[k]) and the length in each (lens[k]), in order; returns
+ * their number. */
+#define O_MAXFACES (3 * O_HOM_R)
+static int leg_walk(const o_ctx* c, const double x[3], const double u[3], const int cell[3], double len,
+                    int cells[][3], double* lens) {
+    double q[3] = {x[0], x[1], x[2]};
+    int cc[3] = {cell[0], cell[1], cell[2]};
+    double left = len;
+    for (int k = 0; k <= O_MAXFACES; k++) {
+        int ax;
+        double d = ct_dist(c, q, u, cc, &ax);
+        cells[k][0] = cc[0]; cells[k][1] = cc[1]; cells[k][2] = cc[2];
+        if (d >= left || k == O_MAXFACES) { lens[k] = left; return k + 1; }
+        lens[k] = d;
+        left -= d;
+        for (int a = 0; a < 3; a++) q[a] += d * u[a];
+        cc[ax] += (u[ax] > 0.0) ? 1 : -1;
+    }
+    return 0;
 }
 
 static void electron(o_ctx* c, o_part* p) {
@@ -778,32 +968,50 @@ static void electron(o_ctx* c, o_part* p) {
         double Tm = T - 0.5 * dEt;
         double L = rho * (orc_lcol(m, Tm, P->wcc) + orc_lrad_soft(m, Tm, P->wcb));
         double sE = dEt / L;
-        /* (b) distance to a hard event, majorant = value at the step's start */
-        double Sh = rho * (orc_sigma_moller(m, T, P->wcc) + orc_sigma_brem(m, T, P->wcb));
-        double sh = -log(rng_u(&p->rng)) / Sh;
+        /* (b) distance to the next tentative hard event: an optical depth
+         * tau = -ln(xi), taken when none is pending, is spent along the path
+         * against each step's majorant Sh (the hard cross section at the
+         * step's start energy, which bounds it over the step because it never
+         * decreases with T), across steps and faces, until it runs out */
+        double Sh = (c->probe && c->probe->no_hard) ? 0.0
+                    : rho * (orc_sigma_moller(m, T, P->wcc) + orc_sigma_brem(m, T, P->wcb));
+        const double xt = rng_u(&p->rng);            /* drawn every step, used when no depth is pending */
+        if (!(p->tau > 0.0)) p->tau = -log(xt);
+        double sh = p->tau / Sh;
         /* (c) distance to the cell boundary */
         int ax;
         double sb = (p->zone == Z_CT) ? ct_dist(c, p->x, p->u, p->cell, &ax) : epid_dist(c, p->x, p->u, layer, &ax);
         double s = sE; int lim = 0;
         if (sh < s) { s = sh; lim = 1; }
-        if (sb < s) { s = sb; lim = 2; }
         double xh = rng_u(&p->rng), xmu = rng_u(&p->rng), xph = rng_u(&p->rng);
-        /* multiple-scattering deflection for the whole step */
-        double G = s * rho * orc_lambda1_inv(m, T);
+        /* Face rule.  In the CT the hinge is placed on the planned step s, which
+         * ignores voxel faces: a step whose hinge lies beyond the face becomes a
+         * face step (straight to the face).  In the EPID, whose layers are
+         * different materials, every step that would reach a layer face is a
+         * face step. */
+        if ((p->zone == Z_CT) ? (xh * s >= sb) : (sb < s)) { s = sb; lim = 2; }
+        /* multiple-scattering deflection for the distance s, with the scattering
+         * power at the mid-step energy */
+        double G = s * rho * orc_lambda1_inv(m, T - 0.5 * dEt * (s / sE));
         double A = orc_wentzel_A(G);
-        double mu = (G > 0.0) ? sample_ms_mu(A, xmu) : 0.0;
+        double mu = (G > 0.0 && !(c->probe && c->probe->no_ms)) ? sample_ms_mu(A, xmu) : 0.0;
+        const int track = c->probe && p->prim && c->probe->path;
         if (lim == 2) {
-            /* Boundary-limited step: straight to the face, energy deposited at the
-             * segment midpoint, the face crossed, then the deflection applied.
-             * (A random hinge here would leave the particle just short of the
-             * face after a small deflection, and the next, ever-shorter steps
-             * would end where rounding decides the crossing.) */
+            /* Face step: straight to the face, energy deposited at the segment
+             * midpoint, the face crossed, then the deflection for the distance
+             * travelled applied.  (A hinge inside such a step would leave the
+             * particle just short of the face after a small deflection, and the
+             * next, ever-shorter steps would end where rounding decides the
+             * crossing.) */
             double mid[3], hc[3] = {p->cell[0], p->cell[1], p->cell[2]};
             for (int a = 0; a < 3; a++) { mid[a] = p->x[a] + 0.5 * s * p->u[a]; p->x[a] += s * p->u[a]; }
+            if (track) c->probe->path[c->probe->hidx] += s;
             double dE = dEt * (s / sE);
             double Tn = T - dE;
+            p->tau -= s * Sh;
             o_part here = *p;
             if (Tn <= tstop) {
+                probe_end(c, p, mid);
                 deposit(c, &here, mid, (int)hc[0], dE + Tn);
                 if (p->type == P_POSITRON) {
                     p->x[0] = mid[0]; p->x[1] = mid[1]; p->x[2] = mid[2];
@@ -818,9 +1026,9 @@ static void electron(o_ctx* c, o_part* p) {
                 int n[3] = {P->nx, P->ny, P->nz};
                 if (p->cell[ax] < 0 || p->cell[ax] >= n[ax]) { transfer_to_epid(c, p); return; }
             } else {
-                if (ax != 0) { c->e_esc += p->E + rest_extra(p); return; }
+                if (ax != 0) { escape(c, p, p->E + rest_extra(p)); return; }
                 int nl = layer + (p->u[2] < 0.0 ? 1 : -1);
-                if (nl < 0 || nl >= P->n_layers) { c->e_esc += p->E + rest_extra(p); return; }
+                if (nl < 0 || nl >= P->n_layers) { escape(c, p, p->E + rest_extra(p)); return; }
                 p->cell[0] = nl;
             }
             rotate(p->u, 1.0 - 2.0 * mu, 2.0 * O_PI * xph);
@@ -835,15 +1043,28 @@ static void electron(o_ctx* c, o_part* p) {
         double s2 = s - s1;
         int ax2;
         double sb2 = (p->zone == Z_CT) ? ct_dist(c, p->x, p->u, p->cell, &ax2) : epid_dist(c, p->x, p->u, layer, &ax2);
-        int crossed = 0;
-        if (s2 >= sb2) { s2 = sb2; crossed = 1; }
+        int crossed = 0, through = 0, ecell[3];
+        if (s2 >= sb2) {
+            /* In the CT the second segment runs its full length through the
+             * faces it meets if the hinge's voxel is homogeneous and the
+             * segment ends in its neighbourhood; otherwise, and in the EPID,
+             * it stops at the face. */
+            if (p->zone == Z_CT) through = leg_through(c, p->x, p->u, p->cell, s2, ecell);
+            if (!through) { s2 = sb2; crossed = 1; }
+        }
         for (int a = 0; a < 3; a++) p->x[a] += s2 * p->u[a];
+        if (track) c->probe->path[c->probe->hidx] += s1 + s2;
         double dE = dEt * ((s1 + s2) / sE);
         double Tn = T - dE;
+        /* a hard-event step that ran its full length ends at the tentative
+         * event, which consumes the optical depth; otherwise spend the path */
+        const int at_event = (lim == 1 && !crossed);
+        if (at_event) p->tau = 0.0; else p->tau -= (s1 + s2) * Sh;
         o_part here = *p;
         here.cell[0] = hcell[0]; here.cell[1] = hcell[1]; here.cell[2] = hcell[2];
         if (Tn <= tstop) {
             /* the particle stops at its hinge point */
+            probe_end(c, p, hinge);
             deposit(c, &here, hinge, hcell[0], dE + Tn);
             if (p->type == P_POSITRON) {
                 p->x[0] = hinge[0]; p->x[1] = hinge[1]; p->x[2] = hinge[2];
@@ -852,7 +1073,30 @@ static void electron(o_ctx* c, o_part* p) {
             }
             return;
         }
-        deposit(c, &here, hinge, hcell[0], dE);
+        if (through) {
+            /* the step's energy split by path length over the voxels of the
+             * second segment (the first segment and the second's first piece
+             * lie in the hinge's voxel); each piece deposited at its midpoint,
+             * the last in the voxel where the step ends */
+            int segcell[O_MAXFACES + 1][3];
+            double seglen[O_MAXFACES + 1];
+            const int nseg = leg_walk(c, hinge, p->u, hcell, s2, segcell, seglen);
+            for (int a = 0; a < 3; a++) segcell[nseg - 1][a] = ecell[a];
+            double left = dE, at = 0.0;
+            for (int k = 0; k < nseg; k++) {
+                double e = (k + 1 < nseg) ? dE * ((k == 0 ? s1 + seglen[0] : seglen[k]) / (s1 + s2)) : left;
+                double mp[3];
+                for (int a = 0; a < 3; a++) mp[a] = hinge[a] + (at + 0.5 * seglen[k]) * p->u[a];
+                o_part piece = *p;
+                for (int a = 0; a < 3; a++) piece.cell[a] = segcell[k][a];
+                deposit(c, &piece, k == 0 ? hinge : mp, piece.cell[0], e);
+                left -= e;
+                at += seglen[k];
+            }
+            for (int a = 0; a < 3; a++) p->cell[a] = ecell[a];
+        } else {
+            deposit(c, &here, hinge, hcell[0], dE);
+        }
         p->E = Tn;
         if (crossed) {
             if (p->zone == Z_CT) {
@@ -860,18 +1104,25 @@ static void electron(o_ctx* c, o_part* p) {
                 int n[3] = {P->nx, P->ny, P->nz};
                 if (p->cell[ax2] < 0 || p->cell[ax2] >= n[ax2]) { transfer_to_epid(c, p); return; }
             } else {
-                if (ax2 != 0) { c->e_esc += p->E + rest_extra(p); return; }
+                if (ax2 != 0) { escape(c, p, p->E + rest_extra(p)); return; }
                 int nl = layer + (p->u[2] < 0.0 ? 1 : -1);
-                if (nl < 0 || nl >= P->n_layers) { c->e_esc += p->E + rest_extra(p); return; }
+                if (nl < 0 || nl >= P->n_layers) { escape(c, p, p->E + rest_extra(p)); return; }
                 p->cell[0] = nl;
             }
             continue;
         }
-        if (lim == 1) {
+        if (at_event) {
             double Sn_m = rho * orc_sigma_moller(m, Tn, P->wcc);
             double Sn_b = rho * orc_sigma_brem(m, Tn, P->wcb);
             if (!(rng_u(&p->rng) * Sh < Sn_m + Sn_b)) continue;        /* delta event */
-            if (rng_u(&p->rng) * (Sn_m + Sn_b) < Sn_m) {
+            const int is_moller = rng_u(&p->rng) * (Sn_m + Sn_b) < Sn_m;
+            orc_probe* Q = c->probe;
+            if (Q && p->prim && !Q->hard_done) {
+                Q->hard_done = 1;
+                if (Q->hard_T) Q->hard_T[Q->hidx] = Tn;
+                if (Q->hard_type) Q->hard_type[Q->hidx] = is_moller ? 0 : 1;
+            }
+            if (is_moller) {
                 c->cnt[C_MOLLER]++;
                 double eps = sample_moller_eps(&p->rng, Tn, P->wcc);
                 double phi = 2.0 * O_PI * rng_u(&p->rng);
@@ -879,8 +1130,21 @@ static void electron(o_ctx* c, o_part* p) {
                 double cs = sqrt(W * (Tn + 2.0 * O_MC2) / (Tn * (W + 2.0 * O_MC2)));
                 double cp = sqrt(Tp * (Tn + 2.0 * O_MC2) / (Tn * (Tp + 2.0 * O_MC2)));
                 double us[3] = {p->u[0], p->u[1], p->u[2]};
+                const double u0[3] = {p->u[0], p->u[1], p->u[2]};
                 rotate(us, cs, phi);
                 rotate(p->u, cp, phi + O_PI);
+                if (Q) {
+                    /* momentum balance of the free-electron collision */
+                    double p0 = p_of_T(Tn), pw = p_of_T(W), pt = p_of_T(Tp), r2 = 0.0;
+                    for (int a = 0; a < 3; a++) {
+                        double d = p0 * u0[a] - pw * us[a] - pt * p->u[a];
+                        r2 += d * d;
+                    }
+                    probe_max(fabs(u0[2]) > 0.99999 ? &Q->polar_dev : &Q->moller_dev, sqrt(r2) / p0);
+                    probe_unit(c, us);
+                    probe_unit(c, p->u);
+                    Q->n_moller++;
+                }
                 emit_charged(c, p, P_ELECTRON, W, us, 0, layer);
                 p->E = Tp;
             } else {
@@ -890,11 +1154,19 @@ static void electron(o_ctx* c, o_part* p) {
                 make_child(p, &g, P_PHOTON, 0);
                 g.u[0] = p->u[0]; g.u[1] = p->u[1]; g.u[2] = p->u[2];
                 g.E = k;
+                if (Q) {
+                    double r2 = 0.0;
+                    for (int a = 0; a < 3; a++) r2 += (g.u[a] - p->u[a]) * (g.u[a] - p->u[a]);
+                    probe_max(&Q->brem_dev, sqrt(r2));
+                    if ((int64_t)Q->n_brem < Q->cap && Q->brem_x) Q->brem_x[Q->n_brem] = log(k / P->wcb) / log(Tn / P->wcb);
+                    Q->n_brem++;
+                }
                 c->cnt[C_PHOTONS2]++;
                 push(c, &g);
                 p->E = Tn - k;
             }
             if (p->E <= tstop) {
+                probe_end(c, p, p->x);
                 deposit(c, p, p->x, layer, p->E);
                 if (p->type == P_POSITRON) annihilate(c, p);
                 return;
@@ -903,6 +1175,7 @@ static void electron(o_ctx* c, o_part* p) {
     }
     c->e_lost += p->E + rest_extra(p);
     c->cnt[C_LOST]++;
+    if (c->probe && p->type == P_POSITRON) c->probe->n_pos_escape++;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1043,6 +1316,18 @@ static void sample_source(const o_ctx* c, o_rng* r, double* X, double* Y, double
     *E = (P->mono_e > 0.0) ? P->mono_e : sample_spectrum(r, P->e_max, P->pcut);
 }
 
+/* Transport every particle on the stack, and their descendants, to the end. */
+static void drain(o_ctx* c) {
+    while (c->sp > 0) {
+        o_part q = c->stack[--c->sp];
+        if (q.type == P_PHOTON) {
+            if (q.zone == Z_CT) photon_ct(c, &q); else photon_epid(c, &q);
+        } else {
+            electron(c, &q);
+        }
+    }
+}
+
 static void run_history(o_ctx* c, uint64_t h, uint64_t seed) {
     const orc_problem* P = c->P;
     c->hist = h;
@@ -1061,14 +1346,7 @@ static void run_history(o_ctx* c, uint64_t h, uint64_t seed) {
     to_patient(c, sb, p.x);
     to_patient_dir(c, ub, p.u);
     enter_world(c, &p);
-    while (c->sp > 0) {
-        o_part q = c->stack[--c->sp];
-        if (q.type == P_PHOTON) {
-            if (q.zone == Z_CT) photon_ct(c, &q); else photon_epid(c, &q);
-        } else {
-            electron(c, &q);
-        }
-    }
+    drain(c);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1078,6 +1356,82 @@ static void run_history(o_ctx* c, uint64_t h, uint64_t seed) {
 typedef struct {
     o_ctx local; uint64_t seed, h0, n; int tid, nthreads;
 } o_job;
+
+/* Macro-cells of M^3 voxels (the last ones along an axis may be partial);
+ * each keeps the largest density of its non-bone and of its bone voxels, the
+ * local Woodcock majorant. */
+static void ctx_macro_grid(o_ctx* c, int M) {
+    const orc_problem* P = c->P;
+    const int n[3] = {P->nx, P->ny, P->nz};
+    free(c->mg_low);
+    free(c->mg_bone);
+    c->mgM = M;
+    for (int a = 0; a < 3; a++) c->mg[a] = (n[a] + M - 1) / M;
+    size_t ncell = (size_t)c->mg[0] * c->mg[1] * c->mg[2];
+    c->mg_low = (double*)calloc(ncell, sizeof(double));
+    c->mg_bone = (double*)calloc(ncell, sizeof(double));
+    for (int iz = 0; iz < P->nz; iz++)
+        for (int iy = 0; iy < P->ny; iy++)
+            for (int ix = 0; ix < P->nx; ix++) {
+                double rho; int m;
+                orc_hu_to_rho_mat(P->hu[((size_t)iz * P->ny + iy) * P->nx + ix], &rho, &m);
+                size_t cc = ((size_t)(iz / M) * c->mg[1] + iy / M) * c->mg[0] + ix / M;
+                double* tgt = (m == 3) ? &c->mg_bone[cc] : &c->mg_low[cc];
+                if (rho > *tgt) *tgt = rho;
+            }
+}
+
+/* A voxel is homogeneous when it lies at least O_HOM_R voxels inside the CT
+ * and the (2 O_HOM_R + 1)^3 box around it holds one material with HU values
+ * (clamped to [-1024, 3071]) spanning at most O_HOM_SPAN: an electron step's
+ * second segment may then run into that box with the voxel's own stopping
+ * power.  The box minimum and maximum are taken one axis at a time (the
+ * extremes of a box are the extremes of its rows' extremes); materials rise
+ * with HU, so one material means the material of the minimum equals that of
+ * the maximum. */
+static int clamp_hu(int h) { return h < -1024 ? -1024 : (h > 3071 ? 3071 : h); }
+static void ctx_homogeneity(o_ctx* c) {
+    const orc_problem* P = c->P;
+    const int n[3] = {P->nx, P->ny, P->nz};
+    const size_t nv = (size_t)n[0] * n[1] * n[2];
+    const size_t st[3] = {1, (size_t)n[0], (size_t)n[0] * n[1]};
+    int* lo = (int*)malloc(sizeof(int) * nv);
+    int* hi = (int*)malloc(sizeof(int) * nv);
+    int* lo2 = (int*)malloc(sizeof(int) * nv);
+    int* hi2 = (int*)malloc(sizeof(int) * nv);
+    for (size_t v = 0; v < nv; v++) lo[v] = hi[v] = clamp_hu(P->hu[v]);
+    for (int a = 0; a < 3; a++) {
+        for (int iz = 0; iz < n[2]; iz++)
+            for (int iy = 0; iy < n[1]; iy++)
+                for (int ix = 0; ix < n[0]; ix++) {
+                    const int idx[3] = {ix, iy, iz};
+                    const size_t v = ((size_t)iz * n[1] + iy) * n[0] + ix;
+                    int mn = lo[v], mx = hi[v];
+                    for (int d = -O_HOM_R; d <= O_HOM_R; d++) {
+                        const int k = idx[a] + d;
+                        if (k < 0 || k >= n[a]) continue;
+                        const size_t w = v + (ptrdiff_t)d * (ptrdiff_t)st[a];
+                        if (lo[w] < mn) mn = lo[w];
+                        if (hi[w] > mx) mx = hi[w];
+                    }
+                    lo2[v] = mn; hi2[v] = mx;
+                }
+        int* t;
+        t = lo; lo = lo2; lo2 = t;
+        t = hi; hi = hi2; hi2 = t;
+    }
+    c->hom = (unsigned char*)calloc(nv, 1);
+    for (int iz = O_HOM_R; iz + O_HOM_R < n[2]; iz++)
+        for (int iy = O_HOM_R; iy + O_HOM_R < n[1]; iy++)
+            for (int ix = O_HOM_R; ix + O_HOM_R < n[0]; ix++) {
+                const size_t v = ((size_t)iz * n[1] + iy) * n[0] + ix;
+                double r; int m_lo, m_hi;
+                orc_hu_to_rho_mat(lo[v], &r, &m_lo);
+                orc_hu_to_rho_mat(hi[v], &r, &m_hi);
+                c->hom[v] = (unsigned char)(m_lo == m_hi && hi[v] - lo[v] <= O_HOM_SPAN);
+            }
+    free(lo); free(hi); free(lo2); free(hi2);
+}
 
 static void ctx_geometry(o_ctx* c, const orc_problem* P) {
     memset(c, 0, sizeof(*c));
@@ -1101,8 +1455,7 @@ static void ctx_geometry(o_ctx* c, const orc_problem* P) {
         if (rho > c->rho_max[m]) c->rho_max[m] = rho;
     }
     /* macro-cells of M^3 voxels, M the smallest power of two >= 4 giving at
-     * most 4096 cells; each keeps the largest density of its non-bone and of
-     * its bone voxels (the local Woodcock majorant) */
+     * most 4096 cells */
     int n[3] = {P->nx, P->ny, P->nz};
     int M = 4;
     for (;;) {
@@ -1111,26 +1464,15 @@ static void ctx_geometry(o_ctx* c, const orc_problem* P) {
         if (cells <= 4096) break;
         M *= 2;
     }
-    c->mgM = M;
-    for (int a = 0; a < 3; a++) c->mg[a] = (n[a] + M - 1) / M;
-    size_t ncell = (size_t)c->mg[0] * c->mg[1] * c->mg[2];
-    c->mg_low = (double*)calloc(ncell, sizeof(double));
-    c->mg_bone = (double*)calloc(ncell, sizeof(double));
-    for (int iz = 0; iz < P->nz; iz++)
-        for (int iy = 0; iy < P->ny; iy++)
-            for (int ix = 0; ix < P->nx; ix++) {
-                double rho; int m;
-                orc_hu_to_rho_mat(P->hu[((size_t)iz * P->ny + iy) * P->nx + ix], &rho, &m);
-                size_t cc = ((size_t)(iz / M) * c->mg[1] + iy / M) * c->mg[0] + ix / M;
-                double* tgt = (m == 3) ? &c->mg_bone[cc] : &c->mg_low[cc];
-                if (rho > *tgt) *tgt = rho;
-            }
+    ctx_macro_grid(c, M);
 }
 
 static void ctx_free(o_ctx* c) {
     free(c->mg_low);
     free(c->mg_bone);
+    free(c->hom);
     c->mg_low = c->mg_bone = NULL;
+    c->hom = NULL;
 }
 
 static void* worker(void* arg) {
@@ -1150,6 +1492,7 @@ int orc_run(const orc_problem* P, uint64_t seed, uint64_t hist_begin, uint64_t n
     if (!P || !R || !R->tally || P->n_layers < 1 || P->n_layers > O_MAXL || P->n_batches < 1) return 1;
     o_ctx base;
     ctx_geometry(&base, P);
+    ctx_homogeneity(&base);
     if (!build_source(&base)) { free(base.rect); free(base.cdf); ctx_free(&base); return 2; }
     if (n_threads < 1) n_threads = 1;
     if (n_threads > P->n_batches) n_threads = P->n_batches;
@@ -1246,11 +1589,13 @@ double orc_csda_path(int m, double rho, double T0, double ecut, double wcc, doub
 /* First real photon interaction along one fixed ray through the CT of P:
  * for n photons of energy E starting at `start` (patient frame) along `dir`,
  * record the flat voxel index (-1 if none before leaving the box) and the
- * interaction type (0 Compton, 1 photoelectric, 2 pair). */
+ * interaction type (0 Compton, 1 photoelectric, 2 pair).  macro_M > 0 sets
+ * the macro-cell size of the majorant grid (0: the default rule). */
 void orc_first_interaction(const orc_problem* P, double E, const double start[3], const double dir[3],
-                           uint64_t seed, uint64_t n, int64_t* vox, int32_t* type) {
+                           uint64_t seed, uint64_t n, int macro_M, int64_t* vox, int32_t* type) {
     o_ctx c;
     ctx_geometry(&c, P);
+    if (macro_M > 0) ctx_macro_grid(&c, macro_M);
     for (uint64_t i = 0; i < n; i++) {
         o_rng r; hook_rng(&r, seed, i);
         double x[3] = {start[0], start[1], start[2]};
@@ -1272,6 +1617,67 @@ void orc_first_interaction(const orc_problem* P, double E, const double start[3]
         }
     }
     ctx_free(&c);
+}
+
+/* Histories h0 .. h0+n-1 whose primary is the probe's particle (instead of a
+ * source sample), transported by the same code as orc_run with the probe
+ * recording.  A photon primary enters the world along its line (CT box entry,
+ * or straight to the EPID when the line misses the CT); a charged primary must
+ * start inside the CT.  One thread; R accumulates as in orc_run (a positron
+ * primary's source energy includes its rest energy 2 mc^2). */
+int orc_pencil(const orc_problem* P, orc_probe* Q, uint64_t seed, uint64_t h0, uint64_t n, orc_result* R) {
+    if (!P || !Q || !R || !R->tally || P->n_layers < 1 || P->n_layers > O_MAXL || P->n_batches < 1) return 1;
+    if (Q->type < P_PHOTON || Q->type > P_POSITRON || !(Q->E > 0.0)) return 1;
+    o_ctx c;
+    ctx_geometry(&c, P);
+    ctx_homogeneity(&c);
+    if (Q->macro_M > 0) ctx_macro_grid(&c, Q->macro_M);
+    c.tally = R->tally;
+    c.vox = R->vox;
+    c.probe = Q;
+    const int nn[3] = {P->nx, P->ny, P->nz};
+    int cell[3];
+    for (int a = 0; a < 3; a++) {
+        cell[a] = (int)floor((Q->x[a] - P->origin[a]) / P->vox[a]);
+        if (Q->type != P_PHOTON && (cell[a] < 0 || cell[a] >= nn[a])) { ctx_free(&c); return 3; }
+    }
+    for (uint64_t i = 0; i < n; i++) {
+        const uint64_t h = h0 + i;
+        c.hist = h;
+        Q->hidx = (int64_t)i;
+        Q->first_done = Q->pix_done = Q->hard_done = 0;
+        if (Q->path) Q->path[i] = 0.0;
+        if (Q->hard_T) Q->hard_T[i] = -1.0;
+        if (Q->hard_type) Q->hard_type[i] = -1;
+        if (Q->first_layer) Q->first_layer[i] = -2;
+        if (Q->first_pixel) Q->first_pixel[i] = -1;
+        if (Q->first_pos) Q->first_pos[3 * i] = Q->first_pos[3 * i + 1] = Q->first_pos[3 * i + 2] = NAN;
+        if (Q->end_pos) Q->end_pos[3 * i] = Q->end_pos[3 * i + 1] = Q->end_pos[3 * i + 2] = NAN;
+        o_part p;
+        memset(&p, 0, sizeof(p));
+        p.type = Q->type;
+        p.prim = 1;
+        p.rng.key[0] = (uint32_t)seed; p.rng.key[1] = (uint32_t)(seed >> 32);
+        p.rng.hlo = (uint32_t)h; p.rng.hhi = (uint32_t)(h >> 32);
+        p.E = Q->E;
+        c.e_src += Q->E + rest_extra(&p);
+        for (int a = 0; a < 3; a++) { p.x[a] = Q->x[a]; p.u[a] = Q->u[a]; }
+        if (Q->type == P_PHOTON) {
+            enter_world(&c, &p);
+        } else {
+            p.zone = Z_CT;
+            for (int a = 0; a < 3; a++) p.cell[a] = cell[a];
+            if (Q->type == P_POSITRON) Q->n_pos_born++;
+            push(&c, &p);
+        }
+        drain(&c);
+    }
+    R->e_src += c.e_src; R->e_ct += c.e_ct; R->e_esc += c.e_esc; R->e_lost += c.e_lost;
+    for (int k = 0; k < O_MAXL; k++) R->e_epid[k] += c.e_epid[k];
+    for (int k = 0; k < C_NCOUNT; k++) R->counters[k] += c.cnt[k];
+    free(c.stack);
+    ctx_free(&c);
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -74,6 +74,8 @@ struct mc_ctx {
     double vox[3] = {0, 0, 0}, origin[3] = {0, 0, 0};
     int16_t* d_hu = nullptr;
     float* d_rho = nullptr;
+    unsigned char* d_hom = nullptr;   // homogeneity flags of the CT voxels
+    int* d_hom_tmp = nullptr;         // two int32 per voxel: scratch of the flag passes
     size_t nvox_alloc = 0;
     unsigned int* d_rho_max = nullptr;
     float* d_thr = nullptr;
@@ -183,6 +185,7 @@ void make_params(const mc_ctx* c, Params& P, uint64_t seed) {
     P.vx = static_cast<float>(c->vox[0]); P.vy = static_cast<float>(c->vox[1]); P.vz = static_cast<float>(c->vox[2]);
     P.ivx = 1.0f / P.vx; P.ivy = 1.0f / P.vy; P.ivz = 1.0f / P.vz;
     P.rho = c->d_rho;
+    P.hom = c->d_hom;
     for (int m = 0; m < 4; ++m) P.rho_max[m] = c->rho_max[m];
     P.mgM = c->mgM; P.mgx = c->mg[0]; P.mgy = c->mg[1]; P.mgz = c->mg[2];
     P.mgrid = c->d_mgrid;
@@ -796,14 +799,14 @@ mc_status mc_create(const mc_config* cfg_in, int device, mc_ctx** out) {
 
     c->cap = cfg.bank_capacity;
     const size_t per = static_cast<size_t>(c->cap) * 4;
-    const size_t total = per * 12 * mc::kNumBanks * 2;
+    const size_t total = per * 13 * mc::kNumBanks * 2;
     if (cudaMalloc(&c->bank_mem, total) != cudaSuccess) return bail(MC_ERR_OOM);
     char* base = static_cast<char*>(c->bank_mem);
     for (int t = 0; t < mc::kNumBanks; ++t) {
         for (int k = 0; k < 2; ++k) {
             BankPtr& b = c->bank[t][k];
-            float** f[7] = {&b.x, &b.y, &b.z, &b.u, &b.v, &b.w, &b.E};
-            for (int i = 0; i < 7; ++i) { *f[i] = reinterpret_cast<float*>(base); base += per; }
+            float** f[8] = {&b.x, &b.y, &b.z, &b.u, &b.v, &b.w, &b.E, &b.tau};
+            for (int i = 0; i < 8; ++i) { *f[i] = reinterpret_cast<float*>(base); base += per; }
             uint32_t** q[5] = {&b.hist, &b.ord, &b.draws, &b.cell, &b.flags};
             for (int i = 0; i < 5; ++i) { *q[i] = reinterpret_cast<uint32_t*>(base); base += per; }
         }
@@ -851,6 +854,8 @@ mc_status mc_destroy(mc_ctx* c) {
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     dfree(c->d_hu);
     dfree(c->d_rho);
+    dfree(c->d_hom);
+    dfree(c->d_hom_tmp);
     dfree(c->d_rho_max);
     dfree(c->d_thr);
     dfree(c->d_mgrid);
@@ -891,14 +896,20 @@ mc_status mc_init_geometry(mc_ctx* c, const int16_t* hu, int nx, int ny, int nz,
     if (nvox > c->nvox_alloc) {
         dfree(c->d_hu);
         dfree(c->d_rho);
+        dfree(c->d_hom);
+        dfree(c->d_hom_tmp);
         CUDA_TRY(c, cudaMalloc(&c->d_hu, nvox * sizeof(int16_t) + 16));
         CUDA_TRY(c, cudaMalloc(&c->d_rho, nvox * sizeof(float) + 32));
+        CUDA_TRY(c, cudaMalloc(&c->d_hom, nvox + 16));
+        CUDA_TRY(c, cudaMalloc(&c->d_hom_tmp, 2 * nvox * sizeof(int)));
         c->nvox_alloc = nvox;
     }
     CUDA_TRY(c, cudaMemcpyAsync(c->d_hu, hu, nvox * sizeof(int16_t),
                                 hu_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaMemsetAsync(c->d_rho_max, 0, sizeof(unsigned int) * 4, s));
     CUDA_TRY(c, mc::launch_hu_to_rho(c->d_hu, c->d_rho, nvox, c->d_rho_max, c->d_thr, c->sm_count, s));
+    CUDA_TRY(c, mc::launch_homogeneity(c->d_hu, nx, ny, nz, mc::kHomRadius, mc::kHomSpan, c->d_hom_tmp, c->d_hom,
+                                       c->sm_count, s));
     unsigned int bits[4];
     CUDA_TRY(c, cudaMemcpyAsync(bits, c->d_rho_max, sizeof(bits), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(c, cudaMemcpyAsync(c->thr, c->d_thr, sizeof(c->thr), cudaMemcpyDeviceToHost, s));

@@ -286,6 +286,62 @@ cudaError_t launch_hu_to_rho(const int16_t* hu, float* rho, size_t n, unsigned i
     return cudaGetLastError();
 }
 
+// One axis of the box extremes behind the homogeneity flags: for each voxel
+// the least and greatest value over `radius` voxels either side along `axis`
+// (cut at the CT's edge), packed as (least & 0xffff) | (greatest << 16).  The
+// first pass reads the clamped HU itself; the last turns the box extremes
+// into the flag.  Extremes of a box are the extremes of its rows' extremes,
+// and materials rise with HU, so one material means that the least and the
+// greatest value have the same material.
+__device__ __forceinline__ int clamp_hu_dev(int h) { return min(max(h, -1024), 3071); }
+__device__ __forceinline__ int material_of_hu(int h) { return (h < -900) ? 0 : (h < -200) ? 1 : (h < 300) ? 2 : 3; }
+
+__global__ void k_hom_pass(const int16_t* __restrict__ hu, const int* __restrict__ in, int nx, int ny, int nz,
+                           int axis, int radius, int span, int* __restrict__ out, unsigned char* __restrict__ flag) {
+    const size_t n = static_cast<size_t>(nx) * ny * nz;
+    const int dim = (axis == 0) ? nx : (axis == 1) ? ny : nz;
+    const size_t stride = (axis == 0) ? 1 : (axis == 1) ? static_cast<size_t>(nx) : static_cast<size_t>(nx) * ny;
+    for (size_t v = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; v < n;
+         v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int ix = static_cast<int>(v % nx), iy = static_cast<int>((v / nx) % ny), iz = static_cast<int>(v / (static_cast<size_t>(nx) * ny));
+        const int k = (axis == 0) ? ix : (axis == 1) ? iy : iz;
+        int lo = 1 << 20, hi = -(1 << 20);
+        for (int d = -radius; d <= radius; ++d) {
+            if (k + d < 0 || k + d >= dim) continue;
+            const size_t w = v + static_cast<ptrdiff_t>(d) * static_cast<ptrdiff_t>(stride);
+            int a, b;
+            if (hu) {
+                a = b = clamp_hu_dev(__ldg(&hu[w]));
+            } else {
+                const int q = __ldg(&in[w]);
+                a = static_cast<int16_t>(q & 0xffff);
+                b = q >> 16;
+            }
+            lo = min(lo, a);
+            hi = max(hi, b);
+        }
+        if (flag) {
+            const bool inside = ix >= radius && ix < nx - radius && iy >= radius && iy < ny - radius &&
+                                iz >= radius && iz < nz - radius;
+            flag[v] = (inside && material_of_hu(lo) == material_of_hu(hi) && hi - lo <= span) ? 1 : 0;
+        } else {
+            out[v] = (lo & 0xffff) | (hi << 16);
+        }
+    }
+}
+
+cudaError_t launch_homogeneity(const int16_t* hu, int nx, int ny, int nz, int radius, int span, int* tmp,
+                               unsigned char* flag, int sm_count, cudaStream_t s) {
+    const size_t n = static_cast<size_t>(nx) * ny * nz;
+    int* a = tmp;
+    int* b = tmp + n;
+    const int grid = sm_count * 8, block = 256;
+    k_hom_pass<<<grid, block, 0, s>>>(hu, nullptr, nx, ny, nz, 0, radius, span, a, nullptr);
+    k_hom_pass<<<grid, block, 0, s>>>(nullptr, a, nx, ny, nz, 1, radius, span, b, nullptr);
+    k_hom_pass<<<grid, block, 0, s>>>(nullptr, b, nx, ny, nz, 2, radius, span, nullptr, flag);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_macro_grid(const float* rho, int nx, int ny, int nz, int M, int mgx, int mgy, int mgz,
                               float thr_bone, float2* grid, int sm_count, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(grid, 0, sizeof(float2) * static_cast<size_t>(mgx) * mgy * mgz, s);

@@ -30,6 +30,11 @@ constexpr int kPhotonNodes = 2048;
 constexpr int kElectronNodes = 512;
 constexpr int kWentzelNodes = 2048;
 constexpr int kMaxMacroCells = 4096;
+// Homogeneous CT voxels (electron steps' second segments may cross their faces):
+// at least kHomRadius voxels inside the CT, one material and an HU span of at
+// most kHomSpan over the (2 kHomRadius + 1)^3 box around them.
+constexpr int kHomRadius = 2;
+constexpr int kHomSpan = 200;
 constexpr int kNumMat = 7;
 constexpr int kMaxLayers = 8;
 constexpr float kQuantaPerMeV = 2.56e8f;      // tally unit 2^-8 eV
@@ -58,7 +63,7 @@ struct MatC {
 };
 
 struct BankPtr {
-    float *x, *y, *z, *u, *v, *w, *E;
+    float *x, *y, *z, *u, *v, *w, *E, *tau;
     uint32_t *hist, *ord, *draws, *cell, *flags;
 };
 
@@ -100,6 +105,7 @@ struct Params {
     int nx, ny, nz;
     float ox, oy, oz, vx, vy, vz, ivx, ivy, ivz;
     const float* rho;
+    const unsigned char* hom;      // per voxel: 1 if homogeneous (electron second segments may cross its faces)
     float rho_max[4];
     float thr[3];                   // density thresholds lung / water / bone
     int mgM, mgx, mgy, mgz;         // macro-cells: M voxels per side, cells per axis (<= 4096 cells)
@@ -252,6 +258,7 @@ __device__ __forceinline__ uint32_t pool_reserve(bool want, uint32_t* counter, v
 
 struct Part {
     float x, y, z, u, v, w, E;
+    float tau;       // charged particles: optical depth left to the next tentative hard event (<= 0: none drawn)
     uint32_t hist, cell, flags;
     Rng rng;
 };
@@ -260,6 +267,7 @@ __device__ __forceinline__ void load_part(const BankPtr& b, uint32_t i, Part& p,
     p.x = b.x[i]; p.y = b.y[i]; p.z = b.z[i];
     p.u = b.u[i]; p.v = b.v[i]; p.w = b.w[i];
     p.E = b.E[i];
+    p.tau = b.tau[i];
     p.hist = b.hist[i];
     p.cell = b.cell[i];
     p.flags = b.flags[i];
@@ -271,6 +279,7 @@ __device__ __forceinline__ void store_part(const BankPtr& b, uint32_t i, const P
     b.x[i] = p.x; b.y[i] = p.y; b.z[i] = p.z;
     b.u[i] = p.u; b.v[i] = p.v; b.w[i] = p.w;
     b.E[i] = p.E;
+    b.tau[i] = p.tau;
     b.hist[i] = p.hist;
     b.ord[i] = p.rng.ord;
     b.draws[i] = p.rng.d;

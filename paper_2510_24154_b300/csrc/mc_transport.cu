@@ -429,21 +429,77 @@ __device__ __forceinline__ bool photon_epid_event(const Params& P, const float2*
     return false;
 }
 
+// Where the second segment of a CT hinge step may run through faces: from
+// the hinge (p's position and direction, voxel `cell`, homogeneous or not:
+// `hom`) for length `len` it ends in voxel `end` (by floor of the end point).
+// Returns true if `cell` is homogeneous and `end` lies within kHomRadius
+// voxels of it along every axis (and so inside the CT).
+constexpr int kMaxLegFaces = 3 * kHomRadius + 1;
+__device__ __forceinline__ bool leg_through(const Params& P, const Part& p, uint32_t cell, bool hom, float len,
+                                            uint32_t& end) {
+    if (!hom) return false;
+    const int ex = __float2int_rd((fmaf(len, p.u, p.x) - P.ox) / P.vx);
+    const int ey = __float2int_rd((fmaf(len, p.v, p.y) - P.oy) / P.vy);
+    const int ez = __float2int_rd((fmaf(len, p.w, p.z) - P.oz) / P.vz);
+    if (abs(ex - cell_x(cell)) > kHomRadius || abs(ey - cell_y(cell)) > kHomRadius ||
+        abs(ez - cell_z(cell)) > kHomRadius)
+        return false;
+    end = pack_cell(ex, ey, ez);
+    return true;
+}
+
+// The patient-dose deposits of a CT hinge step whose second segment ran
+// through faces: the step's energy e_step split by path length, (s1 + d0) /
+// (s1 + len) into the hinge's voxel `cell` (d0: distance to the first face,
+// on axis ax0), then each further piece into the voxel it crosses, walked
+// face by face from the hinge (p's position and direction), the last piece
+// (the remainder) into `end`.
+__device__ __forceinline__ void leg_deposit(const Params& P, Acc& a, const Part& p, uint32_t cell, uint32_t end,
+                                            float len, float d0, int ax0, float s1, float e_step) {
+    int c[3] = {cell_x(cell), cell_y(cell), cell_z(cell)};
+    float e = e_step * ((s1 + d0) / (s1 + len));
+    deposit<false>(P, a, nullptr, cell, 0.0f, 0.0f, 0u, 0u, e);
+    float left = e_step - e, done = d0;
+    int ax = ax0;
+    Part q = p;
+#pragma unroll 1
+    for (int k = 1; k < kMaxLegFaces; ++k) {
+        const float dir = (ax == 0) ? p.u : (ax == 1) ? p.v : p.w;
+        c[ax] += (dir > 0.0f) ? 1 : -1;
+        const uint32_t cc = pack_cell(c[0], c[1], c[2]);
+        if (cc == end) break;
+        q.x = fmaf(done, p.u, p.x); q.y = fmaf(done, p.v, p.y); q.z = fmaf(done, p.w, p.z);
+        const float d = ct_dist(P, q, cc, ax);
+        if (d >= len - done) break;
+        e = e_step * (d / (s1 + len));
+        deposit<false>(P, a, nullptr, cc, 0.0f, 0.0f, 0u, 0u, e);
+        left -= e;
+        done += d;
+    }
+    deposit<false>(P, a, nullptr, end, 0.0f, 0.0f, 0u, 0u, left);
+}
+
 // One condensed-history step of an electron or positron.
 //
 // Step length: the least of the 5 % energy-loss step (midpoint stopping
-// power), the distance to a hard event (delta tracking against the
-// start-of-step cross section) and the distance to the cell face.  The
-// deflection for the whole step is drawn once.  An energy-loss or hard-event
-// limited step is a random hinge (first segment, deflection, second segment
-// clipped at a face); a face-limited step goes straight to the face, deposits
-// at its midpoint, crosses and keeps the deflection only if it stays inside.
-// Both kinds run through one code path, selecting where they differ, so the
-// warp diverges as little as possible.
+// power) and the distance to a hard event (delta tracking against the
+// start-of-step cross section); the deflection, with the scattering power at
+// the mid-step energy, is drawn once.  Faces: in the CT the hinge is placed on
+// that planned step, and a step whose hinge lies beyond the voxel face goes
+// straight to the face, deposits at its midpoint, crosses and then deflects
+// for the distance travelled; otherwise the step is a random hinge whose
+// second segment runs its full length through the faces it meets (its energy
+// split among the voxels by path length) if the hinge's voxel is homogeneous
+// and the segment ends within kHomRadius voxels of it, else it stops at the
+// face.  In the EPID every step that would reach a layer face is
+// a face step and second segments stop at faces.  Both kinds run through one
+// code path, selecting where they differ, so the warp diverges as little as
+// possible.
 template <bool EPID>
 __device__ __forceinline__ bool electron_event(const Params& P, const float2* tab, Acc& a,
                                                unsigned long long* s_energy, unsigned long long* s_events,
-                                               Part& p, Emit& e0, Emit& e1, bool& move, float& rho_c) {
+                                               Part& p, Emit& e0, Emit& e1, bool& move, float& rho_c,
+                                               bool& hom_c) {
     float rho;
     int m, layer = 0;
     if (EPID) {
@@ -451,7 +507,7 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
         rho = P.lrho[layer];
         m = P.lmat[layer];
     } else {
-        rho = rho_c;               // the density of p.cell, loaded when the electron entered it
+        rho = rho_c;               // the density of p.cell, loaded (with hom_c) when the electron entered it
         m = material_of(P, rho);
     }
     ++a.steps;
@@ -464,22 +520,27 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     const float Tm = T - 0.5f * dEt;
     const float L = rho * electron_tab(tab, P, m, logf(Tm)).x;
     const float sE = dEt / L;
-    // (b) hard-event distance against the start-of-step cross section
+    // (b) distance to the next tentative hard event: the optical depth p.tau,
+    // taken when none is pending, is spent against each step's majorant (the
+    // start-of-step hard cross section) across steps and faces
     const float lnT = logf(T);
     // hard bremsstrahlung exists only above wcb: A ln(T / wcb) for T > wcb
     const float Sh = rho * (electron_tab(tab, P, m, lnT).y + mcst.brem * fmaxf(lnT - P.ln_wcb, 0.0f));
-    const float sh = -logf(p.rng.u()) / Sh;
+    const float xt = p.rng.u();                 // drawn every step, used when no depth is pending
+    p.tau = (p.tau > 0.0f) ? p.tau : -logf(xt);
+    const float sh = p.tau / Sh;
     // (c) cell face
     int ax;
     const float sb = EPID ? epid_dist(P, p, layer, ax) : ct_dist(P, p, p.cell, ax);
     float s = sE;
     int lim = 0;
     if (sh < s) { s = sh; lim = 1; }
-    if (sb < s) { s = sb; lim = 2; }
     const float xh = p.rng.u(), xmu = p.rng.u(), xph = p.rng.u();
-    // multiple-scattering deflection for the whole step
-    const float pc2 = T * (T + 2.0f * kMec2);
-    const float pb2 = pc2 * pc2 / ((T + kMec2) * (T + kMec2));
+    if (EPID ? (sb < s) : (xh * s >= sb)) { s = sb; lim = 2; }
+    // multiple-scattering deflection for the distance s, at the mid-step energy
+    const float Tg = T - 0.5f * dEt * (s / sE);
+    const float pc2 = Tg * (Tg + 2.0f * kMec2);
+    const float pb2 = pc2 * pc2 / ((Tg + kMec2) * (Tg + kMec2));
     const float G = s * rho * mcst.msc / pb2;
     float mu = 0.0f;
     if (G > 0.0f) {
@@ -497,27 +558,37 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     const uint32_t hcell = p.cell;
     const float u0 = p.u, v0 = p.v, w0 = p.w;                  // direction before the deflection
     rotate_dir(p.u, p.v, p.w, 1.0f - 2.0f * mu, cp, sp);
-    // second segment (hinge steps only), clipped at the first face it meets
+    // second segment (hinge steps only): in the CT it runs its full length
+    // through the voxels it meets unless it would leave the CT; otherwise it
+    // stops at the first face it meets
     float s2 = 0.0f;
-    bool crossed = face;
-    int cax = ax;
+    bool crossed = face, through = false;
+    int cax = ax, ax2 = 0;
+    float sb2 = 0.0f;
+    uint32_t ecell = p.cell;
     // direction component across the crossed face: in the EPID face 0 is a layer
     // plane (z) and faces 1, 2 are the lateral edges; in the CT faces 0, 1, 2 are x, y, z
     float cdir = EPID ? w0 : (ax == 0) ? u0 : (ax == 1) ? v0 : w0;
     if (!face) {
-        int ax2;
-        const float sb2 = EPID ? epid_dist(P, p, layer, ax2) : ct_dist(P, p, p.cell, ax2);
+        sb2 = EPID ? epid_dist(P, p, layer, ax2) : ct_dist(P, p, p.cell, ax2);
         s2 = s - s1;
         if (s2 >= sb2) {
-            s2 = sb2;
-            crossed = true;
-            cax = ax2;
-            cdir = EPID ? p.w : (ax2 == 0) ? p.u : (ax2 == 1) ? p.v : p.w;
+            if (!EPID) through = leg_through(P, p, p.cell, hom_c, s2, ecell);
+            if (!through) {
+                s2 = sb2;
+                crossed = true;
+                cax = ax2;
+                cdir = EPID ? p.w : (ax2 == 0) ? p.u : (ax2 == 1) ? p.v : p.w;
+            }
         }
         p.x += s2 * p.u; p.y += s2 * p.v; p.z += s2 * p.w;
     }
     const float dE = dEt * ((s1 + s2) / sE);
     const float Tn = T - dE;
+    // a hard-event step that ran its full length ends at the tentative event,
+    // which consumes the optical depth; any other step spends its path
+    const bool at_event = (lim == 1) && !crossed;
+    p.tau = at_event ? 0.0f : p.tau - (s1 + s2) * Sh;
     if (Tn <= P.tstop) {
         deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, p.flags, dE + Tn);
         if (p.flags & kPositron) {
@@ -526,7 +597,23 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
         }
         return false;
     }
-    deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, p.flags, dE);
+    if (!EPID && through) {
+        // the step ends in voxel ecell; with the patient-dose tally on, its
+        // energy is split among the voxels of the second segment
+        if (P.vox) {
+            Part hp = p;
+            hp.x = hx; hp.y = hy; hp.z = hz;
+            leg_deposit(P, a, hp, hcell, ecell, s2, sb2, ax2, s1, dE);
+        } else {
+            deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, p.flags, dE);
+        }
+        p.cell = ecell;
+        const size_t v = (static_cast<size_t>(cell_z(ecell)) * P.ny + cell_y(ecell)) * P.nx + cell_x(ecell);
+        rho_c = __ldg(&P.rho[v]);                               // used next step
+        hom_c = __ldg(&P.hom[v]) != 0;
+    } else {
+        deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, p.flags, dE);
+    }
     p.E = Tn;
     if (crossed) {
         bool out;
@@ -541,7 +628,9 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
             out = ix < 0 || ix >= P.nx || iy < 0 || iy >= P.ny || iz < 0 || iz >= P.nz;
             if (!out) {
                 p.cell = pack_cell(ix, iy, iz);
-                rho_c = __ldg(&P.rho[(static_cast<size_t>(iz) * P.ny + iy) * P.nx + ix]);   // used next step
+                const size_t v = (static_cast<size_t>(iz) * P.ny + iy) * P.nx + ix;
+                rho_c = __ldg(&P.rho[v]);                       // used next step
+                hom_c = __ldg(&P.hom[v]) != 0;
             }
         }
         if (out) {
@@ -553,7 +642,7 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
         }
         return true;
     }
-    if (lim != 1) return true;
+    if (!at_event) return true;
     const float lnTn = logf(Tn);
     const float snm = rho * electron_tab(tab, P, m, lnTn).y;
     const float snb = rho * mcst.brem * fmaxf(lnTn - P.ln_wcb, 0.0f);
@@ -628,6 +717,7 @@ __device__ __forceinline__ void flush_emission(const Params& P, const Emit& e, c
                 b.x[slot] = parent.x; b.y[slot] = parent.y; b.z[slot] = parent.z;
                 b.u[slot] = sg * e.u; b.v[slot] = sg * e.v; b.w[slot] = sg * e.w;
                 b.E[slot] = e.E;
+                b.tau[slot] = 0.0f;
                 b.hist[slot] = parent.hist;
                 b.ord[slot] = ord;
                 b.draws[slot] = 0u;
@@ -663,6 +753,7 @@ __device__ __forceinline__ bool start_primary(const Params& P, unsigned long lon
     const uint32_t idx = static_cast<uint32_t>(k - __ldg(&P.first[f]));
     p.hist = idx;
     p.cell = 0u;
+    p.tau = 0.0f;
     p.flags = static_cast<uint32_t>(f) << kFieldShift;
     p.rng.setup(P.seed, F.hist_base + idx, 0u, 0u);
     const double xi = static_cast<double>(p.rng.u());
@@ -767,6 +858,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
     bool in_open = true;
     int steps_here = 0;
     float rho_c = 0.0f;         // electrons in the CT: density of the current voxel
+    bool hom_c = false;         // and whether it is homogeneous
     // input segment this warp reads first, and the segments found dry
     int seg = static_cast<int>((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kHeadShards);
     uint32_t dry = 0u;
@@ -802,9 +894,12 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
             if (got && !(p.flags & kDead)) {
                 alive = true;
                 steps_here = 0;
-                if (TYPE == kElectronCT)
-                    rho_c = __ldg(&P.rho[(static_cast<size_t>(cell_z(p.cell)) * P.ny + cell_y(p.cell)) * P.nx +
-                                         cell_x(p.cell)]);
+                if (TYPE == kElectronCT) {
+                    const size_t v = (static_cast<size_t>(cell_z(p.cell)) * P.ny + cell_y(p.cell)) * P.nx +
+                                     cell_x(p.cell);
+                    rho_c = __ldg(&P.rho[v]);
+                    hom_c = __ldg(&P.hom[v]) != 0;
+                }
             }
         }
         const unsigned live = __ballot_sync(kFull, alive);
@@ -833,7 +928,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
                 if (rep > 0 && !(keep && e0.dest < 0 && e1.dest < 0)) break;
                 if (TYPE == kPhotonCT) keep = photon_ct_event(P, s_tab, s_grid, acc, s_energy, s_events, p, e0, e1, move);
                 else if (TYPE == kPhotonEPID) keep = photon_epid_event(P, s_tab, acc, s_energy, s_events, p, e0, e1);
-                else keep = electron_event<kEpid>(P, s_tab, acc, s_energy, s_events, p, e0, e1, move, rho_c);
+                else keep = electron_event<kEpid>(P, s_tab, acc, s_energy, s_events, p, e0, e1, move, rho_c, hom_c);
                 if (keep && ++steps_here > P.max_steps) {
                     acc.lost += quanta(p.E + rest_extra(p.flags));
                     atomicAdd(&s_events[kCLost], 1ull);

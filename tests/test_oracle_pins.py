@@ -747,3 +747,353 @@ def test_collimation_arguments_checked():
     for kw in (dict(tg_width=1.0), dict(jaw_transmission=1.0), dict(leaf_gap=-0.1), dict(leaf_transmission=-0.1)):
         with pytest.raises(ValueError):
             _sample(W.Field(edges, leaves, jaws, np.ones(1), **kw), 10)
+
+
+# ------------------------------------------------------------------------
+# Transport-loop pins.  These drive the oracle's own transport code (the
+# function orc_run uses, entered through orc_pencil with one fixed primary
+# particle and a probe that records facts about it), not restatements of it.
+# ------------------------------------------------------------------------
+
+def _box(vox, half=4.0, hu=0, offset=(0.0, 0.0, 0.0)):
+    """A cube of side 2*half of uniform HU, voxels of `vox` cm, centred at `offset`."""
+    n = int(round(2 * half / vox))
+    p = W.config_water_open(n_histories=1)
+    p.phantom = W.Phantom(np.full((n, n, n), hu, np.int16), (vox,) * 3,
+                          tuple(o - half for o in offset))
+    return p
+
+
+_COUPLED = W.Physics(coupled=True)
+_PHOTON_ONLY = W.Physics(coupled=False)
+
+
+def _lw(T):
+    """Restricted stopping power of water (collision + soft radiative), MeV cm^2/g."""
+    return L.orc_lcol(W.MAT_WATER, T, 0.2) + L.orc_lrad_soft(W.MAT_WATER, T, 0.01)
+
+
+def _csda_table(T0, n=800):
+    """Path length s(T) = int_T^T0 dE / L(E) on a dense energy grid (FP64
+    quadrature piece by piece), for inverting the CSDA energy-depth relation."""
+    Ts = np.concatenate([np.linspace(0.2, 0.4, 200), np.geomspace(0.4, T0, n)[1:]]) if T0 > 0.4 else \
+        np.linspace(0.2, T0, n)
+    pieces = [integrate.quad(lambda t: 1.0 / _lw(t), a, b, epsrel=1e-12)[0] for a, b in zip(Ts[:-1], Ts[1:])]
+    R = np.concatenate([[0.0], np.cumsum(pieces)])          # range from 0.2 MeV up to Ts[k]
+    return Ts, R[-1] - R                                     # path from T0 down to Ts[k]
+
+
+@pytest.mark.parametrize("T0", [1.0, 3.0, 6.0])
+@pytest.mark.parametrize("vox", [0.1, 0.25, 0.5])
+def test_electron_loop_track_length_is_the_csda_range(T0, vox):
+    """Electron loop with deflections and hard events off, in water of three
+    voxel sizes: every primary's track length equals int_{Ecut}^{T0} dE/L.
+
+    The step rule integrates with the mid-step stopping power over 5 % energy
+    steps (steps cut at faces restart it): an O(step^2) quadrature whose error
+    stays below 2e-4 here.  A wrong energy scaling of face-limited pieces or a
+    voxel-size dependent track length moves the path by percents."""
+    Ts, s = _csda_table(T0)
+    R = s[0]
+    r = oracle.pencil(_box(vox), "electron", T0, [0, 0, 0], [1, 0, 0], 400, no_ms=True, no_hard=True,
+                      physics=_COUPLED, seed=2)
+    assert np.all(np.abs(r["path"] / R - 1.0) < 1e-3), np.max(np.abs(r["path"] / R - 1.0))
+    assert r["e_ct"] == pytest.approx(400 * T0, rel=1e-12)
+
+
+@pytest.mark.parametrize("T0", [1.0, 6.0])
+@pytest.mark.parametrize("vox", [0.1, 0.25, 0.5])
+def test_electron_loop_deposits_follow_the_csda_energy_profile(T0, vox):
+    """Same straight CSDA electrons: the energy left in voxel i along the track
+    equals T(x_i) - T(x_{i+1}), T(x) the CSDA energy at depth x (and 0 past the
+    range, where the cutoff energy is deposited).  Pins the face crossing (the
+    split of a step's loss between voxels by path length) and the voxel a
+    deposit goes to; bar 1e-3 T0 per voxel (the quadrature error above)."""
+    Ts, s = _csda_table(T0)
+    n_hist = 2000
+    prob = _box(vox)
+    r = oracle.pencil(prob, "electron", T0, [0, 0, 0], [1, 0, 0], n_hist, no_ms=True, no_hard=True,
+                      physics=_COUPLED, seed=4, patient_dose=True)
+    nx = prob.phantom.hu.shape[2]
+    prof = r["vox"].sum(axis=(0, 1))[nx // 2:] / n_hist
+    edges = np.arange(prof.size + 1) * vox
+    order = np.argsort(s)
+    T_of_x = lambda x: np.where(x < s[0], np.interp(x, s[order], Ts[order]), 0.0)
+    want = T_of_x(edges[:-1]) - T_of_x(edges[1:])
+    assert np.max(np.abs(prof - want)) < 1e-3 * T0, np.max(np.abs(prof - want))
+    assert r["vox"].sum(axis=(0, 1))[:nx // 2].sum() == 0.0     # nothing upstream of the start
+
+
+def _lewis_depth(T0):
+    """Lewis (1950): for continuous slowing down with transport cross section
+    1/lambda1(T), <cos theta>(s) = exp(-int_0^s ds'/lambda1), so the mean depth
+    along the initial direction at the end of the track is
+    int_{Ecut}^{T0} exp(-K(T)) dT / L(T),  K(T) = int_T^{T0} dT' / (lambda1 L)."""
+    lam = lambda T: L.orc_lambda1_inv(W.MAT_WATER, T)
+    K = lambda T: integrate.quad(lambda t: lam(t) / _lw(t), T, T0, epsrel=1e-11)[0]
+    return integrate.quad(lambda T: math.exp(-K(T)) / _lw(T), 0.2, T0, epsrel=1e-10, limit=200)[0]
+
+
+@pytest.mark.parametrize("T0", [1.0, 3.0, 6.0])
+@pytest.mark.parametrize("vox", [8.0, 0.5, 0.25, 0.1])
+def test_electron_mean_stopping_depth_is_lewis(T0, vox):
+    """Multiple scattering on (random hinge, Wentzel angles), hard events off:
+    the mean depth at which electrons stop equals Lewis' closed form within
+    3 sigma, with no voxel faces (one 8 cm voxel) and with 5, 2.5 and 1 mm
+    voxels.  Pins the hinge position, the scattering power at the mid-step
+    energy and the face rule (a face step deflects at the face for the
+    distance travelled; a hinge step's second segment runs its full length
+    through faces): each of the alternatives measured (deflection at the end
+    or start, scattering power at the step's start, second segments cut at
+    faces, no deflection before a face) misses by 1-8 % at some voxel size."""
+    n = 100_000
+    start = [0.0, 0.0, 0.0] if vox < 8.0 else [0.01, 0.0, 0.0]
+    r = oracle.pencil(_box(vox), "electron", T0, start, [1, 0, 0], n, no_hard=True, physics=_COUPLED, seed=7)
+    z = r["end_pos"][:, 0] - start[0]
+    assert np.isfinite(z).all()
+    zl = _lewis_depth(T0)
+    sd = z.std() / math.sqrt(n)
+    assert abs(z.mean() - zl) < 3 * sd, (z.mean(), zl, (z.mean() - zl) / sd)
+
+
+def test_depth_dose_does_not_depend_on_voxel_size():
+    """Full electron physics (deflections and hard events on), 3 MeV pencil in
+    water: the depth-dose profile in 5 mm bins is the same for 1, 2.5 and 5 mm
+    voxels (chi^2 over the bins from 10 independent batches each, p > 1e-3)."""
+    T0, n, nb = 3.0, 100_000, 10
+    prof = {}
+    for vox in (0.1, 0.25, 0.5):
+        prob = _box(vox)
+        k = int(round(0.5 / vox))
+        rows = []
+        for b in range(nb):
+            r = oracle.pencil(prob, "electron", T0, [0, 0, 0], [1, 0, 0], n // nb, hist_begin=b * n,
+                              physics=_COUPLED, seed=3, patient_dose=True)
+            rows.append(r["vox"].sum(axis=(0, 1)).reshape(-1, k).sum(axis=1) / (n // nb))
+        rows = np.array(rows)
+        prof[vox] = (rows.mean(0), rows.std(0, ddof=1) / math.sqrt(nb))
+    for a, b in ((0.1, 0.25), (0.1, 0.5), (0.25, 0.5)):
+        (ma, sa), (mb, sb) = prof[a], prof[b]
+        sel = (ma + mb) > 2e-3 * T0
+        chi2 = (((ma - mb) / np.hypot(sa, sb))[sel] ** 2).sum()
+        assert stats.chi2.sf(chi2, sel.sum()) > 1e-3, (a, b, chi2, sel.sum())
+
+
+@pytest.mark.parametrize("T0", [1.0, 3.0, 6.0])
+def test_first_hard_event_follows_the_survival_law(T0):
+    """Full electron physics in water with 2.5 mm voxels: before its first hard
+    event a primary follows the CSDA, so the probability that it has none
+    before slowing to T is exp(-Lambda(T)), Lambda(T) = int_T^T0 Sigma_h/L dT'
+    (Sigma_h: Moller + hard bremsstrahlung).  Checked: the fraction with no
+    hard event at all (3 sigma), the energy distribution of first events (KS)
+    and the fraction whose first event is Moller (3 sigma).  Pins the delta
+    tracking of hard events, its thinning test and its independence of the
+    voxel faces (the optical depth is carried across them)."""
+    Sh = lambda T: L.orc_sigma_moller(W.MAT_WATER, T, 0.2) + L.orc_sigma_brem(W.MAT_WATER, T, 0.01)
+    pts = [0.4] if T0 > 0.4 else None
+    Lam = lambda T: integrate.quad(lambda t: Sh(t) / _lw(t), T, T0, epsrel=1e-11,
+                                   points=[p for p in (pts or []) if T < p < T0] or None)[0]
+    n = 200_000
+    r = oracle.pencil(_box(0.25), "electron", T0, [0, 0, 0], [1, 0, 0], n, physics=_COUPLED, seed=11)
+    ev = r["hard_T"] > 0
+    p_none = math.exp(-Lam(0.2 + 1e-6))
+    assert abs((1 - ev.mean()) - p_none) < 3 * math.sqrt(p_none * (1 - p_none) / n)
+    grid = np.linspace(0.2, T0, 300)
+    cdf = 1.0 - (1.0 - np.exp(-np.array([Lam(t) for t in grid]))) / (1.0 - p_none)
+    assert stats.kstest(r["hard_T"][ev], lambda t: np.interp(t, grid, cdf)).pvalue > 1e-3
+    pm = integrate.quad(lambda T: L.orc_sigma_moller(W.MAT_WATER, T, 0.2) / _lw(T) * math.exp(-Lam(T)),
+                        0.2, T0, epsrel=1e-10, points=pts, limit=200)[0]
+    fm = (r["hard_type"] == 0).mean()
+    assert abs(fm - pm) < 3 * math.sqrt(pm * (1 - pm) / n), (fm, pm)
+
+
+# ---------------------------------------------------------------- EPID -----
+
+def _epid_problem(coupled=False):
+    """The default 3-layer EPID with the water box moved 40 cm off the beam axis,
+    so a pencil from the source meets only vacuum before the detector."""
+    p = W.config_water_open(n_histories=1)
+    ph = p.phantom
+    p.phantom = W.Phantom(ph.hu, ph.vox, (ph.origin[0] + 40.0, ph.origin[1], ph.origin[2]))
+    p.physics = W.Physics(coupled=coupled)
+    return p
+
+
+def _source_ray(prob, X, Y):
+    """Source point and unit direction (patient frame) of the ray through the
+    isocentre-plane point (X, Y) at gantry 0: the source sits at (0, -SAD, 0)
+    and the beam runs along +y, with beam X along +x and beam Y along +z."""
+    sad = prob.field.sad
+    d = np.array([X, sad, Y], dtype=np.float64)
+    return np.array([0.0, -sad, 0.0]), d / np.linalg.norm(d)
+
+
+@pytest.mark.parametrize("E", [0.0502, 0.0503, 0.08, 0.3, 2.0])
+@pytest.mark.parametrize("X", [0.0, 8.0])
+def test_epid_layers_uncollided_transmission(E, X):
+    """Photon pencil onto the Cu / Gd2O2S / a-Si stack (normal, and oblique
+    through X = 8 cm at the isocentre): the layer of the first interaction
+    follows the exact probabilities prod_{k<l} e^{-tau_k} (1 - e^{-tau_l})
+    (chi^2), tau_l = rho_l mu_l(E) t_l / cos theta, and the fraction leaving
+    the far face with no interaction equals exp(-sum_l tau_l) within 0.5 %
+    (at least 3 sigma).  0.0502 and 0.0503 MeV straddle the Gd K edge
+    (50.24 keV), where the phosphor's optical depth jumps from 1.2 to 6.0;
+    above it the stack passes 2.5e-4 of the photons, too few for the 0.5 %
+    bar on the transmission, so there only the layer distribution (whose
+    last category is the transmission) is checked."""
+    prob = _epid_problem()
+    src, d = _source_ray(prob, X, 0.0)
+    cos_t = d[1]
+    taus = []
+    for m, t, rho in prob.epid.layers:
+        taus.append(rho * _mu(m, E).sum() * t / cos_t)
+    taus = np.array(taus)
+    T = math.exp(-taus.sum())
+    resolvable = T > 0.01
+    n = int(max(4e5, (3 / 0.005) ** 2 * (1 - T) / T * 1.1)) if resolvable else 1_000_000
+    r = oracle.pencil(prob, "photon", E, src, d, n, physics=prob.physics, seed=13)
+    got = r["n_exit_uncollided"] / n
+    if resolvable:
+        assert 0.005 * T >= 3 * math.sqrt(T * (1 - T) / n)
+        assert abs(got / T - 1) < 0.005, (got, T)
+    first = r["first_layer"]
+    assert np.all(first >= -2) and not np.any(first == -1)      # never in the CT
+    surv = np.concatenate([[1.0], np.exp(-np.cumsum(taus))])
+    probs = np.append(surv[:-1] * (1 - np.exp(-taus)), surv[-1])   # layers 0..2, then none
+    obs = np.array([(first == l).sum() for l in range(len(taus))] + [(first == -2).sum()])
+    exp_ = n * probs
+    chi2 = ((obs - exp_) ** 2 / exp_).sum()
+    assert stats.chi2.sf(chi2, len(obs) - 1) > 1e-3, (obs, exp_)
+
+
+def test_pixel_mapping_of_a_pencil_on_a_pixel_edge():
+    """A 0.1 MeV pencil from the source through the isocentre point (X, Y), X
+    chosen so that X SID / SAD lies exactly on the edge between pixels 70 and
+    71 at the sensitive layer's mid-plane, Y at the centre of row 40.  For
+    every history whose first interaction is in the sensitive layer:
+    - the interaction point lies on the source ray: beam X = X (SAD - Z) / SAD
+      (magnification) to 1e-9 cm;
+    - its first deposit lands in pixel floor((X (SAD - Z)/SAD + W/2) / p) of
+      row 40, i.e. 70 above the mid-plane and 71 below it (edges belong to the
+      higher-index pixel);
+    - the split between the two follows the exponential depth of the first
+      interaction in the layer: P(above) = (1 - e^{-mu t/2}) / (1 - e^{-mu t})."""
+    prob = _epid_problem()
+    ep, sad, sid = prob.epid, prob.field.sad, prob.field.sid
+    W_ = ep.npx * ep.pitch
+    X = (71 * ep.pitch - W_ / 2) * sad / sid
+    Y = (40.5 * ep.pitch - ep.npy * ep.pitch / 2) * sad / sid
+    src, d = _source_ray(prob, X, Y)
+    E, n = 0.1, 400_000
+    r = oracle.pencil(prob, "photon", E, src, d, n, physics=prob.physics, seed=17)
+    sel = r["first_layer"] == ep.sensitive
+    assert sel.sum() > 50_000
+    pos, pix = r["first_pos"][sel], r["first_pixel"][sel]
+    mag = (sad - pos[:, 2]) / sad
+    assert np.max(np.abs(pos[:, 0] - X * mag)) < 1e-9
+    assert np.max(np.abs(pos[:, 1] - Y * mag)) < 1e-9
+    ix = np.floor((X * mag + W_ / 2) / ep.pitch).astype(np.int64)
+    iy = np.floor((Y * mag + ep.npy * ep.pitch / 2) / ep.pitch).astype(np.int64)
+    assert np.array_equal(pix, iy * ep.npx + ix)
+    assert set(np.unique(ix)) == {70, 71} and set(np.unique(iy)) == {40}
+    m, t, rho = ep.layers[ep.sensitive]
+    mut = rho * _mu(m, E).sum() * t / (sad / math.sqrt(sad ** 2 + X ** 2 + Y ** 2))
+    p_up = (1 - math.exp(-mut / 2)) / (1 - math.exp(-mut))
+    k = sel.sum()
+    assert abs((ix == 70).mean() - p_up) < 3 * math.sqrt(p_up * (1 - p_up) / k)
+
+
+# ------------------------------------------------ interaction kinematics ---
+
+@pytest.fixture(scope="module")
+def six_mev_in_water():
+    """6 MeV photon pencil along the beam into the water box, coupled."""
+    prob = W.config_water_open(n_histories=1)
+    src, d = _source_ray(prob, 0.0, 0.0)
+    return oracle.pencil(prob, "photon", 6.0, src, d, 120_000, physics=_COUPLED, seed=19, cap=50_000)
+
+
+def test_pair_production_and_annihilation(six_mev_in_water):
+    """Every pair event shares E - 2 mc^2 between e- and e+ (uniform split, KS),
+    and every positron ends in exactly one annihilation into two photons of
+    exactly mc^2, back to back, isotropic (KS on cos theta and on the
+    azimuth), unless it leaves the world first."""
+    r = six_mev_in_water
+    assert r["n_pair"] > 5000
+    assert r["pair_dev"] <= 1e-14 * 6.0
+    assert r["n_pos_born"] == r["n_pair"]
+    assert r["n_annih"] + r["n_pos_escape"] == r["n_pos_born"]
+    assert r["n_annih"] > 0.8 * r["n_pair"]
+    assert r["annih_dev"] == 0.0
+    assert stats.kstest(r["pair_frac"], "uniform").pvalue > 1e-3
+    assert stats.kstest(r["annih_cos"], stats.uniform(-1, 2).cdf).pvalue > 1e-3
+    assert stats.kstest(r["annih_phi"], stats.uniform(0, 2 * math.pi).cdf).pvalue > 1e-3
+    out = r["e_ct"] + r["e_epid"].sum() + r["e_esc"] + r["e_lost"]
+    assert abs(out - r["e_src"]) / r["e_src"] < 1e-12
+
+
+def test_compton_moller_and_brems_kinematics(six_mev_in_water):
+    """Each Compton event conserves momentum with the electron's |p| from its
+    kinetic energy (|E0 u0 - E1 u1| = sqrt(T (T + 2 mc^2))) and turns the photon
+    by the sampled angle (u0 . u1 = cos theta), with the azimuth uniform about
+    the incident direction (KS); each Moller event conserves momentum
+    (p0 u0 = pW uW + pT uT); a hard bremsstrahlung photon leaves along the
+    electron with ln(k/wcb) / ln(T/wcb) uniform (KS); every direction set by an
+    interaction is a unit vector.  Directions within 0.00447 rad of the z axis
+    (|w| > 0.99999) are turned in the polar frame, which takes them as the
+    axis itself: there the angle is off by at most sqrt(1 - 0.99999^2) =
+    4.47e-3 and a relative momentum balance by twice that (two rotations of
+    a Moller event)."""
+    r = six_mev_in_water
+    assert min(r["n_compton"], r["n_moller"], r["n_brem"]) > 1000
+    assert r["compton_dev"] < 1e-9
+    assert r["polar_dev"] <= 2 * math.sqrt(1 - 0.99999 ** 2)
+    assert r["moller_dev"] < 1e-9
+    assert r["brem_dev"] == 0.0
+    assert r["unit_dev"] < 1e-12
+    assert stats.kstest(r["compton_phi"], stats.uniform(0, 2 * math.pi).cdf).pvalue > 1e-3
+    assert stats.kstest(r["brem_x"], "uniform").pvalue > 1e-3
+
+
+# ------------------------------------------- Woodcock majorant choice ----
+
+@pytest.mark.parametrize("M", [1, 4, 16])
+def test_woodcock_enumeration_for_any_macro_cell_size(M):
+    """First real interaction on a random 16^3 grid against the exact
+    enumeration, with the majorant grid built from macro-cells of 1, 4 and 16
+    voxels per side (16: one global majorant).  Any majorant that bounds mu
+    along the ray gives the same distribution of real collisions."""
+    rng = np.random.default_rng(23)
+    hu = rng.choice([-1000, -750, -300, 0, 80, 700, 1400], size=(16, 16, 16)).astype(np.int16)
+    ph = W.Phantom(hu, (1.0, 1.0, 1.0), (-8.0, -8.0, -8.0))
+    prob = W.config_water_open(n_histories=1)
+    prob.phantom = ph
+    start = np.array([-7.7, -8.0, -6.9])
+    d = np.array([0.45, 1.0, 0.3]); d /= np.linalg.norm(d)
+    E, n = 1.0, 300_000
+    vox, typ = oracle.first_interaction(prob, E, start, d, n, seed=29, macro_M=M)
+    rho, mat = oracle.hu_to_rho_mat(hu.ravel())
+    cats, probs, trans = [], [], 1.0
+    for _, l, v in _voxel_chords(ph.origin, 1.0, hu.shape, start, d):
+        mu = _mu(mat[v], E) * rho[v]
+        tot = mu.sum()
+        pint = trans * (1 - math.exp(-tot * l))
+        for j in range(3):
+            if mu[j] > 0:
+                cats.append((v, j)); probs.append(pint * mu[j] / tot)
+        trans *= math.exp(-tot * l)
+    cats.append((-1, -1)); probs.append(trans)
+    probs = np.array(probs)
+    index = {c: i for i, c in enumerate(cats)}
+    obs = np.zeros(len(cats))
+    for v, t in zip(vox, typ):
+        obs[index[(int(v), int(t))]] += 1
+    exp_ = n * probs
+    big = exp_ >= 5
+    chi2 = ((obs[big] - exp_[big]) ** 2 / exp_[big]).sum()
+    rest_o, rest_e = obs[~big].sum(), exp_[~big].sum()
+    dof = big.sum() - 1
+    if rest_e > 0:
+        chi2 += (rest_o - rest_e) ** 2 / rest_e
+        dof += 1
+    assert stats.chi2.sf(chi2, dof) > 1e-3
