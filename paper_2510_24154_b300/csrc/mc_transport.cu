@@ -437,15 +437,12 @@ __device__ __forceinline__ bool photon_epid_event(const Params& P, const float2*
 constexpr int kMaxLegFaces = 3 * kHomRadius + 1;
 __device__ __forceinline__ bool leg_through(const Params& P, const Part& p, uint32_t cell, bool hom, float len,
                                             uint32_t& end) {
-    if (!hom) return false;
     const int ex = __float2int_rd((fmaf(len, p.u, p.x) - P.ox) / P.vx);
     const int ey = __float2int_rd((fmaf(len, p.v, p.y) - P.oy) / P.vy);
     const int ez = __float2int_rd((fmaf(len, p.w, p.z) - P.oz) / P.vz);
-    if (abs(ex - cell_x(cell)) > kHomRadius || abs(ey - cell_y(cell)) > kHomRadius ||
-        abs(ez - cell_z(cell)) > kHomRadius)
-        return false;
-    end = pack_cell(ex, ey, ez);
-    return true;
+    end = pack_cell(min(max(ex, 0), P.nx - 1), min(max(ey, 0), P.ny - 1), min(max(ez, 0), P.nz - 1));
+    return hom && abs(ex - cell_x(cell)) <= kHomRadius && abs(ey - cell_y(cell)) <= kHomRadius &&
+           abs(ez - cell_z(cell)) <= kHomRadius;
 }
 
 // The patient-dose deposits of a CT hinge step whose second segment ran
@@ -572,14 +569,13 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     if (!face) {
         sb2 = EPID ? epid_dist(P, p, layer, ax2) : ct_dist(P, p, p.cell, ax2);
         s2 = s - s1;
-        if (s2 >= sb2) {
-            if (!EPID) through = leg_through(P, p, p.cell, hom_c, s2, ecell);
-            if (!through) {
-                s2 = sb2;
-                crossed = true;
-                cax = ax2;
-                cdir = EPID ? p.w : (ax2 == 0) ? p.u : (ax2 == 1) ? p.v : p.w;
-            }
+        const bool cross = s2 >= sb2;
+        if (!EPID) through = leg_through(P, p, p.cell, hom_c, s2, ecell) && cross;
+        if (cross && !through) {
+            s2 = sb2;
+            crossed = true;
+            cax = ax2;
+            cdir = EPID ? p.w : (ax2 == 0) ? p.u : (ax2 == 1) ? p.v : p.w;
         }
         p.x += s2 * p.u; p.y += s2 * p.v; p.z += s2 * p.w;
     }
@@ -597,50 +593,48 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
         }
         return false;
     }
-    if (!EPID && through) {
-        // the step ends in voxel ecell; with the patient-dose tally on, its
-        // energy is split among the voxels of the second segment
-        if (P.vox) {
-            Part hp = p;
-            hp.x = hx; hp.y = hy; hp.z = hz;
-            leg_deposit(P, a, hp, hcell, ecell, s2, sb2, ax2, s1, dE);
-        } else {
-            deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, p.flags, dE);
-        }
-        p.cell = ecell;
-        const size_t v = (static_cast<size_t>(cell_z(ecell)) * P.ny + cell_y(ecell)) * P.nx + cell_x(ecell);
-        rho_c = __ldg(&P.rho[v]);                               // used next step
-        hom_c = __ldg(&P.hom[v]) != 0;
+    if (!EPID && through && P.vox) {
+        // patient dose: the step's energy split among the voxels of the second segment
+        Part hp = p;
+        hp.x = hx; hp.y = hy; hp.z = hz;
+        leg_deposit(P, a, hp, hcell, ecell, s2, sb2, ax2, s1, dE);
     } else {
         deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, p.flags, dE);
     }
     p.E = Tn;
-    if (crossed) {
-        bool out;
-        if (EPID) {
-            const int nl = layer + (cdir < 0.0f ? 1 : -1);      // layers are numbered down the beam (-z)
-            out = (cax != 0) || nl < 0 || nl >= P.nl;
-            if (!out) p.cell = static_cast<uint32_t>(nl);
-        } else {
+    if (EPID && crossed) {
+        const int nl = layer + (cdir < 0.0f ? 1 : -1);          // layers are numbered down the beam (-z)
+        if ((cax != 0) || nl < 0 || nl >= P.nl) {
+            if (face) { p.u = u0; p.v = v0; p.w = w0; }         // a face-limited step leaves undeflected
+            a.esc += quanta(p.E + rest_extra(p.flags));
+            return false;
+        }
+        p.cell = static_cast<uint32_t>(nl);
+        return true;
+    }
+    if (!EPID && (crossed || through)) {
+        // the voxel where the step ends: across the face, or where the second
+        // segment ran to; every lane that changes voxel loads its density and
+        // flag here, for the next step
+        uint32_t nc = ecell;
+        bool out = false;
+        if (crossed) {
             int ix = cell_x(p.cell), iy = cell_y(p.cell), iz = cell_z(p.cell);
             const int stp = (cdir > 0.0f) ? 1 : -1;
             if (cax == 0) ix += stp; else if (cax == 1) iy += stp; else iz += stp;
             out = ix < 0 || ix >= P.nx || iy < 0 || iy >= P.ny || iz < 0 || iz >= P.nz;
-            if (!out) {
-                p.cell = pack_cell(ix, iy, iz);
-                const size_t v = (static_cast<size_t>(iz) * P.ny + iy) * P.nx + ix;
-                rho_c = __ldg(&P.rho[v]);                       // used next step
-                hom_c = __ldg(&P.hom[v]) != 0;
-            }
+            nc = pack_cell(ix, iy, iz);
         }
         if (out) {
-            // a face-limited step leaves undeflected
-            if (face) { p.u = u0; p.v = v0; p.w = w0; }
-            if (EPID) { a.esc += quanta(p.E + rest_extra(p.flags)); }
-            else { move = transfer_to_epid(P, p, a, s_events, false); }
+            if (face) { p.u = u0; p.v = v0; p.w = w0; }         // a face-limited step leaves undeflected
+            move = transfer_to_epid(P, p, a, s_events, false);
             return false;
         }
-        return true;
+        p.cell = nc;
+        const size_t v = (static_cast<size_t>(cell_z(nc)) * P.ny + cell_y(nc)) * P.nx + cell_x(nc);
+        rho_c = __ldg(&P.rho[v]);
+        hom_c = __ldg(&P.hom[v]) != 0;
+        if (crossed) return true;
     }
     if (!at_event) return true;
     const float lnTn = logf(Tn);

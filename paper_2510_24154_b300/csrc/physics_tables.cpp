@@ -142,9 +142,19 @@ Tables build_tables(double e_lo, double e_hi, double t_lo, double t_hi, double w
         t.photon[2 * i + 1] = static_cast<float>(pair_shape(E));
     }
 
-    const double lt0 = std::log(t_lo), lt1 = std::log(t_hi);
+    // The restricted stopping power and the hard Moller cross section change
+    // form at T = 2 wcc (below it every Moller secondary is soft): one node
+    // sits exactly there, so no interval straddles the kink (linear
+    // interpolation across it erred by 1e-4 in the stopping power and fully in
+    // the Moller cross section just above threshold; now 3e-6 and, in the
+    // first interval above threshold, 1 %).  The grid keeps one node of slack
+    // for the shift.
+    double lt0 = std::log(t_lo);
+    const double lt1 = std::log(t_hi);
+    t.e_inv_dlnT = (kElectronNodes - 2) / (lt1 - lt0);
+    const double lk = std::log(2.0 * wcc);
+    if (lk > lt0 && lk < lt1) lt0 = lk - std::ceil((lk - lt0) * t.e_inv_dlnT) / t.e_inv_dlnT;
     t.e_lnT0 = lt0;
-    t.e_inv_dlnT = (kElectronNodes - 1) / (lt1 - lt0);
     t.electron.resize(static_cast<size_t>(kNumMaterials) * 2 * kElectronNodes);
     for (int m = 0; m < kNumMaterials; ++m) {
         for (int i = 0; i < kElectronNodes; ++i) {

@@ -1,6 +1,7 @@
 """GPU tests at the full size of the anthropomorphic workload: a 512 x 512 x 200
 HU phantom at 1 mm, one 40-segment IMRT field, the 1190 x 1190 EPID at
-0.336 mm.  Replay against the FP64 oracle on a sample of histories, the
+0.336 mm.  Replay against the FP64 oracle on a sample of histories (pixel by
+pixel on the full detector grid), the
 radiological thickness of sampled pixels against the oracle's ray sums, and
 the properties of a 2e8-history run (energy closure, no lost particles, the
 statistics falling as 1/sqrt(N))."""
@@ -34,15 +35,16 @@ def test_replay_sample_of_histories(problem):
     for k in ("flights_ct", "real_ct", "compton", "esteps_ct", "esteps_epid", "electrons", "primaries_at_epid"):
         g, o = st["counters"][k], orc["counters"][k]
         assert abs(g - o) <= 3e-3 * o + 5.0 * np.sqrt(o), (k, g, o)
-    # the same histories land on the same pixels: 16 x 16-binned images agree
-    # far better than two independent runs' noise would allow
-    def binned(t):
-        img = t.sum(axis=0)[:1184, :1184]
-        return img.reshape(74, 16, 74, 16).sum(axis=(1, 3))
-    bg, bo = binned(gt), binned(ot)
-    sel = bo > 0.1 * bo.max()
-    assert sel.sum() > 500
-    assert np.abs(bg - bo)[sel].sum() / bo[sel].sum() < 0.02
+    # pixel by pixel on the full 1190 x 1190 grid: 1 %/1 mm global gamma with
+    # the oracle's image as reference, >= 98 % (measured 98.9 %; on this
+    # sparse image every history that rounding takes off its FP64 path fails
+    # its own few pixels, as in the thorax full-grid replay)
+    gd, _, _ = sim.dose()
+    od, _, _ = oracle.dose_stats(ot, n, p.epid)
+    assert gd.shape == (1190, 1190)
+    assert (od > 0.1 * od.max()).sum() > 1000
+    rate = G.gamma_rate(od, gd, p.epid.pitch)
+    assert rate >= 0.98, rate
     sim.close()
 
 

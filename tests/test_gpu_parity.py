@@ -116,7 +116,10 @@ def _compare_replay(p, n, gpu_seed=None):
 
 
 def test_replay_photon_only_water():
-    p = G.water_case(n=1_000_000, coupled=False)
+    """The small single-field workload on its exact grid: photon-only, 1e6
+    histories, water box of 64 x 40 x 64 at 5 mm, open 10 x 10 field, EPID
+    128 x 128 at 3 mm."""
+    p = G.water_case(n=1_000_000, coupled=False, npx=128, pitch=0.3)
     sim, st, orc, gt, ot, (e_g, e_o), (gd, gs, od, os_) = _compare_replay(p, p.n_histories)
     assert abs(e_g / e_o - 1) < 1e-4
     for k in ("flights_ct", "real_ct", "compton", "photo", "pair", "primaries_at_epid", "uncollided_at_epid"):
@@ -154,6 +157,36 @@ def test_independent_streams_three_sigma(case):
     assert frac >= 0.99, (frac, nsel)
 
 
+def test_full_size_thorax_replay_pixel_by_pixel():
+    """The full thorax workload (CT 256 x 256 x 128 at 2 mm, EPID 1024 x 768 at
+    0.39 mm, 9-segment field, coupled) in bench.py's launch configuration,
+    replayed against the oracle pixel by pixel on the full detector grid: a
+    1 %/1 mm global gamma (10 % threshold) with the oracle's image as
+    reference passes at >= 98.5 % of pixels (measured 99.1 %).
+
+    Why not 99.5 % here: at 1e6 histories on 0.39 mm pixels the image is
+    sparse (a pixel above the threshold holds one or two tracks), so each
+    history that FP32 rounding takes off its FP64 path fails its own one to
+    three pixels outright.  Bisecting 65,536 histories one by one found 8
+    whose image differs by more than 1e-3 anywhere: 6 split a layer crossing's
+    energy differently by ~1e-3 (same pixels), 2 put a deposit 1-3 pixels
+    away (a bremsstrahlung photon and a long electron track, whose direction
+    differences grow over the ~60 cm to the detector), i.e. ~3e-5 of
+    histories; each side is bitwise the same when the run is split."""
+    n = 1_000_000
+    p = G.thorax_case(n=n, scale=1, epid_scale=1)
+    sim, st, gt = G.gpu_run(p, bank_capacity=1 << 26)
+    orc = oracle.run(p)
+    assert G.energy_closure(st) < 2e-6 and st["error_flags"] == 0 and st["counters"]["lost"] == 0
+    gd, _, _ = sim.dose()
+    od, _, _ = oracle.dose_stats(orc["tally"], n, p.epid)
+    assert gd.shape == (768, 1024)
+    assert (od > 0.1 * od.max()).sum() > 2000
+    assert gt.sum() == pytest.approx(orc["tally"].sum(), rel=1e-3)
+    rate = G.gamma_rate(od, gd, p.epid.pitch)
+    assert rate >= 0.985, rate
+
+
 def test_full_size_geometry_replay():
     """The full thorax CT (256x256x128 at 2 mm) and EPID (1024x768 at 0.39 mm)
     in the default launch configuration: energy balance, replay of the
@@ -171,23 +204,27 @@ def test_bench_step_statistics_against_oracle_sample():
     """The benchmark step itself (full thorax CT and EPID, 1e8 histories,
     2^26-particle banks): energy balance, no lost particles, and the mean
     sensitive-layer energy and event counts per history within 4 standard
-    errors of an independent oracle sample of 4e5 histories (its batch
-    spread gives the error; the GPU's own error is 16x smaller)."""
-    n_gpu, n_orc = 100_000_000, 400_000
+    errors of an independent oracle sample of 4e5 histories, run as 16 chunks
+    of 25,000 whose spread gives each quantity's standard error (the GPU's
+    own error is 16x smaller)."""
+    n_gpu, n_chunk, n_ch = 100_000_000, 25_000, 16
     p = G.thorax_case(n=n_gpu, scale=1, epid_scale=1, batches=16)
     sim, st, gt = G.gpu_run(p, bank_capacity=1 << 26)
     assert st["histories"] == n_gpu and st["error_flags"] == 0 and st["counters"]["lost"] == 0
     assert G.energy_closure(st) < 2e-6
-    orc = oracle.run(p, n_histories=n_orc, hist_begin=1 << 40)     # streams disjoint from the GPU's
-    per_batch = orc["tally"].reshape(orc["tally"].shape[0], -1).sum(axis=1) / oracle.batch_counts(n_orc, 16)
-    mean_o = orc["tally"].sum() / n_orc
-    se_o = per_batch.std(ddof=1) / np.sqrt(per_batch.size)
-    mean_g = gt.sum() / n_gpu
-    assert abs(mean_g - mean_o) <= 4.0 * se_o, (mean_g, mean_o, se_o)
-    # event counts per history: Poisson-like errors of the oracle sample
-    for k in ("flights_ct", "real_ct", "compton", "esteps_ct", "electrons", "primaries_at_epid"):
-        g, o = st["counters"][k] / n_gpu, orc["counters"][k] / n_orc
-        assert abs(g - o) <= 4.0 * np.sqrt(max(orc["counters"][k], 1)) / n_orc * 3.0, (k, g, o)
+    keys = ("flights_ct", "real_ct", "compton", "esteps_ct", "electrons", "primaries_at_epid")
+    per = {k: [] for k in keys + ("sensitive",)}
+    for c in range(n_ch):                     # streams disjoint from the GPU's
+        orc = oracle.run(p, n_histories=n_chunk, hist_begin=(1 << 40) + c * n_chunk)
+        per["sensitive"].append(orc["tally"].sum() / n_chunk)
+        for k in keys:
+            per[k].append(orc["counters"][k] / n_chunk)
+    got = {"sensitive": gt.sum() / n_gpu}
+    got.update({k: st["counters"][k] / n_gpu for k in keys})
+    for k, v in per.items():
+        v = np.asarray(v)
+        se = v.std(ddof=1) / np.sqrt(n_ch)
+        assert abs(got[k] - v.mean()) <= 4.0 * se, (k, got[k], v.mean(), se)
 
 
 # --------------------------------------------------- determinism --------
@@ -283,8 +320,9 @@ def test_replay_with_collimation():
     assert abs(e_g / e_o - 1) < 1e-3
     for k in ("flights_ct", "real_ct", "compton", "primaries_at_epid", "uncollided_at_epid"):
         assert st["counters"][k] == pytest.approx(orc["counters"][k], rel=5e-4), k
-    img_g, img_o = gt.sum(axis=0), ot.sum(axis=0)
-    assert np.abs(img_g - img_o).sum() / img_o.sum() < 0.02
+    assert G.gamma_rate(od, gd, p.epid.pitch) >= 0.995
+    frac, nsel = G.three_sigma_fraction(gd, gs, od, os_)
+    assert frac >= 0.99 and nsel > 200
 
 
 def test_collimation_arguments_rejected():
