@@ -18,7 +18,11 @@
  *    copied, so they may be freed when the call returns (device inputs: once
  *    the stream has reached the call).
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
- *    ordered on it; mc_run synchronizes it before returning.
+ *    queued on it.  mc_run (graph-driven, the default) returns without
+ *    waiting for the device; every later call of the context that reads or
+ *    changes its device state is ordered after that run (on its own stream by
+ *    an event wait, or by waiting on the host where it says so).  Calls that
+ *    write host outputs return once their results are there.
  *  - Units: cm, MeV, g/cm^3; doses in Gy per source history.
  *  - Arrays are row-major, last index fastest: CT [nz][ny][nx], EPID images
  *    [npy][npx], tallies [B][npy][npx], k-table [ns][nt].
@@ -88,9 +92,12 @@ typedef struct mc_config {
     uint32_t bank_capacity;       /* particles per bank, 0 = 1<<23 */
     uint32_t primaries_per_wave;  /* new histories per transport wave, 0 = bank_capacity / 4; a wave admits
                                      no more than half a bank or the room left in the CT-photon bank */
-    int time_kernels;             /* 1: time every transport launch with CUDA events (mc_run_stats.kernel_ms) */
-    int use_graph;                /* 1: each run is one CUDA-graph launch whose waves loop on the device
-                                     (a conditional while-node); 0: waves are driven from the host */
+    int time_kernels;             /* 1: time every transport launch with CUDA events (mc_run_stats.kernel_ms);
+                                     needs the host-driven loop, so mc_run then waits for the device */
+    int use_graph;                /* 1 (default): each run is one CUDA-graph launch whose waves loop on the
+                                     device (a conditional while-node) and mc_run does not wait for it;
+                                     0: waves are driven from the host, which reads the run control after
+                                     every wave (mc_run then waits, and mc_cancel can stop it) */
     int regs_variant[4];          /* per transport kernel (CT photons, CT electrons, EPID photons, EPID
                                      electrons): build for 2, 3 or 4 CTAs of 256 threads per SM
                                      (register caps 128 / 85 / 64); 0 = the default 4 */
@@ -185,17 +192,32 @@ mc_status mc_init_geometry(mc_ctx* ctx, const int16_t* hu, int nx, int ny, int n
                            const double origin_cm[3], const mc_epid_desc* epid, int hu_on_device,
                            void* stream);
 
-/* Steps a2 (source set-up), a9 (radiological thickness, Sec. 2.2 item 1: a
- * ray sum of density from the source to every pixel centre, FP64
- * accumulation), a10 (Eq. 1 on the bounding rectangle of the union of open
- * apertures) and the k-table upload.  Resets the tally.  lut may be NULL
- * (then mc_get_epid_image is unavailable). */
+/* The field of Sec. 2.1.1 (MLC segments, jaws, MU weights, gantry angle) and
+ * the correction inputs of Sec. 2.2: builds the source's aperture table, the
+ * radiological thickness map (Sec. 2.2 item 1: a ray sum of density from the
+ * source to every pixel centre, FP64 accumulation), the field size of Eq. 1
+ * (on the bounding rectangle of the union of open apertures) and uploads the
+ * k-table of Sec. 3.1.  Resets the tally.  lut may be NULL (then
+ * mc_get_epid_image is unavailable).  Queued on `stream` without waiting for
+ * the device: host data goes through pinned staging, and the device buffers
+ * of the previous field are reused when large enough (when one must grow,
+ * the call first waits for a pending run). */
 mc_status mc_set_field(mc_ctx* ctx, const mc_field_desc* field, const mc_lut_desc* lut, void* stream);
 
-/* Steps a2-a7: transports n_histories histories of every field set on the
- * context (ids continue from the previous run, so repeated calls equal one
- * longer run) with Philox keyed by seed, adding to the tally.  Synchronizes
- * `stream`.  stats may be NULL. */
+/* The Monte Carlo transport of Sec. 2.1: n_histories photons of every field
+ * set on the context from the MLC-shaped source (Sec. 2.1.1) through the CT
+ * patient (Sec. 2.1.2: photoelectric, Compton, pair; Class II condensed
+ * history electrons) into the EPID layer stack (Sec. 2.1.3), the energy left
+ * in the sensitive layer added to the per-pixel tally.  History ids continue
+ * from the previous run, so repeated calls equal one longer run; Philox is
+ * keyed by seed.
+ * With use_graph (the default) and no time_kernels the run is queued on
+ * `stream` as one graph launch and the call returns without waiting; the
+ * tally and the stats are valid once the stream has passed the run.  A
+ * non-NULL `stats` makes the call wait and fill it.  Device-side failures
+ * (MC_ERR_OVERFLOW, MC_ERR_TIMEOUT) of a run that did not wait are returned
+ * by the next mc_get_stats, mc_run, mc_set_field that replaces buffers, or
+ * mc_init_geometry.  With use_graph = 0 or time_kernels the call waits. */
 mc_status mc_run(mc_ctx* ctx, uint64_t n_histories, uint64_t seed, void* stream, mc_run_stats* stats);
 
 /* Batching (several static fields of one plan on one phantom, Sec. 2.3's 25
@@ -210,7 +232,7 @@ mc_status mc_set_fields(mc_ctx* ctx, const mc_field_desc* fields, int n_fields, 
 
 /* Transports n_histories[f] histories of every field f in one wave sequence
  * (one graph launch with use_graph), so fields of uneven sizes share the GPU.
- * Synchronizes `stream`. */
+ * Waits for the device as mc_run does. */
 mc_status mc_run_batch(mc_ctx* ctx, const uint64_t* n_histories, uint64_t seed, void* stream,
                        mc_run_stats* stats);
 
@@ -222,10 +244,14 @@ mc_status mc_get_field_image(mc_ctx* ctx, int field, float* signal, int on_devic
 mc_status mc_get_field_tmap(mc_ctx* ctx, int field, double* t, int on_device, void* stream);
 mc_status mc_get_field_size(mc_ctx* ctx, int field, double* s, double* a, double* b);
 
-/* Step a8 (field 0): per-history dose (Gy) in the sensitive layer and its batch
- * standard error, [npy][npx] doubles (host or device per on_device); sigma
- * may be NULL.  u_out (host, may be NULL) receives the mean relative
- * uncertainty over pixels above half the maximum dose. */
+/* The per-pixel EPID dose and its statistical uncertainty (Sec. 2.3: images
+ * of 1e9 histories at < 1 %; the paper does not define the figure, this
+ * library reports the batch estimate), field 0: per-history dose (Gy) in
+ * the sensitive layer and its batch standard error over B sub-tallies,
+ * [npy][npx] doubles (host or device per on_device); sigma may be NULL.
+ * u_out (host, may be NULL) receives the mean relative uncertainty over
+ * pixels above half the maximum dose.  With on_device and no u_out the work
+ * is queued on `stream` and the call does not wait. */
 mc_status mc_get_dose(mc_ctx* ctx, double* dose, double* sigma, double* u_out, int on_device, void* stream);
 
 /* Step a11 (Sec. 3.1, field 0): signal = k_scale * k(t, s) * dose per pixel, float32
@@ -269,7 +295,9 @@ mc_status mc_resample_image(const double* src, int snx, int sny, double src_pitc
  * of all fields.  MC_ERR_STATE when patient dose is off or nothing has run. */
 mc_status mc_get_patient_dose(mc_ctx* ctx, double* dose, int on_device, void* stream);
 
-/* Cumulative statistics (energy balance from the fixed-point counters). */
+/* Cumulative statistics (energy balance from the fixed-point counters).
+ * Waits for a pending run and returns its device-side outcome (MC_OK,
+ * MC_ERR_OVERFLOW or MC_ERR_TIMEOUT), with the stats filled either way. */
 mc_status mc_get_stats(mc_ctx* ctx, mc_run_stats* stats);
 
 /* Clears tally, counters and the history id sequence. */
@@ -288,8 +316,9 @@ mc_status mc_set_state(mc_ctx* ctx, const void* host_buf, size_t bytes, void* st
  * histories).  Does not clear the tally. */
 mc_status mc_set_history_base(mc_ctx* ctx, uint64_t next_history);
 
-/* Requests that a running mc_run on another host thread stop after its
- * current wave (it then returns MC_ERR_CANCELLED). */
+/* Requests that a host-driven mc_run (use_graph = 0) running on another host
+ * thread stop after its current wave (it then returns MC_ERR_CANCELLED).  A
+ * graph-driven run loops on the device and runs to its end. */
 mc_status mc_cancel(mc_ctx* ctx);
 
 /* Global gamma index (Low et al. 1998), the image comparison of Sec. 2.3.3:

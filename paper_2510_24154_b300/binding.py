@@ -293,10 +293,15 @@ class Simulator:
 
     # -- transport ------------------------------------------------------------
     def run(self, n_histories, seed, stream=None) -> dict:
-        """a2-a7: transport n_histories more histories."""
+        """a2-a7: transport n_histories more histories; waits and returns the stats."""
         st = RunStats()
         self._check(self.lib.mc_run(self.h, int(n_histories), int(seed), _stream_ptr(stream), C.byref(st)))
         return stats_dict(st)
+
+    def run_async(self, n_histories, seed, stream=None) -> None:
+        """a2-a7 queued on `stream` (graph-driven runs return at once); the
+        stats and any device-side failure come from stats()."""
+        self._check(self.lib.mc_run(self.h, int(n_histories), int(seed), _stream_ptr(stream), None))
 
     def run_batch(self, n_histories, seed, stream=None) -> dict:
         """a12: n_histories[f] more histories of every field f, in one wave sequence."""

@@ -122,6 +122,23 @@ struct mc_ctx {
     uint32_t last_launches = 0;
     std::vector<cudaEvent_t> ev_pool;
     cudaStream_t capture_stream = nullptr;
+    // asynchronous (graph-driven) runs: the last run's start and end events,
+    // whether its control block (waves, error bits) and time are still to be
+    // read, and its launches per wave
+    cudaEvent_t ev_run0 = nullptr, ev_run1 = nullptr;
+    cudaGraph_t run_graph = nullptr;          // kept until the run is finalized: destroying an
+    cudaGraphExec_t run_exec = nullptr;       // executable graph waits for it
+    bool run_pending = false;
+    uint32_t run_per_wave = 0;
+    // pinned staging of the host data that calls copy without waiting
+    FieldDev* h_fields = nullptr;              // [kMaxFields]
+    unsigned long long* h_first = nullptr;     // [kMaxFields + 1]
+    char* h_stage = nullptr;                   // source rectangles, CDF, k-table columns
+    size_t h_stage_cap = 0;
+    cudaEvent_t ev_stage = nullptr;            // recorded after the last copies out of h_stage
+    // field buffers are kept while large enough: their capacities in elements
+    size_t cap_tally = 0, cap_pix = 0, cap_parts = 0, cap_rect = 0, cap_cdf = 0, cap_tmap = 0, cap_lut_t = 0,
+           cap_ks = 0;
 };
 
 namespace {
@@ -150,7 +167,17 @@ cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 int npix(const mc_ctx* c) { return c->epid.npx * c->epid.npy; }
 int nfields(const mc_ctx* c) { return static_cast<int>(c->fields.size()); }
 
-void free_field(mc_ctx* c) {
+bool is_electron(int t) { return t == mc::kElectronCT || t == mc::kElectronEPID; }
+
+// Forgets the fields (the device buffers stay for reuse).
+void clear_fields(mc_ctx* c) {
+    c->tally_n = 0;
+    c->fields.clear();
+    c->has_field = false;
+    c->has_lut = false;
+}
+
+void free_field_buffers(mc_ctx* c) {
     dfree(c->d_rect);
     dfree(c->d_cdf);
     dfree(c->d_tmap);
@@ -162,10 +189,58 @@ void free_field(mc_ctx* c) {
     dfree(c->d_partc);
     dfree(c->d_signal);
     dfree(c->d_tally);
-    c->tally_n = 0;
-    c->fields.clear();
-    c->has_field = false;
-    c->has_lut = false;
+    c->cap_tally = c->cap_pix = c->cap_parts = c->cap_rect = c->cap_cdf = c->cap_tmap = c->cap_lut_t = c->cap_ks = 0;
+    clear_fields(c);
+}
+
+// Device buffer p holds at least n elements (kept if it already does;
+// otherwise replaced, contents lost).
+template <typename T>
+cudaError_t ensure(T*& p, size_t& cap, size_t n) {
+    if (n <= cap && p) return cudaSuccess;
+    dfree(p);
+    cap = 0;
+    const cudaError_t e = cudaMalloc(&p, sizeof(T) * (n > 0 ? n : 1));
+    if (e == cudaSuccess) cap = n;
+    return e;
+}
+
+// The bookkeeping of a pending graph-driven run: waits for its end, reads
+// its control block and time.  Returns the run's device-side outcome
+// (bank overflow, wave limit) once; the error bits stay in the stats.
+void release_run_graph(mc_ctx* c) {
+    if (c->run_exec) cudaGraphExecDestroy(c->run_exec);
+    if (c->run_graph) cudaGraphDestroy(c->run_graph);
+    c->run_exec = nullptr;
+    c->run_graph = nullptr;
+}
+
+mc_status finalize_run(mc_ctx* c) {
+    if (!c->run_pending) return MC_OK;
+    c->run_pending = false;
+    const cudaError_t e = cudaEventSynchronize(c->ev_run1);
+    release_run_graph(c);
+    CUDA_TRY(c, e);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev_run0, c->ev_run1);
+    const Ctl& h = *c->h_ctl;
+    c->last_waves = static_cast<int>(h.waves);
+    c->last_error = h.error;
+    c->last_ms = ms;
+    c->last_launches = c->run_per_wave * h.waves;
+    for (int t = 0; t < 4; ++t) {
+        c->last_kernel_ms[t] = 0.0;
+        c->last_kernel_launches[t] = (is_electron(t) && !c->cfg.coupled) ? 0u : h.waves;
+    }
+    if (h.error) return fail(c, MC_ERR_OVERFLOW, "particle bank overflow");
+    if (h.waves >= kMaxWaves) return fail(c, MC_ERR_TIMEOUT, "wave limit reached");
+    return MC_OK;
+}
+
+// Work queued on stream s after this call runs after the pending run.
+mc_status order_after_run(mc_ctx* c, cudaStream_t s) {
+    if (c->run_pending) CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_run1, 0));
+    return MC_OK;
 }
 
 mc_status clear_tally(mc_ctx* c, cudaStream_t s) {
@@ -393,7 +468,8 @@ mc_status build_field(mc_ctx* c, const mc_field_desc* f, int index, std::vector<
 // Per-field device records for a run; `first` is the prefix sum of the
 // histories each field runs in it.
 mc_status upload_fields(mc_ctx* c, const std::vector<uint64_t>& first, cudaStream_t s) {
-    std::vector<FieldDev> fd(c->fields.size());
+    // pinned staging: the previous run (whose copies read it) has finished
+    FieldDev* fd = c->h_fields;
     const size_t per_field = static_cast<size_t>(c->cfg.n_batches) * npix(c);
     for (size_t i = 0; i < c->fields.size(); ++i) {
         const FieldHost& h = c->fields[i];
@@ -412,11 +488,10 @@ mc_status upload_fields(mc_ctx* c, const std::vector<uint64_t>& first, cudaStrea
         d.batch_base = h.hist_done;
         d.tally_off = i * per_field;
     }
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_fields, fd.data(), sizeof(FieldDev) * fd.size(), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_first, first.data(), sizeof(unsigned long long) * first.size(),
+    for (size_t i = 0; i < first.size(); ++i) c->h_first[i] = first[i];
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_fields, fd, sizeof(FieldDev) * c->fields.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_first, c->h_first, sizeof(unsigned long long) * first.size(),
                                 cudaMemcpyHostToDevice, s));
-    // the copies read host vectors that die on return
-    CUDA_TRY(c, cudaStreamSynchronize(s));
     return MC_OK;
 }
 
@@ -427,7 +502,6 @@ struct WaveResult {
     double kms[4] = {0, 0, 0, 0};
 };
 
-bool is_electron(int t) { return t == mc::kElectronCT || t == mc::kElectronEPID; }
 
 const int kOrder[4] = {mc::kPhotonCT, mc::kElectronCT, mc::kPhotonEPID, mc::kElectronEPID};
 
@@ -435,7 +509,7 @@ const int kOrder[4] = {mc::kPhotonCT, mc::kElectronCT, mc::kPhotonEPID, mc::kEle
 // bank swaps, wave-end) is captured into the body of a conditional while-node;
 // the wave-end kernel sets the condition, so the whole run is one launch and
 // the host waits once.  `e0` is recorded just before the launch.
-mc_status run_waves_graph(mc_ctx* c, const Params& P, cudaStream_t s, cudaEvent_t e0, WaveResult& r) {
+mc_status run_waves_graph(mc_ctx* c, const Params& P, cudaStream_t s, WaveResult& r) {
     if (!c->capture_stream) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -480,19 +554,23 @@ mc_status run_waves_graph(mc_ctx* c, const Params& P, cudaStream_t s, cudaEvent_
     const cudaError_t e_end = cudaStreamEndCapture(cs, &captured);
     if (e == cudaSuccess) e = e_end;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_run0, s);
     if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
-    Ctl& h = *c->h_ctl;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cleanup();
-    if (e != cudaSuccess) return fail(c, MC_ERR_CUDA, std::string("graph-driven run: ") + cudaGetErrorString(e));
-    r.waves = static_cast<int>(h.waves);
-    r.launches = per_wave * h.waves;
-    for (int t : kOrder)
-        if (!(is_electron(t) && !c->cfg.coupled)) r.klaunch[t] = h.waves;
-    if (h.error) return fail(c, MC_ERR_OVERFLOW, "particle bank overflow");
-    if (h.waves >= kMaxWaves) return fail(c, MC_ERR_TIMEOUT, "wave limit reached");
+    // the control block comes back with the run; the host reads it (and the
+    // events) only when asked (finalize_run), so the call does not wait
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_run1, s);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);    // a launched graph must finish before it is destroyed
+        cleanup();
+        return fail(c, MC_ERR_CUDA, std::string("graph-driven run: ") + cudaGetErrorString(e));
+    }
+    // the graph stays alive until finalize_run (destroying it here would wait)
+    c->run_graph = graph;
+    c->run_exec = exec;
+    c->run_pending = true;
+    c->run_per_wave = per_wave;
+    r.waves = -1;
     return MC_OK;
 }
 
@@ -556,7 +634,6 @@ mc_status set_fields_impl(mc_ctx* c, const mc_field_desc* f, int n, const mc_lut
             return fail(c, MC_ERR_ARG, "k-table nodes must increase");
     }
     CUDA_TRY(c, cudaSetDevice(c->device));
-    free_field(c);
     std::vector<float4> rect;
     std::vector<double> cdf;
     std::vector<FieldHost> fh(n);
@@ -566,22 +643,63 @@ mc_status set_fields_impl(mc_ctx* c, const mc_field_desc* f, int n, const mc_lut
     }
     const int np = npix(c);
     const size_t tally_n = static_cast<size_t>(n) * c->cfg.n_batches * np;
-    const int parts = (np + 255) / 256;
-    CUDA_TRY(c, cudaMalloc(&c->d_tally, tally_n * sizeof(unsigned long long)));
+    const size_t parts = (np + 255) / 256;
+    const size_t nks = lut ? static_cast<size_t>(n) * lut->nt : 0;
+    // Buffers are kept while large enough, and then nothing here waits for
+    // the device.  A buffer that must grow is replaced, which needs the
+    // previous run to have finished with it.
+    const bool grow = tally_n > c->cap_tally || static_cast<size_t>(np) > c->cap_pix || parts > c->cap_parts ||
+                      rect.size() > c->cap_rect || cdf.size() > c->cap_cdf ||
+                      static_cast<size_t>(n) * np > c->cap_tmap || (lut && (static_cast<size_t>(lut->nt) > c->cap_lut_t ||
+                                                                             nks > c->cap_ks));
+    if (grow) {
+        const mc_status prev = finalize_run(c);
+        if (prev != MC_OK) return prev;
+    } else {
+        const mc_status o = order_after_run(c, s);
+        if (o != MC_OK) return o;
+    }
+    clear_fields(c);
+    CUDA_TRY(c, ensure(c->d_tally, c->cap_tally, tally_n));
     c->tally_n = tally_n;
-    CUDA_TRY(c, cudaMalloc(&c->d_dose, sizeof(double) * np));
-    CUDA_TRY(c, cudaMalloc(&c->d_sigma, sizeof(double) * np));
-    CUDA_TRY(c, cudaMalloc(&c->d_part, sizeof(double) * parts));
-    CUDA_TRY(c, cudaMalloc(&c->d_partc, sizeof(unsigned int) * parts));
-    CUDA_TRY(c, cudaMalloc(&c->d_signal, sizeof(float) * np));
-    CUDA_TRY(c, cudaMalloc(&c->d_rect, sizeof(float4) * rect.size()));
-    CUDA_TRY(c, cudaMalloc(&c->d_cdf, sizeof(double) * cdf.size()));
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_rect, rect.data(), sizeof(float4) * rect.size(), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_cdf, cdf.data(), sizeof(double) * cdf.size(), cudaMemcpyHostToDevice, s));
+    size_t cp = c->cap_pix;
+    CUDA_TRY(c, ensure(c->d_dose, cp, static_cast<size_t>(np)));
+    cp = c->cap_pix;
+    CUDA_TRY(c, ensure(c->d_sigma, cp, static_cast<size_t>(np)));
+    cp = c->cap_pix;
+    CUDA_TRY(c, ensure(c->d_signal, cp, static_cast<size_t>(np)));
+    c->cap_pix = cp;
+    size_t cq = c->cap_parts;
+    CUDA_TRY(c, ensure(c->d_part, cq, parts));
+    cq = c->cap_parts;
+    CUDA_TRY(c, ensure(c->d_partc, cq, parts));
+    c->cap_parts = cq;
+    CUDA_TRY(c, ensure(c->d_rect, c->cap_rect, rect.size()));
+    CUDA_TRY(c, ensure(c->d_cdf, c->cap_cdf, cdf.size()));
+    CUDA_TRY(c, ensure(c->d_tmap, c->cap_tmap, static_cast<size_t>(n) * np));
+    // host data to the device through pinned staging, so the copies need no
+    // wait here; the staging is reused once the previous copies out of it ended
+    const size_t stage_bytes = sizeof(float4) * rect.size() + sizeof(double) * (cdf.size() + nks + (lut ? lut->nt : 0));
+    CUDA_TRY(c, cudaEventSynchronize(c->ev_stage));
+    if (stage_bytes > c->h_stage_cap) {
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        c->h_stage = nullptr;
+        c->h_stage_cap = 0;
+        CUDA_TRY(c, cudaMallocHost(&c->h_stage, stage_bytes));
+        c->h_stage_cap = stage_bytes;
+    }
+    char* stage = c->h_stage;
+    float4* h_rect = reinterpret_cast<float4*>(stage);
+    double* h_cdf = reinterpret_cast<double*>(stage + sizeof(float4) * rect.size());
+    double* h_ks = h_cdf + cdf.size();
+    double* h_lut_t = h_ks + nks;
+    std::memcpy(h_rect, rect.data(), sizeof(float4) * rect.size());
+    std::memcpy(h_cdf, cdf.data(), sizeof(double) * cdf.size());
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_rect, h_rect, sizeof(float4) * rect.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_cdf, h_cdf, sizeof(double) * cdf.size(), cudaMemcpyHostToDevice, s));
 
     // radiological thickness map of every field (a9)
     c->t_offset = lut ? lut->t_offset_cm : 0.0;
-    CUDA_TRY(c, cudaMalloc(&c->d_tmap, sizeof(double) * static_cast<size_t>(n) * np));
     const mc_epid_desc& E = c->epid;
     for (int i = 0; i < n; ++i) {
         const FieldHost& h = fh[i];
@@ -609,31 +727,29 @@ mc_status set_fields_impl(mc_ctx* c, const mc_field_desc* f, int n, const mc_lut
     }
 
     // k-table: the column at each field's s, for the per-pixel step along t
-    std::vector<double> ks;
     if (lut) {
-        ks.resize(static_cast<size_t>(n) * lut->nt);
         for (int i = 0; i < n; ++i) {
             const double sc = std::fmin(std::fmax(fh[i].s_eq, lut->s_nodes[0]), lut->s_nodes[lut->ns - 1]);
             int js = 0;
             while (js + 1 < lut->ns - 1 && lut->s_nodes[js + 1] <= sc) ++js;
             const double fs = (sc - lut->s_nodes[js]) / (lut->s_nodes[js + 1] - lut->s_nodes[js]);
             for (int it = 0; it < lut->nt; ++it)
-                ks[static_cast<size_t>(i) * lut->nt + it] = (1.0 - fs) * lut->k[static_cast<size_t>(js) * lut->nt + it] +
-                                                             fs * lut->k[static_cast<size_t>(js + 1) * lut->nt + it];
+                h_ks[static_cast<size_t>(i) * lut->nt + it] = (1.0 - fs) * lut->k[static_cast<size_t>(js) * lut->nt + it] +
+                                                               fs * lut->k[static_cast<size_t>(js + 1) * lut->nt + it];
         }
-        CUDA_TRY(c, cudaMalloc(&c->d_lut_t, sizeof(double) * lut->nt));
-        CUDA_TRY(c, cudaMalloc(&c->d_lut_ks, sizeof(double) * ks.size()));
-        CUDA_TRY(c, cudaMemcpyAsync(c->d_lut_t, lut->t_nodes, sizeof(double) * lut->nt, cudaMemcpyHostToDevice, s));
-        CUDA_TRY(c, cudaMemcpyAsync(c->d_lut_ks, ks.data(), sizeof(double) * ks.size(), cudaMemcpyHostToDevice, s));
+        std::memcpy(h_lut_t, lut->t_nodes, sizeof(double) * lut->nt);
+        CUDA_TRY(c, ensure(c->d_lut_t, c->cap_lut_t, static_cast<size_t>(lut->nt)));
+        CUDA_TRY(c, ensure(c->d_lut_ks, c->cap_ks, nks));
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_lut_t, h_lut_t, sizeof(double) * lut->nt, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_lut_ks, h_ks, sizeof(double) * nks, cudaMemcpyHostToDevice, s));
         c->lut_nt = lut->nt;
         c->k_scale = lut->k_scale;
         c->has_lut = true;
     }
+    CUDA_TRY(c, cudaEventRecord(c->ev_stage, s));
     c->fields = fh;
     const mc_status st = clear_tally(c, s);
     if (st != MC_OK) return st;
-    // rect, cdf and ks are host vectors: finish their copies before returning
-    CUDA_TRY(c, cudaStreamSynchronize(s));
     c->has_field = true;
     return MC_OK;
 }
@@ -646,6 +762,10 @@ mc_status run_impl(mc_ctx* c, const uint64_t* n, uint64_t seed, cudaStream_t s, 
         first[i + 1] = first[i] + n[i];
     }
     CUDA_TRY(c, cudaSetDevice(c->device));
+    // a previous graph-driven run still in flight: wait for it (its control
+    // block and the pinned staging are reused) and report its outcome
+    const mc_status prev = finalize_run(c);
+    if (prev != MC_OK) return prev;
     c->cancel.store(0);
     mc_status st = upload_fields(c, first, s);
     if (st != MC_OK) return st;
@@ -656,17 +776,21 @@ mc_status run_impl(mc_ctx* c, const uint64_t* n, uint64_t seed, cudaStream_t s, 
     h.n_total = first.back();
     CUDA_TRY(c, cudaMemcpyAsync(c->d_ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaMemsetAsync(c->d_heads, 0, kHeadsBytes, s));
-    cudaEvent_t e0, e1;
-    CUDA_TRY(c, cudaEventCreate(&e0));
-    CUDA_TRY(c, cudaEventCreate(&e1));
-    WaveResult r;
-    const mc_status result = c->cfg.use_graph ? run_waves_graph(c, P, s, e0, r) : run_waves_host(c, P, s, e0, r);
-    float ms = 0.f;
-    if (cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess)
-        cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     for (size_t i = 0; i < c->fields.size(); ++i) c->fields[i].hist_done += n[i];
+    WaveResult r;
+    // per-kernel timing needs the host-driven loop
+    if (c->cfg.use_graph && !c->cfg.time_kernels) {
+        const mc_status result = run_waves_graph(c, P, s, r);
+        if (result != MC_OK) return result;
+        if (!stats) return MC_OK;                 // queued on s; nothing waited for
+        const mc_status outcome = finalize_run(c);
+        const mc_status s2 = mc_get_stats(c, stats);
+        return outcome != MC_OK ? outcome : s2;
+    }
+    const mc_status result = run_waves_host(c, P, s, c->ev_run0, r);
+    float ms = 0.f;
+    if (cudaEventRecord(c->ev_run1, s) == cudaSuccess && cudaEventSynchronize(c->ev_run1) == cudaSuccess)
+        cudaEventElapsedTime(&ms, c->ev_run0, c->ev_run1);
     c->last_waves = r.waves;
     c->last_error = h.error;
     c->last_ms = ms;
@@ -683,17 +807,13 @@ mc_status compute_dose(mc_ctx* c, int field, double* dose, double* sigma, double
     const int B = c->cfg.n_batches;
     const uint64_t N = c->fields[field].hist_done;
     if (N == 0) return fail(c, MC_ERR_STATE, "no histories run");
-    std::vector<double> nb(B);
-    for (int b = 0; b < B; ++b) nb[b] = static_cast<double>(N / B + (static_cast<uint64_t>(b) < N % B ? 1 : 0));
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_nb, nb.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, mc::launch_batch_counts(c->d_nb, B, N, s));
     const mc_epid_desc& E = c->epid;
     const int l = E.sensitive_layer;
     const double mass_kg = E.density[l] * E.pitch_cm * E.pitch_cm * E.thickness_cm[l] * 1e-3;
     const unsigned long long* tally = c->d_tally + static_cast<size_t>(field) * B * npix(c);
     CUDA_TRY(c, mc::launch_dose(tally, npix(c), B, c->d_nb, static_cast<double>(N), kJoulePerMeV / mass_kg, dose,
                                 sigma, c->d_maxbits, c->d_part, c->d_partc, u_dev, s));
-    // nb is a host vector: finish its copy before returning
-    CUDA_TRY(c, cudaStreamSynchronize(s));
     return MC_OK;
 }
 
@@ -735,7 +855,7 @@ void mc_config_default(mc_config* cfg) {
     cfg->bank_capacity = 1u << 23;
     cfg->primaries_per_wave = 0;
     cfg->time_kernels = 0;
-    cfg->use_graph = 0;
+    cfg->use_graph = 1;
     for (int t = 0; t < 4; ++t) cfg->regs_variant[t] = kDefaultRegsVariant[t];
     cfg->patient_dose = 0;
 }
@@ -812,8 +932,13 @@ mc_status mc_create(const mc_config* cfg_in, int device, mc_ctx** out) {
         }
     }
     if (cudaMalloc(&c->d_ctl, sizeof(Ctl)) != cudaSuccess || cudaMallocHost(&c->h_ctl, sizeof(Ctl)) != cudaSuccess ||
-        cudaMalloc(&c->d_heads, kHeadsBytes) != cudaSuccess)
+        cudaMalloc(&c->d_heads, kHeadsBytes) != cudaSuccess ||
+        cudaMallocHost(&c->h_fields, sizeof(FieldDev) * mc::kMaxFields) != cudaSuccess ||
+        cudaMallocHost(&c->h_first, sizeof(unsigned long long) * (mc::kMaxFields + 1)) != cudaSuccess)
         return bail(MC_ERR_OOM);
+    if (cudaEventCreate(&c->ev_run0) != cudaSuccess || cudaEventCreate(&c->ev_run1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_stage, cudaEventDisableTiming) != cudaSuccess)
+        return bail(MC_ERR_CUDA);
     if (cudaMalloc(&c->d_energy, sizeof(unsigned long long) * mc::kNumEnergy) != cudaSuccess ||
         cudaMalloc(&c->d_events, sizeof(unsigned long long) * mc::kNumEvents) != cudaSuccess ||
         cudaMalloc(&c->d_rho_max, sizeof(unsigned int) * 4) != cudaSuccess ||
@@ -845,7 +970,15 @@ mc_status mc_create(const mc_config* cfg_in, int device, mc_ctx** out) {
 mc_status mc_destroy(mc_ctx* c) {
     if (!c) return MC_OK;
     cudaSetDevice(c->device);
-    free_field(c);
+    finalize_run(c);
+    if (c->ev_stage) cudaEventSynchronize(c->ev_stage);
+    free_field_buffers(c);
+    if (c->h_fields) cudaFreeHost(c->h_fields);
+    if (c->h_first) cudaFreeHost(c->h_first);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->ev_run0) cudaEventDestroy(c->ev_run0);
+    if (c->ev_run1) cudaEventDestroy(c->ev_run1);
+    if (c->ev_stage) cudaEventDestroy(c->ev_stage);
     dfree(c->d_ptab);
     dfree(c->d_etab);
     if (c->bank_mem) cudaFree(c->bank_mem);
@@ -891,7 +1024,9 @@ mc_status mc_init_geometry(mc_ctx* c, const int16_t* hu, int nx, int ny, int nz,
             return fail(c, MC_ERR_ARG, "bad EPID layer");
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
-    free_field(c);
+    const mc_status prev = finalize_run(c);          // the CT buffers below may be replaced
+    if (prev != MC_OK) return prev;
+    clear_fields(c);
     const size_t nvox = static_cast<size_t>(nx) * ny * nz;
     if (nvox > c->nvox_alloc) {
         dfree(c->d_hu);
@@ -975,6 +1110,7 @@ mc_status mc_run_batch(mc_ctx* c, const uint64_t* n, uint64_t seed, void* stream
 mc_status mc_get_stats(mc_ctx* c, mc_run_stats* st) {
     if (!c || !st) return MC_ERR_ARG;
     CUDA_TRY(c, cudaSetDevice(c->device));
+    const mc_status outcome = finalize_run(c);
     unsigned long long en[mc::kNumEnergy], ev[mc::kNumEvents];
     CUDA_TRY(c, cudaMemcpy(en, c->d_energy, sizeof(en), cudaMemcpyDeviceToHost));
     CUDA_TRY(c, cudaMemcpy(ev, c->d_events, sizeof(ev), cudaMemcpyDeviceToHost));
@@ -994,7 +1130,7 @@ mc_status mc_get_stats(mc_ctx* c, mc_run_stats* st) {
         st->kernel_launches[t] = c->last_kernel_launches[t];
     }
     st->launches = c->last_launches;
-    return MC_OK;
+    return outcome;
 }
 
 mc_status mc_get_field_dose(mc_ctx* c, int field, double* dose, double* sigma, double* u_out, int on_device,
@@ -1005,6 +1141,7 @@ mc_status mc_get_field_dose(mc_ctx* c, int field, double* dose, double* sigma, d
     if (!dose) return fail(c, MC_ERR_ARG, "null dose");
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
+    { const mc_status o = order_after_run(c, s); if (o != MC_OK) return o; }
     double* dd = on_device ? dose : c->d_dose;
     double* ds = on_device ? (sigma ? sigma : c->d_sigma) : c->d_sigma;
     st = compute_dose(c, field, dd, ds, u_out ? c->d_u : nullptr, s);
@@ -1031,6 +1168,7 @@ mc_status mc_get_field_image(mc_ctx* c, int field, float* signal, int on_device,
     if (!signal) return fail(c, MC_ERR_ARG, "null signal");
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
+    { const mc_status o = order_after_run(c, s); if (o != MC_OK) return o; }
     st = compute_dose(c, field, c->d_dose, c->d_sigma, nullptr, s);
     if (st != MC_OK) return st;
     float* out = on_device ? signal : c->d_signal;
@@ -1054,6 +1192,7 @@ mc_status mc_get_field_tmap(mc_ctx* c, int field, double* t, int on_device, void
     if (!t) return fail(c, MC_ERR_ARG, "null output");
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
+    { const mc_status o = order_after_run(c, s); if (o != MC_OK) return o; }
     CUDA_TRY(c, cudaMemcpyAsync(t, c->d_tmap + static_cast<size_t>(field) * npix(c), sizeof(double) * npix(c),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(s));
@@ -1070,6 +1209,7 @@ mc_status mc_get_tally(mc_ctx* c, uint64_t* tally, int on_device, void* stream) 
     if (!tally) return fail(c, MC_ERR_ARG, "null output");
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
+    { const mc_status o = order_after_run(c, s); if (o != MC_OK) return o; }
     CUDA_TRY(c, cudaMemcpyAsync(tally, c->d_tally, sizeof(uint64_t) * c->tally_n,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(s));
@@ -1086,6 +1226,7 @@ mc_status mc_get_plan_image(mc_ctx* c, const double* weights, double* dose, doub
         if (c->fields[f].hist_done == 0) return fail(c, MC_ERR_STATE, "a field has no histories");
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
+    { const mc_status o = order_after_run(c, s); if (o != MC_OK) return o; }
     double *acc_d = nullptr, *acc_s = nullptr;
     CUDA_TRY(c, cudaMalloc(&acc_d, sizeof(double) * np * 2));
     acc_s = acc_d + np;
@@ -1119,6 +1260,7 @@ mc_status mc_get_patient_dose(mc_ctx* c, double* dose, int on_device, void* stre
     if (N == 0) return fail(c, MC_ERR_STATE, "no histories run");
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
+    { const mc_status o = order_after_run(c, s); if (o != MC_OK) return o; }
     const double vol = c->vox[0] * c->vox[1] * c->vox[2];
     // Gy per history = E[MeV] * J/MeV / (rho[g/cm^3] V[cm^3] 1e-3 kg/g) / N
     const double conv = kJoulePerMeV / (kQuantaPerMeV * vol * 1e-3 * static_cast<double>(N));
@@ -1153,6 +1295,7 @@ mc_status mc_reset_tally(mc_ctx* c, void* stream) {
     if (!c) return MC_ERR_ARG;
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
+    { const mc_status o = order_after_run(c, s); if (o != MC_OK) return o; }
     const mc_status st = clear_tally(c, s);
     if (st != MC_OK) return st;
     CUDA_TRY(c, cudaStreamSynchronize(s));
@@ -1172,6 +1315,7 @@ mc_status mc_get_state(mc_ctx* c, void* buf, size_t bytes, void* stream) {
     if (bytes < state_words(c) * sizeof(uint64_t)) return fail(c, MC_ERR_ARG, "state buffer too small");
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
+    { const mc_status o = order_after_run(c, s); if (o != MC_OK) return o; }
     uint64_t* w = static_cast<uint64_t*>(buf);
     const size_t F = c->fields.size();
     w[0] = kStateMagic; w[1] = c->cfg.n_batches; w[2] = c->epid.npx; w[3] = c->epid.npy; w[4] = F;
@@ -1202,6 +1346,7 @@ mc_status mc_set_state(mc_ctx* c, const void* buf, size_t bytes, void* stream) {
         return fail(c, MC_ERR_ARG, "state does not match this context");
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = as_stream(stream);
+    { const mc_status o = order_after_run(c, s); if (o != MC_OK) return o; }
     const uint64_t* q = w + kStateHead + F;
     CUDA_TRY(c, cudaMemcpyAsync(c->d_energy, q, sizeof(uint64_t) * mc::kNumEnergy, cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_events, q + mc::kNumEnergy, sizeof(uint64_t) * mc::kNumEvents,

@@ -357,6 +357,16 @@ cudaError_t launch_tmap(const TmapArgs& A, double* t, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+__global__ void k_batch_counts(double* nb, int B, unsigned long long n) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) nb[b] = static_cast<double>(n / B + (static_cast<unsigned long long>(b) < n % B ? 1ull : 0ull));
+}
+
+cudaError_t launch_batch_counts(double* nb, int B, unsigned long long n, cudaStream_t s) {
+    k_batch_counts<<<(B + 127) / 128, 128, 0, s>>>(nb, B, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dose(const unsigned long long* tally, int npix, int B, const double* nb, double n_hist,
                         double conv, double* dose, double* sigma, unsigned long long* max_bits, double* part_sum,
                         unsigned int* part_cnt, double* u, cudaStream_t s) {

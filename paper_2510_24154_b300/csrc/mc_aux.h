@@ -41,6 +41,8 @@ cudaError_t launch_homogeneity(const int16_t* hu, int nx, int ny, int nz, int ra
 cudaError_t launch_macro_grid(const float* rho, int nx, int ny, int nz, int M, int mgx, int mgy, int mgz,
                               float thr_bone, float2* grid, int sm_count, cudaStream_t s);
 cudaError_t launch_tmap(const TmapArgs& A, double* t, cudaStream_t s);
+// nb[b] = the number of history indices 0 .. n-1 with index mod B == b.
+cudaError_t launch_batch_counts(double* nb, int B, unsigned long long n, cudaStream_t s);
 cudaError_t launch_dose(const unsigned long long* tally, int npix, int B, const double* nb, double n_hist,
                         double conv, double* dose, double* sigma, unsigned long long* max_bits, double* part_sum,
                         unsigned int* part_cnt, double* u, cudaStream_t s);

@@ -306,6 +306,15 @@ def config_water_open(n_histories=1_000_000, seed=0, npx=128, npy=128, pitch=0.3
         n_histories=n_histories, seed=seed)
 
 
+def config_paper_grid(n_histories=1_000_000_000, seed=0) -> Problem:
+    """The small single-field workload coupled, scored on the EPID grid of the
+    paper's image comparisons: 160 x 160 pixels at 2.5 mm (64 x 40 x 64 water
+    at 5 mm, SSD 90, open 10 x 10 field)."""
+    p = config_water_open(n_histories=n_histories, seed=seed, npx=160, npy=160, pitch=0.25, coupled=True)
+    p.name = "water_open_10x10_paper_grid"
+    return p
+
+
 def config_thorax_imrt(n_histories=100_000_000, seed=1, scale=1, epid_scale=1,
                        n_seg=9, gantry_deg=0.0) -> Problem:
     """Coupled transport through the 256x256x128 thorax CT at 2 mm, one 9-segment
