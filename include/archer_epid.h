@@ -131,12 +131,13 @@ typedef struct mc_field_desc {
     double sad_cm, sid_cm;
     double iso_cm[3];             /* isocentre in CT coordinates */
     int eq1_literal;              /* 0: s = 2ab/(a+b); 1: s = ab/(2(a+b)) exactly as Eq. 1 is printed */
-    /* Collimation (Sec. 2.1.1 transports the beam through jaws and MLC; this
-     * library models them as fluence filters on the isocentre plane, inside
-     * the largest field |X|, |Y| <= 20 cm and the MLC's extent).  Per MU the
+    /* Collimation (Sec. 2.1.1 transports the beam through jaws and MLC), in
+     * one of two models, inside the largest field |X|, |Y| <= 20 cm and the
+     * MLC's extent.  Fluence filters on the isocentre plane: per MU the
      * fluence is (leaf factor) x (jaw factor): 1 inside the effective opening
      * of the point's leaf pair, else leaf_transmission; 1 inside the segment's
-     * jaws, else jaw_transmission.  All zero: the ideal aperture. */
+     * jaws, else jaw_transmission.  All zero: the ideal aperture.  Or slabs
+     * (leaf_thickness_cm / jaw_thickness_cm below). */
     double leaf_transmission;     /* 0 <= T < 1 */
     double jaw_transmission;      /* 0 <= Tj < 1 */
     double tg_width_cm;           /* tongue and groove: within half this width of a pair boundary the
@@ -144,6 +145,19 @@ typedef struct mc_field_desc {
                                      0 <= w < narrowest pair */
     double leaf_gap_cm;           /* dosimetric leaf gap: an open pair's tips move apart by g/2 each
                                      (rounded leaf ends); a pair whose tips meet stays closed; 0 <= g < 2 */
+    /* Collimator slabs: the leaves and jaws as laterally infinite tungsten
+     * slabs (19.3 g/cm^3) of these thicknesses along the beam, the jaws' top
+     * 28 cm and the leaves' top 51 cm from the source.  Either > 0 switches
+     * the source to phase space 2 of Sec. 2.1.1: photons of the open-beam
+     * source are drawn uniformly over the 40 x 40 cm field (segments by MU)
+     * until one leaves the slabs its ray crosses (a jaw slab outside the
+     * segment's jaws, a leaf slab outside its pair's effective opening), with
+     * Compton scattering in the tungsten and photoelectric and pair
+     * absorption there; that photon, from the bottom of its last slab, is the
+     * history.  Then both transmissions above must be 0.  A slab of
+     * thickness 0 is ideal (opaque). */
+    double leaf_thickness_cm;     /* 0 <= t <= 20 */
+    double jaw_thickness_cm;      /* 0 <= t < 23 */
 } mc_field_desc;
 
 /* k(t, s) table of Sec. 3.1 (Eq. 2, Table 1): k[is * nt + it] on strictly

@@ -57,6 +57,7 @@ class _Problem(C.Structure):
         ("ecut", C.c_double), ("wcc", C.c_double), ("wcb", C.c_double), ("step_frac", C.c_double),
         ("n_batches", C.c_int), ("max_steps", C.c_int), ("leaf_trans", C.c_double),
         ("jaw_trans", C.c_double), ("tg_width", C.c_double), ("leaf_gap", C.c_double),
+        ("leaf_thick", C.c_double), ("jaw_thick", C.c_double),
     ]
 
 
@@ -127,6 +128,9 @@ def lib():
         _lib.orc_tmap.argtypes = [P(_Problem), P(C.c_int32), P(C.c_int32), C.c_int64, P(d)]
         _lib.orc_siddon_ray.restype = d
         _lib.orc_siddon_ray.argtypes = [P(_Problem), P(d), P(d)]
+        _lib.orc_sample_ps2_many.restype = i
+        _lib.orc_sample_ps2_many.argtypes = [P(_Problem), u64, u64, u64, P(d), P(d), P(d), P(C.c_int32),
+                                             P(C.c_int32)]
         _lib.orc_sample_source_many.restype = i
         _lib.orc_sample_source_many.argtypes = [P(_Problem), u64, u64, u64, P(d), P(d), P(d)]
         _lib.orc_gamma.restype = d
@@ -174,6 +178,12 @@ class _Marshalled:
         s.jaw_trans = float(getattr(fld, "jaw_transmission", 0.0))
         s.tg_width = float(getattr(fld, "tg_width", 0.0))
         s.leaf_gap = float(getattr(fld, "leaf_gap", 0.0))
+        s.leaf_thick = float(getattr(fld, "leaf_thickness", 0.0))
+        s.jaw_thick = float(getattr(fld, "jaw_thickness", 0.0))
+        if not (0.0 <= s.leaf_thick <= 20.0 and 0.0 <= s.jaw_thick < 23.0):
+            raise ValueError("need 0 <= leaf slab <= 20 cm and 0 <= jaw slab < 23 cm")
+        if (s.leaf_thick > 0.0 or s.jaw_thick > 0.0) and (s.leaf_trans > 0.0 or s.jaw_trans > 0.0):
+            raise ValueError("collimator slabs replace the transmission factors: set those to 0")
         edges = np.asarray(fld.pair_edges, dtype=np.float64)
         if not (0.0 <= s.leaf_trans < 1.0 and 0.0 <= s.jaw_trans < 1.0):
             raise ValueError("transmissions must lie in [0, 1)")
@@ -320,6 +330,22 @@ def sample_source(problem, n, seed=0, hist_begin=0):
     if rc:
         raise RuntimeError("field has no open aperture")
     return X, Y, E
+
+
+def sample_ps2(problem, n, seed=0, hist_begin=0, physics=None, field=None):
+    """Phase-space-2 photons of histories hist_begin.. as the transport draws
+    them (collimator slabs crossed): the source ray's isocentre-plane point
+    (X, Y), the energy (NaN if none left the collimators), whether it
+    scattered in a slab, and how many source photons the history drew."""
+    m = _Marshalled(problem, physics, field)
+    X, Y, E = np.empty(n), np.empty(n), np.empty(n)
+    coll = np.empty(n, dtype=np.int32)
+    k = np.empty(n, dtype=np.int32)
+    rc = lib().orc_sample_ps2_many(C.byref(m.s), int(seed), int(hist_begin), int(n), _dp(X), _dp(Y), _dp(E),
+                                   coll.ctypes.data_as(C.POINTER(C.c_int32)), k.ctypes.data_as(C.POINTER(C.c_int32)))
+    if rc:
+        raise RuntimeError("field has no source rectangle")
+    return X, Y, E, coll.astype(bool), k
 
 
 def tmap(problem, ix=None, iy=None, field=None):

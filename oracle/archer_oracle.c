@@ -46,11 +46,17 @@
 #define O_PE_P 3.2
 #define O_GD_EK 0.05024            /* Gd K edge, MeV */
 #define O_GD_JUMP 5.3              /* Gd K-edge jump ratio */
+#define O_W_EK 0.069525            /* W K edge, MeV */
+#define O_W_JUMP 4.6               /* W K-edge jump ratio */
+#define O_W_RHO 19.3               /* tungsten collimator density, g/cm^3 */
+#define O_JAW_TOP 28.0             /* jaw slab top, cm from the source */
+#define O_MLC_TOP 51.0             /* MLC slab top, cm from the source */
+#define O_MAT_W 7
 #define O_PAIR_C 2.57e-27          /* pair fit: C Z(Z+1) (1-2mc^2/E)^4, cm^2 */
 #define O_BREM_B 4.65e-27          /* bremsstrahlung fit: dsigma/dk = B Z(Z+1)/k, cm^2 */
 #define O_ES 21.2                  /* Rossi scattering energy, MeV */
 #define O_TSTOP 1e-6               /* an electron stops once T <= cutoff + this, MeV */
-#define O_NMAT 7
+#define O_NMAT 8
 #define O_MAXL 8
 #define O_HOM_R 2                  /* half-width of a homogeneous voxel's neighbourhood, voxels */
 #define O_HOM_SPAN 200             /* largest HU span within a homogeneous neighbourhood */
@@ -78,6 +84,8 @@ static const o_matdef O_MATS[O_NMAT] = {
     {3, {{64, 157.25, 0.830790}, {8, 15.999, 0.084524}, {16, 32.06, 0.084686}}, 437.0},
     /* 6 amorphous silicon */
     {1, {{14, 28.085, 1.0}}, 173.0},
+    /* 7 tungsten (collimator slabs; photons only) */
+    {1, {{74, 183.84, 1.0}}, 727.0},
 };
 
 /* ------------------------------------------------------------------------ */
@@ -105,6 +113,7 @@ void orc_mu_photon(int m, double E, double out[3]) {
         zA += el->w * el->Z / el->A;
         double pz = el->w / el->A * pow((double)el->Z, O_PE_N);
         if (el->Z == 64 && E < O_GD_EK) pz /= O_GD_JUMP;
+        if (el->Z == 74 && E < O_W_EK) pz /= O_W_JUMP;
         pe += pz;
         zz += el->w * el->Z * (el->Z + 1.0) / el->A;
     }
@@ -361,6 +370,8 @@ typedef struct {
     double jaw_trans;            /* fluence fraction through the jaws (0: opaque) */
     double tg_width;             /* tongue-and-groove strip width at the isocentre plane, cm */
     double leaf_gap;             /* dosimetric leaf gap of an open pair, cm */
+    double leaf_thick;           /* tungsten leaf slab thickness along the beam, cm (0: no leaf slab) */
+    double jaw_thick;            /* tungsten jaw slab thickness along the beam, cm (0: no jaw slab) */
 } orc_problem;
 
 enum { C_FLIGHTS_CT, C_REAL_CT, C_COMPTON, C_PHOTO, C_PAIR, C_ESTEP_CT, C_ESTEP_EPID, C_MOLLER, C_BREM,
@@ -447,6 +458,7 @@ typedef struct {
     double* mg_bone;                  /* per macro-cell max density of bone voxels */
     unsigned char* hom;               /* per voxel: 1 if homogeneous (see ctx_homogeneity) */
     double* rect;                     /* source rectangles: x0,x1,y0,y1 */
+    int* rflag;                       /* per rectangle: bit 0 behind a closed leaf, bit 1 outside the jaws */
     double* cdf;                      /* cumulative weight */
     int n_rect;
     /* per worker */
@@ -1188,10 +1200,12 @@ static void electron(o_ctx* c, o_part* p) {
  * the opening, the part right of it (a closed pair is one part).  Openings
  * weigh MU x area; closed parts MU x T x area with T the leaf transmission
  * (absent when T = 0).  Returns whether any opening exists. */
-static void add_rect(o_ctx* c, int* n, double* acc, double x0, double x1, double y0, double y1, double w) {
+static void add_rect(o_ctx* c, int* n, double* acc, double x0, double x1, double y0, double y1, double w,
+                     int flag) {
     if (!(x1 > x0) || !(y1 > y0) || !(w > 0.0)) return;
     *acc += w * (x1 - x0) * (y1 - y0);
     c->rect[4 * *n] = x0; c->rect[4 * *n + 1] = x1; c->rect[4 * *n + 2] = y0; c->rect[4 * *n + 3] = y1;
+    c->rflag[*n] = flag;
     c->cdf[*n] = *acc;
     (*n)++;
 }
@@ -1247,7 +1261,12 @@ static int build_source(o_ctx* c) {
     const double C = O_FIELD_HALF, w = P->tg_width;
     int nmax = 25 * P->n_seg * P->n_pairs;
     c->rect = (double*)malloc(sizeof(double) * 4 * (size_t)(nmax > 0 ? nmax : 1));
+    c->rflag = (int*)malloc(sizeof(int) * (size_t)(nmax > 0 ? nmax : 1));
     c->cdf = (double*)malloc(sizeof(double) * (size_t)(nmax > 0 ? nmax : 1));
+    /* collimator slabs (leaves and jaws as tungsten of the stated thickness):
+     * every rectangle of the field weighs MU x area, and its flags say which
+     * slabs its photons cross; without slabs the fluence factors apply */
+    const int slab = P->leaf_thick > 0.0 || P->jaw_thick > 0.0;
     double acc = 0.0;
     int n = 0, open = 0;
     for (int k = 0; k < P->n_seg; k++) {
@@ -1287,9 +1306,18 @@ static int build_source(o_ctx* c) {
                 const int nx = breakpoints(-C, C, xcut, has ? 4 : 2, xb);
                 for (int a = 0; a + 1 < nx; a++) {
                     const double x0 = xb[a], x1 = xb[a + 1], xm = 0.5 * (x0 + x1);
-                    const double leaf = (has && xm >= lo && xm <= hi) ? 1.0 : P->leaf_trans;
-                    const double jaw = (in_jaw_y && xm >= jx0 && xm <= jx1) ? 1.0 : P->jaw_trans;
-                    add_rect(c, &n, &acc, x0, x1, y0, y1, mu * leaf * jaw);
+                    const int in_leaf = has && xm >= lo && xm <= hi;
+                    const int in_jaw = in_jaw_y && xm >= jx0 && xm <= jx1;
+                    double leaf, jaw;
+                    if (slab) {
+                        leaf = (in_leaf || P->leaf_thick > 0.0) ? 1.0 : 0.0;
+                        jaw = (in_jaw || P->jaw_thick > 0.0) ? 1.0 : 0.0;
+                    } else {
+                        leaf = in_leaf ? 1.0 : P->leaf_trans;
+                        jaw = in_jaw ? 1.0 : P->jaw_trans;
+                    }
+                    add_rect(c, &n, &acc, x0, x1, y0, y1, mu * leaf * jaw,
+                             slab ? ((in_leaf ? 0 : 1) | (in_jaw ? 0 : 2)) : 0);
                 }
             }
         }
@@ -1300,8 +1328,9 @@ static int build_source(o_ctx* c) {
     return open;
 }
 
-/* Draws of a primary: rectangle (1), X (1), Y (1), then the spectrum. */
-static void sample_source(const o_ctx* c, o_rng* r, double* X, double* Y, double* E) {
+/* Draws of a primary: rectangle (1), X (1), Y (1), then the spectrum.
+ * Returns the rectangle's slab flags. */
+static int sample_source(const o_ctx* c, o_rng* r, double* X, double* Y, double* E) {
     const orc_problem* P = c->P;
     /* rectangle: first index whose cumulative weight exceeds the draw */
     double xi = rng_u(r);
@@ -1314,6 +1343,82 @@ static void sample_source(const o_ctx* c, o_rng* r, double* X, double* Y, double
     *X = q[0] + (q[1] - q[0]) * rng_u(r);
     *Y = q[2] + (q[3] - q[2]) * rng_u(r);
     *E = (P->mono_e > 0.0) ? P->mono_e : sample_spectrum(r, P->e_max, P->pcut);
+    return c->rflag[lo];
+}
+
+/* Photon transport through a laterally infinite tungsten slab between the
+ * beam-frame planes Z = zt (top) and Z = zb < zt: flights against mu_W(E),
+ * Compton scattering (Klein-Nishina, the photon goes on), photoelectric
+ * absorption and pair production absorbed in the collimator (their electrons
+ * and annihilation photons do not leave the head; stated reading).  x (on or
+ * above the top plane), u, E in the beam frame; returns 1 with the state at
+ * the bottom plane if the photon leaves there, 0 if it is absorbed, falls
+ * below the photon cutoff or leaves through the top. */
+static int slab_transport(const orc_problem* P, o_rng* r, double x[3], double u[3], double* E, double zt, double zb,
+                          int* collided) {
+    for (int f = 0; f < P->max_steps; f++) {
+        double mu[3];
+        orc_mu_photon(O_MAT_W, *E, mu);
+        const double tot = O_W_RHO * (mu[0] + mu[1] + mu[2]);
+        rng_align(r);
+        const double s = -log(rng_u(r)) / tot;
+        double d = INFINITY;
+        if (u[2] < 0.0) d = (zb - x[2]) / u[2];
+        else if (u[2] > 0.0) d = (zt - x[2]) / u[2];
+        if (!(s < d)) {
+            if (!(u[2] < 0.0)) return 0;
+            for (int a = 0; a < 3; a++) x[a] += d * u[a];
+            x[2] = zb;
+            return 1;
+        }
+        for (int a = 0; a < 3; a++) x[a] += s * u[a];
+        const double xi = rng_u(r);
+        if (!(xi * (mu[0] + mu[1] + mu[2]) < mu[0])) return 0;     /* photoelectric or pair */
+        double eps, ct;
+        sample_kn(r, *E, &eps, &ct);
+        rotate(u, ct, 2.0 * O_PI * rng_u(r));
+        *E *= eps;
+        *collided = 1;
+        if (*E < P->pcut) return 0;
+    }
+    return 0;
+}
+
+/* Phase space 2 of Sec. 2.1.1 with the collimators as tungsten slabs: photons
+ * of the open-beam source (phase space 1) are drawn, with the history's own
+ * stream, until one leaves the jaw and leaf slabs it crosses (a rectangle's
+ * flags: bit 1 outside the jaws, bit 0 behind a closed leaf; jaws above the
+ * MLC); that photon is the history.  Returns 1 with its beam-frame position
+ * x (the source, or the bottom of the last slab crossed), direction u,
+ * energy, the isocentre-plane point (X, Y) of its source ray, whether it
+ * scattered in a slab and the number of source photons drawn; 0 if
+ * O_PS1_CAP draws all ended in the collimators. */
+#define O_PS1_CAP 100000
+static int sample_ps2(const o_ctx* c, o_rng* r, double* X, double* Y, double* E, double x[3], double u[3],
+                      int* collided, int* n_ps1) {
+    const orc_problem* P = c->P;
+    for (int k = 0; k < O_PS1_CAP; k++) {
+        const int flag = sample_source(c, r, X, Y, E);
+        *n_ps1 = k + 1;
+        const double nb = sqrt(*X * *X + *Y * *Y + P->sad * P->sad);
+        x[0] = 0.0; x[1] = 0.0; x[2] = P->sad;
+        u[0] = *X / nb; u[1] = *Y / nb; u[2] = -P->sad / nb;
+        *collided = 0;
+        if (flag & 2) {
+            const double zt = P->sad - O_JAW_TOP, t = (zt - x[2]) / u[2];
+            for (int a = 0; a < 3; a++) x[a] += t * u[a];
+            x[2] = zt;
+            if (!slab_transport(P, r, x, u, E, zt, zt - P->jaw_thick, collided)) continue;
+        }
+        if (flag & 1) {
+            const double zt = P->sad - O_MLC_TOP, t = (zt - x[2]) / u[2];
+            for (int a = 0; a < 3; a++) x[a] += t * u[a];
+            x[2] = zt;
+            if (!slab_transport(P, r, x, u, E, zt, zt - P->leaf_thick, collided)) continue;
+        }
+        return 1;
+    }
+    return 0;
 }
 
 /* Transport every particle on the stack, and their descendants, to the end. */
@@ -1329,7 +1434,6 @@ static void drain(o_ctx* c) {
 }
 
 static void run_history(o_ctx* c, uint64_t h, uint64_t seed) {
-    const orc_problem* P = c->P;
     c->hist = h;
     o_part p;
     memset(&p, 0, sizeof(p));
@@ -1337,12 +1441,10 @@ static void run_history(o_ctx* c, uint64_t h, uint64_t seed) {
     p.rng.key[0] = (uint32_t)seed; p.rng.key[1] = (uint32_t)(seed >> 32);
     p.rng.ord = 0; p.rng.hlo = (uint32_t)h; p.rng.hhi = (uint32_t)(h >> 32);
     p.rng.d = 0; p.rng.cvalid = 0;
-    double X, Y;
-    sample_source(c, &p.rng, &X, &Y, &p.E);
+    double X, Y, sb[3], ub[3];
+    int n_ps1;
+    if (!sample_ps2(c, &p.rng, &X, &Y, &p.E, sb, ub, &p.collided, &n_ps1)) return;
     c->e_src += p.E;
-    double nb = sqrt(X * X + Y * Y + P->sad * P->sad);
-    double ub[3] = {X / nb, Y / nb, -P->sad / nb};
-    double sb[3] = {0.0, 0.0, P->sad};
     to_patient(c, sb, p.x);
     to_patient_dir(c, ub, p.u);
     enter_world(c, &p);
@@ -1493,7 +1595,7 @@ int orc_run(const orc_problem* P, uint64_t seed, uint64_t hist_begin, uint64_t n
     o_ctx base;
     ctx_geometry(&base, P);
     ctx_homogeneity(&base);
-    if (!build_source(&base)) { free(base.rect); free(base.cdf); ctx_free(&base); return 2; }
+    if (!build_source(&base)) { free(base.rect); free(base.rflag); free(base.cdf); ctx_free(&base); return 2; }
     if (n_threads < 1) n_threads = 1;
     if (n_threads > P->n_batches) n_threads = P->n_batches;
     o_job* jobs = (o_job*)calloc((size_t)n_threads, sizeof(o_job));
@@ -1521,7 +1623,7 @@ int orc_run(const orc_problem* P, uint64_t seed, uint64_t hist_begin, uint64_t n
         }
         free(l->stack);
     }
-    free(jobs); free(th); free(base.rect); free(base.cdf);
+    free(jobs); free(th); free(base.rect); free(base.rflag); free(base.cdf);
     ctx_free(&base);
     return 0;
 }
@@ -1805,17 +1907,40 @@ double orc_gamma(const double* ref, const double* ev, int nx, int ny, double pix
     return neval ? (double)npass / neval : 1.0;
 }
 
+/* Phase-space-2 samples of histories h0..h0+n-1 (sample_ps2): the final
+ * source ray's isocentre-plane point (X, Y), the energy (NaN if none left
+ * the collimators), whether it scattered in a slab and the source photons
+ * drawn. */
+int orc_sample_ps2_many(const orc_problem* P, uint64_t seed, uint64_t h0, uint64_t n, double* X, double* Y,
+                        double* E, int32_t* collided, int32_t* n_ps1) {
+    o_ctx c;
+    ctx_geometry(&c, P);
+    build_source(&c);
+    if (c.n_rect == 0) { free(c.rect); free(c.rflag); free(c.cdf); ctx_free(&c); return 2; }
+    for (uint64_t i = 0; i < n; i++) {
+        o_rng r; hook_rng(&r, seed, h0 + i);
+        double x[3], u[3];
+        int coll = 0, k = 0;
+        if (!sample_ps2(&c, &r, &X[i], &Y[i], &E[i], x, u, &coll, &k)) E[i] = NAN;
+        collided[i] = coll;
+        n_ps1[i] = k;
+    }
+    free(c.rect); free(c.rflag); free(c.cdf);
+    ctx_free(&c);
+    return 0;
+}
+
 /* Source samples (isocentre-plane X, Y and energy) of histories h0..h0+n-1. */
 int orc_sample_source_many(const orc_problem* P, uint64_t seed, uint64_t h0, uint64_t n, double* X, double* Y,
                            double* E) {
     o_ctx c;
     ctx_geometry(&c, P);
-    if (!build_source(&c)) { free(c.rect); free(c.cdf); ctx_free(&c); return 2; }
+    if (!build_source(&c)) { free(c.rect); free(c.rflag); free(c.cdf); ctx_free(&c); return 2; }
     for (uint64_t i = 0; i < n; i++) {
         o_rng r; hook_rng(&r, seed, h0 + i);
         sample_source(&c, &r, &X[i], &Y[i], &E[i]);
     }
-    free(c.rect); free(c.cdf);
+    free(c.rect); free(c.rflag); free(c.cdf);
     ctx_free(&c);
     return 0;
 }

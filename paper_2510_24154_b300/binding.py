@@ -54,7 +54,8 @@ class FieldDesc(C.Structure):
                 ("mu", C.POINTER(C.c_double)), ("gantry_deg", C.c_double), ("sad_cm", C.c_double),
                 ("sid_cm", C.c_double), ("iso_cm", C.c_double * 3), ("eq1_literal", C.c_int),
                 ("leaf_transmission", C.c_double), ("jaw_transmission", C.c_double),
-                ("tg_width_cm", C.c_double), ("leaf_gap_cm", C.c_double)]
+                ("tg_width_cm", C.c_double), ("leaf_gap_cm", C.c_double),
+                ("leaf_thickness_cm", C.c_double), ("jaw_thickness_cm", C.c_double)]
 
 
 class LutDesc(C.Structure):
@@ -258,6 +259,8 @@ class Simulator:
         f.jaw_transmission = float(getattr(field, "jaw_transmission", 0.0))
         f.tg_width_cm = float(getattr(field, "tg_width", 0.0))
         f.leaf_gap_cm = float(getattr(field, "leaf_gap", 0.0))
+        f.leaf_thickness_cm = float(getattr(field, "leaf_thickness", 0.0))
+        f.jaw_thickness_cm = float(getattr(field, "jaw_thickness", 0.0))
         return f
 
     @staticmethod

@@ -31,6 +31,7 @@ struct FieldHost {
     double sad, sid, zface;
     int rect_off, n_rect;
     double s_eq, bbox_a, bbox_b;
+    double leaf_t, jaw_t;     // collimator slab thicknesses, cm (0: ideal)
     uint64_t stream_base;     // random-stream id of the field's history 0 (f * 2^40)
     uint64_t hist_done;
 };
@@ -92,6 +93,7 @@ struct mc_ctx {
     unsigned long long* d_first = nullptr;
     float4* d_rect = nullptr;
     double* d_cdf = nullptr;
+    unsigned char* d_rflag = nullptr;   // per rectangle: collimator slabs its photons cross
     double* d_tmap = nullptr;    // [F][npix]
     bool has_lut = false;
     int lut_nt = 0;
@@ -138,7 +140,7 @@ struct mc_ctx {
     cudaEvent_t ev_stage = nullptr;            // recorded after the last copies out of h_stage
     // field buffers are kept while large enough: their capacities in elements
     size_t cap_tally = 0, cap_pix = 0, cap_parts = 0, cap_rect = 0, cap_cdf = 0, cap_tmap = 0, cap_lut_t = 0,
-           cap_ks = 0;
+           cap_ks = 0, cap_rflag = 0;
 };
 
 namespace {
@@ -180,6 +182,7 @@ void clear_fields(mc_ctx* c) {
 void free_field_buffers(mc_ctx* c) {
     dfree(c->d_rect);
     dfree(c->d_cdf);
+    dfree(c->d_rflag);
     dfree(c->d_tmap);
     dfree(c->d_lut_t);
     dfree(c->d_lut_ks);
@@ -190,6 +193,7 @@ void free_field_buffers(mc_ctx* c) {
     dfree(c->d_signal);
     dfree(c->d_tally);
     c->cap_tally = c->cap_pix = c->cap_parts = c->cap_rect = c->cap_cdf = c->cap_tmap = c->cap_lut_t = c->cap_ks = 0;
+    c->cap_rflag = 0;
     clear_fields(c);
 }
 
@@ -279,7 +283,13 @@ void make_params(const mc_ctx* c, Params& P, uint64_t seed) {
         P.lmat[l] = E.material[l];
         P.lrho[l] = static_cast<float>(E.density[l]);
     }
-    P.rect = c->d_rect; P.cdf = c->d_cdf;
+    P.rect = c->d_rect; P.cdf = c->d_cdf; P.rflag = c->d_rflag;
+    {
+        const mcphys::MaterialCoefs w = mcphys::tungsten_coefs();
+        P.wmat = {static_cast<float>(w.ne_barn), static_cast<float>(w.pe_above), static_cast<float>(w.pe_below),
+                  static_cast<float>(w.pair), 0.0f, 0.0f};
+        P.w_edge = static_cast<float>(mcphys::kWKEdge);
+    }
     P.e_max = static_cast<float>(c->cfg.e_max_mev);
     P.mono_e = static_cast<float>(c->cfg.mono_energy_mev);
     P.pcut = static_cast<float>(c->cfg.photon_cutoff_mev);
@@ -336,7 +346,7 @@ bool increasing(const double* a, int n) {
 // Source rectangles of one field (weight MU x open area, cumulative in
 // double, appended to rect / cdf), its bounding box, Eq. 1 and beam frame.
 mc_status build_field(mc_ctx* c, const mc_field_desc* f, int index, std::vector<float4>& rect,
-                      std::vector<double>& cdf, FieldHost& out) {
+                      std::vector<double>& cdf, std::vector<unsigned char>& rflag, FieldHost& out) {
     const std::string which = " (field " + std::to_string(index) + ")";
     if (!f->pair_edges_cm || !f->leaves_cm || !f->jaws_cm || !f->mu) return fail(c, MC_ERR_ARG, "null field" + which);
     if (f->n_segments < 1 || f->n_pairs < 1 || f->n_segments * f->n_pairs > (1 << 20))
@@ -352,14 +362,23 @@ mc_status build_field(mc_ctx* c, const mc_field_desc* f, int index, std::vector<
         narrowest = std::fmin(narrowest, f->pair_edges_cm[j + 1] - f->pair_edges_cm[j]);
     if (!(w >= 0.0 && w < narrowest)) return fail(c, MC_ERR_ARG, "tongue-and-groove width must be in [0, narrowest pair)" + which);
     if (!(gap >= 0.0 && gap < 2.0)) return fail(c, MC_ERR_ARG, "leaf gap must be in [0, 2) cm" + which);
+    const double tl = f->leaf_thickness_cm, tj = f->jaw_thickness_cm;
+    if (!(tl >= 0.0 && tl <= 20.0) || !(tj >= 0.0 && tj < 23.0))
+        return fail(c, MC_ERR_ARG, "need 0 <= leaf slab <= 20 cm and 0 <= jaw slab < 23 cm" + which);
+    // collimator slabs: every rectangle weighs MU x area and carries the slabs
+    // its photons cross; they replace the transmission factors
+    const bool slab = tl > 0.0 || tj > 0.0;
+    if (slab && (T > 0.0 || Tj > 0.0))
+        return fail(c, MC_ERR_ARG, "collimator slabs replace the transmission factors: set those to 0" + which);
     const size_t off = rect.size();
     double acc = 0.0, X0 = INFINITY, X1 = -INFINITY, Y0 = INFINITY, Y1 = -INFINITY;
     bool open = false;
-    auto add = [&](double x0, double x1, double y0, double y1, double wt) {
+    auto add = [&](double x0, double x1, double y0, double y1, double wt, unsigned char flag) {
         if (!(x1 > x0) || !(y1 > y0) || !(wt > 0.0)) return;
         acc += wt * (x1 - x0) * (y1 - y0);
         rect.push_back(make_float4(static_cast<float>(x0), static_cast<float>(x1), static_cast<float>(y0),
                                    static_cast<float>(y1)));
+        rflag.push_back(flag);
         cdf.push_back(acc);
     };
     // [lo, hi] framed and split at the cuts strictly inside it, ascending, distinct
@@ -425,9 +444,12 @@ mc_status build_field(mc_ctx* c, const mc_field_desc* f, int index, std::vector<
                                                    : split(-kHalf, kHalf, {jx0, jx1});
                 for (size_t a2 = 0; a2 + 1 < xs.size(); ++a2) {
                     const double x0 = xs[a2], x1 = xs[a2 + 1], xm = 0.5 * (x0 + x1);
-                    const double leaf = (has && xm >= lo && xm <= hi) ? 1.0 : T;
-                    const double jaw = (jaw_y && xm >= jx0 && xm <= jx1) ? 1.0 : Tj;
-                    add(x0, x1, y0, y1, mu * leaf * jaw);
+                    const bool in_leaf = has && xm >= lo && xm <= hi;
+                    const bool in_jaw = jaw_y && xm >= jx0 && xm <= jx1;
+                    const double leaf = in_leaf ? 1.0 : (slab ? (tl > 0.0 ? 1.0 : 0.0) : T);
+                    const double jaw = in_jaw ? 1.0 : (slab ? (tj > 0.0 ? 1.0 : 0.0) : Tj);
+                    const unsigned char flag = slab ? static_cast<unsigned char>((in_leaf ? 0 : 1) | (in_jaw ? 0 : 2)) : 0;
+                    add(x0, x1, y0, y1, mu * leaf * jaw, flag);
                 }
             }
         }
@@ -450,6 +472,8 @@ mc_status build_field(mc_ctx* c, const mc_field_desc* f, int index, std::vector<
     for (int k = 0; k < 3; ++k) out.iso[k] = f->iso_cm[k];
     out.sad = f->sad_cm;
     out.sid = f->sid_cm;
+    out.leaf_t = tl;
+    out.jaw_t = tj;
     out.zface = (out.sad - out.sid) + c->zp[0];
     // the vacuum transfer needs the whole CT above the detector face and below the source
     for (int corner = 0; corner < 8; ++corner) {
@@ -482,6 +506,8 @@ mc_status upload_fields(mc_ctx* c, const std::vector<uint64_t>& first, cudaStrea
         }
         d.sad = static_cast<float>(h.sad);
         d.zface = static_cast<float>(h.zface);
+        d.leaf_t = static_cast<float>(h.leaf_t);
+        d.jaw_t = static_cast<float>(h.jaw_t);
         d.rect_off = h.rect_off;
         d.n_rect = h.n_rect;
         d.hist_base = h.stream_base + h.hist_done;
@@ -636,9 +662,10 @@ mc_status set_fields_impl(mc_ctx* c, const mc_field_desc* f, int n, const mc_lut
     CUDA_TRY(c, cudaSetDevice(c->device));
     std::vector<float4> rect;
     std::vector<double> cdf;
+    std::vector<unsigned char> rflag;
     std::vector<FieldHost> fh(n);
     for (int i = 0; i < n; ++i) {
-        const mc_status st = build_field(c, &f[i], i, rect, cdf, fh[i]);
+        const mc_status st = build_field(c, &f[i], i, rect, cdf, rflag, fh[i]);
         if (st != MC_OK) return st;
     }
     const int np = npix(c);
@@ -649,7 +676,7 @@ mc_status set_fields_impl(mc_ctx* c, const mc_field_desc* f, int n, const mc_lut
     // the device.  A buffer that must grow is replaced, which needs the
     // previous run to have finished with it.
     const bool grow = tally_n > c->cap_tally || static_cast<size_t>(np) > c->cap_pix || parts > c->cap_parts ||
-                      rect.size() > c->cap_rect || cdf.size() > c->cap_cdf ||
+                      rect.size() > c->cap_rect || cdf.size() > c->cap_cdf || rflag.size() > c->cap_rflag ||
                       static_cast<size_t>(n) * np > c->cap_tmap || (lut && (static_cast<size_t>(lut->nt) > c->cap_lut_t ||
                                                                              nks > c->cap_ks));
     if (grow) {
@@ -676,10 +703,12 @@ mc_status set_fields_impl(mc_ctx* c, const mc_field_desc* f, int n, const mc_lut
     c->cap_parts = cq;
     CUDA_TRY(c, ensure(c->d_rect, c->cap_rect, rect.size()));
     CUDA_TRY(c, ensure(c->d_cdf, c->cap_cdf, cdf.size()));
+    CUDA_TRY(c, ensure(c->d_rflag, c->cap_rflag, rflag.size()));
     CUDA_TRY(c, ensure(c->d_tmap, c->cap_tmap, static_cast<size_t>(n) * np));
     // host data to the device through pinned staging, so the copies need no
     // wait here; the staging is reused once the previous copies out of it ended
-    const size_t stage_bytes = sizeof(float4) * rect.size() + sizeof(double) * (cdf.size() + nks + (lut ? lut->nt : 0));
+    const size_t stage_bytes = sizeof(float4) * rect.size() + sizeof(double) * (cdf.size() + nks + (lut ? lut->nt : 0)) +
+                               rflag.size();
     CUDA_TRY(c, cudaEventSynchronize(c->ev_stage));
     if (stage_bytes > c->h_stage_cap) {
         if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -693,8 +722,11 @@ mc_status set_fields_impl(mc_ctx* c, const mc_field_desc* f, int n, const mc_lut
     double* h_cdf = reinterpret_cast<double*>(stage + sizeof(float4) * rect.size());
     double* h_ks = h_cdf + cdf.size();
     double* h_lut_t = h_ks + nks;
+    unsigned char* h_rflag = reinterpret_cast<unsigned char*>(h_lut_t + (lut ? lut->nt : 0));
     std::memcpy(h_rect, rect.data(), sizeof(float4) * rect.size());
     std::memcpy(h_cdf, cdf.data(), sizeof(double) * cdf.size());
+    std::memcpy(h_rflag, rflag.data(), rflag.size());
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_rflag, h_rflag, rflag.size(), cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_rect, h_rect, sizeof(float4) * rect.size(), cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_cdf, h_cdf, sizeof(double) * cdf.size(), cudaMemcpyHostToDevice, s));
 

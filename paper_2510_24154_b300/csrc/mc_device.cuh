@@ -90,6 +90,7 @@ struct Ctl {
 struct FieldDev {
     float ex[3], ey[3], ez[3], iso[3];
     float sad, zface;
+    float leaf_t, jaw_t;            // collimator slab thicknesses (cm); 0 = ideal
     int rect_off, n_rect;
     unsigned long long hist_base;
     unsigned long long batch_base;
@@ -124,7 +125,10 @@ struct Params {
     // source: rectangles and cumulative weights of all fields, concatenated
     const float4* rect;
     const double* cdf;
+    const unsigned char* rflag;     // per rectangle: bit 0 behind a closed leaf, bit 1 outside the jaws (slabs)
     float e_max, mono_e;
+    MatC wmat;                      // tungsten of the collimator slabs (photon coefficients)
+    float w_edge;                   // its K edge, MeV
     // physics
     float pcut, ecut, tstop, wcc, wcb, ln_wcb, step_frac;
     int max_steps, coupled, nbatch;

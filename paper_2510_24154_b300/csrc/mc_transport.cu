@@ -19,6 +19,7 @@
 // Each kernel follows, draw for draw, the sampling order of the written model,
 // so a history fed the same Philox keys replays on another implementation.
 #include "mc_device.cuh"
+#include "physics_tables.h"
 
 namespace mc {
 
@@ -727,6 +728,53 @@ __device__ __forceinline__ void flush_emission(const Params& P, const Emit& e, c
 
 }  // namespace
 
+// Photon transport through a laterally infinite tungsten slab between the
+// beam-frame planes Z = zt and zb < zt (source at Z = SAD, beam along -Z):
+// flights against mu_W(E), Compton scattering (Klein-Nishina; the photon goes
+// on), photoelectric absorption and pair production absorbed in the
+// collimator (their electrons and annihilation photons stay in the head).
+// (x, y, z) starts on the top plane.  Returns true with the state on the
+// bottom plane if the photon leaves there; false if it is absorbed, falls
+// below the photon cutoff or leaves through the top.  The oracle's draws.
+constexpr float kJawTop = 28.0f;     // jaw slab top, cm from the source
+constexpr int kPs1Cap = 100000;      // source photons a history draws at most
+constexpr float kMlcTop = 51.0f;     // leaf slab top, cm from the source
+__device__ __forceinline__ bool slab_transport(const Params& P, Rng& r, float& x, float& y, float& z, float& u,
+                                               float& v, float& w, float& E, float zt, float zb, bool& collided) {
+    for (int f = 0; f < P.max_steps; ++f) {
+        const PhotonXS xs = photon_xs(P.ptab, P, E);
+        const float mc = P.wmat.ne * xs.skn;
+        const float mp = (E < P.w_edge ? P.wmat.pe_below : P.wmat.pe_above) * xs.epow;
+        const float mq = P.wmat.pair * xs.pair;
+        const float tot = mcphys::kWDensity * (mc + mp + mq);
+        r.align();
+        const float s = -logf(r.u()) / tot;
+        float d = INFINITY;
+        if (w < 0.0f) d = (zb - z) / w;
+        else if (w > 0.0f) d = (zt - z) / w;
+        if (!(s < d)) {
+            if (!(w < 0.0f)) return false;
+            x = fmaf(d, u, x);
+            y = fmaf(d, v, y);
+            z = zb;
+            return true;
+        }
+        x = fmaf(s, u, x);
+        y = fmaf(s, v, y);
+        z = fmaf(s, w, z);
+        const float xi = r.u();
+        if (!(xi * (mc + mp + mq) < mc)) return false;          // photoelectric or pair
+        float eps, ct, sp, cp;
+        sample_kn(r, E, eps, ct);
+        azimuth_sincos(r.u(), sp, cp);
+        rotate_dir(u, v, w, ct, cp, sp);
+        E *= eps;
+        collided = true;
+        if (E < P.pcut) return false;
+    }
+    return false;
+}
+
 // Samples the primary of batch history `k` into p (patient frame, at the CT
 // entry point) and returns whether it enters the CT; otherwise `move` tells
 // whether it reached the EPID face.  The field is the one whose history range
@@ -750,22 +798,44 @@ __device__ __forceinline__ bool start_primary(const Params& P, unsigned long lon
     p.tau = 0.0f;
     p.flags = static_cast<uint32_t>(f) << kFieldShift;
     p.rng.setup(P.seed, F.hist_base + idx, 0u, 0u);
-    const double xi = static_cast<double>(p.rng.u());
-    int lo = 0, hi = F.n_rect - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (xi < __ldg(&P.cdf[F.rect_off + mid])) hi = mid; else lo = mid + 1;
+    // phase space 2: photons of the source until one leaves the collimator
+    // slabs its rectangle's flags name (none without slabs: the first one)
+    float bx = 0.0f, by = 0.0f, bz = F.sad, bu = 0.0f, bv = 0.0f, bw = -1.0f;
+    bool got = false, scattered = false;
+    for (int k = 0; k < kPs1Cap && !got; ++k) {
+        const double xi = static_cast<double>(p.rng.u());
+        int lo = 0, hi = F.n_rect - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (xi < __ldg(&P.cdf[F.rect_off + mid])) hi = mid; else lo = mid + 1;
+        }
+        const float4 r = __ldg(&P.rect[F.rect_off + lo]);
+        const float X = r.x + (r.y - r.x) * p.rng.u();
+        const float Y = r.z + (r.w - r.z) * p.rng.u();
+        p.E = (P.mono_e > 0.0f) ? P.mono_e : sample_spectrum(p.rng, P.e_max, P.pcut);
+        const unsigned flag = (F.leaf_t > 0.0f || F.jaw_t > 0.0f) ? __ldg(&P.rflag[F.rect_off + lo]) : 0u;
+        const float nb = sqrtf(X * X + Y * Y + F.sad * F.sad);
+        bx = 0.0f; by = 0.0f; bz = F.sad;
+        bu = X / nb; bv = Y / nb; bw = -F.sad / nb;
+        scattered = false;
+        got = true;
+        if (flag & 2u) {
+            const float zt = F.sad - kJawTop, t = (zt - bz) / bw;
+            bx = fmaf(t, bu, bx); by = fmaf(t, bv, by); bz = zt;
+            got = slab_transport(P, p.rng, bx, by, bz, bu, bv, bw, p.E, zt, zt - F.jaw_t, scattered);
+        }
+        if (got && (flag & 1u)) {
+            const float zt = F.sad - kMlcTop, t = (zt - bz) / bw;
+            bx = fmaf(t, bu, bx); by = fmaf(t, bv, by); bz = zt;
+            got = slab_transport(P, p.rng, bx, by, bz, bu, bv, bw, p.E, zt, zt - F.leaf_t, scattered);
+        }
     }
-    const float4 r = __ldg(&P.rect[F.rect_off + lo]);
-    const float X = r.x + (r.y - r.x) * p.rng.u();
-    const float Y = r.z + (r.w - r.z) * p.rng.u();
-    p.E = (P.mono_e > 0.0f) ? P.mono_e : sample_spectrum(p.rng, P.e_max, P.pcut);
+    if (!got) { move = false; return false; }       // every source photon stayed in the collimators
+    if (scattered) p.flags |= kCollided;
     a.src += quanta(p.E);
-    const float nb = sqrtf(X * X + Y * Y + F.sad * F.sad);
-    const float bu = X / nb, bv = Y / nb, bw = -F.sad / nb;
-    p.x = F.iso[0] + F.sad * F.ez[0];
-    p.y = F.iso[1] + F.sad * F.ez[1];
-    p.z = F.iso[2] + F.sad * F.ez[2];
+    p.x = F.iso[0] + bx * F.ex[0] + by * F.ey[0] + bz * F.ez[0];
+    p.y = F.iso[1] + bx * F.ex[1] + by * F.ey[1] + bz * F.ez[1];
+    p.z = F.iso[2] + bx * F.ex[2] + by * F.ey[2] + bz * F.ez[2];
     p.u = bu * F.ex[0] + bv * F.ey[0] + bw * F.ez[0];
     p.v = bu * F.ex[1] + bv * F.ey[1] + bw * F.ez[1];
     p.w = bu * F.ex[2] + bv * F.ey[2] + bw * F.ez[2];

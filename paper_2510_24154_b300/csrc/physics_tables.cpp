@@ -73,6 +73,18 @@ MaterialCoefs material_coefs(int m) {
     return r;
 }
 
+MaterialCoefs tungsten_coefs() {
+    const double Z = 74.0, per_mol = 1.0 / 183.84;
+    MaterialCoefs r{};
+    r.zA = per_mol * Z;
+    r.I_MeV = 727e-6;
+    r.ne_barn = kAvogadro * r.zA * 1e-24;
+    r.pe_above = kAvogadro * kPeCoef * per_mol * std::pow(Z, kPeZ);
+    r.pe_below = r.pe_above / kWKJump;
+    r.pair = kAvogadro * kPairCoef * per_mol * Z * (Z + 1.0);
+    return r;
+}
+
 double klein_nishina_barn(double E) {
     // 2 pi re^2 { (1+k)/k^2 [2(1+k)/(1+2k) - ln(1+2k)/k] + ln(1+2k)/(2k) - (1+3k)/(1+2k)^2 }
     const double k = E / kMec2, q = 1.0 + 2.0 * k, lq = std::log(q);

@@ -38,6 +38,13 @@ struct MaterialCoefs {
 
 MaterialCoefs material_coefs(int m);
 
+// Tungsten of the collimator slabs (photons only): Z 74, A 183.84, K edge at
+// 69.525 keV with jump ratio 4.6; pe_above / pe_below straddle that edge.
+constexpr double kWKEdge = 0.069525;   // MeV
+constexpr double kWKJump = 4.6;
+constexpr double kWDensity = 19.3;     // g/cm^3
+MaterialCoefs tungsten_coefs();
+
 // Closed forms used to fill the tables.
 double klein_nishina_barn(double E);
 double pair_shape(double E);

@@ -72,6 +72,11 @@ class Field:
                 intersection of both pairs' openings.
     leaf_gap:   dosimetric leaf gap (cm): an open pair's effective opening
                 is wider by this much (rounded leaf ends).
+    leaf_thickness, jaw_thickness: tungsten slab thickness along the beam
+                (cm) of the leaves (top 51 cm from the source) and of the
+                jaws (top 28 cm); either > 0 transports the source photons
+                through the collimators (phase space 2 of Sec. 2.1.1) in
+                place of the transmission factors, which must then be 0.
     """
     pair_edges: np.ndarray
     leaves: np.ndarray
@@ -85,6 +90,8 @@ class Field:
     jaw_transmission: float = 0.0
     tg_width: float = 0.0
     leaf_gap: float = 0.0
+    leaf_thickness: float = 0.0
+    jaw_thickness: float = 0.0
 
 
 @dataclass

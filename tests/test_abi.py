@@ -82,14 +82,16 @@ def test_struct_layouts_match_c(tmp_path):
                  offsetof(mc_field_desc, eq1_literal), offsetof(mc_field_desc, leaf_transmission),
                  offsetof(mc_field_desc, leaf_gap_cm), offsetof(mc_run_stats, gpu_ms),
                  offsetof(mc_run_stats, launches));
+          printf("%zu %zu\\n", offsetof(mc_field_desc, leaf_thickness_cm), offsetof(mc_field_desc, jaw_thickness_cm));
           return 0;
         }""")
     src = tmp_path / "probe.c"
     src.write_text(probe)
     exe = tmp_path / "probe"
     subprocess.run(["gcc", f"-I{ROOT / 'include'}", str(src), "-o", str(exe)], check=True)
-    sizes, offs = [list(map(int, l.split())) for l in
-                   subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()]
+    sizes, offs, slabs = [list(map(int, l.split())) for l in
+                          subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()]
+    assert slabs == [binding.FieldDesc.leaf_thickness_cm.offset, binding.FieldDesc.jaw_thickness_cm.offset]
     assert sizes == [C.sizeof(binding.Config), C.sizeof(binding.EpidDesc), C.sizeof(binding.FieldDesc),
                      C.sizeof(binding.LutDesc), C.sizeof(binding.RunStats), C.sizeof(binding.AluPeaks),
                      binding.AluPeaks.sm_count.offset]

@@ -1097,3 +1097,108 @@ def test_woodcock_enumeration_for_any_macro_cell_size(M):
         chi2 += (rest_o - rest_e) ** 2 / rest_e
         dof += 1
     assert stats.chi2.sf(chi2, dof) > 1e-3
+
+
+# ------------------------------------------- collimator slabs (PS1 -> PS2) ---
+
+def _slab_field(opening, jaws=(-20.0, 20.0, -20.0, 20.0), leaf_t=0.0, jaw_t=0.0):
+    """One segment of the default leaf layout: every pair closed except those
+    inside `opening` (x0, x1, y0, y1), which open to [x0, x1]."""
+    x0, x1, y0, y1 = opening
+    edges = W.millennium_pair_edges()
+    npairs = edges.size - 1
+    leaves = np.zeros((1, npairs, 2))
+    for j in range(npairs):
+        if edges[j] >= y0 and edges[j + 1] <= y1:
+            leaves[0, j] = (x0, x1)
+    return W.Field(pair_edges=edges, leaves=leaves, jaws=np.array([jaws], dtype=float), mu=np.array([1.0]),
+                   leaf_thickness=leaf_t, jaw_thickness=jaw_t)
+
+
+def _oblique_mean(mu_t, region, sad=100.0, n=801):
+    """(1/A) integral over the isocentre-plane rectangle `region` of
+    exp(-mu_t / cos theta), theta the angle of the source ray (midpoint rule,
+    error far below the 0.5 % bars)."""
+    x0, x1, y0, y1 = region
+    xs = x0 + (np.arange(n) + 0.5) * (x1 - x0) / n
+    ys = y0 + (np.arange(n) + 0.5) * (y1 - y0) / n
+    X, Y = np.meshgrid(xs, ys)
+    inv_cos = np.sqrt(X ** 2 + Y ** 2 + sad ** 2) / sad
+    return float(np.exp(-mu_t * inv_cos).mean()), (x1 - x0) * (y1 - y0)
+
+
+@pytest.mark.parametrize("E", [1.0, 4.0])
+def test_leaf_slab_uncollided_transmission(E):
+    """Source photons over the whole 40 x 40 cm field, every leaf closed but
+    those of a 4 x 4 cm opening, 1 cm tungsten leaves: per source photon drawn,
+    the fraction leaving the leaves unscattered from behind them equals
+    (1/A) int exp(-mu_W(E) t / cos theta) dA over the blocked area within
+    0.5 % (the obliquity is 1-4 % of the path), and the fraction from the
+    opening equals its area share.  Pins the slab's attenuation, its path
+    length and the PS1 -> PS2 rejection loop."""
+    fld = _slab_field((-2.0, 2.0, -2.0, 2.0), leaf_t=1.0)
+    prob = W.config_water_open(n_histories=1)
+    prob.field = fld
+    phys = W.Physics(coupled=False, mono_energy=E)
+    n = 400_000
+    X, Y, En, coll, k = oracle.sample_ps2(prob, n, seed=41, physics=phys)
+    assert np.isfinite(En).all()
+    K = k.sum()
+    inside = (np.abs(X) < 2.0) & (np.abs(Y) < 2.0)
+    mu_t = O_W_RHO * _mu(7, E).sum() * 1.0
+    full, A = _oblique_mean(mu_t, (-20, 20, -20, 20))
+    hole, a = _oblique_mean(mu_t, (-2, 2, -2, 2))
+    want_closed = (full * A - hole * a) / A
+    got_closed = ((~inside) & (~coll)).sum() / K
+    sd = math.sqrt(want_closed * (1 - want_closed) / K)
+    assert 0.005 * want_closed >= 3 * sd
+    assert abs(got_closed / want_closed - 1) < 0.005, (got_closed, want_closed)
+    assert inside.sum() / K == pytest.approx(a / A, abs=4 * math.sqrt(a / A / K))
+    assert not coll[inside].any()                    # the opening crosses no slab
+    assert np.all(En[coll] < E) and np.all(En[~coll] == E)
+
+
+def test_jaw_slab_uncollided_transmission():
+    """The same with the leaves open over the whole field and 2 cm tungsten
+    jaws closed to 10 x 10 cm: the fraction leaving the jaws unscattered from
+    outside them is (1/A) int exp(-mu_W t_jaw / cos theta) dA there."""
+    E = 2.0
+    fld = _slab_field((-20.0, 20.0, -20.0, 20.0), jaws=(-5.0, 5.0, -5.0, 5.0), jaw_t=2.0)
+    prob = W.config_water_open(n_histories=1)
+    prob.field = fld
+    n = 700_000
+    X, Y, En, coll, k = oracle.sample_ps2(prob, n, seed=43, physics=W.Physics(coupled=False, mono_energy=E))
+    K = k.sum()
+    inside = (np.abs(X) < 5.0) & (np.abs(Y) < 5.0)
+    mu_t = O_W_RHO * _mu(7, E).sum() * 2.0
+    full, A = _oblique_mean(mu_t, (-20, 20, -20, 20))
+    hole, a = _oblique_mean(mu_t, (-5, 5, -5, 5))
+    want = (full * A - hole * a) / A
+    got = ((~inside) & (~coll)).sum() / K
+    assert 0.005 * want >= 3 * math.sqrt(want * (1 - want) / K)
+    assert abs(got / want - 1) < 0.005, (got, want)
+
+
+def test_leaf_slab_hardens_the_spectrum():
+    """6 MV spectrum through 3 cm tungsten leaves: unscattered photons from
+    behind the leaves near the axis (cos theta >= 0.9996) follow
+    f(E) exp(-mu_W(E) t) normalised, f the Beta(3/2, 7/2) spectrum (KS), and
+    their mean energy exceeds the open beam's."""
+    fld = _slab_field((-2.0, 2.0, -20.0, -16.0), leaf_t=3.0)
+    prob = W.config_water_open(n_histories=1)
+    prob.field = fld
+    n = 250_000
+    X, Y, En, coll, k = oracle.sample_ps2(prob, n, seed=47, physics=W.Physics(coupled=False))
+    sel = (~coll) & (np.abs(X) < 2.0) & (np.abs(Y) < 2.0)
+    assert sel.sum() > 500
+    t = 3.0
+    pdf = lambda e: (e / 6.0) ** 0.5 * (1 - e / 6.0) ** 2.5 * math.exp(-O_W_RHO * _mu(7, e).sum() * t)
+    grid = np.linspace(0.01, 6.0, 1200)
+    dens = np.array([pdf(e) for e in grid])
+    cdf = np.concatenate([[0.0], np.cumsum(0.5 * (dens[1:] + dens[:-1]) * np.diff(grid))])
+    cdf /= cdf[-1]
+    assert stats.kstest(En[sel], lambda e: np.interp(e, grid, cdf)).pvalue > 1e-3
+    assert En[sel].mean() > 1.8 + 0.5
+
+
+O_W_RHO = 19.3
