@@ -48,6 +48,7 @@ typedef struct dn_config {
     int batch;                /* images per step */
     int levels;               /* U-Net levels, 2..5 (4) */
     int base_channels;        /* channels of level 0: 32 (a multiple of 32; 32 * 2^(levels-1) <= 256) */
+    int in_channels;          /* input planes, 1..8 (1): the noisy image, then auxiliary maps */
     uint64_t seed;            /* He-normal initialisation of the weights (biases 0) */
 } dn_config;
 
@@ -68,14 +69,16 @@ mc_status dn_get_params(dn_ctx* ctx, float* params, size_t n);
 /* Gradient of the loss of the last dn_train_step, before its update. */
 mc_status dn_get_grads(dn_ctx* ctx, float* grads, size_t n);
 
-/* Inference: input and output are device float32 [batch][height][width];
- * the network sees input * in_scale (rounded to bfloat16) and the output is
- * the network's bfloat16 output * out_scale. */
+/* Inference: input is device float32 [batch][in_channels][height][width]
+ * (plane 0 the noisy image, planes 1.. auxiliary maps), output device float32
+ * [batch][height][width].  The network sees plane 0 * in_scale and the other
+ * planes as given, each rounded to bfloat16; the output is the network's
+ * bfloat16 output * out_scale. */
 mc_status dn_forward(dn_ctx* ctx, const float* input, float in_scale, float* output, float out_scale,
                      void* stream);
 
-/* One optimisation step on a batch: forward, MSE loss against
- * target * in_scale, backward, Adam with learning rate lr.  loss (host, may be
+/* One optimisation step on a batch: input as for dn_forward, target device
+ * float32 [batch][height][width]; forward, MSE loss against target * in_scale, backward, Adam with learning rate lr.  loss (host, may be
  * NULL) receives the batch loss; it synchronizes the stream when given. */
 mc_status dn_train_step(dn_ctx* ctx, const float* input, const float* target, float in_scale, float lr,
                         double* loss, void* stream);

@@ -289,7 +289,7 @@ struct ConvLayer {
     std::string name;
     int Co = 0, k = 3, ci_total = 0, nsrc = 1, relu = 1;
     int srcC[2] = {0, 0};      // channels stored per source
-    int realC[2] = {0, 0};     // channels with weights (the network input stores 1 in 8)
+    int realC[2] = {0, 0};     // channels with weights (the network input stores in_channels of 8)
     size_t w_off = 0, b_off = 0;
     Buf* in[2] = {nullptr, nullptr};
     Buf* out = nullptr;
@@ -542,10 +542,10 @@ mc_status build(dn_ctx* c) {
     add("out", 1, 1, 1, c->D1[0], nullptr, c->Y, c->gD1[0], nullptr, c->dY, 0);
 
     // parameter offsets (weights [Co][k][k][Ci] then biases); the network input
-    // has one real channel of the 8 stored
+    // has in_channels real channels of the 8 stored
     size_t off = 0;
     for (ConvLayer& ly : c->layers) {
-        for (int q = 0; q < ly.nsrc; ++q) ly.realC[q] = (ly.in[q] == c->X) ? 1 : ly.srcC[q];
+        for (int q = 0; q < ly.nsrc; ++q) ly.realC[q] = (ly.in[q] == c->X) ? c->cfg.in_channels : ly.srcC[q];
         ly.ci_total = ly.realC[0] + ly.realC[1];
         ly.w_off = off;
         off += static_cast<size_t>(ly.Co) * ly.k * ly.k * ly.ci_total;
@@ -615,10 +615,10 @@ mc_status build(dn_ctx* c) {
                         c->d_grads + ly.w_off, c->d_err, c->sm_count))
             return fail(c, MC_ERR_CUDA, "tensor map encoding failed (" + ly.name + " wgrad)");
         // the network input's gradient operand spans the 8 stored channels but
-        // only channel 0 has a weight: restrict the weight gradient to it
+        // only the first in_channels have weights: restrict the weight gradient to them
         if (ly.in[0] == c->X) {
-            ly.wg.a.src_C[0] = 1;
-            ly.wg.a.ci_total = 1;
+            ly.wg.a.src_C[0] = c->cfg.in_channels;
+            ly.wg.a.ci_total = c->cfg.in_channels;
         }
     }
     return MC_OK;
@@ -648,6 +648,7 @@ void dn_config_default(dn_config* cfg) {
     cfg->batch = 1;
     cfg->levels = 4;
     cfg->base_channels = 32;
+    cfg->in_channels = 1;
     cfg->seed = 1;
 }
 
@@ -659,7 +660,7 @@ mc_status dn_create(const dn_config* cfg_in, int device, dn_ctx** out) {
     dn_config cfg;
     if (cfg_in) cfg = *cfg_in; else dn_config_default(&cfg);
     if (cfg.levels < 2 || cfg.levels > 5 || cfg.batch < 1 || cfg.base_channels < 32 || cfg.base_channels % 32 != 0 ||
-        (cfg.base_channels << (cfg.levels - 1)) > 256)
+        (cfg.base_channels << (cfg.levels - 1)) > 256 || cfg.in_channels < 1 || cfg.in_channels > 8)
         return MC_ERR_ARG;
     const int m = 1 << (cfg.levels - 1);
     if (cfg.height < m || cfg.width < m || cfg.height % m != 0 || cfg.width % m != 0 || cfg.height > 16384 ||
@@ -733,8 +734,8 @@ mc_status dn_forward(dn_ctx* c, const float* input, float in_scale, float* outpu
     if (!input || !output) return fail(c, MC_ERR_ARG, "null pointer");
     DN_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const long long npx = static_cast<long long>(c->X->Nb) * c->X->H * c->X->W;
-    DN_TRY(c, dn::launch_prep(input, in_scale, npx, c->X->p, c->X->C, s));
+    const long long hw = static_cast<long long>(c->X->H) * c->X->W, npx = c->X->Nb * hw;
+    DN_TRY(c, dn::launch_prep(input, c->cfg.in_channels, hw, in_scale, npx, c->X->p, c->X->C, s));
     mc_status st = run_forward(c, s);
     if (st != MC_OK) return st;
     DN_TRY(c, dn::launch_to_f32(c->Y->p, c->Y->C, npx, out_scale, output, s));
@@ -756,9 +757,9 @@ mc_status dn_train_step(dn_ctx* c, const float* input, const float* target, floa
     if (!(lr >= 0.0f)) return fail(c, MC_ERR_ARG, "learning rate must be >= 0");
     DN_TRY(c, cudaSetDevice(c->device));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const long long npx = static_cast<long long>(c->X->Nb) * c->X->H * c->X->W;
-    DN_TRY(c, dn::launch_prep(input, in_scale, npx, c->X->p, c->X->C, s));
-    DN_TRY(c, dn::launch_prep(target, in_scale, npx, c->T->p, 1, s));
+    const long long hw = static_cast<long long>(c->X->H) * c->X->W, npx = c->X->Nb * hw;
+    DN_TRY(c, dn::launch_prep(input, c->cfg.in_channels, hw, in_scale, npx, c->X->p, c->X->C, s));
+    DN_TRY(c, dn::launch_prep(target, 1, hw, in_scale, npx, c->T->p, 1, s));
     mc_status st = run_forward(c, s);
     if (st != MC_OK) return st;
     st = run_backward(c, s);

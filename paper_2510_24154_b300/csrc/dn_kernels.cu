@@ -1154,12 +1154,16 @@ __global__ void k_pack_dgrad(const float* __restrict__ w, int Co, int k, int ci_
     }
 }
 
-__global__ void k_prep(const float* __restrict__ img, float scale, long long npix, __nv_bfloat16* __restrict__ out,
-                       int out_C) {
+__global__ void k_prep(const float* __restrict__ img, int planes, long long hw, float scale, long long npix,
+                       __nv_bfloat16* __restrict__ out, int out_C) {
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < npix;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        out[i * out_C] = __float2bfloat16_rn(img[i] * scale);
-        for (int c = 1; c < out_C; ++c) out[i * out_C + c] = __float2bfloat16_rn(0.0f);
+        const long long n = i / hw, p = i - n * hw;
+        const float* src = img + n * planes * hw + p;
+        for (int c = 0; c < out_C; ++c) {
+            const float v = c < planes ? src[c * hw] * (c == 0 ? scale : 1.0f) : 0.0f;
+            out[i * out_C + c] = __float2bfloat16_rn(v);
+        }
     }
 }
 
@@ -1301,9 +1305,9 @@ cudaError_t launch_pack_dxn(const float* w, int Co, int ci_total, int coff, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep(const float* img, float scale, long long npix, __nv_bfloat16* out, int out_C,
-                        cudaStream_t s) {
-    k_prep<<<blocks_for(npix), kThreads, 0, s>>>(img, scale, npix, out, out_C);
+cudaError_t launch_prep(const float* img, int planes, long long hw, float scale, long long npix,
+                        __nv_bfloat16* out, int out_C, cudaStream_t s) {
+    k_prep<<<blocks_for(npix), kThreads, 0, s>>>(img, planes, hw, scale, npix, out, out_C);
     return cudaGetLastError();
 }
 

@@ -109,8 +109,10 @@ cudaError_t launch_pack_dgrad(const float* w, int Co, int k, int ci_total, int r
 // Column-taps-in-N operand [(dx, o)][(dy, chunk, c)], o < Nout (3 * Nout rows).
 cudaError_t launch_pack_dxn(const float* w, int Co, int ci_total, int coff, int C, int CW, int nch, int dgrad,
                             int Nout, __nv_bfloat16* out, cudaStream_t s);
-cudaError_t launch_prep(const float* img, float scale, long long npix, __nv_bfloat16* out, int out_C,
-                        cudaStream_t s);
+// Planar float32 [image][planes][hw] -> NHWC bf16 with out_C stored channels
+// (channels >= planes zero); plane 0 is multiplied by scale.
+cudaError_t launch_prep(const float* img, int planes, long long hw, float scale, long long npix,
+                        __nv_bfloat16* out, int out_C, cudaStream_t s);
 cudaError_t launch_to_f32(const __nv_bfloat16* x, int stride, long long npix, float scale, float* out,
                           cudaStream_t s);
 

@@ -21,7 +21,7 @@ EXPORTED = ("dn_config_default", "dn_create", "dn_destroy", "dn_last_error", "dn
 
 class DnConfig(C.Structure):
     _fields_ = [("height", C.c_int), ("width", C.c_int), ("batch", C.c_int), ("levels", C.c_int),
-                ("base_channels", C.c_int), ("seed", C.c_uint64)]
+                ("base_channels", C.c_int), ("in_channels", C.c_int), ("seed", C.c_uint64)]
 
 
 _lib = None
@@ -78,13 +78,16 @@ def _check(st, what=""):
 class UNet:
     """The denoiser on one GPU: parameters, activations, gradients, Adam state."""
 
-    def __init__(self, height=768, width=1024, batch=1, levels=4, base_channels=32, seed=1, device=0):
+    def __init__(self, height=768, width=1024, batch=1, levels=4, base_channels=32, seed=1, device=0,
+                 in_channels=1):
         self.lib = lib()
-        cfg = DnConfig(height, width, batch, levels, base_channels, seed)
+        cfg = DnConfig(height=height, width=width, batch=batch, levels=levels, base_channels=base_channels,
+                       in_channels=in_channels, seed=seed)
         h = C.c_void_p()
         _check(self.lib.dn_create(C.byref(cfg), device, C.byref(h)), "dn_create")
         self.h = h
         self.shape = (batch, height, width)
+        self.in_channels = in_channels
         n = C.c_size_t()
         self._ck(self.lib.dn_param_count(self.h, C.byref(n)))
         self.n_params = n.value
@@ -120,7 +123,8 @@ class UNet:
         return a
 
     def forward(self, x, out, in_scale=1.0, out_scale=1.0, stream=None):
-        """x, out: CUDA float32 tensors [batch][H][W]."""
+        """x: CUDA float32 [batch][H][W] (one input plane) or [batch][in_channels][H][W];
+        out: CUDA float32 [batch][H][W]."""
         self._ck(self.lib.dn_forward(self.h, _p(x), float(in_scale), _p(out), float(out_scale), _s(stream)))
 
     def train_step(self, x, target, lr, in_scale=1.0, stream=None, want_loss=True):

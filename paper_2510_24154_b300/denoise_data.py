@@ -9,6 +9,13 @@ n_target independent histories (target; history ids from 2^40 on).  Both
 images are divided by the input's mean over the image, so the network works
 on O(1) values and the scale is known at inference.
 
+With aux planes the network is also given what the noisy image cannot tell
+it: the MLC/jaw aperture fluence of the field projected onto the EPID (where
+the field edges are), the radiological thickness t of the CT along each
+pixel's ray (the t-map of Sec. 3.1) and their product, the uncollided primary
+estimate F exp(-mu t).  F and the primary estimate are divided by their image
+means, t by 40 g/cm^2.
+
 Evaluation: the denoised low-count image and the raw one are compared with a
 high-count reference by the global gamma index (2 %, 2 mm, 10 % threshold) on
 the image binned b x b (b = 8 gives 3.1 mm pixels, near the paper's 2.5 mm).
@@ -26,22 +33,103 @@ from .binding import Simulator, gamma
 from .denoise import UNet
 
 TARGET_BASE = 1 << 40
+AUX_PLANES = 3            # aperture fluence, t-map, primary estimate
+MU_PRIMARY = 0.05         # cm^2/g: water near the 6 MV spectrum's mean energy
 
 
-def case_problem(case: int, seed: int = 3, per_phantom: int = 8, phantom_cache: dict | None = None):
-    """Problem of case `case` of the data set with generator seed `seed`."""
+FAMILIES = ("thorax", "anthropomorphic")
+CONFIG5_CASE = -1         # the anthropomorphic workload itself: phantom seed 4, one 40-segment field
+
+
+def family_epid(family: str):
+    """The EPID grid of a case family."""
+    return W.epid_default(1024, 768, 0.039) if family == "thorax" else W.epid_default(1190, 1190, 0.0336)
+
+
+def case_problem(case: int, seed: int = 3, per_phantom: int = 8, phantom_cache: dict | None = None,
+                 family: str = "thorax"):
+    """Problem of case `case` of the data set with generator seed `seed`.
+
+    thorax: the 256x256x128 thorax CT at 2 mm with sizes and positions
+    jittered by up to 20 %, one IMRT field of 5-40 segments at a random gantry
+    angle, EPID 1024 x 768 at 0.39 mm.  anthropomorphic: the 512x512x200 CT at
+    1 mm jittered the same way, EPID 1190 x 1190 at 0.336 mm; case
+    CONFIG5_CASE is the unjittered phantom with its 40-segment field."""
+    if family not in FAMILIES:
+        raise ValueError(f"family must be one of {FAMILIES}")
+    if family == "anthropomorphic" and case == CONFIG5_CASE:
+        prob = W.config_anthropomorphic(n_histories=0, seed=4)
+        prob.seed = seed
+        return prob
     pid = case // per_phantom
     if phantom_cache is not None and pid in phantom_cache:
         ph = phantom_cache[pid]
     else:
-        ph = W.thorax_ct(np.random.default_rng([seed, 7919, pid]), jitter=0.2)
+        prng = np.random.default_rng([seed, 7919, pid])
+        ph = W.thorax_ct(prng, jitter=0.2) if family == "thorax" else W.anthropomorphic_ct(prng, jitter=0.2)
         if phantom_cache is not None:
             phantom_cache.clear()
             phantom_cache[pid] = ph
     rng = np.random.default_rng([seed, case])
     fld = W.imrt_field(rng, int(rng.integers(5, 41)), float(rng.uniform(0.0, 360.0)))
-    return W.Problem(name=f"denoise_case_{case}", phantom=ph, epid=W.epid_default(1024, 768, 0.039), field=fld,
+    return W.Problem(name=f"denoise_{family}_{case}", phantom=ph, epid=family_epid(family), field=fld,
                      lut=W.lut_bilinear(), physics=W.Physics(coupled=True), n_histories=0, seed=seed)
+
+
+def net_shape(epid, levels=4):
+    """Network image size: the EPID grid rounded up to a multiple of
+    2^(levels - 1) (the pooling steps); the margin is zero padding."""
+    m = 1 << (levels - 1)
+    return -(-epid.npy // m) * m, -(-epid.npx // m) * m
+
+
+def _pad(a, shape):
+    """Zero-pads the last two dimensions of a CUDA tensor at the high end."""
+    import torch.nn.functional as Fn
+    return Fn.pad(a, (0, shape[1] - a.shape[-1], 0, shape[0] - a.shape[-2]))
+
+
+def aperture_fluence(field, epid) -> np.ndarray:
+    """MU-weighted aperture of a field on the EPID pixel grid, [npy][npx].
+
+    Pixel (ix, iy) has beam-frame centre (-npx p / 2 + (ix + 1/2) p,
+    -npy p / 2 + (iy + 1/2) p) on the plane at SID; scaled by SAD / SID it
+    falls on the isocentre plane where leaves and jaws are given.  Per
+    segment the value is MU x (leaf factor) x (jaw factor): 1 inside the
+    effective opening (leaf tips apart by the leaf gap; jaws), the leaf or
+    jaw transmission outside.  Tongue-and-groove strips are not drawn."""
+    mag = field.sad / field.sid
+    p = epid.pitch
+    x = (-0.5 * epid.npx * p + (np.arange(epid.npx) + 0.5) * p) * mag
+    y = (-0.5 * epid.npy * p + (np.arange(epid.npy) + 0.5) * p) * mag
+    edges = np.asarray(field.pair_edges, dtype=np.float64)
+    n_pairs = edges.size - 1
+    j = np.searchsorted(edges, y, side="right") - 1
+    in_pair = (j >= 0) & (j < n_pairs)
+    jc = np.clip(j, 0, n_pairs - 1)
+    T, Tj, gap = field.leaf_transmission, field.jaw_transmission, field.leaf_gap
+    F = np.zeros((epid.npy, epid.npx))
+    for k, mu in enumerate(np.asarray(field.mu, dtype=np.float64)):
+        if not mu > 0:
+            continue
+        jx0, jx1, jy0, jy1 = np.asarray(field.jaws[k], dtype=np.float64)
+        jx0, jx1, jy0, jy1 = max(jx0, -20.0), min(jx1, 20.0), max(jy0, -20.0), min(jy1, 20.0)
+        jaw = np.where(((y >= jy0) & (y < jy1))[:, None] & ((x >= jx0) & (x < jx1))[None, :], 1.0, Tj)
+        lv = np.asarray(field.leaves[k], dtype=np.float64)[jc]
+        open_ = in_pair & (lv[:, 1] > lv[:, 0])
+        lo, hi = lv[:, 0] - 0.5 * gap, lv[:, 1] + 0.5 * gap
+        leaf = np.where(open_[:, None] & (x[None, :] >= lo[:, None]) & (x[None, :] < hi[:, None]), 1.0, T)
+        F += mu * leaf * jaw
+    return F
+
+
+def aux_planes(field, epid, tmap):
+    """The auxiliary input planes [AUX_PLANES][npy][npx] (float64 numpy) of a
+    field, given its t-map (g/cm^2)."""
+    F = aperture_fluence(field, epid)
+    P = F * np.exp(-MU_PRIMARY * tmap)
+    nz = lambda a: a / max(float(a.mean()), 1e-300)
+    return np.stack([nz(F), tmap / 40.0, nz(P)])
 
 
 class DoseSource:
@@ -78,23 +166,45 @@ class DoseSource:
         self.sim.dose_device(d)
         return d
 
+    def aux(self, prob):
+        """Auxiliary planes of the field last set (call after image())."""
+        return aux_planes(prob.field, prob.epid, self.sim.tmap())
+
     def close(self):
         self.sim.close()
 
 
-def make_pairs(src: DoseSource, cases, n_input, n_target, seed=3):
-    """Stacked float32 CUDA tensors X, T [len(cases)][768][1024] and the
+def input_planes(src: DoseSource, prob, d_in, aux: bool, shape=None):
+    """Network input of one case: the normalised noisy image [H][W], with aux
+    the planes [1 + AUX_PLANES][H][W] (float32 CUDA, zero-padded to `shape`),
+    and the scale s (dose = image / s)."""
+    torch = src.torch
+    s = 1.0 / max(float(d_in.mean()), 1e-300)
+    x = (d_in * s).float()
+    if aux:
+        a = torch.tensor(src.aux(prob), dtype=torch.float32, device=x.device)
+        x = torch.cat([x[None], a])
+    if shape is not None:
+        x = _pad(x, shape)
+    return x.contiguous(), s
+
+
+def make_pairs(src: DoseSource, cases, n_input, n_target, seed=3, aux=False, family="thorax"):
+    """Stacked float32 CUDA tensors X [len(cases)][H][W] (with aux
+    [len(cases)][1 + AUX_PLANES][H][W]) and T [len(cases)][H][W] at the
+    network size of the family's EPID (768 x 1024 for the thorax), and the
     per-case scales (dose = image / scale)."""
     torch = src.torch
     xs, ts, scales = [], [], []
     cache = {}
     for c in cases:
-        prob = case_problem(c, seed, phantom_cache=cache)
+        prob = case_problem(c, seed, phantom_cache=cache, family=family)
+        shape = net_shape(prob.epid)
         d_in = src.image(prob, n_input, 0, seed)
+        x, s = input_planes(src, prob, d_in, aux, shape)
         d_tg = src.image(prob, n_target, TARGET_BASE, seed)
-        s = 1.0 / max(float(d_in.mean()), 1e-300)
-        xs.append((d_in * s).float())
-        ts.append((d_tg * s).float())
+        xs.append(x)
+        ts.append(_pad((d_tg * s).float(), shape))
         scales.append(s)
     return torch.stack(xs), torch.stack(ts), np.array(scales)
 
@@ -115,7 +225,7 @@ def train(net: UNet, X, T, steps, lr, batch, seed=0, log_every=0, lr_final=None,
         xb = X.index_select(0, idx)
         tb = T.index_select(0, idx)
         if augment:
-            dims = [d for d, f in ((1, rng.random() < 0.5), (2, rng.random() < 0.5)) if f]
+            dims = [d for d, f in ((-2, rng.random() < 0.5), (-1, rng.random() < 0.5)) if f]
             if dims:
                 xb, tb = torch.flip(xb, dims), torch.flip(tb, dims)
         xb, tb = xb.contiguous(), tb.contiguous()
@@ -132,8 +242,8 @@ def bin_image(a, b):
     return a[: ny - ny % b, : nx - nx % b].reshape(ny // b, b, nx // b, b).mean(axis=(1, 3))
 
 
-def evaluate(net: UNet, src: DoseSource, cases, n_input, n_ref, seed=3, b=8, pixel_mm=0.39, dd=0.02,
-             dta_mm=2.0, threshold=0.10, ladder=()):
+def evaluate(net: UNet, src: DoseSource, cases, n_input, n_ref, seed=3, b=8, pixel_mm=None, dd=0.02,
+             dta_mm=2.0, threshold=0.10, ladder=(), aux=False, family="thorax"):
     """Gamma pass rates of raw and denoised n_input-history images against
     n_ref-history references, per case (binned b x b); with a ladder of
     history counts, also the raw images' gamma and RMS error at each count
@@ -142,17 +252,20 @@ def evaluate(net: UNet, src: DoseSource, cases, n_input, n_ref, seed=3, b=8, pix
     out = []
     cache = {}
     for c in cases:
-        prob = case_problem(c, seed, phantom_cache=cache)
+        prob = case_problem(c, seed, phantom_cache=cache, family=family)
+        pixel_mm = 10.0 * prob.epid.pitch if pixel_mm is None else pixel_mm
+        shape = net_shape(prob.epid)
         d_in = src.image(prob, n_input, 0, seed + 1000)
+        x, s = input_planes(src, prob, d_in, aux, shape)
+        x = x[None].contiguous()
         d_ref = src.image(prob, n_ref, TARGET_BASE, seed + 1000)
-        s = 1.0 / max(float(d_in.mean()), 1e-300)
-        x = (d_in * s).float()[None]
-        y = torch.empty_like(x)
+        y = torch.empty((1,) + shape, dtype=torch.float32, device=x.device)
         net.forward(x, y, 1.0, 1.0 / s)
         torch.cuda.synchronize()
+        ny, nx = d_in.shape
         ref = bin_image(d_ref.cpu().numpy(), b)
         raw = bin_image(d_in.cpu().numpy(), b)
-        den = bin_image(y[0].double().cpu().numpy(), b)
+        den = bin_image(y[0, :ny, :nx].double().cpu().numpy(), b)
         dev = f"cuda:{src.device}"
         R = torch.tensor(ref, device=dev)
         g_raw = gamma(R, torch.tensor(raw, device=dev), pixel_mm * b, dd, dta_mm, threshold)

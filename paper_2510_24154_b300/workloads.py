@@ -235,25 +235,34 @@ def thorax_ct(rng: np.random.Generator, nx=256, ny=256, nz=128, vox=0.2,
 
 
 def anthropomorphic_ct(rng: np.random.Generator, nx=512, ny=512, nz=200, vox=0.1,
-                       noise_hu: float = 20.0) -> Phantom:
-    """Larger thorax-like phantom: body outline, spine, rib arcs, lungs, organs."""
+                       noise_hu: float = 20.0, jitter: float = 0.0) -> Phantom:
+    """Larger thorax-like phantom: body outline, spine, rib arcs, lungs, organs.
+    `jitter` scales random +-fraction perturbations of sizes and positions (the
+    denoiser's training phantoms); at 0 no random number is drawn for them."""
+    def j(v):
+        return v * (1.0 + jitter * rng.uniform(-1, 1)) if jitter else v
+
     ox, oy, oz = -nx * vox / 2, -ny * vox / 2, -nz * vox / 2
     x = _centres(nx, vox, ox)[None, None, :]
     y = _centres(ny, vox, oy)[None, :, None]
     z = _centres(nz, vox, oz)[:, None, None]
     hu = np.full((nz, ny, nx), -1000.0, dtype=np.float32)
-    body = (x / 17.0) ** 2 + (y / 11.0) ** 2 <= 1.0
+    bx, by = j(17.0), j(11.0)
+    body = (x / bx) ** 2 + (y / by) ** 2 <= 1.0
     hu = np.where(body, 0.0, hu)
     for sx in (-1.0, 1.0):
-        lung = ((x - 7.0 * sx) / 5.0) ** 2 + ((y + 0.5) / 6.5) ** 2 + (z / 9.0) ** 2 <= 1.0
+        cx, cy, a, b, c = sx * j(7.0), j(-0.5), j(5.0), j(6.5), j(9.0)
+        lung = ((x - cx) / a) ** 2 + ((y - cy) / b) ** 2 + (z / c) ** 2 <= 1.0
         hu = np.where(lung & body, -750.0, hu)
-    organs = (((x - 1.0) / 4.0) ** 2 + ((y + 3.0) / 3.5) ** 2 + ((z - 2.0) / 5.0) ** 2 <= 1.0)
+    cx, cy, cz, a, b, c = j(1.0), j(-3.0), j(2.0), j(4.0), j(3.5), j(5.0)
+    organs = (((x - cx) / a) ** 2 + ((y - cy) / b) ** 2 + ((z - cz) / c) ** 2 <= 1.0)
     hu = np.where(organs & body, 40.0, hu)
-    spine = (x ** 2 + (y - 7.5) ** 2 <= 1.6 ** 2)
+    sy, sr = j(7.5), j(1.6)
+    spine = (x ** 2 + (y - sy) ** 2 <= sr ** 2)
     hu = np.where(spine & body, 1000.0, hu)
-    rr = (x / 15.8) ** 2 + (y / 9.8) ** 2
+    rr = (x / (bx - 1.2)) ** 2 + (y / (by - 1.2)) ** 2
     shell = (rr >= 0.86) & (rr <= 0.95)
-    ribs = shell & (np.cos(2 * np.pi * z / 2.5) > 0.3) & body
+    ribs = shell & (np.cos(2 * np.pi * z / j(2.5)) > 0.3) & body
     hu = np.where(ribs, 700.0, hu)
     hu = hu + rng.normal(0.0, noise_hu, size=hu.shape).astype(np.float32)
     hu = np.clip(np.rint(hu), -1024, 3071).astype(np.int16)

@@ -74,6 +74,7 @@ def test_struct_layouts_match_c(tmp_path):
         #include <stdio.h>
         #include <stddef.h>
         #include "archer_epid.h"
+        #include "archer_denoise.h"
         int main(void) {
           printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mc_config), sizeof(mc_epid_desc), sizeof(mc_field_desc),
                  sizeof(mc_lut_desc), sizeof(mc_run_stats), sizeof(mc_alu_peaks), offsetof(mc_alu_peaks, sm_count));
@@ -83,15 +84,17 @@ def test_struct_layouts_match_c(tmp_path):
                  offsetof(mc_field_desc, leaf_gap_cm), offsetof(mc_run_stats, gpu_ms),
                  offsetof(mc_run_stats, launches));
           printf("%zu %zu\\n", offsetof(mc_field_desc, leaf_thickness_cm), offsetof(mc_field_desc, jaw_thickness_cm));
+          printf("%zu %zu %zu\\n", sizeof(dn_config), offsetof(dn_config, in_channels), offsetof(dn_config, seed));
           return 0;
         }""")
     src = tmp_path / "probe.c"
     src.write_text(probe)
     exe = tmp_path / "probe"
     subprocess.run(["gcc", f"-I{ROOT / 'include'}", str(src), "-o", str(exe)], check=True)
-    sizes, offs, slabs = [list(map(int, l.split())) for l in
-                          subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()]
+    sizes, offs, slabs, dn = [list(map(int, l.split())) for l in
+                              subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()]
     assert slabs == [binding.FieldDesc.leaf_thickness_cm.offset, binding.FieldDesc.jaw_thickness_cm.offset]
+    assert dn == [C.sizeof(denoise.DnConfig), denoise.DnConfig.in_channels.offset, denoise.DnConfig.seed.offset]
     assert sizes == [C.sizeof(binding.Config), C.sizeof(binding.EpidDesc), C.sizeof(binding.FieldDesc),
                      C.sizeof(binding.LutDesc), C.sizeof(binding.RunStats), C.sizeof(binding.AluPeaks),
                      binding.AluPeaks.sm_count.offset]
@@ -105,10 +108,14 @@ def test_denoise_config_layout_and_errors_without_gpu():
     probe_ok = denoise.DnConfig()
     lib = denoise.lib()
     lib.dn_config_default(C.byref(probe_ok))
-    assert (probe_ok.height, probe_ok.width, probe_ok.levels, probe_ok.base_channels) == (768, 1024, 4, 32)
+    assert (probe_ok.height, probe_ok.width, probe_ok.levels, probe_ok.base_channels, probe_ok.in_channels) == \
+        (768, 1024, 4, 32, 1)
     assert lib.dn_create(None, 0, None) == 1
     bad = denoise.DnConfig(height=100, width=1024, batch=1, levels=4, base_channels=32, seed=0)   # not a multiple of 8
     h = C.c_void_p()
     assert lib.dn_create(C.byref(bad), 0, C.byref(h)) == 1 and not h.value
+    for planes in (0, 9):
+        bad = denoise.DnConfig(height=64, width=64, batch=1, levels=4, base_channels=32, in_channels=planes, seed=0)
+        assert lib.dn_create(C.byref(bad), 0, C.byref(h)) == 1 and not h.value
     assert lib.dn_destroy(None) == 0
     assert lib.dn_conv2d_forward(None, 32, None, 0, 1, 8, 8, None, None, 3, 32, 1, None, 32, None) == 1

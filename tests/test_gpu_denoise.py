@@ -156,28 +156,41 @@ def test_pool_and_upsample_parity():
     assert np.allclose(_np(du), ref, rtol=2.0 ** -8, atol=0)
 
 
-def _small_net(levels=3, H=32, Wd=256, batch=2, seed=5):
-    spec = U.UNetSpec(levels=levels, c0=32, cin=1)
+def _small_net(levels=3, H=32, Wd=256, batch=2, seed=5, cin=1):
+    """A seeded network and batch.  With cin > 1 the input is planar
+    [batch][cin][H][W]: the noisy image, a smooth map and a binary mask,
+    the kinds of auxiliary planes the denoiser is given."""
+    spec = U.UNetSpec(levels=levels, c0=32, cin=cin)
     params = W.unet_params(U.layers(spec), seed=seed)
-    net = D.UNet(height=H, width=Wd, batch=batch, levels=levels, base_channels=32, seed=seed)
+    net = D.UNet(height=H, width=Wd, batch=batch, levels=levels, base_channels=32, seed=seed, in_channels=cin)
     net.set_params(params)
     r = np.random.default_rng(seed)
     yy, xx = np.mgrid[0:H, 0:Wd]
     clean = np.exp(-((yy - H / 2) ** 2 / (H * H / 8) + (xx - Wd / 2) ** 2 / (Wd * Wd / 8)))
     x = np.stack([U.bf16_round(np.abs(clean + 0.3 * r.normal(size=clean.shape))) for _ in range(batch)])
+    if cin > 1:
+        aux = [clean * (1 + 0.5 * np.sin(xx / 7.0)), ((np.abs(yy - H / 2) < H / 4) & (np.abs(xx - Wd / 2) < Wd / 3))]
+        planes = [x] + [np.broadcast_to(U.bf16_round(a.astype(np.float64)), x.shape) for a in aux]
+        planes += [U.bf16_round(r.uniform(-1, 1, size=x.shape)) for _ in range(cin - len(planes))]
+        x = np.stack(planes[:cin], axis=1)
     t = U.bf16_round(np.stack([clean] * batch))
     return spec, params, net, x.astype(np.float32), t.astype(np.float32)
 
 
-def test_unet_forward_and_gradient_parity():
-    spec, params, net, x, t = _small_net()
+def _nhwc(x):
+    return x[..., None] if x.ndim == 3 else np.moveaxis(x, 1, 3)
+
+
+@pytest.mark.parametrize("levels,H,Wd,cin", [(3, 32, 256, 1), (4, 128, 256, 1), (3, 32, 256, 3), (4, 64, 128, 8)])
+def test_unet_forward_and_gradient_parity(levels, H, Wd, cin):
+    spec, params, net, x, t = _small_net(levels=levels, H=H, Wd=Wd, cin=cin)
     assert net.n_params == U.param_count(spec)
     xd, td = _f32(x), _f32(t)
     loss = net.train_step(xd, td, lr=0.0)
-    out = torch.zeros_like(xd)
+    out = torch.zeros_like(td)
     net.output(out)
     g = net.grads()
-    y_ref, cache = U.forward(spec, params.astype(np.float64), x[..., None], emulate_bf16=True)
+    y_ref, cache = U.forward(spec, params.astype(np.float64), _nhwc(x), emulate_bf16=True)
     loss_ref, dy = U.mse(y_ref, t[..., None])
     g_ref = U.backward(spec, cache, dy, emulate_bf16=True)
     # output: every element within 2 % of the output's range
@@ -194,6 +207,19 @@ def test_unet_forward_and_gradient_parity():
         cos = float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
         assert rel <= 0.05 and cos >= 0.998, (name, rel, cos)
         o += n
+    net.close()
+
+
+def test_unet_in_scale_multiplies_only_the_image_plane():
+    """in_scale applies to plane 0; auxiliary planes are taken as given."""
+    spec, params, net, x, t = _small_net(cin=3, seed=9)
+    out_a, out_b = torch.zeros_like(_f32(t)), torch.zeros_like(_f32(t))
+    net.forward(_f32(x), out_a, in_scale=1.0)
+    x2 = x.copy()
+    x2[:, 0] *= 0.25
+    net.forward(_f32(x2), out_b, in_scale=4.0)
+    torch.cuda.synchronize()
+    assert torch.equal(out_a, out_b)
     net.close()
 
 
@@ -270,3 +296,26 @@ def test_denoiser_pipeline_on_mc_pairs_small():
     res = evaluate(ev, src, [1000], 100_000, 30_000_000, seed=3)
     assert 0.0 <= res[0]["gamma_raw"] <= 1.0 and 0.0 <= res[0]["gamma_denoised"] <= 1.0
     net.close(); ev.close(); src.close()
+
+
+def test_denoise_experiment_beats_raw_on_held_out_cases():
+    """The evaluation driver on a small case (32 training pairs of 1e6 / 1e9
+    histories, 1500 steps, the aperture, t-map and primary planes as extra
+    input; 2 held-out cases against 1e9-history references): on the held-out
+    cases the denoised image passes the 2 %/2 mm gamma more often than the raw
+    input and has a smaller RMS error, and it matches plain Monte Carlo of
+    more histories than its input.  Measured: gamma 0.70 raw, 0.82 denoised;
+    RMS error 0.57 raw, 0.037 denoised (plain 1e8 histories: 0.058)."""
+    import json
+    import subprocess
+    import sys
+    cmd = [sys.executable, "-m", "paper_2510_24154_b300.denoise_experiment", "--pairs", "32", "--n-input", "1e6",
+           "--n-target", "1e9", "--eval", "2", "--n-ref", "1e9", "--steps", "1500", "--aux", "--ladder",
+           "1e6,1e7,1e8"]
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, check=True).stdout
+    r = json.loads(out.strip().splitlines()[-1])
+    assert r["in_channels"] == 4 and r["eval_cases"] == 2
+    assert r["gamma_denoised_mean"] > r["gamma_raw_mean"] + 0.05, (r["gamma_raw_mean"], r["gamma_denoised_mean"])
+    assert r["rms_denoised_mean"] < r["rms_raw_mean"], (r["rms_raw_mean"], r["rms_denoised_mean"])
+    n_rms = r["matched"]["plain_histories_at_denoised_rms"]
+    assert n_rms is None or n_rms > 3e7
