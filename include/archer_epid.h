@@ -197,7 +197,7 @@ mc_status mc_create(const mc_config* cfg, int device, mc_ctx** out);
 /* Frees every device and host allocation of ctx (NULL is a no-op). */
 mc_status mc_destroy(mc_ctx* ctx);
 
-/* Step a1 (Sec. 2.1.2, HU-to-density curve): copies the int16 HU volume
+/* CT set-up (Sec. 2.1.2, HU-to-density curve): copies the int16 HU volume
  * [nz][ny][nx] (host pointer, or device pointer when hu_on_device != 0) and
  * converts it on the GPU to per-voxel density; material follows from the
  * density thresholds.  vox_cm: voxel size, origin_cm: lower corner of the box.
@@ -268,7 +268,18 @@ mc_status mc_get_field_size(mc_ctx* ctx, int field, double* s, double* a, double
  * is queued on `stream` and the call does not wait. */
 mc_status mc_get_dose(mc_ctx* ctx, double* dose, double* sigma, double* u_out, int on_device, void* stream);
 
-/* Step a11 (Sec. 3.1, field 0): signal = k_scale * k(t, s) * dose per pixel, float32
+/* Mean per-history dose (Gy) over the pixel rectangle [ix0, ix1) x [iy0, iy1)
+ * of field `field` and the batch standard error of that mean (the central
+ * 1 cm x 1 cm region of the Sec. 2.2 calibration, whose signal enters Eq. 2;
+ * uncertainty as for mc_get_dose, Sec. 2.3): mean = sum of the region's
+ * deposits / (N x pixels), the error from the B per-batch region means.
+ * mean and sigma are host doubles (sigma may be NULL).  Errors: MC_ERR_ARG
+ * for an empty rectangle or one not inside the image, MC_ERR_STATE before
+ * any history.  Waits for the device. */
+mc_status mc_get_region_dose(mc_ctx* ctx, int field, int ix0, int ix1, int iy0, int iy1, double* mean,
+                             double* sigma, void* stream);
+
+/* The k(t, s) correction (Sec. 3.1, field 0): signal = k_scale * k(t, s) * dose per pixel, float32
  * [npy][npx] (host or device per on_device). */
 mc_status mc_get_epid_image(mc_ctx* ctx, float* signal, int on_device, void* stream);
 

@@ -25,7 +25,7 @@ STATUS = {0: "MC_OK", 1: "MC_ERR_ARG", 2: "MC_ERR_CUDA", 3: "MC_ERR_OOM", 4: "MC
 # Every entry point declared in include/archer_epid.h.
 EXPORTED = ("mc_config_default", "mc_create", "mc_destroy", "mc_init_geometry", "mc_set_field", "mc_run",
             "mc_set_fields", "mc_run_batch", "mc_get_field_dose", "mc_get_field_image", "mc_get_field_tmap",
-            "mc_get_field_size", "mc_get_dose", "mc_get_epid_image", "mc_get_tmap", "mc_get_tally", "mc_field_size", "mc_get_stats",
+            "mc_get_field_size", "mc_get_dose", "mc_get_region_dose", "mc_get_epid_image", "mc_get_tmap", "mc_get_tally", "mc_field_size", "mc_get_stats",
             "mc_reset_tally", "mc_state_size", "mc_get_state", "mc_set_state", "mc_set_history_base", "mc_cancel",
             "mc_last_error",
             "mc_status_string", "mc_test_philox", "mc_test_uniforms", "mc_dose_stats_noalloc", "mc_gamma",
@@ -116,6 +116,7 @@ def load(build_if_stale: bool = True):
     lib.mc_get_field_tmap.argtypes = [vp, i, vp, i, vp]
     lib.mc_get_field_size.argtypes = [vp, i, P(d), P(d), P(d)]
     lib.mc_get_dose.argtypes = [vp, vp, vp, P(d), i, vp]
+    lib.mc_get_region_dose.argtypes = [vp, i, i, i, i, i, P(d), P(d), vp]
     lib.mc_get_epid_image.argtypes = [vp, vp, i, vp]
     lib.mc_get_tmap.argtypes = [vp, vp, i, vp]
     lib.mc_get_tally.argtypes = [vp, vp, i, vp]
@@ -337,6 +338,14 @@ class Simulator:
         self._check(self.lib.mc_get_field_dose(self.h, int(field), _ptr(dose),
                                                _ptr(sigma) if sigma is not None else None, None, 1,
                                                _stream_ptr(stream)))
+
+    def region_dose(self, ix0, ix1, iy0, iy1, stream=None, field=0):
+        """Mean per-history dose (Gy) over pixels [ix0, ix1) x [iy0, iy1) and
+        the batch standard error of that mean, computed on the device."""
+        m, e = C.c_double(), C.c_double()
+        self._check(self.lib.mc_get_region_dose(self.h, int(field), int(ix0), int(ix1), int(iy0), int(iy1),
+                                                C.byref(m), C.byref(e), _stream_ptr(stream)))
+        return m.value, e.value
 
     def epid_image(self, stream=None, field=0):
         """a11: k(t, s)-corrected signal, float32 numpy [npy][npx]."""

@@ -15,7 +15,7 @@ per-history dose times the field area s^2, in Gy cm^2), as a fixed number of
 monitor units delivers a fixed fluence whatever the field size; each point
 runs histories_per_cm2 x s^2 histories, so all points carry similar
 statistics.  The uncertainty of each S is the batch standard error of the
-region mean.
+region mean.  Both come from the library (mc_get_region_dose) on the device.
 """
 from __future__ import annotations
 
@@ -37,26 +37,25 @@ def slab_phantom(t_cm: float, lateral_cm: float = 40.0, vox: float = 0.5) -> W.P
     return W.Phantom(hu, (vox, vox, vox), origin)
 
 
+def central_rect(epid: W.Epid, half_cm: float = 0.5):
+    """Pixel rectangle [ix0, ix1) x [iy0, iy1) of the pixels whose centres lie
+    within half_cm of the image centre in x and in y."""
+    def span(n):
+        c = ((np.arange(n) + 0.5) - n / 2) * epid.pitch
+        idx = np.nonzero(np.abs(c) <= half_cm)[0]
+        if idx.size == 0:
+            raise ValueError("no pixel centre within the region")
+        return int(idx[0]), int(idx[-1]) + 1
+    (ix0, ix1), (iy0, iy1) = span(epid.npx), span(epid.npy)
+    return ix0, ix1, iy0, iy1
+
+
 def central_region(epid: W.Epid, half_cm: float = 0.5):
-    """Boolean mask [npy][npx] of the pixels whose centres lie within half_cm
-    of the image centre in x and y."""
-    xs = ((np.arange(epid.npx) + 0.5) - epid.npx / 2) * epid.pitch
-    ys = ((np.arange(epid.npy) + 0.5) - epid.npy / 2) * epid.pitch
-    return (np.abs(ys)[:, None] <= half_cm) & (np.abs(xs)[None, :] <= half_cm)
-
-
-def region_signal(tally_mev: np.ndarray, n_hist: int, epid: W.Epid, mask: np.ndarray):
-    """Mean per-history dose (Gy) over the region and its batch standard
-    error, from sub-tallies [B][npy][npx] in MeV (history h in batch h mod B)."""
-    B = tally_mev.shape[0]
-    _, thick, rho = epid.layers[epid.sensitive]
-    conv = 1.602176634e-13 / (rho * epid.pitch * epid.pitch * thick * 1e-3)
-    ids = np.arange(B)
-    nb = (n_hist - ids + B - 1) // B
-    per_batch = tally_mev[:, mask].mean(axis=1) * conv / nb
-    mean = tally_mev[:, mask].sum(axis=0).mean() * conv / n_hist
-    sigma = per_batch.std(ddof=1) / np.sqrt(B)
-    return float(mean), float(sigma)
+    """The same region as a boolean mask [npy][npx]."""
+    ix0, ix1, iy0, iy1 = central_rect(epid, half_cm)
+    m = np.zeros((epid.npy, epid.npx), dtype=bool)
+    m[iy0:iy1, ix0:ix1] = True
+    return m
 
 
 def s_table(histories_per_cm2: float = 1e6, t_nodes=T_NODES, s_nodes=S_NODES, epid: W.Epid | None = None,
@@ -67,7 +66,7 @@ def s_table(histories_per_cm2: float = 1e6, t_nodes=T_NODES, s_nodes=S_NODES, ep
     from .binding import Simulator
     epid = epid or W.epid_default(1024, 768, 0.039)
     physics = physics or W.Physics(coupled=True)
-    mask = central_region(epid)
+    rect = central_rect(epid)
     S = np.zeros((len(s_nodes), len(t_nodes)))
     U = np.zeros_like(S)
     sim = Simulator(physics, device=device)
@@ -82,8 +81,7 @@ def s_table(histories_per_cm2: float = 1e6, t_nodes=T_NODES, s_nodes=S_NODES, ep
                     k = min(n - done, 1 << 31)
                     sim.run(k, seed + 1000 * j + i)
                     done += k
-                tally = sim.tally().astype(np.float64) / 2.56e8
-                m, u = region_signal(tally, n, epid, mask)
+                m, u = sim.region_dose(*rect)
                 S[i, j], U[i, j] = m * s * s, u * s * s
     finally:
         sim.close()

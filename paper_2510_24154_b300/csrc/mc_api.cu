@@ -111,6 +111,8 @@ struct mc_ctx {
     double* d_dose = nullptr;
     double* d_sigma = nullptr;
     double* d_nb = nullptr;
+    unsigned long long* d_rsum = nullptr;    // region statistics: per-batch sums, then mean and error
+    double* d_rstat = nullptr;
     double* d_u = nullptr;
     unsigned long long* d_maxbits = nullptr;
     double* d_part = nullptr;
@@ -976,6 +978,8 @@ mc_status mc_create(const mc_config* cfg_in, int device, mc_ctx** out) {
         cudaMalloc(&c->d_rho_max, sizeof(unsigned int) * 4) != cudaSuccess ||
         cudaMalloc(&c->d_thr, sizeof(float) * 3) != cudaSuccess ||
         cudaMalloc(&c->d_nb, sizeof(double) * cfg.n_batches) != cudaSuccess ||
+        cudaMalloc(&c->d_rsum, sizeof(unsigned long long) * cfg.n_batches) != cudaSuccess ||
+        cudaMalloc(&c->d_rstat, sizeof(double) * 2) != cudaSuccess ||
         cudaMalloc(&c->d_u, sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->d_maxbits, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->d_fields, sizeof(FieldDev) * mc::kMaxFields) != cudaSuccess ||
@@ -1027,6 +1031,8 @@ mc_status mc_destroy(mc_ctx* c) {
     dfree(c->d_energy);
     dfree(c->d_events);
     dfree(c->d_nb);
+    dfree(c->d_rsum);
+    dfree(c->d_rstat);
     dfree(c->d_u);
     dfree(c->d_maxbits);
     dfree(c->d_fields);
@@ -1190,6 +1196,35 @@ mc_status mc_get_field_dose(mc_ctx* c, int field, double* dose, double* sigma, d
 
 mc_status mc_get_dose(mc_ctx* c, double* dose, double* sigma, double* u_out, int on_device, void* stream) {
     return mc_get_field_dose(c, 0, dose, sigma, u_out, on_device, stream);
+}
+
+mc_status mc_get_region_dose(mc_ctx* c, int field, int ix0, int ix1, int iy0, int iy1, double* mean,
+                             double* sigma, void* stream) {
+    if (!c) return MC_ERR_ARG;
+    mc_status st = check_field(c, field);
+    if (st != MC_OK) return st;
+    if (!mean) return fail(c, MC_ERR_ARG, "null mean");
+    if (ix0 < 0 || iy0 < 0 || ix1 <= ix0 || iy1 <= iy0 || ix1 > c->epid.npx || iy1 > c->epid.npy)
+        return fail(c, MC_ERR_ARG, "region must be a non-empty pixel rectangle inside the image");
+    const int B = c->cfg.n_batches;
+    const uint64_t N = c->fields[field].hist_done;
+    if (N == 0) return fail(c, MC_ERR_STATE, "no histories run");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaStream_t s = as_stream(stream);
+    { const mc_status o = order_after_run(c, s); if (o != MC_OK) return o; }
+    CUDA_TRY(c, mc::launch_batch_counts(c->d_nb, B, N, s));
+    const mc_epid_desc& E = c->epid;
+    const int l = E.sensitive_layer;
+    const double mass_kg = E.density[l] * E.pitch_cm * E.pitch_cm * E.thickness_cm[l] * 1e-3;
+    const unsigned long long* tally = c->d_tally + static_cast<size_t>(field) * B * npix(c);
+    CUDA_TRY(c, mc::launch_region_stats(tally, E.npx, E.npy, B, c->d_nb, static_cast<double>(N),
+                                        kJoulePerMeV / mass_kg, ix0, ix1, iy0, iy1, c->d_rsum, c->d_rstat, s));
+    double h[2];
+    CUDA_TRY(c, cudaMemcpyAsync(h, c->d_rstat, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    *mean = h[0];
+    if (sigma) *sigma = h[1];
+    return MC_OK;
 }
 
 mc_status mc_get_field_image(mc_ctx* c, int field, float* signal, int on_device, void* stream) {

@@ -362,6 +362,57 @@ __global__ void k_batch_counts(double* nb, int B, unsigned long long n) {
     if (b < B) nb[b] = static_cast<double>(n / B + (static_cast<unsigned long long>(b) < n % B ? 1ull : 0ull));
 }
 
+// Region statistics (Sec. 2.2 calibration region, Sec. 2.3 uncertainty): per
+// batch b the exact integer sum of its sub-tally over pixels [ix0, ix0 + w) x
+// [iy0, iy0 + h); then, one thread, the region's mean dose per history
+// D = sum_b E_b / (N n_pix) and the batch standard error of the region mean,
+// sqrt(sum_b (D_b - D)^2 / (B (B - 1))) with D_b = E_b / (N_b n_pix).
+__global__ void k_region_sums(const unsigned long long* __restrict__ tally, int npx, int npix, int ix0, int iy0,
+                              int w, int h, unsigned long long* __restrict__ sums) {
+    const int b = blockIdx.y;
+    const long long n = static_cast<long long>(w) * h;
+    const unsigned long long* t = tally + static_cast<size_t>(b) * npix;
+    unsigned long long acc = 0;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int r = static_cast<int>(i / w), q = static_cast<int>(i - static_cast<long long>(r) * w);
+        acc += t[static_cast<size_t>(iy0 + r) * npx + ix0 + q];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(sums + b, acc);
+}
+
+__global__ void k_region_stats(const unsigned long long* __restrict__ sums, const double* __restrict__ nb, int B,
+                               double n_hist, double conv_per_pix, double* __restrict__ out) {
+    const double per_q = 1.0 / 2.56e8;              // MeV per tally unit
+    double tot = 0.0;
+    for (int b = 0; b < B; ++b) tot += static_cast<double>(sums[b]);
+    const double mean = tot * per_q / n_hist * conv_per_pix;
+    double ss = 0.0;
+    for (int b = 0; b < B; ++b) {
+        const double db = static_cast<double>(sums[b]) * per_q / nb[b] * conv_per_pix;
+        ss += (db - mean) * (db - mean);
+    }
+    out[0] = mean;
+    out[1] = sqrt(ss / (static_cast<double>(B) * (B - 1)));
+}
+
+cudaError_t launch_region_stats(const unsigned long long* tally, int npx, int npy, int B, const double* nb,
+                                double n_hist, double conv, int ix0, int ix1, int iy0, int iy1,
+                                unsigned long long* sums, double* out, cudaStream_t s) {
+    const int w = ix1 - ix0, h = iy1 - iy0;
+    const long long n = static_cast<long long>(w) * h;
+    cudaError_t e = cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * B, s);
+    if (e != cudaSuccess) return e;
+    const int block = 256;
+    const int gx = static_cast<int>(std::min<long long>((n + block - 1) / block, 64));
+    k_region_sums<<<dim3(gx, B), block, 0, s>>>(tally, npx, npx * npy, ix0, iy0, w, h, sums);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_region_stats<<<1, 1, 0, s>>>(sums, nb, B, n_hist, conv / static_cast<double>(n), out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch_counts(double* nb, int B, unsigned long long n, cudaStream_t s) {
     k_batch_counts<<<(B + 127) / 128, 128, 0, s>>>(nb, B, n);
     return cudaGetLastError();

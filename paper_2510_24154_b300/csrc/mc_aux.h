@@ -43,6 +43,11 @@ cudaError_t launch_macro_grid(const float* rho, int nx, int ny, int nz, int M, i
 cudaError_t launch_tmap(const TmapArgs& A, double* t, cudaStream_t s);
 // nb[b] = the number of history indices 0 .. n-1 with index mod B == b.
 cudaError_t launch_batch_counts(double* nb, int B, unsigned long long n, cudaStream_t s);
+// Mean dose per history over pixels [ix0, ix1) x [iy0, iy1) and its batch
+// standard error into out[0], out[1]; sums is B words of scratch.
+cudaError_t launch_region_stats(const unsigned long long* tally, int npx, int npy, int B, const double* nb,
+                                double n_hist, double conv, int ix0, int ix1, int iy0, int iy1,
+                                unsigned long long* sums, double* out, cudaStream_t s);
 cudaError_t launch_dose(const unsigned long long* tally, int npix, int B, const double* nb, double n_hist,
                         double conv, double* dose, double* sigma, unsigned long long* max_bits, double* part_sum,
                         unsigned int* part_cnt, double* u, cudaStream_t s);

@@ -1,6 +1,6 @@
 """Host logic of the S(t, s) calibration sweep (Sec. 2.2, Eq. 2): slab
-geometry, the central 1 cm x 1 cm region, the region statistics and
-k = M / S."""
+geometry, the central 1 cm x 1 cm region and k = M / S (the region
+statistics are the library's, checked on the GPU)."""
 import numpy as np
 import pytest
 
@@ -21,22 +21,15 @@ def test_slab_and_region():
     assert (xs.min(), xs.max(), ys.min(), ys.max()) == (499, 524, 371, 396)
 
 
-def test_region_signal_closed_form():
-    ep = W.epid_default(64, 48, 0.25)
-    m = CAL.central_region(ep)
-    B, n = 16, 1600
-    tally = np.full((B, 48, 64), 2.0)              # 2 MeV per pixel per batch
-    mean, sd = CAL.region_signal(tally, n, ep, m)
-    _, thick, rho = ep.layers[ep.sensitive]
-    conv = 1.602176634e-13 / (rho * 0.25 * 0.25 * thick * 1e-3)
-    assert mean == pytest.approx(2.0 * B * conv / n, rel=1e-12)
-    assert sd == pytest.approx(0.0, abs=1e-30)
-    tally[3] *= 3.0                                 # one batch three times hotter
-    mean, sd = CAL.region_signal(tally, n, ep, m)
-    per = np.full(B, 2.0 * conv / (n / B))
-    per[3] *= 3.0
-    assert mean == pytest.approx(per.mean(), rel=1e-12)
-    assert sd == pytest.approx(per.std(ddof=1) / np.sqrt(B), rel=1e-12)
+def test_central_rect_is_the_mask():
+    for ep in (W.epid_default(1024, 768, 0.039), W.epid_default(64, 48, 0.25), W.epid_default(65, 47, 0.3)):
+        ix0, ix1, iy0, iy1 = CAL.central_rect(ep)
+        xs = ((np.arange(ep.npx) + 0.5) - ep.npx / 2) * ep.pitch
+        ys = ((np.arange(ep.npy) + 0.5) - ep.npy / 2) * ep.pitch
+        assert list(np.nonzero(np.abs(xs) <= 0.5)[0]) == list(range(ix0, ix1))
+        assert list(np.nonzero(np.abs(ys) <= 0.5)[0]) == list(range(iy0, iy1))
+    with pytest.raises(ValueError):
+        CAL.central_rect(W.epid_default(2, 2, 2.0))               # pixel centres 1 cm from the centre
 
 
 def test_k_table_is_the_ratio():

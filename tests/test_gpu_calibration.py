@@ -13,6 +13,39 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 
+def test_region_dose_is_the_tally_statistic():
+    """mc_get_region_dose against the same statistic taken from the raw
+    sub-tallies: mean = sum of the region's deposits / (N pixels), error =
+    the batch standard error of the per-batch region means; and its
+    argument checks."""
+    from paper_2510_24154_b300.binding import MCError, Simulator
+    ep = W.epid_default(128, 96, 0.312)
+    sim = Simulator(W.Physics(coupled=True))
+    try:
+        sim.init_geometry(CAL.slab_phantom(5.0), ep)
+        sim.set_field(W.open_field(8.0, 8.0))
+        n = 300_001                                  # B does not divide it
+        sim.run(n, 7)
+        tally = sim.tally().astype(np.float64) / 2.56e8
+        B = tally.shape[0]
+        nb = oracle.batch_counts(n, B).astype(float)
+        _, thick, rho = ep.layers[ep.sensitive]
+        conv = 1.602176634e-13 / (rho * ep.pitch ** 2 * thick * 1e-3)
+        for rect in (CAL.central_rect(ep), (0, 128, 0, 96), (5, 6, 90, 96), (60, 70, 40, 41)):
+            ix0, ix1, iy0, iy1 = rect
+            reg = tally[:, iy0:iy1, ix0:ix1].reshape(B, -1)
+            want = reg.sum() * conv / (n * reg.shape[1])
+            per = reg.sum(axis=1) * conv / (nb * reg.shape[1])
+            want_sd = np.sqrt(((per - want) ** 2).sum() / (B * (B - 1)))
+            m, sd = sim.region_dose(*rect)
+            assert m == pytest.approx(want, rel=1e-12, abs=1e-300) and sd == pytest.approx(want_sd, rel=1e-9, abs=1e-300)
+        for bad in ((0, 0, 0, 1), (-1, 3, 0, 1), (0, 129, 0, 1), (0, 1, 5, 4)):
+            with pytest.raises(MCError):
+                sim.region_dose(*bad)
+    finally:
+        sim.close()
+
+
 def test_s_table_trends():
     ep = W.epid_default(256, 192, 0.156)
     S, U = CAL.s_table(1e6, epid=ep)
