@@ -268,6 +268,18 @@ mc_status mc_get_field_size(mc_ctx* ctx, int field, double* s, double* a, double
  * is queued on `stream` and the call does not wait. */
 mc_status mc_get_dose(mc_ctx* ctx, double* dose, double* sigma, double* u_out, int on_device, void* stream);
 
+/* The field's source fluence on the EPID grid: the probability density
+ * (cm^-2 at the isocentre plane) of a history's source ray crossing that
+ * plane at each pixel centre scaled by SAD / SID -- the MLC- and
+ * jaw-modulated source of Sec. 2.1.1 that mc_run samples (MU weights, leaf
+ * and jaw transmission, tongue and groove, leaf gap; with collimator slabs,
+ * the rays before the slabs).  It integrates to 1 over the isocentre plane.
+ * Segments add their densities with atomics, so repeated calls agree up to
+ * the order of those sums (~1e-16 relative).
+ * F: [npy][npx] doubles, host or device per on_device.  With on_device the
+ * work is queued on `stream` and the call does not wait. */
+mc_status mc_get_field_fluence(mc_ctx* ctx, int field, double* F, int on_device, void* stream);
+
 /* Mean per-history dose (Gy) over the pixel rectangle [ix0, ix1) x [iy0, iy1)
  * of field `field` and the batch standard error of that mean (the central
  * 1 cm x 1 cm region of the Sec. 2.2 calibration, whose signal enters Eq. 2;

@@ -25,7 +25,7 @@ STATUS = {0: "MC_OK", 1: "MC_ERR_ARG", 2: "MC_ERR_CUDA", 3: "MC_ERR_OOM", 4: "MC
 # Every entry point declared in include/archer_epid.h.
 EXPORTED = ("mc_config_default", "mc_create", "mc_destroy", "mc_init_geometry", "mc_set_field", "mc_run",
             "mc_set_fields", "mc_run_batch", "mc_get_field_dose", "mc_get_field_image", "mc_get_field_tmap",
-            "mc_get_field_size", "mc_get_dose", "mc_get_region_dose", "mc_get_epid_image", "mc_get_tmap", "mc_get_tally", "mc_field_size", "mc_get_stats",
+            "mc_get_field_size", "mc_get_dose", "mc_get_region_dose", "mc_get_field_fluence", "mc_get_epid_image", "mc_get_tmap", "mc_get_tally", "mc_field_size", "mc_get_stats",
             "mc_reset_tally", "mc_state_size", "mc_get_state", "mc_set_state", "mc_set_history_base", "mc_cancel",
             "mc_last_error",
             "mc_status_string", "mc_test_philox", "mc_test_uniforms", "mc_dose_stats_noalloc", "mc_gamma",
@@ -117,6 +117,7 @@ def load(build_if_stale: bool = True):
     lib.mc_get_field_size.argtypes = [vp, i, P(d), P(d), P(d)]
     lib.mc_get_dose.argtypes = [vp, vp, vp, P(d), i, vp]
     lib.mc_get_region_dose.argtypes = [vp, i, i, i, i, i, P(d), P(d), vp]
+    lib.mc_get_field_fluence.argtypes = [vp, i, vp, i, vp]
     lib.mc_get_epid_image.argtypes = [vp, vp, i, vp]
     lib.mc_get_tmap.argtypes = [vp, vp, i, vp]
     lib.mc_get_tally.argtypes = [vp, vp, i, vp]
@@ -338,6 +339,23 @@ class Simulator:
         self._check(self.lib.mc_get_field_dose(self.h, int(field), _ptr(dose),
                                                _ptr(sigma) if sigma is not None else None, None, 1,
                                                _stream_ptr(stream)))
+
+    def fluence(self, stream=None, field=0):
+        """Source fluence density (cm^-2 at the isocentre plane) at the EPID
+        pixel centres, float64 numpy [npy][npx]."""
+        ny, nx = self._npix()
+        out = np.empty((ny, nx))
+        self._check(self.lib.mc_get_field_fluence(self.h, int(field), C.c_void_p(out.ctypes.data), 0,
+                                                  _stream_ptr(stream)))
+        return out
+
+    def fluence_device(self, out, stream=None, field=0):
+        """As fluence(), into a CUDA float64 tensor [npy][npx] (queued on the stream)."""
+        self._check(self.lib.mc_get_field_fluence(self.h, int(field), _ptr(out), 1, _stream_ptr(stream)))
+
+    def tmap_device(self, out, stream=None, field=0):
+        """The t-map into a CUDA float64 tensor [npy][npx] (queued on the stream)."""
+        self._check(self.lib.mc_get_field_tmap(self.h, int(field), _ptr(out), 1, _stream_ptr(stream)))
 
     def region_dose(self, ix0, ix1, iy0, iy1, stream=None, field=0):
         """Mean per-history dose (Gy) over pixels [ix0, ix1) x [iy0, iy1) and

@@ -109,6 +109,7 @@ struct mc_ctx {
     size_t vox_n = 0;
     // statistics scratch
     double* d_dose = nullptr;
+    double* d_flu = nullptr;                 // source fluence on the EPID grid (mc_get_field_fluence)
     double* d_sigma = nullptr;
     double* d_nb = nullptr;
     unsigned long long* d_rsum = nullptr;    // region statistics: per-batch sums, then mean and error
@@ -189,6 +190,7 @@ void free_field_buffers(mc_ctx* c) {
     dfree(c->d_lut_t);
     dfree(c->d_lut_ks);
     dfree(c->d_dose);
+    dfree(c->d_flu);
     dfree(c->d_sigma);
     dfree(c->d_part);
     dfree(c->d_partc);
@@ -697,6 +699,8 @@ mc_status set_fields_impl(mc_ctx* c, const mc_field_desc* f, int n, const mc_lut
     CUDA_TRY(c, ensure(c->d_sigma, cp, static_cast<size_t>(np)));
     cp = c->cap_pix;
     CUDA_TRY(c, ensure(c->d_signal, cp, static_cast<size_t>(np)));
+    cp = c->cap_pix;
+    CUDA_TRY(c, ensure(c->d_flu, cp, static_cast<size_t>(np)));
     c->cap_pix = cp;
     size_t cq = c->cap_parts;
     CUDA_TRY(c, ensure(c->d_part, cq, parts));
@@ -1196,6 +1200,26 @@ mc_status mc_get_field_dose(mc_ctx* c, int field, double* dose, double* sigma, d
 
 mc_status mc_get_dose(mc_ctx* c, double* dose, double* sigma, double* u_out, int on_device, void* stream) {
     return mc_get_field_dose(c, 0, dose, sigma, u_out, on_device, stream);
+}
+
+mc_status mc_get_field_fluence(mc_ctx* c, int field, double* F, int on_device, void* stream) {
+    if (!c) return MC_ERR_ARG;
+    mc_status st = check_field(c, field);
+    if (st != MC_OK) return st;
+    if (!F) return fail(c, MC_ERR_ARG, "null fluence");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaStream_t s = as_stream(stream);
+    { const mc_status o = order_after_run(c, s); if (o != MC_OK) return o; }
+    const FieldHost& h = c->fields[field];
+    const mc_epid_desc& E = c->epid;
+    double* out = on_device ? F : c->d_flu;
+    CUDA_TRY(c, mc::launch_fluence(c->d_rect + h.rect_off, c->d_cdf + h.rect_off, h.n_rect, E.npx, E.npy, E.pitch_cm,
+                                   h.sid / h.sad, out, s));
+    if (!on_device) {
+        CUDA_TRY(c, cudaMemcpyAsync(F, c->d_flu, sizeof(double) * npix(c), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+    }
+    return MC_OK;
 }
 
 mc_status mc_get_region_dose(mc_ctx* c, int field, int ix0, int ix1, int iy0, int iy1, double* mean,

@@ -362,6 +362,46 @@ __global__ void k_batch_counts(double* nb, int B, unsigned long long n) {
     if (b < B) nb[b] = static_cast<double>(n / B + (static_cast<unsigned long long>(b) < n % B ? 1ull : 0ull));
 }
 
+// Source fluence on the EPID grid (Sec. 2.1.1: the MLC-modulated source the
+// transport samples).  Rectangle i of a field carries probability
+// cdf[i] - cdf[i-1] spread uniformly over its area; a pixel takes the density
+// of the rectangle (one per segment) that holds its centre projected to the
+// isocentre plane.  Rectangles are half-open [x0, x1) x [y0, y1) and
+// neighbours share their float edges, so the pixel ranges below, computed
+// from those edges, tile without gaps or overlaps.  One block per rectangle,
+// one double atomic per covered pixel.
+__global__ void k_fluence(const float4* __restrict__ rect, const double* __restrict__ cdf, int npx, int npy,
+                          double pitch, double mag, double* __restrict__ F) {
+    const int i = blockIdx.x;
+    const float4 r = rect[i];
+    const double w = cdf[i] - (i > 0 ? cdf[i - 1] : 0.0);
+    const double area = (static_cast<double>(r.y) - r.x) * (static_cast<double>(r.w) - r.z);
+    if (!(w > 0.0) || !(area > 0.0)) return;
+    const double dens = w / area;
+    // first pixel index whose centre (-n p / 2 + (k + 1/2) p) / mag is >= the edge
+    auto first = [&](double edge, int n) {
+        const double k = ceil((edge * mag + 0.5 * n * pitch) / pitch - 0.5);
+        return static_cast<int>(fmin(fmax(k, 0.0), static_cast<double>(n)));
+    };
+    const int ix0 = first(r.x, npx), ix1 = first(r.y, npx);
+    const int iy0 = first(r.z, npy), iy1 = first(r.w, npy);
+    const int wx = ix1 - ix0, hy = iy1 - iy0;
+    if (wx <= 0 || hy <= 0) return;
+    const long long n = static_cast<long long>(wx) * hy;
+    for (long long q = threadIdx.x; q < n; q += blockDim.x) {
+        const int yy = static_cast<int>(q / wx), xx = static_cast<int>(q - static_cast<long long>(yy) * wx);
+        atomicAdd(F + static_cast<size_t>(iy0 + yy) * npx + ix0 + xx, dens);
+    }
+}
+
+cudaError_t launch_fluence(const float4* rect, const double* cdf, int n_rect, int npx, int npy, double pitch,
+                           double mag, double* F, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(F, 0, sizeof(double) * static_cast<size_t>(npx) * npy, s);
+    if (e != cudaSuccess || n_rect <= 0) return e;
+    k_fluence<<<n_rect, 256, 0, s>>>(rect, cdf, npx, npy, pitch, mag, F);
+    return cudaGetLastError();
+}
+
 // Region statistics (Sec. 2.2 calibration region, Sec. 2.3 uncertainty): per
 // batch b the exact integer sum of its sub-tally over pixels [ix0, ix0 + w) x
 // [iy0, iy0 + h); then, one thread, the region's mean dose per history

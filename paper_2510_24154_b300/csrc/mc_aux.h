@@ -43,6 +43,11 @@ cudaError_t launch_macro_grid(const float* rho, int nx, int ny, int nz, int M, i
 cudaError_t launch_tmap(const TmapArgs& A, double* t, cudaStream_t s);
 // nb[b] = the number of history indices 0 .. n-1 with index mod B == b.
 cudaError_t launch_batch_counts(double* nb, int B, unsigned long long n, cudaStream_t s);
+// Source-position density (cm^-2 at the isocentre plane) at each EPID pixel
+// centre projected by 1 / mag = SAD / SID, from a field's source rectangles
+// and their normalised cumulative weights; F[npy][npx] is overwritten.
+cudaError_t launch_fluence(const float4* rect, const double* cdf, int n_rect, int npx, int npy, double pitch,
+                           double mag, double* F, cudaStream_t s);
 // Mean dose per history over pixels [ix0, ix1) x [iy0, iy1) and its batch
 // standard error into out[0], out[1]; sums is B words of scratch.
 cudaError_t launch_region_stats(const unsigned long long* tally, int npx, int npy, int B, const double* nb,

@@ -10,11 +10,12 @@ images are divided by the input's mean over the image, so the network works
 on O(1) values and the scale is known at inference.
 
 With aux planes the network is also given what the noisy image cannot tell
-it: the MLC/jaw aperture fluence of the field projected onto the EPID (where
-the field edges are), the radiological thickness t of the CT along each
-pixel's ray (the t-map of Sec. 3.1) and their product, the uncollided primary
-estimate F exp(-mu t).  F and the primary estimate are divided by their image
-means, t by 40 g/cm^2.
+it: the field's source fluence F on the EPID grid (where the MLC and jaw
+edges are; the library's mc_get_field_fluence), the radiological thickness t
+of the CT along each pixel's ray (the t-map of Sec. 3.1) and their product,
+the uncollided primary estimate F exp(-mu t).  F and the primary estimate
+are divided by their image means, t by 40 g/cm^2.  All three are computed
+on the device.
 
 Evaluation: the denoised low-count image and the raw one are compared with a
 high-count reference by the global gamma index (2 %, 2 mm, 10 % threshold) on
@@ -89,47 +90,14 @@ def _pad(a, shape):
     return Fn.pad(a, (0, shape[1] - a.shape[-1], 0, shape[0] - a.shape[-2]))
 
 
-def aperture_fluence(field, epid) -> np.ndarray:
-    """MU-weighted aperture of a field on the EPID pixel grid, [npy][npx].
-
-    Pixel (ix, iy) has beam-frame centre (-npx p / 2 + (ix + 1/2) p,
-    -npy p / 2 + (iy + 1/2) p) on the plane at SID; scaled by SAD / SID it
-    falls on the isocentre plane where leaves and jaws are given.  Per
-    segment the value is MU x (leaf factor) x (jaw factor): 1 inside the
-    effective opening (leaf tips apart by the leaf gap; jaws), the leaf or
-    jaw transmission outside.  Tongue-and-groove strips are not drawn."""
-    mag = field.sad / field.sid
-    p = epid.pitch
-    x = (-0.5 * epid.npx * p + (np.arange(epid.npx) + 0.5) * p) * mag
-    y = (-0.5 * epid.npy * p + (np.arange(epid.npy) + 0.5) * p) * mag
-    edges = np.asarray(field.pair_edges, dtype=np.float64)
-    n_pairs = edges.size - 1
-    j = np.searchsorted(edges, y, side="right") - 1
-    in_pair = (j >= 0) & (j < n_pairs)
-    jc = np.clip(j, 0, n_pairs - 1)
-    T, Tj, gap = field.leaf_transmission, field.jaw_transmission, field.leaf_gap
-    F = np.zeros((epid.npy, epid.npx))
-    for k, mu in enumerate(np.asarray(field.mu, dtype=np.float64)):
-        if not mu > 0:
-            continue
-        jx0, jx1, jy0, jy1 = np.asarray(field.jaws[k], dtype=np.float64)
-        jx0, jx1, jy0, jy1 = max(jx0, -20.0), min(jx1, 20.0), max(jy0, -20.0), min(jy1, 20.0)
-        jaw = np.where(((y >= jy0) & (y < jy1))[:, None] & ((x >= jx0) & (x < jx1))[None, :], 1.0, Tj)
-        lv = np.asarray(field.leaves[k], dtype=np.float64)[jc]
-        open_ = in_pair & (lv[:, 1] > lv[:, 0])
-        lo, hi = lv[:, 0] - 0.5 * gap, lv[:, 1] + 0.5 * gap
-        leaf = np.where(open_[:, None] & (x[None, :] >= lo[:, None]) & (x[None, :] < hi[:, None]), 1.0, T)
-        F += mu * leaf * jaw
-    return F
-
-
-def aux_planes(field, epid, tmap):
-    """The auxiliary input planes [AUX_PLANES][npy][npx] (float64 numpy) of a
-    field, given its t-map (g/cm^2)."""
-    F = aperture_fluence(field, epid)
-    P = F * np.exp(-MU_PRIMARY * tmap)
-    nz = lambda a: a / max(float(a.mean()), 1e-300)
-    return np.stack([nz(F), tmap / 40.0, nz(P)])
+def aux_planes(F, t):
+    """The auxiliary input planes [AUX_PLANES][npy][npx] from the source
+    fluence F and the t-map t (g/cm^2), torch tensors [npy][npx] on one
+    device: F / mean(F), t / 40 and F exp(-MU_PRIMARY t) / its mean."""
+    import torch
+    P = F * torch.exp(-MU_PRIMARY * t)
+    nz = lambda a: a / torch.clamp(a.mean(), min=1e-300)
+    return torch.stack([nz(F), t / 40.0, nz(P)])
 
 
 class DoseSource:
@@ -167,8 +135,13 @@ class DoseSource:
         return d
 
     def aux(self, prob):
-        """Auxiliary planes of the field last set (call after image())."""
-        return aux_planes(prob.field, prob.epid, self.sim.tmap())
+        """Auxiliary planes (float64 CUDA) of the field last set (call after image())."""
+        torch = self.torch
+        F = torch.empty((prob.epid.npy, prob.epid.npx), dtype=torch.float64, device=f"cuda:{self.device}")
+        t = torch.empty_like(F)
+        self.sim.fluence_device(F)
+        self.sim.tmap_device(t)
+        return aux_planes(F, t)
 
     def close(self):
         self.sim.close()
@@ -182,8 +155,7 @@ def input_planes(src: DoseSource, prob, d_in, aux: bool, shape=None):
     s = 1.0 / max(float(d_in.mean()), 1e-300)
     x = (d_in * s).float()
     if aux:
-        a = torch.tensor(src.aux(prob), dtype=torch.float32, device=x.device)
-        x = torch.cat([x[None], a])
+        x = torch.cat([x[None], src.aux(prob).float()])
     if shape is not None:
         x = _pad(x, shape)
     return x.contiguous(), s
@@ -285,6 +257,15 @@ def evaluate(net: UNet, src: DoseSource, cases, n_input, n_ref, seed=3, b=8, pix
             row["ladder"].append({"n": float(n), "rms": rel(d_n),
                                   "gamma": gamma(R, torch.tensor(d_n, device=dev), pixel_mm * b, dd, dta_mm,
                                                  threshold)})
+        # the denoised route of this field end to end on the device: field
+        # set-up (t-map), n_input histories, dose, fluence, input planes, inference
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d_r = src.image(prob, n_input, 0, seed + 1000)
+        x_r, s_r = input_planes(src, prob, d_r, aux, shape)
+        net.forward(x_r[None].contiguous(), y, 1.0, 1.0 / s_r)
+        torch.cuda.synchronize()
+        row["route_s"] = time.perf_counter() - t0
         out.append(row)
     return out
 

@@ -96,6 +96,8 @@ def main():
     matched = {
         "mc_histories_per_s": rate, "inference_s": t_inf,
         "denoised_s_per_field": args.n_input / rate + t_inf,
+        # measured per held-out field: set-up, transport, dose, planes and inference
+        "denoised_route_s_measured_median": float(np.median([r["route_s"] for r in res])),
         "plain_histories_at_denoised_gamma": n_g,
         "plain_s_per_field_at_denoised_gamma": None if n_g is None else n_g / rate,
         "plain_histories_at_denoised_rms": n_e,
