@@ -47,10 +47,27 @@ __device__ __forceinline__ KStep kstep(const ConvArgs& a, int i) {
 }
 
 
+// The mask words the vector path of epilogue16 reads for columns co0 ..
+// co0+15 of one pixel, loaded ahead so their latency overlaps the TMEM read.
+__device__ __forceinline__ void epi_mask16(const ConvArgs& a, int co0, size_t pix, uint4* mv) {
+    const int d = (a.ndst > 1 && co0 >= a.dst_split) ? 1 : 0;
+    const int cc0 = co0 - (d ? a.dst_split : 0);
+    const int dC = a.dst_C[d];
+    const int dend = d ? a.N : (a.ndst > 1 ? a.dst_split : a.N);
+    const __nv_bfloat16* mk = a.mask[d];
+    if (mk && co0 + 16 <= dend && (dC & 7) == 0 && (cc0 & 7) == 0) {
+        const uint4* m = reinterpret_cast<const uint4*>(mk + pix * dC + cc0);
+        mv[0] = __ldg(m);
+        mv[1] = __ldg(m + 1);
+    }
+}
+
 // Epilogue of 16 accumulator columns (output channels co0 .. co0+15) of one
 // pixel: bias, ReLU, the mask of the source layer, the split of a
-// concatenated input, bf16 rounding; 16-byte stores where aligned.
-__device__ __forceinline__ void epilogue16(const ConvArgs& a, const float* bias, const float* v, int co0, size_t pix) {
+// concatenated input, bf16 rounding; 16-byte stores where aligned.  mvp: the
+// mask words from epi_mask16, or null to load them here.
+__device__ __forceinline__ void epilogue16(const ConvArgs& a, const float* bias, const float* v, int co0, size_t pix,
+                                           const uint4* mvp = nullptr) {
     const int d = (a.ndst > 1 && co0 >= a.dst_split) ? 1 : 0;
     const int cc0 = co0 - (d ? a.dst_split : 0);
     const int dC = a.dst_C[d];
@@ -61,7 +78,7 @@ __device__ __forceinline__ void epilogue16(const ConvArgs& a, const float* bias,
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             uint4 mv = make_uint4(0, 0, 0, 0);
-            if (mk) mv = *reinterpret_cast<const uint4*>(mk + cc0 + 8 * h);
+            if (mk) mv = mvp ? mvp[h] : *reinterpret_cast<const uint4*>(mk + cc0 + 8 * h);
             const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mv);
             __align__(16) __nv_bfloat16 o[8];
 #pragma unroll
@@ -264,12 +281,18 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv(const __grid_constant_
             const bool valid = x < a.W;
             const size_t pix = (static_cast<size_t>(n) * a.H + y) * a.W + x;
             const uint32_t tbase = tmem + buf * static_cast<uint32_t>(a.buf_cols) + (static_cast<uint32_t>(q * 32) << 16);
-            for (int c = 0; c < a.N_tile; c += 16) {
-                float v[16];
-                tmem_ld16(tbase + static_cast<uint32_t>(c), v);
+            for (int c = 0; c < a.N_tile; c += 32) {
+                const bool two = c + 32 <= a.N_tile;        // uniform: the loads are warp-wide
                 const int co0 = n0 + c;
-                if (!valid || co0 >= a.N) continue;
-                epilogue16(a, s_bias, v, co0, pix);
+                uint4 mv[4];
+                if (valid && co0 < a.N) epi_mask16(a, co0, pix, mv);
+                if (valid && two && co0 + 16 < a.N) epi_mask16(a, co0 + 16, pix, mv + 2);
+                float v[32];
+                if (two) tmem_ld32(tbase + static_cast<uint32_t>(c), v);
+                else tmem_ld16(tbase + static_cast<uint32_t>(c), v);
+                if (!valid) continue;
+                if (co0 < a.N) epilogue16(a, s_bias, v, co0, pix, mv);
+                if (two && co0 + 16 < a.N) epilogue16(a, s_bias, v + 16, co0 + 16, pix, mv + 2);
             }
             // this warp's TMEM reads are complete (tcgen05.wait::ld): hand the buffer back
             tc_fence_before();
@@ -478,11 +501,17 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_res(const __grid_const
                 const size_t pix = (static_cast<size_t>(n) * a.H + y) * a.W + x;
                 const uint32_t tbase = tmem + (buf * static_cast<uint32_t>(R) + r) * acc_cols +
                                        (static_cast<uint32_t>(q * 32) << 16);
-                for (int c = 0; c < a.N_tile; c += 16) {
-                    float v[16];
-                    tmem_ld16(tbase + static_cast<uint32_t>(c), v);
-                    if (!valid || c >= a.N) continue;
-                    epilogue16(a, s_bias, v, c, pix);
+                for (int c = 0; c < a.N_tile; c += 32) {
+                    const bool two = c + 32 <= a.N_tile;    // uniform: the loads are warp-wide
+                    uint4 mv[4];
+                    if (valid && c < a.N) epi_mask16(a, c, pix, mv);
+                    if (valid && two && c + 16 < a.N) epi_mask16(a, c + 16, pix, mv + 2);
+                    float v[32];
+                    if (two) tmem_ld32(tbase + static_cast<uint32_t>(c), v);
+                    else tmem_ld16(tbase + static_cast<uint32_t>(c), v);
+                    if (!valid) continue;
+                    if (c < a.N) epilogue16(a, s_bias, v, c, pix, mv);
+                    if (two && c + 16 < a.N) epilogue16(a, s_bias, v + 16, c + 16, pix, mv + 2);
                 }
             }
             tc_fence_before();
@@ -666,19 +695,25 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_dxn(const __grid_const
         float* gx = xch + g * 128;
         const uint32_t ge = static_cast<uint32_t>(GE);
         uint32_t lt = static_cast<uint32_t>(g);
+        bool dead = false;
         for (int t = blockIdx.x + g * gridDim.x; t < total; t += GE * gridDim.x, lt += ge) {
             const uint32_t buf = lt % ge;
-            const bool ok = mbar_wait(&accf[buf], (lt / ge) & 1, a.err, kErrWaitDone);
-            tc_fence_after();
-            __syncwarp();
-            if (!ok || *abort_flag) {
-                *abort_flag = 1u;
-                break;
+            // A warp that gives up (a wait ran out) stays in the loop without
+            // waiting or storing: its group meets at named barriers below, so
+            // every warp of the group must take the same number of them.
+            if (!dead) {
+                const bool ok = mbar_wait(&accf[buf], (lt / ge) & 1, a.err, kErrWaitDone);
+                tc_fence_after();
+                __syncwarp();
+                if (!ok || *abort_flag) {
+                    *abort_flag = 1u;
+                    dead = true;
+                }
             }
             int x0, y, n;
             decode(t, x0, y, n);
             const int x = x0 - 1 + r;
-            const bool valid = r >= 1 && r <= 126 && x < a.W;
+            const bool valid = !dead && r >= 1 && r <= 126 && x < a.W;
             const size_t pix = (static_cast<size_t>(n) * a.H + y) * a.W + (valid ? x : 0);
             const uint32_t tbase = tmem + buf * static_cast<uint32_t>(a.buf_cols) +
                                    (static_cast<uint32_t>(q * 32) << 16);
@@ -708,7 +743,7 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_dxn(const __grid_const
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acce[buf]);
+            if (lane == 0 && !dead) mbar_arrive(&acce[buf]);
         }
     }
     tc_fence_before();
