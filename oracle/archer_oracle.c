@@ -1556,14 +1556,18 @@ static void ctx_geometry(o_ctx* c, const orc_problem* P) {
         c->mat_present[m] = 1;
         if (rho > c->rho_max[m]) c->rho_max[m] = rho;
     }
-    /* macro-cells of M^3 voxels, M the smallest power of two >= 4 giving at
-     * most 4096 cells */
+    /* macro-cells of M^3 voxels, M the smallest power of two >= 4 whose
+     * cells are at least 6 cm along every axis and number at most 4096 (any
+     * majorant that bounds mu along the ray gives the same real collisions;
+     * the size only trades virtual collisions against cell steps) */
     int n[3] = {P->nx, P->ny, P->nz};
+    double vmin = fmin(P->vox[0], fmin(P->vox[1], P->vox[2]));
     int M = 4;
     for (;;) {
         long cells = 1;
         for (int a = 0; a < 3; a++) cells *= (n[a] + M - 1) / M;
-        if (cells <= 4096) break;
+        /* (a cell as large as the whole CT also ends the search) */
+        if (cells <= 4096 && (M * vmin >= 6.0 || (M >= n[0] && M >= n[1] && M >= n[2]))) break;
         M *= 2;
     }
     ctx_macro_grid(c, M);

@@ -1092,11 +1092,16 @@ mc_status mc_init_geometry(mc_ctx* c, const int16_t* hu, int nx, int ny, int nz,
     CUDA_TRY(c, cudaMemcpyAsync(c->thr, c->d_thr, sizeof(c->thr), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
     for (int m = 0; m < 4; ++m) std::memcpy(&c->rho_max[m], &bits[m], sizeof(float));
-    // macro-cells: M the smallest power of two >= 4 giving at most 4096 cells
+    // macro-cells: M the smallest power of two >= 4 whose cells are at least
+    // kMacroCellCm along every axis and number at most 4096 (measured: cells
+    // of ~6 cm beat 3 cm and 13 cm on the 2 mm thorax and the 1 mm
+    // anthropomorphic CT)
     int M = 4;
+    const double vmin = std::fmin(vox_cm[0], std::fmin(vox_cm[1], vox_cm[2]));   // > 0, checked above
     for (;;) {
         const long cells = static_cast<long>((nx + M - 1) / M) * ((ny + M - 1) / M) * ((nz + M - 1) / M);
-        if (cells <= mc::kMaxMacroCells) break;
+        // (a cell as large as the whole CT also ends the search)
+        if (cells <= mc::kMaxMacroCells && (M * vmin >= mc::kMacroCellCm || M >= std::max({nx, ny, nz}))) break;
         M *= 2;
     }
     c->mgM = M;

@@ -30,6 +30,7 @@ constexpr int kPhotonNodes = 2048;
 constexpr int kElectronNodes = 512;
 constexpr int kWentzelNodes = 2048;
 constexpr int kMaxMacroCells = 4096;
+constexpr double kMacroCellCm = 6.0;   // least macro-cell edge (cm) of the Woodcock majorant grid
 // Homogeneous CT voxels (electron steps' second segments may cross their faces):
 // at least kHomRadius voxels inside the CT, one material and an HU span of at
 // most kHomSpan over the (2 kHomRadius + 1)^3 box around them.
