@@ -512,12 +512,12 @@ def main():
     agg = {"kernel_ms": np.zeros(4), "kernel_launches": np.zeros(4), "esteps_ct": 0, "launches": 0}
 
     def step(record):
-        sim.init_geometry(p.phantom, p.epid, stream=stream, hu_device=hu_dev)     # a1
-        sim.set_field(p.field, p.lut, stream=stream)                              # a2 set-up, a9, a10
+        sim.init_geometry(p.phantom, p.epid, stream=stream, hu_device=hu_dev)     # CT set-up
+        sim.set_field(p.field, p.lut, stream=stream)                              # source, t-map, Eq. 1
         sim.set_history_base(rank * N)
-        st = sim.run(N, SEED, stream=stream)                                      # a2-a7
-        sim.dose_device(dose, sigma, stream=stream)                               # a8
-        sim.epid_image_device(signal, stream=stream)                              # a8 + a11
+        st = sim.run(N, SEED, stream=stream)                                      # transport
+        sim.dose_device(dose, sigma, stream=stream)                               # statistics
+        sim.epid_image_device(signal, stream=stream)                              # k(t, s) image
         flush.zero_()
         if record:
             agg["kernel_ms"] += np.array(st["kernel_ms"])

@@ -1,4 +1,4 @@
-"""FP64 reference of the EPID-image denoiser (a14).
+"""FP64 reference of the EPID-image denoiser (the learned denoiser the paper names as future work, Sec. 5).
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, ``__graft_entry__.smoke()`` and
 the CPU legs of ``bench.py``; the CUDA product path never imports it, and it

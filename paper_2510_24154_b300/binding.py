@@ -224,7 +224,7 @@ class Simulator:
 
     # -- set-up -------------------------------------------------------------
     def init_geometry(self, phantom, epid, stream=None, hu_device=None):
-        """a1: HU volume (numpy int16 [nz][ny][nx], or a CUDA int16 tensor via hu_device)."""
+        """CT set-up (Sec. 2.1.2): HU volume (numpy int16 [nz][ny][nx], or a CUDA int16 tensor via hu_device)."""
         nz, ny, nx = phantom.hu.shape
         vox = (C.c_double * 3)(*phantom.vox)
         org = (C.c_double * 3)(*phantom.origin)
@@ -281,7 +281,7 @@ class Simulator:
         return C.byref(L)
 
     def set_field(self, field, lut=None, stream=None):
-        """a2 set-up, a9 t-map, a10 Eq. 1, k-table upload; resets the tally."""
+        """Source set-up (Sec. 2.1.1), t-map (Sec. 2.2), Eq. 1, k-table upload; resets the tally."""
         keep = []
         f = self._field_desc(field, lut, keep)
         lp = self._lut_desc(lut, keep)
@@ -289,7 +289,7 @@ class Simulator:
         self.n_fields = 1
 
     def set_fields(self, fields, lut=None, stream=None):
-        """a12: several fields of one plan (own source, gantry angle, t-map, s and tally each)."""
+        """Several fields of one plan (own source, gantry angle, t-map, s and tally each)."""
         keep = []
         arr = (FieldDesc * len(fields))(*[self._field_desc(f, lut, keep) for f in fields])
         lp = self._lut_desc(lut, keep)
@@ -298,18 +298,18 @@ class Simulator:
 
     # -- transport ------------------------------------------------------------
     def run(self, n_histories, seed, stream=None) -> dict:
-        """a2-a7: transport n_histories more histories; waits and returns the stats."""
+        """Transport (Sec. 2.1) of n_histories more histories; waits and returns the stats."""
         st = RunStats()
         self._check(self.lib.mc_run(self.h, int(n_histories), int(seed), _stream_ptr(stream), C.byref(st)))
         return stats_dict(st)
 
     def run_async(self, n_histories, seed, stream=None) -> None:
-        """a2-a7 queued on `stream` (graph-driven runs return at once); the
+        """Transport (Sec. 2.1) queued on `stream` (graph-driven runs return at once); the
         stats and any device-side failure come from stats()."""
         self._check(self.lib.mc_run(self.h, int(n_histories), int(seed), _stream_ptr(stream), None))
 
     def run_batch(self, n_histories, seed, stream=None) -> dict:
-        """a12: n_histories[f] more histories of every field f, in one wave sequence."""
+        """n_histories[f] more histories of every field f, in one wave sequence."""
         n = (C.c_uint64 * self.n_fields)(*[int(v) for v in n_histories])
         st = RunStats()
         self._check(self.lib.mc_run_batch(self.h, n, int(seed), _stream_ptr(stream), C.byref(st)))
@@ -325,7 +325,7 @@ class Simulator:
         return self.epid.npy, self.epid.npx
 
     def dose(self, stream=None, with_sigma=True, field=0):
-        """a8: (dose, sigma, u) as numpy arrays (Gy per history) and the scalar u."""
+        """Dose statistics (Sec. 2.3): (dose, sigma, u) as numpy arrays (Gy per history) and the scalar u."""
         ny, nx = self._npix()
         d = np.empty((ny, nx))
         s = np.empty((ny, nx)) if with_sigma else None
@@ -366,7 +366,7 @@ class Simulator:
         return m.value, e.value
 
     def epid_image(self, stream=None, field=0):
-        """a11: k(t, s)-corrected signal, float32 numpy [npy][npx]."""
+        """The k(t, s)-corrected signal (Sec. 3.1), float32 numpy [npy][npx]."""
         ny, nx = self._npix()
         out = np.empty((ny, nx), dtype=np.float32)
         self._check(self.lib.mc_get_field_image(self.h, int(field), C.c_void_p(out.ctypes.data), 0,

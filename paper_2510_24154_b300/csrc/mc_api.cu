@@ -736,7 +736,7 @@ mc_status set_fields_impl(mc_ctx* c, const mc_field_desc* f, int n, const mc_lut
     CUDA_TRY(c, cudaMemcpyAsync(c->d_rect, h_rect, sizeof(float4) * rect.size(), cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_cdf, h_cdf, sizeof(double) * cdf.size(), cudaMemcpyHostToDevice, s));
 
-    // radiological thickness map of every field (a9)
+    // radiological thickness map of every field (Sec. 2.2)
     c->t_offset = lut ? lut->t_offset_cm : 0.0;
     const mc_epid_desc& E = c->epid;
     for (int i = 0; i < n; ++i) {

@@ -1,6 +1,7 @@
-// Streaming kernels around the transport: HU -> density (a1), radiological
-// thickness ray sums (a9), dose statistics over the batch sub-tallies (a8) and
-// the k(t, s) dose-to-signal correction (a11), plus two diagnostics.
+// Streaming kernels around the transport: HU -> density (Sec. 2.1.2),
+// radiological thickness ray sums (Sec. 2.2), dose statistics over the batch
+// sub-tallies (Sec. 2.3) and the k(t, s) dose-to-signal correction (Sec. 3.1),
+// plus two diagnostics.
 #include "mc_aux.h"
 
 #include <algorithm>
@@ -8,7 +9,7 @@
 
 namespace mc {
 
-// ------------------------------------------------------------- a1 --------
+// ---------------------------------------------- HU -> density --------
 // HU-to-density curve (Sec. 2.1.2; the curve itself is a stated reading):
 // rho = 1 + HU/1000 for HU <= 0, 1 + 0.6 HU/1000 above, floored at air's
 // 0.001205, HU clamped to [-1024, 3071].  Material follows from density
@@ -100,7 +101,7 @@ __global__ void k_hu_to_rho(const int16_t* __restrict__ hu, float* __restrict__ 
     if (blockIdx.x == 0 && threadIdx.x == 0) { thr[0] = t0; thr[1] = t1; thr[2] = t2; }
 }
 
-// ------------------------------------------------------------- a9 --------
+// ------------------------------------------ radiological thickness ----
 // Radiological thickness (Sec. 2.2, item 1): t = sum_v rho_v l_v along the
 // ray from the source to each pixel centre on the sensitive layer's
 // mid-plane.  Incremental voxel traversal (the Siddon parametrisation walked
@@ -166,7 +167,7 @@ __global__ void k_tmap(TmapArgs A, double* __restrict__ t) {
     t[pix] = acc + A.t_offset;
 }
 
-// ------------------------------------------------------------- a8 --------
+// ------------------------------------------------ dose statistics ----
 // Per pixel: dose per history D = sum_b E_b / N, batch doses D_b = E_b / N_b,
 // sigma = sqrt(sum_b (D_b - D)^2 / (B (B - 1))).  Also the image maximum.
 __global__ void k_dose(const unsigned long long* __restrict__ tally, int npix, int B, const double* __restrict__ nb,
@@ -238,7 +239,7 @@ __global__ void k_u_final(const double* part_sum, const unsigned int* part_cnt, 
     }
 }
 
-// ------------------------------------------------------------ a11 --------
+// ------------------------------------------------- k(t, s) table ----
 // signal = k_scale * k(t, s) * dose.  ks holds the table's column already
 // interpolated at the field's s (the bilinear rule taken one axis at a time);
 // here the per-pixel linear step along t, clamped at the end nodes.

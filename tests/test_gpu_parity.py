@@ -85,7 +85,7 @@ def test_tmap_full_size_sampled_pixels():
 
 
 def test_dose_stats_and_lut_from_gpu_tally():
-    """a8 and a11 on the GPU's own integer tally: dose and sigma to FP64
+    """Dose statistics and the k(t, s) correction on the GPU's own integer tally: dose and sigma to FP64
     rounding, signal to float32 rounding of k(t, s) * dose."""
     for lut in (G.W.lut_bilinear(), G.W.lut_wavy(), G.W.lut_table1()):
         p = G.thorax_case(n=20_000, scale=4, epid_scale=8)
