@@ -101,11 +101,13 @@ struct ConvPlan {
 bool dxn_fits(int k, int N, int nsrc, const int srcC[2]) {
     if (k != 3 || !(N == 32 || N == 64)) return false;
     size_t bytes = 0;
+    int steps = 0;
     for (int s = 0; s < nsrc; ++s) {
         const int CW = cw_for(srcC[s]);
         bytes = (bytes + 1023) / 1024 * 1024 + static_cast<size_t>(3 * chunks(srcC[s], CW)) * 3 * N * CW * 2;
+        steps += 3 * chunks(srcC[s], CW);
     }
-    return bytes <= 150u * 1024u;
+    return bytes <= 150u * 1024u && steps <= dn::kDxnMaxSteps;
 }
 
 bool plan_conv(ConvPlan& P, int nsrc, const bf16* const src[2], const int srcC[2], int Nb, int H, int W, int k,

@@ -32,21 +32,6 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
     return p + ((1024u - (a & 1023u)) & 1023u);
 }
 
-struct KStep {
-    int tap, s, ch;
-};
-
-__device__ __forceinline__ KStep kstep(const ConvArgs& a, int i) {
-    const int chunks = a.src[0].nch + (a.nsrc > 1 ? a.src[1].nch : 0);
-    KStep k;
-    k.tap = i / chunks;
-    const int r = i - k.tap * chunks;
-    k.s = (r < a.src[0].nch) ? 0 : 1;
-    k.ch = k.s ? r - a.src[0].nch : r;
-    return k;
-}
-
-
 // The mask words the vector path of epilogue16 reads for columns co0 ..
 // co0+15 of one pixel, loaded ahead so their latency overlaps the TMEM read.
 __device__ __forceinline__ void epi_mask16(const ConvArgs& a, int co0, size_t pix, uint4* mv) {
@@ -182,27 +167,28 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv(const __grid_constant_
 
     if (warp == 0) {
         if (lane == 0) {
-            uint32_t it = 0;
+            uint32_t it = 0, st = 0, ph = 0;
+            const int nch0 = a.src[0].nch, chunks = nch0 + (a.nsrc > 1 ? a.src[1].nch : 0);
             for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
                 int x0, y, n, n0;
                 decode(t, x0, y, n, n0);
+                int tap = 0, dy = 0, dx = 0, r = 0;          // K step i = (tap, chunk r), counted
                 for (int i = 0; i < a.nk; ++i, ++it) {
-                    const uint32_t st = it % S;
-                    if (it >= static_cast<uint32_t>(S) &&
-                        !mbar_wait(&empty[st], ((it / S) - 1) & 1, a.err, kErrWaitEmpty)) {
+                    if (it >= static_cast<uint32_t>(S) && !mbar_wait(&empty[st], ph ^ 1u, a.err, kErrWaitEmpty)) {
                         *abort_flag = 1u;
                         break;
                     }
-                    const KStep ks = kstep(a, i);
-                    const ConvSrc& src = a.src[ks.s];
+                    const int s_ = r < nch0 ? 0 : 1, ch = s_ ? r - nch0 : r;
+                    const ConvSrc& src = a.src[s_];
                     uint8_t* sa = tiles + st * a.stage_bytes;
                     uint8_t* sb = sa + a.a_region;
                     const uint32_t bytes =
                         (128u + static_cast<uint32_t>(a.N_tile)) * static_cast<uint32_t>(src.CW) * 2u;
                     mbar_expect_tx(&full[st], bytes);
-                    const int dy = ks.tap / a.k, dx = ks.tap - dy * a.k;
-                    tma_load_4d(sa, ks.s ? &ta1 : &ta0, &full[st], ks.ch * src.CW, x0 + dx - p, y + dy - p, n);
-                    tma_load_2d(sb, ks.s ? &tb1 : &tb0, &full[st], (ks.tap * src.nch + ks.ch) * src.CW, n0);
+                    tma_load_4d(sa, s_ ? &ta1 : &ta0, &full[st], ch * src.CW, x0 + dx - p, y + dy - p, n);
+                    tma_load_2d(sb, s_ ? &tb1 : &tb0, &full[st], (tap * src.nch + ch) * src.CW, n0);
+                    if (++st == static_cast<uint32_t>(S)) { st = 0; ph ^= 1u; }
+                    if (++r == chunks) { r = 0; ++tap; if (++dx == a.k) { dx = 0; ++dy; } }
                 }
                 if (*abort_flag) break;
             }
@@ -214,49 +200,61 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv(const __grid_constant_
             }
         }
     } else if (warp <= 3) {
-        // MMA warps 1 .. n_issue: warp 1 + js issues column slice js of every tile
+        // MMA warps 1 .. n_issue: warp 1 + js issues column slice js of every
+        // tile.  The descriptors of stage 0 are built once per source; a stage
+        // adds its offset and each 16-channel slice 32 bytes (2 descriptor
+        // units), so the issuing thread's loop stays short.
         const uint32_t js = static_cast<uint32_t>(warp - 1);
         if (lane == 0 && warp <= a.n_issue) {
-            uint32_t it = 0, lt = 0;
-            uint32_t commits[kConvMaxGroups] = {0u, 0u, 0u, 0u};
+            const uint32_t t0 = smem_u32(tiles);
+            uint64_t da_s[2], db_s[2];
+            int n16_s[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int CW = a.src[q < a.nsrc ? q : 0].CW;
+                const uint32_t row = static_cast<uint32_t>(CW) * 2u, swz = swz_for_row(row);
+                da_s[q] = smem_desc(t0, 16u, 8u * row, swz);
+                db_s[q] = smem_desc(t0 + a.a_region + js * static_cast<uint32_t>(a.n_slice) * row, 16u, 8u * row, swz);
+                n16_s[q] = CW / 16;
+            }
+            const uint64_t stage_units = a.stage_bytes >> 4;
+            const int nch0 = a.src[0].nch, chunks = nch0 + (a.nsrc > 1 ? a.src[1].nch : 0);
+            uint32_t st = 0, ph = 0, lt = 0, buf = 0, bph = 0, ncommit = 0;
             const uint32_t ge = static_cast<uint32_t>(GE);
             for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++lt) {
-                const uint32_t buf = lt % ge;
-                if (lt >= ge && !mbar_wait(&acce[buf], ((lt / ge) - 1) & 1, a.err, kErrWaitEmpty)) {
+                if (lt >= ge && !mbar_wait(&acce[buf], bph ^ 1u, a.err, kErrWaitEmpty)) {
                     *abort_flag = 1u;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem + buf * static_cast<uint32_t>(a.buf_cols);
-                for (int i = 0; i < a.nk; ++i, ++it) {
-                    const uint32_t st = it % S;
-                    if (!mbar_wait(&full[st], (it / S) & 1, a.err, kErrWaitFull)) {
+                const uint32_t dj = tmem + buf * static_cast<uint32_t>(a.buf_cols) + js * static_cast<uint32_t>(a.n_slice);
+                int r = 0;                                   // chunk within the tap
+                for (int i = 0; i < a.nk; ++i) {
+                    if (!mbar_wait(&full[st], ph, a.err, kErrWaitFull)) {
                         *abort_flag = 1u;
                         break;
                     }
                     tc_fence_after();
-                    const KStep ks = kstep(a, i);
-                    const int CW = a.src[ks.s].CW;
-                    const uint32_t sa = smem_u32(tiles + st * a.stage_bytes);
-                    const uint32_t sb = sa + a.a_region;
-                    const uint32_t row = static_cast<uint32_t>(CW) * 2u;
-                    const uint32_t swz = swz_for_row(row);
-                    const uint32_t sbj = sb + js * static_cast<uint32_t>(a.n_slice) * row;
-                    const uint32_t dj = d + js * static_cast<uint32_t>(a.n_slice);
-                    for (int kk = 0; kk < CW / 16; ++kk) {
-                        const uint64_t da = smem_desc(sa + kk * 32u, 16u, 8u * row, swz);
-                        const uint64_t db = smem_desc(sbj + kk * 32u, 16u, 8u * row, swz);
-                        tc_mma(dj, da, db, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                    }
+                    const bool s1 = r >= nch0;
+                    const uint64_t off = st * stage_units;
+                    const uint64_t da = (s1 ? da_s[1] : da_s[0]) + off, db = (s1 ? db_s[1] : db_s[0]) + off;
+                    const int n16 = s1 ? n16_s[1] : n16_s[0];
+                    for (int kk = 0; kk < n16; ++kk)
+                        tc_mma(dj, da + 2u * kk, db + 2u * kk, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
                     tc_commit(&empty[st]);
+                    if (++st == static_cast<uint32_t>(S)) { st = 0; ph ^= 1u; }
+                    if (++r == chunks) r = 0;
                 }
                 tc_commit(&accf[buf]);   // also covers a tile cut short by an abort
-                ++commits[buf];
+                ++ncommit;
+                if (++buf == ge) { buf = 0; bph ^= 1u; }
                 if (*abort_flag) break;
             }
             // no MMA of this CTA may still run when its TMEM is freed
-            for (int b = 0; b < GE; ++b)
-                if (commits[b]) mbar_wait(&accf[b], (commits[b] - 1) & 1, a.err, kErrWaitTail);
+            for (uint32_t b = 0; b < ge && b < ncommit; ++b) {
+                const uint32_t uses = (ncommit - b + ge - 1) / ge;
+                mbar_wait(&accf[b], (uses - 1) & 1u, a.err, kErrWaitTail);
+            }
         }
     } else {
         // epilogue: warps 4 + 4g .. 7 + 4g drain buffer g (the tiles lt with
@@ -373,15 +371,8 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_res(const __grid_const
         n = r / groups;
         x0 = xs << 7;
     };
-    // K step i of a tile -> (input row j, column shift dx, source s, chunk c)
-    auto step = [&](int i, int& j, int& dx, int& s_, int& c) {
-        const int r = i % chunks;
-        const int jd = i / chunks;
-        j = jd / k;
-        dx = jd - j * k;
-        s_ = r < a.src[0].nch ? 0 : 1;
-        c = s_ ? r - a.src[0].nch : r;
-    };
+    // K step i of a tile is (input row j, column shift dx, chunk over both
+    // sources), chunk fastest: the producer and the MMA warps count them
 
     if (warp == 0) {
         if (lane == 0) {
@@ -395,23 +386,24 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_res(const __grid_const
                         tma_load_2d(wsm + a.w_off[s_] + (t * src.nch + c) * tile_bytes, s_ ? &tb1 : &tb0, wbar,
                                     (t * src.nch + c) * src.CW, 0);
             }
-            uint32_t it = 0;
+            uint32_t it = 0, st = 0, ph = 0;
+            const int nch0 = a.src[0].nch;
             for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
                 int x0, y0, n;
                 decode(t, x0, y0, n);
+                int j = 0, dx = 0, rr = 0;                   // K step i = (input row, shift, chunk), counted
                 for (int i = 0; i < steps; ++i, ++it) {
-                    const uint32_t st = it % S;
-                    if (it >= static_cast<uint32_t>(S) &&
-                        !mbar_wait(&empty[st], ((it / S) - 1) & 1, a.err, kErrWaitEmpty)) {
+                    if (it >= static_cast<uint32_t>(S) && !mbar_wait(&empty[st], ph ^ 1u, a.err, kErrWaitEmpty)) {
                         *abort_flag = 1u;
                         break;
                     }
-                    int j, dx, s_, c;
-                    step(i, j, dx, s_, c);
+                    const int s_ = rr < nch0 ? 0 : 1, c = s_ ? rr - nch0 : rr;
                     const ConvSrc& src = a.src[s_];
                     mbar_expect_tx(&full[st], 128u * static_cast<uint32_t>(src.CW) * 2u);
                     tma_load_4d(tiles + st * a.stage_bytes, s_ ? &ta1 : &ta0, &full[st], c * src.CW, x0 + dx - p,
                                 y0 - p + j, n);
+                    if (++st == static_cast<uint32_t>(S)) { st = 0; ph ^= 1u; }
+                    if (++rr == chunks) { rr = 0; if (++dx == k) { dx = 0; ++j; } }
                 }
                 if (*abort_flag) break;
             }
@@ -423,59 +415,74 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_res(const __grid_const
             mbar_wait(wbar, 0, a.err, kErrWaitTail);
         }
     } else if (warp <= 3) {
-        // MMA warps 1 .. n_issue: warp 1 + js issues column slice js of every tile
+        // MMA warps 1 .. n_issue: warp 1 + js issues column slice js of every
+        // tile.  Descriptors are built once per source (activation stage 0,
+        // this slice's weights of tap 0, chunk 0) and advanced by offsets; the
+        // K step's (input row, column shift, chunk) is counted, not divided out.
         const uint32_t js = static_cast<uint32_t>(warp - 1);
         if (lane == 0 && warp <= a.n_issue) {
+            const uint32_t t0 = smem_u32(tiles), wbase = smem_u32(wsm);
+            uint64_t da_s[2], dw_s[2], tb_s[2];
+            int n16_s[2], nch_s[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const ConvSrc& src = a.src[q < a.nsrc ? q : 0];
+                const uint32_t row = static_cast<uint32_t>(src.CW) * 2u, swz = swz_for_row(row);
+                da_s[q] = smem_desc(t0, 16u, 8u * row, swz);
+                dw_s[q] = smem_desc(wbase + a.w_off[q < a.nsrc ? q : 0] + js * static_cast<uint32_t>(a.n_slice) * row,
+                                    16u, 8u * row, swz);
+                tb_s[q] = (static_cast<uint64_t>(a.N_tile) * row) >> 4;   // one weight box, descriptor units
+                n16_s[q] = src.CW / 16;
+                nch_s[q] = src.nch;
+            }
+            const uint64_t stage_units = a.stage_bytes >> 4;
+            const int nch0 = a.src[0].nch;
             const bool wok = mbar_wait(wbar, 0, a.err, kErrWaitFull);
             if (!wok) *abort_flag = 1u;
             tc_fence_after();
-            uint32_t it = 0, lt = 0;
-            uint32_t commits[kConvMaxGroups] = {0u, 0u, 0u, 0u};
-            const uint32_t wbase = smem_u32(wsm);
+            uint32_t st = 0, ph = 0, lt = 0, buf = 0, bph = 0, ncommit = 0;
             const uint32_t ge = static_cast<uint32_t>(GE);
             for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++lt) {
-                const uint32_t buf = lt % ge;
-                if (lt >= ge && !mbar_wait(&acce[buf], ((lt / ge) - 1) & 1, a.err, kErrWaitEmpty)) {
+                if (lt >= ge && !mbar_wait(&acce[buf], bph ^ 1u, a.err, kErrWaitEmpty)) {
                     *abort_flag = 1u;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d0 = tmem + buf * static_cast<uint32_t>(R) * acc_cols;
-                for (int i = 0; i < steps; ++i, ++it) {
-                    const uint32_t st = it % S;
-                    if (!mbar_wait(&full[st], (it / S) & 1, a.err, kErrWaitFull)) {
+                const uint32_t d0 = tmem + buf * static_cast<uint32_t>(R) * acc_cols + js * static_cast<uint32_t>(a.n_slice);
+                int j = 0, dx = 0, rr = 0;                   // input row, column shift, chunk (all sources)
+                for (int i = 0; i < steps; ++i) {
+                    if (!mbar_wait(&full[st], ph, a.err, kErrWaitFull)) {
                         *abort_flag = 1u;
                         break;
                     }
                     tc_fence_after();
-                    int j, dx, s_, c;
-                    step(i, j, dx, s_, c);
-                    const ConvSrc& src = a.src[s_];
-                    const uint32_t row = static_cast<uint32_t>(src.CW) * 2u;
-                    const uint32_t swz = swz_for_row(row);
-                    const uint32_t sa = smem_u32(tiles + st * a.stage_bytes);
-                    const uint32_t tile_bytes = static_cast<uint32_t>(a.N_tile) * row;
+                    const bool s1 = rr >= nch0;
+                    const int c = s1 ? rr - nch0 : rr;
+                    const uint64_t da = (s1 ? da_s[1] : da_s[0]) + st * stage_units;
+                    const uint64_t dw = s1 ? dw_s[1] : dw_s[0], tb = s1 ? tb_s[1] : tb_s[0];
+                    const int n16 = s1 ? n16_s[1] : n16_s[0], nch = s1 ? nch_s[1] : nch_s[0];
                     for (int dy = 0; dy < k; ++dy) {
                         const int r = j - dy;
                         if (r < 0 || r >= R) continue;
-                        const uint32_t wt = wbase + a.w_off[s_] + ((dy * k + dx) * src.nch + c) * tile_bytes +
-                                            js * static_cast<uint32_t>(a.n_slice) * row;
-                        const bool first = (dy == 0 && dx == 0 && s_ == 0 && c == 0);
-                        const uint32_t dr = d0 + static_cast<uint32_t>(r) * acc_cols + js * static_cast<uint32_t>(a.n_slice);
-                        for (int kk = 0; kk < src.CW / 16; ++kk) {
-                            const uint64_t da = smem_desc(sa + kk * 32u, 16u, 8u * row, swz);
-                            const uint64_t db = smem_desc(wt + kk * 32u, 16u, 8u * row, swz);
-                            tc_mma(dr, da, db, a.idesc, (first && kk == 0) ? 0u : 1u);
-                        }
+                        const uint64_t db = dw + static_cast<uint64_t>((dy * k + dx) * nch + c) * tb;
+                        const bool first = (dy == 0 && dx == 0 && rr == 0);
+                        const uint32_t dr = d0 + static_cast<uint32_t>(r) * acc_cols;
+                        for (int kk = 0; kk < n16; ++kk)
+                            tc_mma(dr, da + 2u * kk, db + 2u * kk, a.idesc, (first && kk == 0) ? 0u : 1u);
                     }
                     tc_commit(&empty[st]);
+                    if (++st == static_cast<uint32_t>(S)) { st = 0; ph ^= 1u; }
+                    if (++rr == chunks) { rr = 0; if (++dx == k) { dx = 0; ++j; } }
                 }
                 tc_commit(&accf[buf]);
-                ++commits[buf];
+                ++ncommit;
+                if (++buf == ge) { buf = 0; bph ^= 1u; }
                 if (*abort_flag) break;
             }
-            for (int b = 0; b < GE; ++b)
-                if (commits[b]) mbar_wait(&accf[b], (commits[b] - 1) & 1, a.err, kErrWaitTail);
+            for (uint32_t b = 0; b < ge && b < ncommit; ++b) {
+                const uint32_t uses = (ncommit - b + ge - 1) / ge;
+                mbar_wait(&accf[b], (uses - 1) & 1u, a.err, kErrWaitTail);
+            }
         }
     } else {
         const int g = (warp - 4) >> 2;             // epilogue group = accumulator buffer
@@ -553,6 +560,8 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_dxn(const __grid_const
     volatile uint32_t* abort_flag = tslot + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ float s_bias[kConvMaxN];                  // the epilogue's bias, read once
+    __shared__ uint64_t s_da[3][kDxnMaxSteps], s_db[3][kDxnMaxSteps];   // per MMA warp and K step
+    __shared__ uint8_t s_nkk[3][kDxnMaxSteps];
     if (a.bias)
         for (int i = threadIdx.x; i < a.N; i += blockDim.x) s_bias[i] = __ldg(&a.bias[i]);
 
@@ -613,23 +622,24 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_dxn(const __grid_const
                         tma_load_2d(wsm + a.w_off[s_] + (dy * src.nch + c) * tile_bytes, s_ ? &tb1 : &tb0, wbar,
                                     (dy * src.nch + c) * src.CW, 0);
             }
-            uint32_t it = 0;
+            uint32_t it = 0, st = 0, ph = 0;
+            const int nch0 = a.src[0].nch;
             for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
                 int x0, y, n;
                 decode(t, x0, y, n);
+                int dy = 0, rr = 0;                          // K step i = (row tap, chunk), counted
                 for (int i = 0; i < steps; ++i, ++it) {
-                    const uint32_t st = it % S;
-                    if (it >= static_cast<uint32_t>(S) &&
-                        !mbar_wait(&empty[st], ((it / S) - 1) & 1, a.err, kErrWaitEmpty)) {
+                    if (it >= static_cast<uint32_t>(S) && !mbar_wait(&empty[st], ph ^ 1u, a.err, kErrWaitEmpty)) {
                         *abort_flag = 1u;
                         break;
                     }
-                    int dy, s_, c;
-                    step(i, dy, s_, c);
+                    const int s_ = rr < nch0 ? 0 : 1, c = s_ ? rr - nch0 : rr;
                     const ConvSrc& src = a.src[s_];
                     mbar_expect_tx(&full[st], 128u * static_cast<uint32_t>(src.CW) * 2u);
                     tma_load_4d(tiles + st * a.stage_bytes, s_ ? &ta1 : &ta0, &full[st], c * src.CW, x0 - 1,
                                 y + dy - 1, n);
+                    if (++st == static_cast<uint32_t>(S)) { st = 0; ph ^= 1u; }
+                    if (++rr == chunks) { rr = 0; ++dy; }
                 }
                 if (*abort_flag) break;
             }
@@ -641,52 +651,67 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_dxn(const __grid_const
             mbar_wait(wbar, 0, a.err, kErrWaitTail);
         }
     } else if (warp <= 3) {
-        // MMA warps 1 .. n_issue: warp 1 + js issues column slice js of every tile
+        // MMA warps 1 .. n_issue: warp 1 + js issues column slice js of every tile.
+        // The issuing thread shares its scheduler with busy epilogue warps, so
+        // its loop is kept short: the descriptors of every K step (A in stage
+        // 0, B of this slice) are built once, a stage adds its offset and each
+        // 16-channel slice 32 bytes (2 descriptor units).
         const uint32_t js = static_cast<uint32_t>(warp - 1);
         if (lane == 0 && warp <= a.n_issue) {
+            uint64_t* da0 = s_da[js];
+            uint64_t* db0 = s_db[js];
+            uint8_t* nkk = s_nkk[js];
+            const uint32_t wbase = smem_u32(wsm);
+            const uint32_t tbase_a = smem_u32(tiles);
+            for (int i = 0; i < steps; ++i) {
+                int dy, s_, c;
+                step(i, dy, s_, c);
+                const ConvSrc& src = a.src[s_];
+                const uint32_t row = static_cast<uint32_t>(src.CW) * 2u;
+                const uint32_t swz = swz_for_row(row);
+                const uint32_t wt = wbase + a.w_off[s_] + (dy * src.nch + c) * (static_cast<uint32_t>(N3) * row) +
+                                    js * static_cast<uint32_t>(a.n_slice) * row;
+                da0[i] = smem_desc(tbase_a, 16u, 8u * row, swz);
+                db0[i] = smem_desc(wt, 16u, 8u * row, swz);
+                nkk[i] = static_cast<uint8_t>(src.CW / 16);
+            }
+            const uint64_t stage_units = a.stage_bytes >> 4;
             if (!mbar_wait(wbar, 0, a.err, kErrWaitFull)) *abort_flag = 1u;
             tc_fence_after();
-            uint32_t it = 0, lt = 0;
-            uint32_t commits[kConvMaxGroups] = {0u, 0u, 0u, 0u};
-            const uint32_t wbase = smem_u32(wsm);
+            uint32_t st = 0, ph = 0, lt = 0, buf = 0, bph = 0, ncommit = 0;
             const uint32_t ge = static_cast<uint32_t>(GE);
             for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++lt) {
-                const uint32_t buf = lt % ge;
-                if (lt >= ge && !mbar_wait(&acce[buf], ((lt / ge) - 1) & 1, a.err, kErrWaitEmpty)) {
+                if (lt >= ge && !mbar_wait(&acce[buf], bph ^ 1u, a.err, kErrWaitEmpty)) {
                     *abort_flag = 1u;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem + buf * static_cast<uint32_t>(a.buf_cols);
-                for (int i = 0; i < steps; ++i, ++it) {
-                    const uint32_t st = it % S;
-                    if (!mbar_wait(&full[st], (it / S) & 1, a.err, kErrWaitFull)) {
+                const uint32_t dj = tmem + buf * static_cast<uint32_t>(a.buf_cols) + js * static_cast<uint32_t>(a.n_slice);
+                for (int i = 0; i < steps; ++i) {
+                    if (!mbar_wait(&full[st], ph, a.err, kErrWaitFull)) {
                         *abort_flag = 1u;
                         break;
                     }
                     tc_fence_after();
-                    int dy, s_, c;
-                    step(i, dy, s_, c);
-                    const ConvSrc& src = a.src[s_];
-                    const uint32_t row = static_cast<uint32_t>(src.CW) * 2u;
-                    const uint32_t swz = swz_for_row(row);
-                    const uint32_t sa = smem_u32(tiles + st * a.stage_bytes);
-                    const uint32_t wt = wbase + a.w_off[s_] + (dy * src.nch + c) * (static_cast<uint32_t>(N3) * row) +
-                                        js * static_cast<uint32_t>(a.n_slice) * row;
-                    const uint32_t dj = d + js * static_cast<uint32_t>(a.n_slice);
-                    for (int kk = 0; kk < src.CW / 16; ++kk) {
-                        const uint64_t da = smem_desc(sa + kk * 32u, 16u, 8u * row, swz);
-                        const uint64_t db = smem_desc(wt + kk * 32u, 16u, 8u * row, swz);
-                        tc_mma(dj, da, db, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                    }
+                    const uint64_t da = da0[i] + st * stage_units, db = db0[i];
+                    const int n16 = nkk[i];
+                    for (int kk = 0; kk < n16; ++kk)
+                        tc_mma(dj, da + 2u * kk, db + 2u * kk, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
                     tc_commit(&empty[st]);
+                    if (++st == static_cast<uint32_t>(S)) { st = 0; ph ^= 1u; }
                 }
-                tc_commit(&accf[buf]);
-                ++commits[buf];
+                tc_commit(&accf[buf]);            // also covers a tile cut short by an abort
+                ++ncommit;
+                if (++buf == ge) { buf = 0; bph ^= 1u; }
                 if (*abort_flag) break;
             }
-            for (int b = 0; b < GE; ++b)
-                if (commits[b]) mbar_wait(&accf[b], (commits[b] - 1) & 1, a.err, kErrWaitTail);
+            // no MMA of this CTA may still run when its TMEM is freed: wait for
+            // the last commit of every buffer used (commits j < ncommit with
+            // j mod ge = b)
+            for (uint32_t b = 0; b < ge && b < ncommit; ++b) {
+                const uint32_t uses = (ncommit - b + ge - 1) / ge;
+                mbar_wait(&accf[b], (uses - 1) & 1u, a.err, kErrWaitTail);
+            }
         }
     } else {
         const int g = (warp - 4) >> 2;          // epilogue group = accumulator buffer

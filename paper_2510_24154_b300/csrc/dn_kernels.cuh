@@ -59,6 +59,8 @@ struct ConvArgs {
 constexpr int kConvMaxGroups = 4;
 constexpr int kConvMaxN = 512;      // output channels of one convolution
 constexpr int kConvMaxThreads = 32 * (4 + 4 * kConvMaxGroups);
+// Column-tap convolution: K steps per tile (3 row taps x channel chunks) at most.
+constexpr int kDxnMaxSteps = 24;
 
 // MMA-issuing warps of the weight-gradient kernel (see k_wgrad).
 constexpr int kWgradIssuers = 3;
