@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_dxn(const __grid_const
     uint64_t* acce = accf + GE;
     uint64_t* wbar = acce + GE;
     float* xch = reinterpret_cast<float*>(wbar + 1);     // [groups][2 sides][4 warps][16]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(xch + GE * 2 * 4 * 16);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(xch + GE * 2 * 2 * 4 * 16);
     volatile uint32_t* abort_flag = tslot + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ float s_bias[kConvMaxN];                  // the epilogue's bias, read once
@@ -717,7 +717,8 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_dxn(const __grid_const
         const int g = (warp - 4) >> 2;          // epilogue group = accumulator buffer
         const int q = warp & 3;                 // TMEM lane quarter: rows 32q .. 32q+31
         const int r = q * 32 + lane;
-        float* gx = xch + g * 128;
+        float* gx0 = xch + g * 256;
+        uint32_t xb = 0;
         const uint32_t ge = static_cast<uint32_t>(GE);
         uint32_t lt = static_cast<uint32_t>(g);
         bool dead = false;
@@ -744,10 +745,12 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_dxn(const __grid_const
                                    (static_cast<uint32_t>(q * 32) << 16);
             for (int c = 0; c < N; c += 16) {
                 float v0[16], v1[16], v2[16], o[16];
-                tmem_ld16(tbase + static_cast<uint32_t>(c), v0);
-                tmem_ld16(tbase + static_cast<uint32_t>(N + c), v1);
-                tmem_ld16(tbase + static_cast<uint32_t>(2 * N + c), v2);
-                // rows 32q-1 and 32q+32 live in the neighbouring warps
+                tmem_ld16x3(tbase + static_cast<uint32_t>(c), tbase + static_cast<uint32_t>(N + c),
+                            tbase + static_cast<uint32_t>(2 * N + c), v0, v1, v2);
+                // rows 32q-1 and 32q+32 live in the neighbouring warps; the
+                // exchange buffers alternate, so one barrier per chunk suffices
+                float* gx = gx0 + (xb & 1u) * 128;
+                ++xb;
                 if (lane == 31)
 #pragma unroll
                     for (int j = 0; j < 16; ++j) gx[(0 * 4 + q) * 16 + j] = v0[j];
@@ -763,7 +766,6 @@ __global__ void __launch_bounds__(kConvMaxThreads) k_conv_dxn(const __grid_const
                     if (lane == 31) right = q < 3 ? gx[(1 * 4 + q + 1) * 16 + j] : 0.0f;
                     o[j] = left + v1[j] + right;
                 }
-                asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
                 if (valid) epilogue16(a, s_bias, o, c, pix);
             }
             tc_fence_before();
@@ -1265,7 +1267,7 @@ cudaError_t launch_conv(const CUtensorMap* ta, const CUtensorMap* tb, const Conv
         const long long total = static_cast<long long>((a.W + 125) / 126) * a.H * a.Nb;
         const int grid = static_cast<int>(std::min<long long>(total, a.grid));
         const size_t smem = 1024 + a.w_bytes + static_cast<size_t>(a.stages) * a.stage_bytes +
-                            (2 * a.stages + 2 * a.epi_groups + 1) * 8 + a.epi_groups * 2 * 4 * 16 * 4 + 16;
+                            (2 * a.stages + 2 * a.epi_groups + 1) * 8 + a.epi_groups * 2 * 2 * 4 * 16 * 4 + 16;
         k_conv_dxn<<<grid, 32 * (4 + 4 * a.epi_groups), smem, s>>>(ta[0], ta[a.nsrc > 1 ? 1 : 0], tb[0],
                                                                  tb[a.nsrc > 1 ? 1 : 0], a);
         return cudaGetLastError();
