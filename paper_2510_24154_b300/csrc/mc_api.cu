@@ -92,6 +92,7 @@ struct mc_ctx {
     FieldDev* d_fields = nullptr;
     unsigned long long* d_first = nullptr;
     float4* d_rect = nullptr;
+    uint32_t* d_guide = nullptr;             // cut-point tables of the source CDFs
     double* d_cdf = nullptr;
     unsigned char* d_rflag = nullptr;   // per rectangle: collimator slabs its photons cross
     double* d_tmap = nullptr;    // [F][npix]
@@ -142,6 +143,7 @@ struct mc_ctx {
     size_t h_stage_cap = 0;
     cudaEvent_t ev_stage = nullptr;            // recorded after the last copies out of h_stage
     // field buffers are kept while large enough: their capacities in elements
+    size_t cap_guide = 0;
     size_t cap_tally = 0, cap_pix = 0, cap_parts = 0, cap_rect = 0, cap_cdf = 0, cap_tmap = 0, cap_lut_t = 0,
            cap_ks = 0, cap_rflag = 0;
 };
@@ -184,6 +186,7 @@ void clear_fields(mc_ctx* c) {
 
 void free_field_buffers(mc_ctx* c) {
     dfree(c->d_rect);
+    dfree(c->d_guide);
     dfree(c->d_cdf);
     dfree(c->d_rflag);
     dfree(c->d_tmap);
@@ -198,6 +201,7 @@ void free_field_buffers(mc_ctx* c) {
     dfree(c->d_tally);
     c->cap_tally = c->cap_pix = c->cap_parts = c->cap_rect = c->cap_cdf = c->cap_tmap = c->cap_lut_t = c->cap_ks = 0;
     c->cap_rflag = 0;
+    c->cap_guide = 0;
     clear_fields(c);
 }
 
@@ -287,7 +291,7 @@ void make_params(const mc_ctx* c, Params& P, uint64_t seed) {
         P.lmat[l] = E.material[l];
         P.lrho[l] = static_cast<float>(E.density[l]);
     }
-    P.rect = c->d_rect; P.cdf = c->d_cdf; P.rflag = c->d_rflag;
+    P.rect = c->d_rect; P.cdf = c->d_cdf; P.guide = c->d_guide; P.rflag = c->d_rflag;
     {
         const mcphys::MaterialCoefs w = mcphys::tungsten_coefs();
         P.wmat = {static_cast<float>(w.ne_barn), static_cast<float>(w.pe_above), static_cast<float>(w.pe_below),
@@ -681,6 +685,7 @@ mc_status set_fields_impl(mc_ctx* c, const mc_field_desc* f, int n, const mc_lut
     // previous run to have finished with it.
     const bool grow = tally_n > c->cap_tally || static_cast<size_t>(np) > c->cap_pix || parts > c->cap_parts ||
                       rect.size() > c->cap_rect || cdf.size() > c->cap_cdf || rflag.size() > c->cap_rflag ||
+                      rect.size() > c->cap_guide ||
                       static_cast<size_t>(n) * np > c->cap_tmap || (lut && (static_cast<size_t>(lut->nt) > c->cap_lut_t ||
                                                                              nks > c->cap_ks));
     if (grow) {
@@ -710,11 +715,25 @@ mc_status set_fields_impl(mc_ctx* c, const mc_field_desc* f, int n, const mc_lut
     CUDA_TRY(c, ensure(c->d_rect, c->cap_rect, rect.size()));
     CUDA_TRY(c, ensure(c->d_cdf, c->cap_cdf, cdf.size()));
     CUDA_TRY(c, ensure(c->d_rflag, c->cap_rflag, rflag.size()));
+    CUDA_TRY(c, ensure(c->d_guide, c->cap_guide, rect.size()));
     CUDA_TRY(c, ensure(c->d_tmap, c->cap_tmap, static_cast<size_t>(n) * np));
     // host data to the device through pinned staging, so the copies need no
     // wait here; the staging is reused once the previous copies out of it ended
+    // cut points of every field's CDF: the source search starts at
+    // guide[floor(xi n)] and scans to the first rectangle whose cumulative
+    // weight exceeds xi, the same rectangle a binary search finds
+    std::vector<uint32_t> guide(rect.size());
+    for (int i = 0; i < n; ++i) {
+        const int off = fh[i].rect_off, nr = fh[i].n_rect;
+        int r = 0;
+        for (int j = 0; j < nr; ++j) {
+            const double u = static_cast<double>(j) / nr;
+            while (r < nr - 1 && u >= cdf[off + r]) ++r;
+            guide[off + j] = static_cast<uint32_t>(r);
+        }
+    }
     const size_t stage_bytes = sizeof(float4) * rect.size() + sizeof(double) * (cdf.size() + nks + (lut ? lut->nt : 0)) +
-                               rflag.size();
+                               sizeof(uint32_t) * guide.size() + rflag.size();
     CUDA_TRY(c, cudaEventSynchronize(c->ev_stage));
     if (stage_bytes > c->h_stage_cap) {
         if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -728,7 +747,10 @@ mc_status set_fields_impl(mc_ctx* c, const mc_field_desc* f, int n, const mc_lut
     double* h_cdf = reinterpret_cast<double*>(stage + sizeof(float4) * rect.size());
     double* h_ks = h_cdf + cdf.size();
     double* h_lut_t = h_ks + nks;
-    unsigned char* h_rflag = reinterpret_cast<unsigned char*>(h_lut_t + (lut ? lut->nt : 0));
+    uint32_t* h_guide = reinterpret_cast<uint32_t*>(h_lut_t + (lut ? lut->nt : 0));
+    unsigned char* h_rflag = reinterpret_cast<unsigned char*>(h_guide + guide.size());
+    std::memcpy(h_guide, guide.data(), sizeof(uint32_t) * guide.size());
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_guide, h_guide, sizeof(uint32_t) * guide.size(), cudaMemcpyHostToDevice, s));
     std::memcpy(h_rect, rect.data(), sizeof(float4) * rect.size());
     std::memcpy(h_cdf, cdf.data(), sizeof(double) * cdf.size());
     std::memcpy(h_rflag, rflag.data(), rflag.size());

@@ -126,6 +126,9 @@ struct Params {
     // source: rectangles and cumulative weights of all fields, concatenated
     const float4* rect;
     const double* cdf;
+    // per field, n_rect cut points: guide[rect_off + j] = the first rectangle
+    // whose cumulative weight exceeds j / n_rect (where the search starts)
+    const uint32_t* guide;
     const unsigned char* rflag;     // per rectangle: bit 0 behind a closed leaf, bit 1 outside the jaws (slabs)
     float e_max, mono_e;
     MatC wmat;                      // tungsten of the collimator slabs (photon coefficients)

@@ -803,12 +803,14 @@ __device__ __forceinline__ bool start_primary(const Params& P, unsigned long lon
     float bx = 0.0f, by = 0.0f, bz = F.sad, bu = 0.0f, bv = 0.0f, bw = -1.0f;
     bool got = false, scattered = false;
     for (int k = 0; k < kPs1Cap && !got; ++k) {
+        // the first rectangle whose cumulative weight exceeds xi (the last if
+        // none does): from the cut point of xi, scanned either way, so the
+        // result is exactly that of a binary search over the CDF
         const double xi = static_cast<double>(p.rng.u());
-        int lo = 0, hi = F.n_rect - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (xi < __ldg(&P.cdf[F.rect_off + mid])) hi = mid; else lo = mid + 1;
-        }
+        const double* cdf = P.cdf + F.rect_off;
+        int lo = __ldg(&P.guide[F.rect_off + min(static_cast<int>(xi * F.n_rect), F.n_rect - 1)]);
+        while (lo > 0 && xi < __ldg(&cdf[lo - 1])) --lo;
+        while (lo < F.n_rect - 1 && xi >= __ldg(&cdf[lo])) ++lo;
         const float4 r = __ldg(&P.rect[F.rect_off + lo]);
         const float X = r.x + (r.y - r.x) * p.rng.u();
         const float Y = r.z + (r.w - r.z) * p.rng.u();
