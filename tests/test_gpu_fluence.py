@@ -79,3 +79,41 @@ def test_fluence_matches_sampled_source_positions(modifiers):
     # the map mirrored about the image centre fails the same comparison
     zt = (counts[sel] - n * Fa[::-1, ::-1][sel] * area) / np.sqrt(expect[sel])
     assert zt.std() > 3
+
+
+def test_fluence_and_region_dose_of_every_field_of_a_batch():
+    """In a two-field batch each field's fluence equals that of the field
+    set up alone, and the region statistic of field 1 is that of its own
+    sub-tallies (the other field's histories do not enter it)."""
+    from paper_2510_24154_b300 import calibration as CAL
+    ep = W.epid_default(96, 80, 0.45)
+    f0 = W.imrt_field(np.random.default_rng(3), 4, gantry_deg=0.0)
+    f1 = W.imrt_field(np.random.default_rng(4), 7, gantry_deg=90.0)
+    f1.tg_width, f1.leaf_gap = 0.1, 0.06
+    prob = W.config_water_open(npx=96, npy=80, pitch=0.45)
+    sim = Simulator(prob.physics)
+    try:
+        sim.init_geometry(prob.phantom, ep)
+        sim.set_fields([f0, f1])
+        both = [sim.fluence(field=f) for f in range(2)]
+        for f, fld in enumerate((f0, f1)):
+            sim.set_field(fld)
+            assert np.allclose(both[f], sim.fluence(), rtol=1e-12, atol=0)
+        sim.set_fields([f0, f1])
+        sim.run_batch([20_000, 30_000], 9)
+        tally = sim.tally(field=1).astype(np.float64) / 2.56e8
+        B = tally.shape[0]
+        nb = oracle.batch_counts(30_000, B).astype(float)
+        _, thick, rho = ep.layers[ep.sensitive]
+        conv = 1.602176634e-13 / (rho * ep.pitch ** 2 * thick * 1e-3)
+        ix0, ix1, iy0, iy1 = CAL.central_rect(ep, half_cm=3.0)
+        reg = tally[:, iy0:iy1, ix0:ix1].reshape(B, -1)
+        want = reg.sum() * conv / (30_000 * reg.shape[1])
+        per = reg.sum(axis=1) * conv / (nb * reg.shape[1])
+        want_sd = np.sqrt(((per - want) ** 2).sum() / (B * (B - 1)))
+        m, sd = sim.region_dose(ix0, ix1, iy0, iy1, field=1)
+        assert want > 0 and m == pytest.approx(want, rel=1e-12) and sd == pytest.approx(want_sd, rel=1e-9)
+        with pytest.raises(MCError):
+            sim.region_dose(ix0, ix1, iy0, iy1, field=2)
+    finally:
+        sim.close()
