@@ -75,7 +75,7 @@ struct mc_ctx {
     double vox[3] = {0, 0, 0}, origin[3] = {0, 0, 0};
     int16_t* d_hu = nullptr;
     float* d_rho = nullptr;
-    unsigned char* d_hom = nullptr;   // homogeneity flags of the CT voxels
+    float* d_rho_hom = nullptr;       // CT densities, sign bit set on homogeneous voxels
     int* d_hom_tmp = nullptr;         // two int32 per voxel: scratch of the flag passes
     size_t nvox_alloc = 0;
     unsigned int* d_rho_max = nullptr;
@@ -272,7 +272,7 @@ void make_params(const mc_ctx* c, Params& P, uint64_t seed) {
     P.vx = static_cast<float>(c->vox[0]); P.vy = static_cast<float>(c->vox[1]); P.vz = static_cast<float>(c->vox[2]);
     P.ivx = 1.0f / P.vx; P.ivy = 1.0f / P.vy; P.ivz = 1.0f / P.vz;
     P.rho = c->d_rho;
-    P.hom = c->d_hom;
+    P.rho_hom = c->d_rho_hom;
     for (int m = 0; m < 4; ++m) P.rho_max[m] = c->rho_max[m];
     P.mgM = c->mgM; P.mgx = c->mg[0]; P.mgy = c->mg[1]; P.mgz = c->mg[2];
     P.mgrid = c->d_mgrid;
@@ -324,6 +324,7 @@ void make_params(const mc_ctx* c, Params& P, uint64_t seed) {
     P.w_lnG0 = static_cast<float>(c->tabs.w_lnG0);
     P.w_idx = static_cast<float>(c->tabs.w_inv_dlnG);
     P.seed = seed;
+    P.key = mc::philox_key(seed);
     P.tally = c->d_tally;
     P.energy = c->d_energy;
     P.events = c->d_events;
@@ -1049,7 +1050,7 @@ mc_status mc_destroy(mc_ctx* c) {
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     dfree(c->d_hu);
     dfree(c->d_rho);
-    dfree(c->d_hom);
+    dfree(c->d_rho_hom);
     dfree(c->d_hom_tmp);
     dfree(c->d_rho_max);
     dfree(c->d_thr);
@@ -1095,11 +1096,11 @@ mc_status mc_init_geometry(mc_ctx* c, const int16_t* hu, int nx, int ny, int nz,
     if (nvox > c->nvox_alloc) {
         dfree(c->d_hu);
         dfree(c->d_rho);
-        dfree(c->d_hom);
+        dfree(c->d_rho_hom);
         dfree(c->d_hom_tmp);
         CUDA_TRY(c, cudaMalloc(&c->d_hu, nvox * sizeof(int16_t) + 16));
         CUDA_TRY(c, cudaMalloc(&c->d_rho, nvox * sizeof(float) + 32));
-        CUDA_TRY(c, cudaMalloc(&c->d_hom, nvox + 16));
+        CUDA_TRY(c, cudaMalloc(&c->d_rho_hom, nvox * sizeof(float) + 32));
         CUDA_TRY(c, cudaMalloc(&c->d_hom_tmp, 2 * nvox * sizeof(int)));
         c->nvox_alloc = nvox;
     }
@@ -1107,8 +1108,8 @@ mc_status mc_init_geometry(mc_ctx* c, const int16_t* hu, int nx, int ny, int nz,
                                 hu_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaMemsetAsync(c->d_rho_max, 0, sizeof(unsigned int) * 4, s));
     CUDA_TRY(c, mc::launch_hu_to_rho(c->d_hu, c->d_rho, nvox, c->d_rho_max, c->d_thr, c->sm_count, s));
-    CUDA_TRY(c, mc::launch_homogeneity(c->d_hu, nx, ny, nz, mc::kHomRadius, mc::kHomSpan, c->d_hom_tmp, c->d_hom,
-                                       c->sm_count, s));
+    CUDA_TRY(c, mc::launch_homogeneity(c->d_hu, c->d_rho, nx, ny, nz, mc::kHomRadius, mc::kHomSpan, c->d_hom_tmp,
+                                       c->d_rho_hom, c->sm_count, s));
     unsigned int bits[4];
     CUDA_TRY(c, cudaMemcpyAsync(bits, c->d_rho_max, sizeof(bits), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(c, cudaMemcpyAsync(c->thr, c->d_thr, sizeof(c->thr), cudaMemcpyDeviceToHost, s));

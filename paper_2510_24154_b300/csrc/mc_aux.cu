@@ -271,9 +271,10 @@ __global__ void k_test_philox(const uint32_t* in, uint32_t* out, int n) {
 
 __global__ void k_test_uniforms(unsigned long long seed, unsigned long long hist, uint32_t ord, int n, float* out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const PhiloxKey K = philox_key(seed);
     Rng r;
-    r.setup(seed, hist, ord, 0u);
-    for (int i = 0; i < n; ++i) out[i] = r.u();
+    r.setup(K, hist, ord, 0u);
+    for (int i = 0; i < n; ++i) out[i] = r.u(K);
 }
 
 // ----------------------------------------------------------- launchers ---
@@ -291,14 +292,15 @@ cudaError_t launch_hu_to_rho(const int16_t* hu, float* rho, size_t n, unsigned i
 // the least and greatest value over `radius` voxels either side along `axis`
 // (cut at the CT's edge), packed as (least & 0xffff) | (greatest << 16).  The
 // first pass reads the clamped HU itself; the last turns the box extremes
-// into the flag.  Extremes of a box are the extremes of its rows' extremes,
+// into the flag, written as the sign of the voxel's density.  Extremes of a box are the extremes of its rows' extremes,
 // and materials rise with HU, so one material means that the least and the
 // greatest value have the same material.
 __device__ __forceinline__ int clamp_hu_dev(int h) { return min(max(h, -1024), 3071); }
 __device__ __forceinline__ int material_of_hu(int h) { return (h < -900) ? 0 : (h < -200) ? 1 : (h < 300) ? 2 : 3; }
 
 __global__ void k_hom_pass(const int16_t* __restrict__ hu, const int* __restrict__ in, int nx, int ny, int nz,
-                           int axis, int radius, int span, int* __restrict__ out, unsigned char* __restrict__ flag) {
+                           int axis, int radius, int span, int* __restrict__ out, const float* __restrict__ rho,
+                           float* __restrict__ rho_hom) {
     const size_t n = static_cast<size_t>(nx) * ny * nz;
     const int dim = (axis == 0) ? nx : (axis == 1) ? ny : nz;
     const size_t stride = (axis == 0) ? 1 : (axis == 1) ? static_cast<size_t>(nx) : static_cast<size_t>(nx) * ny;
@@ -321,25 +323,26 @@ __global__ void k_hom_pass(const int16_t* __restrict__ hu, const int* __restrict
             lo = min(lo, a);
             hi = max(hi, b);
         }
-        if (flag) {
+        if (rho_hom) {
             const bool inside = ix >= radius && ix < nx - radius && iy >= radius && iy < ny - radius &&
                                 iz >= radius && iz < nz - radius;
-            flag[v] = (inside && material_of_hu(lo) == material_of_hu(hi) && hi - lo <= span) ? 1 : 0;
+            const bool hom = inside && material_of_hu(lo) == material_of_hu(hi) && hi - lo <= span;
+            rho_hom[v] = __int_as_float(__float_as_int(__ldg(&rho[v])) | (hom ? 0x80000000 : 0));
         } else {
             out[v] = (lo & 0xffff) | (hi << 16);
         }
     }
 }
 
-cudaError_t launch_homogeneity(const int16_t* hu, int nx, int ny, int nz, int radius, int span, int* tmp,
-                               unsigned char* flag, int sm_count, cudaStream_t s) {
+cudaError_t launch_homogeneity(const int16_t* hu, const float* rho, int nx, int ny, int nz, int radius, int span,
+                               int* tmp, float* rho_hom, int sm_count, cudaStream_t s) {
     const size_t n = static_cast<size_t>(nx) * ny * nz;
     int* a = tmp;
     int* b = tmp + n;
     const int grid = sm_count * 8, block = 256;
-    k_hom_pass<<<grid, block, 0, s>>>(hu, nullptr, nx, ny, nz, 0, radius, span, a, nullptr);
-    k_hom_pass<<<grid, block, 0, s>>>(nullptr, a, nx, ny, nz, 1, radius, span, b, nullptr);
-    k_hom_pass<<<grid, block, 0, s>>>(nullptr, b, nx, ny, nz, 2, radius, span, nullptr, flag);
+    k_hom_pass<<<grid, block, 0, s>>>(hu, nullptr, nx, ny, nz, 0, radius, span, a, nullptr, nullptr);
+    k_hom_pass<<<grid, block, 0, s>>>(nullptr, a, nx, ny, nz, 1, radius, span, b, nullptr, nullptr);
+    k_hom_pass<<<grid, block, 0, s>>>(nullptr, b, nx, ny, nz, 2, radius, span, nullptr, rho, rho_hom);
     return cudaGetLastError();
 }
 

@@ -32,12 +32,14 @@ cudaError_t launch_wave_end(Ctl* c, cudaGraphConditionalHandle h, unsigned int m
 
 cudaError_t launch_hu_to_rho(const int16_t* hu, float* rho, size_t n, unsigned int* rho_max_bits, float* thr,
                              int sm_count, cudaStream_t s);
-// Homogeneity flags of the CT for the electron transport: flag[v] = 1 when
-// voxel v lies at least `radius` voxels inside the CT and the (2 radius + 1)^3
+// Homogeneity flags of the CT for the electron transport, stored as the sign
+// bit of a copy of the density (rho_hom[v] = -rho[v] where homogeneous, so one
+// 4-byte load gives an electron entering a voxel both): voxel v is homogeneous
+// when it lies at least `radius` voxels inside the CT and the (2 radius + 1)^3
 // box around it holds one material with HU values (clamped to [-1024, 3071])
 // spanning at most `span`.  tmp: two int32 buffers of n voxels each (scratch).
-cudaError_t launch_homogeneity(const int16_t* hu, int nx, int ny, int nz, int radius, int span, int* tmp,
-                               unsigned char* flag, int sm_count, cudaStream_t s);
+cudaError_t launch_homogeneity(const int16_t* hu, const float* rho, int nx, int ny, int nz, int radius, int span,
+                               int* tmp, float* rho_hom, int sm_count, cudaStream_t s);
 cudaError_t launch_macro_grid(const float* rho, int nx, int ny, int nz, int M, int mgx, int mgy, int mgz,
                               float thr_bone, float2* grid, int sm_count, cudaStream_t s);
 cudaError_t launch_tmap(const TmapArgs& A, double* t, cudaStream_t s);

@@ -98,6 +98,26 @@ struct FieldDev {
     unsigned long long tally_off;
 };
 
+// Philox4x32-10 round keys of one seed: round r uses (k[2r], k[2r+1]) =
+// (seed_lo + r 0x9E3779B9, seed_hi + r 0xBB67AE85).  Kernels get them in their
+// parameters, so the rounds read them as constant operands instead of
+// keeping the key in registers and bumping it every round.
+struct PhiloxKey {
+    uint32_t k[20];
+};
+
+__host__ __device__ inline PhiloxKey philox_key(unsigned long long seed) {
+    PhiloxKey K;
+    uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        K.k[2 * r] = k0;
+        K.k[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return K;
+}
+
 constexpr uint32_t kFieldShift = 8;             // particle flags bits 8..15: field index
 constexpr uint32_t kFieldMask = 0xff00u;
 constexpr int kMaxFields = 256;
@@ -107,7 +127,9 @@ struct Params {
     int nx, ny, nz;
     float ox, oy, oz, vx, vy, vz, ivx, ivy, ivz;
     const float* rho;
-    const unsigned char* hom;      // per voxel: 1 if homogeneous (electron second segments may cross its faces)
+    // per voxel: the density with the sign bit set where the voxel is homogeneous
+    // (electron second segments may cross its faces): one load gives an electron both
+    const float* rho_hom;
     float rho_max[4];
     float thr[3];                   // density thresholds lung / water / bone
     int mgM, mgx, mgy, mgz;         // macro-cells: M voxels per side, cells per axis (<= 4096 cells)
@@ -144,6 +166,7 @@ struct Params {
     float w_lnG0, w_idx;
     // run
     unsigned long long seed;
+    PhiloxKey key;                  // round keys of `seed`
     unsigned long long* tally;      // [n_fields][B][npy][npx]
     unsigned long long* energy;     // [kNumEnergy]
     unsigned long long* events;     // [kNumEvents]
@@ -170,6 +193,16 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKey& K) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ K.k[2 * r], lo1, hi0 ^ c.w ^ K.k[2 * r + 1], lo0);
+    }
+    return c;
+}
+
 __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     h ^= h >> 16; h *= 0x85EBCA6Bu; h ^= h >> 13; h *= 0xC2B2AE35u; h ^= h >> 16;
     return h;
@@ -182,26 +215,23 @@ __device__ __forceinline__ uint32_t child_ordinal(uint32_t parent, uint32_t draw
 struct Rng {
     uint32_t ord, hlo, hhi, d;
     uint32_t w0, w1, w2, w3;
-    uint32_t k0, k1;
 
-    __device__ __forceinline__ void setup(unsigned long long seed, unsigned long long hist, uint32_t o, uint32_t draws) {
-        k0 = static_cast<uint32_t>(seed);
-        k1 = static_cast<uint32_t>(seed >> 32);
+    __device__ __forceinline__ void setup(const PhiloxKey& K, unsigned long long hist, uint32_t o, uint32_t draws) {
         hlo = static_cast<uint32_t>(hist);
         hhi = static_cast<uint32_t>(hist >> 32);
         ord = o;
         d = draws;
-        if (d & 3u) refill();
+        if (d & 3u) refill(K);
     }
-    __device__ __forceinline__ void refill() {
-        const uint4 r = philox4x32_10(make_uint4(d >> 2, ord, hlo, hhi), k0, k1);
+    __device__ __forceinline__ void refill(const PhiloxKey& K) {
+        const uint4 r = philox4x32_10(make_uint4(d >> 2, ord, hlo, hhi), K);
         w0 = r.x; w1 = r.y; w2 = r.z; w3 = r.w;
     }
     // Electron steps and photon flights start on a fresh Philox block, so the
     // lanes of a warp refill together.
     __device__ __forceinline__ void align() { d = (d + 3u) & ~3u; }
-    __device__ __forceinline__ float u() {
-        if ((d & 3u) == 0u) refill();
+    __device__ __forceinline__ float u(const PhiloxKey& K) {
+        if ((d & 3u) == 0u) refill(K);
         const uint32_t j = d & 3u;
         const uint32_t w = (j == 0u) ? w0 : (j == 1u) ? w1 : (j == 2u) ? w2 : w3;
         ++d;
@@ -280,7 +310,7 @@ __device__ __forceinline__ void load_part(const BankPtr& b, uint32_t i, Part& p,
     p.cell = b.cell[i];
     p.flags = b.flags[i];
     const int f = static_cast<int>((p.flags & kFieldMask) >> kFieldShift);
-    p.rng.setup(P.seed, __ldg(&P.fields[f].hist_base) + p.hist, b.ord[i], b.draws[i]);
+    p.rng.setup(P.key, __ldg(&P.fields[f].hist_base) + p.hist, b.ord[i], b.draws[i]);
 }
 
 __device__ __forceinline__ void store_part(const BankPtr& b, uint32_t i, const Part& p) {

@@ -154,9 +154,9 @@ __device__ __forceinline__ void charged(const Params& P, Acc& a, unsigned long l
 // two direction draws.  Encoded as one emission record of count 2.
 template <bool EPID>
 __device__ __forceinline__ void annihilate(const Params& P, unsigned long long* s_events, Part& p, Emit& e) {
-    const float ct = 2.0f * p.rng.u() - 1.0f;
+    const float ct = 2.0f * p.rng.u(P.key) - 1.0f;
     float sp, cp;
-    azimuth_sincos(p.rng.u(), sp, cp);
+    azimuth_sincos(p.rng.u(P.key), sp, cp);
     const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
     e.dest = EPID ? kPhotonEPID : kPhotonCT;
     e.E = kMec2;
@@ -168,13 +168,13 @@ __device__ __forceinline__ void annihilate(const Params& P, unsigned long long* 
 }
 
 // Klein-Nishina composition-rejection; returns eps = E'/E and cos(theta).
-__device__ __forceinline__ void sample_kn(Rng& r, float E, float& eps, float& ct) {
+__device__ __forceinline__ void sample_kn(const PhiloxKey& K, Rng& r, float E, float& eps, float& ct) {
     const float k = E / kMec2;
     const float e0 = 1.0f / (1.0f + 2.0f * k);
     const float a1 = logf(1.0f + 2.0f * k);
     const float a2 = 0.5f * (1.0f - e0 * e0);
     for (int it = 0; it < 4096; ++it) {
-        const float r1 = r.u(), r2 = r.u(), r3 = r.u();
+        const float r1 = r.u(K), r2 = r.u(K), r3 = r.u(K);
         float e;
         if (r1 * (a1 + a2) < a1) e = expf(-a1 * r2);
         else e = sqrtf(e0 * e0 + (1.0f - e0 * e0) * r2);
@@ -187,12 +187,12 @@ __device__ __forceinline__ void sample_kn(Rng& r, float E, float& eps, float& ct
 }
 
 // Moller energy fraction on [wcc/T, 1/2]: 1/eps^2 proposal, rejection on the bracket.
-__device__ __forceinline__ float sample_moller(Rng& r, float T, float wcc) {
+__device__ __forceinline__ float sample_moller(const PhiloxKey& K, Rng& r, float T, float wcc) {
     const float tau = T / kMec2, g = tau + 1.0f;
     const float ec = wcc / T, c = tau / g, bb = (2.0f * tau + 1.0f) / (g * g);
     const float gmax = 2.0f - bb + 0.25f * c * c;
     for (int it = 0; it < 4096; ++it) {
-        const float r1 = r.u(), r2 = r.u();
+        const float r1 = r.u(K), r2 = r.u(K);
         const float eps = ec / (1.0f - r1 * (1.0f - 2.0f * ec));
         const float x = eps / (1.0f - eps);
         const float gv = 1.0f + x * x + c * c * eps * eps - bb * x;
@@ -204,9 +204,9 @@ __device__ __forceinline__ float sample_moller(Rng& r, float T, float wcc) {
 // Source spectrum E = Emax X, X ~ Beta(3/2, 7/2) as G1/(G1+G2) with
 // G1 = Exp + N^2/2 and G2 = 3 Exp + N'^2/2 (one Box-Muller pair), redrawn
 // below the photon cutoff.  Six draws per attempt.
-__device__ __forceinline__ float sample_spectrum(Rng& r, float emax, float pcut) {
+__device__ __forceinline__ float sample_spectrum(const PhiloxKey& K, Rng& r, float emax, float pcut) {
     for (int it = 0; it < 4096; ++it) {
-        const float ua = r.u(), ub = r.u(), uc = r.u(), ud = r.u(), u1 = r.u(), u2 = r.u();
+        const float ua = r.u(K), ub = r.u(K), uc = r.u(K), ud = r.u(K), u1 = r.u(K), u2 = r.u(K);
         const float L = -logf(u1);
         const float c = cospif(2.0f * u2);
         const float g1 = -logf(ua) + L * c * c;
@@ -224,14 +224,14 @@ __device__ __forceinline__ bool photon_interact(const Params& P, Acc& a, unsigne
                                                 unsigned long long* s_events, Part& p, float mc, float mp,
                                                 float mq, Emit& e0, Emit& e1) {
     const float tot = mc + mp + mq;
-    const float xi = p.rng.u();
+    const float xi = p.rng.u(P.key);
     p.flags |= kCollided;
     if (xi * tot < mc) {
         count_event(s_events, kCCompton);
         float eps, ct;
-        sample_kn(p.rng, p.E, eps, ct);
+        sample_kn(P.key, p.rng, p.E, eps, ct);
         float sp, cp;
-        azimuth_sincos(p.rng.u(), sp, cp);
+        azimuth_sincos(p.rng.u(P.key), sp, cp);
         const float E0 = p.E, E1 = eps * E0;
         const float u0 = p.u, v0 = p.v, w0 = p.w;
         rotate_dir(p.u, p.v, p.w, ct, cp, sp);
@@ -254,7 +254,7 @@ __device__ __forceinline__ bool photon_interact(const Params& P, Acc& a, unsigne
     }
     count_event(s_events, kCPair);
     const float avail = p.E - kTwoMec2;
-    const float xu = p.rng.u();
+    const float xu = p.rng.u(P.key);
     const float Tm = xu * avail, Tp = avail - Tm;
     if (P.coupled) {
         charged<EPID>(P, a, s_energy, s_events, p, e0, Tm, p.u, p.v, p.w, 0u, false);
@@ -322,7 +322,7 @@ __device__ __forceinline__ bool photon_ct_event(const Params& P, const float2* t
     }
     const float mul = fmaxf(tot[0], fmaxf(tot[1], tot[2])), mub = tot[3];
     p.rng.align();
-    float tau = -logf(p.rng.u());
+    float tau = -logf(p.rng.u(P.key));
     ++a.flights;
     const int M = P.mgM;
     const float iu = 1.0f / p.u, iv = 1.0f / p.v, iw = 1.0f / p.w;
@@ -390,7 +390,7 @@ __device__ __forceinline__ bool photon_ct_event(const Params& P, const float2* t
     const float rho = __ldg(&P.rho[(static_cast<size_t>(iz) * P.ny + iy) * P.nx + ix]);
     const int m = material_of(P, rho);
     const float tm = (m == 0) ? tot[0] : (m == 1) ? tot[1] : (m == 2) ? tot[2] : tot[3];
-    if (!(p.rng.u() * Sc < rho * tm)) return true;            // virtual
+    if (!(p.rng.u(P.key) * Sc < rho * tm)) return true;      // virtual
     count_event(s_events, kCRealCT);
     p.cell = pack_cell(ix, iy, iz);
     float mc, mp, mq;
@@ -404,7 +404,7 @@ __device__ __forceinline__ bool photon_epid_event(const Params& P, const float2*
                                                   Part& p, Emit& e0, Emit& e1) {
     const PhotonXS xs = photon_xs(tab, P, p.E);
     p.rng.align();
-    float tau = -logf(p.rng.u());
+    float tau = -logf(p.rng.u(P.key));
     ++a.flights;
     for (int guard = 0; guard < 4 * kMaxLayers + 8; ++guard) {
         const int l = static_cast<int>(p.cell);
@@ -524,7 +524,7 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     const float lnT = logf(T);
     // hard bremsstrahlung exists only above wcb: A ln(T / wcb) for T > wcb
     const float Sh = rho * (electron_tab(tab, P, m, lnT).y + mcst.brem * fmaxf(lnT - P.ln_wcb, 0.0f));
-    const float xt = p.rng.u();                 // drawn every step, used when no depth is pending
+    const float xt = p.rng.u(P.key);            // drawn every step, used when no depth is pending
     p.tau = (p.tau > 0.0f) ? p.tau : -logf(xt);
     const float sh = p.tau / Sh;
     // (c) cell face
@@ -533,7 +533,7 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     float s = sE;
     int lim = 0;
     if (sh < s) { s = sh; lim = 1; }
-    const float xh = p.rng.u(), xmu = p.rng.u(), xph = p.rng.u();
+    const float xh = p.rng.u(P.key), xmu = p.rng.u(P.key), xph = p.rng.u(P.key);
     if (EPID ? (sb < s) : (xh * s >= sb)) { s = sb; lim = 2; }
     // multiple-scattering deflection for the distance s, at the mid-step energy
     const float Tg = T - 0.5f * dEt * (s / sE);
@@ -633,20 +633,21 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
         }
         p.cell = nc;
         const size_t v = (static_cast<size_t>(cell_z(nc)) * P.ny + cell_y(nc)) * P.nx + cell_x(nc);
-        rho_c = __ldg(&P.rho[v]);
-        hom_c = __ldg(&P.hom[v]) != 0;
+        const float rh = __ldg(&P.rho_hom[v]);
+        rho_c = fabsf(rh);
+        hom_c = __float_as_int(rh) < 0;
         if (crossed) return true;
     }
     if (!at_event) return true;
     const float lnTn = logf(Tn);
     const float snm = rho * electron_tab(tab, P, m, lnTn).y;
     const float snb = rho * mcst.brem * fmaxf(lnTn - P.ln_wcb, 0.0f);
-    if (!(p.rng.u() * Sh < snm + snb)) return true;             // delta event
-    if (p.rng.u() * (snm + snb) < snm) {
+    if (!(p.rng.u(P.key) * Sh < snm + snb)) return true;      // delta event
+    if (p.rng.u(P.key) * (snm + snb) < snm) {
         count_event(s_events, kCMoller);
-        const float eps = sample_moller(p.rng, Tn, P.wcc);
+        const float eps = sample_moller(P.key, p.rng, Tn, P.wcc);
         float sph, cph;
-        azimuth_sincos(p.rng.u(), sph, cph);
+        azimuth_sincos(p.rng.u(P.key), sph, cph);
         const float W = eps * Tn, Tp = Tn - W;
         const float cs = sqrtf(W * (Tn + 2.0f * kMec2) / (Tn * (W + 2.0f * kMec2)));
         const float cpr = sqrtf(Tp * (Tn + 2.0f * kMec2) / (Tn * (Tp + 2.0f * kMec2)));
@@ -657,7 +658,7 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
         p.E = Tp;
     } else {
         count_event(s_events, kCBrem);
-        const float k = P.wcb * expf(p.rng.u() * logf(Tn / P.wcb));
+        const float k = P.wcb * expf(p.rng.u(P.key) * logf(Tn / P.wcb));
         e0.dest = EPID ? kPhotonEPID : kPhotonCT;
         e0.E = k; e0.u = p.u; e0.v = p.v; e0.w = p.w;
         e0.ord = child_ordinal(p.rng.ord, p.rng.d, 0u);
@@ -748,7 +749,7 @@ __device__ __forceinline__ bool slab_transport(const Params& P, Rng& r, float& x
         const float mq = P.wmat.pair * xs.pair;
         const float tot = mcphys::kWDensity * (mc + mp + mq);
         r.align();
-        const float s = -logf(r.u()) / tot;
+        const float s = -logf(r.u(P.key)) / tot;
         float d = INFINITY;
         if (w < 0.0f) d = (zb - z) / w;
         else if (w > 0.0f) d = (zt - z) / w;
@@ -762,11 +763,11 @@ __device__ __forceinline__ bool slab_transport(const Params& P, Rng& r, float& x
         x = fmaf(s, u, x);
         y = fmaf(s, v, y);
         z = fmaf(s, w, z);
-        const float xi = r.u();
+        const float xi = r.u(P.key);
         if (!(xi * (mc + mp + mq) < mc)) return false;          // photoelectric or pair
         float eps, ct, sp, cp;
-        sample_kn(r, E, eps, ct);
-        azimuth_sincos(r.u(), sp, cp);
+        sample_kn(P.key, r, E, eps, ct);
+        azimuth_sincos(r.u(P.key), sp, cp);
         rotate_dir(u, v, w, ct, cp, sp);
         E *= eps;
         collided = true;
@@ -797,7 +798,7 @@ __device__ __forceinline__ bool start_primary(const Params& P, unsigned long lon
     p.cell = 0u;
     p.tau = 0.0f;
     p.flags = static_cast<uint32_t>(f) << kFieldShift;
-    p.rng.setup(P.seed, F.hist_base + idx, 0u, 0u);
+    p.rng.setup(P.key, F.hist_base + idx, 0u, 0u);
     // phase space 2: photons of the source until one leaves the collimator
     // slabs its rectangle's flags name (none without slabs: the first one)
     float bx = 0.0f, by = 0.0f, bz = F.sad, bu = 0.0f, bv = 0.0f, bw = -1.0f;
@@ -806,15 +807,15 @@ __device__ __forceinline__ bool start_primary(const Params& P, unsigned long lon
         // the first rectangle whose cumulative weight exceeds xi (the last if
         // none does): from the cut point of xi, scanned either way, so the
         // result is exactly that of a binary search over the CDF
-        const double xi = static_cast<double>(p.rng.u());
+        const double xi = static_cast<double>(p.rng.u(P.key));
         const double* cdf = P.cdf + F.rect_off;
         int lo = __ldg(&P.guide[F.rect_off + min(static_cast<int>(xi * F.n_rect), F.n_rect - 1)]);
         while (lo > 0 && xi < __ldg(&cdf[lo - 1])) --lo;
         while (lo < F.n_rect - 1 && xi >= __ldg(&cdf[lo])) ++lo;
         const float4 r = __ldg(&P.rect[F.rect_off + lo]);
-        const float X = r.x + (r.y - r.x) * p.rng.u();
-        const float Y = r.z + (r.w - r.z) * p.rng.u();
-        p.E = (P.mono_e > 0.0f) ? P.mono_e : sample_spectrum(p.rng, P.e_max, P.pcut);
+        const float X = r.x + (r.y - r.x) * p.rng.u(P.key);
+        const float Y = r.z + (r.w - r.z) * p.rng.u(P.key);
+        p.E = (P.mono_e > 0.0f) ? P.mono_e : sample_spectrum(P.key, p.rng, P.e_max, P.pcut);
         const unsigned flag = (F.leaf_t > 0.0f || F.jaw_t > 0.0f) ? __ldg(&P.rflag[F.rect_off + lo]) : 0u;
         const float nb = sqrtf(X * X + Y * Y + F.sad * F.sad);
         bx = 0.0f; by = 0.0f; bz = F.sad;
@@ -963,8 +964,9 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const Params P) {
                 if (TYPE == kElectronCT) {
                     const size_t v = (static_cast<size_t>(cell_z(p.cell)) * P.ny + cell_y(p.cell)) * P.nx +
                                      cell_x(p.cell);
-                    rho_c = __ldg(&P.rho[v]);
-                    hom_c = __ldg(&P.hom[v]) != 0;
+                    const float rh = __ldg(&P.rho_hom[v]);
+                    rho_c = fabsf(rh);
+                    hom_c = __float_as_int(rh) < 0;
                 }
             }
         }
