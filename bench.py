@@ -33,12 +33,13 @@ WORKLOAD = "thorax_imrt_9seg: CT 256x256x128 int16 HU @2mm, 9 MLC segments x 60 
            "EPID 1024x768 @0.39mm (Cu/Gd2O2S/a-Si), k-table 64x32, coupled photon/electron"
 # Per CT electron step, counted by ncu over the CT-electron launch of the
 # timed step of the 2e6-history thorax case (one wave, 36.2 M steps;
-# profiles/electron_ct_small_case.md): executed thread instructions,
-# single-precision operations (FADD + FMUL + 2 FFMA; no packed forms issued)
-# and DRAM bytes read + written.
-INST_PER_ESTEP_CT = 547.6
-FLOPS_PER_ESTEP_CT = 149.8
-DRAM_BYTES_PER_ESTEP_CT = 3.42
+# profiles/electron_ct_small_case.md): executed thread instructions, executed
+# warp instructions, single-precision operations (FADD + FMUL + 2 FFMA; no
+# packed forms issued) and DRAM bytes read + written.
+INST_PER_ESTEP_CT = 566.9
+WARP_INST_PER_ESTEP_CT = 31.45
+FLOPS_PER_ESTEP_CT = 154.7
+DRAM_BYTES_PER_ESTEP_CT = 3.17
 # instruction issue: 148 SMs x 4 schedulers x 32 lanes x 2.032 GHz
 ISSUE_PEAK_TINST = 148 * 4 * 32 * 2.032e9 / 1e12
 # run-control block read back after every wave of a host-driven run
@@ -576,6 +577,7 @@ def main():
         "traffic_note": "ncu DRAM read+write per CT electron step on the 2e6-history case, scaled by the "
                         "steps of one launch here",
         "inst_per_unit": INST_PER_ESTEP_CT, "unit_of_work": "CT electron step",
+        "lanes_per_warp_inst": INST_PER_ESTEP_CT / WARP_INST_PER_ESTEP_CT,
         "units_per_launch": steps_per_launch, "avg_launch_ms": avg_ms,
         "fp32": {"flops_per_unit": FLOPS_PER_ESTEP_CT,
                  "achieved_tflops": flops / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0,

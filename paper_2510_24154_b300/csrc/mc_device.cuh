@@ -465,11 +465,11 @@ __device__ __forceinline__ float2 electron_tab(const float2* tab, const Params& 
 // error below 2e-3 everywhere and 3e-5 on average against the root of the
 // defining equation, the same fixed work on every lane.
 __device__ __forceinline__ float wentzel_A(const float* wtab, const Params& P, float G) {
-    if (G > 13.1223634f) return -1.0f;
-    const float x = (logf(G) - P.w_lnG0) * P.w_idx;
+    const float x = (logf(fminf(G, 13.1223634f)) - P.w_lnG0) * P.w_idx;
     const int i = min(max(__float2int_rd(x), 0), kWentzelNodes - 2);
     const float f = x - static_cast<float>(i);
-    return expf(fmaf(f, wtab[i + 1] - wtab[i], wtab[i]));
+    const float A = expf(fmaf(f, wtab[i + 1] - wtab[i], wtab[i]));
+    return (G > 13.1223634f) ? -1.0f : A;
 }
 
 }  // namespace mc

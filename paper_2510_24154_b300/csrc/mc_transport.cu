@@ -175,9 +175,9 @@ __device__ __forceinline__ void sample_kn(const PhiloxKey& K, Rng& r, float E, f
     const float a2 = 0.5f * (1.0f - e0 * e0);
     for (int it = 0; it < 4096; ++it) {
         const float r1 = r.u(K), r2 = r.u(K), r3 = r.u(K);
-        float e;
-        if (r1 * (a1 + a2) < a1) e = expf(-a1 * r2);
-        else e = sqrtf(e0 * e0 + (1.0f - e0 * e0) * r2);
+        // both branches of the composition are evaluated and one is kept
+        const float ea = expf(-a1 * r2), eb = sqrtf(e0 * e0 + (1.0f - e0 * e0) * r2);
+        const float e = (r1 * (a1 + a2) < a1) ? ea : eb;
         const float t = (1.0f - e) / (k * e);
         const float s2 = t * (2.0f - t);
         const float g = 1.0f - e * s2 / (1.0f + e * e);
@@ -273,30 +273,28 @@ __device__ __forceinline__ bool photon_interact(const Params& P, Acc& a, unsigne
 
 // Distance to leave EPID layer l; which = 0 (layer plane), 1 (x edge), 2 (y edge).
 __device__ __forceinline__ float epid_dist(const Params& P, const Part& p, int l, int& which) {
-    float dz = INFINITY, dx = INFINITY, dy = INFINITY;
-    if (p.w < 0.0f) dz = (P.zp[l + 1] - p.z) / p.w;
-    else if (p.w > 0.0f) dz = (P.zp[l] - p.z) / p.w;
-    if (p.u > 0.0f) dx = (P.hwx - p.x) / p.u;
-    else if (p.u < 0.0f) dx = (-P.hwx - p.x) / p.u;
-    if (p.v > 0.0f) dy = (P.hwy - p.y) / p.v;
-    else if (p.v < 0.0f) dy = (-P.hwy - p.y) / p.v;
+    const float zf = (p.w < 0.0f) ? P.zp[l + 1] : P.zp[l];
+    const float dz = (p.w != 0.0f) ? (zf - p.z) / p.w : INFINITY;
+    const float dx = (p.u != 0.0f) ? ((p.u > 0.0f ? P.hwx : -P.hwx) - p.x) / p.u : INFINITY;
+    const float dy = (p.v != 0.0f) ? ((p.v > 0.0f ? P.hwy : -P.hwy) - p.y) / p.v : INFINITY;
     float d = dz; which = 0;
     if (dx < d) { d = dx; which = 1; }
     if (dy < d) { d = dy; which = 2; }
     return fmaxf(d, 0.0f);
 }
 
-// Distance to the faces of CT voxel `cell`; axis = 0, 1, 2.
+// Distance to the faces of CT voxel `cell`; axis = 0, 1, 2.  Branch-free:
+// the face ahead on each axis is chosen by the sign of the direction, and an
+// axis the direction does not move along is never the nearest.
 __device__ __forceinline__ float ct_dist(const Params& P, const Part& p, uint32_t cell, int& axis) {
-    const int ix = cell_x(cell), iy = cell_y(cell), iz = cell_z(cell);
-    float dx = INFINITY, dy = INFINITY, dz = INFINITY;
-    if (p.u > 0.0f) dx = (P.ox + (ix + 1) * P.vx - p.x) / p.u;
-    else if (p.u < 0.0f) dx = (P.ox + ix * P.vx - p.x) / p.u;
-    if (p.v > 0.0f) dy = (P.oy + (iy + 1) * P.vy - p.y) / p.v;
-    else if (p.v < 0.0f) dy = (P.oy + iy * P.vy - p.y) / p.v;
-    if (p.w > 0.0f) dz = (P.oz + (iz + 1) * P.vz - p.z) / p.w;
-    else if (p.w < 0.0f) dz = (P.oz + iz * P.vz - p.z) / p.w;
-    float d = dx; axis = 0;
+    const int fx = cell_x(cell) + (p.u > 0.0f ? 1 : 0);
+    const int fy = cell_y(cell) + (p.v > 0.0f ? 1 : 0);
+    const int fz = cell_z(cell) + (p.w > 0.0f ? 1 : 0);
+    const float dx = (p.u != 0.0f) ? (P.ox + fx * P.vx - p.x) / p.u : INFINITY;
+    const float dy = (p.v != 0.0f) ? (P.oy + fy * P.vy - p.y) / p.v : INFINITY;
+    const float dz = (p.w != 0.0f) ? (P.oz + fz * P.vz - p.z) / p.w : INFINITY;
+    float d = dx;
+    axis = 0;
     if (dy < d) { d = dy; axis = 1; }
     if (dz < d) { d = dz; axis = 2; }
     return fmaxf(d, 0.0f);
@@ -342,6 +340,14 @@ __device__ __forceinline__ bool photon_ct_event(const Params& P, const float2* t
     float tx = exit_t(cx, sx, P.nx, P.ox, P.vx, x0, p.u, iu);
     float ty = exit_t(cy, sy, P.ny, P.oy, P.vy, y0, p.v, iv);
     float tz = exit_t(cz, sz, P.nz, P.oz, P.vz, z0, p.w, iw);
+    // path length across one whole cell per axis, and where the line leaves
+    // the CT on each axis (no cell's exit lies beyond it)
+    const float dx = static_cast<float>(M) * P.vx * fabsf(iu);
+    const float dy = static_cast<float>(M) * P.vy * fabsf(iv);
+    const float dz = static_cast<float>(M) * P.vz * fabsf(iw);
+    const float ex = exit_t(sx > 0 ? P.mgx - 1 : 0, sx, P.nx, P.ox, P.vx, x0, p.u, iu);
+    const float ey = exit_t(sy > 0 ? P.mgy - 1 : 0, sy, P.ny, P.oy, P.vy, y0, p.v, iv);
+    const float ez = exit_t(sz > 0 ? P.mgz - 1 : 0, sz, P.nz, P.oz, P.vz, z0, p.w, iw);
     float t = 0.0f, Sc = 0.0f;
     const int guard = P.mgx + P.mgy + P.mgz + 3;
     bool inside = false;
@@ -360,21 +366,16 @@ __device__ __forceinline__ bool photon_ct_event(const Params& P, const float2* t
         }
         tau -= Sc * d;
         t = fmaxf(tn, t);
-        bool out;
-        if (ax == 0) {
-            cx += sx;
-            out = cx < 0 || cx >= P.mgx;
-            tx = exit_t(cx, sx, P.nx, P.ox, P.vx, x0, p.u, iu);
-        } else if (ax == 1) {
-            cy += sy;
-            out = cy < 0 || cy >= P.mgy;
-            ty = exit_t(cy, sy, P.ny, P.oy, P.vy, y0, p.v, iv);
-        } else {
-            cz += sz;
-            out = cz < 0 || cz >= P.mgz;
-            tz = exit_t(cz, sz, P.nz, P.oz, P.vz, z0, p.w, iw);
-        }
-        if (out) break;
+        const bool bx = (ax == 0), by = (ax == 1), bz = (ax == 2);
+        cx += bx ? sx : 0;
+        cy += by ? sy : 0;
+        cz += bz ? sz : 0;
+        tx = bx ? fminf(tx + dx, ex) : tx;
+        ty = by ? fminf(ty + dy, ey) : ty;
+        tz = bz ? fminf(tz + dz, ez) : tz;
+        if (static_cast<unsigned>(cx) >= static_cast<unsigned>(P.mgx) ||
+            static_cast<unsigned>(cy) >= static_cast<unsigned>(P.mgy) ||
+            static_cast<unsigned>(cz) >= static_cast<unsigned>(P.mgz)) break;
     }
     p.x = fmaf(t, p.u, x0);
     p.y = fmaf(t, p.v, y0);
@@ -540,11 +541,8 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     const float pc2 = Tg * (Tg + 2.0f * kMec2);
     const float pb2 = pc2 * pc2 / ((Tg + kMec2) * (Tg + kMec2));
     const float G = s * rho * mcst.msc / pb2;
-    float mu = 0.0f;
-    if (G > 0.0f) {
-        const float A = wentzel_A(reinterpret_cast<const float*>(tab + kNumMat * kElectronNodes), P, G);
-        mu = (A < 0.0f) ? xmu : A * xmu / (1.0f - xmu + A);
-    }
+    const float A = wentzel_A(reinterpret_cast<const float*>(tab + kNumMat * kElectronNodes), P, G);
+    const float mu = !(G > 0.0f) ? 0.0f : (A < 0.0f) ? xmu : A * xmu / (1.0f - xmu + A);
     float sp, cp;
     azimuth_sincos(xph, sp, cp);
     const bool face = (lim == 2);
@@ -567,10 +565,12 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     // direction component across the crossed face: in the EPID face 0 is a layer
     // plane (z) and faces 1, 2 are the lateral edges; in the CT faces 0, 1, 2 are x, y, z
     float cdir = EPID ? w0 : (ax == 0) ? u0 : (ax == 1) ? v0 : w0;
-    if (!face) {
+    {
+        // evaluated on every lane (a face step's results are not taken): the
+        // warp runs this part once either way, without a divergent branch
         sb2 = EPID ? epid_dist(P, p, layer, ax2) : ct_dist(P, p, p.cell, ax2);
-        s2 = s - s1;
-        const bool cross = s2 >= sb2;
+        s2 = face ? 0.0f : s - s1;
+        const bool cross = !face && s2 >= sb2;
         if (!EPID) through = leg_through(P, p, p.cell, hom_c, s2, ecell) && cross;
         if (cross && !through) {
             s2 = sb2;
@@ -622,7 +622,9 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
         if (crossed) {
             int ix = cell_x(p.cell), iy = cell_y(p.cell), iz = cell_z(p.cell);
             const int stp = (cdir > 0.0f) ? 1 : -1;
-            if (cax == 0) ix += stp; else if (cax == 1) iy += stp; else iz += stp;
+            ix += (cax == 0) ? stp : 0;
+            iy += (cax == 1) ? stp : 0;
+            iz += (cax == 2) ? stp : 0;
             out = ix < 0 || ix >= P.nx || iy < 0 || iy >= P.ny || iz < 0 || iz >= P.nz;
             nc = pack_cell(ix, iy, iz);
         }
