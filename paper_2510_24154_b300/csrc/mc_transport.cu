@@ -115,15 +115,18 @@ __device__ __forceinline__ bool transfer_to_epid(const Params& P, Part& p, Acc& 
     to_beam(F, p.x, p.y, p.z, bx, by, bz);
     to_beam_dir(F, p.u, p.v, p.w, bu, bv, bw);
     const float eexit = p.E + rest_extra(p.flags);
-    if (bw >= 0.0f) { a.esc += quanta(eexit); return false; }
     const float t = (F.zface - bz) / bw;
     const float X = bx + t * bu, Y = by + t * bv;
-    if (!(fabsf(X) < P.hwx && fabsf(Y) < P.hwy)) { a.esc += quanta(eexit); return false; }
+    // the line meets the detector face going down (branch-free: a particle
+    // that misses it leaves the world and its state is not used again)
+    const bool hit = bw < 0.0f && fabsf(X) < P.hwx && fabsf(Y) < P.hwy;
+    a.esc += hit ? 0ull : quanta(eexit);
     // inside the detector z is measured from its face, where single precision
     // resolves the 0.29 mm phosphor to ~1e-8 cm (at Z = -50 cm it would be 4e-6 cm)
     p.x = X; p.y = Y; p.z = 0.0f;
     p.u = bu; p.v = bv; p.w = bw;
     p.cell = 0u;
+    if (!hit) return false;
     if (is_photon && p.rng.ord == 0u) {
         count_event(s_events, kCPrimAtEPID);
         if (!(p.flags & kCollided)) count_event(s_events, kCUncollided);
@@ -586,21 +589,23 @@ __device__ __forceinline__ bool electron_event(const Params& P, const float2* ta
     // which consumes the optical depth; any other step spends its path
     const bool at_event = (lim == 1) && !crossed;
     p.tau = at_event ? 0.0f : p.tau - (s1 + s2) * Sh;
-    if (Tn <= P.tstop) {
-        deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, p.flags, dE + Tn);
-        if (p.flags & kPositron) {
-            p.x = hx; p.y = hy; p.z = hz; p.cell = hcell;
-            annihilate<EPID>(P, s_events, p, e0);
-        }
-        return false;
-    }
-    if (!EPID && through && P.vox) {
+    // a step that ends at or below the stopping energy deposits what is left
+    // at its hinge (the same deposit as any other step, with Tn added)
+    const bool stop = Tn <= P.tstop;
+    if (!EPID && through && P.vox && !stop) {
         // patient dose: the step's energy split among the voxels of the second segment
         Part hp = p;
         hp.x = hx; hp.y = hy; hp.z = hz;
         leg_deposit(P, a, hp, hcell, ecell, s2, sb2, ax2, s1, dE);
     } else {
-        deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, p.flags, dE);
+        deposit<EPID>(P, a, s_energy, hcell, hx, hy, p.hist, p.flags, stop ? dE + Tn : dE);
+    }
+    if (stop) {
+        if (p.flags & kPositron) {
+            p.x = hx; p.y = hy; p.z = hz; p.cell = hcell;
+            annihilate<EPID>(P, s_events, p, e0);
+        }
+        return false;
     }
     p.E = Tn;
     if (EPID && crossed) {
