@@ -36,10 +36,10 @@ WORKLOAD = "thorax_imrt_9seg: CT 256x256x128 int16 HU @2mm, 9 MLC segments x 60 
 # profiles/electron_ct_small_case.md): executed thread instructions, executed
 # warp instructions, single-precision operations (FADD + FMUL + 2 FFMA; no
 # packed forms issued) and DRAM bytes read + written.
-INST_PER_ESTEP_CT = 566.9
-WARP_INST_PER_ESTEP_CT = 31.45
-FLOPS_PER_ESTEP_CT = 154.7
-DRAM_BYTES_PER_ESTEP_CT = 3.17
+INST_PER_ESTEP_CT = 532.4
+WARP_INST_PER_ESTEP_CT = 28.90
+FLOPS_PER_ESTEP_CT = 155.7
+DRAM_BYTES_PER_ESTEP_CT = 3.09
 # instruction issue: 148 SMs x 4 schedulers x 32 lanes x 2.032 GHz
 ISSUE_PEAK_TINST = 148 * 4 * 32 * 2.032e9 / 1e12
 # run-control block read back after every wave of a host-driven run
