@@ -112,6 +112,7 @@ def test_conv_backward_data_parity(case):
     dict(N=1, H=3, W=64, c0=32, c1=0, co=1, k=1),
     dict(N=1, H=6, W=128, c0=128, c1=0, co=256, k=3),
     dict(N=1, H=3, W=136, c0=8, c1=0, co=32, k=3),
+    dict(N=2, H=3, W=70, c0=64, c1=0, co=128, k=3),
 ])
 def test_conv_backward_weights_parity(case):
     r = np.random.default_rng(3)
