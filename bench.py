@@ -41,8 +41,9 @@ WARP_INST_PER_ESTEP_CT = 28.90
 FLOPS_PER_ESTEP_CT = 155.7
 DRAM_BYTES_PER_ESTEP_CT = 3.09
 # The same launch under ncu --set full (profiles/electron_ct_small_case.md):
-# fraction of scheduler cycles that issued a warp instruction, and warps
-# resident per scheduler out of 16.
+# fraction of scheduler cycles that issued a warp instruction, and the
+# fraction of the SM's 64 warp slots occupied (at most 0.5 here: 4 CTAs of
+# 256 threads, register-limited).
 NCU_ISSUE_ACTIVE_ECT = 0.652
 NCU_WARPS_ACTIVE_ECT = 0.456
 # instruction issue: 148 SMs x 4 schedulers x 32 lanes x 2.032 GHz
@@ -585,7 +586,7 @@ def main():
         "lanes_per_warp_inst": INST_PER_ESTEP_CT / WARP_INST_PER_ESTEP_CT,
         "ncu_issue_active": NCU_ISSUE_ACTIVE_ECT, "ncu_warps_active": NCU_WARPS_ACTIVE_ECT,
         "ncu_note": "ncu --set full of this kernel on the 2e6-history case: scheduler cycles that issued, "
-                    "resident warps of the SM's maximum (4 CTAs of 256 threads, register-limited)",
+                    "occupied warp slots of the SM's 64 (at most 0.5: 4 CTAs of 256 threads, register-limited)",
         "units_per_launch": steps_per_launch, "avg_launch_ms": avg_ms,
         "fp32": {"flops_per_unit": FLOPS_PER_ESTEP_CT,
                  "achieved_tflops": flops / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0,
